@@ -1,0 +1,317 @@
+/*
+ * spsvm.h -- C ABI of libspsvm.so, a GB300 (sm_103a) implementation of the
+ * sparse primal kernel SVM (SP-SVM) of "Parallel Support Vector Machines in
+ * Practice" (Tyree, Gardner, Weinberger, Agrawal, Tran), Section 4,
+ * "Sparse primal optimization", Eq. 4.
+ *
+ * Problem.  Given points x_1..x_n in R^d with labels y_i in {-1,+1}, an RBF
+ * kernel k(x,z) = exp(-gamma ||x-z||^2) (Section 2) and lambda = 1/C, find a
+ * basis J (indices of training points, grown greedily) and coefficients
+ * beta minimising
+ *     f(beta) = lambda/2 beta^T K_JJ beta + 1/2 sum_i max(0, 1 - y_i o_i)^2,
+ *     o = K_nJ beta,
+ * which is Eq. 4 divided by C with the bias dropped (Section 2 omits b).
+ *
+ * Conventions for every entry point below.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory on the current device; "host" pointers are ordinary memory.
+ *  - Matrices of points are row-major: element (i, k) of X is X[i*ldx + k],
+ *    ldx >= d.  Float data are IEEE binary32 unless stated.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Step-level calls only enqueue work; they do not
+ *    synchronise unless stated.
+ *  - Every call returns SPSVM_OK (0) or a negative status code; no C++
+ *    exception crosses the ABI.  spsvm_last_error() gives a message for the
+ *    last failure on the calling thread.
+ *  - Nothing here allocates device memory except spsvm_fit with a NULL
+ *    workspace, spsvm_model_* (the model's own basis copy) and the
+ *    batched / server entry points, which say so.
+ */
+#ifndef SPSVM_H
+#define SPSVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPSVM_OK               0
+#define SPSVM_ERR_ARG         (-1)  /* invalid argument (shape, pointer, value) */
+#define SPSVM_ERR_OOM         (-2)  /* workspace too small or allocation failed */
+#define SPSVM_ERR_NOT_PD      (-3)  /* Newton matrix not positive definite after one shifted retry */
+#define SPSVM_ERR_NO_CONVERGE (-4)  /* max Newton steps reached; a model is still returned */
+#define SPSVM_ERR_CUDA        (-5)  /* CUDA runtime or launch error */
+#define SPSVM_ERR_TIMEOUT     (-6)  /* bounded device wait gave up */
+#define SPSVM_ERR_BUSY        (-7)  /* server: request not admitted yet */
+
+/* ---- arithmetic forms -------------------------------------------------- */
+/* SPSVM_FP32: kernel block and Gram matrix in FP32 SIMT arithmetic, kernel
+ *   matrix stored in FP32.
+ * SPSVM_BF16X3: kernel block and Gram matrix on tcgen05 tensor cores with
+ *   each FP32 operand split as hi + lo (both BF16) and the three products
+ *   hi*hi + hi*lo + lo*hi accumulated in FP32; kernel matrix stored as the
+ *   BF16 hi and lo planes.
+ * In both forms the Cholesky factorisation, triangular solves and the
+ * refinement of the Newton direction run in FP64. */
+#define SPSVM_FP32    0
+#define SPSVM_BF16X3  1
+
+/* ---- stored kernel matrix ---------------------------------------------- */
+/* K_nJ stored basis-major: row j (one basis vector) holds k(x_i, x_{J_j})
+ * for i = 0..n-1 contiguously.  FP32: element (j, i) at
+ * ((float*)data)[j*ld + i].  BF16X3: hi plane at ((uint16_t*)data)[j*ld + i],
+ * lo plane at ((uint16_t*)data)[plane + j*ld + i]; value = hi + lo.
+ * ld and plane are in elements; ld >= n, ld % 8 == 0, data 16-byte aligned. */
+typedef struct spsvm_kmat {
+  void*   data;     /* device */
+  int32_t format;   /* SPSVM_FP32 or SPSVM_BF16X3 */
+  int32_t pad_;
+  int64_t n;        /* points (columns of the stored matrix) */
+  int64_t rows;     /* basis vectors stored */
+  int64_t ld;       /* elements between consecutive rows */
+  int64_t plane;    /* elements between hi and lo planes (BF16X3 only) */
+} spsvm_kmat;
+
+/* Points prepared once per X: squared norms and, for SPSVM_BF16X3, the BF16
+ * split planes (hi = bf16(x), lo = bf16(x - hi)), each n x ldh with the
+ * columns d..ldh-1 zero.  All pointers device; X is borrowed. */
+typedef struct spsvm_points {
+  const float* X;   /* device, n x d row-major, leading dimension ldx */
+  int64_t n, d, ldx;
+  float*    norms;  /* device, n: ||x_i||^2 (FP64 accumulation, rounded) */
+  uint16_t* hi;     /* device, n x ldh, or NULL for SPSVM_FP32 */
+  uint16_t* lo;     /* device, n x ldh, or NULL */
+  int64_t   ldh;    /* multiple of 64, >= d */
+} spsvm_points;
+
+/* ======================================================================= */
+/* Step-level entry points: one per step of the fit, in the order a Newton */
+/* growth round runs them.  The fit below is built from exactly these.    */
+/* ======================================================================= */
+
+/* Row norms ||x_i||^2 of the RBF distance expansion
+ * ||x - z||^2 = ||x||^2 + ||z||^2 - 2 x^T z (Section 2, RBF kernel); and for
+ * precision == SPSVM_BF16X3 the hi/lo planes.  Fills p->norms (and p->hi,
+ * p->lo), which the caller allocated.  Errors: ARG if a pointer is NULL or
+ * n < 0, d < 1, ldx < d, ldh < d or ldh % 64 != 0. */
+int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* stream);
+
+/* Kernel block (Section 2 RBF; Section 4: K_nJ, O(|J| n) memory):
+ *   out row (row0 + c), column i  =  exp(-gamma * max(0, ||x_i||^2 +
+ *   ||x_{idx[c]}||^2 - 2 x_i^T x_{idx[c]}))   for c < m, i < n.
+ * idx: device, m indices into the points.  out->format selects FP32 or
+ * BF16X3 storage and must match `precision` (SPSVM_FP32 arithmetic may store
+ * either).  Requires row0 + m <= out->rows.  Errors: ARG. */
+int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int32_t m,
+                       float gamma, int32_t precision, spsvm_kmat* out,
+                       int64_t row0, void* stream);
+
+/* Basis-vector selection score (Section 4, "Basis vector selection": a
+ * heuristic estimate of the loss reduction from adding each sampled
+ * point).  For each candidate c = idx[k]:
+ *   g_k = lambda * o[c] + sum_{i in S} (o_i - y_i) K_ic,
+ *   h_k = lambda * 1   + sum_{i in S} K_ic^2,      (K_cc = 1 for RBF)
+ *   delta_k = g_k^2 / (2 h_k),
+ * with S = {i : y_i o_i < 1} and o = K_nJ beta (so o[c] = k_cJ beta).
+ * This is the second-order estimate of the decrease of f from a new
+ * coefficient beta_c started at 0.  Kernel values are computed in
+ * `precision` and reduced without being stored.
+ * y, o: device, n.  idx: device, kappa.  g, h, delta: device, kappa (FP64).
+ * scratch: device, at least spsvm_score_scratch_bytes(n, kappa) bytes.
+ * Errors: ARG, OOM (scratch too small). */
+size_t spsvm_score_scratch_bytes(int64_t n, int32_t kappa);
+int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o,
+                           const int64_t* idx, int32_t kappa, float gamma,
+                           double lambda, int32_t precision, double* g, double* h,
+                           double* delta, void* scratch, size_t scratch_bytes,
+                           void* stream);
+
+/* Outputs and active set (Eq. 4): o = K_nJ beta (FP32 result, products in
+ * FP32, sums of 32 terms promoted to FP64); active[i] = (y_i o_i < 1);
+ * stats[0] = 1/2 sum_i max(0, 1 - y_i o_i)^2, stats[1] = #{y_i o_i <= 0},
+ * stats[2] = |S|.  beta: device FP64, K->rows entries.  If beta is NULL, o
+ * is taken as given (not recomputed) and only flags/stats are produced.
+ * o, y: device n.  active: device n bytes.  stats: device 3 doubles.
+ * scratch: device, spsvm_reduce_scratch_bytes(n) bytes. */
+size_t spsvm_reduce_scratch_bytes(int64_t n);
+int spsvm_outputs(const spsvm_kmat* K, const double* beta, const float* y,
+                  float* o, uint8_t* active, double* stats, void* scratch,
+                  size_t scratch_bytes, void* stream);
+
+/* Forward product u = K_nJ v (Eq. 4's o = K_nJ beta for any v; used for
+ * the line-search direction u = K_nJ d).  v: device FP64 (K->rows);
+ * u: device FP32 (n).  If `accumulate`, u += K_nJ v instead. */
+int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_t accumulate,
+               void* stream);
+
+/* Active-set compaction and masked transposed products (gradient of
+ * Eq. 4: grad f = lambda K_JJ beta + K_SJ^T (o_S - y_S); Newton right-hand
+ * side r = K_SJ^T y_S):
+ *   pos[i]  = number of active points before i (exclusive scan);
+ *   Kc row j, column pos[i] = K row j, column i   for active i (if Kc != NULL),
+ *             zero-filled up to Kc->n (a multiple of 128);
+ *   w1out_j = sum_{i active} w1_i K_ji,  w2out_j = sum_{i active} w2_i K_ji
+ *   (each optional: NULL skips it).
+ * active: device n bytes; w1, w2: device FP32 n; outputs device FP64.
+ * n_active: device int64, written with |S|.  Kc must have the format of K,
+ * the same rows and Kc->n >= |S| rounded up to 128 (Kc->n = round_up(n,128)
+ * is always enough).  scratch: spsvm_compact_scratch_bytes(n, K->rows). */
+size_t spsvm_compact_scratch_bytes(int64_t n, int64_t rows);
+int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active,
+                         const float* w1, const float* w2, double* w1out,
+                         double* w2out, spsvm_kmat* Kc, int64_t* n_active,
+                         int32_t* pos, void* scratch, size_t scratch_bytes,
+                         void* stream);
+
+/* Masked Gram matrix (the generalised Hessian of Eq. 4 on the active set):
+ *   H = lambda * K_JJ + Kc^T Kc,   Kc = K_SJ (compacted, rows = basis),
+ * where K_JJ[a][b] = K row b at column J[a] (symmetrised).  The
+ * contraction over the first ns columns of Kc runs in `precision` with FP32
+ * partial sums per slice of 8192 points, combined in FP64.  H: device FP64,
+ * m x m, leading dimension ldh, both triangles written.  J: device int64, m.
+ * scratch: spsvm_gram_scratch_bytes(m, ns). */
+size_t spsvm_gram_scratch_bytes(int64_t m, int64_t ns);
+int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
+               const spsvm_kmat* K, const int64_t* J, double lambda,
+               int32_t precision, double* H, int64_t ldh, void* scratch,
+               size_t scratch_bytes, void* stream);
+
+/* FP64 Cholesky factorisation H = L L^T in place (lower triangle; the
+ * strict upper triangle is not referenced), the direct solver of the Newton
+ * system of Section 4's reoptimisation.  info: device int32, 0 on success,
+ * else k+1 for the first non-positive pivot k.  Synchronous only in that
+ * info is written by the last kernel; read it after a stream sync. */
+int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* stream);
+
+/* Solves L L^T x = b in place (b overwritten by x), FP64.  L from
+ * spsvm_cholesky.  b: device FP64, m. */
+int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b,
+                         void* stream);
+
+/* Exact line search along a Newton direction (f is convex and piecewise
+ * quadratic along a line; Section 4's Newton reoptimisation):
+ *   phi'(t) = a0 + a1 t - sum_i v_i max(0, m_i - t v_i),
+ *   m_i = 1 - y_i o_i, v_i = y_i u_i, a0 = lambda d^T o_J, a1 = lambda d^T u_J,
+ * where o_J, u_J are o, u at the basis points (K_JJ beta = o_J).  Returns in
+ * *t_host (and t_dev if not NULL) the smallest t >= 0 with phi'(t) = 0,
+ * found by bracketing on a 33-point grid and solving the linear piece
+ * exactly once a grid cell holds no breakpoint m_i / v_i; t = 1 if
+ * |phi'(1)| <= 1e-6 |phi'(0)|.  d: device FP64 (m); J: device int64 (m).
+ * Synchronises the stream.  scratch: spsvm_line_scratch_bytes(n). */
+size_t spsvm_line_scratch_bytes(int64_t n);
+int spsvm_line_search(const float* o, const float* u, const float* y, int64_t n,
+                      const double* d, const int64_t* J, int32_t m, double lambda,
+                      double* t_host, double* t_dev, void* scratch,
+                      size_t scratch_bytes, void* stream);
+
+/* Decision values (Section 4, h(x) = w^T phi(x) restricted to the basis):
+ *   out[i] = sum_{j<m} beta_j exp(-gamma ||q_i - b_j||^2)
+ * for query rows q (nq x d, ldq) and basis rows b (m x d, ldb), computed
+ * tile by tile without storing the kernel block.  beta FP64; out FP32.
+ * All device.  scratch: spsvm_decision_scratch_bytes(nq, m, d). */
+size_t spsvm_decision_scratch_bytes(int64_t nq, int64_t m, int64_t d);
+int spsvm_decision(const float* B, int64_t m, int64_t ldb, const double* beta,
+                   const float* Q, int64_t nq, int64_t ldq, int64_t d, float gamma,
+                   int32_t precision, float* out, void* scratch,
+                   size_t scratch_bytes, void* stream);
+
+/* ======================================================================= */
+/* Whole fit and prediction                                                */
+/* ======================================================================= */
+
+typedef struct spsvm_model spsvm_model;   /* opaque, owned by the library */
+
+/* Options; an all-zero struct selects every default. */
+typedef struct spsvm_options {
+  int32_t  candidates;     /* kappa, points sampled per selection round (0 -> 256) */
+  int32_t  add_per_round;  /* q, basis vectors added per round (0 -> 64) */
+  int32_t  max_newton;     /* Newton steps per reoptimisation (0 -> 50) */
+  int32_t  precision;      /* SPSVM_FP32 (0) or SPSVM_BF16X3 */
+  double   growth_tol;     /* Section 4 stop: (change in training error rate) /
+                              (vectors added) < growth_tol; 0 -> run to budget.
+                              Section 5 uses 5e-6. */
+  double   rel_tol;        /* also stop Newton when ||grad|| <= rel_tol ||r||
+                              (0 -> 1e-6 FP32, 2e-5 BF16X3) */
+  uint64_t seed;           /* candidate draw: counter-based splitmix64 */
+  const int64_t* initial_basis;  /* host, n_initial indices (fixed basis), or NULL */
+  int32_t  n_initial;
+  int32_t  fixed_basis;    /* nonzero: no growth rounds (J = initial_basis) */
+  int32_t  refine;         /* iterative-refinement sweeps per Newton step (0 -> 1, <0 -> none) */
+  int32_t  record;         /* keep candidates / chosen per round for replay checks */
+  void*    stream;         /* cudaStream_t for all work (NULL = default stream) */
+} spsvm_options;
+
+/* Per-Newton-step record (kept for every fit). */
+typedef struct spsvm_step {
+  int32_t basis;           /* |J| during the step */
+  int32_t active;          /* |S| before the step */
+  double  gnorm;           /* ||grad f|| before the step */
+  double  t;               /* line-search step taken (0 for the final check) */
+  double  loss;            /* 1/2 sum max(0, 1 - y o)^2 after the step */
+  int32_t errors;          /* #{y_i o_i <= 0} after the step */
+  int32_t pad_;
+} spsvm_step;
+
+/* Device bytes the fit needs for n points in d dimensions and the budget;
+ * the fit lays out all its buffers inside one workspace of this size. */
+size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_budget,
+                                 const spsvm_options* opt);
+
+/* Trains SP-SVM (Section 4): cycles basis-vector selection (kappa random
+ * candidates from the points not in J, scored as in
+ * spsvm_score_candidates, the q best appended) and reoptimisation of Eq. 4
+ * by Newton steps with exact line search, until |J| = basis_budget or the
+ * growth stop fires.  X: device, n x d (ldx); y: device, n values +-1.
+ * gamma > 0, lambda > 0, 1 <= basis_budget <= n.  Newton stops at
+ * ||grad|| <= max(tol, rel_tol ||r||), when the active set repeats after a
+ * full step, or at max_newton.  workspace: device, spsvm_fit_workspace_bytes
+ * bytes, or NULL to let the library allocate (and free) it.  On success
+ * *out is a self-contained model (basis rows copied).  Returns OK,
+ * NO_CONVERGE (model still returned), or an error (no model).
+ * X and y are borrowed for the duration of the call only. */
+int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
+              float gamma, double lambda, int32_t basis_budget, double tol,
+              const spsvm_options* opt, void* workspace, size_t workspace_bytes,
+              spsvm_model** out);
+
+/* Decision values for nq query rows (device, nq x d, ldq) into decision
+ * (device FP32, nq); label = +1 if decision >= 0 else -1. */
+int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
+                  float* decision, void* stream);
+
+/* Model facts.  Any output pointer may be NULL. */
+int spsvm_model_info(const spsvm_model* model, int32_t* n_basis, int64_t* d,
+                     float* gamma, double* lambda, double* objective,
+                     int32_t* newton_steps, int32_t* rounds, int32_t* status);
+/* Copies J (host int64, n_basis) and beta (host FP64, n_basis). */
+int spsvm_model_get(const spsvm_model* model, int64_t* basis_idx, double* beta);
+/* Per-step history: copies min(cap, steps) records; *count = steps. */
+int spsvm_model_history(const spsvm_model* model, spsvm_step* out, int32_t cap,
+                        int32_t* count);
+/* Round r's candidate list and chosen list (record = 1 only). */
+int spsvm_model_round(const spsvm_model* model, int32_t r, int64_t* candidates,
+                      int32_t* n_candidates, int64_t* chosen, int32_t* n_chosen);
+/* Final training outputs o = K_nJ beta (host FP32, n) as the fit left them. */
+int spsvm_model_outputs(const spsvm_model* model, float* o, int64_t n);
+void spsvm_free(spsvm_model* model);
+
+/* Candidate draw used by the fit (exported so that checks can reproduce
+ * it): the points not in J in increasing order, then a partial
+ * Fisher-Yates shuffle whose k-th swap partner is k + R mod (m - k), with
+ * R = splitmix64 finaliser of seed + (counter + 1) * 0x9E3779B97F4A7C15,
+ * counter = round * 2^32 + k.  J, out: host.  Returns the count drawn. */
+int32_t spsvm_draw_candidates(int64_t n, const int64_t* J, int32_t nJ, int32_t kappa,
+                              uint64_t seed, uint32_t round, int64_t* out);
+
+const char* spsvm_strerror(int code);
+const char* spsvm_last_error(void);
+/* Library version string and the SM architecture it was compiled for. */
+const char* spsvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPSVM_H */

@@ -1,0 +1,365 @@
+"""Python face of the C ABI: the same entry-point names as include/spsvm.h,
+taking torch tensors for device memory and the current torch CUDA stream.
+Only argument marshalling happens here."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import (SPSVM_BF16X3, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
+                   spsvm_kmat, spsvm_options, spsvm_points, spsvm_step)
+
+
+def _lib():
+    return L.load()
+
+
+def _prec(p):
+    if isinstance(p, str):
+        return L.PRECISIONS[p]
+    return int(p)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+
+
+# ---------------------------------------------------------------- points
+@dataclass
+class Points:
+    """Prepared points (spsvm_points) with the buffers that back it."""
+    X: torch.Tensor
+    norms: torch.Tensor
+    hi: torch.Tensor | None
+    lo: torch.Tensor | None
+    ldh: int
+
+    def struct(self):
+        s = spsvm_points()
+        s.X = ptr(self.X)
+        s.n, s.d = self.X.shape
+        s.ldx = self.X.stride(0)
+        s.norms = ptr(self.norms)
+        s.hi = ptr(self.hi)
+        s.lo = ptr(self.lo)
+        s.ldh = self.ldh
+        return s
+
+
+def spsvm_prepare_points(X: torch.Tensor, precision="fp32") -> Points:
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.stride(1) == 1
+    n, d = X.shape
+    ldh = ((d + 63) // 64) * 64
+    p = _prec(precision)
+    norms = torch.empty(n, dtype=torch.float32, device=X.device)
+    hi = lo = None
+    if p == SPSVM_BF16X3:
+        hi = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
+        lo = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
+    P = Points(X, norms, hi, lo, ldh)
+    s = P.struct()
+    check(_lib().spsvm_prepare_points(C.byref(s), p, stream_ptr()), "spsvm_prepare_points")
+    return P
+
+
+# ---------------------------------------------------------------- K storage
+@dataclass
+class KMat:
+    """A stored kernel matrix (spsvm_kmat) backed by a torch tensor."""
+    buf: torch.Tensor
+    format: int
+    n: int
+    rows: int
+    ld: int
+    plane: int
+
+    def struct(self, rows=None):
+        s = spsvm_kmat()
+        s.data = ptr(self.buf)
+        s.format = self.format
+        s.n = self.n
+        s.rows = self.rows if rows is None else rows
+        s.ld = self.ld
+        s.plane = self.plane
+        return s
+
+    def to_float(self, rows=None):
+        """FP32 copy of rows x n (hi + lo for BF16X3), on the device."""
+        r = self.rows if rows is None else rows
+        if self.format == SPSVM_FP32:
+            return self.buf.view(-1)[: r * self.ld].view(r, self.ld)[:, : self.n].clone()
+        flat = self.buf.view(-1)
+        hi = flat[: r * self.ld].view(r, self.ld)[:, : self.n].float()
+        lo = flat[self.plane: self.plane + r * self.ld].view(r, self.ld)[:, : self.n].float()
+        return hi + lo
+
+
+def kmat_empty(n, rows, precision="fp32", device="cuda", ld=None):
+    p = _prec(precision)
+    ld = ld if ld is not None else ((n + 127) // 128) * 128
+    if p == SPSVM_FP32:
+        buf = torch.zeros(max(1, rows * ld), dtype=torch.float32, device=device)
+        return KMat(buf, p, n, rows, ld, 0)
+    plane = rows * ld
+    buf = torch.zeros(max(1, 2 * plane), dtype=torch.bfloat16, device=device)
+    return KMat(buf, p, n, rows, ld, plane)
+
+
+def spsvm_kernel_block(P: Points, idx: torch.Tensor, gamma, precision, out: KMat, row0=0):
+    s = P.struct()
+    k = out.struct()
+    check(_lib().spsvm_kernel_block(C.byref(s), ptr(idx), int(idx.numel()), float(gamma),
+                                    _prec(precision), C.byref(k), int(row0), stream_ptr()),
+          "spsvm_kernel_block")
+    return out
+
+
+def spsvm_score_candidates(P: Points, y, o, idx, gamma, lam, precision):
+    n = P.X.shape[0]
+    kappa = int(idx.numel())
+    dev = P.X.device
+    g = torch.empty(kappa, dtype=torch.float64, device=dev)
+    h = torch.empty_like(g)
+    delta = torch.empty_like(g)
+    sb = _lib().spsvm_score_scratch_bytes(n, kappa)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=dev)
+    s = P.struct()
+    check(_lib().spsvm_score_candidates(C.byref(s), ptr(y), ptr(o), ptr(idx), kappa, float(gamma),
+                                        float(lam), _prec(precision), ptr(g), ptr(h), ptr(delta),
+                                        ptr(scratch), sb, stream_ptr()),
+          "spsvm_score_candidates")
+    return g, h, delta
+
+
+def spsvm_outputs(K: KMat, beta, y, o, rows=None):
+    n = K.n
+    dev = y.device
+    active = torch.empty(n, dtype=torch.uint8, device=dev)
+    stats = torch.empty(3, dtype=torch.float64, device=dev)
+    sb = _lib().spsvm_reduce_scratch_bytes(n)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=dev)
+    k = K.struct(rows)
+    check(_lib().spsvm_outputs(C.byref(k), ptr(beta), ptr(y), ptr(o), ptr(active), ptr(stats),
+                               ptr(scratch), sb, stream_ptr()), "spsvm_outputs")
+    return active, stats
+
+
+def spsvm_gemv(K: KMat, v, u, accumulate=False, rows=None):
+    k = K.struct(rows)
+    check(_lib().spsvm_gemv(C.byref(k), ptr(v), ptr(u), int(bool(accumulate)), stream_ptr()),
+          "spsvm_gemv")
+    return u
+
+
+def spsvm_compact_active(K: KMat, active, w1=None, w2=None, Kc: KMat | None = None, rows=None):
+    n = K.n
+    r = K.rows if rows is None else rows
+    dev = active.device
+    w1o = torch.empty(max(1, r), dtype=torch.float64, device=dev) if w1 is not None else None
+    w2o = torch.empty(max(1, r), dtype=torch.float64, device=dev) if w2 is not None else None
+    nact = torch.zeros(1, dtype=torch.int64, device=dev)
+    pos = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+    sb = _lib().spsvm_compact_scratch_bytes(n, r)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=dev)
+    k = K.struct(rows)
+    kc = Kc.struct(rows) if Kc is not None else None
+    check(_lib().spsvm_compact_active(C.byref(k), ptr(active), ptr(w1), ptr(w2), ptr(w1o), ptr(w2o),
+                                      C.byref(kc) if kc is not None else None, ptr(nact), ptr(pos),
+                                      ptr(scratch), sb, stream_ptr()), "spsvm_compact_active")
+    return w1o, w2o, nact, pos
+
+
+def spsvm_gram(Kc: KMat, nact, ns_max, K: KMat, J, lam, precision, rows=None):
+    m = K.rows if rows is None else rows
+    dev = J.device
+    H = torch.empty((max(1, m), max(1, m)), dtype=torch.float64, device=dev)
+    sb = _lib().spsvm_gram_scratch_bytes(m, ns_max)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=dev)
+    kc = Kc.struct(rows)
+    k = K.struct(rows)
+    check(_lib().spsvm_gram(C.byref(kc), ptr(nact), int(ns_max), C.byref(k), ptr(J), float(lam),
+                            _prec(precision), ptr(H), H.stride(0), ptr(scratch), sb, stream_ptr()),
+          "spsvm_gram")
+    return H[:m, :m]
+
+
+def spsvm_cholesky(H: torch.Tensor):
+    """In-place lower Cholesky factor of H (FP64, square); returns info."""
+    m = H.shape[0]
+    info = torch.zeros(1, dtype=torch.int32, device=H.device)
+    check(_lib().spsvm_cholesky(ptr(H), m, H.stride(0), ptr(info), stream_ptr()), "spsvm_cholesky")
+    return int(info.item())
+
+
+def spsvm_cholesky_solve(Lf: torch.Tensor, b: torch.Tensor):
+    check(_lib().spsvm_cholesky_solve(ptr(Lf), Lf.shape[0], Lf.stride(0), ptr(b), stream_ptr()),
+          "spsvm_cholesky_solve")
+    return b
+
+
+def spsvm_line_search(o, u, y, d, J, lam):
+    n = o.numel()
+    sb = _lib().spsvm_line_scratch_bytes(n)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=o.device)
+    t = C.c_double(0.0)
+    check(_lib().spsvm_line_search(ptr(o), ptr(u), ptr(y), n, ptr(d), ptr(J), int(J.numel()),
+                                   float(lam), C.byref(t), None, ptr(scratch), sb, stream_ptr()),
+          "spsvm_line_search")
+    return t.value
+
+
+def spsvm_decision(B, beta, Q, gamma, precision="fp32"):
+    m, d = B.shape
+    nq = Q.shape[0]
+    out = torch.empty(nq, dtype=torch.float32, device=Q.device)
+    sb = _lib().spsvm_decision_scratch_bytes(nq, m, d)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=Q.device)
+    check(_lib().spsvm_decision(ptr(B), m, B.stride(0), ptr(beta), ptr(Q), nq, Q.stride(0), d,
+                                float(gamma), _prec(precision), ptr(out), ptr(scratch), sb,
+                                stream_ptr()), "spsvm_decision")
+    return out
+
+
+def spsvm_draw_candidates(n, J, kappa, seed, round_index):
+    J = np.ascontiguousarray(np.asarray(J, dtype=np.int64))
+    out = np.empty(max(1, kappa), dtype=np.int64)
+    k = _lib().spsvm_draw_candidates(int(n), J.ctypes.data if len(J) else None, len(J), int(kappa),
+                                     C.c_uint64(int(seed) & ((1 << 64) - 1)),
+                                     C.c_uint32(int(round_index) & 0xFFFFFFFF), out.ctypes.data)
+    if k < 0:
+        raise ValueError("spsvm_draw_candidates: bad arguments")
+    return out[:k].copy()
+
+
+# ---------------------------------------------------------------- fit/predict
+def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp32",
+                 growth_tol=0.0, rel_tol=0.0, seed=0, initial_basis=None, fixed_basis=False,
+                 refine=0, record=False, stream=None):
+    o = spsvm_options()
+    o.candidates = int(candidates)
+    o.add_per_round = int(add_per_round)
+    o.max_newton = int(max_newton)
+    o.precision = _prec(precision)
+    o.growth_tol = float(growth_tol)
+    o.rel_tol = float(rel_tol)
+    o.seed = int(seed) & ((1 << 64) - 1)
+    keep = None
+    if initial_basis is not None and len(initial_basis):
+        keep = np.ascontiguousarray(np.asarray(initial_basis, dtype=np.int64))
+        o.initial_basis = keep.ctypes.data_as(C.POINTER(C.c_int64))
+        o.n_initial = len(keep)
+    o.fixed_basis = int(bool(fixed_basis))
+    o.refine = int(refine)
+    o.record = int(bool(record))
+    o.stream = stream_ptr(stream) if torch.cuda.is_available() else None
+    return o, keep
+
+
+class Model:
+    """Owns an spsvm_model handle."""
+
+    def __init__(self, handle, status):
+        self.handle = C.c_void_p(handle)
+        self.status = status
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                _lib().spsvm_free(self.handle)
+                self.handle = C.c_void_p(None)
+        except Exception:
+            pass
+
+    def info(self):
+        nb = C.c_int32()
+        d = C.c_int64()
+        g = C.c_float()
+        lam = C.c_double()
+        obj = C.c_double()
+        steps = C.c_int32()
+        rounds = C.c_int32()
+        st = C.c_int32()
+        check(_lib().spsvm_model_info(self.handle, C.byref(nb), C.byref(d), C.byref(g),
+                                      C.byref(lam), C.byref(obj), C.byref(steps), C.byref(rounds),
+                                      C.byref(st)), "spsvm_model_info")
+        return dict(n_basis=nb.value, d=d.value, gamma=g.value, lam=lam.value,
+                    objective=obj.value, newton_steps=steps.value, rounds=rounds.value,
+                    status=st.value)
+
+    def basis_and_beta(self):
+        nb = self.info()["n_basis"]
+        J = np.empty(max(1, nb), dtype=np.int64)
+        beta = np.empty(max(1, nb), dtype=np.float64)
+        check(_lib().spsvm_model_get(self.handle, J.ctypes.data, beta.ctypes.data),
+              "spsvm_model_get")
+        return J[:nb], beta[:nb]
+
+    def history(self):
+        cnt = C.c_int32()
+        check(_lib().spsvm_model_history(self.handle, None, 0, C.byref(cnt)), "spsvm_model_history")
+        arr = (spsvm_step * max(1, cnt.value))()
+        check(_lib().spsvm_model_history(self.handle, C.cast(arr, C.c_void_p), cnt.value,
+                                         C.byref(cnt)), "spsvm_model_history")
+        return [dict(basis=a.basis, active=a.active, gnorm=a.gnorm, t=a.t, loss=a.loss,
+                     errors=a.errors) for a in arr[:cnt.value]]
+
+    def round(self, r):
+        nc = C.c_int32()
+        nch = C.c_int32()
+        check(_lib().spsvm_model_round(self.handle, int(r), None, C.byref(nc), None, C.byref(nch)),
+              "spsvm_model_round")
+        cand = np.empty(max(1, nc.value), dtype=np.int64)
+        ch = np.empty(max(1, nch.value), dtype=np.int64)
+        check(_lib().spsvm_model_round(self.handle, int(r), cand.ctypes.data, C.byref(nc),
+                                       ch.ctypes.data, C.byref(nch)), "spsvm_model_round")
+        return cand[:nc.value], ch[:nch.value]
+
+    def outputs(self, n):
+        o = np.empty(n, dtype=np.float32)
+        check(_lib().spsvm_model_outputs(self.handle, o.ctypes.data, int(n)), "spsvm_model_outputs")
+        return o
+
+    def predict(self, Xq: torch.Tensor, stream=None):
+        return spsvm_predict(self, Xq, stream)
+
+
+def spsvm_fit_workspace_bytes(n, d, budget, options):
+    return _lib().spsvm_fit_workspace_bytes(int(n), int(d), int(budget), C.byref(options))
+
+
+def spsvm_fit(X: torch.Tensor, y: torch.Tensor, gamma, lam, budget, tol=1e-6, workspace=None,
+              **opts):
+    """Trains SP-SVM on device tensors X (n x d float32) and y (n float32
+    in {-1,+1}); the workspace is a torch uint8 CUDA tensor (allocated here
+    when not given)."""
+    _require_cuda(X, y)
+    assert X.dtype == torch.float32 and y.dtype == torch.float32 and X.stride(1) == 1
+    n, d = X.shape
+    o, keep = make_options(**opts)
+    wsb = _lib().spsvm_fit_workspace_bytes(n, d, int(budget), C.byref(o))
+    if workspace is None:
+        workspace = torch.empty(max(1, wsb), dtype=torch.uint8, device=X.device)
+    handle = C.c_void_p()
+    rc = _lib().spsvm_fit(ptr(X), n, d, X.stride(0), ptr(y), float(gamma), float(lam), int(budget),
+                          float(tol), C.byref(o), ptr(workspace), workspace.numel(),
+                          C.byref(handle))
+    del keep
+    if rc not in (L.SPSVM_OK, L.SPSVM_ERR_NO_CONVERGE):
+        check(rc, "spsvm_fit")
+    return Model(handle.value, rc)
+
+
+def spsvm_predict(model: Model, Xq: torch.Tensor, stream=None):
+    _require_cuda(Xq)
+    assert Xq.dtype == torch.float32 and Xq.stride(1) == 1
+    out = torch.empty(Xq.shape[0], dtype=torch.float32, device=Xq.device)
+    check(_lib().spsvm_predict(model.handle, ptr(Xq), Xq.shape[0], Xq.stride(0), ptr(out),
+                               stream_ptr(stream)), "spsvm_predict")
+    return out

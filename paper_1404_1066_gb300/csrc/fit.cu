@@ -1,0 +1,699 @@
+// SP-SVM fit orchestration (Section 4, "Sparse primal optimization"): the
+// cycle of basis-vector selection and reoptimisation of Eq. 4, built from
+// the step-level entry points; the model object and prediction.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+struct spsvm_model {
+  int64_t n = 0, d = 0;
+  float gamma = 0.f;
+  double lambda = 0.0;
+  int32_t precision = SPSVM_FP32;
+  std::vector<int64_t> J;
+  std::vector<double> beta;
+  std::vector<spsvm_step> history;
+  std::vector<std::vector<int64_t>> cand_rounds, chosen_rounds;
+  std::vector<float> o;
+  double objective = 0.0;
+  int32_t status = SPSVM_OK;
+  int32_t rounds = 0;
+  int device = 0;
+  float* basis_dev = nullptr;    // |J| x d, row-major
+  double* beta_dev = nullptr;
+  void* scratch_dev = nullptr;   // decision scratch
+  size_t scratch_bytes = 0;
+};
+
+namespace spsvm {
+
+namespace {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+uint64_t splitmix_at(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1) * kGolden;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---- small device kernels used by the orchestration ---------------------
+__global__ void sub_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                           float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] - b[i];
+}
+
+// g_k = lambda o[J_k] + gs_k ; rhs_k = -g_k
+__global__ void grad_finish(const float* __restrict__ o, const int64_t* __restrict__ J,
+                            const double* __restrict__ gs, int32_t m, double lambda,
+                            double* __restrict__ g, double* __restrict__ rhs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const double v = lambda * (double)o[J[k]] + gs[k];
+  g[k] = v;
+  rhs[k] = -v;
+}
+
+// rho_k = -g_k - lambda u[J_k] - ws_k   (residual of H d = -g, H applied exactly)
+__global__ void refine_resid(const double* __restrict__ g, const float* __restrict__ u,
+                             const int64_t* __restrict__ J, const double* __restrict__ ws,
+                             int32_t m, double lambda, double* __restrict__ rho) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  rho[k] = -g[k] - lambda * (double)u[J[k]] - ws[k];
+}
+
+__global__ void axpy_d(double* __restrict__ y, const double* __restrict__ x, double a, int32_t m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < m) y[k] += a * x[k];
+}
+
+__global__ void update_o(float* __restrict__ o, const float* __restrict__ u, double t, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (float)((double)o[i] + t * (double)u[i]);
+}
+
+__global__ void count_diff(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b, int64_t n,
+                           unsigned long long* __restrict__ out) {
+  __shared__ int sh[32];
+  int c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += (a[i] != b[i]);
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+// out[0] = sum_k beta_k o[J_k] ; out[1] = sum g_k^2 ; out[2] = sum r_k^2
+__global__ void small_dots(const double* __restrict__ beta, const float* __restrict__ o,
+                           const int64_t* __restrict__ J, const double* __restrict__ g,
+                           const double* __restrict__ r, int32_t m, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    a += beta[k] * (double)o[J[k]];
+    b += g[k] * g[k];
+    c += r[k] * r[k];
+  }
+  a = block_sum(a, sh);
+  __syncthreads();
+  b = block_sum(b, sh);
+  __syncthreads();
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+__global__ void add_diag(double* __restrict__ H, int64_t ldh, int32_t m, double shift) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < m) H[(int64_t)k * ldh + k] += shift;
+}
+
+__global__ void diag_sum(const double* __restrict__ H, int64_t ldh, int32_t m, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) s += H[(int64_t)k * ldh + k];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void gather_rows(const float* __restrict__ X, int64_t ldx, int64_t d,
+                            const int64_t* __restrict__ J, int32_t m, float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * d) return;
+  const int64_t r = e / d, k = e % d;
+  out[e] = X[J[r] * ldx + k];
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = ceil_div(n, threads);
+  const int64_t cap = 8 * (int64_t)sm_count();
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---- workspace layout ------------------------------------------------------
+struct Layout {
+  int64_t n, d, ldn, ldh, jcap, kappa, q;
+  size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
+      off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_ws, off_J, off_cand,
+      off_cg, off_ch, off_cd, off_small, off_scratch, total;
+  size_t scratch_bytes;
+  size_t kbytes;
+};
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int32_t kappa,
+                   int32_t q) {
+  Layout L{};
+  L.n = n;
+  L.d = d;
+  L.ldn = round_up(n > 0 ? n : 1, 128);
+  L.ldh = round_up(d, 64);
+  L.jcap = round_up(budget, 64);
+  L.kappa = kappa;
+  L.q = q;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += al(bytes);
+    return o;
+  };
+  L.off_norms = take(n * 4);
+  const bool bf = precision == SPSVM_BF16X3;
+  L.off_xhi = take(bf ? (size_t)n * L.ldh * 2 : 0);
+  L.off_xlo = take(bf ? (size_t)n * L.ldh * 2 : 0);
+  L.kbytes = (size_t)L.jcap * L.ldn * 4;   // FP32, or two BF16 planes
+  L.off_K = take(L.kbytes);
+  L.off_Kc = take(L.kbytes);
+  L.off_o = take(n * 4);
+  L.off_u = take(n * 4);
+  L.off_res = take(n * 4);
+  L.off_act0 = take(n);
+  L.off_act1 = take(n);
+  L.off_pos = take(n * 4);
+  L.off_H = take((size_t)L.jcap * L.jcap * 8);
+  L.off_beta = take(L.jcap * 8);
+  L.off_dir = take(L.jcap * 8);
+  L.off_g = take(L.jcap * 8);
+  L.off_r = take(L.jcap * 8);
+  L.off_rhs = take(L.jcap * 8);
+  L.off_tmp = take(L.jcap * 8);
+  L.off_ws = take(L.jcap * 8);
+  L.off_J = take(L.jcap * 8);
+  L.off_cand = take(kappa * 8);
+  L.off_cg = take(kappa * 8);
+  L.off_ch = take(kappa * 8);
+  L.off_cd = take(kappa * 8);
+  L.off_small = take(256);
+  size_t sc = spsvm_score_scratch_bytes(n, kappa);
+  sc = std::max(sc, spsvm_reduce_scratch_bytes(n));
+  sc = std::max(sc, spsvm_compact_scratch_bytes(n, L.jcap));
+  // the Gram split count depends on |J|: cover every size the fit can reach
+  for (int64_t mm = 1; mm <= L.jcap; ++mm) sc = std::max(sc, spsvm_gram_scratch_bytes(mm, n));
+  sc = std::max(sc, spsvm_line_scratch_bytes(n));
+  L.scratch_bytes = al(sc);
+  L.off_scratch = take(L.scratch_bytes);
+  L.total = off;
+  return L;
+}
+
+struct Opts {
+  int32_t kappa, q, max_newton, precision, refine, record;
+  double growth_tol, rel_tol;
+  uint64_t seed;
+  bool fixed;
+  cudaStream_t stream;
+};
+
+Opts resolve(const spsvm_options* o) {
+  Opts r{};
+  r.kappa = (o && o->candidates > 0) ? o->candidates : 256;
+  r.q = (o && o->add_per_round > 0) ? o->add_per_round : 64;
+  r.max_newton = (o && o->max_newton > 0) ? o->max_newton : 50;
+  r.precision = o ? o->precision : SPSVM_FP32;
+  r.refine = (o && o->refine != 0) ? (o->refine < 0 ? 0 : o->refine) : 1;
+  r.record = o ? o->record : 0;
+  r.growth_tol = o ? o->growth_tol : 0.0;
+  r.rel_tol = (o && o->rel_tol > 0) ? o->rel_tol : (r.precision == SPSVM_BF16X3 ? 2e-5 : 1e-6);
+  r.seed = o ? o->seed : 0;
+  r.fixed = o && o->fixed_basis;
+  r.stream = o ? as_stream(o->stream) : nullptr;
+  return r;
+}
+
+struct Fit {
+  const float* X;
+  const float* y;
+  int64_t n, d, ldx;
+  float gamma;
+  double lambda, tol;
+  int32_t budget;
+  Opts op;
+  Layout L;
+  char* ws;
+  cudaStream_t s;
+  spsvm_points pts;
+  spsvm_model* model;
+  std::vector<int64_t> J;     // host copy of the basis
+  int32_t m = 0;              // current |J|
+  int32_t act_cur = 0;        // which active buffer holds the current flags
+
+  template <typename T>
+  T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
+
+  spsvm_kmat kmat() {
+    spsvm_kmat K{};
+    K.data = ws + L.off_K;
+    K.format = op.precision == SPSVM_BF16X3 ? SPSVM_BF16X3 : SPSVM_FP32;
+    K.n = n;
+    K.rows = m;
+    K.ld = L.ldn;
+    K.plane = (int64_t)L.jcap * L.ldn;
+    return K;
+  }
+  spsvm_kmat kcmat() {
+    spsvm_kmat K = kmat();
+    K.data = ws + L.off_Kc;
+    K.n = L.ldn;
+    return K;
+  }
+
+  int sync() {
+    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPSVM_OK;
+  }
+
+  // Refresh active flags and stats from the current o into buffer `which`.
+  int flags(int which, double stats_host[3]) {
+    spsvm_kmat K = kmat();
+    uint8_t* act = at<uint8_t>(which ? L.off_act1 : L.off_act0);
+    double* st = at<double>(L.off_small);
+    SPSVM_TRY(spsvm_outputs(&K, nullptr, y, at<float>(L.off_o), act, st, ws + L.off_scratch,
+                            L.scratch_bytes, s));
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(stats_host, st, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return sync();
+  }
+
+  int newton() {
+    spsvm_kmat K = kmat();
+    spsvm_kmat Kc = kcmat();
+    const int tpb = 256;
+    const int mb = (int)ceil_div(m, tpb);
+    double* beta = at<double>(L.off_beta);
+    double* dir = at<double>(L.off_dir);
+    double* g = at<double>(L.off_g);
+    double* r = at<double>(L.off_r);
+    double* rhs = at<double>(L.off_rhs);
+    double* tmp = at<double>(L.off_tmp);
+    double* wsum = at<double>(L.off_ws);
+    double* H = at<double>(L.off_H);
+    float* o = at<float>(L.off_o);
+    float* u = at<float>(L.off_u);
+    float* res = at<float>(L.off_res);
+    int64_t* Jd = at<int64_t>(L.off_J);
+    char* small = ws + L.off_small;
+    int64_t* n_active = reinterpret_cast<int64_t*>(small + 64);
+    int32_t* info = reinterpret_cast<int32_t*>(small + 80);
+    unsigned long long* ndiff = reinterpret_cast<unsigned long long*>(small + 96);
+    double* dots = reinterpret_cast<double*>(small + 128);
+    void* scratch = ws + L.off_scratch;
+    const size_t sb = L.scratch_bytes;
+    const int64_t ldH = L.jcap;
+
+    // exact outputs at the start of the reoptimisation
+    double st[3];
+    SPSVM_TRY(spsvm_outputs(&K, beta, y, o, at<uint8_t>(act_cur ? L.off_act1 : L.off_act0),
+                            at<double>(L.off_small), scratch, sb, s));
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(st, at<double>(L.off_small), sizeof(st), cudaMemcpyDeviceToHost, s));
+    SPSVM_TRY(sync());
+    int32_t status = SPSVM_ERR_NO_CONVERGE;
+    for (int it = 0; it < op.max_newton; ++it) {
+      uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
+      sub_kernel<<<grid_for(n, tpb), tpb, 0, s>>>(o, y, n, res);
+      SPSVM_LAUNCH_CHECK();
+      SPSVM_TRY(spsvm_compact_active(&K, act, res, y, wsum, r, &Kc, n_active,
+                                     at<int32_t>(L.off_pos), scratch, sb, s));
+      grad_finish<<<mb, tpb, 0, s>>>(o, Jd, wsum, m, op_lambda(), g, rhs);
+      SPSVM_LAUNCH_CHECK();
+      small_dots<<<1, 256, 0, s>>>(beta, o, Jd, g, r, m, dots);
+      SPSVM_LAUNCH_CHECK();
+      double dh[3];
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      const double gnorm = std::sqrt(dh[1]), rnorm = std::sqrt(dh[2]);
+      model->objective = 0.5 * lambda * dh[0] + st[0];
+      if (gnorm <= std::max(tol, op.rel_tol * rnorm)) {
+        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], 0};
+        model->history.push_back(rec);
+        status = SPSVM_OK;
+        break;
+      }
+      // Newton system on the active set
+      SPSVM_TRY(spsvm_gram(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s));
+      SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, s));
+      int32_t info_h = 0;
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      if (info_h != 0) {
+        // one retry with a diagonal shift of 1e-10 trace(H) / |J|
+        SPSVM_TRY(spsvm_gram(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s));
+        diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
+        SPSVM_LAUNCH_CHECK();
+        double tr = 0.0;
+        SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
+        SPSVM_TRY(sync());
+        add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, 1e-10 * tr / m);
+        SPSVM_LAUNCH_CHECK();
+        SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, s));
+        SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
+        SPSVM_TRY(sync());
+        if (info_h != 0)
+          return set_error(SPSVM_ERR_NOT_PD, "Newton matrix not positive definite (pivot %d, |J|=%d)",
+                           info_h, m);
+      }
+      // d = -H^{-1} g, then refinement against the exactly applied H
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, s));
+      SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
+      for (int k = 0; k < op.refine; ++k) {
+        SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
+                                       at<int32_t>(L.off_pos), scratch, sb, s));
+        refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
+        SPSVM_LAUNCH_CHECK();
+        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, s));
+        axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
+        SPSVM_LAUNCH_CHECK();
+        SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
+      }
+      double t = 0.0;
+      SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
+      axpy_d<<<mb, tpb, 0, s>>>(beta, dir, t, m);
+      SPSVM_LAUNCH_CHECK();
+      update_o<<<grid_for(n, tpb), tpb, 0, s>>>(o, u, t, n);
+      SPSVM_LAUNCH_CHECK();
+      const int nxt = act_cur ^ 1;
+      double st2[3];
+      SPSVM_TRY(flags(nxt, st2));
+      SPSVM_CUDA_TRY(cudaMemsetAsync(ndiff, 0, sizeof(*ndiff), s));
+      count_diff<<<grid_for(n, tpb), tpb, 0, s>>>(at<uint8_t>(L.off_act0), at<uint8_t>(L.off_act1),
+                                                  n, ndiff);
+      SPSVM_LAUNCH_CHECK();
+      unsigned long long nd = 0;
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(&nd, ndiff, sizeof(nd), cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], 0};
+      model->history.push_back(rec);
+      act_cur = nxt;
+      std::memcpy(st, st2, sizeof(st));
+      if (t == 1.0 && nd == 0) {
+        status = SPSVM_OK;
+        break;
+      }
+    }
+    model->status = status;
+    return SPSVM_OK;
+  }
+
+  double op_lambda() const { return lambda; }
+
+  int run() {
+    s = op.stream;
+    std::memset(&pts, 0, sizeof(pts));
+    pts.X = X;
+    pts.n = n;
+    pts.d = d;
+    pts.ldx = ldx;
+    pts.norms = at<float>(L.off_norms);
+    pts.ldh = L.ldh;
+    if (op.precision == SPSVM_BF16X3) {
+      pts.hi = at<uint16_t>(L.off_xhi);
+      pts.lo = at<uint16_t>(L.off_xlo);
+    }
+    SPSVM_TRY(spsvm_prepare_points(&pts, op.precision, s));
+    SPSVM_CUDA_TRY(cudaMemsetAsync(ws + L.off_beta, 0, L.jcap * 8, s));
+    SPSVM_CUDA_TRY(cudaMemsetAsync(ws + L.off_o, 0, n * 4, s));
+    int64_t* Jd = at<int64_t>(L.off_J);
+    if (!J.empty()) {
+      m = (int32_t)J.size();
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(Jd, J.data(), m * 8, cudaMemcpyHostToDevice, s));
+      spsvm_kmat K = kmat();
+      SPSVM_TRY(spsvm_kernel_block(&pts, Jd, m, gamma, op.precision, &K, 0, s));
+      SPSVM_TRY(newton());
+    }
+    double st[3];
+    SPSVM_TRY(flags(act_cur, st));
+    double E_prev = st[1] / (double)n;
+    uint32_t round = 0;
+    std::vector<int64_t> cand(op.kappa);
+    std::vector<double> delta(op.kappa);
+    while (!op.fixed && m < budget) {
+      const int32_t nc = spsvm_draw_candidates(n, J.data(), m, op.kappa, op.seed, round, cand.data());
+      if (nc <= 0) break;
+      int64_t* cd = at<int64_t>(L.off_cand);
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(cd, cand.data(), nc * 8, cudaMemcpyHostToDevice, s));
+      SPSVM_TRY(spsvm_score_candidates(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
+                                       op.precision, at<double>(L.off_cg), at<double>(L.off_ch),
+                                       at<double>(L.off_cd), ws + L.off_scratch, L.scratch_bytes, s));
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(delta.data(), at<double>(L.off_cd), nc * 8,
+                                     cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      const int32_t qq = std::min<int32_t>(std::min(op.q, budget - m), nc);
+      std::vector<int32_t> order(nc);
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (delta[a] != delta[b]) return delta[a] > delta[b];
+        return cand[a] < cand[b];
+      });
+      std::vector<int64_t> chosen(qq);
+      for (int k = 0; k < qq; ++k) chosen[k] = cand[order[k]];
+      if (op.record) {
+        model->cand_rounds.emplace_back(cand.begin(), cand.begin() + nc);
+        model->chosen_rounds.push_back(chosen);
+      }
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(Jd + m, chosen.data(), qq * 8, cudaMemcpyHostToDevice, s));
+      for (auto c : chosen) J.push_back(c);
+      const int32_t m0 = m;
+      m += qq;
+      spsvm_kmat K = kmat();
+      SPSVM_TRY(spsvm_kernel_block(&pts, Jd + m0, qq, gamma, op.precision, &K, m0, s));
+      SPSVM_TRY(newton());
+      ++round;
+      SPSVM_TRY(flags(act_cur, st));
+      const double E = st[1] / (double)n;
+      if (op.growth_tol > 0 && (E_prev - E) / qq < op.growth_tol) break;
+      E_prev = E;
+    }
+    model->rounds = (int32_t)round;
+    return finish();
+  }
+
+  int finish() {
+    model->J = J;
+    model->beta.assign(m, 0.0);
+    if (m > 0)
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta.data(), ws + L.off_beta, m * 8,
+                                     cudaMemcpyDeviceToHost, s));
+    model->o.assign(n, 0.f);
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(model->o.data(), ws + L.off_o, n * 4, cudaMemcpyDeviceToHost, s));
+    SPSVM_TRY(sync());
+    if (m > 0) {
+      SPSVM_CUDA_TRY(cudaMalloc(&model->basis_dev, (size_t)m * d * 4));
+      SPSVM_CUDA_TRY(cudaMalloc(&model->beta_dev, (size_t)m * 8));
+      gather_rows<<<(unsigned)ceil_div((int64_t)m * d, 256), 256, 0, s>>>(
+          X, ldx, d, at<int64_t>(L.off_J), m, model->basis_dev);
+      SPSVM_LAUNCH_CHECK();
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta_dev, model->beta.data(), m * 8,
+                                     cudaMemcpyHostToDevice, s));
+    }
+    model->scratch_bytes = spsvm_decision_scratch_bytes(0, m, d);
+    SPSVM_CUDA_TRY(cudaMalloc(&model->scratch_dev, model->scratch_bytes));
+    return sync();
+  }
+};
+
+}  // namespace
+}  // namespace spsvm
+
+using namespace spsvm;
+
+extern "C" int32_t spsvm_draw_candidates(int64_t n, const int64_t* J, int32_t nJ, int32_t kappa,
+                                         uint64_t seed, uint32_t round, int64_t* out) {
+  if (n < 0 || nJ < 0 || kappa < 0 || (nJ > 0 && !J) || (kappa > 0 && !out)) return -1;
+  std::vector<char> inJ((size_t)n, 0);
+  for (int32_t k = 0; k < nJ; ++k)
+    if (J[k] >= 0 && J[k] < n) inJ[(size_t)J[k]] = 1;
+  std::vector<int64_t> pool;
+  pool.reserve((size_t)n);
+  for (int64_t i = 0; i < n; ++i)
+    if (!inJ[(size_t)i]) pool.push_back(i);
+  const int64_t mm = (int64_t)pool.size();
+  const int32_t kk = (int32_t)std::min<int64_t>(kappa, mm);
+  for (int32_t k = 0; k < kk; ++k) {
+    const uint64_t r = splitmix_at(seed, ((uint64_t)round << 32) | (uint64_t)(uint32_t)k);
+    const int64_t j = k + (int64_t)(r % (uint64_t)(mm - k));
+    std::swap(pool[k], pool[j]);
+  }
+  for (int32_t k = 0; k < kk; ++k) out[k] = pool[k];
+  return kk;
+}
+
+extern "C" size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_budget,
+                                            const spsvm_options* opt) {
+  if (n < 1 || d < 1 || basis_budget < 1) return 0;
+  const Opts op = resolve(opt);
+  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q).total;
+}
+
+extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
+                         float gamma, double lambda, int32_t basis_budget, double tol,
+                         const spsvm_options* opt, void* workspace, size_t workspace_bytes,
+                         spsvm_model** out) {
+  if (!out) return set_error(SPSVM_ERR_ARG, "fit: NULL out");
+  *out = nullptr;
+  if (!X || !y || n < 1 || d < 1 || ldx < d)
+    return set_error(SPSVM_ERR_ARG, "fit: bad data arguments (n=%lld d=%lld ldx=%lld)",
+                     (long long)n, (long long)d, (long long)ldx);
+  if (!(gamma > 0.f) || !(lambda > 0.0) || basis_budget < 1 || basis_budget > n || tol < 0)
+    return set_error(SPSVM_ERR_ARG, "fit: need gamma > 0, lambda > 0, 1 <= budget <= n, tol >= 0");
+  if (n > (int64_t)INT32_MAX) return set_error(SPSVM_ERR_ARG, "fit: n too large");
+  Opts op = resolve(opt);
+  if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16X3)
+    return set_error(SPSVM_ERR_ARG, "fit: bad precision %d", op.precision);
+  std::vector<int64_t> J0;
+  if (opt && opt->n_initial > 0) {
+    if (!opt->initial_basis) return set_error(SPSVM_ERR_ARG, "fit: NULL initial_basis");
+    std::vector<char> seen((size_t)n, 0);
+    for (int32_t k = 0; k < opt->n_initial; ++k) {
+      const int64_t j = opt->initial_basis[k];
+      if (j < 0 || j >= n || seen[(size_t)j])
+        return set_error(SPSVM_ERR_ARG, "fit: initial basis index %lld invalid or repeated",
+                         (long long)j);
+      seen[(size_t)j] = 1;
+      J0.push_back(j);
+    }
+    if ((int32_t)J0.size() > basis_budget) basis_budget = (int32_t)J0.size();
+  }
+  if (op.fixed && J0.empty()) return set_error(SPSVM_ERR_ARG, "fit: fixed_basis needs an initial basis");
+  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q);
+  bool own = false;
+  if (!workspace) {
+    cudaError_t e = cudaMalloc(&workspace, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SPSVM_ERR_OOM, "fit: cannot allocate %zu bytes", L.total);
+    }
+    own = true;
+  } else if (workspace_bytes < L.total) {
+    return set_error(SPSVM_ERR_OOM, "fit: workspace %zu < %zu bytes", workspace_bytes, L.total);
+  }
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) {
+    if (own) cudaFree(workspace);
+    return set_error(SPSVM_ERR_ARG, "fit: workspace must be 256-byte aligned");
+  }
+  spsvm_model* model = new spsvm_model();
+  model->n = n;
+  model->d = d;
+  model->gamma = gamma;
+  model->lambda = lambda;
+  model->precision = op.precision;
+  cudaGetDevice(&model->device);
+  Fit f;
+  f.X = X;
+  f.y = y;
+  f.n = n;
+  f.d = d;
+  f.ldx = ldx;
+  f.gamma = gamma;
+  f.lambda = lambda;
+  f.tol = tol;
+  f.budget = basis_budget;
+  f.op = op;
+  f.L = L;
+  f.ws = static_cast<char*>(workspace);
+  f.model = model;
+  f.J = J0;
+  int rc = f.run();
+  if (own) {
+    cudaStreamSynchronize(f.s);
+    cudaFree(workspace);
+  }
+  if (rc != SPSVM_OK) {
+    spsvm_free(model);
+    return rc;
+  }
+  *out = model;
+  return model->status == SPSVM_ERR_NO_CONVERGE ? SPSVM_ERR_NO_CONVERGE : SPSVM_OK;
+}
+
+extern "C" int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
+                             float* decision, void* stream) {
+  if (!model || !Xq || !decision || nq < 0 || ldq < model->d)
+    return set_error(SPSVM_ERR_ARG, "predict: bad arguments");
+  if (nq == 0) return SPSVM_OK;
+  if (model->J.empty()) {
+    SPSVM_CUDA_TRY(cudaMemsetAsync(decision, 0, nq * 4, as_stream(stream)));
+    return SPSVM_OK;
+  }
+  return spsvm_decision(model->basis_dev, (int64_t)model->J.size(), model->d, model->beta_dev, Xq, nq,
+                        ldq, model->d, model->gamma, model->precision, decision, model->scratch_dev,
+                        model->scratch_bytes, stream);
+}
+
+extern "C" int spsvm_model_info(const spsvm_model* m, int32_t* n_basis, int64_t* d, float* gamma,
+                                double* lambda, double* objective, int32_t* newton_steps,
+                                int32_t* rounds, int32_t* status) {
+  if (!m) return set_error(SPSVM_ERR_ARG, "model_info: NULL model");
+  if (n_basis) *n_basis = (int32_t)m->J.size();
+  if (d) *d = m->d;
+  if (gamma) *gamma = m->gamma;
+  if (lambda) *lambda = m->lambda;
+  if (objective) *objective = m->objective;
+  if (newton_steps) {
+    int32_t c = 0;
+    for (const auto& h : m->history) c += (h.t != 0.0);
+    *newton_steps = c;
+  }
+  if (rounds) *rounds = m->rounds;
+  if (status) *status = m->status;
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_model_get(const spsvm_model* m, int64_t* basis_idx, double* beta) {
+  if (!m) return set_error(SPSVM_ERR_ARG, "model_get: NULL model");
+  if (basis_idx) std::copy(m->J.begin(), m->J.end(), basis_idx);
+  if (beta) std::copy(m->beta.begin(), m->beta.end(), beta);
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_model_history(const spsvm_model* m, spsvm_step* out, int32_t cap,
+                                   int32_t* count) {
+  if (!m) return set_error(SPSVM_ERR_ARG, "model_history: NULL model");
+  if (count) *count = (int32_t)m->history.size();
+  if (out && cap > 0) {
+    const size_t k = std::min<size_t>(cap, m->history.size());
+    std::copy(m->history.begin(), m->history.begin() + k, out);
+  }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_model_round(const spsvm_model* m, int32_t r, int64_t* candidates,
+                                 int32_t* n_candidates, int64_t* chosen, int32_t* n_chosen) {
+  if (!m) return set_error(SPSVM_ERR_ARG, "model_round: NULL model");
+  if (r < 0 || r >= (int32_t)m->cand_rounds.size())
+    return set_error(SPSVM_ERR_ARG, "model_round: round %d not recorded", r);
+  const auto& c = m->cand_rounds[r];
+  const auto& h = m->chosen_rounds[r];
+  if (n_candidates) *n_candidates = (int32_t)c.size();
+  if (n_chosen) *n_chosen = (int32_t)h.size();
+  if (candidates) std::copy(c.begin(), c.end(), candidates);
+  if (chosen) std::copy(h.begin(), h.end(), chosen);
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_model_outputs(const spsvm_model* m, float* o, int64_t n) {
+  if (!m || !o || n != m->n) return set_error(SPSVM_ERR_ARG, "model_outputs: bad arguments");
+  std::copy(m->o.begin(), m->o.end(), o);
+  return SPSVM_OK;
+}
+
+extern "C" void spsvm_free(spsvm_model* m) {
+  if (!m) return;
+  if (m->basis_dev) cudaFree(m->basis_dev);
+  if (m->beta_dev) cudaFree(m->beta_dev);
+  if (m->scratch_dev) cudaFree(m->scratch_dev);
+  delete m;
+}

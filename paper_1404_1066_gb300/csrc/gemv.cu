@@ -1,0 +1,439 @@
+// HBM-bound passes over the stored kernel matrix K_nJ (basis-major):
+//   * o = K_nJ beta with the active set, loss and error count of Eq. 4;
+//   * u = K_nJ v (line-search direction);
+//   * active-set compaction K_SJ with the masked transposed products
+//     K_SJ^T w (gradient and Newton right-hand side of Eq. 4).
+// Products are FP32; every 32 terms the running sum is promoted to FP64.
+#include "internal.h"
+
+namespace spsvm {
+
+namespace {
+
+constexpr int GV_T = 256;          // threads per block
+constexpr int GV_P = 4;            // consecutive points per thread
+constexpr int GV_PTS = GV_T * GV_P;
+constexpr int GV_CHUNK = 32;       // terms summed in FP32 before promotion
+constexpr int GV_BETA = 2048;      // beta entries staged in shared memory per pass
+
+// Loads 4 consecutive kernel values of row j starting at point i (i % 4 == 0,
+// i + 3 < n) as FP32.
+__device__ __forceinline__ float4 load4(const KView& K, int64_t j, int64_t i) {
+  if (K.format == SPSVM_FP32) {
+    return *reinterpret_cast<const float4*>(static_cast<const float*>(K.data) + j * K.ld + i);
+  }
+  const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(K.data);
+  const uint2 h = *reinterpret_cast<const uint2*>(base + j * K.ld + i);
+  const uint2 l = *reinterpret_cast<const uint2*>(base + K.plane + j * K.ld + i);
+  const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&h);
+  const __nv_bfloat162* ll = reinterpret_cast<const __nv_bfloat162*>(&l);
+  const float2 h0 = __bfloat1622float2(hh[0]), h1 = __bfloat1622float2(hh[1]);
+  const float2 l0 = __bfloat1622float2(ll[0]), l1 = __bfloat1622float2(ll[1]);
+  return make_float4(h0.x + l0.x, h0.y + l0.y, h1.x + l1.x, h1.y + l1.y);
+}
+
+// acc[p] = sum_j K[j][i+p] v_j for the thread's 4 points.
+__device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64_t n,
+                                             const double* __restrict__ v, int64_t i,
+                                             float* vs, double acc[GV_P]) {
+#pragma unroll
+  for (int p = 0; p < GV_P; ++p) acc[p] = 0.0;
+  const bool full = (i + GV_P <= n);
+  for (int64_t j0 = 0; j0 < rows; j0 += GV_BETA) {
+    const int cnt = (int)min64(GV_BETA, rows - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) vs[t] = (float)v[j0 + t];
+    __syncthreads();
+    if (i >= n) continue;
+    for (int c0 = 0; c0 < cnt; c0 += GV_CHUNK) {
+      const int ce = min(cnt, c0 + GV_CHUNK);
+      float f[GV_P] = {0.f, 0.f, 0.f, 0.f};
+      if (full) {
+#pragma unroll 8
+        for (int c = c0; c < ce; ++c) {
+          const float4 k4 = load4(K, j0 + c, i);
+          const float b = vs[c];
+          f[0] = fmaf(k4.x, b, f[0]);
+          f[1] = fmaf(k4.y, b, f[1]);
+          f[2] = fmaf(k4.z, b, f[2]);
+          f[3] = fmaf(k4.w, b, f[3]);
+        }
+      } else {
+        for (int c = c0; c < ce; ++c) {
+          const float b = vs[c];
+          for (int p = 0; p < GV_P; ++p)
+            if (i + p < n) f[p] = fmaf(K.at(j0 + c, i + p), b, f[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < GV_P; ++p) acc[p] += (double)f[p];
+    }
+  }
+}
+
+// o = K beta (or given), active flags, per-block loss / errors / |S|.
+__global__ void __launch_bounds__(GV_T) outputs_kernel(
+    KView K, int64_t rows, int64_t n, const double* __restrict__ beta,
+    const float* __restrict__ y, float* __restrict__ o, uint8_t* __restrict__ active,
+    double* __restrict__ part, int accumulate) {
+  __shared__ float vs[GV_BETA];
+  __shared__ double sh[32];
+  const int64_t i = ((int64_t)blockIdx.x * GV_T + threadIdx.x) * GV_P;
+  double acc[GV_P];
+  if (beta) row_products(K, rows, n, beta, i, vs, acc);
+  double loss = 0.0, err = 0.0, act = 0.0;
+  if (i < n) {
+#pragma unroll
+    for (int p = 0; p < GV_P; ++p) {
+      const int64_t ii = i + p;
+      if (ii >= n) break;
+      float oi;
+      if (beta) {
+        oi = accumulate ? (float)((double)o[ii] + acc[p]) : (float)acc[p];
+        o[ii] = oi;
+      } else {
+        oi = o[ii];
+      }
+      const float yi = y[ii];
+      const float margin = yi * oi;
+      const bool s = margin < 1.0f;
+      if (active) active[ii] = s ? 1 : 0;
+      if (s) {
+        const double xi = 1.0 - (double)margin;
+        loss += xi * xi;
+        act += 1.0;
+      }
+      if (margin <= 0.0f) err += 1.0;
+    }
+  }
+  if (part) {
+    loss = block_sum(loss, sh);
+    __syncthreads();
+    err = block_sum(err, sh);
+    __syncthreads();
+    act = block_sum(act, sh);
+    if (threadIdx.x == 0) {
+      part[3 * blockIdx.x + 0] = 0.5 * loss;
+      part[3 * blockIdx.x + 1] = err;
+      part[3 * blockIdx.x + 2] = act;
+    }
+  }
+}
+
+__global__ void gemv_kernel(KView K, int64_t rows, int64_t n, const double* __restrict__ v,
+                            float* __restrict__ u, int accumulate) {
+  __shared__ float vs[GV_BETA];
+  const int64_t i = ((int64_t)blockIdx.x * GV_T + threadIdx.x) * GV_P;
+  double acc[GV_P];
+  row_products(K, rows, n, v, i, vs, acc);
+  if (i >= n) return;
+#pragma unroll
+  for (int p = 0; p < GV_P; ++p) {
+    const int64_t ii = i + p;
+    if (ii < n) u[ii] = accumulate ? (float)((double)u[ii] + acc[p]) : (float)acc[p];
+  }
+}
+
+// Fixed-order sum of per-block triples.
+__global__ void sum_triples(const double* __restrict__ part, int64_t blocks, double* out) {
+  __shared__ double sh[32];
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < blocks; b += blockDim.x) s += part[3 * b + c];
+    s = block_sum(s, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) out[c] = s;
+  }
+}
+
+// ---- active-set scan -----------------------------------------------------
+constexpr int SC_T = 256;
+constexpr int SC_PTS = SC_T * 4;
+
+__global__ void scan_count(const uint8_t* __restrict__ active, int64_t n, int32_t* __restrict__ counts) {
+  __shared__ int sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SC_PTS;
+  int c = 0;
+  for (int p = 0; p < 4; ++p) {
+    const int64_t i = base + threadIdx.x + (int64_t)SC_T * p;
+    if (i < n) c += active[i];
+  }
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of block counts in one block; writes the total to *total.
+__global__ void scan_blocks(int32_t* __restrict__ counts, int64_t nb, int64_t* __restrict__ total) {
+  __shared__ int32_t sh[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    const int32_t v = (b < nb) ? counts[b] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      int32_t add = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    const int32_t incl = sh[threadIdx.x];
+    if (b < nb) counts[b] = (int32_t)(carry + incl - v);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
+                           const int32_t* __restrict__ offsets, int32_t* __restrict__ pos) {
+  __shared__ int32_t sh[SC_PTS];
+  const int64_t base = (int64_t)blockIdx.x * SC_PTS;
+  for (int p = 0; p < 4; ++p) {
+    const int64_t i = base + threadIdx.x * 4 + p;
+    sh[threadIdx.x * 4 + p] = (i < n) ? active[i] : 0;
+  }
+  __syncthreads();
+  // sequential scan per thread over its 4, then block scan of thread sums
+  int32_t local[4], run = 0;
+  for (int p = 0; p < 4; ++p) { local[p] = run; run += sh[threadIdx.x * 4 + p]; }
+  __shared__ int32_t ts[SC_T];
+  ts[threadIdx.x] = run;
+  __syncthreads();
+  for (int off = 1; off < SC_T; off <<= 1) {
+    int32_t add = (threadIdx.x >= (unsigned)off) ? ts[threadIdx.x - off] : 0;
+    __syncthreads();
+    ts[threadIdx.x] += add;
+    __syncthreads();
+  }
+  const int32_t excl = ts[threadIdx.x] - run + offsets[blockIdx.x];
+  for (int p = 0; p < 4; ++p) {
+    const int64_t i = base + threadIdx.x * 4 + p;
+    if (i < n) pos[i] = excl + local[p];
+  }
+}
+
+// ---- compaction + masked transposed products ---------------------------
+constexpr int CP_T = 256;
+constexpr int CP_ROWS = 8;      // basis rows per block
+
+__global__ void __launch_bounds__(CP_T) compact_kernel(
+    KView K, int64_t rows, int64_t n, const uint8_t* __restrict__ active,
+    const int32_t* __restrict__ pos, const float* __restrict__ w1, const float* __restrict__ w2,
+    void* kc_data, int64_t kc_ld, int64_t kc_plane, int64_t chunks_per_block,
+    double2* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t j0 = (int64_t)blockIdx.x * CP_ROWS;
+  const int64_t c_begin = (int64_t)blockIdx.y * chunks_per_block;
+  const int64_t nchunks = ceil_div(n, (int64_t)CP_T);
+  const int64_t c_end = min(nchunks, c_begin + chunks_per_block);
+  double s1[CP_ROWS], s2[CP_ROWS];
+  float f1[CP_ROWS], f2[CP_ROWS];
+#pragma unroll
+  for (int r = 0; r < CP_ROWS; ++r) { s1[r] = 0.0; s2[r] = 0.0; f1[r] = 0.f; f2[r] = 0.f; }
+  int since = 0;
+  for (int64_t c = c_begin; c < c_end; ++c) {
+    const int64_t i = c * CP_T + threadIdx.x;
+    if (i >= n) continue;
+    if (!active[i]) continue;
+    const int32_t q = pos[i];
+    const float a = w1 ? w1[i] : 0.f, b = w2 ? w2[i] : 0.f;
+#pragma unroll
+    for (int r = 0; r < CP_ROWS; ++r) {
+      const int64_t j = j0 + r;
+      if (j >= rows) break;
+      float v;
+      if (K.format == SPSVM_FP32) {
+        v = static_cast<const float*>(K.data)[j * K.ld + i];
+        if (kc_data) static_cast<float*>(kc_data)[j * kc_ld + q] = v;
+      } else {
+        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(K.data);
+        const __nv_bfloat16 h = src[j * K.ld + i], l = src[K.plane + j * K.ld + i];
+        if (kc_data) {
+          __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(kc_data);
+          dst[j * kc_ld + q] = h;
+          dst[kc_plane + j * kc_ld + q] = l;
+        }
+        v = __bfloat162float(h) + __bfloat162float(l);
+      }
+      f1[r] = fmaf(a, v, f1[r]);
+      f2[r] = fmaf(b, v, f2[r]);
+    }
+    if (++since == 32) {
+#pragma unroll
+      for (int r = 0; r < CP_ROWS; ++r) {
+        s1[r] += (double)f1[r]; s2[r] += (double)f2[r]; f1[r] = 0.f; f2[r] = 0.f;
+      }
+      since = 0;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < CP_ROWS; ++r) { s1[r] += (double)f1[r]; s2[r] += (double)f2[r]; }
+  for (int r = 0; r < CP_ROWS; ++r) {
+    const double a = block_sum(s1[r], sh);
+    __syncthreads();
+    const double b = block_sum(s2[r], sh);
+    __syncthreads();
+    const int64_t j = j0 + r;
+    if (threadIdx.x == 0 && j < rows) part[(int64_t)blockIdx.y * rows + j] = make_double2(a, b);
+  }
+}
+
+__global__ void compact_finish(const double2* __restrict__ part, int64_t ysplit, int64_t rows,
+                               double* w1out, double* w2out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= rows) return;
+  double a = 0.0, b = 0.0;
+  for (int64_t s = 0; s < ysplit; ++s) {
+    const double2 p = part[s * rows + j];
+    a += p.x;
+    b += p.y;
+  }
+  if (w1out) w1out[j] = a;
+  if (w2out) w2out[j] = b;
+}
+
+// Zero columns [ns, kc_n) of every row of the compact matrix.
+__global__ void zero_tail(void* kc_data, int32_t format, int64_t rows, int64_t kc_ld,
+                          int64_t kc_plane, int64_t kc_n, const int64_t* __restrict__ ns_dev) {
+  const int64_t ns = *ns_dev;
+  const int64_t end = min(kc_n, round_up(ns, (int64_t)128));
+  const int64_t width = end - ns;
+  if (width <= 0) return;
+  const int64_t total = rows * width;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / width, c = ns + e % width;
+    if (format == SPSVM_FP32) {
+      static_cast<float*>(kc_data)[j * kc_ld + c] = 0.f;
+    } else {
+      __nv_bfloat16* p = static_cast<__nv_bfloat16*>(kc_data);
+      p[j * kc_ld + c] = __float2bfloat16_rn(0.f);
+      p[kc_plane + j * kc_ld + c] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace spsvm
+
+using namespace spsvm;
+
+extern "C" size_t spsvm_reduce_scratch_bytes(int64_t n) {
+  if (n < 0) return 0;
+  return (size_t)(ceil_div(n, GV_PTS) * 3 * sizeof(double) + 64);
+}
+
+extern "C" int spsvm_outputs(const spsvm_kmat* K, const double* beta, const float* y, float* o,
+                             uint8_t* active, double* stats, void* scratch, size_t scratch_bytes,
+                             void* stream) {
+  SPSVM_TRY(check_kmat(K, "outputs"));
+  if (!y || !o) return set_error(SPSVM_ERR_ARG, "outputs: NULL y/o");
+  if (K->n == 0) return SPSVM_OK;
+  if (stats && (!scratch || scratch_bytes < spsvm_reduce_scratch_bytes(K->n)))
+    return set_error(SPSVM_ERR_OOM, "outputs: scratch too small");
+  cudaStream_t s = as_stream(stream);
+  const int64_t blocks = ceil_div(K->n, GV_PTS);
+  double* part = stats ? static_cast<double*>(scratch) : nullptr;
+  outputs_kernel<<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y, o, active,
+                                                    part, 0);
+  SPSVM_LAUNCH_CHECK();
+  if (stats) {
+    sum_triples<<<1, 256, 0, s>>>(part, blocks, stats);
+    SPSVM_LAUNCH_CHECK();
+  }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_t accumulate,
+                          void* stream) {
+  SPSVM_TRY(check_kmat(K, "gemv"));
+  if (!v || !u) return set_error(SPSVM_ERR_ARG, "gemv: NULL pointer");
+  if (K->n == 0) return SPSVM_OK;
+  const int64_t blocks = ceil_div(K->n, GV_PTS);
+  gemv_kernel<<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(view(K), K->rows, K->n, v, u,
+                                                                accumulate);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+namespace {
+int64_t compact_ysplit(int64_t n, int64_t rows) {
+  const int64_t rowblocks = ceil_div(rows, CP_ROWS);
+  const int64_t nchunks = ceil_div(n, CP_T);
+  int64_t want = ceil_div(4 * (int64_t)sm_count(), rowblocks);
+  if (want < 1) want = 1;
+  if (want > nchunks) want = nchunks;
+  return want;
+}
+}  // namespace
+
+extern "C" size_t spsvm_compact_scratch_bytes(int64_t n, int64_t rows) {
+  if (n < 0 || rows < 0) return 0;
+  const int64_t scan_blocks_n = ceil_div(n, SC_PTS);
+  // partials for the largest split the launcher may pick (bounded by chunks)
+  const int64_t ysplit = ceil_div(n, CP_T) < 1024 ? ceil_div(n, CP_T) : 1024;
+  return (size_t)(round_up(scan_blocks_n * 4, 256) +
+                  round_up((ysplit > 0 ? ysplit : 1) * (rows > 0 ? rows : 1) * 16, 256));
+}
+
+extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, const float* w1,
+                                    const float* w2, double* w1out, double* w2out,
+                                    spsvm_kmat* Kc, int64_t* n_active, int32_t* pos,
+                                    void* scratch, size_t scratch_bytes, void* stream) {
+  SPSVM_TRY(check_kmat(K, "compact"));
+  if (!active || !n_active || !pos) return set_error(SPSVM_ERR_ARG, "compact: NULL pointer");
+  if (Kc) {
+    SPSVM_TRY(check_kmat(Kc, "compact(out)"));
+    if (Kc->format != K->format || Kc->rows < K->rows || Kc->n < round_up(K->n, 128))
+      return set_error(SPSVM_ERR_ARG, "compact: output matrix too small or wrong format");
+  }
+  if ((w1out && !w1) || (w2out && !w2)) return set_error(SPSVM_ERR_ARG, "compact: missing weights");
+  if (!scratch || scratch_bytes < spsvm_compact_scratch_bytes(K->n, K->rows))
+    return set_error(SPSVM_ERR_OOM, "compact: scratch too small");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = K->n;
+  const int64_t sb = ceil_div(n, SC_PTS);
+  int32_t* counts = static_cast<int32_t*>(scratch);
+  double2* part = reinterpret_cast<double2*>(static_cast<char*>(scratch) + round_up(sb * 4, 256));
+  if (n == 0) {
+    SPSVM_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(int64_t), s));
+  } else {
+    scan_count<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts);
+    SPSVM_LAUNCH_CHECK();
+    scan_blocks<<<1, 1024, 0, s>>>(counts, sb, n_active);
+    SPSVM_LAUNCH_CHECK();
+    scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts, pos);
+    SPSVM_LAUNCH_CHECK();
+  }
+  if (K->rows > 0 && n > 0) {
+    int64_t ysplit = compact_ysplit(n, K->rows);
+    if (ysplit > 1024) ysplit = 1024;
+    const int64_t nchunks = ceil_div(n, CP_T);
+    const int64_t per = ceil_div(nchunks, ysplit);
+    ysplit = ceil_div(nchunks, per);
+    dim3 grid((unsigned)ceil_div(K->rows, CP_ROWS), (unsigned)ysplit);
+    compact_kernel<<<grid, CP_T, 0, s>>>(view(K), K->rows, n, active, pos, w1, w2,
+                                         Kc ? Kc->data : nullptr, Kc ? Kc->ld : 0,
+                                         Kc ? Kc->plane : 0, per, part);
+    SPSVM_LAUNCH_CHECK();
+    if (w1out || w2out) {
+      compact_finish<<<(unsigned)ceil_div(K->rows, 256), 256, 0, s>>>(part, ysplit, K->rows,
+                                                                       w1out, w2out);
+      SPSVM_LAUNCH_CHECK();
+    }
+  } else if (K->rows > 0) {
+    if (w1out) SPSVM_CUDA_TRY(cudaMemsetAsync(w1out, 0, K->rows * sizeof(double), s));
+    if (w2out) SPSVM_CUDA_TRY(cudaMemsetAsync(w2out, 0, K->rows * sizeof(double), s));
+  }
+  if (Kc && K->rows > 0) {
+    const int64_t kc_n = round_up(n, 128) <= Kc->n ? round_up(n, 128) : Kc->n;
+    zero_tail<<<4 * sm_count(), 256, 0, s>>>(Kc->data, Kc->format, K->rows, Kc->ld, Kc->plane,
+                                             kc_n, n_active);
+    SPSVM_LAUNCH_CHECK();
+  }
+  return SPSVM_OK;
+}

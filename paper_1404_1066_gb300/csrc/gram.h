@@ -1,0 +1,18 @@
+// Shared declarations of the Gram-matrix (masked SYRK) launchers.
+#pragma once
+#include "internal.h"
+
+namespace spsvm {
+
+// Points per FP32 partial sum before promotion to FP64.
+constexpr int64_t GRAM_SLICE = 8192;
+
+int64_t gram_simt_splits(int64_t m, int64_t ns_max);
+int launch_gram_simt(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, int64_t m,
+                     double* part, int64_t ldp, int64_t splits, cudaStream_t s);
+
+int64_t gram_tc_splits(int64_t m, int64_t ns_max);
+int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, int64_t m,
+                   double* part, int64_t ldp, int64_t splits, cudaStream_t s);
+
+}  // namespace spsvm

@@ -1,0 +1,184 @@
+// Masked Gram matrix H = lambda K_JJ + K_SJ^T K_SJ (the generalised Hessian
+// of Eq. 4 on the active set S) in FP32 SIMT arithmetic, with FP32 sums per
+// slice of 8192 points promoted to FP64.  Also the FP64 finishing pass
+// shared by both arithmetic forms.
+#include "internal.h"
+#include "gram.h"
+
+namespace spsvm {
+
+namespace {
+
+constexpr int GT = 64;      // output tile
+constexpr int GK = 32;      // points per smem stage
+constexpr int GNT = 256;    // 16 x 16 threads, 4 x 4 outputs each
+
+// Maps a linear index to the (ta <= tb) upper-triangular tile pair.
+__device__ __forceinline__ void tri_index(int64_t t, int64_t T, int& ta, int& tb) {
+  // rows of the upper triangle: row a has T - a tiles
+  int a = 0;
+  int64_t rem = t;
+  while (rem >= T - a) { rem -= T - a; ++a; }
+  ta = a;
+  tb = a + (int)rem;
+}
+
+__global__ void __launch_bounds__(GNT) gram_simt_kernel(
+    KView Kc, int64_t m, const int64_t* __restrict__ ns_dev, int64_t slices_per_split,
+    double* __restrict__ part, int64_t ldp) {
+  __shared__ float As[GK][GT + 1];
+  __shared__ float Bs[GK][GT + 1];
+  const int64_t T = ceil_div(m, (int64_t)GT);
+  int ta, tb;
+  tri_index(blockIdx.x, T, ta, tb);
+  const int64_t a0 = (int64_t)ta * GT, b0 = (int64_t)tb * GT;
+  const int64_t ns = *ns_dev;
+  const int64_t p_begin = (int64_t)blockIdx.y * slices_per_split * GRAM_SLICE;
+  const int64_t p_end = min(ns, p_begin + slices_per_split * GRAM_SLICE);
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  double accd[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accd[r][c] = 0.0;
+  for (int64_t s0 = p_begin; s0 < p_end; s0 += GRAM_SLICE) {
+    const int64_t s1 = min(p_end, s0 + GRAM_SLICE);
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int64_t p0 = s0; p0 < s1; p0 += GK) {
+#pragma unroll
+      for (int r = 0; r < (GT * GK) / GNT; ++r) {
+        const int e = t + GNT * r;
+        const int row = e / GK, col = e % GK;
+        const int64_t p = p0 + col;
+        const bool okp = p < s1;
+        As[col][row] = (okp && a0 + row < m) ? Kc.at(a0 + row, p) : 0.f;
+        Bs[col][row] = (okp && b0 + row < m) ? Kc.at(b0 + row, p) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < GK; ++kk) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) accd[r][c] += (double)acc[r][c];
+  }
+  double* P = part + (int64_t)blockIdx.y * ldp * ldp;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t a = a0 + ty + 16 * r;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t b = b0 + tx + 16 * c;
+      if (a < m && b < m) P[a * ldp + b] = accd[r][c];
+    }
+  }
+}
+
+}  // namespace
+
+int64_t gram_simt_splits(int64_t m, int64_t ns_max) {
+  const int64_t T = ceil_div(m, (int64_t)GT);
+  const int64_t tiles = T * (T + 1) / 2;
+  const int64_t slices = ceil_div(ns_max > 0 ? ns_max : 1, GRAM_SLICE);
+  int64_t want = ceil_div(2 * (int64_t)sm_count(), tiles > 0 ? tiles : 1);
+  if (want < 1) want = 1;
+  if (want > slices) want = slices;
+  return want;
+}
+
+int launch_gram_simt(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, int64_t m,
+                     double* part, int64_t ldp, int64_t splits, cudaStream_t s) {
+  const int64_t T = ceil_div(m, (int64_t)GT);
+  const int64_t tiles = T * (T + 1) / 2;
+  const int64_t slices = ceil_div(ns_max > 0 ? ns_max : 1, GRAM_SLICE);
+  const int64_t per = ceil_div(slices, splits);
+  dim3 grid((unsigned)tiles, (unsigned)splits);
+  gram_simt_kernel<<<grid, GNT, 0, s>>>(view(Kc), m, ns_dev, per, part, ldp);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+// H[a][b] = lambda * (K[b][J[a]] + K[a][J[b]]) / 2 + sum_s part[s][min][max].
+__global__ void gram_finish_kernel(const double* __restrict__ part, int64_t splits, int64_t ldp,
+                                   KView K, const int64_t* __restrict__ J, int64_t m,
+                                   double lambda, double* __restrict__ H, int64_t ldh,
+                                   int upper_only_tiles) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int64_t a = e / m, b = e % m;
+  const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  double s = 0.0;
+  for (int64_t k = 0; k < splits; ++k) s += part[k * ldp * ldp + lo * ldp + hi];
+  const double kjj = 0.5 * ((double)K.at(hi, J[lo]) + (double)K.at(lo, J[hi]));
+  H[a * ldh + b] = lambda * kjj + s;
+}
+
+int launch_gram_finish(const double* part, int64_t splits, int64_t ldp, const spsvm_kmat* K,
+                       const int64_t* J, int64_t m, double lambda, double* H, int64_t ldh,
+                       cudaStream_t s) {
+  const int64_t total = m * m;
+  gram_finish_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, splits, ldp, view(K), J,
+                                                                     m, lambda, H, ldh, 1);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+}  // namespace spsvm
+
+using namespace spsvm;
+
+extern "C" size_t spsvm_gram_scratch_bytes(int64_t m, int64_t ns) {
+  if (m < 0 || ns < 0) return 0;
+  const int64_t ldp = round_up(m > 0 ? m : 1, 64);
+  int64_t splits = gram_simt_splits(m, ns);
+  const int64_t tc = gram_tc_splits(m, ns);
+  if (tc > splits) splits = tc;
+  return (size_t)(splits * ldp * ldp * (int64_t)sizeof(double));
+}
+
+extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
+                          const spsvm_kmat* K, const int64_t* J, double lambda, int32_t precision,
+                          double* H, int64_t ldh, void* scratch, size_t scratch_bytes,
+                          void* stream) {
+  SPSVM_TRY(check_kmat(Kc, "gram(Kc)"));
+  SPSVM_TRY(check_kmat(K, "gram(K)"));
+  if (!ns_dev || !J || !H) return set_error(SPSVM_ERR_ARG, "gram: NULL pointer");
+  const int64_t m = K->rows;
+  if (Kc->rows < m || ldh < m || ns_max < 0 || ns_max > Kc->n || !(lambda > 0.0))
+    return set_error(SPSVM_ERR_ARG, "gram: bad shapes m=%lld Kc.rows=%lld ldh=%lld ns_max=%lld",
+                     (long long)m, (long long)Kc->rows, (long long)ldh, (long long)ns_max);
+  if (m == 0) return SPSVM_OK;
+  if (!scratch || scratch_bytes < spsvm_gram_scratch_bytes(m, ns_max))
+    return set_error(SPSVM_ERR_OOM, "gram: scratch too small");
+  cudaStream_t s = as_stream(stream);
+  const int64_t ldp = round_up(m, 64);
+  double* part = static_cast<double*>(scratch);
+  int64_t splits;
+  if (precision == SPSVM_BF16X3) {
+    if (Kc->format != SPSVM_BF16X3) return set_error(SPSVM_ERR_ARG, "gram: BF16X3 needs split planes");
+    splits = gram_tc_splits(m, ns_max);
+    SPSVM_TRY(launch_gram_tc(Kc, ns_dev, ns_max, m, part, ldp, splits, s));
+  } else if (precision == SPSVM_FP32) {
+    splits = gram_simt_splits(m, ns_max);
+    SPSVM_TRY(launch_gram_simt(Kc, ns_dev, ns_max, m, part, ldp, splits, s));
+  } else {
+    return set_error(SPSVM_ERR_ARG, "gram: bad precision");
+  }
+  return launch_gram_finish(part, splits, ldp, K, J, m, lambda, H, ldh, s);
+}

@@ -1,0 +1,131 @@
+// Internal helpers shared by the CUDA translation units of libspsvm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "spsvm.h"
+
+namespace spsvm {
+
+// Records a message for spsvm_last_error() and returns `code`.
+int set_error(int code, const char* fmt, ...);
+
+#define SPSVM_CUDA_TRY(expr)                                                 \
+  do {                                                                       \
+    cudaError_t e_ = (expr);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return ::spsvm::set_error(SPSVM_ERR_CUDA, "%s:%d %s: %s", __FILE__,    \
+                                __LINE__, #expr, cudaGetErrorString(e_));    \
+  } while (0)
+
+#define SPSVM_LAUNCH_CHECK()                                                 \
+  do {                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                     \
+    if (e_ != cudaSuccess)                                                   \
+      return ::spsvm::set_error(SPSVM_ERR_CUDA, "%s:%d launch: %s", __FILE__, \
+                                __LINE__, cudaGetErrorString(e_));           \
+  } while (0)
+
+#define SPSVM_TRY(expr)                                                      \
+  do {                                                                       \
+    int s_ = (expr);                                                         \
+    if (s_ != SPSVM_OK) return s_;                                           \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Checks a stored-kernel-matrix descriptor.
+int check_kmat(const spsvm_kmat* K, const char* what);
+
+// Element (row j, column i) of a stored kernel matrix as FP32.
+struct KView {
+  const void* data;
+  int32_t format;
+  int64_t ld, plane;
+  __device__ __forceinline__ float at(int64_t j, int64_t i) const {
+    if (format == SPSVM_FP32) return static_cast<const float*>(data)[j * ld + i];
+    const __nv_bfloat16* h = static_cast<const __nv_bfloat16*>(data);
+    return __bfloat162float(h[j * ld + i]) + __bfloat162float(h[plane + j * ld + i]);
+  }
+};
+
+inline KView view(const spsvm_kmat* K) {
+  return KView{K->data, K->format, K->ld, K->plane};
+}
+
+// Splits an FP32 value into BF16 hi + lo (hi = round(x), lo = round(x - hi)).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Stores an FP32 kernel value into a kernel matrix (FP32 or hi/lo planes).
+__device__ __forceinline__ void kstore(void* data, int32_t format, int64_t plane,
+                                       int64_t off, float v) {
+  if (format == SPSVM_FP32) {
+    static_cast<float*>(data)[off] = v;
+  } else {
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(data);
+    p[off] = h;
+    p[plane + off] = l;
+  }
+}
+
+// RBF value from the distance expansion; clamps rounding below zero.
+__device__ __forceinline__ float rbf_from_dot(float xn, float zn, float dot, float gamma) {
+  float d2 = fmaxf(xn + zn - 2.0f * dot, 0.0f);
+  return expf(-gamma * d2);
+}
+
+// Warp sum of a double.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh /* >= 32 entries */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (w == 0) r = warp_sum(r);
+  return r;
+}
+
+// Host-side launchers implemented in the .cu files (used by the fit).
+int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t m,
+                             float gamma, spsvm_kmat* out, int64_t row0, cudaStream_t s);
+int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m,
+                           float gamma, spsvm_kmat* out, int64_t row0, cudaStream_t s);
+bool tc_available();
+
+}  // namespace spsvm

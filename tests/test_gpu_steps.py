@@ -1,0 +1,283 @@
+"""Step-by-step parity of the CUDA path against the float64 oracle, element
+by element, on seeded inputs that span several tiles with ragged tails.
+Each step is fed the same inputs on both sides (for the HBM passes the
+oracle's own kernel matrix, rounded to the stored format), so that only the
+step under test differs.
+
+Tolerances (derived from the arithmetic, stated per test):
+  * kernel values: FP32 form, |dK| <= 2e-6 + 4 eps32 gamma (|x|^2+|z|^2);
+    BF16X3 form, split products carry 2^-16 relative error per operand, so
+    |dK| <= 6e-5 * gamma * (|x|^2 + |z|^2) + 2e-6.
+  * sums of n products in FP32 with FP64 promotion every 32 terms:
+    |err| <= 1e-5 * sum |terms|.
+  * FP64 Cholesky / solves: backward-stable, 1e-10 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import spsvm as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _data(n, d, seed, scale=1.0):
+    g = np.random.default_rng(seed)
+    X = (g.standard_normal((n, d)) * scale + 0.3).astype(np.float32)
+    y = np.where(g.random(n) < 0.5, 1.0, -1.0).astype(np.float32)
+    return X, y
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    return t if dtype is None else t.to(dtype)
+
+
+def _store(K_rows, fmt, sp):
+    """Loads a (rows x n) float64 matrix into a KMat of the given format."""
+    rows, n = K_rows.shape
+    km = sp.kmat_empty(n, rows, fmt)
+    ld = km.ld
+    K32 = torch.from_numpy(K_rows.astype(np.float32)).to(DEV)
+    if fmt == "fp32":
+        km.buf.view(-1)[: rows * ld].view(rows, ld)[:, :n] = K32
+        ref = K32.double()
+    else:
+        hi = K32.to(torch.bfloat16)
+        lo = (K32 - hi.float()).to(torch.bfloat16)
+        km.buf.view(-1)[: rows * ld].view(rows, ld)[:, :n] = hi
+        km.buf.view(-1)[km.plane: km.plane + rows * ld].view(rows, ld)[:, :n] = lo
+        ref = hi.double() + lo.double()
+    return km, ref.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import paper_1404_1066_gb300 as sp
+    sp.load()
+    return sp
+
+
+@pytest.mark.parametrize("n,d,m", [(1000, 20, 70), (257, 37, 64), (130, 5, 1), (3000, 130, 129)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_kernel_block(sp, n, d, m, prec):
+    X, _ = _data(n, d, 1)
+    gamma = 1.0 / d
+    g = np.random.default_rng(2)
+    idx = g.choice(n, size=m, replace=False).astype(np.int64)
+    P = sp.spsvm_prepare_points(_t(X), prec)
+    nrm = P.norms.cpu().numpy()
+    np.testing.assert_allclose(nrm, (X.astype(np.float64) ** 2).sum(1), rtol=1e-6)
+    km = sp.kmat_empty(n, m + 3, prec)
+    sp.spsvm_kernel_block(P, _t(idx), gamma, prec, km, row0=3)
+    torch.cuda.synchronize()
+    got = km.to_float().cpu().numpy().astype(np.float64)[3:]
+    ref = O.rbf_kernel(X, X[idx], gamma).T
+    sq = (X.astype(np.float64) ** 2).sum(1)
+    scale = gamma * (sq[None, :] + sq[idx][:, None])
+    tol = (4 * 2 ** -24 * scale + 2e-6) if prec == "fp32" else (6e-5 * scale + 2e-6)
+    assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
+    # rows before row0 untouched
+    assert float(km.to_float()[:3].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_score_candidates(sp, prec):
+    n, d = 2100, 24
+    X, y = _data(n, d, 3)
+    gamma, lam = 1.0 / d, 1e-3
+    g = np.random.default_rng(4)
+    J = g.choice(n, size=40, replace=False)
+    beta = g.standard_normal(40) * 0.3
+    o = (O.rbf_kernel(X, X[J], gamma) @ beta).astype(np.float32).astype(np.float64)
+    pool = np.setdiff1d(np.arange(n), J)
+    cand = g.choice(pool, size=100, replace=False).astype(np.int64)
+    P = sp.spsvm_prepare_points(_t(X), prec)
+    gg, hh, dd = sp.spsvm_score_candidates(P, _t(y), _t(o.astype(np.float32)), _t(cand), gamma,
+                                           lam, prec)
+    # oracle with o as given (the reg term lambda k_cJ beta is o_c)
+    delta, gr, hr = O.score_candidates(X, y.astype(np.float64), list(J), beta, o, cand, gamma, lam)
+    gr = lam * o[cand] + (gr - lam * (O.rbf_kernel(X[cand], X[J], gamma) @ beta))
+    delta = gr * gr / (2 * hr)
+    S = y * o < 1
+    res = np.where(S, o - y, 0)
+    Kc = O.rbf_kernel(X, X[cand], gamma)
+    gabs = np.abs(res) @ Kc + lam * np.abs(o[cand])
+    ktol = 4 * 2 ** -24 if prec == "fp32" else 6e-5
+    sq = (X.astype(np.float64) ** 2).sum(1)
+    kerr = ktol * gamma * (sq.max() + sq.max()) + 2e-6
+    gtol = 1e-5 * gabs + kerr * np.abs(res).sum()
+    htol = 1e-5 * hr + 2 * kerr * S.sum()
+    assert np.all(np.abs(gg.cpu().numpy() - gr) <= gtol)
+    assert np.all(np.abs(hh.cpu().numpy() - hr) <= htol)
+    # ranking agrees wherever the scores are separated by more than the error
+    dg = dd.cpu().numpy()
+    rel = np.abs(dg - delta) / delta
+    assert np.all(rel <= 2 * (gtol / np.abs(gr) + htol / hr) + 1e-12)
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("n,m", [(1000, 70), (4099, 129), (33, 1)])
+def test_outputs_gemv(sp, fmt, n, m):
+    g = np.random.default_rng(5)
+    K = np.exp(-g.random((m, n)) * 3)
+    km, Kref = _store(K, fmt, sp)
+    beta = g.standard_normal(m)
+    y = np.where(g.random(n) < 0.5, 1.0, -1.0).astype(np.float32)
+    o = torch.zeros(n, dtype=torch.float32, device=DEV)
+    active, stats = sp.spsvm_outputs(km, _t(beta), _t(y), o)
+    torch.cuda.synchronize()
+    o_ref = Kref.T @ beta
+    og = o.cpu().numpy().astype(np.float64)
+    tol = 1e-6 * (np.abs(Kref.T) @ np.abs(beta)) + 1e-7 * np.abs(o_ref)
+    assert np.all(np.abs(og - o_ref) <= tol)
+    # flags, loss and errors from the GPU's own o (same precision decides)
+    margin = y.astype(np.float32) * o.cpu().numpy()
+    np.testing.assert_array_equal(active.cpu().numpy(), (margin < 1).astype(np.uint8))
+    st = stats.cpu().numpy()
+    xi = np.maximum(0, 1 - margin.astype(np.float64))
+    assert st[0] == pytest.approx(0.5 * np.sum(xi ** 2), rel=1e-12)
+    assert st[1] == np.sum(margin <= 0)
+    assert st[2] == np.sum(margin < 1)
+    u = torch.empty(n, dtype=torch.float32, device=DEV)
+    v = g.standard_normal(m)
+    sp.spsvm_gemv(km, _t(v), u)
+    torch.cuda.synchronize()
+    u_ref = Kref.T @ v
+    assert np.all(np.abs(u.cpu().numpy() - u_ref) <= 1e-6 * (np.abs(Kref.T) @ np.abs(v)) + 1e-7 * np.abs(u_ref))
+    sp.spsvm_gemv(km, _t(v), u, accumulate=True)
+    torch.cuda.synchronize()
+    assert np.all(np.abs(u.cpu().numpy() - 2 * u_ref) <= 4e-6 * (np.abs(Kref.T) @ np.abs(v)) + 2e-7 * np.abs(u_ref))
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("n,m,p", [(5000, 70, 0.5), (1000, 8, 0.0), (1000, 9, 1.0), (777, 64, 0.03)])
+def test_compact_and_masked_products(sp, fmt, n, m, p):
+    g = np.random.default_rng(6)
+    K = np.exp(-g.random((m, n)) * 3)
+    km, Kref = _store(K, fmt, sp)
+    act = (g.random(n) < p).astype(np.uint8)
+    w1 = g.standard_normal(n).astype(np.float32)
+    w2 = g.standard_normal(n).astype(np.float32)
+    kc = sp.kmat_empty(km.ld, m, fmt, ld=km.ld)
+    a, b, nact, pos = sp.spsvm_compact_active(km, _t(act), _t(w1), _t(w2), kc)
+    torch.cuda.synchronize()
+    S = act.astype(bool)
+    ns = int(S.sum())
+    assert int(nact.item()) == ns
+    np.testing.assert_array_equal(pos.cpu().numpy()[S], np.arange(ns))
+    # the compacted rows are exact copies; the tail to a multiple of 128 is zero
+    kcf = kc.to_float().cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(kcf[:, :ns], Kref[:, S])
+    tail = ((ns + 127) // 128) * 128
+    assert np.all(kcf[:, ns:tail] == 0)
+    ra = Kref[:, S] @ w1[S].astype(np.float64)
+    rb = Kref[:, S] @ w2[S].astype(np.float64)
+    tola = 1e-6 * (np.abs(Kref[:, S]) @ np.abs(w1[S])) + 1e-12
+    tolb = 1e-6 * (np.abs(Kref[:, S]) @ np.abs(w2[S])) + 1e-12
+    assert np.all(np.abs(a.cpu().numpy() - ra) <= tola)
+    assert np.all(np.abs(b.cpu().numpy() - rb) <= tolb)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("n,m,p", [(9000, 70, 0.6), (20000, 130, 0.5), (300, 64, 1.0), (2000, 1, 0.7)])
+def test_gram(sp, prec, n, m, p):
+    g = np.random.default_rng(7)
+    n_all = n
+    X, _ = _data(n_all, 12, 8)
+    J = g.choice(n_all, size=m, replace=False)
+    K = O.rbf_kernel(X, X[J], 1.0 / 12).T          # rows = basis
+    km, Kref = _store(K, prec, sp)
+    act = (g.random(n) < p).astype(np.uint8)
+    kc = sp.kmat_empty(km.ld, m, prec, ld=km.ld)
+    _, _, nact, _ = sp.spsvm_compact_active(km, _t(act), None, None, kc)
+    lam = 1e-3
+    H = sp.spsvm_gram(kc, nact, n, km, _t(J.astype(np.int64)), lam, prec)
+    torch.cuda.synchronize()
+    S = act.astype(bool)
+    KS = Kref[:, S]
+    KJJ = Kref[:, J].T
+    Href = lam * 0.5 * (KJJ + KJJ.T) + KS @ KS.T
+    Hg = H.cpu().numpy()
+    np.testing.assert_array_equal(Hg, Hg.T)
+    bound = np.abs(KS) @ np.abs(KS).T
+    rel = 1e-5 if prec == "fp32" else 2.5e-5
+    assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))
+
+
+@pytest.mark.parametrize("m", [1, 5, 63, 64, 65, 200, 513])
+def test_cholesky_and_solve(sp, m):
+    g = np.random.default_rng(m)
+    A = g.standard_normal((m, m + 3))
+    H = A @ A.T + 1e-2 * np.eye(m)
+    Ht = _t(H.copy())
+    info = sp.spsvm_cholesky(Ht)
+    assert info == 0
+    Lg = np.tril(Ht.cpu().numpy())
+    Lr = np.linalg.cholesky(H)
+    np.testing.assert_allclose(Lg, Lr, rtol=1e-9, atol=1e-12 * np.abs(Lr).max())
+    b = g.standard_normal(m)
+    bt = _t(b.copy())
+    sp.spsvm_cholesky_solve(Ht, bt)
+    x = bt.cpu().numpy()
+    xr = np.linalg.solve(H, b)
+    assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr) * max(1, np.linalg.cond(H) * 1e-6)
+
+
+def test_cholesky_reports_indefinite(sp):
+    H = np.eye(100)
+    H[70, 70] = -1.0
+    info = sp.spsvm_cholesky(_t(H))
+    assert info == 71
+    assert sp.spsvm_cholesky(_t(np.zeros((3, 3)))) == 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_line_search(sp, seed):
+    g = np.random.default_rng(100 + seed)
+    n, m = 4000 + seed * 37, 30
+    X, y = _data(n, 6, seed)
+    y = y.astype(np.float64)
+    J = g.choice(n, size=m, replace=False)
+    KnJ = O.rbf_kernel(X, X[J], 0.2)
+    KJJ = KnJ[J]
+    lam = 1e-3
+    beta = g.standard_normal(m) * 0.5
+    o = KnJ @ beta
+    S = y * o < 1
+    H = lam * KJJ + KnJ[S].T @ KnJ[S]
+    bb = np.linalg.solve(H, KnJ[S].T @ y[S])
+    d = (bb - beta) * (1.0 if seed % 3 else 0.3)
+    u = KnJ @ d
+    o32 = o.astype(np.float32)
+    u32 = u.astype(np.float32)
+    # both sides see the FP32-rounded o and u
+    t_ref = O.line_search(beta, d, o32.astype(np.float64), u32.astype(np.float64), y, KJJ, lam)
+    # a0, a1 computed on the GPU from o_J, u_J: feed consistent values
+    t = sp.spsvm_line_search(_t(o32), _t(u32), _t(y.astype(np.float32)), _t(d), _t(J.astype(np.int64)), lam)
+    # compare through phi: the GPU step is as good as the exact minimiser
+    phi = lambda s: O.objective(beta + s * d, KnJ, KJJ, y, lam)
+    assert phi(t) <= phi(t_ref) + 1e-7 * abs(phi(t_ref))
+    assert t == pytest.approx(t_ref, rel=2e-4, abs=1e-6)
+
+
+@pytest.mark.parametrize("nq,m,d", [(1000, 70, 20), (129, 1, 3), (5000, 257, 64)])
+def test_decision(sp, nq, m, d):
+    g = np.random.default_rng(9)
+    B = g.standard_normal((m, d)).astype(np.float32)
+    Q = g.standard_normal((nq, d)).astype(np.float32)
+    beta = g.standard_normal(m)
+    gamma = 0.5 / d
+    out = sp.spsvm_decision(_t(B), _t(beta), _t(Q), gamma)
+    torch.cuda.synchronize()
+    Kq = O.rbf_kernel(Q, B, gamma)
+    ref = Kq @ beta
+    sq = (Q.astype(np.float64) ** 2).sum(1)
+    sb = (B.astype(np.float64) ** 2).sum(1)
+    krel = 4 * 2 ** -24 * gamma * (sq[:, None] + sb[None, :])
+    tol = (Kq * krel) @ np.abs(beta) + 1e-6 * (Kq @ np.abs(beta)) + 1e-7
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= tol)
