@@ -1,0 +1,355 @@
+"""SP-SVM benchmark on GB300.
+
+One step = one whole SP-SVM fit (row norms, candidate scoring, kernel-block
+growth, Newton reoptimisation with masked Gram, FP64 Cholesky, refinement and
+line search; Section 4, Eq. 4) followed by prediction on 100,000 held-out
+queries, on the Gaussian-mixture workload n = 500,000, d = 128, |J| grown 64
+at a time from 256 candidates to 4,096.  Inputs stay resident in HBM; the
+kernel matrix (8.2 GB) and X (256 MB) are far larger than L2 (129 MB), so no
+explicit L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the float64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SP-SVM fit sec & kernel TFLOP/s (n=500k,|J|=4096) vs FP32 form; serve p50/p99"
+WORKLOAD = dict(workload="gaussian_mixture_precision_form", n=500_000, d=128, basis=4096,
+                candidates=256, add_per_round=64, lam=1e-4, gamma="1/d", components=10,
+                queries=100_000)
+
+SLOTS = ["kernel_block", "score", "outputs", "gemv", "compact", "gram", "cholesky", "solve",
+         "line_search", "decision", "fit"]
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            P = json.load(f)
+        return P, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(seconds_budget=20.0, steps=1):
+    """The float64 oracle, as it stands, on a bounded sample of the workload:
+    n = 4,000 rows of the same mixture, d = 128, |J| = 256 (4 rounds of 64
+    from 256 candidates).  Returns per-step sample seconds, the factor that
+    scales a sample fit to the full workload, and the BLAS thread count."""
+    from oracle import spsvm as O
+    from paper_1404_1066_gb300 import synth
+    p = synth.gaussian_mixture(n=4000, d=128, budget=256, seed=1003)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.fit(p.X, p.y, p.gamma, p.lam, 256, tol=1e-6, kappa=256, q=64, seed=1)
+        times.append(time.perf_counter() - t0)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    # cost model of a fit: rounds ~ |J|, each Newton step ~ n |J|^2
+    factor = (500_000 / 4000) * (4096 / 256) ** 3
+    return times, factor, cores, "oracle fit on n=4,000 rows of the same mixture, d=128, |J|=256; " \
+        f"scaled by (n ratio) x (|J| ratio)^3 = {factor:.3g} to the full workload"
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_baseline_run(steps=1)
+    times, factor, cores, sample = cpu_baseline_run(steps=args.steps)
+    per = statistics.mean(times) * factor
+    line = dict(metric=METRIC, value=per, unit="s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(WORKLOAD, l2="inputs larger than L2"), impl="reference",
+                cpu_baseline=dict(value=per, unit="s", cores=cores, kind="oracle", sample=sample,
+                                  sample_seconds=times),
+                e2e=dict(value=per, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1404_1066_gb300 as sp
+    from paper_1404_1066_gb300 import synth
+    import ctypes as C
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    lib = sp.load()
+    n, d, J = args.n, args.d, args.basis
+    prec = args.precision
+    p = synth.gaussian_mixture(n=n, d=d, budget=J, seed=1003 + rank)
+    Xq_h = synth.queries_like(p, args.queries, seed=77 + rank)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    Xq = torch.from_numpy(Xq_h).cuda()
+    opts = dict(precision=prec, candidates=256, add_per_round=64, seed=1)
+    o, _ = sp.make_options(**opts)
+    wsb = lib.spsvm_fit_workspace_bytes(n, d, J, C.byref(o))
+    work = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        m = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=work, **opts)
+        f = sp.spsvm_predict(m, Xq)
+        return m, f
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    lib.spsvm_profile_enable(1)
+    launches0 = lib.spsvm_launch_count()
+    torch.cuda.synchronize()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        model, f = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = lib.spsvm_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = {}
+    for k, name in enumerate(SLOTS):
+        nm = C.c_char_p()
+        L = C.c_int64()
+        t = C.c_double()
+        w = C.c_double()
+        lib.spsvm_profile_read(k, C.byref(nm), C.byref(L), C.byref(t), C.byref(w))
+        prof[name] = dict(launches=L.value, ms=t.value, work=w.value)
+    lib.spsvm_profile_enable(0)
+    clocks = sampler.stop()
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    info = model.info()
+
+    # end to end through the public API from pinned host buffers
+    Xh = torch.from_numpy(p.X).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    Xqh = torch.from_numpy(Xq_h).pin_memory()
+    out_h = torch.empty(args.queries, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        Xd = Xh.to("cuda", non_blocking=True)
+        yd = yh.to("cuda", non_blocking=True)
+        Xqd = Xqh.to("cuda", non_blocking=True)
+        m2 = sp.spsvm_fit(Xd, yd, p.gamma, p.lam, J, 1e-6, workspace=work, **opts)
+        fo = sp.spsvm_predict(m2, Xqd)
+        out_h.copy_(fo, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    h2d = p.X.nbytes + p.y.nbytes + Xq_h.nbytes
+    d2h = args.queries * 4
+
+    # kernel-block throughput: the full n x |J| block of the final basis
+    Jidx = torch.from_numpy(model.basis_and_beta()[0]).cuda()
+    P = sp.spsvm_prepare_points(X, prec)
+    km = sp.kmat_empty(n, J, prec)
+    for _ in range(2):
+        sp.spsvm_kernel_block(P, Jidx, p.gamma, prec, km)
+    kb0 = torch.cuda.Event(enable_timing=True)
+    kb1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    kb0.record(stream)
+    for _ in range(reps):
+        sp.spsvm_kernel_block(P, Jidx, p.gamma, prec, km)
+    kb1.record(stream)
+    torch.cuda.synchronize()
+    kb_ms = kb0.elapsed_time(kb1) / reps
+    split = 3.0 if prec == "bf16x3" else 1.0
+    kb_tflops = split * 2.0 * n * J * d / (kb_ms * 1e-3) / 1e12
+    del km
+
+    # FP32 form on the same workload (one fit), for the "vs FP32 form" leg
+    fp32_form = None
+    if args.fp32_form and prec != "fp32":
+        del work
+        torch.cuda.empty_cache()
+        o32, _ = sp.make_options(**dict(opts, precision="fp32"))
+        w32 = torch.empty(lib.spsvm_fit_workspace_bytes(n, d, J, C.byref(o32)), dtype=torch.uint8,
+                          device="cuda")
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        m32 = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=w32, **dict(opts, precision="fp32"))
+        a1.record(stream)
+        torch.cuda.synchronize()
+        f32 = sp.spsvm_predict(m32, Xq).cpu().numpy()
+        fb = f.cpu().numpy()
+        fp32_form = dict(fit_s=a0.elapsed_time(a1) / 1e3,
+                         decision_max_rel_diff=float(np.max(np.abs(fb - f32) / np.maximum(1, np.abs(f32)))),
+                         newton_steps=m32.info()["newton_steps"])
+        del w32
+
+    # roofline for the dominant kernel of the step
+    peaks, src = _peaks()
+    dom = max(("gram", "cholesky", "kernel_block", "compact", "gemv", "outputs", "solve", "score",
+               "decision", "line_search"), key=lambda k: prof[k]["ms"])
+    pr = prof[dom]
+    per_launch_ms = pr["ms"] / max(1, pr["launches"])
+    per_launch_work = pr["work"] / max(1, pr["launches"])
+    if dom in ("gram", "kernel_block", "score", "decision") and prec == "bf16x3":
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = 3.0 * per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+    elif dom in ("gram", "kernel_block", "score", "decision"):
+        bound, unit = "alu", "TFLOP/s"
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x 2 flops x max clock
+    elif dom == "cholesky":
+        bound, unit = "alu", "TFLOP/s"
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        peak = 1.25                            # FP64 rate of GB300
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+    roofline = dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
+                    frac=achieved / peak, traffic=None, peak_source=src,
+                    launches=pr["launches"], ms_per_launch=per_launch_ms)
+
+    line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=False, scaling="weak",
+                vs_baseline=None, dtype="bf16x3+f64" if prec == "bf16x3" else "f32+f64",
+                data="synthetic",
+                config=dict(WORKLOAD, precision=prec, l2="inputs larger than L2 (no flush)",
+                            step="fit + predict(100k queries)", parallelism=f"replicas{ws}"),
+                e2e=dict(value=e2e_ms / 1e3, unit="s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                gpu_launches=int(launches // max(1, args.steps)),
+                clocks=clocks, roofline=roofline,
+                kernel_block=dict(ms=kb_ms, tflops=kb_tflops, n=n, basis=J, d=d),
+                fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
+                         objective=info["objective"], status=info["status"]),
+                profile={k: v for k, v in prof.items() if v["launches"]},
+                fp32_form=fp32_form)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, factor, cores, sample = cpu_baseline_run(steps=1)
+        line["cpu_baseline"] = dict(value=times[0] * factor, unit="s", cores=cores, kind="oracle",
+                                    sample=sample, sample_seconds=times[0])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--n", type=int, default=500_000)
+    ap.add_argument("--d", type=int, default=128)
+    ap.add_argument("--basis", type=int, default=4096)
+    ap.add_argument("--queries", type=int, default=100_000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp32-form", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

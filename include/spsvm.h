@@ -179,17 +179,22 @@ int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
                int32_t precision, double* H, int64_t ldh, void* scratch,
                size_t scratch_bytes, void* stream);
 
-/* FP64 Cholesky factorisation H = L L^T in place (lower triangle; the
- * strict upper triangle is not referenced), the direct solver of the Newton
- * system of Section 4's reoptimisation.  info: device int32, 0 on success,
- * else k+1 for the first non-positive pivot k.  Synchronous only in that
- * info is written by the last kernel; read it after a stream sync. */
+/* FP64 Cholesky factorisation H = L L^T in place (lower triangle, read and
+ * written), the direct solver of the Newton system of Section 4's
+ * reoptimisation.  Blocked right-looking with 64 x 64 blocks.  On success
+ * the strict upper triangle of each 64 x 64 diagonal block is overwritten
+ * with the inverse of that block of L (transposed), which
+ * spsvm_cholesky_solve uses; the rest of the upper triangle is not touched.
+ * info: device int32, 0 on success, else k+1 for the first non-positive
+ * pivot k (the factor is then incomplete).  Read info after a stream sync. */
 int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* stream);
 
-/* Solves L L^T x = b in place (b overwritten by x), FP64.  L from
- * spsvm_cholesky.  b: device FP64, m. */
+/* Solves L L^T x = b in place (b overwritten by x), FP64, by blocked
+ * forward and backward substitution (one launch per 64-row block, each
+ * spread over the GPU).  L from spsvm_cholesky.  b: device FP64, m;
+ * work: device FP64, m (overwritten). */
 int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b,
-                         void* stream);
+                         double* work, void* stream);
 
 /* Exact line search along a Newton direction (f is convex and piecewise
  * quadratic along a line; Section 4's Newton reoptimisation):
@@ -305,6 +310,27 @@ void spsvm_free(spsvm_model* model);
  * counter = round * 2^32 + k.  J, out: host.  Returns the count drawn. */
 int32_t spsvm_draw_candidates(int64_t n, const int64_t* J, int32_t nJ, int32_t kappa,
                               uint64_t seed, uint32_t round, int64_t* out);
+
+/* ---- instrumentation (no paper counterpart: measurement support) ---- */
+/* Number of CUDA kernel launches the library has issued in this process. */
+uint64_t spsvm_launch_count(void);
+/* Per-step kernel timing with CUDA events recorded on the launching stream
+ * around each step's launches.  enable(1) clears the totals and starts
+ * recording, enable(0) stops.  Slots: 0 kernel_block, 1 score, 2 outputs,
+ * 3 gemv, 4 compact, 5 gram, 6 cholesky, 7 solve, 8 line_search,
+ * 9 decision, 10 fit.  read() waits for the recorded events and returns the
+ * launch count, total milliseconds and total algorithmic work (flops for
+ * kernel_block / score / gram / cholesky / decision, bytes for the HBM
+ * passes) of a slot.  `name` receives a static string. */
+int spsvm_profile_enable(int32_t on);
+int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches, double* ms,
+                       double* work);
+
+/* Status word of the tensor-core kernels.  Every wait inside them is
+ * bounded; a wait that gives up records a nonzero site code here and the
+ * kernel returns without its result.  Reads and clears the word (a
+ * synchronous copy from the device); returns OK, or TIMEOUT with *code set. */
+int spsvm_device_status(int32_t* code);
 
 const char* spsvm_strerror(int code);
 const char* spsvm_last_error(void);

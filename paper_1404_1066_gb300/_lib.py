@@ -79,7 +79,7 @@ SIGNATURES = {
     "spsvm_gram": (_I32, [C.POINTER(spsvm_kmat), _P, _I64, C.POINTER(spsvm_kmat), _P, _D, _I32,
                           _P, _I64, _P, _SZ, _P]),
     "spsvm_cholesky": (_I32, [_P, _I64, _I64, _P, _P]),
-    "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P]),
+    "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P, _P]),
     "spsvm_line_scratch_bytes": (_SZ, [_I64]),
     "spsvm_line_search": (_I32, [_P, _P, _P, _I64, _P, _P, _I32, _D, C.POINTER(_D), _P, _P, _SZ,
                                  _P]),
@@ -99,6 +99,11 @@ SIGNATURES = {
     "spsvm_model_outputs": (_I32, [_P, _P, _I64]),
     "spsvm_free": (None, [_P]),
     "spsvm_draw_candidates": (_I32, [_I64, _P, _I32, _I32, C.c_uint64, C.c_uint32, _P]),
+    "spsvm_launch_count": (C.c_uint64, []),
+    "spsvm_profile_enable": (_I32, [_I32]),
+    "spsvm_profile_read": (_I32, [_I32, C.POINTER(C.c_char_p), C.POINTER(_I64), C.POINTER(_D),
+                                  C.POINTER(_D)]),
+    "spsvm_device_status": (_I32, [C.POINTER(_I32)]),
     "spsvm_strerror": (C.c_char_p, [_I32]),
     "spsvm_last_error": (C.c_char_p, []),
     "spsvm_version": (C.c_char_p, []),

@@ -199,7 +199,9 @@ def spsvm_cholesky(H: torch.Tensor):
 
 
 def spsvm_cholesky_solve(Lf: torch.Tensor, b: torch.Tensor):
-    check(_lib().spsvm_cholesky_solve(ptr(Lf), Lf.shape[0], Lf.stride(0), ptr(b), stream_ptr()),
+    work = torch.empty(max(1, Lf.shape[0]), dtype=torch.float64, device=Lf.device)
+    check(_lib().spsvm_cholesky_solve(ptr(Lf), Lf.shape[0], Lf.stride(0), ptr(b), ptr(work),
+                                      stream_ptr()),
           "spsvm_cholesky_solve")
     return b
 

@@ -142,59 +142,105 @@ __global__ void __launch_bounds__(256) syrk_trailing(double* __restrict__ H, int
   }
 }
 
-// L L^T x = b in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) chol_solve_kernel(const double* __restrict__ L,
-                                                          int64_t ldh, int64_t m,
-                                                          double* __restrict__ b) {
+// Inverse of each lower-triangular diagonal block L_kk, stored transposed in
+// the (otherwise unused) strict upper triangle of the block: element (i, j),
+// i > j, of inv(L_kk) at H[(k0 + j) * ldh + k0 + i].  The diagonal of the
+// inverse is 1 / L_ii and is not stored.
+__global__ void __launch_bounds__(64) diag_inverse(double* __restrict__ H, int64_t ldh, int64_t m) {
+  __shared__ double Ls[NB][NB + 1];
+  const int64_t k0 = (int64_t)blockIdx.x * NB;
+  const int nb = (int)min64(NB, m - k0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ls[r][c] = (r < nb && c <= r) ? H[(k0 + r) * ldh + k0 + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // thread j solves L x = e_j (column j of the inverse) for rows i > j and
+  // keeps x_i in its own row of the upper triangle, Ls[j][i]; it reads only
+  // the lower triangle (Ls[i][l], l < i) and its own row.
+  const int j = threadIdx.x;
+  if (j < nb) {
+    const double xj = 1.0 / Ls[j][j];
+    for (int i = j + 1; i < nb; ++i) {
+      double acc = Ls[i][j] * xj;
+      for (int l = j + 1; l < i; ++l) acc += Ls[i][l] * Ls[j][l];
+      Ls[j][i] = -acc / Ls[i][i];
+    }
+    for (int i = j + 1; i < nb; ++i) H[(k0 + j) * ldh + k0 + i] = Ls[j][i];
+  }
+}
+
+// inv(L_kk)[i][j] for i >= j from the stored block inverse.
+__device__ __forceinline__ double inv_at(const double* __restrict__ L, int64_t ldh, int64_t k0,
+                                         int i, int j) {
+  return (i == j) ? 1.0 / L[(k0 + i) * ldh + k0 + i] : L[(k0 + j) * ldh + k0 + i];
+}
+
+constexpr int SV_T = 256;
+constexpr int SV_ROWS = 64;   // rows updated per block (8 warps x 8 rows)
+
+// Forward step for block k: z_k = inv(L_kk) b_k (into z), b_r -= L[r][k] z_k
+// for the rows r below the block handled by this CTA.
+__global__ void __launch_bounds__(SV_T) trsv_fwd_step(const double* __restrict__ L, int64_t ldh,
+                                                      int64_t m, int64_t k0,
+                                                      double* __restrict__ b,
+                                                      double* __restrict__ z) {
+  __shared__ double zs[NB];
+  __shared__ double bs[NB];
+  const int nb = (int)min64(NB, m - k0);
+  if (threadIdx.x < NB) bs[threadIdx.x] = threadIdx.x < nb ? b[k0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  {
+    // 4 threads per row of the block
+    const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+    double acc = 0.0;
+    if (i < nb)
+      for (int j = q; j <= i; j += 4) acc += inv_at(L, ldh, k0, i, j) * bs[j];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (q == 0 && i < NB) zs[i] = (i < nb) ? acc : 0.0;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < nb) z[k0 + threadIdx.x] = zs[threadIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = k0 + nb + (int64_t)blockIdx.x * SV_ROWS;
+  for (int rr = warp; rr < SV_ROWS; rr += SV_T / 32) {
+    const int64_t r = r0 + rr;
+    if (r >= m) break;
+    double s = 0.0;
+    for (int l = lane; l < nb; l += 32) s += L[r * ldh + k0 + l] * zs[l];
+    s = warp_sum(s);
+    if (lane == 0) b[r] -= s;
+  }
+}
+
+// Backward step for block k: x_k = inv(L_kk)^T z_k (into x), z_r -= sum_l
+// L[k0+l][r] x_l for the rows r < k0 handled by this CTA.
+__global__ void __launch_bounds__(SV_T) trsv_bwd_step(const double* __restrict__ L, int64_t ldh,
+                                                      int64_t m, int64_t k0,
+                                                      double* __restrict__ z,
+                                                      double* __restrict__ x) {
   __shared__ double xs[NB];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // forward: L z = b
-  for (int64_t k0 = 0; k0 < m; k0 += NB) {
-    const int nb = (int)min64(NB, m - k0);
-    if (warp == 0) {
-      for (int j = 0; j < nb; ++j) {
-        double s = 0.0;
-        for (int l = lane; l < j; l += 32) s += L[(k0 + j) * ldh + k0 + l] * xs[l];
-        s = warp_sum(s);
-        if (lane == 0) xs[j] = (b[k0 + j] - s) / L[(k0 + j) * ldh + k0 + j];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) b[k0 + threadIdx.x] = xs[threadIdx.x];
-    // update the rows below: b_r -= L[r][k0:k0+nb] . z_k
-    for (int64_t r = k0 + nb + warp; r < m; r += nw) {
-      double s = 0.0;
-      for (int l = lane; l < nb; l += 32) s += L[r * ldh + k0 + l] * xs[l];
-      s = warp_sum(s);
-      if (lane == 0) b[r] -= s;
-    }
-    __syncthreads();
+  __shared__ double zsh[NB];
+  const int nb = (int)min64(NB, m - k0);
+  if (threadIdx.x < NB) zsh[threadIdx.x] = threadIdx.x < nb ? z[k0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  {
+    const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
+    double acc = 0.0;
+    if (j < nb)
+      for (int i = j + q; i < nb; i += 4) acc += inv_at(L, ldh, k0, i, j) * zsh[i];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (q == 0 && j < NB) xs[j] = (j < nb) ? acc : 0.0;
   }
-  // backward: L^T x = z
-  const int64_t nblk = ceil_div(m, (int64_t)NB);
-  for (int64_t kb = nblk - 1; kb >= 0; --kb) {
-    const int64_t k0 = kb * NB;
-    const int nb = (int)min64(NB, m - k0);
-    if (warp == 0) {
-      for (int j = nb - 1; j >= 0; --j) {
-        double s = 0.0;
-        for (int l = j + 1 + lane; l < nb; l += 32) s += L[(k0 + l) * ldh + k0 + j] * xs[l];
-        s = warp_sum(s);
-        if (lane == 0) xs[j] = (b[k0 + j] - s) / L[(k0 + j) * ldh + k0 + j];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) b[k0 + threadIdx.x] = xs[threadIdx.x];
-    // z_r -= sum_{l in block} L[l][r] x_l for r < k0
-    for (int64_t r = threadIdx.x; r < k0; r += blockDim.x) {
-      double s = 0.0;
-      for (int l = 0; l < nb; ++l) s += L[(k0 + l) * ldh + r] * xs[l];
-      b[r] -= s;
-    }
-    __syncthreads();
-  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < nb) x[k0 + threadIdx.x] = xs[threadIdx.x];
+  const int64_t r = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (r >= k0) return;
+  double s = 0.0;
+  for (int l = 0; l < nb; ++l) s += L[(k0 + l) * ldh + r] * xs[l];
+  z[r] -= s;
 }
 
 }  // namespace
@@ -205,6 +251,7 @@ using namespace spsvm;
 extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* stream) {
   if (!H || !info || m < 0 || ldh < m) return set_error(SPSVM_ERR_ARG, "cholesky: bad arguments");
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   for (int64_t k0 = 0; k0 < m; k0 += NB) {
     potrf_diag<<<1, 256, 0, s>>>(H, ldh, m, k0, info);
@@ -217,14 +264,32 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
     syrk_trailing<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
   }
+  if (m > 0) {
+    diag_inverse<<<(unsigned)ceil_div(m, (int64_t)NB), 64, 0, s>>>(H, ldh, m);
+    SPSVM_LAUNCH_CHECK();
+  }
   return SPSVM_OK;
 }
 
 extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b,
-                                    void* stream) {
-  if (!L || !b || m < 0 || ldh < m) return set_error(SPSVM_ERR_ARG, "cholesky_solve: bad arguments");
+                                    double* work, void* stream) {
+  if (!L || !b || !work || m < 0 || ldh < m)
+    return set_error(SPSVM_ERR_ARG, "cholesky_solve: bad arguments");
   if (m == 0) return SPSVM_OK;
-  chol_solve_kernel<<<1, 1024, 0, as_stream(stream)>>>(L, ldh, m, b);
-  SPSVM_LAUNCH_CHECK();
+  cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_SOLVE, s, 8.0 * (double)m * m);
+  // forward: rows below each block are updated in b, z_k goes to work
+  for (int64_t k0 = 0; k0 < m; k0 += NB) {
+    const int64_t below = m - min64(m, k0 + NB);
+    const unsigned grid = (unsigned)(below > 0 ? ceil_div(below, (int64_t)SV_ROWS) : 1);
+    trsv_fwd_step<<<grid, SV_T, 0, s>>>(L, ldh, m, k0, b, work);
+    SPSVM_LAUNCH_CHECK();
+  }
+  // backward: rows above each block are updated in work, x_k goes to b
+  for (int64_t k0 = ((m - 1) / NB) * NB; k0 >= 0; k0 -= NB) {
+    const unsigned grid = (unsigned)(k0 > 0 ? ceil_div(k0, (int64_t)SV_T) : 1);
+    trsv_bwd_step<<<grid, SV_T, 0, s>>>(L, ldh, m, k0, work, b);
+    SPSVM_LAUNCH_CHECK();
+  }
   return SPSVM_OK;
 }

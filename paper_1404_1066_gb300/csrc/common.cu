@@ -3,6 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -71,9 +74,106 @@ __global__ void prepare_points_kernel(const float* __restrict__ X, int64_t n, in
   }
 }
 
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- kernel timing -----------------------------------------------------
+namespace {
+const char* kSlotNames[PROF_SLOTS] = {"kernel_block", "score", "outputs", "gemv", "compact",
+                                      "gram", "cholesky", "solve", "line_search", "decision",
+                                      "fit"};
+struct Pending {
+  int slot;
+  cudaEvent_t e0, e1;
+  double work;
+};
+struct Totals {
+  long long launches = 0;
+  double ms = 0.0, work = 0.0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+Totals g_totals[PROF_SLOTS];
+
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void resolve_locked() {
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      g_totals[p.slot].launches += 1;
+      g_totals[p.slot].ms += ms;
+      g_totals[p.slot].work += p.work;
+    } else {
+      cudaGetLastError();
+    }
+    g_free_events.push_back(p.e0);
+    g_free_events.push_back(p.e1);
+  }
+  g_pending.clear();
+}
+}  // namespace
+
+ProfScope::ProfScope(int slot_, cudaStream_t s_, double work_)
+    : slot(slot_), s(s_), work(work_), e0(nullptr) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  cudaEvent_t e = take_event();
+  if (e && cudaEventRecord(e, s) == cudaSuccess) e0 = e;
+}
+
+ProfScope::~ProfScope() {
+  if (!e0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e1 = take_event();
+  if (!e1 || cudaEventRecord(e1, s) != cudaSuccess) {
+    g_free_events.push_back(static_cast<cudaEvent_t>(e0));
+    return;
+  }
+  g_pending.push_back(Pending{slot, static_cast<cudaEvent_t>(e0), e1, work});
+  if (g_pending.size() > 4096) resolve_locked();
+}
+
 }  // namespace spsvm
 
 using namespace spsvm;
+
+extern "C" uint64_t spsvm_launch_count(void) { return g_launches.load(); }
+
+extern "C" int spsvm_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  resolve_locked();
+  for (auto& t : g_totals) t = Totals{};
+  g_prof_on = on != 0;
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches,
+                                  double* ms, double* work) {
+  if (slot < 0 || slot >= PROF_SLOTS) return set_error(SPSVM_ERR_ARG, "profile_read: bad slot");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  resolve_locked();
+  if (name) *name = kSlotNames[slot];
+  if (launches) *launches = g_totals[slot].launches;
+  if (ms) *ms = g_totals[slot].ms;
+  if (work) *work = g_totals[slot].work;
+  return SPSVM_OK;
+}
 
 extern "C" const char* spsvm_strerror(int code) {
   switch (code) {

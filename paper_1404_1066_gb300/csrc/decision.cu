@@ -142,6 +142,7 @@ extern "C" int spsvm_decision(const float* B, int64_t m, int64_t ldb, const doub
   if (!scratch || scratch_bytes < spsvm_decision_scratch_bytes(nq, m, d))
     return set_error(SPSVM_ERR_OOM, "decision: scratch too small");
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_DECISION, s, 2.0 * (double)nq * m * (double)d);
   float* bnorm = static_cast<float*>(scratch);
   if (m > 0) {
     row_norms_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(B, m, d, ldb, bnorm);

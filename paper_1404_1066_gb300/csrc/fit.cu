@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "gram.h"
 
 struct spsvm_model {
   int64_t n = 0, d = 0;
@@ -148,7 +149,7 @@ int grid_for(int64_t n, int threads) {
 struct Layout {
   int64_t n, d, ldn, ldh, jcap, kappa, q;
   size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
-      off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_ws, off_J, off_cand,
+      off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_ws, off_sv, off_J, off_cand,
       off_cg, off_ch, off_cd, off_small, off_scratch, total;
   size_t scratch_bytes;
   size_t kbytes;
@@ -193,6 +194,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_rhs = take(L.jcap * 8);
   L.off_tmp = take(L.jcap * 8);
   L.off_ws = take(L.jcap * 8);
+  L.off_sv = take(L.jcap * 8);
   L.off_J = take(L.jcap * 8);
   L.off_cand = take(kappa * 8);
   L.off_cg = take(kappa * 8);
@@ -274,6 +276,10 @@ struct Fit {
 
   int sync() {
     SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (op.precision == SPSVM_BF16X3) {
+      int32_t code = 0;
+      SPSVM_TRY(spsvm_device_status(&code));
+    }
     return SPSVM_OK;
   }
 
@@ -343,14 +349,14 @@ struct Fit {
         break;
       }
       // Newton system on the active set
-      SPSVM_TRY(spsvm_gram(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s));
+      SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s, st[2]));
       SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, s));
       int32_t info_h = 0;
       SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
       if (info_h != 0) {
         // one retry with a diagonal shift of 1e-10 trace(H) / |J|
-        SPSVM_TRY(spsvm_gram(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s));
+        SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s, st[2]));
         diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
         SPSVM_LAUNCH_CHECK();
         double tr = 0.0;
@@ -367,14 +373,14 @@ struct Fit {
       }
       // d = -H^{-1} g, then refinement against the exactly applied H
       SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, s));
+      SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, at<double>(L.off_sv), s));
       SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
       for (int k = 0; k < op.refine; ++k) {
         SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
                                        at<int32_t>(L.off_pos), scratch, sb, s));
         refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
         SPSVM_LAUNCH_CHECK();
-        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, s));
+        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, at<double>(L.off_sv), s));
         axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
         SPSVM_LAUNCH_CHECK();
         SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
@@ -412,6 +418,7 @@ struct Fit {
 
   int run() {
     s = op.stream;
+    ProfScope prof(PROF_FIT, s, 1.0);
     std::memset(&pts, 0, sizeof(pts));
     pts.X = X;
     pts.n = n;

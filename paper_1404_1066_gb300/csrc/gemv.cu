@@ -336,6 +336,7 @@ extern "C" int spsvm_outputs(const spsvm_kmat* K, const double* beta, const floa
   if (stats && (!scratch || scratch_bytes < spsvm_reduce_scratch_bytes(K->n)))
     return set_error(SPSVM_ERR_OOM, "outputs: scratch too small");
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_OUTPUTS, s, beta ? 4.0 * (double)K->rows * K->n : 9.0 * K->n);
   const int64_t blocks = ceil_div(K->n, GV_PTS);
   double* part = stats ? static_cast<double*>(scratch) : nullptr;
   outputs_kernel<<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y, o, active,
@@ -354,6 +355,7 @@ extern "C" int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_
   if (!v || !u) return set_error(SPSVM_ERR_ARG, "gemv: NULL pointer");
   if (K->n == 0) return SPSVM_OK;
   const int64_t blocks = ceil_div(K->n, GV_PTS);
+  ProfScope prof(PROF_GEMV, as_stream(stream), 4.0 * (double)K->rows * K->n);
   gemv_kernel<<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(view(K), K->rows, K->n, v, u,
                                                                 accumulate);
   SPSVM_LAUNCH_CHECK();
@@ -395,6 +397,7 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
   if (!scratch || scratch_bytes < spsvm_compact_scratch_bytes(K->n, K->rows))
     return set_error(SPSVM_ERR_OOM, "compact: scratch too small");
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_COMPACT, s, 4.0 * (double)K->rows * K->n);
   const int64_t n = K->n;
   const int64_t sb = ceil_div(n, SC_PTS);
   int32_t* counts = static_cast<int32_t*>(scratch);

@@ -11,6 +11,10 @@ int64_t gram_simt_splits(int64_t m, int64_t ns_max);
 int launch_gram_simt(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, int64_t m,
                      double* part, int64_t ldp, int64_t splits, cudaStream_t s);
 
+int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const spsvm_kmat* K,
+              const int64_t* J, double lambda, int32_t precision, double* H, int64_t ldh,
+              void* scratch, size_t scratch_bytes, cudaStream_t s, double ns_work);
+
 int64_t gram_tc_splits(int64_t m, int64_t ns_max);
 int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, int64_t m,
                    double* part, int64_t ldp, int64_t splits, cudaStream_t s);

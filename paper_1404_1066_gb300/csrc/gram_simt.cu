@@ -152,10 +152,10 @@ extern "C" size_t spsvm_gram_scratch_bytes(int64_t m, int64_t ns) {
   return (size_t)(splits * ldp * ldp * (int64_t)sizeof(double));
 }
 
-extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
-                          const spsvm_kmat* K, const int64_t* J, double lambda, int32_t precision,
-                          double* H, int64_t ldh, void* scratch, size_t scratch_bytes,
-                          void* stream) {
+namespace spsvm {
+int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const spsvm_kmat* K,
+              const int64_t* J, double lambda, int32_t precision, double* H, int64_t ldh,
+              void* scratch, size_t scratch_bytes, cudaStream_t s, double ns_work) {
   SPSVM_TRY(check_kmat(Kc, "gram(Kc)"));
   SPSVM_TRY(check_kmat(K, "gram(K)"));
   if (!ns_dev || !J || !H) return set_error(SPSVM_ERR_ARG, "gram: NULL pointer");
@@ -166,7 +166,8 @@ extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t n
   if (m == 0) return SPSVM_OK;
   if (!scratch || scratch_bytes < spsvm_gram_scratch_bytes(m, ns_max))
     return set_error(SPSVM_ERR_OOM, "gram: scratch too small");
-  cudaStream_t s = as_stream(stream);
+  // algorithmic work: one multiply-add per active point per unique entry
+  ProfScope prof(PROF_GRAM, s, ns_work * (double)m * (double)(m + 1));
   const int64_t ldp = round_up(m, 64);
   double* part = static_cast<double*>(scratch);
   int64_t splits;
@@ -181,4 +182,13 @@ extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t n
     return set_error(SPSVM_ERR_ARG, "gram: bad precision");
   }
   return launch_gram_finish(part, splits, ldp, K, J, m, lambda, H, ldh, s);
+}
+}  // namespace spsvm
+
+extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
+                          const spsvm_kmat* K, const int64_t* J, double lambda, int32_t precision,
+                          double* H, int64_t ldh, void* scratch, size_t scratch_bytes,
+                          void* stream) {
+  return gram_impl(Kc, ns_dev, ns_max, K, J, lambda, precision, H, ldh, scratch, scratch_bytes,
+                   as_stream(stream), (double)ns_max);
 }

@@ -21,8 +21,11 @@ int set_error(int code, const char* fmt, ...);
                                 __LINE__, #expr, cudaGetErrorString(e_));    \
   } while (0)
 
+void count_launch();
+
 #define SPSVM_LAUNCH_CHECK()                                                 \
   do {                                                                       \
+    ::spsvm::count_launch();                                                 \
     cudaError_t e_ = cudaGetLastError();                                     \
     if (e_ != cudaSuccess)                                                   \
       return ::spsvm::set_error(SPSVM_ERR_CUDA, "%s:%d launch: %s", __FILE__, \
@@ -120,6 +123,20 @@ __device__ __forceinline__ T block_sum(T v, T* sh /* >= 32 entries */) {
   if (w == 0) r = warp_sum(r);
   return r;
 }
+
+// Kernel timing slots (CUDA events on the launching stream, when enabled).
+enum ProfSlot {
+  PROF_KERNEL_BLOCK = 0, PROF_SCORE, PROF_OUTPUTS, PROF_GEMV, PROF_COMPACT, PROF_GRAM,
+  PROF_CHOLESKY, PROF_SOLVE, PROF_LINE, PROF_DECISION, PROF_FIT, PROF_SLOTS
+};
+struct ProfScope {
+  int slot;
+  cudaStream_t s;
+  double work;
+  void* e0;
+  ProfScope(int slot, cudaStream_t s, double work);
+  ~ProfScope();
+};
 
 // Host-side launchers implemented in the .cu files (used by the fit).
 int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t m,

@@ -202,6 +202,7 @@ extern "C" int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int
     return set_error(SPSVM_ERR_ARG, "kernel_block: m=%d row0=%lld rows=%lld n=%lld/%lld gamma=%g",
                      m, (long long)row0, (long long)out->rows, (long long)out->n,
                      (long long)p->n, (double)gamma);
+  ProfScope prof(PROF_KERNEL_BLOCK, as_stream(stream), 2.0 * (double)p->n * m * (double)p->d);
   if (precision == SPSVM_BF16X3) {
     if (out->format != SPSVM_BF16X3 || !p->hi || !p->lo)
       return set_error(SPSVM_ERR_ARG, "kernel_block: BF16X3 needs split planes and BF16X3 output");
@@ -237,6 +238,7 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
     return set_error(SPSVM_ERR_OOM, "score_candidates: scratch %zu < %zu", scratch_bytes,
                      spsvm_score_scratch_bytes(p->n, kappa));
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_SCORE, s, 2.0 * (double)p->n * kappa * (double)p->d);
   double2* part = static_cast<double2*>(scratch);
   int64_t tiles = ceil_div(p->n, TM);
   if (precision == SPSVM_BF16X3) {

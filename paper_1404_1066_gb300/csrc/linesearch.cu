@@ -122,6 +122,7 @@ extern "C" int spsvm_line_search(const float* o, const float* u, const float* y,
   if (!scratch || scratch_bytes < spsvm_line_scratch_bytes(n))
     return set_error(SPSVM_ERR_OOM, "line_search: scratch too small");
   cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_LINE, s, 12.0 * (double)n);
   const int nb = ls_blocks();
   double* coef = static_cast<double*>(scratch);
   LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
