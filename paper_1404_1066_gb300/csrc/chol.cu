@@ -8,93 +8,84 @@ namespace spsvm {
 
 namespace {
 
-constexpr int NB = 64;
+constexpr int NB = 64;   // diagonal blocks of the triangular solve
+constexpr int PB = 32;   // panel width of the factorisation
 
-__global__ void __launch_bounds__(256) potrf_diag(double* __restrict__ H, int64_t ldh, int64_t m,
-                                                  int64_t k0, int32_t* __restrict__ info) {
-  __shared__ double A[NB][NB + 1];
-  __shared__ int fail;
+// Factors the PB x PB diagonal block at k0 in place, one warp: thread i owns
+// row i of the block in shared memory.
+__global__ void __launch_bounds__(32) potrf_diag(double* __restrict__ H, int64_t ldh, int64_t m,
+                                                 int64_t k0, int32_t* __restrict__ info) {
+  __shared__ double A[PB][PB + 1];
   if (*info != 0) return;
-  const int nb = (int)min64(NB, m - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    A[r][c] = (r < nb && c <= r) ? H[(k0 + r) * ldh + k0 + c] : 0.0;
-  }
-  if (threadIdx.x == 0) fail = 0;
-  __syncthreads();
+  const int nb = (int)min64(PB, m - k0);
+  const int i = threadIdx.x;
+  for (int c = 0; c < PB; ++c)
+    A[i][c] = (i < nb && c <= i) ? H[(k0 + i) * ldh + k0 + c] : 0.0;
+  __syncwarp();
+  int fail = 0;
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
+    if (i == j) {
       const double d = A[j][j];
-      if (!(d > 0.0)) {
-        fail = j + 1;
-      } else {
-        A[j][j] = sqrt(d);
-      }
+      A[j][j] = (d > 0.0) ? sqrt(d) : d;
     }
-    __syncthreads();
-    if (fail) break;
-    const double inv = 1.0 / A[j][j];
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] *= inv;
-    __syncthreads();
-    // trailing update of the lower triangle: rows i > j, columns j < l <= i
-    const int w = nb - j - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int i = j + 1 + e / w, l = j + 1 + e % w;
-      if (l <= i) A[i][l] -= A[i][j] * A[l][j];
+    __syncwarp();
+    const double piv = A[j][j];
+    if (!(piv > 0.0)) {
+      fail = j + 1;
+      break;
     }
-    __syncthreads();
+    if (i > j && i < nb) A[i][j] /= piv;
+    __syncwarp();
+    if (i > j && i < nb) {
+      const double aij = A[i][j];
+      for (int l = j + 1; l <= i; ++l) A[i][l] -= aij * A[l][j];
+    }
+    __syncwarp();
   }
   if (fail) {
-    if (threadIdx.x == 0) *info = (int32_t)(k0 + fail);
+    if (i == 0) *info = (int32_t)(k0 + fail);
     return;
   }
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (r < nb && c <= r) H[(k0 + r) * ldh + k0 + c] = A[r][c];
-  }
+  if (i < nb)
+    for (int c = 0; c <= i; ++c) H[(k0 + i) * ldh + k0 + c] = A[i][c];
 }
 
-// Rows r >= k0 + NB: L[r][k0:k0+nb] = H[r][k0:k0+nb] L_kk^{-T}.
-__global__ void __launch_bounds__(128) trsm_panel(double* __restrict__ H, int64_t ldh, int64_t m,
-                                                  int64_t k0, const int32_t* __restrict__ info) {
-  __shared__ double L[NB][NB + 1];
+// Rows r >= k0 + PB: L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, one thread per row.
+__global__ void __launch_bounds__(32) trsm_panel(double* __restrict__ H, int64_t ldh, int64_t m,
+                                                 int64_t k0, const int32_t* __restrict__ info) {
+  __shared__ double L[PB][PB + 1];
   if (*info != 0) return;
-  const int nb = (int)min64(NB, m - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    double v = 0.0;
-    if (r < nb && c <= r) v = H[(k0 + r) * ldh + k0 + c];
-    else if (r == c) v = 1.0;   // identity padding of a partial block
-    L[r][c] = v;
+  for (int e = threadIdx.x; e < PB * PB; e += blockDim.x) {
+    const int r = e / PB, c = e % PB;
+    L[r][c] = (c <= r) ? H[(k0 + r) * ldh + k0 + c] : 0.0;
   }
   __syncthreads();
-  const int64_t r = k0 + NB + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = k0 + PB + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m) return;
   double* row = H + r * ldh + k0;
-  double x[NB];
+  double x[PB];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) x[j] = (j < nb) ? row[j] : 0.0;
+  for (int j = 0; j < PB; ++j) x[j] = row[j];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
+  for (int j = 0; j < PB; ++j) {
     double s = x[j];
 #pragma unroll
     for (int l = 0; l < j; ++l) s -= x[l] * L[j][l];
     x[j] = s / L[j][j];
   }
 #pragma unroll
-  for (int j = 0; j < NB; ++j)
-    if (j < nb) row[j] = x[j];
+  for (int j = 0; j < PB; ++j) row[j] = x[j];
 }
 
-// Trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l] for r >= c >= k0 + NB.
+// Trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l] for r >= c >= k0 + PB,
+// 64 x 64 lower tiles.
 __global__ void __launch_bounds__(256) syrk_trailing(double* __restrict__ H, int64_t ldh,
                                                      int64_t m, int64_t k0,
                                                      const int32_t* __restrict__ info) {
   __shared__ double Ar[16][64 + 1];
   __shared__ double Ac[16][64 + 1];
   if (*info != 0) return;
-  const int nb = (int)min64(NB, m - k0);
-  const int64_t base = k0 + NB;
+  const int64_t base = k0 + PB;
   const int64_t T = ceil_div(m - base, (int64_t)64);
   // lower tile (ti >= tj) from the linear block index
   int64_t t = blockIdx.x, ti = 0;
@@ -108,13 +99,13 @@ __global__ void __launch_bounds__(256) syrk_trailing(double* __restrict__ H, int
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  for (int l0 = 0; l0 < nb; l0 += 16) {
+#pragma unroll
+  for (int l0 = 0; l0 < PB; l0 += 16) {
     for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
       const int rr = e / 16, ll = e % 16;
       const int64_t gr = r0 + rr, gc = c0 + rr;
-      const bool okl = l0 + ll < nb;
-      Ar[ll][rr] = (okl && gr < m) ? H[gr * ldh + k0 + l0 + ll] : 0.0;
-      Ac[ll][rr] = (okl && gc < m) ? H[gc * ldh + k0 + l0 + ll] : 0.0;
+      Ar[ll][rr] = (gr < m) ? H[gr * ldh + k0 + l0 + ll] : 0.0;
+      Ac[ll][rr] = (gc < m) ? H[gc * ldh + k0 + l0 + ll] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -170,76 +161,92 @@ __global__ void __launch_bounds__(64) diag_inverse(double* __restrict__ H, int64
   }
 }
 
-// inv(L_kk)[i][j] for i >= j from the stored block inverse.
-__device__ __forceinline__ double inv_at(const double* __restrict__ L, int64_t ldh, int64_t k0,
-                                         int i, int j) {
-  return (i == j) ? 1.0 / L[(k0 + i) * ldh + k0 + i] : L[(k0 + j) * ldh + k0 + i];
+constexpr int SV_T = 256;
+
+// Loads inv(L_kk) (lower, 64 x 64, zero above the diagonal) of block k0.
+__device__ __forceinline__ void load_block_inverse(const double* __restrict__ L, int64_t ldh,
+                                                   int64_t k0, int nb, double (*Li)[NB + 1]) {
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int j = e / NB, i = e % NB;   // i fastest: row k0+j of the stored inverse
+    double v = 0.0;
+    if (i < nb && j < nb) {
+      if (i == j) v = 1.0 / L[(k0 + i) * ldh + k0 + i];
+      else if (j < i) v = L[(k0 + j) * ldh + k0 + i];
+    }
+    Li[i][j] = v;
+  }
 }
 
-constexpr int SV_T = 256;
-constexpr int SV_ROWS = 64;   // rows updated per block (8 warps x 8 rows)
-
-// Forward step for block k: z_k = inv(L_kk) b_k (into z), b_r -= L[r][k] z_k
-// for the rows r below the block handled by this CTA.
+// Forward step for block k: z_k = inv(L_kk) b_k (into z), then b_r -= L[r][k] z_k
+// for the rows below the block, one thread per row.
 __global__ void __launch_bounds__(SV_T) trsv_fwd_step(const double* __restrict__ L, int64_t ldh,
                                                       int64_t m, int64_t k0,
                                                       double* __restrict__ b,
                                                       double* __restrict__ z) {
+  __shared__ double Li[NB][NB + 1];
   __shared__ double zs[NB];
   __shared__ double bs[NB];
   const int nb = (int)min64(NB, m - k0);
+  load_block_inverse(L, ldh, k0, nb, Li);
   if (threadIdx.x < NB) bs[threadIdx.x] = threadIdx.x < nb ? b[k0 + threadIdx.x] : 0.0;
   __syncthreads();
   {
-    // 4 threads per row of the block
     const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
     double acc = 0.0;
-    if (i < nb)
-      for (int j = q; j <= i; j += 4) acc += inv_at(L, ldh, k0, i, j) * bs[j];
+#pragma unroll
+    for (int j = q; j < NB; j += 4) acc += Li[i][j] * bs[j];
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (q == 0 && i < NB) zs[i] = (i < nb) ? acc : 0.0;
+    if (q == 0) zs[i] = acc;
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x < nb) z[k0 + threadIdx.x] = zs[threadIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t r0 = k0 + nb + (int64_t)blockIdx.x * SV_ROWS;
-  for (int rr = warp; rr < SV_ROWS; rr += SV_T / 32) {
-    const int64_t r = r0 + rr;
-    if (r >= m) break;
-    double s = 0.0;
-    for (int l = lane; l < nb; l += 32) s += L[r * ldh + k0 + l] * zs[l];
-    s = warp_sum(s);
-    if (lane == 0) b[r] -= s;
+  const int64_t r = k0 + nb + (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (r >= m) return;
+  const double2* row = reinterpret_cast<const double2*>(L + r * ldh + k0);
+  double s = 0.0;
+  if (nb == NB && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
+#pragma unroll
+    for (int l = 0; l < NB / 2; ++l) {
+      const double2 v = row[l];
+      s += v.x * zs[2 * l] + v.y * zs[2 * l + 1];
+    }
+  } else {
+    for (int l = 0; l < nb; ++l) s += L[r * ldh + k0 + l] * zs[l];
   }
+  b[r] -= s;
 }
 
-// Backward step for block k: x_k = inv(L_kk)^T z_k (into x), z_r -= sum_l
-// L[k0+l][r] x_l for the rows r < k0 handled by this CTA.
+// Backward step for block k: x_k = inv(L_kk)^T z_k (into x), then z_r -=
+// sum_l L[k0+l][r] x_l for the rows r < k0, one thread per row.
 __global__ void __launch_bounds__(SV_T) trsv_bwd_step(const double* __restrict__ L, int64_t ldh,
                                                       int64_t m, int64_t k0,
                                                       double* __restrict__ z,
                                                       double* __restrict__ x) {
+  __shared__ double Li[NB][NB + 1];
   __shared__ double xs[NB];
   __shared__ double zsh[NB];
   const int nb = (int)min64(NB, m - k0);
+  load_block_inverse(L, ldh, k0, nb, Li);
   if (threadIdx.x < NB) zsh[threadIdx.x] = threadIdx.x < nb ? z[k0 + threadIdx.x] : 0.0;
   __syncthreads();
   {
     const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
     double acc = 0.0;
-    if (j < nb)
-      for (int i = j + q; i < nb; i += 4) acc += inv_at(L, ldh, k0, i, j) * zsh[i];
+#pragma unroll
+    for (int i = q; i < NB; i += 4) acc += Li[i][j] * zsh[i];
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (q == 0 && j < NB) xs[j] = (j < nb) ? acc : 0.0;
+    if (q == 0) xs[j] = acc;
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x < nb) x[k0 + threadIdx.x] = xs[threadIdx.x];
   const int64_t r = (int64_t)blockIdx.x * SV_T + threadIdx.x;
   if (r >= k0) return;
   double s = 0.0;
-  for (int l = 0; l < nb; ++l) s += L[(k0 + l) * ldh + r] * xs[l];
+#pragma unroll 16
+  for (int l = 0; l < NB; ++l)
+    if (l < nb) s += L[(k0 + l) * ldh + r] * xs[l];
   z[r] -= s;
 }
 
@@ -253,12 +260,12 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
   cudaStream_t s = as_stream(stream);
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
-  for (int64_t k0 = 0; k0 < m; k0 += NB) {
-    potrf_diag<<<1, 256, 0, s>>>(H, ldh, m, k0, info);
+  for (int64_t k0 = 0; k0 < m; k0 += PB) {
+    potrf_diag<<<1, 32, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
-    const int64_t below = m - (k0 + NB);
+    const int64_t below = m - (k0 + PB);
     if (below <= 0) break;
-    trsm_panel<<<(unsigned)ceil_div(below, 128), 128, 0, s>>>(H, ldh, m, k0, info);
+    trsm_panel<<<(unsigned)ceil_div(below, 32), 32, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
     const int64_t T = ceil_div(below, (int64_t)64);
     syrk_trailing<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(H, ldh, m, k0, info);
@@ -281,7 +288,7 @@ extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, dou
   // forward: rows below each block are updated in b, z_k goes to work
   for (int64_t k0 = 0; k0 < m; k0 += NB) {
     const int64_t below = m - min64(m, k0 + NB);
-    const unsigned grid = (unsigned)(below > 0 ? ceil_div(below, (int64_t)SV_ROWS) : 1);
+    const unsigned grid = (unsigned)(below > 0 ? ceil_div(below, (int64_t)SV_T) : 1);
     trsv_fwd_step<<<grid, SV_T, 0, s>>>(L, ldh, m, k0, b, work);
     SPSVM_LAUNCH_CHECK();
   }

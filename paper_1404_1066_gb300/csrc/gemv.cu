@@ -11,28 +11,37 @@ namespace spsvm {
 namespace {
 
 constexpr int GV_T = 256;          // threads per block
-constexpr int GV_P = 4;            // consecutive points per thread
+constexpr int GV_P = 8;            // consecutive points per thread
 constexpr int GV_PTS = GV_T * GV_P;
 constexpr int GV_CHUNK = 32;       // terms summed in FP32 before promotion
 constexpr int GV_BETA = 2048;      // beta entries staged in shared memory per pass
 
-// Loads 4 consecutive kernel values of row j starting at point i (i % 4 == 0,
-// i + 3 < n) as FP32.
-__device__ __forceinline__ float4 load4(const KView& K, int64_t j, int64_t i) {
-  if (K.format == SPSVM_FP32) {
-    return *reinterpret_cast<const float4*>(static_cast<const float*>(K.data) + j * K.ld + i);
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Loads 8 consecutive kernel values of row j from point i (i % 8 == 0,
+// i + 7 < n) as FP32: two 16-byte loads either way (FP32, or the hi and lo
+// BF16 planes).
+template <int FMT>
+__device__ __forceinline__ void load8(const KView& K, int64_t j, int64_t i, float k[8]) {
+  if (FMT == SPSVM_FP32) {
+    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(K.data) + j * K.ld + i);
+    const float4 a = p[0], b = p[1];
+    k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+    k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+  } else {
+    const uint16_t* base = static_cast<const uint16_t*>(K.data);
+    const uint4 h = *reinterpret_cast<const uint4*>(base + j * K.ld + i);
+    const uint4 l = *reinterpret_cast<const uint4*>(base + K.plane + j * K.ld + i);
+    k[0] = bf_lo(h.x) + bf_lo(l.x); k[1] = bf_hi(h.x) + bf_hi(l.x);
+    k[2] = bf_lo(h.y) + bf_lo(l.y); k[3] = bf_hi(h.y) + bf_hi(l.y);
+    k[4] = bf_lo(h.z) + bf_lo(l.z); k[5] = bf_hi(h.z) + bf_hi(l.z);
+    k[6] = bf_lo(h.w) + bf_lo(l.w); k[7] = bf_hi(h.w) + bf_hi(l.w);
   }
-  const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(K.data);
-  const uint2 h = *reinterpret_cast<const uint2*>(base + j * K.ld + i);
-  const uint2 l = *reinterpret_cast<const uint2*>(base + K.plane + j * K.ld + i);
-  const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&h);
-  const __nv_bfloat162* ll = reinterpret_cast<const __nv_bfloat162*>(&l);
-  const float2 h0 = __bfloat1622float2(hh[0]), h1 = __bfloat1622float2(hh[1]);
-  const float2 l0 = __bfloat1622float2(ll[0]), l1 = __bfloat1622float2(ll[1]);
-  return make_float4(h0.x + l0.x, h0.y + l0.y, h1.x + l1.x, h1.y + l1.y);
 }
 
-// acc[p] = sum_j K[j][i+p] v_j for the thread's 4 points.
+// acc[p] = sum_j K[j][i+p] v_j for the thread's 8 points.
+template <int FMT>
 __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64_t n,
                                              const double* __restrict__ v, int64_t i,
                                              float* vs, double acc[GV_P]) {
@@ -47,16 +56,17 @@ __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64
     if (i >= n) continue;
     for (int c0 = 0; c0 < cnt; c0 += GV_CHUNK) {
       const int ce = min(cnt, c0 + GV_CHUNK);
-      float f[GV_P] = {0.f, 0.f, 0.f, 0.f};
+      float f[GV_P];
+#pragma unroll
+      for (int p = 0; p < GV_P; ++p) f[p] = 0.f;
       if (full) {
-#pragma unroll 8
+#pragma unroll 4
         for (int c = c0; c < ce; ++c) {
-          const float4 k4 = load4(K, j0 + c, i);
+          float k[8];
+          load8<FMT>(K, j0 + c, i, k);
           const float b = vs[c];
-          f[0] = fmaf(k4.x, b, f[0]);
-          f[1] = fmaf(k4.y, b, f[1]);
-          f[2] = fmaf(k4.z, b, f[2]);
-          f[3] = fmaf(k4.w, b, f[3]);
+#pragma unroll
+          for (int p = 0; p < GV_P; ++p) f[p] = fmaf(k[p], b, f[p]);
         }
       } else {
         for (int c = c0; c < ce; ++c) {
@@ -72,6 +82,7 @@ __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64
 }
 
 // o = K beta (or given), active flags, per-block loss / errors / |S|.
+template <int FMT>
 __global__ void __launch_bounds__(GV_T) outputs_kernel(
     KView K, int64_t rows, int64_t n, const double* __restrict__ beta,
     const float* __restrict__ y, float* __restrict__ o, uint8_t* __restrict__ active,
@@ -80,7 +91,7 @@ __global__ void __launch_bounds__(GV_T) outputs_kernel(
   __shared__ double sh[32];
   const int64_t i = ((int64_t)blockIdx.x * GV_T + threadIdx.x) * GV_P;
   double acc[GV_P];
-  if (beta) row_products(K, rows, n, beta, i, vs, acc);
+  if (beta) row_products<FMT>(K, rows, n, beta, i, vs, acc);
   double loss = 0.0, err = 0.0, act = 0.0;
   if (i < n) {
 #pragma unroll
@@ -120,12 +131,14 @@ __global__ void __launch_bounds__(GV_T) outputs_kernel(
   }
 }
 
-__global__ void gemv_kernel(KView K, int64_t rows, int64_t n, const double* __restrict__ v,
-                            float* __restrict__ u, int accumulate) {
+template <int FMT>
+__global__ void __launch_bounds__(GV_T) gemv_kernel(KView K, int64_t rows, int64_t n,
+                                                    const double* __restrict__ v,
+                                                    float* __restrict__ u, int accumulate) {
   __shared__ float vs[GV_BETA];
   const int64_t i = ((int64_t)blockIdx.x * GV_T + threadIdx.x) * GV_P;
   double acc[GV_P];
-  row_products(K, rows, n, v, i, vs, acc);
+  row_products<FMT>(K, rows, n, v, i, vs, acc);
   if (i >= n) return;
 #pragma unroll
   for (int p = 0; p < GV_P; ++p) {
@@ -339,8 +352,12 @@ extern "C" int spsvm_outputs(const spsvm_kmat* K, const double* beta, const floa
   ProfScope prof(PROF_OUTPUTS, s, beta ? 4.0 * (double)K->rows * K->n : 9.0 * K->n);
   const int64_t blocks = ceil_div(K->n, GV_PTS);
   double* part = stats ? static_cast<double*>(scratch) : nullptr;
-  outputs_kernel<<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y, o, active,
-                                                    part, 0);
+  if (K->format == SPSVM_FP32)
+    outputs_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y,
+                                                                  o, active, part, 0);
+  else
+    outputs_kernel<SPSVM_BF16X3><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta,
+                                                                    y, o, active, part, 0);
   SPSVM_LAUNCH_CHECK();
   if (stats) {
     sum_triples<<<1, 256, 0, s>>>(part, blocks, stats);
@@ -356,8 +373,12 @@ extern "C" int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_
   if (K->n == 0) return SPSVM_OK;
   const int64_t blocks = ceil_div(K->n, GV_PTS);
   ProfScope prof(PROF_GEMV, as_stream(stream), 4.0 * (double)K->rows * K->n);
-  gemv_kernel<<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(view(K), K->rows, K->n, v, u,
-                                                                accumulate);
+  if (K->format == SPSVM_FP32)
+    gemv_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
+        view(K), K->rows, K->n, v, u, accumulate);
+  else
+    gemv_kernel<SPSVM_BF16X3><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
+        view(K), K->rows, K->n, v, u, accumulate);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }

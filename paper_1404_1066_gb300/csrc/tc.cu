@@ -32,46 +32,50 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernel block / scores: C[i][c] = x_i . z_c over one 128 x BN tile.
+// Kernel block / scores: D[c][i] = z_c . x_i over one tile of 128 basis (or
+// candidate) rows c (the MMA M dimension, gathered by index into shared
+// memory) and 256 points i (the N dimension, loaded by TMA).  TMEM lane c
+// holds row c, so each thread writes or reduces a contiguous run of points.
 // ---------------------------------------------------------------------------
 constexpr int KB_THREADS = 128;
-constexpr int KB_A_BYTES = 128 * 128;   // one plane, 128 rows x 64 BF16
+constexpr int KB_M = 128;                  // basis rows per tile
+constexpr int KB_N = 256;                  // points per tile
+constexpr int KB_A_BYTES = KB_M * 128;     // one plane: 128 rows x 64 BF16
+constexpr int KB_B_BYTES = KB_N * 128;     // one plane: 256 rows x 64 BF16
+constexpr int KB_STAGE = 2 * KB_A_BYTES + 2 * KB_B_BYTES;
+constexpr int KB_BAR_OFF = 2 * KB_STAGE;   // 5 mbarriers + TMEM slot
+constexpr int KB_ZROW_OFF = KB_BAR_OFF + 64;
+constexpr int KB_XN_OFF = KB_ZROW_OFF + KB_M * 8;
+constexpr int KB_RES_OFF = KB_XN_OFF + KB_N * 4;
+constexpr int KB_ACT_OFF = KB_RES_OFF + KB_N * 4;
+constexpr int KB_SMEM = KB_ACT_OFF + KB_N * 4 + 1024;   // + alignment slack
 
-template <int BN>
-struct KbSmem {
-  static constexpr int B_BYTES = BN * 128;
-  static constexpr int STAGE = 2 * KB_A_BYTES + 2 * B_BYTES;
-  static constexpr int BAR_OFF = 2 * STAGE;          // 5 mbarriers + TMEM slot
-  static constexpr int ZROW_OFF = BAR_OFF + 64;
-  static constexpr int ZN_OFF = ZROW_OFF + BN * 8;
-  static constexpr int RED_OFF = ZN_OFF + BN * 4;
-  static constexpr int TOTAL = RED_OFF + 4 * BN * 8 + 1024;   // + alignment slack
-};
-
-template <int BN, bool SCORE>
+template <bool SCORE>
 __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
     const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
     const uint16_t* __restrict__ Xhi, const uint16_t* __restrict__ Xlo, int64_t ldh, int64_t n,
     const float* __restrict__ norms, const int64_t* __restrict__ idx, int32_t m, float gamma,
-    void* out, int32_t format, int64_t ld, int64_t plane, int64_t row0,
+    uint16_t* __restrict__ out, int64_t ld, int64_t plane, int64_t row0,
     const float* __restrict__ y, const float* __restrict__ o, double2* __restrict__ part,
     int32_t kappa) {
-  using S = KbSmem<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + KB_BAR_OFF);
   uint64_t* empty = full + 2;
   uint64_t* done = full + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 5);
-  int64_t* zrow = reinterpret_cast<int64_t*>(smem + S::ZROW_OFF);
-  float* zn = reinterpret_cast<float*>(smem + S::ZN_OFF);
-  float2* red = reinterpret_cast<float2*>(smem + S::RED_OFF);
+  int64_t* zrow = reinterpret_cast<int64_t*>(smem + KB_ZROW_OFF);
+  float* xn_s = reinterpret_cast<float*>(smem + KB_XN_OFF);
+  float* res_s = reinterpret_cast<float*>(smem + KB_RES_OFF);
+  float* act_s = reinterpret_cast<float*>(smem + KB_ACT_OFF);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = (int64_t)blockIdx.y * 128;
-  const int c0 = blockIdx.x * BN;
-  const int m_here = min(BN, m - c0);
-  constexpr uint32_t IDESC = idesc_bf16_f32(128, BN);
+  const int c0 = blockIdx.x * KB_M;
+  const int64_t i0 = (int64_t)blockIdx.y * KB_N;
+  const int m_here = min(KB_M, m - c0);
+  constexpr uint32_t IDESC = idesc_bf16_f32(KB_M, KB_N);
+  // once any block has given up a wait, the remaining blocks exit at once
+  if (__syncthreads_or(tid == 0 && *(volatile int*)&g_tc_status != 0)) return;
 
   if (tid == 0) {
     mbar_init(&full[0], 1);
@@ -83,11 +87,27 @@ __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
     prefetch_tmap(&map_hi);
     prefetch_tmap(&map_lo);
   }
-  if (warp == 0) tmem_alloc(tmem_slot, BN);
-  for (int c = tid; c < BN; c += KB_THREADS) {
-    const int64_t r = (c < m_here) ? idx[c0 + c] : -1;
-    zrow[c] = r;
-    zn[c] = (r >= 0) ? norms[r] : 0.f;
+  if (warp == 0) tmem_alloc(tmem_slot, KB_N);
+  {
+    const int c = tid;   // KB_THREADS == KB_M
+    zrow[c] = (c < m_here) ? idx[c0 + c] : -1;
+  }
+  for (int j = tid; j < KB_N; j += KB_THREADS) {
+    const int64_t i = i0 + j;
+    const bool in = i < n;
+    xn_s[j] = in ? norms[i] : 0.f;
+    if (SCORE) {
+      float r = 0.f, a = 0.f;
+      if (in) {
+        const float oi = o[i], yi = y[i];
+        if (yi * oi < 1.0f) {
+          r = oi - yi;
+          a = 1.f;
+        }
+      }
+      res_s[j] = r;
+      act_s[j] = a;
+    }
   }
   fence_before_sync();
   __syncthreads();
@@ -99,21 +119,24 @@ __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
   int used_kc[2] = {-1, -1};   // thread 0: last chunk whose load was waited on
   for (int kc = 0; kc < nK; ++kc) {
     const int s = kc & 1;
-    uint8_t* st = smem + s * S::STAGE;
+    uint8_t* st = smem + s * KB_STAGE;
     if (kc >= 2 && ok) ok = mbar_wait(&empty[s], ((kc - 2) >> 1) & 1, &g_tc_status, 1);
     if (!__syncthreads_and(ok)) {
       ok = false;
       break;
     }
+    uint8_t* ah = st;
+    uint8_t* al = st + KB_A_BYTES;
+    uint8_t* bh = st + 2 * KB_A_BYTES;
+    uint8_t* bl = bh + KB_B_BYTES;
     if (tid == 0) {
-      mbar_expect_tx(&full[s], 2 * KB_A_BYTES);
-      tma_load_2d(st, &map_hi, kc * 64, (int)i0, &full[s]);
-      tma_load_2d(st + KB_A_BYTES, &map_lo, kc * 64, (int)i0, &full[s]);
+      mbar_expect_tx(&full[s], 2 * KB_B_BYTES);
+      tma_load_2d(bh, &map_hi, kc * 64, (int)i0, &full[s]);
+      tma_load_2d(bl, &map_lo, kc * 64, (int)i0, &full[s]);
       last_kc[s] = kc;
     }
-    uint8_t* bh = st + 2 * KB_A_BYTES;
-    uint8_t* bl = bh + S::B_BYTES;
-    for (int e = tid; e < BN * 8; e += KB_THREADS) {
+    // gather the basis rows (128-byte swizzle, as TMA would lay them out)
+    for (int e = tid; e < KB_M * 8; e += KB_THREADS) {
       const int r = e >> 3, ch = e & 7;
       uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
       const int64_t zr = zrow[r];
@@ -123,8 +146,8 @@ __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
         vl = *reinterpret_cast<const uint4*>(Xlo + off);
       }
       const int so = r * 128 + ((ch ^ (r & 7)) << 4);
-      *reinterpret_cast<uint4*>(bh + so) = vh;
-      *reinterpret_cast<uint4*>(bl + so) = vl;
+      *reinterpret_cast<uint4*>(ah + so) = vh;
+      *reinterpret_cast<uint4*>(al + so) = vl;
     }
     fence_proxy_async();
     __syncthreads();
@@ -132,7 +155,7 @@ __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
       if (mbar_wait(&full[s], (kc >> 1) & 1, &g_tc_status, 2)) {
         used_kc[s] = kc;
         fence_after_sync();
-        const uint32_t a_hi = smem_u32(st), a_lo = smem_u32(st + KB_A_BYTES);
+        const uint32_t a_hi = smem_u32(ah), a_lo = smem_u32(al);
         const uint32_t b_hi = smem_u32(bh), b_lo = smem_u32(bl);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -161,75 +184,69 @@ __global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
   fence_after_sync();
 
   if (got) {
-    const int64_t i = i0 + 32 * warp + lane;
-    const bool in = i < n;
-    const float xn = in ? norms[i] : 0.f;
-    float res = 0.f, act = 0.f;
-    if (SCORE && in) {
-      const float oi = o[i], yi = y[i];
-      const bool sflag = yi * oi < 1.0f;
-      res = sflag ? (oi - yi) : 0.f;
-      act = sflag ? 1.f : 0.f;
-    }
+    const int c = 32 * warp + lane;               // basis row of this thread
+    const bool crow = c < m_here;
+    const float zn = crow ? norms[zrow[c]] : 0.f;
+    // K = 2^(g2 (2 dot - |x|^2 - |z|^2)), g2 = gamma log2(e)
+    const float g2 = gamma * 1.4426950408889634f;
+    const int64_t npts = min64(KB_N, n - i0);
     const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int cc = 0; cc * 32 < m_here; ++cc) {
+    float gs = 0.f, hs = 0.f;
+    for (int cc = 0; cc < KB_N / 32; ++cc) {
+      if (cc * 32 >= npts) break;                 // uniform across the block
       float v[32];
       tmem_ld32(tbase + cc * 32, v);
-      if (!SCORE) {
-        if (in) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = cc * 32 + j;
-            if (c < m_here) {
-              const float kv = rbf_from_dot(xn, zn[c], v[j], gamma);
-              kstore(out, format, plane, (row0 + c0 + c) * ld + i, kv);
+      for (int j = 0; j < 32; ++j) {
+        const float d2 = fmaxf(xn_s[cc * 32 + j] + zn - 2.0f * v[j], 0.0f);
+        v[j] = exp2f(-g2 * d2);
+      }
+      if (!SCORE) {
+        if (crow) {
+          uint16_t* dh = out + (row0 + c0 + c) * ld + i0 + cc * 32;
+          uint16_t* dl = dh + plane;
+          if (cc * 32 + 32 <= npts) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint32_t wh[4], wl[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                __nv_bfloat16 h0, l0, h1, l1;
+                split_bf16(v[8 * q + 2 * t], h0, l0);
+                split_bf16(v[8 * q + 2 * t + 1], h1, l1);
+                wh[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                wl[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+              }
+              *reinterpret_cast<uint4*>(dh + 8 * q) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+              *reinterpret_cast<uint4*>(dl + 8 * q) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+            }
+          } else {
+            for (int j = 0; j < 32; ++j) {
+              if (cc * 32 + j >= npts) break;
+              __nv_bfloat16 h, l;
+              split_bf16(v[j], h, l);
+              dh[j] = __bfloat16_as_ushort(h);
+              dl[j] = __bfloat16_as_ushort(l);
             }
           }
         }
       } else {
-        float g[32], h[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int c = cc * 32 + j;
-          const float kv = (in && c < m_here) ? rbf_from_dot(xn, zn[c], v[j], gamma) : 0.f;
-          g[j] = res * kv;
-          h[j] = act * kv * kv;
+          const float kv = v[j];
+          gs = fmaf(res_s[cc * 32 + j], kv, gs);
+          hs = fmaf(act_s[cc * 32 + j] * kv, kv, hs);
         }
-        // reduce-scatter across the warp: lane j ends with the sum of column j
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          const bool upper = (lane & off) != 0;
-#pragma unroll
-          for (int j = 0; j < off; ++j) {
-            const float sg = upper ? g[j] : g[j + off];
-            const float kg = upper ? g[j + off] : g[j];
-            const float sh = upper ? h[j] : h[j + off];
-            const float kh = upper ? h[j + off] : h[j];
-            g[j] = kg + __shfl_xor_sync(0xffffffffu, sg, off);
-            h[j] = kh + __shfl_xor_sync(0xffffffffu, sh, off);
-          }
-        }
-        red[warp * BN + cc * 32 + lane] = make_float2(g[0], h[0]);
       }
     }
-    if (SCORE) {
-      __syncthreads();
-      for (int c = tid; c < m_here; c += KB_THREADS) {
-        double gs = 0.0, hs = 0.0;
-        for (int w = 0; w < 4; ++w) {
-          gs += (double)red[w * BN + c].x;
-          hs += (double)red[w * BN + c].y;
-        }
-        part[(int64_t)blockIdx.y * kappa + c0 + c] = make_double2(gs, hs);
-      }
-    }
+    if (SCORE && crow) part[(int64_t)blockIdx.y * kappa + c0 + c] = make_double2(gs, hs);
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     __syncwarp();
     fence_after_sync();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, KB_N);
   }
 }
 
@@ -260,6 +277,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (__syncthreads_or(tid == 0 && *(volatile int*)&g_tc_status != 0)) return;
   // upper-triangular tile (ta <= tb)
   const int64_t T = ceil_div(m, (int64_t)GR_TILE);
   int64_t rem = blockIdx.x, ta = 0;
@@ -406,16 +424,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D BF16 map over rows x inner (row pitch `pitch_elems`), 64 x 128 boxes,
+// 2-D BF16 map over rows x inner (row pitch `pitch_elems`), 64 x box_rows boxes,
 // 128-byte swizzle, zero fill outside the tensor.
-int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int64_t pitch_elems) {
+int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int64_t pitch_elems,
+             uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * 2) % 16)
     return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)(rows > 0 ? rows : 1)};
   cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * 2)};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {64, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -424,26 +443,24 @@ int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, in
   return SPSVM_OK;
 }
 
-template <int BN, bool SCORE>
-int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, void* out,
-              int32_t format, int64_t ld, int64_t plane, int64_t row0, const float* y,
-              const float* o, double2* part, int32_t kappa, cudaStream_t s) {
-  if (ceil_div(p->n, (int64_t)128) > 65535)
-    return set_error(SPSVM_ERR_ARG, "BF16X3 kernel block: n > 8,388,480 points");
+template <bool SCORE>
+int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, uint16_t* out,
+              int64_t ld, int64_t plane, int64_t row0, const float* y, const float* o,
+              double2* part, int32_t kappa, cudaStream_t s) {
+  if (ceil_div(p->n, (int64_t)KB_N) > 65535)
+    return set_error(SPSVM_ERR_ARG, "BF16X3 kernel block: n > 16,776,960 points");
   CUtensorMap mh, ml;
-  SPSVM_TRY(make_map(&mh, p->hi, p->ldh, p->n, p->ldh));
-  SPSVM_TRY(make_map(&ml, p->lo, p->ldh, p->n, p->ldh));
-  auto kern = kblock_tc_kernel<BN, SCORE>;
+  SPSVM_TRY(make_map(&mh, p->hi, p->ldh, p->n, p->ldh, KB_N));
+  SPSVM_TRY(make_map(&ml, p->lo, p->ldh, p->n, p->ldh, KB_N));
+  auto kern = kblock_tc_kernel<SCORE>;
   static bool attr = false;
   if (!attr) {
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        KbSmem<BN>::TOTAL));
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, KB_SMEM));
     attr = true;
   }
-  dim3 grid((unsigned)ceil_div(m, BN), (unsigned)ceil_div(p->n, (int64_t)128));
-  kern<<<grid, KB_THREADS, KbSmem<BN>::TOTAL, s>>>(
-      mh, ml, p->hi, p->lo, p->ldh, p->n, p->norms, idx, m, gamma, out, format, ld, plane, row0,
-      y, o, part, kappa);
+  dim3 grid((unsigned)ceil_div(m, KB_M), (unsigned)ceil_div(p->n, (int64_t)KB_N));
+  kern<<<grid, KB_THREADS, KB_SMEM, s>>>(mh, ml, p->hi, p->lo, p->ldh, p->n, p->norms, idx, m,
+                                         gamma, out, ld, plane, row0, y, o, part, kappa);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -455,23 +472,19 @@ bool tc_available() { return encode_fn() != nullptr; }
 int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
                            spsvm_kmat* out, int64_t row0, cudaStream_t s) {
   if (m == 0 || p->n == 0) return SPSVM_OK;
-  if (m <= 128)
-    return launch_kb<128, false>(p, idx, m, gamma, out->data, out->format, out->ld, out->plane,
-                                 row0, nullptr, nullptr, nullptr, 0, s);
-  return launch_kb<256, false>(p, idx, m, gamma, out->data, out->format, out->ld, out->plane, row0,
-                               nullptr, nullptr, nullptr, 0, s);
+  if (out->format != SPSVM_BF16X3 || (out->ld % 8) != 0 || (out->plane % 8) != 0)
+    return set_error(SPSVM_ERR_ARG,
+                     "BF16X3 kernel block: needs BF16X3 storage with ld %% 8 == 0, plane %% 8 == 0");
+  return launch_kb<false>(p, idx, m, gamma, static_cast<uint16_t*>(out->data), out->ld, out->plane,
+                          row0, nullptr, nullptr, nullptr, 0, s);
 }
 
-int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)128); }
+int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)KB_N); }
 
 int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const int64_t* idx,
                     int32_t kappa, float gamma, double2* part, int64_t tiles, cudaStream_t s) {
   (void)tiles;
-  if (kappa <= 128)
-    return launch_kb<128, true>(p, idx, kappa, gamma, nullptr, SPSVM_FP32, 0, 0, 0, y, o, part,
-                                kappa, s);
-  return launch_kb<256, true>(p, idx, kappa, gamma, nullptr, SPSVM_FP32, 0, 0, 0, y, o, part,
-                              kappa, s);
+  return launch_kb<true>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, s);
 }
 
 int64_t gram_tc_splits(int64_t m, int64_t ns_max) {
@@ -489,8 +502,8 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
   const uint16_t* hi = static_cast<const uint16_t*>(Kc->data);
   const uint16_t* lo = hi + Kc->plane;
   CUtensorMap mh, ml;
-  SPSVM_TRY(make_map(&mh, hi, Kc->ld, m, Kc->ld));
-  SPSVM_TRY(make_map(&ml, lo, Kc->ld, m, Kc->ld));
+  SPSVM_TRY(make_map(&mh, hi, Kc->ld, m, Kc->ld, GR_TILE));
+  SPSVM_TRY(make_map(&ml, lo, Kc->ld, m, Kc->ld, GR_TILE));
   static bool attr = false;
   if (!attr) {
     SPSVM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

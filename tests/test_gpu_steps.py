@@ -205,7 +205,8 @@ def test_gram(sp, prec, n, m, p):
     Hg = H.cpu().numpy()
     np.testing.assert_array_equal(Hg, Hg.T)
     bound = np.abs(KS) @ np.abs(KS).T
-    rel = 1e-5 if prec == "fp32" else 2.5e-5
+    # BF16X3: dropped lo*lo term (2^-16) plus tensor-core FP32 accumulation
+    rel = 1e-5 if prec == "fp32" else 1e-4
     assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))
 
 
