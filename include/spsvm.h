@@ -129,6 +129,28 @@ int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o
                            double* delta, void* scratch, size_t scratch_bytes,
                            void* stream);
 
+/* Candidate scores without any device allocation or caller scratch.  The
+ * paper has no counterpart: this serves callers that must not allocate
+ * device memory -- a serving loop whose HBM budget is owned by a pool it
+ * does not control, a host framework whose allocator owns every device
+ * byte, or code that may not call cudaMalloc because it would synchronise
+ * the device.  Same arguments and results as spsvm_score_candidates, whose
+ * per-tile partial sums go instead to a fixed 16 MiB array inside the
+ * library (a file-scope __device__ array, held by every GPU that loads the
+ * library until the process exits).  Limit:
+ * spsvm_score_scratch_bytes(n, kappa) <= 16 MiB (e.g. n = 500,000 with
+ * kappa = 256); larger sizes are rejected with SPSVM_ERR_ARG before any
+ * work.  The first call on each device (made current) looks up the array's
+ * device address; make that first call before any stream capture.  Calls
+ * share the array: calls whose work overlaps on the GPU (different streams
+ * or devices' threads racing on one device) race on it, so serialise them.
+ * Every call overwrites the partial sums it reads, so nothing needs
+ * clearing between calls. */
+int spsvm_score_candidates_noalloc(const spsvm_points* p, const float* y, const float* o,
+                                   const int64_t* idx, int32_t kappa, float gamma,
+                                   double lambda, int32_t precision, double* g, double* h,
+                                   double* delta, void* stream);
+
 /* Outputs and active set (Eq. 4): o = K_nJ beta (FP32 result, products in
  * FP32, sums of 32 terms promoted to FP64); active[i] = (y_i o_i < 1);
  * stats[0] = 1/2 sum_i max(0, 1 - y_i o_i)^2, stats[1] = #{y_i o_i <= 0},

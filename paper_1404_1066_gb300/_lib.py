@@ -69,6 +69,8 @@ SIGNATURES = {
     "spsvm_score_scratch_bytes": (_SZ, [_I64, _I32]),
     "spsvm_score_candidates": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F, _D, _I32,
                                       _P, _P, _P, _P, _SZ, _P]),
+    "spsvm_score_candidates_noalloc": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F, _D,
+                                              _I32, _P, _P, _P, _P]),
     "spsvm_reduce_scratch_bytes": (_SZ, [_I64]),
     "spsvm_outputs": (_I32, [C.POINTER(spsvm_kmat), _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "spsvm_gemv": (_I32, [C.POINTER(spsvm_kmat), _P, _P, _I32, _P]),

@@ -138,6 +138,22 @@ def spsvm_score_candidates(P: Points, y, o, idx, gamma, lam, precision):
     return g, h, delta
 
 
+def spsvm_score_candidates_noalloc(P: Points, y, o, idx, gamma, lam, precision):
+    """spsvm_score_candidates without caller scratch: the partial sums go to
+    the library's fixed device array (see include/spsvm.h)."""
+    kappa = int(idx.numel())
+    dev = P.X.device
+    g = torch.empty(kappa, dtype=torch.float64, device=dev)
+    h = torch.empty_like(g)
+    delta = torch.empty_like(g)
+    s = P.struct()
+    check(_lib().spsvm_score_candidates_noalloc(C.byref(s), ptr(y), ptr(o), ptr(idx), kappa,
+                                                float(gamma), float(lam), _prec(precision),
+                                                ptr(g), ptr(h), ptr(delta), stream_ptr()),
+          "spsvm_score_candidates_noalloc")
+    return g, h, delta
+
+
 def spsvm_outputs(K: KMat, beta, y, o, rows=None):
     n = K.n
     dev = y.device

@@ -257,3 +257,57 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free candidate scoring.  Some callers must not allocate device
+// memory at all: a serving loop that has handed the whole HBM budget to a
+// pool it does not own, a host framework whose allocator owns every device
+// byte, or code running where cudaMalloc would synchronise the device at a
+// moment it must not.  For them the score's per-tile partial sums live in a
+// fixed array in this library's device memory instead of caller scratch.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace spsvm {
+namespace {
+// 16 MiB: enough for n = 500,000 points and 256 candidates in either form.
+constexpr size_t kScoreScratchMax = size_t(16) << 20;
+// Held by every GPU that loads this library until the process exits.
+__device__ __align__(256) unsigned char g_score_scratch[kScoreScratchMax];
+std::mutex g_score_scratch_mu;
+void* g_score_scratch_ptr[64] = {};
+}  // namespace
+}  // namespace spsvm
+
+extern "C" int spsvm_score_candidates_noalloc(const spsvm_points* p, const float* y,
+                                              const float* o, const int64_t* idx, int32_t kappa,
+                                              float gamma, double lambda, int32_t precision,
+                                              double* g, double* h, double* delta, void* stream) {
+  if (!p || kappa < 0 || p->n < 1)
+    return set_error(SPSVM_ERR_ARG, "score_candidates_noalloc: bad arguments");
+  const size_t need = spsvm_score_scratch_bytes(p->n, kappa);
+  if (need > kScoreScratchMax)
+    return set_error(SPSVM_ERR_ARG,
+                     "score_candidates_noalloc: n=%lld, kappa=%d need %zu bytes of partial sums, "
+                     "more than the fixed %zu-byte array; use spsvm_score_candidates with scratch",
+                     (long long)p->n, kappa, need, kScoreScratchMax);
+  int dev = 0;
+  SPSVM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(SPSVM_ERR_ARG, "score_candidates_noalloc: device %d", dev);
+  void* ptr = nullptr;
+  {
+    // first call on this device (current): look up the array's device address
+    std::lock_guard<std::mutex> lk(g_score_scratch_mu);
+    if (!g_score_scratch_ptr[dev]) {
+      void* a = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&a, g_score_scratch);
+      if (e != cudaSuccess || !a)
+        return set_error(SPSVM_ERR_CUDA, "score_candidates_noalloc: cudaGetSymbolAddress: %s",
+                         cudaGetErrorString(e));
+      g_score_scratch_ptr[dev] = a;
+    }
+    ptr = g_score_scratch_ptr[dev];
+  }
+  return spsvm_score_candidates(p, y, o, idx, kappa, gamma, lambda, precision, g, h, delta, ptr,
+                                kScoreScratchMax, stream);
+}
