@@ -104,10 +104,14 @@ int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* stream);
  *   ||x_{idx[c]}||^2 - 2 x_i^T x_{idx[c]}))   for c < m, i < n.
  * idx: device, m indices into the points.  out->format selects FP32 or
  * BF16X3 storage and must match `precision` (SPSVM_FP32 arithmetic may store
- * either).  Requires row0 + m <= out->rows.  Errors: ARG. */
+ * either).  Requires row0 + m <= out->rows.  scratch: device, at least
+ * spsvm_kernel_block_scratch_bytes(m, d, precision) bytes (the BF16X3 form
+ * gathers the m basis rows there; 0 bytes for SPSVM_FP32).  Errors: ARG,
+ * OOM (scratch too small). */
+size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision);
 int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int32_t m,
                        float gamma, int32_t precision, spsvm_kmat* out,
-                       int64_t row0, void* stream);
+                       int64_t row0, void* scratch, size_t scratch_bytes, void* stream);
 
 /* Basis-vector selection score (Section 4, "Basis vector selection": a
  * heuristic estimate of the loss reduction from adding each sampled
@@ -120,9 +124,9 @@ int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int32_t m,
  * coefficient beta_c started at 0.  Kernel values are computed in
  * `precision` and reduced without being stored.
  * y, o: device, n.  idx: device, kappa.  g, h, delta: device, kappa (FP64).
- * scratch: device, at least spsvm_score_scratch_bytes(n, kappa) bytes.
+ * scratch: device, at least spsvm_score_scratch_bytes(n, d, kappa) bytes.
  * Errors: ARG, OOM (scratch too small). */
-size_t spsvm_score_scratch_bytes(int64_t n, int32_t kappa);
+size_t spsvm_score_scratch_bytes(int64_t n, int64_t d, int32_t kappa);
 int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o,
                            const int64_t* idx, int32_t kappa, float gamma,
                            double lambda, int32_t precision, double* g, double* h,
@@ -138,9 +142,9 @@ int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o
  * per-tile partial sums go instead to a fixed 16 MiB array inside the
  * library (a file-scope __device__ array, held by every GPU that loads the
  * library until the process exits).  Limit:
- * spsvm_score_scratch_bytes(n, kappa) <= 16 MiB (e.g. n = 500,000 with
- * kappa = 256); larger sizes are rejected with SPSVM_ERR_ARG before any
- * work.  The first call on each device (made current) looks up the array's
+ * spsvm_score_scratch_bytes(n, d, kappa) <= 16 MiB (e.g. n = 500,000,
+ * d = 128, kappa = 256); larger sizes are rejected with SPSVM_ERR_ARG
+ * before any work.  The first call on each device (made current) looks up the array's
  * device address; make that first call before any stream capture.  Calls
  * share the array: calls whose work overlaps on the GPU (different streams
  * or devices' threads racing on one device) race on it, so serialise them.

@@ -64,9 +64,10 @@ _SZ = C.c_size_t
 # name -> (restype, argtypes); the full list of exported entry points.
 SIGNATURES = {
     "spsvm_prepare_points": (_I32, [C.POINTER(spsvm_points), _I32, _P]),
+    "spsvm_kernel_block_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
     "spsvm_kernel_block": (_I32, [C.POINTER(spsvm_points), _P, _I32, _F, _I32,
-                                  C.POINTER(spsvm_kmat), _I64, _P]),
-    "spsvm_score_scratch_bytes": (_SZ, [_I64, _I32]),
+                                  C.POINTER(spsvm_kmat), _I64, _P, _SZ, _P]),
+    "spsvm_score_scratch_bytes": (_SZ, [_I64, _I64, _I32]),
     "spsvm_score_candidates": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F, _D, _I32,
                                       _P, _P, _P, _P, _SZ, _P]),
     "spsvm_score_candidates_noalloc": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F, _D,

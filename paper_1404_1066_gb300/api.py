@@ -112,11 +112,17 @@ def kmat_empty(n, rows, precision="fp32", device="cuda", ld=None):
     return KMat(buf, p, n, rows, ld, plane)
 
 
-def spsvm_kernel_block(P: Points, idx: torch.Tensor, gamma, precision, out: KMat, row0=0):
+def spsvm_kernel_block(P: Points, idx: torch.Tensor, gamma, precision, out: KMat, row0=0,
+                       scratch=None):
     s = P.struct()
     k = out.struct()
-    check(_lib().spsvm_kernel_block(C.byref(s), ptr(idx), int(idx.numel()), float(gamma),
-                                    _prec(precision), C.byref(k), int(row0), stream_ptr()),
+    m = int(idx.numel())
+    sb = _lib().spsvm_kernel_block_scratch_bytes(m, P.X.shape[1], _prec(precision))
+    if scratch is None:
+        scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=P.X.device)
+    check(_lib().spsvm_kernel_block(C.byref(s), ptr(idx), m, float(gamma), _prec(precision),
+                                    C.byref(k), int(row0), ptr(scratch), scratch.numel(),
+                                    stream_ptr()),
           "spsvm_kernel_block")
     return out
 
@@ -128,7 +134,7 @@ def spsvm_score_candidates(P: Points, y, o, idx, gamma, lam, precision):
     g = torch.empty(kappa, dtype=torch.float64, device=dev)
     h = torch.empty_like(g)
     delta = torch.empty_like(g)
-    sb = _lib().spsvm_score_scratch_bytes(n, kappa)
+    sb = _lib().spsvm_score_scratch_bytes(n, P.X.shape[1], kappa)
     scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=dev)
     s = P.struct()
     check(_lib().spsvm_score_candidates(C.byref(s), ptr(y), ptr(o), ptr(idx), kappa, float(gamma),

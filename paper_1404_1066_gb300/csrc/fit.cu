@@ -201,7 +201,8 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_ch = take(kappa * 8);
   L.off_cd = take(kappa * 8);
   L.off_small = take(256);
-  size_t sc = spsvm_score_scratch_bytes(n, kappa);
+  size_t sc = spsvm_score_scratch_bytes(n, d, kappa);
+  sc = std::max(sc, spsvm_kernel_block_scratch_bytes(L.jcap, d, precision));
   sc = std::max(sc, spsvm_reduce_scratch_bytes(n));
   sc = std::max(sc, spsvm_compact_scratch_bytes(n, L.jcap));
   // the Gram split count depends on |J|: cover every size the fit can reach
@@ -438,7 +439,8 @@ struct Fit {
       m = (int32_t)J.size();
       SPSVM_CUDA_TRY(cudaMemcpyAsync(Jd, J.data(), m * 8, cudaMemcpyHostToDevice, s));
       spsvm_kmat K = kmat();
-      SPSVM_TRY(spsvm_kernel_block(&pts, Jd, m, gamma, op.precision, &K, 0, s));
+      SPSVM_TRY(spsvm_kernel_block(&pts, Jd, m, gamma, op.precision, &K, 0, ws + L.off_scratch,
+                                   L.scratch_bytes, s));
       SPSVM_TRY(newton());
     }
     double st[3];
@@ -476,7 +478,8 @@ struct Fit {
       const int32_t m0 = m;
       m += qq;
       spsvm_kmat K = kmat();
-      SPSVM_TRY(spsvm_kernel_block(&pts, Jd + m0, qq, gamma, op.precision, &K, m0, s));
+      SPSVM_TRY(spsvm_kernel_block(&pts, Jd + m0, qq, gamma, op.precision, &K, m0,
+                                   ws + L.off_scratch, L.scratch_bytes, s));
       SPSVM_TRY(newton());
       ++round;
       SPSVM_TRY(flags(act_cur, st));

@@ -142,7 +142,9 @@ struct ProfScope {
 int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t m,
                              float gamma, spsvm_kmat* out, int64_t row0, cudaStream_t s);
 int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m,
-                           float gamma, spsvm_kmat* out, int64_t row0, cudaStream_t s);
+                           float gamma, spsvm_kmat* out, int64_t row0, void* scratch,
+                           size_t scratch_bytes, cudaStream_t s);
+size_t kernel_block_tc_scratch(int64_t m, int64_t ldh);
 bool tc_available();
 
 }  // namespace spsvm

@@ -193,9 +193,15 @@ int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t 
 
 using namespace spsvm;
 
+extern "C" size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision) {
+  if (m < 0 || d < 1 || precision != SPSVM_BF16X3) return 0;
+  return kernel_block_tc_scratch(m, round_up(d, 64));
+}
+
 extern "C" int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int32_t m,
                                   float gamma, int32_t precision, spsvm_kmat* out,
-                                  int64_t row0, void* stream) {
+                                  int64_t row0, void* scratch, size_t scratch_bytes,
+                                  void* stream) {
   if (!p || !p->X || !p->norms || !idx) return set_error(SPSVM_ERR_ARG, "kernel_block: NULL pointer");
   SPSVM_TRY(check_kmat(out, "kernel_block"));
   if (m < 0 || row0 < 0 || row0 + m > out->rows || out->n != p->n || !(gamma > 0.f))
@@ -206,22 +212,30 @@ extern "C" int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int
   if (precision == SPSVM_BF16X3) {
     if (out->format != SPSVM_BF16X3 || !p->hi || !p->lo)
       return set_error(SPSVM_ERR_ARG, "kernel_block: BF16X3 needs split planes and BF16X3 output");
-    return launch_kernel_block_tc(p, idx, m, gamma, out, row0, as_stream(stream));
+    return launch_kernel_block_tc(p, idx, m, gamma, out, row0, scratch, scratch_bytes,
+                                  as_stream(stream));
   }
   if (precision != SPSVM_FP32) return set_error(SPSVM_ERR_ARG, "kernel_block: bad precision");
   return launch_kernel_block_simt(p, idx, m, gamma, out, row0, as_stream(stream));
 }
 
-extern "C" size_t spsvm_score_scratch_bytes(int64_t n, int32_t kappa) {
-  if (n < 0 || kappa < 0) return 0;
-  const int64_t tiles = ceil_div(n, TM);
-  return (size_t)(tiles * (int64_t)kappa * (int64_t)sizeof(double2));
-}
-
 namespace spsvm {
 int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const int64_t* idx,
-                    int32_t kappa, float gamma, double2* part, int64_t tiles, cudaStream_t s);
+                    int32_t kappa, float gamma, double2* part, int64_t tiles, void* zbuf,
+                    size_t zbytes, cudaStream_t s);
 int64_t score_tc_tiles(int64_t n);
+namespace {
+// per-tile partial sums (tiles of 128 points in both forms), then room for
+// the gathered candidate rows of the tensor-core form
+size_t score_part_bytes(int64_t n, int32_t kappa) {
+  return (size_t)round_up(ceil_div(n, TM) * (int64_t)kappa * (int64_t)sizeof(double2), 256);
+}
+}  // namespace
+}  // namespace spsvm
+
+extern "C" size_t spsvm_score_scratch_bytes(int64_t n, int64_t d, int32_t kappa) {
+  if (n < 0 || kappa < 0 || d < 1) return 0;
+  return score_part_bytes(n, kappa) + kernel_block_tc_scratch(kappa, round_up(d, 64));
 }
 
 extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o,
@@ -234,9 +248,9 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
   if (kappa < 0 || p->n < 1 || !(gamma > 0.f) || !(lambda > 0.0))
     return set_error(SPSVM_ERR_ARG, "score_candidates: bad arguments");
   if (kappa == 0) return SPSVM_OK;
-  if (scratch_bytes < spsvm_score_scratch_bytes(p->n, kappa) || !scratch)
-    return set_error(SPSVM_ERR_OOM, "score_candidates: scratch %zu < %zu", scratch_bytes,
-                     spsvm_score_scratch_bytes(p->n, kappa));
+  const size_t need = spsvm_score_scratch_bytes(p->n, p->d, kappa);
+  if (scratch_bytes < need || !scratch)
+    return set_error(SPSVM_ERR_OOM, "score_candidates: scratch %zu < %zu", scratch_bytes, need);
   cudaStream_t s = as_stream(stream);
   ProfScope prof(PROF_SCORE, s, 2.0 * (double)p->n * kappa * (double)p->d);
   double2* part = static_cast<double2*>(scratch);
@@ -244,7 +258,9 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
   if (precision == SPSVM_BF16X3) {
     if (!p->hi || !p->lo) return set_error(SPSVM_ERR_ARG, "score_candidates: BF16X3 needs split planes");
     tiles = score_tc_tiles(p->n);
-    SPSVM_TRY(launch_score_tc(p, y, o, idx, kappa, gamma, part, tiles, s));
+    const size_t pb = score_part_bytes(p->n, kappa);
+    SPSVM_TRY(launch_score_tc(p, y, o, idx, kappa, gamma, part, tiles,
+                              static_cast<char*>(scratch) + pb, scratch_bytes - pb, s));
   } else if (precision == SPSVM_FP32) {
     dim3 grid((unsigned)tiles, (unsigned)ceil_div(kappa, TN));
     score_partials_simt<<<grid, NT, 0, s>>>(p->X, p->n, p->d, p->ldx, p->norms, y, o, idx,
@@ -285,12 +301,12 @@ extern "C" int spsvm_score_candidates_noalloc(const spsvm_points* p, const float
                                               double* g, double* h, double* delta, void* stream) {
   if (!p || kappa < 0 || p->n < 1)
     return set_error(SPSVM_ERR_ARG, "score_candidates_noalloc: bad arguments");
-  const size_t need = spsvm_score_scratch_bytes(p->n, kappa);
+  const size_t need = spsvm_score_scratch_bytes(p->n, p->d, kappa);
   if (need > kScoreScratchMax)
     return set_error(SPSVM_ERR_ARG,
-                     "score_candidates_noalloc: n=%lld, kappa=%d need %zu bytes of partial sums, "
-                     "more than the fixed %zu-byte array; use spsvm_score_candidates with scratch",
-                     (long long)p->n, kappa, need, kScoreScratchMax);
+                     "score_candidates_noalloc: n=%lld, d=%lld, kappa=%d need %zu bytes of "
+                     "scratch, more than the fixed %zu-byte array; use spsvm_score_candidates",
+                     (long long)p->n, (long long)p->d, kappa, need, kScoreScratchMax);
   int dev = 0;
   SPSVM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_error(SPSVM_ERR_ARG, "score_candidates_noalloc: device %d", dev);

@@ -32,222 +32,333 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernel block / scores: D[c][i] = z_c . x_i over one tile of 128 basis (or
-// candidate) rows c (the MMA M dimension, gathered by index into shared
-// memory) and 256 points i (the N dimension, loaded by TMA).  TMEM lane c
-// holds row c, so each thread writes or reduces a contiguous run of points.
+// Kernel block / scores, persistent and warp-specialised.  D[c][i] = z_c . x_i
+// over tiles of 128 basis (or candidate) rows c (MMA M; the rows gathered
+// beforehand into contiguous BF16 planes Z) by 128 points i (MMA N), both
+// operands streamed by TMA through a 3-stage shared-memory ring.  Warp 0
+// issues the TMA loads, warp 1 the MMAs into one of two TMEM accumulators,
+// warps 2-9 drain the other accumulator (TMEM lane c = row c; warps w and
+// w + 4 share a lane quarter and split the 128 columns), so the epilogue of
+// one tile overlaps the MMAs of the next.  Tiles are ordered point-tile
+// major so the CTAs in flight share their X tiles through L2.
 // ---------------------------------------------------------------------------
-constexpr int KB_THREADS = 128;
-constexpr int KB_M = 128;                  // basis rows per tile
-constexpr int KB_N = 256;                  // points per tile
-constexpr int KB_A_BYTES = KB_M * 128;     // one plane: 128 rows x 64 BF16
-constexpr int KB_B_BYTES = KB_N * 128;     // one plane: 256 rows x 64 BF16
-constexpr int KB_STAGE = 2 * KB_A_BYTES + 2 * KB_B_BYTES;
-constexpr int KB_BAR_OFF = 2 * KB_STAGE;   // 5 mbarriers + TMEM slot
-constexpr int KB_ZROW_OFF = KB_BAR_OFF + 64;
-constexpr int KB_XN_OFF = KB_ZROW_OFF + KB_M * 8;
-constexpr int KB_RES_OFF = KB_XN_OFF + KB_N * 4;
-constexpr int KB_ACT_OFF = KB_RES_OFF + KB_N * 4;
-constexpr int KB_SMEM = KB_ACT_OFF + KB_N * 4 + 1024;   // + alignment slack
+constexpr int PK_M = 128;
+constexpr int PK_N = 128;
+constexpr int PK_STAGES = 2;
+constexpr int PK_PLANE_A = PK_M * 128;                     // 16 KB: 128 rows x 64 BF16
+constexpr int PK_PLANE_B = PK_N * 128;
+constexpr int PK_STAGE = 2 * PK_PLANE_A + 2 * PK_PLANE_B;  // 64 KB
+constexpr int PK_EPI_WARPS = 8;
+constexpr int PK_THREADS = 32 * (2 + PK_EPI_WARPS);
+constexpr int PK_OUT_BOX = 32 * 128;                       // one plane: 32 rows x 64 BF16
+constexpr int PK_OUT_OFF = PK_STAGES * PK_STAGE;           // per epilogue warp: hi and lo boxes
+constexpr int PK_BAR_OFF = PK_OUT_OFF + PK_EPI_WARPS * 2 * PK_OUT_BOX;
+constexpr int PK_RED_OFF = PK_BAR_OFF + 256;
+constexpr int PK_STAGE_OFF = PK_RED_OFF + 4 * 32 * 8;      // per epilogue warp: 3 x 64 floats
+constexpr int PK_SMEM = PK_STAGE_OFF + PK_EPI_WARPS * 192 * 4 + 1024;   // + alignment slack
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until the shared-memory sources of every committed bulk store have been read.
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Tile order: groups of PK_GROUP consecutive point tiles, each group swept
+// over all basis blocks with the point tile varying fastest.  The CTAs in
+// flight then share a few X tiles through L2 while each basis row receives
+// PK_GROUP x 256 contiguous bytes per plane, so the kernel-matrix writes
+// reach DRAM in long runs.
+constexpr int64_t PK_GROUP = 16;
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT, int& cb,
+                                            int64_t& pt) {
+  const int64_t per = nCB * PK_GROUP;
+  const int64_t g = t / per, r = t % per;
+  const int64_t g0 = g * PK_GROUP;
+  const int64_t gw = min64(PK_GROUP, nPT - g0);   // the last group may be narrower
+  cb = (int)(r / gw);
+  pt = g0 + r % gw;
+}
 
 template <bool SCORE>
-__global__ void __launch_bounds__(KB_THREADS, 1) kblock_tc_kernel(
-    const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-    const uint16_t* __restrict__ Xhi, const uint16_t* __restrict__ Xlo, int64_t ldh, int64_t n,
-    const float* __restrict__ norms, const int64_t* __restrict__ idx, int32_t m, float gamma,
-    uint16_t* __restrict__ out, int64_t ld, int64_t plane, int64_t row0,
-    const float* __restrict__ y, const float* __restrict__ o, double2* __restrict__ part,
-    int32_t kappa) {
+__global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
+    const __grid_constant__ CUtensorMap map_zhi, const __grid_constant__ CUtensorMap map_zlo,
+    const __grid_constant__ CUtensorMap map_xhi, const __grid_constant__ CUtensorMap map_xlo,
+    const __grid_constant__ CUtensorMap map_ohi, const __grid_constant__ CUtensorMap map_olo,
+    int64_t ldh, int64_t n, int32_t m, const float* __restrict__ norms,
+    const int64_t* __restrict__ idx, float gamma, int64_t row0, const float* __restrict__ y,
+    const float* __restrict__ o, double2* __restrict__ part, int32_t kappa) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + KB_BAR_OFF);
-  uint64_t* empty = full + 2;
-  uint64_t* done = full + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 5);
-  int64_t* zrow = reinterpret_cast<int64_t*>(smem + KB_ZROW_OFF);
-  float* xn_s = reinterpret_cast<float*>(smem + KB_XN_OFF);
-  float* res_s = reinterpret_cast<float*>(smem + KB_RES_OFF);
-  float* act_s = reinterpret_cast<float*>(smem + KB_ACT_OFF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + PK_BAR_OFF);
+  uint64_t* empty = full + PK_STAGES;
+  uint64_t* tfull = empty + PK_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* redf = tempty + 2;   // per lane quarter: half-tile sums written
+  uint64_t* rede = redf + 4;     // per lane quarter: half-tile sums consumed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rede + 4);
+  float2* red = reinterpret_cast<float2*>(smem + PK_RED_OFF);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c0 = blockIdx.x * KB_M;
-  const int64_t i0 = (int64_t)blockIdx.y * KB_N;
-  const int m_here = min(KB_M, m - c0);
-  constexpr uint32_t IDESC = idesc_bf16_f32(KB_M, KB_N);
-  // once any block has given up a wait, the remaining blocks exit at once
   if (__syncthreads_or(tid == 0 && *(volatile int*)&g_tc_status != 0)) return;
+  const int64_t nCB = ceil_div((int64_t)m, (int64_t)PK_M);
+  const int64_t nPT = ceil_div(n, (int64_t)PK_N);
+  const int64_t T = nCB * nPT;
+  const int nK = (int)(ldh / 64);
+  constexpr uint32_t IDESC = idesc_bf16_f32(PK_M, PK_N);
 
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], 1);
-    mbar_init(&empty[1], 1);
-    mbar_init(done, 1);
+    for (int s = 0; s < PK_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 32 * PK_EPI_WARPS);
+    }
+    for (int qd = 0; qd < 4; ++qd) {
+      mbar_init(&redf[qd], 32);
+      mbar_init(&rede[qd], 32);
+    }
     fence_barrier_init();
-    prefetch_tmap(&map_hi);
-    prefetch_tmap(&map_lo);
-  }
-  if (warp == 0) tmem_alloc(tmem_slot, KB_N);
-  {
-    const int c = tid;   // KB_THREADS == KB_M
-    zrow[c] = (c < m_here) ? idx[c0 + c] : -1;
-  }
-  for (int j = tid; j < KB_N; j += KB_THREADS) {
-    const int64_t i = i0 + j;
-    const bool in = i < n;
-    xn_s[j] = in ? norms[i] : 0.f;
-    if (SCORE) {
-      float r = 0.f, a = 0.f;
-      if (in) {
-        const float oi = o[i], yi = y[i];
-        if (yi * oi < 1.0f) {
-          r = oi - yi;
-          a = 1.f;
-        }
-      }
-      res_s[j] = r;
-      act_s[j] = a;
+    prefetch_tmap(&map_zhi);
+    prefetch_tmap(&map_zlo);
+    prefetch_tmap(&map_xhi);
+    prefetch_tmap(&map_xlo);
+    if (!SCORE) {
+      prefetch_tmap(&map_ohi);
+      prefetch_tmap(&map_olo);
     }
   }
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * PK_N);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const int nK = (int)(ldh / 64);
-  bool ok = true;
-  int last_kc[2] = {-1, -1};   // thread 0: last chunk loaded into each stage
-  int used_kc[2] = {-1, -1};   // thread 0: last chunk whose load was waited on
-  for (int kc = 0; kc < nK; ++kc) {
-    const int s = kc & 1;
-    uint8_t* st = smem + s * KB_STAGE;
-    if (kc >= 2 && ok) ok = mbar_wait(&empty[s], ((kc - 2) >> 1) & 1, &g_tc_status, 1);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    uint8_t* ah = st;
-    uint8_t* al = st + KB_A_BYTES;
-    uint8_t* bh = st + 2 * KB_A_BYTES;
-    uint8_t* bl = bh + KB_B_BYTES;
-    if (tid == 0) {
-      mbar_expect_tx(&full[s], 2 * KB_B_BYTES);
-      tma_load_2d(bh, &map_hi, kc * 64, (int)i0, &full[s]);
-      tma_load_2d(bl, &map_lo, kc * 64, (int)i0, &full[s]);
-      last_kc[s] = kc;
-    }
-    // gather the basis rows (128-byte swizzle, as TMA would lay them out)
-    for (int e = tid; e < KB_M * 8; e += KB_THREADS) {
-      const int r = e >> 3, ch = e & 7;
-      uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
-      const int64_t zr = zrow[r];
-      if (zr >= 0) {
-        const int64_t off = zr * ldh + (int64_t)kc * 64 + ch * 8;
-        vh = *reinterpret_cast<const uint4*>(Xhi + off);
-        vl = *reinterpret_cast<const uint4*>(Xlo + off);
-      }
-      const int so = r * 128 + ((ch ^ (r & 7)) << 4);
-      *reinterpret_cast<uint4*>(ah + so) = vh;
-      *reinterpret_cast<uint4*>(al + so) = vl;
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      if (mbar_wait(&full[s], (kc >> 1) & 1, &g_tc_status, 2)) {
-        used_kc[s] = kc;
-        fence_after_sync();
-        const uint32_t a_hi = smem_u32(ah), a_lo = smem_u32(al);
-        const uint32_t b_hi = smem_u32(bh), b_lo = smem_u32(bl);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t koff = k * 32;
-          mma_bf16(tmem, desc_sw128(a_hi + koff), desc_sw128(b_hi + koff), IDESC,
-                   (kc | k) != 0);
-          mma_bf16(tmem, desc_sw128(a_hi + koff), desc_sw128(b_lo + koff), IDESC, 1);
-          mma_bf16(tmem, desc_sw128(a_lo + koff), desc_sw128(b_hi + koff), IDESC, 1);
-        }
-        mma_commit(&empty[s]);
-      } else {
-        ok = false;
-      }
-    }
-  }
-  if (tid == 0) {
-    mma_commit(done);
-    // no TMA copy may still be in flight when the block exits
-    for (int s = 0; s < 2; ++s)
-      if (last_kc[s] >= 0 && last_kc[s] != used_kc[s])
-        mbar_wait(&full[s], (uint32_t)((last_kc[s] >> 1) & 1), &g_tc_status, 4);
-  }
-  ok = __syncthreads_and(ok);
-  bool got = mbar_wait(done, 0, &g_tc_status, 3);
-  got = __syncthreads_and(got) && ok;
-  fence_after_sync();
 
-  if (got) {
-    const int c = 32 * warp + lane;               // basis row of this thread
-    const bool crow = c < m_here;
-    const float zn = crow ? norms[zrow[c]] : 0.f;
-    // K = 2^(g2 (2 dot - |x|^2 - |z|^2)), g2 = gamma log2(e)
-    const float g2 = gamma * 1.4426950408889634f;
-    const int64_t npts = min64(KB_N, n - i0);
-    const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
-    float gs = 0.f, hs = 0.f;
-    for (int cc = 0; cc < KB_N / 32; ++cc) {
-      if (cc * 32 >= npts) break;                 // uniform across the block
-      float v[32];
-      tmem_ld32(tbase + cc * 32, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float d2 = fmaxf(xn_s[cc * 32 + j] + zn - 2.0f * v[j], 0.0f);
-        v[j] = exp2f(-g2 * d2);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int64_t q = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        int cb;
+        int64_t pt;
+        tile_coords(t, nCB, nPT, cb, pt);
+        for (int kc = 0; kc < nK; ++kc, ++q) {
+          const int s = (int)(q % PK_STAGES);
+          const uint32_t ph = (uint32_t)((q / PK_STAGES) & 1);
+          if (!mbar_wait(&empty[s], ph ^ 1u, &g_tc_status, 21)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * PK_STAGE;
+          mbar_expect_tx(&full[s], PK_STAGE);
+          tma_load_2d(st, &map_zhi, kc * 64, cb * PK_M, &full[s]);
+          tma_load_2d(st + PK_PLANE_A, &map_zlo, kc * 64, cb * PK_M, &full[s]);
+          tma_load_2d(st + 2 * PK_PLANE_A, &map_xhi, kc * 64, pt * PK_N, &full[s]);
+          tma_load_2d(st + 2 * PK_PLANE_A + PK_PLANE_B, &map_xlo, kc * 64, pt * PK_N, &full[s]);
+        }
       }
-      if (!SCORE) {
-        if (crow) {
-          uint16_t* dh = out + (row0 + c0 + c) * ld + i0 + cc * 32;
-          uint16_t* dl = dh + plane;
-          if (cc * 32 + 32 <= npts) {
+      // no copy may be in flight when the block exits
+      for (int64_t r = (q > PK_STAGES ? q - PK_STAGES : 0); r < q; ++r)
+        mbar_wait(&full[r % PK_STAGES], (uint32_t)((r / PK_STAGES) & 1), &g_tc_status, 22);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      int64_t q = 0, j = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x, ++j) {
+        const int acc = (int)(j & 1);
+        if (!mbar_wait(&tempty[acc], (uint32_t)(((j >> 1) & 1) ^ 1), &g_tc_status, 23)) break;
+        fence_after_sync();
+        const uint32_t d = tmem + acc * PK_N;
+        for (int kc = 0; kc < nK; ++kc, ++q) {
+          const int s = (int)(q % PK_STAGES);
+          const uint32_t ph = (uint32_t)((q / PK_STAGES) & 1);
+          if (!mbar_wait(&full[s], ph, &g_tc_status, 24)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t base = smem_u32(smem + s * PK_STAGE);
+          const uint32_t a_hi = base, a_lo = base + PK_PLANE_A;
+          const uint32_t b_hi = base + 2 * PK_PLANE_A, b_lo = b_hi + PK_PLANE_B;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint32_t wh[4], wl[4];
-#pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                __nv_bfloat16 h0, l0, h1, l1;
-                split_bf16(v[8 * q + 2 * t], h0, l0);
-                split_bf16(v[8 * q + 2 * t + 1], h1, l1);
-                wh[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                wl[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-              }
-              *reinterpret_cast<uint4*>(dh + 8 * q) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-              *reinterpret_cast<uint4*>(dl + 8 * q) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-            }
-          } else {
-            for (int j = 0; j < 32; ++j) {
-              if (cc * 32 + j >= npts) break;
-              __nv_bfloat16 h, l;
-              split_bf16(v[j], h, l);
-              dh[j] = __bfloat16_as_ushort(h);
-              dl[j] = __bfloat16_as_ushort(l);
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t koff = k * 32;
+            mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_hi + koff), IDESC,
+                     (kc | k) != 0 ? 1u : 0u);
+            mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_lo + koff), IDESC, 1u);
+            mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_hi + koff), IDESC, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[acc]);
+      }
+    }
+  } else {
+    // ---- epilogue
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int c_in = 32 * quarter + lane;
+    const float g2 = gamma * 1.4426950408889634f;   // K = 2^(-g2 |x - z|^2)
+    float* stage = reinterpret_cast<float*>(smem + PK_STAGE_OFF) + (warp - 2) * 192;
+    uint8_t* obox = smem + PK_OUT_OFF + (warp - 2) * 2 * PK_OUT_BOX;
+    int64_t j = 0;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++j) {
+      int cb;
+      int64_t pt;
+      tile_coords(t, nCB, nPT, cb, pt);
+      const int64_t c = (int64_t)cb * PK_M + c_in;
+      const bool crow = c < m;
+      const float zn = crow ? norms[idx[c]] : 0.f;
+      const int64_t ib = pt * PK_N + half * 64;
+      const int64_t npts = min64(64, n - ib);
+      // this warp's 64 points: norms (and for scores the active residual / flag)
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int jj = h2 * 32 + lane;
+        const int64_t i = ib + jj;
+        const bool in = jj < npts;
+        stage[jj] = in ? norms[i] : 0.f;
+        if (SCORE) {
+          float r = 0.f, a = 0.f;
+          if (in) {
+            const float oi = o[i], yi = y[i];
+            if (yi * oi < 1.0f) {
+              r = oi - yi;
+              a = 1.f;
             }
           }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float kv = v[j];
-          gs = fmaf(res_s[cc * 32 + j], kv, gs);
-          hs = fmaf(act_s[cc * 32 + j] * kv, kv, hs);
+          stage[64 + jj] = r;
+          stage[128 + jj] = a;
         }
       }
+      __syncwarp();
+      const int acc = (int)(j & 1);
+      if (!mbar_wait(&tfull[acc], (uint32_t)((j >> 1) & 1), &g_tc_status, 25)) break;
+      fence_after_sync();
+      float gs = 0.f, hs = 0.f;
+      const uint32_t tb = tmem + acc * PK_N + half * 64 + ((uint32_t)(32 * quarter) << 16);
+      if (!SCORE) {
+        // the previous tile's boxes must have been read out before they are rewritten
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
+      }
+      const float zz = -g2 * zn;
+      for (int cc = 0; cc < 2; ++cc) {
+        if (cc * 32 >= npts) break;   // uniform per warp
+        float v[32];
+        tmem_ld32(tb + cc * 32, v);
+        // arg = -g2 * max(|x|^2 + |z|^2 - 2 x.z, 0); points past n carry zero
+        // norms here and are clipped by the store or weighted by zero flags
+#pragma unroll
+        for (int jj = 0; jj < 32; jj += 4) {
+          const float4 x4 = *reinterpret_cast<const float4*>(stage + cc * 32 + jj);
+          v[jj + 0] = ex2_approx(fminf(fmaf(-g2, x4.x, fmaf(2.0f * g2, v[jj + 0], zz)), 0.0f));
+          v[jj + 1] = ex2_approx(fminf(fmaf(-g2, x4.y, fmaf(2.0f * g2, v[jj + 1], zz)), 0.0f));
+          v[jj + 2] = ex2_approx(fminf(fmaf(-g2, x4.z, fmaf(2.0f * g2, v[jj + 2], zz)), 0.0f));
+          v[jj + 3] = ex2_approx(fminf(fmaf(-g2, x4.w, fmaf(2.0f * g2, v[jj + 3], zz)), 0.0f));
+        }
+        if (!SCORE) {
+          // hi / lo into this warp's swizzled output boxes (row = lane)
+          uint8_t* bh = obox;
+          uint8_t* bl = obox + PK_OUT_BOX;
+#pragma unroll
+          for (int qd = 0; qd < 4; ++qd) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float a0 = v[8 * qd + 2 * u], a1 = v[8 * qd + 2 * u + 1];
+              const __nv_bfloat162 h2v = __floats2bfloat162_rn(a0, a1);
+              const float2 hf = __bfloat1622float2(h2v);
+              const __nv_bfloat162 l2v = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
+              wh[u] = *reinterpret_cast<const uint32_t*>(&h2v);
+              wl[u] = *reinterpret_cast<const uint32_t*>(&l2v);
+            }
+            const int ch = cc * 4 + qd;   // 16-byte chunk of the 128-byte box row
+            const int so = lane * 128 + ((ch ^ (lane & 7)) << 4);
+            *reinterpret_cast<uint4*>(bh + so) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4*>(bl + so) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const float kv = v[jj];
+            gs = fmaf(stage[64 + cc * 32 + jj], kv, gs);
+            hs = fmaf(stage[128 + cc * 32 + jj] * kv, kv, hs);
+          }
+        }
+      }
+      fence_before_sync();
+      mbar_arrive(&tempty[acc]);
+      if (!SCORE && npts > 0) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          const int x = (int)ib, yrow = (int)(row0 + (int64_t)cb * PK_M + 32 * quarter);
+          tma_store_2d(&map_ohi, x, yrow, obox);
+          tma_store_2d(&map_olo, x, yrow, obox + PK_OUT_BOX);
+          bulk_commit();
+        }
+      }
+      if (SCORE) {
+        // the two warps of a lane quarter combine their halves of the tile
+        const uint32_t par = (uint32_t)(j & 1);
+        if (half == 1) {
+          if (!mbar_wait(&rede[quarter], par ^ 1u, &g_tc_status, 26)) break;
+          red[quarter * 32 + lane] = make_float2(gs, hs);
+          mbar_arrive(&redf[quarter]);
+        } else {
+          if (!mbar_wait(&redf[quarter], par, &g_tc_status, 27)) break;
+          const float2 r2 = red[quarter * 32 + lane];
+          mbar_arrive(&rede[quarter]);
+          if (crow)
+            part[pt * kappa + c] = make_double2((double)gs + (double)r2.x, (double)hs + (double)r2.y);
+        }
+      }
+      __syncwarp();
     }
-    if (SCORE && crow) part[(int64_t)blockIdx.y * kappa + c0 + c] = make_double2(gs, hs);
+    if (!SCORE && lane == 0) bulk_wait_all();
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     __syncwarp();
     fence_after_sync();
-    tmem_dealloc(tmem, KB_N);
+    tmem_dealloc(tmem, 2 * PK_N);
   }
+}
+
+// Z planes: rows idx[0..m) of the split X planes, zero rows up to m_pad.
+__global__ void gather_rows_bf16(const uint16_t* __restrict__ Xhi, const uint16_t* __restrict__ Xlo,
+                                 int64_t ldh, const int64_t* __restrict__ idx, int32_t m,
+                                 int64_t m_pad, uint16_t* __restrict__ Zhi,
+                                 uint16_t* __restrict__ Zlo) {
+  const int64_t chunks = ldh / 8;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m_pad * chunks) return;
+  const int64_t r = e / chunks, ch = e % chunks;
+  uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
+  if (r < m) {
+    const int64_t src = idx[r] * ldh + ch * 8;
+    vh = *reinterpret_cast<const uint4*>(Xhi + src);
+    vl = *reinterpret_cast<const uint4*>(Xlo + src);
+  }
+  *reinterpret_cast<uint4*>(Zhi + r * ldh + ch * 8) = vh;
+  *reinterpret_cast<uint4*>(Zlo + r * ldh + ch * 8) = vl;
 }
 
 // ---------------------------------------------------------------------------
@@ -427,14 +538,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2-D BF16 map over rows x inner (row pitch `pitch_elems`), 64 x box_rows boxes,
 // 128-byte swizzle, zero fill outside the tensor.
 int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int64_t pitch_elems,
-             uint32_t box_rows) {
+             uint32_t box_rows, uint32_t box_inner) {
   auto fn = encode_fn();
   if (!fn) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * 2) % 16)
     return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)(rows > 0 ? rows : 1)};
   cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * 2)};
-  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -446,21 +557,39 @@ int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, in
 template <bool SCORE>
 int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, uint16_t* out,
               int64_t ld, int64_t plane, int64_t row0, const float* y, const float* o,
-              double2* part, int32_t kappa, cudaStream_t s) {
-  if (ceil_div(p->n, (int64_t)KB_N) > 65535)
-    return set_error(SPSVM_ERR_ARG, "BF16X3 kernel block: n > 16,776,960 points");
-  CUtensorMap mh, ml;
-  SPSVM_TRY(make_map(&mh, p->hi, p->ldh, p->n, p->ldh, KB_N));
-  SPSVM_TRY(make_map(&ml, p->lo, p->ldh, p->n, p->ldh, KB_N));
+              double2* part, int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s) {
+  const int64_t m_pad = round_up(m, (int64_t)PK_M);
+  if (!zbuf || zbytes < (size_t)(m_pad * p->ldh * 4))
+    return set_error(SPSVM_ERR_OOM, "BF16X3 kernel block: scratch too small for the gathered rows");
+  uint16_t* zhi = static_cast<uint16_t*>(zbuf);
+  uint16_t* zlo = zhi + m_pad * p->ldh;
+  const int64_t work = m_pad * (p->ldh / 8);
+  gather_rows_bf16<<<(unsigned)ceil_div(work, (int64_t)256), 256, 0, s>>>(
+      p->hi, p->lo, p->ldh, idx, m, m_pad, zhi, zlo);
+  SPSVM_LAUNCH_CHECK();
+  CUtensorMap mzh, mzl, mxh, mxl, moh, mol;
+  SPSVM_TRY(make_map(&mzh, zhi, p->ldh, m_pad, p->ldh, PK_M, 64));
+  SPSVM_TRY(make_map(&mzl, zlo, p->ldh, m_pad, p->ldh, PK_M, 64));
+  SPSVM_TRY(make_map(&mxh, p->hi, p->ldh, p->n, p->ldh, PK_N, 64));
+  SPSVM_TRY(make_map(&mxl, p->lo, p->ldh, p->n, p->ldh, PK_N, 64));
+  if (!SCORE) {
+    // output rows [0, row0 + m): rows past the basis block are clipped, never written
+    SPSVM_TRY(make_map(&moh, out, p->n, row0 + m, ld, 32, 64));
+    SPSVM_TRY(make_map(&mol, out + plane, p->n, row0 + m, ld, 32, 64));
+  } else {
+    moh = mxh;
+    mol = mxl;
+  }
   auto kern = kblock_tc_kernel<SCORE>;
   static bool attr = false;
   if (!attr) {
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, KB_SMEM));
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
     attr = true;
   }
-  dim3 grid((unsigned)ceil_div(m, KB_M), (unsigned)ceil_div(p->n, (int64_t)KB_N));
-  kern<<<grid, KB_THREADS, KB_SMEM, s>>>(mh, ml, p->hi, p->lo, p->ldh, p->n, p->norms, idx, m,
-                                         gamma, out, ld, plane, row0, y, o, part, kappa);
+  const int64_t tiles = ceil_div((int64_t)m, (int64_t)PK_M) * ceil_div(p->n, (int64_t)PK_N);
+  const int grid = (int)min64(tiles, (int64_t)sm_count());
+  kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzl, mxh, mxl, moh, mol, p->ldh, p->n, m, p->norms,
+                                         idx, gamma, row0, y, o, part, kappa);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -469,22 +598,28 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
 
 bool tc_available() { return encode_fn() != nullptr; }
 
+size_t kernel_block_tc_scratch(int64_t m, int64_t ldh) {
+  return (size_t)(round_up(m, (int64_t)PK_M) * ldh * 4);
+}
+
 int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
-                           spsvm_kmat* out, int64_t row0, cudaStream_t s) {
+                           spsvm_kmat* out, int64_t row0, void* scratch, size_t scratch_bytes,
+                           cudaStream_t s) {
   if (m == 0 || p->n == 0) return SPSVM_OK;
   if (out->format != SPSVM_BF16X3 || (out->ld % 8) != 0 || (out->plane % 8) != 0)
     return set_error(SPSVM_ERR_ARG,
                      "BF16X3 kernel block: needs BF16X3 storage with ld %% 8 == 0, plane %% 8 == 0");
   return launch_kb<false>(p, idx, m, gamma, static_cast<uint16_t*>(out->data), out->ld, out->plane,
-                          row0, nullptr, nullptr, nullptr, 0, s);
+                          row0, nullptr, nullptr, nullptr, 0, scratch, scratch_bytes, s);
 }
 
-int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)KB_N); }
+int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)PK_N); }
 
 int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const int64_t* idx,
-                    int32_t kappa, float gamma, double2* part, int64_t tiles, cudaStream_t s) {
+                    int32_t kappa, float gamma, double2* part, int64_t tiles, void* zbuf,
+                    size_t zbytes, cudaStream_t s) {
   (void)tiles;
-  return launch_kb<true>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, s);
+  return launch_kb<true>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
 }
 
 int64_t gram_tc_splits(int64_t m, int64_t ns_max) {
@@ -502,8 +637,8 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
   const uint16_t* hi = static_cast<const uint16_t*>(Kc->data);
   const uint16_t* lo = hi + Kc->plane;
   CUtensorMap mh, ml;
-  SPSVM_TRY(make_map(&mh, hi, Kc->ld, m, Kc->ld, GR_TILE));
-  SPSVM_TRY(make_map(&ml, lo, Kc->ld, m, Kc->ld, GR_TILE));
+  SPSVM_TRY(make_map(&mh, hi, Kc->ld, m, Kc->ld, GR_TILE, 64));
+  SPSVM_TRY(make_map(&ml, lo, Kc->ld, m, Kc->ld, GR_TILE, 64));
   static bool attr = false;
   if (!attr) {
     SPSVM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -148,5 +148,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 2^x by the hardware approximation (relative error about 2^-22; x <= 0
+// here, results below 2^-126 flush to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 }  // namespace tc
 }  // namespace spsvm
