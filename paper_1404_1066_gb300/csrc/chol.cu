@@ -11,54 +11,66 @@ namespace {
 constexpr int NB = 64;   // diagonal blocks of the triangular solve
 constexpr int PB = 32;   // panel width of the factorisation
 
-// Factors the PB x PB diagonal block at k0 in place, one warp: thread i owns
-// row i of the block in shared memory.
+// Factors the PB x PB diagonal block at k0 in place with one warp: lane i
+// holds row i of the block in registers; each column's pivot and entries are
+// broadcast with warp shuffles.
+__device__ __forceinline__ double shfl_d(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
 __global__ void __launch_bounds__(32) potrf_diag(double* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, int32_t* __restrict__ info) {
-  __shared__ double A[PB][PB + 1];
   if (*info != 0) return;
   const int nb = (int)min64(PB, m - k0);
   const int i = threadIdx.x;
+  double a[PB];
+#pragma unroll
   for (int c = 0; c < PB; ++c)
-    A[i][c] = (i < nb && c <= i) ? H[(k0 + i) * ldh + k0 + c] : 0.0;
-  __syncwarp();
+    a[c] = (i < nb && c <= i) ? H[(k0 + i) * ldh + k0 + c] : (c == i ? 1.0 : 0.0);
   int fail = 0;
-  for (int j = 0; j < nb; ++j) {
-    if (i == j) {
-      const double d = A[j][j];
-      A[j][j] = (d > 0.0) ? sqrt(d) : d;
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    if (j < nb && fail == 0) {
+      const double djj = shfl_d(a[j], j);   // A[j][j], updated by the previous columns
+      if (!(djj > 0.0)) {
+        fail = j + 1;
+      } else {
+        const double ljj = sqrt(djj);
+        const double inv = 1.0 / ljj;
+        if (i == j) a[j] = ljj;
+        else if (i > j) a[j] *= inv;       // L[i][j]
+#pragma unroll
+        for (int l = j + 1; l < PB; ++l) {
+          const double llj = shfl_d(a[j], l);  // L[l][j]
+          if (i >= l) a[l] = fma(-a[j], llj, a[l]);
+        }
+      }
     }
-    __syncwarp();
-    const double piv = A[j][j];
-    if (!(piv > 0.0)) {
-      fail = j + 1;
-      break;
-    }
-    if (i > j && i < nb) A[i][j] /= piv;
-    __syncwarp();
-    if (i > j && i < nb) {
-      const double aij = A[i][j];
-      for (int l = j + 1; l <= i; ++l) A[i][l] -= aij * A[l][j];
-    }
-    __syncwarp();
   }
   if (fail) {
     if (i == 0) *info = (int32_t)(k0 + fail);
     return;
   }
-  if (i < nb)
-    for (int c = 0; c <= i; ++c) H[(k0 + i) * ldh + k0 + c] = A[i][c];
+  if (i < nb) {
+#pragma unroll
+    for (int c = 0; c < PB; ++c)
+      if (c <= i) H[(k0 + i) * ldh + k0 + c] = a[c];
+  }
 }
 
-// Rows r >= k0 + PB: L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, one thread per row.
+// Rows r >= k0 + PB: L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, one thread per
+// row, reciprocal pivots and four partial sums per dot product.
 __global__ void __launch_bounds__(32) trsm_panel(double* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, const int32_t* __restrict__ info) {
   __shared__ double L[PB][PB + 1];
+  __shared__ double rd[PB];
   if (*info != 0) return;
   for (int e = threadIdx.x; e < PB * PB; e += blockDim.x) {
     const int r = e / PB, c = e % PB;
     L[r][c] = (c <= r) ? H[(k0 + r) * ldh + k0 + c] : 0.0;
   }
+  __syncthreads();
+  if (threadIdx.x < PB) rd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
   __syncthreads();
   const int64_t r = k0 + PB + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m) return;
@@ -68,10 +80,15 @@ __global__ void __launch_bounds__(32) trsm_panel(double* __restrict__ H, int64_t
   for (int j = 0; j < PB; ++j) x[j] = row[j];
 #pragma unroll
   for (int j = 0; j < PB; ++j) {
-    double s = x[j];
+    double s0 = x[j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-    for (int l = 0; l < j; ++l) s -= x[l] * L[j][l];
-    x[j] = s / L[j][j];
+    for (int l = 0; l < j; ++l) {
+      if ((l & 3) == 0) s0 = fma(-x[l], L[j][l], s0);
+      else if ((l & 3) == 1) s1 = fma(-x[l], L[j][l], s1);
+      else if ((l & 3) == 2) s2 = fma(-x[l], L[j][l], s2);
+      else s3 = fma(-x[l], L[j][l], s3);
+    }
+    x[j] = ((s0 + s1) + (s2 + s3)) * rd[j];
   }
 #pragma unroll
   for (int j = 0; j < PB; ++j) row[j] = x[j];
@@ -161,7 +178,8 @@ __global__ void __launch_bounds__(64) diag_inverse(double* __restrict__ H, int64
   }
 }
 
-constexpr int SV_T = 256;
+constexpr int SV_T = 256;      // threads of the block-inverse product
+constexpr int SV_ROWS = 64;    // rows updated per CTA
 
 // Loads inv(L_kk) (lower, 64 x 64, zero above the diagonal) of block k0.
 __device__ __forceinline__ void load_block_inverse(const double* __restrict__ L, int64_t ldh,
@@ -201,7 +219,8 @@ __global__ void __launch_bounds__(SV_T) trsv_fwd_step(const double* __restrict__
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x < nb) z[k0 + threadIdx.x] = zs[threadIdx.x];
-  const int64_t r = k0 + nb + (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (threadIdx.x >= SV_ROWS) return;
+  const int64_t r = k0 + nb + (int64_t)blockIdx.x * SV_ROWS + threadIdx.x;
   if (r >= m) return;
   const double2* row = reinterpret_cast<const double2*>(L + r * ldh + k0);
   double s = 0.0;
@@ -241,7 +260,8 @@ __global__ void __launch_bounds__(SV_T) trsv_bwd_step(const double* __restrict__
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x < nb) x[k0 + threadIdx.x] = xs[threadIdx.x];
-  const int64_t r = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (threadIdx.x >= SV_ROWS) return;
+  const int64_t r = (int64_t)blockIdx.x * SV_ROWS + threadIdx.x;
   if (r >= k0) return;
   double s = 0.0;
 #pragma unroll 16
@@ -288,13 +308,13 @@ extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, dou
   // forward: rows below each block are updated in b, z_k goes to work
   for (int64_t k0 = 0; k0 < m; k0 += NB) {
     const int64_t below = m - min64(m, k0 + NB);
-    const unsigned grid = (unsigned)(below > 0 ? ceil_div(below, (int64_t)SV_T) : 1);
+    const unsigned grid = (unsigned)(below > 0 ? ceil_div(below, (int64_t)SV_ROWS) : 1);
     trsv_fwd_step<<<grid, SV_T, 0, s>>>(L, ldh, m, k0, b, work);
     SPSVM_LAUNCH_CHECK();
   }
   // backward: rows above each block are updated in work, x_k goes to b
   for (int64_t k0 = ((m - 1) / NB) * NB; k0 >= 0; k0 -= NB) {
-    const unsigned grid = (unsigned)(k0 > 0 ? ceil_div(k0, (int64_t)SV_T) : 1);
+    const unsigned grid = (unsigned)(k0 > 0 ? ceil_div(k0, (int64_t)SV_ROWS) : 1);
     trsv_bwd_step<<<grid, SV_T, 0, s>>>(L, ldh, m, k0, work, b);
     SPSVM_LAUNCH_CHECK();
   }
