@@ -212,8 +212,17 @@ int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max,
  * with the inverse of that block of L (transposed), which
  * spsvm_cholesky_solve uses; the rest of the upper triangle is not touched.
  * info: device int32, 0 on success, else k+1 for the first non-positive
- * pivot k (the factor is then incomplete).  Read info after a stream sync. */
-int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* stream);
+ * pivot k (the factor is then incomplete).  Read info after a stream sync.
+ * work: device, spsvm_cholesky_work_bytes(m) bytes, or NULL.  With work, the
+ * trailing updates of the 64-column steps run on the tensor cores in an
+ * FP64-faithful split form (each panel row scaled by a power of two and cut
+ * into eight 7-bit integer slices, exact in BF16; the slice products are
+ * exact integers in the FP32 accumulators and are recombined in FP64), so the
+ * result matches the FP64 factorisation to within FP64 rounding; without
+ * work every step runs in FP64 on the CUDA cores. */
+size_t spsvm_cholesky_work_bytes(int64_t m);
+int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* work,
+                   size_t work_bytes, void* stream);
 
 /* Solves L L^T x = b in place (b overwritten by x), FP64, by blocked
  * forward and backward substitution (one launch per 64-row block, each

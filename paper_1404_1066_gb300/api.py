@@ -212,11 +212,15 @@ def spsvm_gram(Kc: KMat, nact, ns_max, K: KMat, J, lam, precision, rows=None):
     return H[:m, :m]
 
 
-def spsvm_cholesky(H: torch.Tensor):
-    """In-place lower Cholesky factor of H (FP64, square); returns info."""
+def spsvm_cholesky(H: torch.Tensor, tensor_cores=True):
+    """In-place lower Cholesky factor of H (FP64, square); returns info.
+    tensor_cores selects the FP64-faithful tensor-core trailing update."""
     m = H.shape[0]
     info = torch.zeros(1, dtype=torch.int32, device=H.device)
-    check(_lib().spsvm_cholesky(ptr(H), m, H.stride(0), ptr(info), stream_ptr()), "spsvm_cholesky")
+    wb = _lib().spsvm_cholesky_work_bytes(m) if tensor_cores else 0
+    work = torch.empty(max(1, wb), dtype=torch.uint8, device=H.device) if wb else None
+    check(_lib().spsvm_cholesky(ptr(H), m, H.stride(0), ptr(info), ptr(work), wb, stream_ptr()),
+          "spsvm_cholesky")
     return int(info.item())
 
 

@@ -275,12 +275,42 @@ __global__ void __launch_bounds__(SV_T) trsv_bwd_step(const double* __restrict__
 
 using namespace spsvm;
 
-extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* stream) {
+namespace spsvm {
+size_t chol_tc_work_bytes(int64_t m);
+int chol_tc_panel_update(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
+                         cudaStream_t s);
+int chol_tc_trailing(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
+                     void* work, cudaStream_t s);
+}  // namespace spsvm
+
+extern "C" size_t spsvm_cholesky_work_bytes(int64_t m) {
+  return m > 0 ? chol_tc_work_bytes(m) : 0;
+}
+
+extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* work,
+                              size_t work_bytes, void* stream) {
   if (!H || !info || m < 0 || ldh < m) return set_error(SPSVM_ERR_ARG, "cholesky: bad arguments");
   cudaStream_t s = as_stream(stream);
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
-  for (int64_t k0 = 0; k0 < m; k0 += PB) {
+  int64_t k0 = 0;
+  if (work && work_bytes >= chol_tc_work_bytes(m)) {
+    // 64-column steps with the trailing update on the tensor cores while the
+    // trailing matrix is large; the last few hundred columns run natively
+    for (; m - (k0 + 64) >= 256; k0 += 64) {
+      potrf_diag<<<1, 32, 0, s>>>(H, ldh, m, k0, info);
+      SPSVM_LAUNCH_CHECK();
+      trsm_panel<<<(unsigned)ceil_div(m - (k0 + PB), 32), 32, 0, s>>>(H, ldh, m, k0, info);
+      SPSVM_LAUNCH_CHECK();
+      SPSVM_TRY(chol_tc_panel_update(H, ldh, m, k0, info, s));
+      potrf_diag<<<1, 32, 0, s>>>(H, ldh, m, k0 + PB, info);
+      SPSVM_LAUNCH_CHECK();
+      trsm_panel<<<(unsigned)ceil_div(m - (k0 + 2 * PB), 32), 32, 0, s>>>(H, ldh, m, k0 + PB, info);
+      SPSVM_LAUNCH_CHECK();
+      SPSVM_TRY(chol_tc_trailing(H, ldh, m, k0, info, work, s));
+    }
+  }
+  for (; k0 < m; k0 += PB) {
     potrf_diag<<<1, 32, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
     const int64_t below = m - (k0 + PB);

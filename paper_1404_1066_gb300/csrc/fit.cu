@@ -150,9 +150,10 @@ struct Layout {
   int64_t n, d, ldn, ldh, jcap, kappa, q;
   size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
       off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_ws, off_sv, off_J, off_cand,
-      off_cg, off_ch, off_cd, off_small, off_scratch, total;
+      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, total;
   size_t scratch_bytes;
   size_t kbytes;
+  size_t chw_bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -210,6 +211,8 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   sc = std::max(sc, spsvm_line_scratch_bytes(n));
   L.scratch_bytes = al(sc);
   L.off_scratch = take(L.scratch_bytes);
+  L.chw_bytes = spsvm_cholesky_work_bytes(L.jcap);
+  L.off_chw = take(L.chw_bytes);
   L.total = off;
   return L;
 }
@@ -351,7 +354,7 @@ struct Fit {
       }
       // Newton system on the active set
       SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s, st[2]));
-      SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, s));
+      SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
       int32_t info_h = 0;
       SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
@@ -365,7 +368,7 @@ struct Fit {
         SPSVM_TRY(sync());
         add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, 1e-10 * tr / m);
         SPSVM_LAUNCH_CHECK();
-        SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, s));
+        SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
         SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
         SPSVM_TRY(sync());
         if (info_h != 0)

@@ -670,8 +670,14 @@ int tc_take_status() {
 
 }  // namespace spsvm
 
+namespace spsvm {
+int chol_tc_status();
+}
+
 extern "C" int spsvm_device_status(int32_t* code) {
-  const int v = spsvm::tc_take_status();
+  int v = spsvm::tc_take_status();
+  const int v2 = spsvm::chol_tc_status();
+  if (v == 0 && v2 != 0) v = (v2 > 0) ? 100 + v2 : v2;
   if (code) *code = v;
   if (v < 0) return spsvm::set_error(SPSVM_ERR_CUDA, "device status unreadable");
   if (v > 0) return spsvm::set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", v);

@@ -210,13 +210,14 @@ def test_gram(sp, prec, n, m, p):
     assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))
 
 
-@pytest.mark.parametrize("m", [1, 5, 63, 64, 65, 200, 513])
-def test_cholesky_and_solve(sp, m):
+@pytest.mark.parametrize("tc", [False, True])
+@pytest.mark.parametrize("m", [1, 5, 63, 64, 65, 200, 513, 1500])
+def test_cholesky_and_solve(sp, m, tc):
     g = np.random.default_rng(m)
     A = g.standard_normal((m, m + 3))
     H = A @ A.T + 1e-2 * np.eye(m)
     Ht = _t(H.copy())
-    info = sp.spsvm_cholesky(Ht)
+    info = sp.spsvm_cholesky(Ht, tensor_cores=tc)
     assert info == 0
     Lg = np.tril(Ht.cpu().numpy())
     Lr = np.linalg.cholesky(H)
@@ -227,6 +228,24 @@ def test_cholesky_and_solve(sp, m):
     x = bt.cpu().numpy()
     xr = np.linalg.solve(H, b)
     assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr) * max(1, np.linalg.cond(H) * 1e-6)
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_cholesky_ill_conditioned_newton_matrix(sp, tc):
+    # the Newton matrix of Eq. 4 on RBF data: lambda K_JJ + K_SJ^T K_SJ,
+    # lambda = 1e-4, kernel rows of nearby points (condition number ~1e9)
+    g = np.random.default_rng(3)
+    X = g.standard_normal((3000, 8)) * 0.7
+    J = np.arange(0, 3000, 3)[:900]
+    K = O.rbf_kernel(X, X[J], 0.125)
+    S = g.random(3000) < 0.3
+    H = 1e-4 * K[J] + K[S].T @ K[S]
+    H = 0.5 * (H + H.T)
+    Ht = _t(H.copy())
+    assert sp.spsvm_cholesky(Ht, tensor_cores=tc) == 0
+    Lg = np.tril(Ht.cpu().numpy())
+    # backward error of the factorisation, as FP64 Cholesky guarantees
+    assert np.linalg.norm(Lg @ Lg.T - H) <= 1e-13 * np.linalg.norm(H)
 
 
 def test_cholesky_reports_indefinite(sp):

@@ -70,5 +70,5 @@ def test_workspace_size_and_argument_checks():
     # bad arguments are rejected before any device work
     h = C.c_void_p()
     assert lib.spsvm_fit(None, 10, 2, 2, None, 1.0, 1.0, 1, 0.0, None, None, 0, C.byref(h)) == -1
-    assert lib.spsvm_cholesky(None, 4, 4, None, None) == -1
+    assert lib.spsvm_cholesky(None, 4, 4, None, None, 0, None) == -1
     assert b"NULL" in lib.spsvm_last_error() or b"bad" in lib.spsvm_last_error()
