@@ -11,13 +11,23 @@ namespace {
 constexpr int NB = 64;   // diagonal blocks of the triangular solve
 constexpr int PB = 32;   // panel width of the factorisation
 
-// Factors the PB x PB diagonal block at k0 in place with one warp: lane i
-// holds row i of the block in registers; each column's pivot and entries are
-// broadcast with warp shuffles.
+// 1 / sqrt(d) in FP64 without the long-latency FP64 sqrt and division: the
+// FP32 estimate refined by two Newton steps y <- y (3 - d y^2) / 2, each of
+// which doubles the number of correct bits (about 23 -> 46 -> full FP64).
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  return y;
+}
+
 __device__ __forceinline__ double shfl_d(double v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
+// Factors the PB x PB diagonal block at k0 in place with one warp: lane i
+// holds row i of the block in registers; pivots and column entries are
+// broadcast with warp shuffles.
 __global__ void __launch_bounds__(32) potrf_diag(double* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, int32_t* __restrict__ info) {
   if (*info != 0) return;
@@ -32,13 +42,12 @@ __global__ void __launch_bounds__(32) potrf_diag(double* __restrict__ H, int64_t
   for (int j = 0; j < PB; ++j) {
     if (j < nb && fail == 0) {
       const double djj = shfl_d(a[j], j);   // A[j][j], updated by the previous columns
-      if (!(djj > 0.0)) {
+      if (!(djj > 0.0) || !(djj < 1e300)) {
         fail = j + 1;
       } else {
-        const double ljj = sqrt(djj);
-        const double inv = 1.0 / ljj;
-        if (i == j) a[j] = ljj;
-        else if (i > j) a[j] *= inv;       // L[i][j]
+        const double y = rsqrt_fp64(djj);
+        if (i == j) a[j] = djj * y;          // L_jj = sqrt(d)
+        else if (i > j) a[j] *= y;           // L[i][j]
 #pragma unroll
         for (int l = j + 1; l < PB; ++l) {
           const double llj = shfl_d(a[j], l);  // L[l][j]
@@ -59,7 +68,9 @@ __global__ void __launch_bounds__(32) potrf_diag(double* __restrict__ H, int64_t
 }
 
 // Rows r >= k0 + PB: L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, one thread per
-// row, reciprocal pivots and four partial sums per dot product.
+// row, column-oriented substitution: x_j = b_j / L_jj, then b_l -= x_j L_lj
+// for the remaining l (independent updates, so the dependent chain is two
+// operations per column).
 __global__ void __launch_bounds__(32) trsm_panel(double* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, const int32_t* __restrict__ info) {
   __shared__ double L[PB][PB + 1];
@@ -80,15 +91,9 @@ __global__ void __launch_bounds__(32) trsm_panel(double* __restrict__ H, int64_t
   for (int j = 0; j < PB; ++j) x[j] = row[j];
 #pragma unroll
   for (int j = 0; j < PB; ++j) {
-    double s0 = x[j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    x[j] *= rd[j];
 #pragma unroll
-    for (int l = 0; l < j; ++l) {
-      if ((l & 3) == 0) s0 = fma(-x[l], L[j][l], s0);
-      else if ((l & 3) == 1) s1 = fma(-x[l], L[j][l], s1);
-      else if ((l & 3) == 2) s2 = fma(-x[l], L[j][l], s2);
-      else s3 = fma(-x[l], L[j][l], s3);
-    }
-    x[j] = ((s0 + s1) + (s2 + s3)) * rd[j];
+    for (int l = j + 1; l < PB; ++l) x[l] = fma(-x[j], L[l][j], x[l]);
   }
 #pragma unroll
   for (int j = 0; j < PB; ++j) row[j] = x[j];

@@ -40,6 +40,12 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
+// 2^k for integer k (exact power of two).
+__device__ __forceinline__ double pow2(int k) {
+  if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(1.0, k);
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
                                             uint64_t* bar) {
   asm volatile(
@@ -148,23 +154,36 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
     const int er = rin ? ex[r] : 0;
     const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16);
     for (int cc = 0; cc < OZ_TN / 32; ++cc) {
-      double acc[32];
+      // each level sum is an exact integer below 2^24; levels 0-3 and 4-7
+      // combine exactly into two 64-bit integers (below 2^46 each)
+      long long hi[32], lo[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+      for (int j = 0; j < 32; ++j) {
+        hi[j] = 0;
+        lo[j] = 0;
+      }
+#pragma unroll
       for (int lv = 0; lv < OZ_LEVELS; ++lv) {
         float v[32];
         tmem_ld32(tb + lv * OZ_TN + cc * 32, v);
-        const double sc = ldexp(1.0, -7 * (lv + 2));
+        const int sh = 7 * (3 - (lv & 3));
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = fma((double)v[j], sc, acc[j]);
+        for (int j = 0; j < 32; ++j) {
+          const long long q = (long long)__float2int_rn(v[j]) * (1LL << sh);
+          if (lv < 4) hi[j] += q;
+          else lo[j] += q;
+        }
       }
       if (rin) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int64_t c = c0 + cc * 32 + j;
           if (c <= r && c < m) {
+            // value = hi 2^-35 + lo 2^-63, times 2^(e_r + e_c)
+            const int e = er + ec[cc * 32 + j];
+            const double val = fma((double)lo[j], pow2(e - 63), (double)hi[j] * pow2(e - 35));
             double* p = H + r * ldh + c;
-            *p = fma(-acc[j], ldexp(1.0, er + ec[cc * 32 + j]), *p);
+            *p -= val;
           }
         }
       }
