@@ -346,6 +346,65 @@ void spsvm_free(spsvm_model* model);
 int32_t spsvm_draw_candidates(int64_t n, const int64_t* J, int32_t nJ, int32_t kappa,
                               uint64_t seed, uint32_t round, int64_t* out);
 
+/* ======================================================================= */
+/* Many fits at once (Section 5 trains one binary SP-SVM per class pair;    */
+/* the grid of one-vs-rest classes x (gamma, lambda) and the request loop   */
+/* below have no further counterpart in the paper).                          */
+/* ======================================================================= */
+
+/* One binary problem on rows of a shared X. */
+typedef struct spsvm_problem {
+  const int64_t* rows;     /* host, n_rows indices into X, or NULL for all rows */
+  int64_t  n_rows;
+  const float* y;          /* host, n_rows labels +-1 (for those rows, in order) */
+  float    gamma;
+  float    pad_;
+  double   lambda;
+  int32_t  basis_budget;
+  int32_t  pad2_;
+  double   tol;
+  uint64_t seed;           /* candidate draw seed (0: the options' seed) */
+} spsvm_problem;
+
+/* Fits `count` problems on the shared device matrix X (n x d, ldx).  Work is
+ * spread over `workers` host threads, each with its own CUDA stream and its
+ * own device buffers (allocated here, freed on return), largest problem
+ * first.  Each problem's result equals what spsvm_fit returns for it alone
+ * (fixed reduction order; no cross-problem arithmetic).  outs[p] receives
+ * the model (or NULL), status[p] the fit's status.  Returns OK, or the first
+ * error with status[] telling which problems failed. */
+int spsvm_fit_batched(const float* X, int64_t n, int64_t d, int64_t ldx,
+                      const spsvm_problem* probs, int32_t count, const spsvm_options* opt,
+                      int32_t workers, spsvm_model** outs, int32_t* status);
+
+/* Request loop.  Requests carry host data (copied at submission).  Each has
+ * an HBM footprint (fit: X, y, the fit workspace and the model; predict: the
+ * queries and results); a request is admitted, in arrival order, when a
+ * worker is free and the footprints of the requests running plus its own fit
+ * in the budget; later requests that fit run ahead of one that does not
+ * (continuous batching), unless it has waited more than two seconds.  A
+ * predict request is admitted once its fit request has finished.  Workers
+ * own one CUDA stream each, so admitted requests overlap on the device.
+ * The server allocates device memory per request and frees it when done. */
+typedef struct spsvm_server spsvm_server;
+int spsvm_server_create(size_t hbm_budget_bytes, int32_t workers, spsvm_server** out);
+int spsvm_server_submit_fit(spsvm_server* s, const float* X, int64_t n, int64_t d,
+                            const float* y, float gamma, double lambda, int32_t basis_budget,
+                            double tol, const spsvm_options* opt, int64_t* request_id);
+int spsvm_server_submit_predict(spsvm_server* s, int64_t fit_request_id, const float* Xq,
+                                int64_t nq, int64_t* request_id);
+/* Waits up to timeout_s (negative: forever) for a request; TIMEOUT if it has
+ * not finished.  latency_ms: submission to completion. */
+int spsvm_server_wait(spsvm_server* s, int64_t request_id, double timeout_s, int32_t* status,
+                      double* latency_ms);
+/* Results of a finished request: decision values (host, cap >= nq) of a
+ * predict, or the model of a fit (owned by the server until destroy). */
+int spsvm_server_result(spsvm_server* s, int64_t request_id, float* decision, int64_t cap,
+                        spsvm_model** model);
+int spsvm_server_stats(spsvm_server* s, int64_t* done, int64_t* queued, size_t* hbm_in_use,
+                       size_t* hbm_peak);
+void spsvm_server_destroy(spsvm_server* s);
+
 /* ---- instrumentation (no paper counterpart: measurement support) ---- */
 /* Number of CUDA kernel launches the library has issued in this process. */
 uint64_t spsvm_launch_count(void);

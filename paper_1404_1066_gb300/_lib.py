@@ -48,6 +48,13 @@ class spsvm_options(C.Structure):
                 ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p)]
 
 
+class spsvm_problem(C.Structure):
+    _fields_ = [("rows", C.c_void_p), ("n_rows", C.c_int64), ("y", C.c_void_p),
+                ("gamma", C.c_float), ("pad_", C.c_float), ("lambda_", C.c_double),
+                ("basis_budget", C.c_int32), ("pad2_", C.c_int32), ("tol", C.c_double),
+                ("seed", C.c_uint64)]
+
+
 class spsvm_step(C.Structure):
     _fields_ = [("basis", C.c_int32), ("active", C.c_int32), ("gnorm", C.c_double),
                 ("t", C.c_double), ("loss", C.c_double), ("errors", C.c_int32),
@@ -103,6 +110,17 @@ SIGNATURES = {
     "spsvm_model_outputs": (_I32, [_P, _P, _I64]),
     "spsvm_free": (None, [_P]),
     "spsvm_draw_candidates": (_I32, [_I64, _P, _I32, _I32, C.c_uint64, C.c_uint32, _P]),
+    "spsvm_fit_batched": (_I32, [_P, _I64, _I64, _I64, C.POINTER(spsvm_problem), _I32,
+                                 C.POINTER(spsvm_options), _I32, _P, _P]),
+    "spsvm_server_create": (_I32, [_SZ, _I32, C.POINTER(_P)]),
+    "spsvm_server_submit_fit": (_I32, [_P, _P, _I64, _I64, _P, _F, _D, _I32, _D,
+                                       C.POINTER(spsvm_options), C.POINTER(_I64)]),
+    "spsvm_server_submit_predict": (_I32, [_P, _I64, _P, _I64, C.POINTER(_I64)]),
+    "spsvm_server_wait": (_I32, [_P, _I64, _D, C.POINTER(_I32), C.POINTER(_D)]),
+    "spsvm_server_result": (_I32, [_P, _I64, _P, _I64, C.POINTER(_P)]),
+    "spsvm_server_stats": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_SZ),
+                                  C.POINTER(_SZ)]),
+    "spsvm_server_destroy": (None, [_P]),
     "spsvm_launch_count": (C.c_uint64, []),
     "spsvm_profile_enable": (_I32, [_I32]),
     "spsvm_profile_read": (_I32, [_I32, C.POINTER(C.c_char_p), C.POINTER(_I64), C.POINTER(_D),

@@ -11,7 +11,7 @@ import torch
 
 from . import _lib as L
 from ._lib import (SPSVM_BF16X3, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
-                   spsvm_kmat, spsvm_options, spsvm_points, spsvm_step)
+                   spsvm_kmat, spsvm_options, spsvm_points, spsvm_problem, spsvm_step)
 
 
 def _lib():
@@ -391,3 +391,118 @@ def spsvm_predict(model: Model, Xq: torch.Tensor, stream=None):
     check(_lib().spsvm_predict(model.handle, ptr(Xq), Xq.shape[0], Xq.stride(0), ptr(out),
                                stream_ptr(stream)), "spsvm_predict")
     return out
+
+
+# ---------------------------------------------------------------- batched / serving
+def spsvm_fit_batched(X: torch.Tensor, problems, workers=4, **opts):
+    """problems: list of dicts with rows (int64 array or None), y (float32
+    array), gamma, lam, budget, tol, seed.  Returns (models, statuses)."""
+    _require_cuda(X)
+    n, d = X.shape
+    keep = []
+    arr = (spsvm_problem * max(1, len(problems)))()
+    for k, p in enumerate(problems):
+        rows = p.get("rows")
+        y = np.ascontiguousarray(np.asarray(p["y"], dtype=np.float32))
+        keep.append(y)
+        q = arr[k]
+        if rows is not None:
+            rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+            keep.append(rows)
+            q.rows = rows.ctypes.data
+            q.n_rows = len(rows)
+        else:
+            q.rows = None
+            q.n_rows = n
+        q.y = y.ctypes.data
+        q.gamma = float(p["gamma"])
+        q.lambda_ = float(p["lam"])
+        q.basis_budget = int(p["budget"])
+        q.tol = float(p.get("tol", 1e-6))
+        q.seed = int(p.get("seed", 0))
+    o, k0 = make_options(**opts)
+    outs = (C.c_void_p * max(1, len(problems)))()
+    st = (C.c_int32 * max(1, len(problems)))()
+    rc = _lib().spsvm_fit_batched(ptr(X), n, d, X.stride(0), arr, len(problems), C.byref(o),
+                                  int(workers), C.cast(outs, C.c_void_p), C.cast(st, C.c_void_p))
+    del keep, k0
+    models = [Model(outs[k], st[k]) if outs[k] else None for k in range(len(problems))]
+    if rc != L.SPSVM_OK and all(m is None for m in models):
+        check(rc, "spsvm_fit_batched")
+    return models, [st[k] for k in range(len(problems))]
+
+
+class _Borrowed(Model):
+    """A model owned by the server (not freed here)."""
+
+    def __del__(self):
+        pass
+
+
+class Server:
+    """spsvm_server: continuous-batching request loop with HBM admission."""
+
+    def __init__(self, hbm_budget_bytes, workers=4):
+        h = C.c_void_p()
+        check(_lib().spsvm_server_create(int(hbm_budget_bytes), int(workers), C.byref(h)),
+              "spsvm_server_create")
+        self.h = h
+
+    def submit_fit(self, X, y, gamma, lam, budget, tol=1e-6, **opts):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+        o, keep = make_options(**opts)
+        rid = C.c_int64()
+        check(_lib().spsvm_server_submit_fit(self.h, X.ctypes.data, X.shape[0], X.shape[1],
+                                             y.ctypes.data, float(gamma), float(lam), int(budget),
+                                             float(tol), C.byref(o), C.byref(rid)),
+              "spsvm_server_submit_fit")
+        del keep
+        return rid.value
+
+    def submit_predict(self, fit_id, Xq):
+        Xq = np.ascontiguousarray(np.asarray(Xq, dtype=np.float32))
+        rid = C.c_int64()
+        check(_lib().spsvm_server_submit_predict(self.h, int(fit_id), Xq.ctypes.data, Xq.shape[0],
+                                                 C.byref(rid)), "spsvm_server_submit_predict")
+        self._nq = getattr(self, "_nq", {})
+        self._nq[rid.value] = Xq.shape[0]
+        return rid.value
+
+    def wait(self, rid, timeout_s=-1.0):
+        st = C.c_int32()
+        lat = C.c_double()
+        check(_lib().spsvm_server_wait(self.h, int(rid), float(timeout_s), C.byref(st),
+                                       C.byref(lat)), "spsvm_server_wait")
+        return st.value, lat.value
+
+    def decision(self, rid):
+        nq = self._nq[rid]
+        out = np.empty(nq, dtype=np.float32)
+        check(_lib().spsvm_server_result(self.h, int(rid), out.ctypes.data, nq, None),
+              "spsvm_server_result")
+        return out
+
+    def model(self, rid):
+        m = C.c_void_p()
+        check(_lib().spsvm_server_result(self.h, int(rid), None, 0, C.byref(m)),
+              "spsvm_server_result")
+        return _Borrowed(m.value, 0) if m.value else None
+
+    def stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        c, d = C.c_size_t(), C.c_size_t()
+        check(_lib().spsvm_server_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+              "spsvm_server_stats")
+        return dict(done=a.value, queued=b.value, hbm_in_use=c.value, hbm_peak=d.value)
+
+    def close(self):
+        if self.h and self.h.value:
+            _lib().spsvm_server_destroy(self.h)
+            self.h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

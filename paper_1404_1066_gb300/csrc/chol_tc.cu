@@ -225,17 +225,17 @@ __global__ void __launch_bounds__(256) oz_panel_update(double* __restrict__ H, i
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // thread-safe one-time lookup of the driver's tensor-map encoder
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -286,12 +286,8 @@ int chol_tc_trailing(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_
   CUtensorMap ma, mb;
   SPSVM_TRY(make_slice_map(&ma, sl, m, OZ_TM));
   SPSVM_TRY(make_slice_map(&mb, sl, m, OZ_TN));
-  static bool attr = false;
-  if (!attr) {
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        OZ_SMEM));
-    attr = true;
-  }
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      OZ_SMEM));
   dim3 grid((unsigned)ceil_div(R, (int64_t)OZ_TN), (unsigned)ceil_div(R, (int64_t)OZ_TM));
   oz_trailing<<<grid, 128, OZ_SMEM, s>>>(ma, mb, H, ldh, m, base, ex, info);
   SPSVM_LAUNCH_CHECK();

@@ -521,17 +521,17 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
 // host side
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // thread-safe one-time lookup of the driver's tensor-map encoder
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -581,11 +581,7 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
     mol = mxl;
   }
   auto kern = kblock_tc_kernel<SCORE>;
-  static bool attr = false;
-  if (!attr) {
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
-    attr = true;
-  }
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
   const int64_t tiles = ceil_div((int64_t)m, (int64_t)PK_M) * ceil_div(p->n, (int64_t)PK_N);
   const int grid = (int)min64(tiles, (int64_t)sm_count());
   kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzl, mxh, mxl, moh, mol, p->ldh, p->n, m, p->norms,
@@ -639,12 +635,8 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
   CUtensorMap mh, ml;
   SPSVM_TRY(make_map(&mh, hi, Kc->ld, m, Kc->ld, GR_TILE, 64));
   SPSVM_TRY(make_map(&ml, lo, Kc->ld, m, Kc->ld, GR_TILE, 64));
-  static bool attr = false;
-  if (!attr) {
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        GR_SMEM));
-    attr = true;
-  }
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      GR_SMEM));
   const int64_t T = ceil_div(m, (int64_t)GR_TILE);
   const int64_t tiles = T * (T + 1) / 2;
   const int64_t slices = ceil_div(ns_max > 0 ? ns_max : 1, GRAM_SLICE);
