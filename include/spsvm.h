@@ -41,7 +41,7 @@ extern "C" {
 #define SPSVM_OK               0
 #define SPSVM_ERR_ARG         (-1)  /* invalid argument (shape, pointer, value) */
 #define SPSVM_ERR_OOM         (-2)  /* workspace too small or allocation failed */
-#define SPSVM_ERR_NOT_PD      (-3)  /* Newton matrix not positive definite after one shifted retry */
+#define SPSVM_ERR_NOT_PD      (-3)  /* Newton matrix not positive definite even with jitter 1e-2 tr(H)/|J| */
 #define SPSVM_ERR_NO_CONVERGE (-4)  /* max Newton steps reached; a model is still returned */
 #define SPSVM_ERR_CUDA        (-5)  /* CUDA runtime or launch error */
 #define SPSVM_ERR_TIMEOUT     (-6)  /* bounded device wait gave up */
@@ -292,7 +292,8 @@ typedef struct spsvm_step {
   double  t;               /* line-search step taken (0 for the final check) */
   double  loss;            /* 1/2 sum max(0, 1 - y o)^2 after the step */
   int32_t errors;          /* #{y_i o_i <= 0} after the step */
-  int32_t pad_;
+  int32_t jitter;          /* diagonal jitter level l of the factorisation: H + 10^(l-10) tr(H)/|J| I
+                              (-1: none); tried upwards from the fit's previous level */
 } spsvm_step;
 
 /* Device bytes the fit needs for n points in d dimensions and the budget;

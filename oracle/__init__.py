@@ -16,7 +16,8 @@ Parity status of each function (see the pins in tests/test_oracle_*.py):
   Accuracy figures of the paper's Table 1: parity unpinned (datasets absent).
 """
 from .spsvm import (  # noqa: F401
-    rbf_kernel, objective, gradient, hessian, newton_solve, line_search,
+    rbf_kernel, objective, gradient, hessian, newton_solve, jittered_cholesky, cholesky_solve,
+    jitter_shift, JITTER_MAX_LEVEL, line_search,
     line_search_derivative, score_candidates, select_top, draw_candidates,
     splitmix64, newton, fit, predict, FitResult,
 )

@@ -97,23 +97,44 @@ def hessian(beta, KnJ, KJJ, y, lam):
 # --------------------------------------------------------------------------
 # Newton system (Cholesky in float64)
 # --------------------------------------------------------------------------
-def newton_solve(H, r):
-    """beta_bar = H^{-1} r by Cholesky H = L L^T and two triangular solves.
-    If the factorisation breaks down, retry once with
-    H + 1e-10 * trace(H)/|J| * I, else raise NotPositiveDefinite."""
+JITTER_MAX_LEVEL = 8
+
+
+def jitter_shift(trace, m, level):
+    """Diagonal jitter of level l >= 0: 10^(l-10) tr(H)/|J|; level -1 is none."""
+    return 0.0 if level < 0 else 10.0 ** (level - 10) * trace / m
+
+
+def jittered_cholesky(H, level=-1):
+    """Cholesky factor of H + jitter_shift(tr H, |J|, l) I for the first
+    l = level, level + 1, ..., JITTER_MAX_LEVEL that factorises (level -1:
+    H itself).  H is positive definite in exact arithmetic (lambda > 0,
+    distinct basis points), but a computed H of a smooth kernel can lose that
+    at rounding level.  Returns (L, l); raises NotPositiveDefinite when every
+    level breaks down."""
     m = H.shape[0]
-    if m == 0:
-        return np.zeros(0)
-    try:
-        L = scipy.linalg.cholesky(H, lower=True)
-    except np.linalg.LinAlgError:
-        shift = 1e-10 * np.trace(H) / m
+    tr = float(np.trace(H))
+    for lv in range(level, JITTER_MAX_LEVEL + 1):
         try:
-            L = scipy.linalg.cholesky(H + shift * np.eye(m), lower=True)
-        except np.linalg.LinAlgError as e:
-            raise NotPositiveDefinite(str(e)) from e
-    z = scipy.linalg.solve_triangular(L, r, lower=True)
+            return scipy.linalg.cholesky(H + jitter_shift(tr, m, lv) * np.eye(m), lower=True), lv
+        except np.linalg.LinAlgError:
+            continue
+    raise NotPositiveDefinite(f"no jitter level up to {JITTER_MAX_LEVEL} factorises H")
+
+
+def cholesky_solve(L, b):
+    """(L L^T)^{-1} b by two triangular solves."""
+    z = scipy.linalg.solve_triangular(L, b, lower=True)
     return scipy.linalg.solve_triangular(L.T, z, lower=False)
+
+
+def newton_solve(H, r, level=-1):
+    """beta_bar = (H + shift I)^{-1} r with the jitter of jittered_cholesky
+    (shift 0 when H itself factorises).  Returns (beta_bar, l)."""
+    if H.shape[0] == 0:
+        return np.zeros(0), level
+    L, lv = jittered_cholesky(H, level)
+    return cholesky_solve(L, r), lv
 
 
 # --------------------------------------------------------------------------
@@ -241,13 +262,18 @@ def select_top(delta, cand, q):
 # --------------------------------------------------------------------------
 # Reoptimisation of Eq. 4 on a fixed basis
 # --------------------------------------------------------------------------
-def newton(KnJ, KJJ, y, lam, beta, tol, max_newton, history=None):
+def newton(KnJ, KJJ, y, lam, beta, tol, max_newton, history=None, jitter=None):
     """Newton iterations with exact line search on a fixed J.
 
     Stops when ||grad f|| <= tol, when the active set repeats after a full
-    step (t = 1; the quadratic piece's minimiser is then stationary), or
-    after max_newton steps.  Returns (beta, o, status) with status one of
-    'tol', 'repeat', 'max'."""
+    unjittered step (t = 1; the quadratic piece's minimiser is then
+    stationary), when no jitter level gives descent, or after max_newton
+    steps.  Returns (beta, o, status) with status one of 'tol', 'repeat',
+    'stall', 'max'.  jitter: a one-element list holding the jitter level that
+    factorised the previous Newton matrix of this fit (-1 at the start); each
+    factorisation starts from that level and stores its own."""
+    if jitter is None:
+        jitter = [-1]
     o = KnJ @ beta
     status = "max"
     for _ in range(max_newton):
@@ -259,23 +285,40 @@ def newton(KnJ, KJJ, y, lam, beta, tol, max_newton, history=None):
             if history is not None:
                 history.append(dict(objective=objective(beta, KnJ, KJJ, y, lam),
                                     gnorm=gn, active=int(S.sum()), t=0.0,
-                                    basis=len(beta), step=False))
+                                    basis=len(beta), step=False, jitter=jitter[0]))
             break
         KS = KnJ[S]
         H = lam * KJJ + KS.T @ KS
         r = KS.T @ y[S]
-        beta_bar = newton_solve(H, r)
-        d = beta_bar - beta
+        # Section 4's step d = beta_bar - beta, beta_bar = H^{-1} K_SJ^T y_S.
+        # With a jitter the step is the regularised Newton step
+        # d = -(H + shift I)^{-1} grad f (the same at shift 0); when the line
+        # search finds no descent along d the jitter goes up one level.
+        Lc, lv = jittered_cholesky(H, jitter[0])
+        d = cholesky_solve(Lc, r) - beta if lv < 0 else -cholesky_solve(Lc, g)
         u = KnJ @ d
         t = line_search(beta, d, o, u, y, KJJ, lam)
+        while t == 0.0 and lv < JITTER_MAX_LEVEL:
+            Lc, lv = jittered_cholesky(H, lv + 1)
+            d = -cholesky_solve(Lc, g)
+            u = KnJ @ d
+            t = line_search(beta, d, o, u, y, KJJ, lam)
+        jitter[0] = lv
+        if t == 0.0:
+            status = "stall"
+            if history is not None:
+                history.append(dict(objective=objective(beta, KnJ, KJJ, y, lam),
+                                    gnorm=gn, active=int(S.sum()), t=0.0,
+                                    basis=len(beta), step=False, jitter=lv))
+            break
         beta = beta + t * d
         o = KnJ @ beta
         S_new = active_set(y, o)
         if history is not None:
             history.append(dict(objective=objective(beta, KnJ, KJJ, y, lam),
                                 gnorm=gn, active=int(S.sum()), t=float(t),
-                                basis=len(beta), step=True))
-        if t == 1.0 and np.array_equal(S_new, S):
+                                basis=len(beta), step=True, jitter=jitter[0]))
+        if t == 1.0 and np.array_equal(S_new, S) and lv < 0:
             status = "repeat"
             break
     return beta, o, status
@@ -313,8 +356,9 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
     beta = np.zeros(len(J))
     res = FitResult(J=np.asarray(J, dtype=np.int64), beta=beta, o=np.zeros(n))
     status = ""
+    jitter = [-1]
     if J:
-        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history)
+        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
     else:
         o = np.zeros(n)
     E_prev = float(np.mean(y * o <= 0))
@@ -346,7 +390,7 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         J = J + [int(c) for c in chosen]
         KnJ = np.hstack([KnJ, rbf_kernel(X, X[chosen], gamma)])
         beta = np.concatenate([beta, np.zeros(len(chosen))])
-        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history)
+        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
         rnd += 1
         E = float(np.mean(y * o <= 0))
         if growth_tol > 0 and (E_prev - E) / len(chosen) < growth_tol:

@@ -58,7 +58,7 @@ class spsvm_problem(C.Structure):
 class spsvm_step(C.Structure):
     _fields_ = [("basis", C.c_int32), ("active", C.c_int32), ("gnorm", C.c_double),
                 ("t", C.c_double), ("loss", C.c_double), ("errors", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("jitter", C.c_int32)]
 
 
 _P = C.c_void_p

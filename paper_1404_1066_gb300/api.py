@@ -336,7 +336,7 @@ class Model:
         check(_lib().spsvm_model_history(self.handle, C.cast(arr, C.c_void_p), cnt.value,
                                          C.byref(cnt)), "spsvm_model_history")
         return [dict(basis=a.basis, active=a.active, gnorm=a.gnorm, t=a.t, loss=a.loss,
-                     errors=a.errors) for a in arr[:cnt.value]]
+                     errors=a.errors, jitter=a.jitter) for a in arr[:cnt.value]]
 
     def round(self, r):
         nc = C.c_int32()

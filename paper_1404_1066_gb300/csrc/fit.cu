@@ -241,6 +241,8 @@ Opts resolve(const spsvm_options* o) {
   return r;
 }
 
+constexpr int32_t kJitterMaxLevel = 8;   // largest jitter 1e-2 tr(H)/|J|
+
 struct Fit {
   const float* X;
   const float* y;
@@ -257,6 +259,7 @@ struct Fit {
   std::vector<int64_t> J;     // host copy of the basis
   int32_t m = 0;              // current |J|
   int32_t act_cur = 0;        // which active buffer holds the current flags
+  int32_t jitter = -1;        // jitter level that factorised the last Newton matrix
 
   template <typename T>
   T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
@@ -347,50 +350,73 @@ struct Fit {
       const double gnorm = std::sqrt(dh[1]), rnorm = std::sqrt(dh[2]);
       model->objective = 0.5 * lambda * dh[0] + st[0];
       if (gnorm <= std::max(tol, op.rel_tol * rnorm)) {
-        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], 0};
+        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
         model->history.push_back(rec);
         status = SPSVM_OK;
         break;
       }
-      // Newton system on the active set
-      SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s, st[2]));
-      SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
-      int32_t info_h = 0;
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
-      if (info_h != 0) {
-        // one retry with a diagonal shift of 1e-10 trace(H) / |J|
-        SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s, st[2]));
-        diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
-        SPSVM_LAUNCH_CHECK();
-        double tr = 0.0;
-        SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
-        SPSVM_TRY(sync());
-        add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, 1e-10 * tr / m);
-        SPSVM_LAUNCH_CHECK();
-        SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
-        SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
-        SPSVM_TRY(sync());
-        if (info_h != 0)
-          return set_error(SPSVM_ERR_NOT_PD, "Newton matrix not positive definite (pivot %d, |J|=%d)",
-                           info_h, m);
+      // Newton system on the active set.  Factorise H + 10^(l-10) tr(H)/|J| I
+      // for l = jitter, jitter + 1, ... (l = -1: H itself): a computed H of a
+      // smooth kernel can be indefinite at rounding level.  The direction is
+      // d = -(H + shift I)^{-1} grad f; when the line search finds no descent
+      // along it (t = 0: the computed H is too far from the exact one in its
+      // smallest directions) the level goes up and d is recomputed.  The
+      // level never goes down within a fit.
+      bool h_fresh = false;   // H holds the unfactorised matrix
+      double tr = -1.0, t = 0.0;
+      for (;;) {
+        for (int32_t lv = jitter;; ++lv) {
+          if (lv > kJitterMaxLevel)
+            return set_error(SPSVM_ERR_NOT_PD,
+                             "Newton matrix not positive definite up to jitter 1e-2 tr(H)/|J| (|J|=%d)", m);
+          if (!h_fresh)
+            SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb,
+                                s, st[2]));
+          h_fresh = false;   // the factorisation overwrites H
+          if (lv >= 0) {
+            if (tr < 0.0) {
+              diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
+              SPSVM_LAUNCH_CHECK();
+              SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
+              SPSVM_TRY(sync());
+            }
+            add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, std::pow(10.0, lv - 10) * tr / m);
+            SPSVM_LAUNCH_CHECK();
+          }
+          SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
+          int32_t info_h = 0;
+          SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
+          SPSVM_TRY(sync());
+          if (info_h == 0) {
+            jitter = lv;
+            break;
+          }
+        }
+        // d = -H^{-1} g, then refinement against the exactly applied H
+        SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, at<double>(L.off_sv), s));
+        SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
+        for (int k = 0; k < op.refine; ++k) {
+          SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
+                                         at<int32_t>(L.off_pos), scratch, sb, s));
+          refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
+          SPSVM_LAUNCH_CHECK();
+          SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, at<double>(L.off_sv), s));
+          axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
+          SPSVM_LAUNCH_CHECK();
+          SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
+        }
+        t = 0.0;
+        SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
+        if (t > 0.0 || jitter >= kJitterMaxLevel) break;
+        ++jitter;
       }
-      // d = -H^{-1} g, then refinement against the exactly applied H
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, at<double>(L.off_sv), s));
-      SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
-      for (int k = 0; k < op.refine; ++k) {
-        SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
-                                       at<int32_t>(L.off_pos), scratch, sb, s));
-        refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
-        SPSVM_LAUNCH_CHECK();
-        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, at<double>(L.off_sv), s));
-        axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
-        SPSVM_LAUNCH_CHECK();
-        SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
+      if (!(t > 0.0)) {
+        // no descent even at the largest jitter: rounding level reached
+        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
+        model->history.push_back(rec);
+        break;
       }
-      double t = 0.0;
-      SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
       axpy_d<<<mb, tpb, 0, s>>>(beta, dir, t, m);
       SPSVM_LAUNCH_CHECK();
       update_o<<<grid_for(n, tpb), tpb, 0, s>>>(o, u, t, n);
@@ -405,11 +431,13 @@ struct Fit {
       unsigned long long nd = 0;
       SPSVM_CUDA_TRY(cudaMemcpyAsync(&nd, ndiff, sizeof(nd), cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
-      spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], 0};
+      spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], jitter};
       model->history.push_back(rec);
       act_cur = nxt;
       std::memcpy(st, st2, sizeof(st));
-      if (t == 1.0 && nd == 0) {
+      // a full exact Newton step that keeps the active set lands on the
+      // minimiser of f (with a jitter only the gradient test decides)
+      if (t == 1.0 && nd == 0 && jitter < 0) {
         status = SPSVM_OK;
         break;
       }

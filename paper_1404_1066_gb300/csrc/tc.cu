@@ -363,7 +363,9 @@ __global__ void gather_rows_bf16(const uint16_t* __restrict__ Xhi, const uint16_
 
 // ---------------------------------------------------------------------------
 // Masked Gram matrix: P[a][b] (+)= sum_p Kc[a][p] Kc[b][p] over 128 x 128
-// upper-triangular tiles.  Warp 0: TMEM owner and TMA producer; warp 1: MMA
+// upper-triangular tiles, Kc = hi + lo with all four plane products, so P
+// is the Gram matrix of the stored values up to FP32 accumulation rounding
+// (positive semidefinite to that level).  Warp 0: TMEM owner and TMA producer; warp 1: MMA
 // issuer; warps 2-5: epilogue.
 // ---------------------------------------------------------------------------
 constexpr int GR_THREADS = 192;
@@ -474,6 +476,9 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
                    (q != q0 || k != 0) ? 1u : 0u);
           mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_lo + koff), IDESC, 1u);
           mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_hi + koff), IDESC, 1u);
+          // lo x lo too: without it the sum is (hi + lo)^T (hi + lo) - lo^T lo,
+          // indefinite in the null space of a short K_SJ
+          mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_lo + koff), IDESC, 1u);
         }
         mma_commit(&empty[s]);
       }

@@ -95,3 +95,35 @@ def test_fit_argument_errors(sp):
         sp.spsvm_fit(X, y, 1.0, 1e-3, 11)
     with pytest.raises(sp.SpsvmError):
         sp.spsvm_fit(X, y, 1.0, 1e-3, 5, initial_basis=[1, 1], fixed_basis=True)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_smooth_kernel_small_lambda_reaches_oracle_minimum(sp, prec):
+    """gamma = 0.25/d, lambda = 1e-5 on a nearly separable mixture: after the
+    first step the active set holds a few points and H ~ lambda K_JJ has
+    relative smallest eigenvalue ~5e-7, under the rounding level of K in
+    BF16X3 (and near that of FP32), so the computed H can be indefinite and
+    the diagonal jitter schedule must carry the fit.  beta is then
+    ill-determined but the objective is not: the float64 objective at the
+    GPU beta must reach the oracle's minimum on the same basis."""
+    n, m, lam = 3000, 256, 1e-5
+    p = synth.gaussian_mixture(n=n, d=256, budget=m, seed=41)
+    gamma = 0.25 / 256
+    J0 = np.sort(np.random.default_rng(5).choice(n, m, replace=False))
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    mdl = sp.spsvm_fit(X, y, gamma, lam, m, 1e-8, precision=prec, initial_basis=J0,
+                       fixed_basis=True, max_newton=400)
+    assert mdl.status in (0, -4), mdl.status
+    J, beta = mdl.basis_and_beta()
+    np.testing.assert_array_equal(J, J0)
+    r = O.fit(p.X, p.y, gamma, lam, m, tol=1e-8, initial_basis=J0, grow=False, max_newton=400)
+    assert r.status == "tol"
+    yd = p.y.astype(np.float64)
+    K = O.rbf_kernel(p.X, p.X[J0], gamma)
+    f_gpu = O.objective(beta, K, K[J0], yd, lam)
+    f_orc = O.objective(r.beta, K, K[J0], yd, lam)
+    levels = sorted({h["jitter"] for h in mdl.history()})
+    assert f_orc * (1 - 1e-9) <= f_gpu <= f_orc * (1 + 1e-3), (f_gpu, f_orc, levels)
+    if prec == "bf16x3":
+        assert max(levels) >= 0, levels

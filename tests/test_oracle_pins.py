@@ -313,6 +313,67 @@ def test_newton_solve_against_lu_and_breakdown():
     A = g.standard_normal((20, 20))
     H = A @ A.T + 1e-3 * np.eye(20)
     r = g.standard_normal(20)
-    np.testing.assert_allclose(O.newton_solve(H, r), scipy.linalg.solve(H, r), rtol=1e-8)
+    x, lv = O.newton_solve(H, r)
+    assert lv == -1
+    np.testing.assert_allclose(x, scipy.linalg.solve(H, r), rtol=1e-8)
     with pytest.raises(O.NotPositiveDefinite):
         O.newton_solve(-np.eye(3), np.ones(3))
+
+
+def test_newton_solve_jitter_levels_against_eigendecomposition():
+    """A symmetric matrix with one eigenvalue at -3e-8 tr(H)/|J|: levels -1
+    (none), 0, 1, 2 (shift 1e-8 tr/|J|) leave it indefinite, level 3 (1e-7)
+    is the first that factorises; the solve must equal Q diag(1/(e + shift))
+    Q^T r from the eigendecomposition.  A start level above the needed one
+    is kept (the level never goes down within a fit)."""
+    g = np.random.default_rng(11)
+    m = 20
+    Q, _ = np.linalg.qr(g.standard_normal((m, m)))
+    e = np.arange(1.0, m + 1.0)
+    e[-1] = 0.0
+    e[-1] = -3e-8 * e.sum() / m
+    H = (Q * e) @ Q.T
+    H = 0.5 * (H + H.T)
+    r = g.standard_normal(m)
+    tr = np.trace(H)
+    x, lv = O.newton_solve(H, r)
+    assert lv == 3
+    shift = 1e-7 * tr / m
+    np.testing.assert_allclose(x, Q @ ((Q.T @ r) / (e + shift)), rtol=1e-6)
+    x5, lv5 = O.newton_solve(H, r, 5)
+    assert lv5 == 5
+    np.testing.assert_allclose(x5, Q @ ((Q.T @ r) / (e + 1e-5 * tr / m)), rtol=1e-8)
+    # a level beyond the last one is a breakdown
+    with pytest.raises(O.NotPositiveDefinite):
+        O.newton_solve(H - 1e-1 * tr / m * np.eye(m), r)
+
+
+def test_newton_no_descent_raises_jitter(monkeypatch):
+    """When the line search finds no descent (t = 0) along the Newton step,
+    the jitter goes up one level and the step becomes the regularised Newton
+    step -(H + 1e-10 tr(H)/|J| I)^{-1} grad f; the level is kept."""
+    g = np.random.default_rng(17)
+    X = g.standard_normal((60, 3))
+    y = np.where(X[:, 0] + 0.3 * g.standard_normal(60) > 0, 1.0, -1.0)
+    J = [0, 5, 9, 20]
+    lam, gamma = 1e-2, 0.5
+    KnJ = O.rbf_kernel(X, X[J], gamma)
+    KJJ = KnJ[J]
+    beta0 = np.zeros(len(J))
+    real = O.line_search
+    calls = []
+
+    def first_fails(*a):
+        calls.append(1)
+        return 0.0 if len(calls) == 1 else real(*a)
+
+    monkeypatch.setattr(O, "line_search", first_fails)
+    hist, jit = [], [-1]
+    beta1, _, _ = O.newton(KnJ, KJJ, y, lam, beta0, 1e-12, 1, hist, jit)
+    assert jit == [0] and hist[0]["jitter"] == 0 and len(calls) == 2
+    S = y * (KnJ @ beta0) < 1
+    H = lam * KJJ + KnJ[S].T @ KnJ[S]
+    grad = lam * KJJ @ beta0 + KnJ[S].T @ (KnJ[S] @ beta0 - y[S])
+    d = -np.linalg.solve(H + 1e-10 * np.trace(H) / len(J) * np.eye(len(J)), grad)
+    t = real(beta0, d, KnJ @ beta0, KnJ @ d, y, KJJ, lam)
+    np.testing.assert_allclose(beta1, beta0 + t * d, rtol=1e-9)
