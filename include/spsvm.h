@@ -423,8 +423,10 @@ int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches, doubl
 
 /* Status word of the tensor-core kernels.  Every wait inside them is
  * bounded; a wait that gives up records a nonzero site code here and the
- * kernel returns without its result.  Reads and clears the word (a
- * synchronous copy from the device); returns OK, or TIMEOUT with *code set. */
+ * kernel returns without its result.  Waits for the legacy default stream,
+ * then reads and clears the word; returns OK, or TIMEOUT with *code set
+ * (site codes of the Cholesky update are offset by 100).  The fits check it
+ * themselves, in order on their own stream. */
 int spsvm_device_status(int32_t* code);
 
 const char* spsvm_strerror(int code);

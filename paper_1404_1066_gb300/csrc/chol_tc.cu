@@ -294,17 +294,10 @@ int chol_tc_trailing(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_
   return SPSVM_OK;
 }
 
-int chol_tc_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_oz_status, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  if (v != 0) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_oz_status, &zero, sizeof(int));
-  }
-  return v;
+// Device address of the status word (symbols are per translation unit).
+int oz_status_address(void** p) {
+  SPSVM_CUDA_TRY(cudaGetSymbolAddress(p, g_oz_status));
+  return SPSVM_OK;
 }
 
 }  // namespace spsvm

@@ -281,13 +281,12 @@ struct Fit {
     return K;
   }
 
+  // Waits for the fit's stream and checks the bounded waits of the
+  // tensor-core kernels (kernel block, Gram and the Cholesky update, which
+  // runs in both precisions).
   int sync() {
-    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (op.precision == SPSVM_BF16X3) {
-      int32_t code = 0;
-      SPSVM_TRY(spsvm_device_status(&code));
-    }
-    return SPSVM_OK;
+    int32_t code = 0;
+    return device_status_on(s, &code);
   }
 
   // Refresh active flags and stats from the current o into buffer `which`.

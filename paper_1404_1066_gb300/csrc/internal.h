@@ -147,4 +147,8 @@ int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m,
 size_t kernel_block_tc_scratch(int64_t m, int64_t ldh);
 bool tc_available();
 
+// Synchronises s and takes the status words of the bounded device waits
+// (stream-ordered copies; returns TIMEOUT with *code set when one gave up).
+int device_status_on(cudaStream_t s, int32_t* code);
+
 }  // namespace spsvm

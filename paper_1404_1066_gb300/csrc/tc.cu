@@ -14,6 +14,8 @@
 //     partial sums per 8192 points promoted to FP64.
 #include <cudaTypedefs.h>
 
+#include <mutex>
+
 #include "gram.h"
 #include "internal.h"
 #include "tc_ptx.h"
@@ -652,31 +654,58 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
   return SPSVM_OK;
 }
 
-int tc_take_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
+int oz_status_address(void** p);
+
+// Device addresses of the two status words, looked up once per device.
+static int status_addresses(void** tc, void** oz) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static void* addr[kMaxDev][2] = {};
+  int dev = 0;
+  SPSVM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return set_error(SPSVM_ERR_CUDA, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev][0]) {
+    void* a = nullptr;
+    void* b = nullptr;
+    SPSVM_CUDA_TRY(cudaGetSymbolAddress(&a, g_tc_status));
+    SPSVM_TRY(oz_status_address(&b));
+    addr[dev][0] = a;
+    addr[dev][1] = b;
   }
-  if (v != 0) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int));
+  *tc = addr[dev][0];
+  *oz = addr[dev][1];
+  return SPSVM_OK;
+}
+
+// Synchronises stream s and takes (reads and clears) the status words of the
+// bounded device waits, in order on s: no legacy-stream copy, so concurrent
+// fits on other streams are not serialised by it.  code: 0, or the site of
+// the first wait that gave up (Cholesky sites + 100).
+int device_status_on(cudaStream_t s, int32_t* code) {
+  void* tc = nullptr;
+  void* oz = nullptr;
+  SPSVM_TRY(status_addresses(&tc, &oz));
+  int v[2] = {0, 0};
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[0], tc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[1], oz, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (v[0] != 0 || v[1] != 0) {
+    if (v[0] != 0) SPSVM_CUDA_TRY(cudaMemsetAsync(tc, 0, sizeof(int), s));
+    if (v[1] != 0) SPSVM_CUDA_TRY(cudaMemsetAsync(oz, 0, sizeof(int), s));
+    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
   }
-  return v;
+  const int c = v[0] != 0 ? v[0] : (v[1] != 0 ? 100 + v[1] : 0);
+  if (code) *code = c;
+  if (c != 0) return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", c);
+  return SPSVM_OK;
 }
 
 }  // namespace spsvm
 
-namespace spsvm {
-int chol_tc_status();
-}
-
 extern "C" int spsvm_device_status(int32_t* code) {
-  int v = spsvm::tc_take_status();
-  const int v2 = spsvm::chol_tc_status();
-  if (v == 0 && v2 != 0) v = (v2 > 0) ? 100 + v2 : v2;
-  if (code) *code = v;
-  if (v < 0) return spsvm::set_error(SPSVM_ERR_CUDA, "device status unreadable");
-  if (v > 0) return spsvm::set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", v);
-  return SPSVM_OK;
+  if (code) *code = 0;
+  const int rc = spsvm::device_status_on(cudaStreamLegacy, code);
+  if (rc == SPSVM_ERR_CUDA && code) *code = -1;
+  return rc;
 }
