@@ -224,12 +224,18 @@ size_t spsvm_cholesky_work_bytes(int64_t m);
 int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, void* work,
                    size_t work_bytes, void* stream);
 
-/* Solves L L^T x = b in place (b overwritten by x), FP64, by blocked
- * forward and backward substitution (one launch per 64-row block, each
- * spread over the GPU).  L from spsvm_cholesky.  b: device FP64, m;
- * work: device FP64, m (overwritten). */
-int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b,
-                         double* work, void* stream);
+/* Solves L L^T x = b in place (b overwritten by x), FP64: forward then
+ * backward substitution over 64-row block rows, one launch each, one CTA
+ * per block row; each CTA applies the solution blocks published before its
+ * own (bounded flag waits; a wait that gives up leaves b incomplete and
+ * spsvm_device_status reports TIMEOUT).  L from spsvm_cholesky (it uses the
+ * diagonal-block inverses that spsvm_cholesky stores).  b: device FP64, m;
+ * work: device, 16-byte aligned, spsvm_cholesky_solve_work_bytes(m) bytes
+ * (overwritten); smaller work returns SPSVM_ERR_OOM.  The Newton direction
+ * of Section 4's reoptimisation. */
+size_t spsvm_cholesky_solve_work_bytes(int64_t m);
+int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b, void* work,
+                         size_t work_bytes, void* stream);
 
 /* Exact line search along a Newton direction (f is convex and piecewise
  * quadratic along a line; Section 4's Newton reoptimisation):
@@ -421,11 +427,13 @@ int spsvm_profile_enable(int32_t on);
 int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches, double* ms,
                        double* work);
 
-/* Status word of the tensor-core kernels.  Every wait inside them is
- * bounded; a wait that gives up records a nonzero site code here and the
- * kernel returns without its result.  Waits for the legacy default stream,
- * then reads and clears the word; returns OK, or TIMEOUT with *code set
- * (site codes of the Cholesky update are offset by 100).  The fits check it
+/* Status words of the kernels that wait on the device (tensor-core kernel
+ * block, score and Gram; the Cholesky update; the triangular solves).
+ * Every such wait is bounded; a wait that gives up records a nonzero site
+ * code and the kernel returns without its result.  Waits for the legacy
+ * default stream, then reads and clears the words; returns OK, or TIMEOUT
+ * with *code set (site codes of the Cholesky update are offset by 100,
+ * those of the triangular solves by 200).  The fits check them
  * themselves, in order on their own stream. */
 int spsvm_device_status(int32_t* code);
 

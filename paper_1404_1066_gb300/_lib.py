@@ -90,7 +90,8 @@ SIGNATURES = {
                           _P, _I64, _P, _SZ, _P]),
     "spsvm_cholesky_work_bytes": (_SZ, [_I64]),
     "spsvm_cholesky": (_I32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
-    "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P, _P]),
+    "spsvm_cholesky_solve_work_bytes": (_SZ, [_I64]),
+    "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "spsvm_line_scratch_bytes": (_SZ, [_I64]),
     "spsvm_line_search": (_I32, [_P, _P, _P, _I64, _P, _P, _I32, _D, C.POINTER(_D), _P, _P, _SZ,
                                  _P]),

@@ -225,8 +225,9 @@ def spsvm_cholesky(H: torch.Tensor, tensor_cores=True):
 
 
 def spsvm_cholesky_solve(Lf: torch.Tensor, b: torch.Tensor):
-    work = torch.empty(max(1, Lf.shape[0]), dtype=torch.float64, device=Lf.device)
-    check(_lib().spsvm_cholesky_solve(ptr(Lf), Lf.shape[0], Lf.stride(0), ptr(b), ptr(work),
+    wb = _lib().spsvm_cholesky_solve_work_bytes(Lf.shape[0])
+    work = torch.empty(max(16, wb), dtype=torch.uint8, device=Lf.device)
+    check(_lib().spsvm_cholesky_solve(ptr(Lf), Lf.shape[0], Lf.stride(0), ptr(b), ptr(work), wb,
                                       stream_ptr()),
           "spsvm_cholesky_solve")
     return b

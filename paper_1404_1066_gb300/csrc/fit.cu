@@ -153,7 +153,7 @@ struct Layout {
       off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, total;
   size_t scratch_bytes;
   size_t kbytes;
-  size_t chw_bytes;
+  size_t chw_bytes, sv_bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -195,7 +195,8 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_rhs = take(L.jcap * 8);
   L.off_tmp = take(L.jcap * 8);
   L.off_ws = take(L.jcap * 8);
-  L.off_sv = take(L.jcap * 8);
+  L.sv_bytes = spsvm_cholesky_solve_work_bytes(L.jcap);
+  L.off_sv = take(L.sv_bytes);
   L.off_J = take(L.jcap * 8);
   L.off_cand = take(kappa * 8);
   L.off_cg = take(kappa * 8);
@@ -393,14 +394,14 @@ struct Fit {
         }
         // d = -H^{-1} g, then refinement against the exactly applied H
         SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, at<double>(L.off_sv), s));
+        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, ws + L.off_sv, L.sv_bytes, s));
         SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
         for (int k = 0; k < op.refine; ++k) {
           SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
                                          at<int32_t>(L.off_pos), scratch, sb, s));
           refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
           SPSVM_LAUNCH_CHECK();
-          SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, at<double>(L.off_sv), s));
+          SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, ws + L.off_sv, L.sv_bytes, s));
           axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
           SPSVM_LAUNCH_CHECK();
           SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));

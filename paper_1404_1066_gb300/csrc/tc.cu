@@ -655,47 +655,52 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
 }
 
 int oz_status_address(void** p);
+int sv_status_address(void** p);
 
-// Device addresses of the two status words, looked up once per device.
-static int status_addresses(void** tc, void** oz) {
+// Device addresses of the status words of the bounded waits (kernel block /
+// score / Gram, Cholesky update, triangular solves), looked up once per
+// device.
+constexpr int kStatusWords = 3;
+
+static int status_addresses(void* out[kStatusWords]) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
-  static void* addr[kMaxDev][2] = {};
+  static void* addr[kMaxDev][kStatusWords] = {};
   int dev = 0;
   SPSVM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDev) return set_error(SPSVM_ERR_CUDA, "device %d out of range", dev);
   std::lock_guard<std::mutex> lk(mu);
   if (!addr[dev][0]) {
-    void* a = nullptr;
-    void* b = nullptr;
-    SPSVM_CUDA_TRY(cudaGetSymbolAddress(&a, g_tc_status));
-    SPSVM_TRY(oz_status_address(&b));
-    addr[dev][0] = a;
-    addr[dev][1] = b;
+    void* a[kStatusWords] = {};
+    SPSVM_CUDA_TRY(cudaGetSymbolAddress(&a[0], g_tc_status));
+    SPSVM_TRY(oz_status_address(&a[1]));
+    SPSVM_TRY(sv_status_address(&a[2]));
+    for (int k = 0; k < kStatusWords; ++k) addr[dev][k] = a[k];
   }
-  *tc = addr[dev][0];
-  *oz = addr[dev][1];
+  for (int k = 0; k < kStatusWords; ++k) out[k] = addr[dev][k];
   return SPSVM_OK;
 }
 
-// Synchronises stream s and takes (reads and clears) the status words of the
-// bounded device waits, in order on s: no legacy-stream copy, so concurrent
-// fits on other streams are not serialised by it.  code: 0, or the site of
-// the first wait that gave up (Cholesky sites + 100).
+// Synchronises stream s and takes (reads and clears) the status words, in
+// order on s: no legacy-stream copy, so concurrent fits on other streams are
+// not serialised by it.  code: 0, or the site of the first wait that gave up
+// (Cholesky update sites + 100, triangular-solve sites + 200).
 int device_status_on(cudaStream_t s, int32_t* code) {
-  void* tc = nullptr;
-  void* oz = nullptr;
-  SPSVM_TRY(status_addresses(&tc, &oz));
-  int v[2] = {0, 0};
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[0], tc, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[1], oz, sizeof(int), cudaMemcpyDeviceToHost, s));
+  void* a[kStatusWords];
+  SPSVM_TRY(status_addresses(a));
+  int v[kStatusWords] = {};
+  for (int k = 0; k < kStatusWords; ++k)
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[k], a[k], sizeof(int), cudaMemcpyDeviceToHost, s));
   SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (v[0] != 0 || v[1] != 0) {
-    if (v[0] != 0) SPSVM_CUDA_TRY(cudaMemsetAsync(tc, 0, sizeof(int), s));
-    if (v[1] != 0) SPSVM_CUDA_TRY(cudaMemsetAsync(oz, 0, sizeof(int), s));
-    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  int c = 0;
+  bool any = false;
+  for (int k = 0; k < kStatusWords; ++k) {
+    if (v[k] == 0) continue;
+    SPSVM_CUDA_TRY(cudaMemsetAsync(a[k], 0, sizeof(int), s));
+    if (!any) c = 100 * k + v[k];
+    any = true;
   }
-  const int c = v[0] != 0 ? v[0] : (v[1] != 0 ? 100 + v[1] : 0);
+  if (any) SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
   if (code) *code = c;
   if (c != 0) return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", c);
   return SPSVM_OK;

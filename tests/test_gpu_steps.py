@@ -12,6 +12,7 @@ Tolerances (derived from the arithmetic, stated per test):
     |err| <= 1e-5 * sum |terms|.
   * FP64 Cholesky / solves: backward-stable, 1e-10 relative.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -205,7 +206,8 @@ def test_gram(sp, prec, n, m, p):
     Hg = H.cpu().numpy()
     np.testing.assert_array_equal(Hg, Hg.T)
     bound = np.abs(KS) @ np.abs(KS).T
-    # BF16X3: dropped lo*lo term (2^-16) plus tensor-core FP32 accumulation
+    # BF16X3: the stored hi+lo kernel values carry ~2^-17 relative error,
+    # plus tensor-core FP32 accumulation
     rel = 1e-5 if prec == "fp32" else 1e-4
     assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))
 
@@ -228,6 +230,39 @@ def test_cholesky_and_solve(sp, m, tc):
     x = bt.cpu().numpy()
     xr = np.linalg.solve(H, b)
     assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr) * max(1, np.linalg.cond(H) * 1e-6)
+
+
+@pytest.mark.parametrize("m", [2, 64, 127, 4100])
+def test_solve_padded_rows_and_reused_work(sp, m):
+    """Row pitch larger than m, a ragged last block, and several solves with
+    the same factor and the same work buffer (the flags are reset per call)."""
+    g = np.random.default_rng(m + 1)
+    A = g.standard_normal((m, m + 5)) / np.sqrt(m)
+    H = A @ A.T + 0.5 * np.eye(m)
+    big = np.zeros((m, m + 37))
+    big[:, :m] = H
+    Hb = _t(big)
+    Hv = Hb[:, :m]
+    assert Hv.stride(0) == m + 37
+    assert sp.spsvm_cholesky(Hv) == 0
+    lib = sp.load()
+    wb = lib.spsvm_cholesky_solve_work_bytes(m)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    for k in range(3):
+        b = g.standard_normal(m)
+        bt = _t(b.copy())
+        rc = lib.spsvm_cholesky_solve(Hv.data_ptr(), m, m + 37, bt.data_ptr(), work.data_ptr(),
+                                      wb, None)
+        assert rc == 0
+        torch.cuda.synchronize()
+        code = ctypes.c_int32(-9)
+        assert lib.spsvm_device_status(ctypes.byref(code)) == 0 and code.value == 0
+        xr = np.linalg.solve(H, b)
+        np.testing.assert_allclose(bt.cpu().numpy(), xr, rtol=1e-10, atol=1e-12 * np.abs(xr).max())
+    # too small a work buffer is refused before any launch
+    rc = lib.spsvm_cholesky_solve(Hv.data_ptr(), m, m + 37, bt.data_ptr(), work.data_ptr(),
+                                  wb - 1, None)
+    assert rc == -2
 
 
 @pytest.mark.parametrize("tc", [False, True])
