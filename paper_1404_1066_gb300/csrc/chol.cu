@@ -2,6 +2,9 @@
 // the Newton system of Section 4's reoptimisation.  Blocked right-looking
 // factorisation with 64 x 64 blocks: diagonal block in shared memory, panel
 // triangular solve, trailing symmetric update.
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 
 namespace spsvm {
@@ -374,8 +377,64 @@ namespace spsvm {
 size_t chol_tc_work_bytes(int64_t m);
 int chol_tc_panel_update(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
                          cudaStream_t s);
-int chol_tc_trailing(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
-                     void* work, cudaStream_t s);
+int chol_tc_slice(const double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
+                  void* work, int buf, cudaStream_t s);
+int chol_tc_update(double* H, int64_t ldh, int64_t m, int64_t cbase, int64_t cend,
+                   const int32_t* info, void* work, int buf, cudaStream_t s);
+int chol_tc_carveout();
+
+namespace {
+
+// A second stream (highest priority) and two events for the look-ahead of
+// the factorisation, taken from a per-device pool for the duration of one
+// call.
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+std::mutex g_side_mu;
+std::vector<SideStream> g_side_pool;
+
+int side_acquire(SideStream* out) {
+  int dev = 0;
+  SPSVM_CUDA_TRY(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    for (size_t k = 0; k < g_side_pool.size(); ++k) {
+      if (g_side_pool[k].dev == dev) {
+        *out = g_side_pool[k];
+        g_side_pool.erase(g_side_pool.begin() + (std::ptrdiff_t)k);
+        return SPSVM_OK;
+      }
+    }
+  }
+  SideStream ss;
+  ss.dev = dev;
+  int least = 0, greatest = 0;
+  SPSVM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  SPSVM_CUDA_TRY(cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, greatest));
+  SPSVM_CUDA_TRY(cudaEventCreateWithFlags(&ss.a, cudaEventDisableTiming));
+  SPSVM_CUDA_TRY(cudaEventCreateWithFlags(&ss.b, cudaEventDisableTiming));
+  *out = ss;
+  return SPSVM_OK;
+}
+
+void side_release(const SideStream& ss) {
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  g_side_pool.push_back(ss);
+}
+
+struct SideGuard {
+  SideStream ss;
+  bool held = false;
+  ~SideGuard() {
+    if (held) side_release(ss);
+  }
+};
+
+}  // namespace
 }  // namespace spsvm
 
 extern "C" size_t spsvm_cholesky_work_bytes(int64_t m) {
@@ -389,22 +448,51 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   int64_t k0 = 0;
-  if (work && work_bytes >= chol_tc_work_bytes(m)) {
+  if (work && work_bytes >= chol_tc_work_bytes(m) && m - 64 >= 256) {
     // 64-column steps with the trailing update on the tensor cores while the
-    // trailing matrix is large; the last few hundred columns run natively
-    for (; m - (k0 + 64) >= 256; k0 += 64) {
-      potrf_diag<<<1, PT, 0, s>>>(H, ldh, m, k0, info);
+    // trailing matrix is large; the last few hundred columns run natively.
+    // Look-ahead: the panel chain and the update of the next panel's 64
+    // columns run on a high-priority stream p; the rest of the trailing
+    // update runs on s while p factors the next panel (with equal
+    // priorities the update's pending tiles would hold the SMs and the panel
+    // kernels would wait for the whole grid).
+    // the panel kernels run beside the tensor-core update, which takes the
+    // largest shared-memory carveout; an SM holds CTAs of one carveout only
+    SPSVM_TRY(chol_tc_carveout());
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(potrf_diag, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(trsm_panel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+    SideGuard side;
+    SPSVM_TRY(side_acquire(&side.ss));
+    side.held = true;
+    cudaStream_t p = side.ss.s;
+    SPSVM_CUDA_TRY(cudaEventRecord(side.ss.b, s));   // H as the caller left it
+    SPSVM_CUDA_TRY(cudaStreamWaitEvent(p, side.ss.b, 0));
+    int buf = 0;
+    for (; m - (k0 + 64) >= 256; k0 += 64, buf ^= 1) {
+      potrf_diag<<<1, PT, 0, p>>>(H, ldh, m, k0, info);
       SPSVM_LAUNCH_CHECK();
-      trsm_panel<<<(unsigned)ceil_div(m - (k0 + PB), PT / 4), PT, 0, s>>>(H, ldh, m, k0, info);
+      trsm_panel<<<(unsigned)ceil_div(m - (k0 + PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0, info);
       SPSVM_LAUNCH_CHECK();
-      SPSVM_TRY(chol_tc_panel_update(H, ldh, m, k0, info, s));
-      potrf_diag<<<1, PT, 0, s>>>(H, ldh, m, k0 + PB, info);
+      SPSVM_TRY(chol_tc_panel_update(H, ldh, m, k0, info, p));
+      potrf_diag<<<1, PT, 0, p>>>(H, ldh, m, k0 + PB, info);
       SPSVM_LAUNCH_CHECK();
-      trsm_panel<<<(unsigned)ceil_div(m - (k0 + 2 * PB), PT / 4), PT, 0, s>>>(H, ldh, m, k0 + PB,
+      trsm_panel<<<(unsigned)ceil_div(m - (k0 + 2 * PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0 + PB,
                                                                              info);
       SPSVM_LAUNCH_CHECK();
-      SPSVM_TRY(chol_tc_trailing(H, ldh, m, k0, info, work, s));
+      // slices of this panel (the buffer was last read by the update on s
+      // two panels ago, which p waited for one panel ago)
+      SPSVM_TRY(chol_tc_slice(H, ldh, m, k0, info, work, buf, p));
+      // the update on s of the previous panel touches the columns updated next
+      SPSVM_CUDA_TRY(cudaStreamWaitEvent(p, side.ss.b, 0));
+      SPSVM_TRY(chol_tc_update(H, ldh, m, k0 + 64, k0 + 128, info, work, buf, p));
+      SPSVM_CUDA_TRY(cudaEventRecord(side.ss.a, p));
+      SPSVM_CUDA_TRY(cudaStreamWaitEvent(s, side.ss.a, 0));
+      SPSVM_TRY(chol_tc_update(H, ldh, m, k0 + 128, m, info, work, buf, s));
+      SPSVM_CUDA_TRY(cudaEventRecord(side.ss.b, s));
     }
+    // s has waited for everything p did (the last record of a)
   }
   for (; k0 < m; k0 += PB) {
     potrf_diag<<<1, PT, 0, s>>>(H, ldh, m, k0, info);

@@ -85,18 +85,19 @@ __global__ void oz_slice(const double* __restrict__ H, int64_t ldh, int64_t m, i
   if (lane == 0) ex[r] = e;
 }
 
-// Lower tile (ti, tj) of the trailing matrix A22 = H[base:, base:]:
-// rows base + 128 ti .., columns base + 64 tj ...
+// Lower tile (ti, tj) of the trailing update restricted to columns
+// [cbase, cend): rows cbase + 128 ti .., columns cbase + 64 tj ...  (rows
+// below the diagonal only; the slices cover every row >= cbase).
 __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CUtensorMap map_a,
                                                       const __grid_constant__ CUtensorMap map_b,
                                                       double* __restrict__ H, int64_t ldh,
-                                                      int64_t m, int64_t base,
+                                                      int64_t m, int64_t cbase, int64_t cend,
                                                       const int32_t* __restrict__ ex,
                                                       const int32_t* __restrict__ info) {
   extern __shared__ uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ti = blockIdx.y, tj = blockIdx.x;
-  const int64_t r0 = base + ti * OZ_TM, c0 = base + tj * OZ_TN;
+  const int64_t r0 = cbase + ti * OZ_TM, c0 = cbase + tj * OZ_TN;
   // only tiles touching the lower triangle
   if (c0 > r0 + OZ_TM - 1) return;
   if (__syncthreads_or(tid == 0 && (*(volatile int*)&g_oz_status != 0 || *info != 0))) return;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(tmem_slot, 512);
-  if (tid < OZ_TN) ec[tid] = (c0 + tid < m) ? ex[c0 + tid] : 0;
+  if (tid < OZ_TN) ec[tid] = (c0 + tid < cend) ? ex[c0 + tid] : 0;
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int64_t c = c0 + cc * 32 + j;
-          if (c <= r && c < m) {
+          if (c <= r && c < cend) {
             // value = hi 2^-35 + lo 2^-63, times 2^(e_r + e_c)
             const int e = er + ec[cc * 32 + j];
             const double val = fma((double)lo[j], pow2(e - 63), (double)hi[j] * pow2(e - 35));
@@ -256,14 +257,16 @@ int make_slice_map(CUtensorMap* map, const uint16_t* base, int64_t m, uint32_t r
 
 }  // namespace
 
-size_t chol_tc_work_bytes(int64_t m) {
+// Slice planes and exponents of one panel.
+static size_t slice_buf_bytes(int64_t m) {
   return (size_t)round_up(OZ_SLICES * m * OZ_PB * 2, 256) + (size_t)round_up(m * 4, 256);
 }
 
-// One 64-column step of the factorisation starting at k0 with the trailing
-// update on the tensor cores.  The caller factors the two 32-column halves of
-// the panel (potrf / trsm); this routine provides the rank-32 update between
-// them and the trailing update after them.
+// Two slice buffers, so that the update of one panel can still read its
+// slices while the next panel is being sliced.
+size_t chol_tc_work_bytes(int64_t m) { return 2 * slice_buf_bytes(m); }
+
+// Rank-32 update of the second half of the panel at k0 with its first half.
 int chol_tc_panel_update(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
                          cudaStream_t s) {
   const int64_t rows = m - (k0 + 32);
@@ -273,23 +276,48 @@ int chol_tc_panel_update(double* H, int64_t ldh, int64_t m, int64_t k0, const in
   return SPSVM_OK;
 }
 
-int chol_tc_trailing(double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
-                     void* work, cudaStream_t s) {
+// The panel-side kernels of this file take the largest shared-memory
+// carveout, like the update, so that they can share SMs with it.
+int chol_tc_carveout() {
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_panel_update, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_slice, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+  return SPSVM_OK;
+}
+
+// Slices of the rows >= k0 + 64 of the factored panel [k0, k0 + 64) into
+// buffer `buf` (0 or 1) of the work area.
+int chol_tc_slice(const double* H, int64_t ldh, int64_t m, int64_t k0, const int32_t* info,
+                  void* work, int buf, cudaStream_t s) {
   const int64_t base = k0 + OZ_PB;
   const int64_t R = m - base;
   if (R <= 0) return SPSVM_OK;
-  uint16_t* sl = static_cast<uint16_t*>(work);
-  int32_t* ex = reinterpret_cast<int32_t*>(static_cast<char*>(work) +
-                                           round_up(OZ_SLICES * m * OZ_PB * 2, 256));
+  char* w = static_cast<char*>(work) + buf * slice_buf_bytes(m);
+  uint16_t* sl = reinterpret_cast<uint16_t*>(w);
+  int32_t* ex = reinterpret_cast<int32_t*>(w + round_up(OZ_SLICES * m * OZ_PB * 2, 256));
   oz_slice<<<(unsigned)ceil_div(R, (int64_t)8), 256, 0, s>>>(H, ldh, m, k0, base, sl, ex, info);
   SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+// Trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l] for the columns
+// cbase <= c < cend (cbase >= k0 + 64) and rows r >= c, from the slices in
+// buffer `buf`.
+int chol_tc_update(double* H, int64_t ldh, int64_t m, int64_t cbase, int64_t cend,
+                   const int32_t* info, void* work, int buf, cudaStream_t s) {
+  const int64_t R = m - cbase;
+  if (R <= 0 || cend <= cbase) return SPSVM_OK;
+  char* w = static_cast<char*>(work) + buf * slice_buf_bytes(m);
+  const uint16_t* sl = reinterpret_cast<const uint16_t*>(w);
+  const int32_t* ex = reinterpret_cast<const int32_t*>(w + round_up(OZ_SLICES * m * OZ_PB * 2, 256));
   CUtensorMap ma, mb;
   SPSVM_TRY(make_slice_map(&ma, sl, m, OZ_TM));
   SPSVM_TRY(make_slice_map(&mb, sl, m, OZ_TN));
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       OZ_SMEM));
-  dim3 grid((unsigned)ceil_div(R, (int64_t)OZ_TN), (unsigned)ceil_div(R, (int64_t)OZ_TM));
-  oz_trailing<<<grid, 128, OZ_SMEM, s>>>(ma, mb, H, ldh, m, base, ex, info);
+  dim3 grid((unsigned)ceil_div(cend - cbase, (int64_t)OZ_TN), (unsigned)ceil_div(R, (int64_t)OZ_TM));
+  oz_trailing<<<grid, 128, OZ_SMEM, s>>>(ma, mb, H, ldh, m, cbase, cend, ex, info);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
