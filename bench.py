@@ -12,6 +12,8 @@ explicit L2 flush is needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU
 oracle on a bounded sample of the same workload on the host cores.
+--micro cholesky [--sizes m1,m2,...] times the FP64 factorisation and solve
+of the Newton system alone (the profiles' capture command).
 """
 from __future__ import annotations
 
@@ -202,6 +204,49 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
                 fit_p99_ms=pct(lats["fit"], 99), predict_p50_ms=pct(lats["predict"], 50),
                 predict_p99_ms=pct(lats["predict"], 99), hbm_peak_gb=stats["hbm_peak"] / 2 ** 30,
                 workers=workers, budget_gb=budget_gb, arrival_rate=20.0)
+
+
+def run_micro(args):
+    """FP64 Cholesky factorisation and solve of the Newton system alone, at
+    the given sizes: random SPD matrices A A^T / m + I / 2 (seeded), one
+    JSON line with event-timed milliseconds per factorisation and per solve."""
+    import torch
+    import paper_1404_1066_gb300 as sp
+    lib = sp.load()
+    out = {}
+    for m in [int(v) for v in args.sizes.split(",")]:
+        g = np.random.default_rng(m)
+        A = g.standard_normal((m, m + 5)) / np.sqrt(m)
+        H0 = torch.from_numpy(A @ A.T + 0.5 * np.eye(m)).cuda()
+        b0 = torch.from_numpy(g.standard_normal(m)).cuda()
+        Hs = [H0.clone() for _ in range(args.warmup + args.steps)]
+        for k in range(args.warmup):
+            assert sp.spsvm_cholesky(Hs[k]) == 0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(args.warmup, args.warmup + args.steps):
+            sp.spsvm_cholesky(Hs[k])
+        e1.record()
+        torch.cuda.synchronize()
+        fac = e0.elapsed_time(e1) / max(1, args.steps)
+        L = Hs[-1]
+        b = b0.clone()
+        for _ in range(args.warmup):
+            sp.spsvm_cholesky_solve(L, b)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            sp.spsvm_cholesky_solve(L, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out[str(m)] = dict(factor_ms=fac, solve_ms=e0.elapsed_time(e1) / max(1, args.steps),
+                           fp64_equiv_tflops=m ** 3 / 3.0 / (fac * 1e-3) / 1e12)
+        del Hs, L
+    print(json.dumps(dict(micro="cholesky", steps=args.steps, warmup=args.warmup, sizes=out)),
+          flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -423,11 +468,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--micro", choices=["cholesky"], default=None,
+                    help="time one hot-path step alone instead of the whole fit")
+    ap.add_argument("--sizes", default="512,1024,2048,4096")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.micro:
+        return run_micro(args)
     return run_ours(args)
 
 
