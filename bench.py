@@ -241,8 +241,21 @@ def run_micro(args):
             sp.spsvm_cholesky_solve(L, b)
         e1.record()
         torch.cuda.synchronize()
-        out[str(m)] = dict(factor_ms=fac, solve_ms=e0.elapsed_time(e1) / max(1, args.steps),
-                           fp64_equiv_tflops=m ** 3 / 3.0 / (fac * 1e-3) / 1e12)
+        sol = e0.elapsed_time(e1) / max(1, args.steps)
+        # mixed: FP32 factor + FP64 refinement (H kept), one solve included
+        Hm = H0.clone()
+        for _ in range(args.warmup):
+            sp.spsvm_solve_mixed(Hm, b0)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            info, st, _, iters, be = sp.spsvm_solve_mixed(Hm, b0)
+        e1.record()
+        torch.cuda.synchronize()
+        out[str(m)] = dict(factor_ms=fac, solve_ms=sol,
+                           fp64_equiv_tflops=m ** 3 / 3.0 / (fac * 1e-3) / 1e12,
+                           mixed_factor_and_solve_ms=e0.elapsed_time(e1) / max(1, args.steps),
+                           mixed_iters=iters, mixed_backward_error=be, mixed_status=st)
         del Hs, L
     print(json.dumps(dict(micro="cholesky", steps=args.steps, warmup=args.warmup, sizes=out)),
           flush=True)

@@ -59,6 +59,10 @@ extern "C" {
 #define SPSVM_FP32    0
 #define SPSVM_BF16X3  1
 
+/* Newton-system solvers (spsvm_options.newton_solver). */
+#define SPSVM_SOLVE_MIXED 0
+#define SPSVM_SOLVE_FP64  1
+
 /* ---- stored kernel matrix ---------------------------------------------- */
 /* K_nJ stored basis-major: row j (one basis vector) holds k(x_i, x_{J_j})
  * for i = 0..n-1 contiguously.  FP32: element (j, i) at
@@ -237,6 +241,27 @@ size_t spsvm_cholesky_solve_work_bytes(int64_t m);
 int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b, void* work,
                          size_t work_bytes, void* stream);
 
+/* Mixed-precision solve of the Newton system (H + shift I) x = b of
+ * Section 4's reoptimisation: an FP32 Cholesky factor of H + shift I, then
+ * iterative refinement with FP64 residuals until the normwise backward error
+ * ||r||_inf / (||H + shift I||_inf ||x||_inf + ||b||_inf) is at most tol.
+ * H: device FP64, m x m, full and symmetric, row pitch ldh, read only (not
+ * overwritten, unlike spsvm_cholesky).  shift >= 0.
+ * spsvm_cholesky_mixed converts and factors into work (device, 256-byte
+ * aligned, spsvm_mixed_work_bytes(m) bytes); info: device int32, 0 on success,
+ * else k+1 for the first non-positive FP32 pivot k.  spsvm_solve_mixed then
+ * solves for b (device FP64, m) into x (device FP64, m) with the factor in
+ * work; it synchronises the stream once per refinement step and returns OK,
+ * or SPSVM_ERR_NO_CONVERGE when the residual stops shrinking (by half per
+ * step) or max_iter steps do not reach tol (x then holds the last iterate).
+ * iters, backward_error: host, may be NULL. */
+size_t spsvm_mixed_work_bytes(int64_t m);
+int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, double shift, int32_t* info,
+                         void* work, size_t work_bytes, void* stream);
+int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift, const double* b,
+                      double* x, int32_t max_iter, double tol, int32_t* iters,
+                      double* backward_error, void* work, size_t work_bytes, void* stream);
+
 /* Exact line search along a Newton direction (f is convex and piecewise
  * quadratic along a line; Section 4's Newton reoptimisation):
  *   phi'(t) = a0 + a1 t - sum_i v_i max(0, m_i - t v_i),
@@ -288,6 +313,9 @@ typedef struct spsvm_options {
   int32_t  refine;         /* iterative-refinement sweeps per Newton step (0 -> 1, <0 -> none) */
   int32_t  record;         /* keep candidates / chosen per round for replay checks */
   void*    stream;         /* cudaStream_t for all work (NULL = default stream) */
+  int32_t  newton_solver;  /* SPSVM_SOLVE_MIXED (0): FP32 factor + FP64 refinement to FP64
+                              backward error, FP64 factorisation when that fails;
+                              SPSVM_SOLVE_FP64: FP64 factorisation always */
 } spsvm_options;
 
 /* Per-Newton-step record (kept for every fit). */

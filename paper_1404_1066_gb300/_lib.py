@@ -23,6 +23,8 @@ SPSVM_ERR_BUSY = -7
 
 SPSVM_FP32 = 0
 SPSVM_BF16X3 = 1
+SPSVM_SOLVE_MIXED = 0
+SPSVM_SOLVE_FP64 = 1
 
 PRECISIONS = {"fp32": SPSVM_FP32, "bf16x3": SPSVM_BF16X3}
 
@@ -45,7 +47,8 @@ class spsvm_options(C.Structure):
                 ("growth_tol", C.c_double), ("rel_tol", C.c_double),
                 ("seed", C.c_uint64), ("initial_basis", C.POINTER(C.c_int64)),
                 ("n_initial", C.c_int32), ("fixed_basis", C.c_int32),
-                ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p)]
+                ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p),
+                ("newton_solver", C.c_int32)]
 
 
 class spsvm_problem(C.Structure):
@@ -91,6 +94,10 @@ SIGNATURES = {
     "spsvm_cholesky_work_bytes": (_SZ, [_I64]),
     "spsvm_cholesky": (_I32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "spsvm_cholesky_solve_work_bytes": (_SZ, [_I64]),
+    "spsvm_mixed_work_bytes": (_SZ, [_I64]),
+    "spsvm_cholesky_mixed": (_I32, [_P, _I64, _I64, C.c_double, _P, _P, _SZ, _P]),
+    "spsvm_solve_mixed": (_I32, [_P, _I64, _I64, C.c_double, _P, _P, _I32, C.c_double,
+                                 C.POINTER(_I32), C.POINTER(C.c_double), _P, _SZ, _P]),
     "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "spsvm_line_scratch_bytes": (_SZ, [_I64]),
     "spsvm_line_search": (_I32, [_P, _P, _P, _I64, _P, _P, _I32, _D, C.POINTER(_D), _P, _P, _SZ,

@@ -224,6 +224,30 @@ def spsvm_cholesky(H: torch.Tensor, tensor_cores=True):
     return int(info.item())
 
 
+def spsvm_solve_mixed(H: torch.Tensor, b: torch.Tensor, shift=0.0, max_iter=30, tol=1e-13):
+    """Solves (H + shift I) x = b (H FP64, full symmetric, not overwritten) with
+    an FP32 factor and FP64 refinement.  Returns (info, status, x, iters,
+    backward_error): info != 0 when the FP32 factorisation broke down."""
+    m = H.shape[0]
+    wb = _lib().spsvm_mixed_work_bytes(m)
+    work = torch.empty(max(256, wb), dtype=torch.uint8, device=H.device)
+    info = torch.zeros(1, dtype=torch.int32, device=H.device)
+    check(_lib().spsvm_cholesky_mixed(ptr(H), m, H.stride(0), float(shift), ptr(info), ptr(work),
+                                      wb, stream_ptr()), "spsvm_cholesky_mixed")
+    inf = int(info.item())
+    x = torch.zeros(m, dtype=torch.float64, device=H.device)
+    if inf != 0:
+        return inf, None, x, 0, None
+    it = C.c_int32()
+    be = C.c_double()
+    st = _lib().spsvm_solve_mixed(ptr(H), m, H.stride(0), float(shift), ptr(b), ptr(x),
+                                  int(max_iter), float(tol), C.byref(it), C.byref(be), ptr(work),
+                                  wb, stream_ptr())
+    if st not in (L.SPSVM_OK, L.SPSVM_ERR_NO_CONVERGE):
+        check(st, "spsvm_solve_mixed")
+    return 0, st, x, it.value, be.value
+
+
 def spsvm_cholesky_solve(Lf: torch.Tensor, b: torch.Tensor):
     wb = _lib().spsvm_cholesky_solve_work_bytes(Lf.shape[0])
     work = torch.empty(max(16, wb), dtype=torch.uint8, device=Lf.device)
@@ -270,7 +294,7 @@ def spsvm_draw_candidates(n, J, kappa, seed, round_index):
 # ---------------------------------------------------------------- fit/predict
 def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp32",
                  growth_tol=0.0, rel_tol=0.0, seed=0, initial_basis=None, fixed_basis=False,
-                 refine=0, record=False, stream=None):
+                 refine=0, record=False, stream=None, newton_solver="mixed"):
     o = spsvm_options()
     o.candidates = int(candidates)
     o.add_per_round = int(add_per_round)
@@ -288,6 +312,7 @@ def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp3
     o.refine = int(refine)
     o.record = int(bool(record))
     o.stream = stream_ptr(stream) if torch.cuda.is_available() else None
+    o.newton_solver = {"mixed": L.SPSVM_SOLVE_MIXED, "fp64": L.SPSVM_SOLVE_FP64}[newton_solver]
     return o, keep
 
 

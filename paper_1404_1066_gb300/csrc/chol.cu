@@ -25,15 +25,17 @@ constexpr int PB = 32;   // panel width of the factorisation
 // 1 / sqrt(d) in FP64 without the long-latency FP64 sqrt and division: the
 // FP32 estimate refined by two Newton steps y <- y (3 - d y^2) / 2, each of
 // which doubles the number of correct bits (about 23 -> 46 -> full FP64).
-__device__ __forceinline__ double rsqrt_fp64(double d) {
+__device__ __forceinline__ double rsqrt_t(double d) {
   double y = (double)rsqrtf((float)d);
   y = y * fma(-0.5 * d, y * y, 1.5);
   y = y * fma(-0.5 * d, y * y, 1.5);
   return y;
 }
 
-__device__ __forceinline__ double shfl_d(double v, int src) {
-  return __shfl_sync(0xffffffffu, v, src);
+// FP32: the hardware estimate and one Newton step.
+__device__ __forceinline__ float rsqrt_t(float d) {
+  const float y = rsqrtf(d);
+  return y * fmaf(-0.5f * d, y * y, 1.5f);
 }
 
 // GB300 issues FP64 at about half an operation per clock per SM
@@ -43,50 +45,62 @@ __device__ __forceinline__ double shfl_d(double v, int src) {
 // 4, so that a triangular loop wastes at most one predicated slot per step.
 constexpr int PT = 128;   // threads of the panel kernels
 
-// Factors the PB x PB diagonal block at k0 in place, column by column in
-// shared memory: pivot, column scaling, rank-1 update of the trailing lower
-// triangle.  Thread t updates row t / 4, columns t % 4 + 4 i.
-__global__ void __launch_bounds__(PT) potrf_diag(double* __restrict__ H, int64_t ldh, int64_t m,
+// Factors the PB x PB diagonal block at k0 in place, left-looking: for
+// column j, every row r >= j first subtracts sum_{k<j} L[r][k] L[j][k] (four
+// threads per row, each over k = q mod 4, two accumulators, reduced by
+// shuffle), then warp 0 alone takes the pivot: L_jj = sqrt(d), L[r][j] /= L_jj.
+// Only one warp spends FP64 issue slots on the reciprocal square root, and
+// no rank-1 update sits between two pivots.
+template <typename T>
+__global__ void __launch_bounds__(PT) potrf_diag(T* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, int32_t* __restrict__ info) {
-  __shared__ double A[PB][PB + 1];
-  __shared__ double piv[PB];
+  __shared__ T A[PB][PB + 1];
+  __shared__ int fail_s;
   if (*info != 0) return;
   const int nb = (int)min64(PB, m - k0);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int e = t; e < PB * PB; e += PT) {
     const int r = e / PB, c = e % PB;
     A[r][c] = (r < nb && c <= r) ? H[(k0 + r) * ldh + k0 + c] : (r == c ? 1.0 : 0.0);
   }
+  if (t == 0) fail_s = 0;
   __syncthreads();
   const int r = t >> 2, q = t & 3;
-  int fail = 0;
   for (int j = 0; j < nb; ++j) {
-    const double d = A[j][j];   // updated by the previous columns; not written in this one
-    if (!(d > 0.0) || !(d < 1e300)) {
-      fail = j + 1;             // the same value in every thread
-      break;
+    const bool act = r >= j && r < nb;
+    T s0 = 0.0, s1 = 0.0;
+    if (act) {
+      for (int k = q; k < j; k += 8) {
+        s0 = fma(A[r][k], A[j][k], s0);
+        if (k + 4 < j) s1 = fma(A[r][k + 4], A[j][k + 4], s1);
+      }
     }
-    const double y = rsqrt_fp64(d);
-    if (t == 0) piv[j] = d * y;               // L_jj = sqrt(d)
-    if (t > j && t < nb) A[t][j] *= y;         // L[t][j]
+    T sum = s0 + s1;
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    if (act && q == 0) A[r][j] -= sum;
     __syncthreads();
-    if (r > j) {
-      const double lr = A[r][j];
-#pragma unroll
-      for (int i = 0; i < PB / 4; ++i) {
-        const int c = q + 4 * i;
-        if (c > j && c <= r) A[r][c] = fma(-lr, A[c][j], A[r][c]);
+    if (warp == 0) {
+      const T d = A[j][j];
+      if (!(d > 0.0) || !(d < 1e300)) {
+        if (lane == 0) fail_s = j + 1;
+      } else {
+        const T y = rsqrt_t(d);
+        if (lane > j && lane < nb) A[lane][j] *= y;   // L[lane][j]
+        __syncwarp();
+        if (lane == 0) A[j][j] = d * y;               // L_jj = sqrt(d)
       }
     }
     __syncthreads();
+    if (fail_s) break;   // the same value in every thread
   }
-  if (fail) {
-    if (t == 0) *info = (int32_t)(k0 + fail);
+  if (fail_s) {
+    if (t == 0) *info = (int32_t)(k0 + fail_s);
     return;
   }
   for (int e = t; e < PB * PB; e += PT) {
     const int rr = e / PB, cc = e % PB;
-    if (rr < nb && cc <= rr) H[(k0 + rr) * ldh + k0 + cc] = (rr == cc) ? piv[rr] : A[rr][cc];
+    if (rr < nb && cc <= rr) H[(k0 + rr) * ldh + k0 + cc] = A[rr][cc];
   }
 }
 
@@ -94,30 +108,31 @@ __global__ void __launch_bounds__(PT) potrf_diag(double* __restrict__ H, int64_t
 // column-oriented substitution, x_j = b_j / L_jj then b_l -= x_j L_lj for
 // l > j.  Four threads per row (32 rows per CTA); thread q of a row holds
 // columns q + 4 i and x_j travels by shuffle from the thread that owns it.
-__global__ void __launch_bounds__(PT) trsm_panel(double* __restrict__ H, int64_t ldh, int64_t m,
+template <typename T>
+__global__ void __launch_bounds__(PT) trsm_panel(T* __restrict__ H, int64_t ldh, int64_t m,
                                                  int64_t k0, const int32_t* __restrict__ info) {
-  __shared__ double L[PB][PB + 1];
-  __shared__ double rd[PB];
+  __shared__ T L[PB][PB + 1];
+  __shared__ T rd[PB];
   if (*info != 0) return;
   for (int e = threadIdx.x; e < PB * PB; e += PT) {
     const int r = e / PB, c = e % PB;
     L[r][c] = (c <= r) ? H[(k0 + r) * ldh + k0 + c] : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x < PB) rd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
+  if (threadIdx.x < PB) rd[threadIdx.x] = T(1) / L[threadIdx.x][threadIdx.x];
   __syncthreads();
   const int t = threadIdx.x, lane = t & 31, q = t & 3;
   const int64_t r = k0 + PB + (int64_t)blockIdx.x * (PT / 4) + (t >> 2);
   const bool ok = r < m;
-  double* row = H + (ok ? r : k0) * ldh + k0;
-  double x[PB / 4];
+  T* row = H + (ok ? r : k0) * ldh + k0;
+  T x[PB / 4];
 #pragma unroll
   for (int i = 0; i < PB / 4; ++i) x[i] = ok ? row[q + 4 * i] : 0.0;
 #pragma unroll
   for (int j = 0; j < PB; ++j) {
     const int owner = j & 3, ji = j >> 2;
     if (q == owner) x[ji] *= rd[j];
-    const double xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
+    const T xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
 #pragma unroll
     for (int i = ji; i < PB / 4; ++i)
       if (q + 4 * i > j) x[i] = fma(-xj, L[q + 4 * i][j], x[i]);
@@ -131,14 +146,15 @@ __global__ void __launch_bounds__(PT) trsm_panel(double* __restrict__ H, int64_t
 // Trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l] for r >= c >= k0 + PB
 // over 32 x 32 lower tiles (small tiles spread the FP64 work over more SMs);
 // thread t: row t / 4 of the tile, columns t % 4 + 4 i.
-__global__ void __launch_bounds__(PT) syrk_trailing(double* __restrict__ H, int64_t ldh,
+template <typename T>
+__global__ void __launch_bounds__(PT) syrk_trailing(T* __restrict__ H, int64_t ldh,
                                                     int64_t m, int64_t k0,
                                                     const int32_t* __restrict__ info) {
-  __shared__ double Ar[PB][PB + 1];   // Ar[rr][l] = L[r0 + rr][k0 + l]
-  __shared__ double Ac[PB][PB + 1];   // Ac[l][cc] = L[c0 + cc][k0 + l]
+  __shared__ T Ar[PB][PB + 1];   // Ar[rr][l] = L[r0 + rr][k0 + l]
+  __shared__ T Ac[PB][PB + 1];   // Ac[l][cc] = L[c0 + cc][k0 + l]
   if (*info != 0) return;
   const int64_t base = k0 + PB;
-  const int64_t T = ceil_div(m - base, (int64_t)PB);
+  const int64_t ntile = ceil_div(m - base, (int64_t)PB);
   // lower tile (ti >= tj) from the linear block index
   int64_t tt = blockIdx.x, ti = 0;
   while (tt > ti) {
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(PT) syrk_trailing(double* __restrict__ H, int6
     ++ti;
   }
   const int64_t tj = tt;
-  if (ti >= T) return;
+  if (ti >= ntile) return;
   const int64_t r0 = base + ti * PB, c0 = base + tj * PB;
   for (int e = threadIdx.x; e < PB * PB; e += PT) {
     const int rr = e / PB, ll = e % PB;
@@ -156,12 +172,12 @@ __global__ void __launch_bounds__(PT) syrk_trailing(double* __restrict__ H, int6
   }
   __syncthreads();
   const int rr = threadIdx.x >> 2, q = threadIdx.x & 3;
-  double acc[PB / 4];
+  T acc[PB / 4];
 #pragma unroll
   for (int i = 0; i < PB / 4; ++i) acc[i] = 0.0;
 #pragma unroll 8
   for (int l = 0; l < PB; ++l) {
-    const double a = Ar[rr][l];
+    const T a = Ar[rr][l];
 #pragma unroll
     for (int i = 0; i < PB / 4; ++i) acc[i] = fma(a, Ac[l][q + 4 * i], acc[i]);
   }
@@ -178,28 +194,88 @@ __global__ void __launch_bounds__(PT) syrk_trailing(double* __restrict__ H, int6
 // Inverse of each lower-triangular diagonal block L_kk, stored transposed in
 // the (otherwise unused) strict upper triangle of the block: element (i, j),
 // i > j, of inv(L_kk) at H[(k0 + j) * ldh + k0 + i].  The diagonal of the
-// inverse is 1 / L_ii and is not stored.
-__global__ void __launch_bounds__(64) diag_inverse(double* __restrict__ H, int64_t ldh, int64_t m) {
-  __shared__ double Ls[NB][NB + 1];
+// inverse is 1 / L_ii and is not stored.  With L_kk = [[A, 0], [B, C]] in
+// 32 x 32 blocks, inv = [[inv A, 0], [-inv C B inv A, inv C]]: the two
+// half inverses are formed at once (128 threads each, row by row, four
+// threads per column with a shuffle reduction), then the off-diagonal block
+// by two 32 x 32 products (256 threads, four outputs each).
+constexpr int DI_T = 256;
+template <typename T>
+__global__ void __launch_bounds__(DI_T) diag_inverse(T* __restrict__ H, int64_t ldh, int64_t m) {
+  __shared__ T Ls[NB][NB + 1];   // lower: L; strict upper of each half: that half's inverse
+  __shared__ T Xs[NB / 2][NB / 2 + 1];   // inv C B inv A (lower-left block), then negated
+  __shared__ T rd[NB];
   const int64_t k0 = (int64_t)blockIdx.x * NB;
   const int nb = (int)min64(NB, m - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+  const int t = threadIdx.x;
+  for (int e = t; e < NB * NB; e += DI_T) {
     const int r = e / NB, c = e % NB;
     Ls[r][c] = (r < nb && c <= r) ? H[(k0 + r) * ldh + k0 + c] : (r == c ? 1.0 : 0.0);
   }
   __syncthreads();
-  // thread j solves L x = e_j (column j of the inverse) for rows i > j and
-  // keeps x_i in its own row of the upper triangle, Ls[j][i]; it reads only
-  // the lower triangle (Ls[i][l], l < i) and its own row.
-  const int j = threadIdx.x;
-  if (j < nb) {
-    const double xj = 1.0 / Ls[j][j];
-    for (int i = j + 1; i < nb; ++i) {
-      double acc = Ls[i][j] * xj;
-      for (int l = j + 1; l < i; ++l) acc += Ls[i][l] * Ls[j][l];
-      Ls[j][i] = -acc / Ls[i][i];
+  if (t < NB) rd[t] = T(1) / Ls[t][t];
+  __syncthreads();
+  // half h (0: rows/cols 0-31, 1: 32-63); X = inv(L_hh) kept as X[i][c] at Ls[o + c][o + i]
+  // (strict upper of the half), i > c; X[c][c] = rd.
+  {
+    const int h = t >> 7, o = 32 * h;
+    const int c = (t & 127) >> 2, q = t & 3;
+    for (int i = 1; i < 32; ++i) {
+      // X[i][c] = -(sum_{k=c}^{i-1} L[i][k] X[k][c]) / L[i][i], c < i
+      T s = 0.0;
+      if (c < i) {
+        for (int k = c + q; k < i; k += 4) {
+          const T xkc = (k == c) ? rd[o + c] : Ls[o + c][o + k];
+          s = fma(Ls[o + i][o + k], xkc, s);
+        }
+      }
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (c < i && q == 0) Ls[o + c][o + i] = -s * rd[o + i];
+      __syncthreads();
     }
-    for (int i = j + 1; i < nb; ++i) H[(k0 + j) * ldh + k0 + i] = Ls[j][i];
+  }
+  // T = B inv A (B = L[32..63][0..31]), then X21 = -inv C T; thread: row rr, columns cc + 8 v
+  {
+    const int rr = t >> 3, c0 = t & 7;
+    T acc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int cc = c0 + 8 * v;
+      T sum = 0.0;
+      for (int k = cc; k < 32; ++k) {
+        const T aik = (k == cc) ? rd[cc] : Ls[cc][k];   // inv A [k][cc]
+        sum = fma(Ls[32 + rr][k], aik, sum);
+      }
+      acc[v] = sum;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Xs[rr][c0 + 8 * v] = acc[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int cc = c0 + 8 * v;
+      T sum = 0.0;
+      for (int k = 0; k <= rr; ++k) {
+        const T cik = (k == rr) ? rd[32 + rr] : Ls[32 + k][32 + rr];   // inv C [rr][k]
+        sum = fma(cik, Xs[k][cc], sum);
+      }
+      acc[v] = -sum;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Xs[rr][c0 + 8 * v] = acc[v];
+  }
+  __syncthreads();
+  // store: element (i, j), i > j, of the inverse at H[(k0 + j) * ldh + k0 + i]
+  for (int e = t; e < NB * NB; e += DI_T) {
+    const int j = e / NB, i = e % NB;
+    if (i <= j || i >= nb) continue;
+    T v;
+    if (i < 32) v = Ls[j][i];                       // inv A
+    else if (j >= 32) v = Ls[j][i];                 // inv C (its strict upper, same layout)
+    else v = Xs[i - 32][j];                         // lower-left block
+    H[(k0 + j) * ldh + k0 + i] = v;
   }
 }
 
@@ -240,13 +316,14 @@ __device__ unsigned wait_flag(const unsigned* f, int code) {
 // Inverse of the 64 x 64 diagonal block at r0 (lower), Li[i][j], from the
 // transposed copy diag_inverse leaves in the upper triangle; zero-padded
 // past nb.
-__device__ __forceinline__ void load_diag_inverse(const double* __restrict__ L, int64_t ldh,
-                                                  int64_t r0, int nb, double (*Li)[NB + 1]) {
+template <typename T>
+__device__ __forceinline__ void load_diag_inverse(const T* __restrict__ L, int64_t ldh,
+                                                  int64_t r0, int nb, T (*Li)[NB + 1]) {
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int j = e / NB, i = e % NB;   // stored at (row r0 + j, column r0 + i)
-    double v = 0.0;
+    T v = 0.0;
     if (i < nb && j < nb) {
-      if (i == j) v = 1.0 / L[(r0 + i) * ldh + r0 + i];
+      if (i == j) v = T(1) / L[(r0 + i) * ldh + r0 + i];
       else if (j < i) v = L[(r0 + j) * ldh + r0 + i];
     }
     Li[i][j] = v;
@@ -255,12 +332,13 @@ __device__ __forceinline__ void load_diag_inverse(const double* __restrict__ L, 
 
 // z = L^{-1} b.  Thread t: row t / 4 of the block row, columns 16 (t % 4) ..
 // + 15 of each 64-column block.
+template <typename T>
 __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
-    const double* __restrict__ L, int64_t ldh, int64_t m, const double* __restrict__ b,
-    double* __restrict__ z, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double xs[2][NB];
-  __shared__ double v[NB];
+    const T* __restrict__ L, int64_t ldh, int64_t m, const T* __restrict__ b,
+    T* __restrict__ z, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
+  __shared__ T Li[NB][NB + 1];
+  __shared__ T xs[2][NB];
+  __shared__ T v[NB];
   __shared__ unsigned k_s, state_s;
   const int t = threadIdx.x;
   if (t == 0) k_s = atomicAdd(ticket, 1u);
@@ -271,11 +349,11 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
   load_diag_inverse(L, ldh, r0, nb, Li);
   const int r = t >> 2, q = t & 3;
   const bool row_ok = r < nb;
-  const double* __restrict__ Lrow = L + (r0 + (row_ok ? r : 0)) * ldh + 16 * q;
-  double acc = 0.0;
+  const T* __restrict__ Lrow = L + (r0 + (row_ok ? r : 0)) * ldh + 16 * q;
+  T acc = 0.0;
   bool ok = true;
   for (int64_t j = 0; j < k; ++j) {
-    double a[16];
+    T a[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) a[c] = row_ok ? __ldg(Lrow + j * NB + c) : 0.0;
     if (t == 0) state_s = wait_flag(&flags[j], 21);
@@ -284,7 +362,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
       ok = false;
       break;
     }
-    double* xb = xs[j & 1];
+    T* xb = xs[j & 1];
     if (t < NB) xb[t] = __ldcg(z + j * NB + t);   // blocks before the last are full
     __syncthreads();
 #pragma unroll
@@ -298,7 +376,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   if (q == 0) v[r] = row_ok ? b[r0 + r] - acc : 0.0;
   __syncthreads();
-  double sres = 0.0;
+  T sres = 0.0;
 #pragma unroll
   for (int c = 0; c < 16; ++c) sres = fma(Li[r][16 * q + c], v[16 * q + c], sres);
   sres += __shfl_xor_sync(0xffffffffu, sres, 1);
@@ -311,13 +389,14 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
 
 // x = L^{-T} z.  Block rows from the last; thread t: column t % 64 of the
 // block, rows 16 (t / 64) .. + 15 of each later 64-row block.
+template <typename T>
 __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
-    const double* __restrict__ L, int64_t ldh, int64_t m, const double* __restrict__ z,
-    double* __restrict__ x, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double xs[2][NB];
-  __shared__ double part[4][NB];
-  __shared__ double v[NB];
+    const T* __restrict__ L, int64_t ldh, int64_t m, const T* __restrict__ z,
+    T* __restrict__ x, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
+  __shared__ T Li[NB][NB + 1];
+  __shared__ T xs[2][NB];
+  __shared__ T part[4][NB];
+  __shared__ T v[NB];
   __shared__ unsigned k_s, state_s;
   const int t = threadIdx.x;
   const int64_t B = ceil_div(m, (int64_t)NB);
@@ -328,10 +407,10 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
   const int nb = (int)min64(NB, m - r0);
   load_diag_inverse(L, ldh, r0, nb, Li);
   const int c = t & (NB - 1), g = t >> 6;
-  double acc = 0.0;
+  T acc = 0.0;
   bool ok = true;
   for (int64_t j = B - 1; j > k; --j) {
-    double a[16];
+    T a[16];
     const int64_t rb = j * NB + 16 * g;
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr)
@@ -342,7 +421,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
       ok = false;
       break;
     }
-    double* xb = xs[j & 1];
+    T* xb = xs[j & 1];
     if (t < NB) xb[t] = (j * NB + t < m) ? __ldcg(x + j * NB + t) : 0.0;
     __syncthreads();
 #pragma unroll
@@ -357,7 +436,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
   if (t < NB) v[t] = (t < nb) ? z[r0 + t] - (part[0][t] + part[1][t] + part[2][t] + part[3][t]) : 0.0;
   __syncthreads();
   // x_k = Li^T v, the 64 rows of the sum split over the four thread groups
-  double sres = 0.0;
+  T sres = 0.0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) sres = fma(Li[16 * g + i][c], v[16 * g + i], sres);
   part[g][c] = sres;
@@ -366,6 +445,144 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
   __threadfence();
   __syncthreads();
   if (t == 0) st_release_u32(&flags[k], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP32 factor of H + shift I, FP64 iterative refinement.
+// ---------------------------------------------------------------------------
+constexpr int MX_T = 256;
+
+// L (FP32, lower triangle) = H + shift I; per-block maximum of the FP64 row
+// sums |H_i.| + |shift| (the infinity norm, order-independent).
+__global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ H, int64_t ldh,
+                                                     int64_t m, double shift, float* __restrict__ L,
+                                                     int64_t ldl, double* __restrict__ rowmax) {
+  __shared__ double wmax[MX_T / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * (MX_T / 32) + w;
+  double rs = 0.0;
+  if (r < m) {
+    for (int64_t c = lane; c < m; c += 32) {
+      const double v = H[r * ldh + c] + (c == r ? shift : 0.0);
+      rs += fabs(v);
+      if (c <= r) L[r * ldl + c] = (float)v;
+    }
+  }
+  rs = warp_sum(rs);
+  if (lane == 0) wmax[w] = rs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wmax[k]);
+    rowmax[blockIdx.x] = mx;
+  }
+}
+
+// z = (float) r, and the block maxima of |r| (the right-hand side's norm on
+// the first call).
+__global__ void __launch_bounds__(MX_T) to_f32_vec(const double* __restrict__ r, int64_t m,
+                                                   float* __restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
+  if (i < m) z[i] = (float)r[i];
+}
+
+// x += (double) z; block maxima of |x|.
+__global__ void __launch_bounds__(MX_T) add_f32(double* __restrict__ x, const float* __restrict__ z,
+                                                int64_t m, double* __restrict__ xmax) {
+  __shared__ double wm[MX_T / 32];
+  const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
+  double a = 0.0;
+  if (i < m) {
+    const double v = x[i] + (double)z[i];
+    x[i] = v;
+    a = fabs(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wm[k]);
+    xmax[blockIdx.x] = mx;
+  }
+}
+
+// r = b - (H + shift I) x (H full and symmetric, FP64), one warp per row;
+// block maxima of |r|.
+__global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ H, int64_t ldh,
+                                                     int64_t m, double shift,
+                                                     const double* __restrict__ b,
+                                                     const double* __restrict__ x,
+                                                     double* __restrict__ r,
+                                                     double* __restrict__ rmax) {
+  __shared__ double wm[MX_T / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (MX_T / 32) + w;
+  double a = 0.0;
+  if (i < m) {
+    const double* __restrict__ Hi = H + i * ldh;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t c = lane;
+    for (; c + 32 < m; c += 64) {
+      s0 = fma(Hi[c], x[c], s0);
+      s1 = fma(Hi[c + 32], x[c + 32], s1);
+    }
+    if (c < m) s0 = fma(Hi[c], x[c], s0);
+    double s = warp_sum(s0 + s1);
+    if (lane == 0) {
+      const double ri = b[i] - s - shift * x[i];
+      r[i] = ri;
+      a = fabs(ri);
+    }
+  }
+  if (lane == 0) wm[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wm[k]);
+    rmax[blockIdx.x] = mx;
+  }
+}
+
+// out[k] = max of blocks of the partial maxima (three arrays, one block).
+__global__ void __launch_bounds__(MX_T) max3(const double* __restrict__ a, int64_t na,
+                                             const double* __restrict__ b, int64_t nb,
+                                             const double* __restrict__ c, int64_t nc,
+                                             double* __restrict__ out) {
+  __shared__ double sm[3][MX_T];
+  const double* src[3] = {a, b, c};
+  const int64_t n[3] = {na, nb, nc};
+  for (int k = 0; k < 3; ++k) {
+    double mx = 0.0;
+    if (src[k])
+      for (int64_t e = threadIdx.x; e < n[k]; e += MX_T) mx = fmax(mx, src[k][e]);
+    sm[k][threadIdx.x] = mx;
+  }
+  __syncthreads();
+  for (int o = MX_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] = fmax(sm[k][threadIdx.x], sm[k][threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// Block maxima of |v|.
+__global__ void __launch_bounds__(MX_T) absmax_blocks(const double* __restrict__ v, int64_t m,
+                                                      double* __restrict__ out) {
+  __shared__ double wm[MX_T / 32];
+  const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
+  double a = i < m ? fabs(v[i]) : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wm[k]);
+    out[blockIdx.x] = mx;
+  }
 }
 
 }  // namespace
@@ -459,9 +676,9 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
     // the panel kernels run beside the tensor-core update, which takes the
     // largest shared-memory carveout; an SM holds CTAs of one carveout only
     SPSVM_TRY(chol_tc_carveout());
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(potrf_diag, cudaFuncAttributePreferredSharedMemoryCarveout,
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(potrf_diag<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
-    SPSVM_CUDA_TRY(cudaFuncSetAttribute(trsm_panel, cudaFuncAttributePreferredSharedMemoryCarveout,
+    SPSVM_CUDA_TRY(cudaFuncSetAttribute(trsm_panel<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
     SideGuard side;
     SPSVM_TRY(side_acquire(&side.ss));
@@ -471,14 +688,14 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
     SPSVM_CUDA_TRY(cudaStreamWaitEvent(p, side.ss.b, 0));
     int buf = 0;
     for (; m - (k0 + 64) >= 256; k0 += 64, buf ^= 1) {
-      potrf_diag<<<1, PT, 0, p>>>(H, ldh, m, k0, info);
+      potrf_diag<double><<<1, PT, 0, p>>>(H, ldh, m, k0, info);
       SPSVM_LAUNCH_CHECK();
-      trsm_panel<<<(unsigned)ceil_div(m - (k0 + PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0, info);
+      trsm_panel<double><<<(unsigned)ceil_div(m - (k0 + PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0, info);
       SPSVM_LAUNCH_CHECK();
       SPSVM_TRY(chol_tc_panel_update(H, ldh, m, k0, info, p));
-      potrf_diag<<<1, PT, 0, p>>>(H, ldh, m, k0 + PB, info);
+      potrf_diag<double><<<1, PT, 0, p>>>(H, ldh, m, k0 + PB, info);
       SPSVM_LAUNCH_CHECK();
-      trsm_panel<<<(unsigned)ceil_div(m - (k0 + 2 * PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0 + PB,
+      trsm_panel<double><<<(unsigned)ceil_div(m - (k0 + 2 * PB), PT / 4), PT, 0, p>>>(H, ldh, m, k0 + PB,
                                                                              info);
       SPSVM_LAUNCH_CHECK();
       // slices of this panel (the buffer was last read by the update on s
@@ -495,18 +712,18 @@ extern "C" int spsvm_cholesky(double* H, int64_t m, int64_t ldh, int32_t* info, 
     // s has waited for everything p did (the last record of a)
   }
   for (; k0 < m; k0 += PB) {
-    potrf_diag<<<1, PT, 0, s>>>(H, ldh, m, k0, info);
+    potrf_diag<double><<<1, PT, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
     const int64_t below = m - (k0 + PB);
     if (below <= 0) break;
-    trsm_panel<<<(unsigned)ceil_div(below, PT / 4), PT, 0, s>>>(H, ldh, m, k0, info);
+    trsm_panel<double><<<(unsigned)ceil_div(below, PT / 4), PT, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
     const int64_t T = ceil_div(below, (int64_t)PB);
-    syrk_trailing<<<(unsigned)(T * (T + 1) / 2), PT, 0, s>>>(H, ldh, m, k0, info);
+    syrk_trailing<double><<<(unsigned)(T * (T + 1) / 2), PT, 0, s>>>(H, ldh, m, k0, info);
     SPSVM_LAUNCH_CHECK();
   }
   if (m > 0) {
-    diag_inverse<<<(unsigned)ceil_div(m, (int64_t)NB), 64, 0, s>>>(H, ldh, m);
+    diag_inverse<double><<<(unsigned)ceil_div(m, (int64_t)NB), DI_T, 0, s>>>(H, ldh, m);
     SPSVM_LAUNCH_CHECK();
   }
   return SPSVM_OK;
@@ -533,9 +750,146 @@ extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, dou
   double* z = static_cast<double*>(work);
   unsigned* flags = reinterpret_cast<unsigned*>(static_cast<char*>(work) + solve_flags_offset(m));
   SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(2 * B + 2) * 4, s));
-  trsv_fwd_onepass<<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, b, z, flags, flags + 2 * B);
+  trsv_fwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, b, z, flags, flags + 2 * B);
   SPSVM_LAUNCH_CHECK();
-  trsv_bwd_onepass<<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, z, b, flags + B, flags + 2 * B + 1);
+  trsv_bwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, z, b, flags + B, flags + 2 * B + 1);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision Newton solve (host side)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct MixedLayout {
+  int64_t ldl, B, nrow_blocks, nvec_blocks;
+  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, total;
+};
+
+MixedLayout mixed_layout(int64_t m) {
+  MixedLayout ly{};
+  auto al = [](size_t b) { return (size_t)round_up((int64_t)b, (int64_t)256); };
+  ly.ldl = round_up(m, (int64_t)4);
+  ly.B = ceil_div(m, (int64_t)NB);
+  ly.nrow_blocks = ceil_div(m, (int64_t)(MX_T / 32));
+  ly.nvec_blocks = ceil_div(m, (int64_t)MX_T);
+  size_t off = 0;
+  ly.L = off;      off += al((size_t)m * ly.ldl * 4);
+  ly.sw = off;     ly.sw_bytes = al((size_t)m * 4) + al((size_t)(2 * ly.B + 2) * 4); off += ly.sw_bytes;
+  ly.z32 = off;    off += al((size_t)m * 4);
+  ly.r = off;      off += al((size_t)m * 8);
+  ly.rowmax = off; off += al((size_t)ly.nrow_blocks * 8);
+  ly.xmax = off;   off += al((size_t)ly.nvec_blocks * 8);
+  ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
+  ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
+  ly.norms = off;  off += al(8 * 8);
+  ly.total = off;
+  return ly;
+}
+
+}  // namespace
+
+extern "C" size_t spsvm_mixed_work_bytes(int64_t m) { return m > 0 ? mixed_layout(m).total : 0; }
+
+extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, double shift,
+                                    int32_t* info, void* work, size_t work_bytes, void* stream) {
+  if (!H || !info || m < 0 || ldh < m || !(shift >= 0.0))
+    return set_error(SPSVM_ERR_ARG, "cholesky_mixed: bad arguments");
+  cudaStream_t s = as_stream(stream);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  if (m == 0) return SPSVM_OK;
+  const MixedLayout ly = mixed_layout(m);
+  if (!work || work_bytes < ly.total || (reinterpret_cast<uintptr_t>(work) & 255) != 0)
+    return set_error(SPSVM_ERR_OOM, "cholesky_mixed: work too small or misaligned");
+  ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
+  char* w = static_cast<char*>(work);
+  float* L = reinterpret_cast<float*>(w + ly.L);
+  to_f32_shift<<<(unsigned)ly.nrow_blocks, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
+                                                         reinterpret_cast<double*>(w + ly.rowmax));
+  SPSVM_LAUNCH_CHECK();
+  for (int64_t k0 = 0; k0 < m; k0 += PB) {
+    potrf_diag<float><<<1, PT, 0, s>>>(L, ly.ldl, m, k0, info);
+    SPSVM_LAUNCH_CHECK();
+    const int64_t below = m - (k0 + PB);
+    if (below <= 0) break;
+    trsm_panel<float><<<(unsigned)ceil_div(below, PT / 4), PT, 0, s>>>(L, ly.ldl, m, k0, info);
+    SPSVM_LAUNCH_CHECK();
+    const int64_t T = ceil_div(below, (int64_t)PB);
+    syrk_trailing<float><<<(unsigned)(T * (T + 1) / 2), PT, 0, s>>>(L, ly.ldl, m, k0, info);
+    SPSVM_LAUNCH_CHECK();
+  }
+  diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift,
+                                 const double* b, double* x, int32_t max_iter, double tol,
+                                 int32_t* iters, double* backward_error, void* work,
+                                 size_t work_bytes, void* stream) {
+  if (!H || !b || !x || m < 0 || ldh < m || max_iter < 1 || !(tol > 0.0) || !(shift >= 0.0))
+    return set_error(SPSVM_ERR_ARG, "solve_mixed: bad arguments");
+  if (iters) *iters = 0;
+  if (backward_error) *backward_error = 0.0;
+  if (m == 0) return SPSVM_OK;
+  const MixedLayout ly = mixed_layout(m);
+  if (!work || work_bytes < ly.total || (reinterpret_cast<uintptr_t>(work) & 255) != 0)
+    return set_error(SPSVM_ERR_OOM, "solve_mixed: work too small or misaligned");
+  cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_SOLVE, s, 8.0 * (double)m * m);
+  char* w = static_cast<char*>(work);
+  const float* L = reinterpret_cast<const float*>(w + ly.L);
+  float* zw = reinterpret_cast<float*>(w + ly.sw);
+  unsigned* flags = reinterpret_cast<unsigned*>(w + ly.sw + round_up(m * 4, (int64_t)256));
+  float* z32 = reinterpret_cast<float*>(w + ly.z32);
+  double* r = reinterpret_cast<double*>(w + ly.r);
+  double* rowmax = reinterpret_cast<double*>(w + ly.rowmax);
+  double* xmax = reinterpret_cast<double*>(w + ly.xmax);
+  double* rmax = reinterpret_cast<double*>(w + ly.rmax);
+  double* bmax = reinterpret_cast<double*>(w + ly.bmax);
+  double* norms = reinterpret_cast<double*>(w + ly.norms);
+  const unsigned vb = (unsigned)ly.nvec_blocks, rb = (unsigned)ly.nrow_blocks;
+  SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+  absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax);
+  SPSVM_LAUNCH_CHECK();
+  // norms[0] = ||H + shift I||_inf, norms[3] = ||b||_inf
+  max3<<<1, MX_T, 0, s>>>(rowmax, ly.nrow_blocks, bmax, ly.nvec_blocks, nullptr, 0, norms);
+  SPSVM_LAUNCH_CHECK();
+  double hn[3] = {0, 0, 0};
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double prev = INFINITY;
+  for (int it = 0; it < max_iter; ++it) {
+    // z = (L L^T)^{-1} r in FP32, x += z, r = b - (H + shift I) x in FP64
+    to_f32_vec<<<vb, MX_T, 0, s>>>(r, m, z32);
+    SPSVM_LAUNCH_CHECK();
+    SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(2 * ly.B + 2) * 4, s));
+    trsv_fwd_onepass<float><<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zw, flags,
+                                                                  flags + 2 * ly.B);
+    SPSVM_LAUNCH_CHECK();
+    trsv_bwd_onepass<float><<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, z32, flags + ly.B,
+                                                                  flags + 2 * ly.B + 1);
+    SPSVM_LAUNCH_CHECK();
+    add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
+    SPSVM_LAUNCH_CHECK();
+    residual_f64<<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
+    SPSVM_LAUNCH_CHECK();
+    max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4);
+    SPSVM_LAUNCH_CHECK();
+    double nv[2] = {0, 0};
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(nv, norms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int32_t code = 0;
+    SPSVM_TRY(device_status_on(s, &code));   // synchronises s
+    const double denom = hn[0] * nv[0] + hn[1];
+    const double be = denom > 0.0 ? nv[1] / denom : 0.0;
+    if (iters) *iters = it + 1;
+    if (backward_error) *backward_error = be;
+    if (!(be == be)) return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: not finite");
+    if (be <= tol) return SPSVM_OK;
+    if (it > 0 && nv[1] > 0.5 * prev)
+      return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: refinement stagnates (backward error %.3g)", be);
+    prev = nv[1];
+  }
+  return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: %d iterations not enough", max_iter);
 }

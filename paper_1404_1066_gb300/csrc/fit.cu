@@ -149,17 +149,18 @@ int grid_for(int64_t n, int threads) {
 struct Layout {
   int64_t n, d, ldn, ldh, jcap, kappa, q;
   size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
-      off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_ws, off_sv, off_J, off_cand,
-      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, total;
+      off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_tmp2, off_ws, off_sv, off_J,
+      off_cand,
+      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, total;
   size_t scratch_bytes;
   size_t kbytes;
-  size_t chw_bytes, sv_bytes;
+  size_t chw_bytes, sv_bytes, mix_bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int32_t kappa,
-                   int32_t q) {
+                   int32_t q, int32_t solver) {
   Layout L{};
   L.n = n;
   L.d = d;
@@ -194,6 +195,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_r = take(L.jcap * 8);
   L.off_rhs = take(L.jcap * 8);
   L.off_tmp = take(L.jcap * 8);
+  L.off_tmp2 = take(L.jcap * 8);
   L.off_ws = take(L.jcap * 8);
   L.sv_bytes = spsvm_cholesky_solve_work_bytes(L.jcap);
   L.off_sv = take(L.sv_bytes);
@@ -214,12 +216,15 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_scratch = take(L.scratch_bytes);
   L.chw_bytes = spsvm_cholesky_work_bytes(L.jcap);
   L.off_chw = take(L.chw_bytes);
+  // FP32 factor and refinement vectors of the mixed Newton solve
+  L.mix_bytes = solver == SPSVM_SOLVE_MIXED ? spsvm_mixed_work_bytes(L.jcap) : 0;
+  L.off_mix = take(L.mix_bytes);
   L.total = off;
   return L;
 }
 
 struct Opts {
-  int32_t kappa, q, max_newton, precision, refine, record;
+  int32_t kappa, q, max_newton, precision, refine, record, solver;
   double growth_tol, rel_tol;
   uint64_t seed;
   bool fixed;
@@ -239,10 +244,15 @@ Opts resolve(const spsvm_options* o) {
   r.seed = o ? o->seed : 0;
   r.fixed = o && o->fixed_basis;
   r.stream = o ? as_stream(o->stream) : nullptr;
+  r.solver = (o && o->newton_solver == SPSVM_SOLVE_FP64) ? SPSVM_SOLVE_FP64 : SPSVM_SOLVE_MIXED;
   return r;
 }
 
 constexpr int32_t kJitterMaxLevel = 8;   // largest jitter 1e-2 tr(H)/|J|
+// mixed Newton solve: refinement steps and the FP64-level backward error it
+// must reach (else the FP64 factorisation is used)
+constexpr int32_t kMixedIters = 30;
+constexpr double kMixedTol = 1e-13;
 
 struct Fit {
   const float* X;
@@ -362,46 +372,78 @@ struct Fit {
       // along it (t = 0: the computed H is too far from the exact one in its
       // smallest directions) the level goes up and d is recomputed.  The
       // level never goes down within a fit.
-      bool h_fresh = false;   // H holds the unfactorised matrix
-      double tr = -1.0, t = 0.0;
+      bool h_fresh = false;   // H holds the unfactorised, unshifted matrix
+      bool mixed = false;     // the factor in use is the FP32 one (H kept intact)
+      double tr = -1.0, t = 0.0, shift = 0.0;
+      double* tmp2 = at<double>(L.off_tmp2);
+      void* mixw = ws + L.off_mix;
       for (;;) {
         for (int32_t lv = jitter;; ++lv) {
           if (lv > kJitterMaxLevel)
             return set_error(SPSVM_ERR_NOT_PD,
                              "Newton matrix not positive definite up to jitter 1e-2 tr(H)/|J| (|J|=%d)", m);
-          if (!h_fresh)
+          if (!h_fresh) {
             SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb,
                                 s, st[2]));
-          h_fresh = false;   // the factorisation overwrites H
-          if (lv >= 0) {
-            if (tr < 0.0) {
-              diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
-              SPSVM_LAUNCH_CHECK();
-              SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
-              SPSVM_TRY(sync());
+            h_fresh = true;
+          }
+          if (lv >= 0 && tr < 0.0) {
+            diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
+            SPSVM_LAUNCH_CHECK();
+            SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
+            SPSVM_TRY(sync());
+          }
+          shift = lv >= 0 ? std::pow(10.0, lv - 10) * tr / m : 0.0;
+          int32_t info_h = 0;
+          // FP32 factor of H + shift I and FP64 refinement to FP64 backward
+          // error; H is kept, so a failure costs no Gram rebuild
+          mixed = false;
+          if (op.solver == SPSVM_SOLVE_MIXED) {
+            SPSVM_TRY(spsvm_cholesky_mixed(H, m, ldH, shift, info, mixw, L.mix_bytes, s));
+            SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
+            SPSVM_TRY(sync());
+            if (info_h == 0) {
+              const int rc = spsvm_solve_mixed(H, m, ldH, shift, rhs, dir, kMixedIters, kMixedTol,
+                                               nullptr, nullptr, mixw, L.mix_bytes, s);
+              if (rc == SPSVM_OK) mixed = true;
+              else if (rc != SPSVM_ERR_NO_CONVERGE) return rc;
             }
-            add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, std::pow(10.0, lv - 10) * tr / m);
+          }
+          if (mixed) {
+            jitter = lv;
+            break;
+          }
+          // FP64 factorisation in place (H is overwritten by its factor)
+          if (lv >= 0) {
+            add_diag<<<mb, tpb, 0, s>>>(H, ldH, m, shift);
             SPSVM_LAUNCH_CHECK();
           }
+          h_fresh = false;
           SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
-          int32_t info_h = 0;
           SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
           SPSVM_TRY(sync());
           if (info_h == 0) {
             jitter = lv;
+            SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, ws + L.off_sv, L.sv_bytes, s));
             break;
           }
         }
-        // d = -H^{-1} g, then refinement against the exactly applied H
-        SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, dir, ws + L.off_sv, L.sv_bytes, s));
+        // d = -(H + shift I)^{-1} g, then refinement against the exactly applied H
         SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
         for (int k = 0; k < op.refine; ++k) {
           SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
                                          at<int32_t>(L.off_pos), scratch, sb, s));
           refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
           SPSVM_LAUNCH_CHECK();
-          SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, ws + L.off_sv, L.sv_bytes, s));
+          if (mixed) {
+            const int rc = spsvm_solve_mixed(H, m, ldH, shift, tmp, tmp2, kMixedIters, kMixedTol,
+                                             nullptr, nullptr, mixw, L.mix_bytes, s);
+            if (rc != SPSVM_OK && rc != SPSVM_ERR_NO_CONVERGE) return rc;
+            SPSVM_CUDA_TRY(cudaMemcpyAsync(tmp, tmp2, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+          } else {
+            SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, ws + L.off_sv, L.sv_bytes, s));
+          }
           axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
           SPSVM_LAUNCH_CHECK();
           SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
@@ -576,7 +618,7 @@ extern "C" size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_
                                             const spsvm_options* opt) {
   if (n < 1 || d < 1 || basis_budget < 1) return 0;
   const Opts op = resolve(opt);
-  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q).total;
+  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver).total;
 }
 
 extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
@@ -609,7 +651,7 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     if ((int32_t)J0.size() > basis_budget) basis_budget = (int32_t)J0.size();
   }
   if (op.fixed && J0.empty()) return set_error(SPSVM_ERR_ARG, "fit: fixed_basis needs an initial basis");
-  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q);
+  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver);
   bool own = false;
   if (!workspace) {
     cudaError_t e = cudaMalloc(&workspace, L.total);

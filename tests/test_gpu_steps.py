@@ -265,6 +265,50 @@ def test_solve_padded_rows_and_reused_work(sp, m):
     assert rc == -2
 
 
+@pytest.mark.parametrize("shift", [0.0, 0.3])
+@pytest.mark.parametrize("m", [1, 63, 64, 65, 300, 1500])
+def test_mixed_solve_reaches_fp64_backward_error(sp, m, shift):
+    """FP32 factor + FP64 refinement: (H + shift I) x = b to a normwise
+    backward error <= 1e-13 (an FP64 Cholesky solve reaches ~1e-16..1e-14),
+    with H left bit-unchanged."""
+    g = np.random.default_rng(m + 7)
+    A = g.standard_normal((m, m + 3)) / np.sqrt(m)
+    H = A @ A.T + 1e-2 * np.eye(m)
+    b = g.standard_normal(m)
+    Ht = _t(H.copy())
+    info, st, x, iters, be = sp.spsvm_solve_mixed(Ht, _t(b.copy()), shift=shift)
+    assert info == 0 and st == 0, (info, st, iters, be)
+    np.testing.assert_array_equal(Ht.cpu().numpy(), H)
+    xs = x.cpu().numpy()
+    Hs = H + shift * np.eye(m)
+    r = b - Hs @ xs
+    ref_be = np.max(np.abs(r)) / (np.max(np.abs(Hs).sum(1)) * np.max(np.abs(xs)) + np.max(np.abs(b)))
+    assert ref_be <= 1e-13 and be <= 1e-13, (ref_be, be, iters)
+    xr = np.linalg.solve(Hs, b)
+    assert np.linalg.norm(xs - xr) <= 1e-10 * np.linalg.norm(xr) * max(1.0, np.linalg.cond(Hs) * 1e-4)
+
+
+def test_mixed_solve_reports_fp32_breakdown_and_stagnation(sp):
+    H = np.eye(100)
+    H[70, 70] = -1.0
+    info, st, _, _, _ = sp.spsvm_solve_mixed(_t(H), _t(np.ones(100)))
+    assert info == 71 and st is None
+    # condition number ~1e12: the FP32 factor either breaks down or cannot
+    # refine to FP64 backward error; never a wrong "converged" answer
+    g = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(g.standard_normal((200, 200)))
+    H = (Q * np.logspace(0, -12, 200)) @ Q.T
+    H = 0.5 * (H + H.T)
+    b = g.standard_normal(200)
+    info, st, x, iters, be = sp.spsvm_solve_mixed(_t(H), _t(b))
+    if info == 0 and st == 0:
+        xs = x.cpu().numpy()
+        r = b - H @ xs
+        assert np.max(np.abs(r)) <= 1e-13 * (np.max(np.abs(H).sum(1)) * np.max(np.abs(xs)) + np.max(np.abs(b)))
+    else:
+        assert info != 0 or st == -4
+
+
 @pytest.mark.parametrize("tc", [False, True])
 def test_cholesky_ill_conditioned_newton_matrix(sp, tc):
     # the Newton matrix of Eq. 4 on RBF data: lambda K_JJ + K_SJ^T K_SJ,
