@@ -452,29 +452,190 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
 // ---------------------------------------------------------------------------
 constexpr int MX_T = 256;
 
-// L (FP32, lower triangle) = H + shift I; per-block maximum of the FP64 row
-// sums |H_i.| + |shift| (the infinity norm, order-independent).
+// FP64 -> FP32 with round to nearest even, from the IEEE-754 encodings with
+// integer operations only (GB300 issues the FP64 conversion instruction at
+// its FP64 rate).  Results below the FP32 normal range flush to signed zero
+// and results above it become infinity (an FP32 factor then breaks down and
+// the caller falls back to FP64).
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned long long man = u & 0xfffffffffffffull;
+  if ((int)((u >> 52) & 0x7ff) == 0x7ff)   // inf / nan
+    return __uint_as_float(sign | 0x7f800000u | (man ? 0x400000u : 0u));
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m23 = (unsigned)(man >> 29);
+  const unsigned rem = (unsigned)(man & 0x1fffffffu);
+  const unsigned up = (rem > 0x10000000u) || (rem == 0x10000000u && (m23 & 1u));
+  unsigned bits = ((unsigned)e << 23) + m23 + up;   // a carry moves into the exponent
+  if (bits >= 0x7f800000u) bits = 0x7f800000u;
+  return __uint_as_float(sign | bits);
+}
+
+// L (FP32, lower triangle) = H + shift I, one block per row (the row's
+// loads all in flight at once); rowsum[r] = sum_c |H_rc + shift [c = r]|,
+// accumulated in FP32 (a norm estimate for the backward error; GB300's FP64
+// rate would make an FP64 add per element the bound of this pass).  The
+// infinity norm is the maximum of rowsum (order-independent).
 __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ H, int64_t ldh,
                                                      int64_t m, double shift, float* __restrict__ L,
-                                                     int64_t ldl, double* __restrict__ rowmax) {
-  __shared__ double wmax[MX_T / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t r = (int64_t)blockIdx.x * (MX_T / 32) + w;
-  double rs = 0.0;
-  if (r < m) {
-    for (int64_t c = lane; c < m; c += 32) {
-      const double v = H[r * ldh + c] + (c == r ? shift : 0.0);
-      rs += fabs(v);
-      if (c <= r) L[r * ldl + c] = (float)v;
-    }
+                                                     int64_t ldl, double* __restrict__ rowsum) {
+  __shared__ float ws[MX_T / 32];
+  const int64_t r = blockIdx.x;
+  const double* __restrict__ Hr = H + r * ldh;
+  float* __restrict__ Lr = L + r * ldl;
+  float rs = 0.0f;
+#pragma unroll 4
+  for (int64_t c = threadIdx.x; c < m; c += MX_T) {
+    float v = (c == r) ? f64_to_f32_rn(Hr[c] + shift) : f64_to_f32_rn(Hr[c]);
+    rs += fabsf(v);
+    if (c <= r) Lr[c] = v;
   }
   rs = warp_sum(rs);
-  if (lane == 0) wmax[w] = rs;
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = rs;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wmax[k]);
-    rowmax[blockIdx.x] = mx;
+    float t = 0.0f;
+    for (int k = 0; k < MX_T / 32; ++k) t += ws[k];
+    rowsum[r] = (double)t;
+  }
+}
+
+// FP32 panel step in one launch: every CTA factors the PB x PB diagonal
+// block at k0 with its first warp (registers and shuffles; the same
+// instructions on the same data in every CTA, so every copy is the same
+// bits), CTA 0 stores it, and all CTAs solve their 32 rows below it
+// (L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, four threads per row as in
+// trsm_panel).  Replaces a factor launch and a solve launch per panel.
+__global__ void __launch_bounds__(PT) panel32(float* __restrict__ H, int64_t ldh, int64_t m,
+                                              int64_t k0, int32_t* __restrict__ info) {
+  __shared__ float Ls[PB][PB + 1];
+  __shared__ float rd[PB];
+  __shared__ int fail_s;
+  if (*info != 0) return;
+  const int nb = (int)min64(PB, m - k0);
+  const int t = threadIdx.x, lane = t & 31;
+  if (t < 32) {
+    float a[PB];
+#pragma unroll
+    for (int c = 0; c < PB; ++c)
+      a[c] = (lane < nb && c <= lane) ? H[(k0 + lane) * ldh + k0 + c] : (c == lane ? 1.0f : 0.0f);
+    int fail = 0;
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      if (j < nb && fail == 0) {
+        const float d = __shfl_sync(0xffffffffu, a[j], j);
+        if (!(d > 0.0f) || !(d < 3.0e38f)) {
+          fail = j + 1;
+        } else {
+          const float y = rsqrt_t(d);
+          if (lane == j) a[j] = d * y;
+          else if (lane > j) a[j] *= y;
+          // all of the column's shuffles first (independent, issued back to
+          // back), then the updates
+          float col[PB];
+#pragma unroll
+          for (int l = j + 1; l < PB; ++l) col[l] = __shfl_sync(0xffffffffu, a[j], l);
+#pragma unroll
+          for (int l = j + 1; l < PB; ++l)
+            if (lane >= l) a[l] = fmaf(-a[j], col[l], a[l]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < PB; ++c) Ls[lane][c] = (c <= lane) ? a[c] : 0.0f;
+    if (lane == 0) fail_s = fail;
+    if (blockIdx.x == 0 && fail == 0 && lane < nb) {
+#pragma unroll
+      for (int c = 0; c < PB; ++c)
+        if (c <= lane) H[(k0 + lane) * ldh + k0 + c] = a[c];
+    }
+  }
+  __syncthreads();
+  if (fail_s) {
+    if (blockIdx.x == 0 && t == 0) *info = (int32_t)(k0 + fail_s);
+    return;
+  }
+  if (t < PB) rd[t] = 1.0f / Ls[t][t];
+  __syncthreads();
+  const int q = t & 3;
+  const int64_t r = k0 + PB + (int64_t)blockIdx.x * (PT / 4) + (t >> 2);
+  const bool ok = r < m;
+  float* row = H + (ok ? r : k0) * ldh + k0;
+  float x[PB / 4];
+#pragma unroll
+  for (int i = 0; i < PB / 4; ++i) x[i] = ok ? row[q + 4 * i] : 0.0f;
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    const int owner = j & 3, ji = j >> 2;
+    if (q == owner) x[ji] *= rd[j];
+    const float xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
+#pragma unroll
+    for (int i = ji; i < PB / 4; ++i)
+      if (q + 4 * i > j) x[i] = fmaf(-xj, Ls[q + 4 * i][j], x[i]);
+  }
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < PB / 4; ++i) row[q + 4 * i] = x[i];
+  }
+}
+
+// FP32 trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l], r >= c >= k0 + PB,
+// over 64 x 64 lower tiles: 256 threads, a 4 x 4 register block each (rows
+// 4 ty .. +3, columns 4 tx .. +3), the panel strips in shared memory read
+// as 16-byte vectors (two shared loads per 16 FMAs).
+constexpr int SY_T = 64;
+constexpr int SY_P = SY_T + 4;   // 16-byte aligned strip rows
+__global__ void __launch_bounds__(256) syrk32_tile64(float* __restrict__ H, int64_t ldh, int64_t m,
+                                                     int64_t k0, const int32_t* __restrict__ info) {
+  __shared__ __align__(16) float Ar[PB][SY_P];   // Ar[l][rr] = L[r0 + rr][k0 + l]
+  __shared__ __align__(16) float Ac[PB][SY_P];   // Ac[l][cc] = L[c0 + cc][k0 + l]
+  if (*info != 0) return;
+  const int64_t base = k0 + PB;
+  const int64_t ntile = ceil_div(m - base, (int64_t)SY_T);
+  int64_t tt = blockIdx.x, ti = 0;
+  while (tt > ti) {
+    tt -= ti + 1;
+    ++ti;
+  }
+  const int64_t tj = tt;
+  if (ti >= ntile) return;
+  const int64_t r0 = base + ti * SY_T, c0 = base + tj * SY_T;
+  for (int e = threadIdx.x; e < SY_T * PB; e += 256) {
+    const int rr = e / PB, ll = e % PB;
+    const int64_t gr = r0 + rr, gc = c0 + rr;
+    Ar[ll][rr] = (gr < m) ? H[gr * ldh + k0 + ll] : 0.0f;
+    Ac[ll][rr] = (gc < m) ? H[gc * ldh + k0 + ll] : 0.0f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 8
+  for (int l = 0; l < PB; ++l) {
+    const float4 av = *reinterpret_cast<const float4*>(&Ar[l][4 * ty]);
+    const float4 bv = *reinterpret_cast<const float4*>(&Ac[l][4 * tx]);
+    const float ar[4] = {av.x, av.y, av.z, av.w};
+    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = r0 + 4 * ty + a;
+    if (r >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t c = c0 + 4 * tx + b;
+      if (c <= r) H[r * ldh + c] -= acc[a][b];
+    }
   }
 }
 
@@ -483,7 +644,7 @@ __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ 
 __global__ void __launch_bounds__(MX_T) to_f32_vec(const double* __restrict__ r, int64_t m,
                                                    float* __restrict__ z) {
   const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
-  if (i < m) z[i] = (float)r[i];
+  if (i < m) z[i] = f64_to_f32_rn(r[i]);
 }
 
 // x += (double) z; block maxima of |x|.
@@ -508,8 +669,10 @@ __global__ void __launch_bounds__(MX_T) add_f32(double* __restrict__ x, const fl
   }
 }
 
-// r = b - (H + shift I) x (H full and symmetric, FP64), one warp per row;
+// r = b - (H + shift I) x (H full and symmetric, FP64), one warp per row,
+// 16-byte loads four deep per lane when H's rows and x are 16-byte aligned;
 // block maxima of |r|.
+template <bool VEC>
 __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ H, int64_t ldh,
                                                      int64_t m, double shift,
                                                      const double* __restrict__ b,
@@ -522,14 +685,33 @@ __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ 
   double a = 0.0;
   if (i < m) {
     const double* __restrict__ Hi = H + i * ldh;
-    double s0 = 0.0, s1 = 0.0;
-    int64_t c = lane;
-    for (; c + 32 < m; c += 64) {
-      s0 = fma(Hi[c], x[c], s0);
-      s1 = fma(Hi[c + 32], x[c + 32], s1);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (VEC) {
+      const double2* __restrict__ H2 = reinterpret_cast<const double2*>(Hi);
+      const double2* __restrict__ x2 = reinterpret_cast<const double2*>(x);
+      const int64_t half = m >> 1;
+      for (int64_t c = lane; c < half; c += 128) {
+        double2 h0 = make_double2(0, 0), h1 = h0, h2 = h0, h3 = h0;
+        double2 x0 = h0, x1 = h0, y2 = h0, x3 = h0;
+        if (c < half) { h0 = H2[c]; x0 = x2[c]; }
+        if (c + 32 < half) { h1 = H2[c + 32]; x1 = x2[c + 32]; }
+        if (c + 64 < half) { h2 = H2[c + 64]; y2 = x2[c + 64]; }
+        if (c + 96 < half) { h3 = H2[c + 96]; x3 = x2[c + 96]; }
+        s0 = fma(h0.y, x0.y, fma(h0.x, x0.x, s0));
+        s1 = fma(h1.y, x1.y, fma(h1.x, x1.x, s1));
+        s2 = fma(h2.y, y2.y, fma(h2.x, y2.x, s2));
+        s3 = fma(h3.y, x3.y, fma(h3.x, x3.x, s3));
+      }
+      if ((m & 1) && lane == 0) s0 = fma(Hi[m - 1], x[m - 1], s0);
+    } else {
+      for (int64_t c = lane; c < m; c += 128) {
+        s0 = fma(Hi[c], x[c], s0);
+        if (c + 32 < m) s1 = fma(Hi[c + 32], x[c + 32], s1);
+        if (c + 64 < m) s2 = fma(Hi[c + 64], x[c + 64], s2);
+        if (c + 96 < m) s3 = fma(Hi[c + 96], x[c + 96], s3);
+      }
     }
-    if (c < m) s0 = fma(Hi[c], x[c], s0);
-    double s = warp_sum(s0 + s1);
+    const double s = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) {
       const double ri = b[i] - s - shift * x[i];
       r[i] = ri;
@@ -779,7 +961,7 @@ MixedLayout mixed_layout(int64_t m) {
   ly.sw = off;     ly.sw_bytes = al((size_t)m * 4) + al((size_t)(2 * ly.B + 2) * 4); off += ly.sw_bytes;
   ly.z32 = off;    off += al((size_t)m * 4);
   ly.r = off;      off += al((size_t)m * 8);
-  ly.rowmax = off; off += al((size_t)ly.nrow_blocks * 8);
+  ly.rowmax = off; off += al((size_t)m * 8);
   ly.xmax = off;   off += al((size_t)ly.nvec_blocks * 8);
   ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
   ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
@@ -805,18 +987,17 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   char* w = static_cast<char*>(work);
   float* L = reinterpret_cast<float*>(w + ly.L);
-  to_f32_shift<<<(unsigned)ly.nrow_blocks, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
-                                                         reinterpret_cast<double*>(w + ly.rowmax));
+  to_f32_shift<<<(unsigned)m, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
+                                            reinterpret_cast<double*>(w + ly.rowmax));
   SPSVM_LAUNCH_CHECK();
   for (int64_t k0 = 0; k0 < m; k0 += PB) {
-    potrf_diag<float><<<1, PT, 0, s>>>(L, ly.ldl, m, k0, info);
-    SPSVM_LAUNCH_CHECK();
     const int64_t below = m - (k0 + PB);
-    if (below <= 0) break;
-    trsm_panel<float><<<(unsigned)ceil_div(below, PT / 4), PT, 0, s>>>(L, ly.ldl, m, k0, info);
+    panel32<<<(unsigned)(below > 0 ? ceil_div(below, (int64_t)(PT / 4)) : 1), PT, 0, s>>>(
+        L, ly.ldl, m, k0, info);
     SPSVM_LAUNCH_CHECK();
-    const int64_t T = ceil_div(below, (int64_t)PB);
-    syrk_trailing<float><<<(unsigned)(T * (T + 1) / 2), PT, 0, s>>>(L, ly.ldl, m, k0, info);
+    if (below <= 0) break;
+    const int64_t nt = ceil_div(below, (int64_t)SY_T);
+    syrk32_tile64<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(L, ly.ldl, m, k0, info);
     SPSVM_LAUNCH_CHECK();
   }
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
@@ -850,12 +1031,14 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
   double* bmax = reinterpret_cast<double*>(w + ly.bmax);
   double* norms = reinterpret_cast<double*>(w + ly.norms);
   const unsigned vb = (unsigned)ly.nvec_blocks, rb = (unsigned)ly.nrow_blocks;
+  const bool vec = (ldh % 2) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
   SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
   absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax);
   SPSVM_LAUNCH_CHECK();
   // norms[0] = ||H + shift I||_inf, norms[3] = ||b||_inf
-  max3<<<1, MX_T, 0, s>>>(rowmax, ly.nrow_blocks, bmax, ly.nvec_blocks, nullptr, 0, norms);
+  max3<<<1, MX_T, 0, s>>>(rowmax, m, bmax, ly.nvec_blocks, nullptr, 0, norms);
   SPSVM_LAUNCH_CHECK();
   double hn[3] = {0, 0, 0};
   SPSVM_CUDA_TRY(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -873,7 +1056,10 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
     SPSVM_LAUNCH_CHECK();
     add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
     SPSVM_LAUNCH_CHECK();
-    residual_f64<<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
+    if (vec)
+      residual_f64<true><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
+    else
+      residual_f64<false><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
     SPSVM_LAUNCH_CHECK();
     max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4);
     SPSVM_LAUNCH_CHECK();

@@ -437,7 +437,8 @@ struct Fit {
           refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
           SPSVM_LAUNCH_CHECK();
           if (mixed) {
-            const int rc = spsvm_solve_mixed(H, m, ldH, shift, tmp, tmp2, kMixedIters, kMixedTol,
+            // a correction of ~1e-5 relative size: 1e-6 backward error suffices
+            const int rc = spsvm_solve_mixed(H, m, ldH, shift, tmp, tmp2, kMixedIters, 1e-6,
                                              nullptr, nullptr, mixw, L.mix_bytes, s);
             if (rc != SPSVM_OK && rc != SPSVM_ERR_NO_CONVERGE) return rc;
             SPSVM_CUDA_TRY(cudaMemcpyAsync(tmp, tmp2, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
