@@ -310,7 +310,8 @@ typedef struct spsvm_options {
   const int64_t* initial_basis;  /* host, n_initial indices (fixed basis), or NULL */
   int32_t  n_initial;
   int32_t  fixed_basis;    /* nonzero: no growth rounds (J = initial_basis) */
-  int32_t  refine;         /* iterative-refinement sweeps per Newton step (0 -> 1, <0 -> none) */
+  int32_t  refine;         /* refinement sweeps per Newton step against the exactly applied
+                              H (two passes over K each); <= 0 -> none (default) */
   int32_t  record;         /* keep candidates / chosen per round for replay checks */
   void*    stream;         /* cudaStream_t for all work (NULL = default stream) */
   int32_t  newton_solver;  /* SPSVM_SOLVE_MIXED (0): FP32 factor + FP64 refinement to FP64

@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ 
 // (L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, four threads per row as in
 // trsm_panel).  Replaces a factor launch and a solve launch per panel.
 __global__ void __launch_bounds__(PT) panel32(float* __restrict__ H, int64_t ldh, int64_t m,
-                                              int64_t k0, int32_t* __restrict__ info) {
+                                              int64_t k0, int32_t* __restrict__ info,
+                                              float* __restrict__ diag_out) {
   __shared__ float Ls[PB][PB + 1];
   __shared__ float rd[PB];
   __shared__ int fail_s;
@@ -547,10 +548,15 @@ __global__ void __launch_bounds__(PT) panel32(float* __restrict__ H, int64_t ldh
 #pragma unroll
     for (int c = 0; c < PB; ++c) Ls[lane][c] = (c <= lane) ? a[c] : 0.0f;
     if (lane == 0) fail_s = fail;
+    // CTA 0 keeps the factor: in diag_out when a trailing update follows
+    // (it copies it into place; other CTAs of this launch may still be
+    // reading the unfactored block), in place for the last panel (one CTA)
     if (blockIdx.x == 0 && fail == 0 && lane < nb) {
+      const bool last = m - k0 <= PB;
+      float* dst = last ? H + (k0 + lane) * ldh + k0 : diag_out + lane * PB;
 #pragma unroll
       for (int c = 0; c < PB; ++c)
-        if (c <= lane) H[(k0 + lane) * ldh + k0 + c] = a[c];
+        if (c <= lane) dst[c] = a[c];
     }
   }
   __syncthreads();
@@ -589,10 +595,17 @@ __global__ void __launch_bounds__(PT) panel32(float* __restrict__ H, int64_t ldh
 constexpr int SY_T = 64;
 constexpr int SY_P = SY_T + 4;   // 16-byte aligned strip rows
 __global__ void __launch_bounds__(256) syrk32_tile64(float* __restrict__ H, int64_t ldh, int64_t m,
-                                                     int64_t k0, const int32_t* __restrict__ info) {
+                                                     int64_t k0, const int32_t* __restrict__ info,
+                                                     const float* __restrict__ diag_in) {
   __shared__ __align__(16) float Ar[PB][SY_P];   // Ar[l][rr] = L[r0 + rr][k0 + l]
   __shared__ __align__(16) float Ac[PB][SY_P];   // Ac[l][cc] = L[c0 + cc][k0 + l]
   if (*info != 0) return;
+  if (blockIdx.x == 0) {   // the panel's diagonal factor into place (not read here)
+    for (int e = threadIdx.x; e < PB * PB; e += 256) {
+      const int rr = e / PB, cc = e % PB;
+      if (cc <= rr) H[(k0 + rr) * ldh + k0 + cc] = diag_in[rr * PB + cc];
+    }
+  }
   const int64_t base = k0 + PB;
   const int64_t ntile = ceil_div(m - base, (int64_t)SY_T);
   int64_t tt = blockIdx.x, ti = 0;
@@ -946,7 +959,7 @@ namespace {
 
 struct MixedLayout {
   int64_t ldl, B, nrow_blocks, nvec_blocks;
-  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, total;
+  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, diag, total;
 };
 
 MixedLayout mixed_layout(int64_t m) {
@@ -966,6 +979,7 @@ MixedLayout mixed_layout(int64_t m) {
   ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
   ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
   ly.norms = off;  off += al(8 * 8);
+  ly.diag = off;   off += al((size_t)PB * PB * 4);   // a panel's diagonal factor in transit
   ly.total = off;
   return ly;
 }
@@ -987,17 +1001,18 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   char* w = static_cast<char*>(work);
   float* L = reinterpret_cast<float*>(w + ly.L);
+  float* diagbuf = reinterpret_cast<float*>(w + ly.diag);
   to_f32_shift<<<(unsigned)m, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
                                             reinterpret_cast<double*>(w + ly.rowmax));
   SPSVM_LAUNCH_CHECK();
   for (int64_t k0 = 0; k0 < m; k0 += PB) {
     const int64_t below = m - (k0 + PB);
     panel32<<<(unsigned)(below > 0 ? ceil_div(below, (int64_t)(PT / 4)) : 1), PT, 0, s>>>(
-        L, ly.ldl, m, k0, info);
+        L, ly.ldl, m, k0, info, diagbuf);
     SPSVM_LAUNCH_CHECK();
     if (below <= 0) break;
     const int64_t nt = ceil_div(below, (int64_t)SY_T);
-    syrk32_tile64<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(L, ly.ldl, m, k0, info);
+    syrk32_tile64<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(L, ly.ldl, m, k0, info, diagbuf);
     SPSVM_LAUNCH_CHECK();
   }
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);

@@ -237,7 +237,7 @@ Opts resolve(const spsvm_options* o) {
   r.q = (o && o->add_per_round > 0) ? o->add_per_round : 64;
   r.max_newton = (o && o->max_newton > 0) ? o->max_newton : 50;
   r.precision = o ? o->precision : SPSVM_FP32;
-  r.refine = (o && o->refine != 0) ? (o->refine < 0 ? 0 : o->refine) : 1;
+  r.refine = (o && o->refine > 0) ? o->refine : 0;
   r.record = o ? o->record : 0;
   r.growth_tol = o ? o->growth_tol : 0.0;
   r.rel_tol = (o && o->rel_tol > 0) ? o->rel_tol : (r.precision == SPSVM_BF16X3 ? 2e-5 : 1e-6);
@@ -344,11 +344,44 @@ struct Fit {
     SPSVM_CUDA_TRY(cudaMemcpyAsync(st, at<double>(L.off_small), sizeof(st), cudaMemcpyDeviceToHost, s));
     SPSVM_TRY(sync());
     int32_t status = SPSVM_ERR_NO_CONVERGE;
+    double* tmp2 = at<double>(L.off_tmp2);
+    void* mixw = ws + L.off_mix;
+    // (H + shift I)^{-1} b with the factor in hand: the FP32 one with FP64
+    // refinement (H kept), or the FP64 one in H
+    auto solve_with = [&](bool use_mixed, double sh, const double* b, double* x, double btol) -> int {
+      if (use_mixed)
+        return spsvm_solve_mixed(H, m, ldH, sh, b, x, kMixedIters, btol, nullptr, nullptr, mixw,
+                                 L.mix_bytes, s);
+      if (x != b) SPSVM_CUDA_TRY(cudaMemcpyAsync(x, b, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      return spsvm_cholesky_solve(H, m, ldH, x, ws + L.off_sv, L.sv_bytes, s);
+    };
+    // u = K_nJ d, then the optional refinement sweeps against the exactly
+    // applied H (two more passes over K each)
+    auto finish_direction = [&](const uint8_t* act, bool use_mixed, double sh) -> int {
+      SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
+      for (int k = 0; k < op.refine; ++k) {
+        SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
+                                       at<int32_t>(L.off_pos), scratch, sb, s));
+        refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
+        SPSVM_LAUNCH_CHECK();
+        // a correction of ~1e-5 relative size: 1e-6 backward error suffices
+        const int rc = solve_with(use_mixed, sh, tmp, tmp2, 1e-6);
+        if (rc != SPSVM_OK && rc != SPSVM_ERR_NO_CONVERGE) return rc;
+        axpy_d<<<mb, tpb, 0, s>>>(dir, tmp2, 1.0, m);
+        SPSVM_LAUNCH_CHECK();
+        SPSVM_TRY(spsvm_gemv(&K, tmp2, u, 1, s));
+      }
+      return SPSVM_OK;
+    };
+    // the factor in hand (valid while the active set does not change)
+    bool reuse = false, fac_mixed = false;
+    double fac_shift = 0.0;
     for (int it = 0; it < op.max_newton; ++it) {
       uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
       sub_kernel<<<grid_for(n, tpb), tpb, 0, s>>>(o, y, n, res);
       SPSVM_LAUNCH_CHECK();
-      SPSVM_TRY(spsvm_compact_active(&K, act, res, y, wsum, r, &Kc, n_active,
+      // K_SJ is only needed for a new Gram matrix
+      SPSVM_TRY(spsvm_compact_active(&K, act, res, y, wsum, r, reuse ? nullptr : &Kc, n_active,
                                      at<int32_t>(L.off_pos), scratch, sb, s));
       grad_finish<<<mb, tpb, 0, s>>>(o, Jd, wsum, m, op_lambda(), g, rhs);
       SPSVM_LAUNCH_CHECK();
@@ -372,12 +405,24 @@ struct Fit {
       // along it (t = 0: the computed H is too far from the exact one in its
       // smallest directions) the level goes up and d is recomputed.  The
       // level never goes down within a fit.
+      double t = 0.0;
+      bool stepped = false;
+      if (reuse) {
+        // the active set has not changed since the factor in hand was formed,
+        // so H has not either: only the right-hand side is new
+        const int rc = solve_with(fac_mixed, fac_shift, rhs, dir, kMixedTol);
+        if (rc == SPSVM_OK) {
+          SPSVM_TRY(finish_direction(act, fac_mixed, fac_shift));
+          SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
+          stepped = t > 0.0;
+        } else if (rc != SPSVM_ERR_NO_CONVERGE) {
+          return rc;
+        }
+      }
       bool h_fresh = false;   // H holds the unfactorised, unshifted matrix
       bool mixed = false;     // the factor in use is the FP32 one (H kept intact)
-      double tr = -1.0, t = 0.0, shift = 0.0;
-      double* tmp2 = at<double>(L.off_tmp2);
-      void* mixw = ws + L.off_mix;
-      for (;;) {
+      double tr = -1.0, shift = 0.0;
+      for (; !stepped;) {
         for (int32_t lv = jitter;; ++lv) {
           if (lv > kJitterMaxLevel)
             return set_error(SPSVM_ERR_NOT_PD,
@@ -429,26 +474,10 @@ struct Fit {
             break;
           }
         }
-        // d = -(H + shift I)^{-1} g, then refinement against the exactly applied H
-        SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
-        for (int k = 0; k < op.refine; ++k) {
-          SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
-                                         at<int32_t>(L.off_pos), scratch, sb, s));
-          refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
-          SPSVM_LAUNCH_CHECK();
-          if (mixed) {
-            // a correction of ~1e-5 relative size: 1e-6 backward error suffices
-            const int rc = spsvm_solve_mixed(H, m, ldH, shift, tmp, tmp2, kMixedIters, 1e-6,
-                                             nullptr, nullptr, mixw, L.mix_bytes, s);
-            if (rc != SPSVM_OK && rc != SPSVM_ERR_NO_CONVERGE) return rc;
-            SPSVM_CUDA_TRY(cudaMemcpyAsync(tmp, tmp2, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-          } else {
-            SPSVM_TRY(spsvm_cholesky_solve(H, m, ldH, tmp, ws + L.off_sv, L.sv_bytes, s));
-          }
-          axpy_d<<<mb, tpb, 0, s>>>(dir, tmp, 1.0, m);
-          SPSVM_LAUNCH_CHECK();
-          SPSVM_TRY(spsvm_gemv(&K, tmp, u, 1, s));
-        }
+        // d = -(H + shift I)^{-1} g (computed above), u = K_nJ d
+        SPSVM_TRY(finish_direction(act, mixed, shift));
+        fac_mixed = mixed;
+        fac_shift = shift;
         t = 0.0;
         SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
         if (t > 0.0 || jitter >= kJitterMaxLevel) break;
@@ -478,12 +507,15 @@ struct Fit {
       model->history.push_back(rec);
       act_cur = nxt;
       std::memcpy(st, st2, sizeof(st));
-      // a full exact Newton step that keeps the active set lands on the
-      // minimiser of f (with a jitter only the gradient test decides)
-      if (t == 1.0 && nd == 0 && jitter < 0) {
+      // a full Newton step that keeps the active set lands on the minimiser of
+      // f when the direction is exact (unshifted, refined against the exactly
+      // applied H); otherwise the next step's gradient test decides, and that
+      // step reuses the factor (the active set, hence H, is unchanged)
+      if (t == 1.0 && nd == 0 && jitter < 0 && op.refine > 0) {
         status = SPSVM_OK;
         break;
       }
+      reuse = nd == 0;
     }
     model->status = status;
     return SPSVM_OK;
