@@ -417,25 +417,38 @@ def run_ours(args):
     pr = prof[dom]
     per_launch_ms = pr["ms"] / max(1, pr["launches"])
     per_launch_work = pr["work"] / max(1, pr["launches"])
+    fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x 2 flops x max clock (80.5)
+    note = None
     if dom in ("gram", "kernel_block", "score", "decision") and prec == "bf16x3":
         bound, unit = "tensor", "TFLOP/s"
-        achieved = 3.0 * per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        products = 4.0 if dom == "gram" else 3.0    # split-BF16 products per FP32 product
+        achieved = products * per_launch_work / (per_launch_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
     elif dom in ("gram", "kernel_block", "score", "decision"):
         bound, unit = "alu", "TFLOP/s"
         achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x 2 flops x max clock
+        peak = fp32_simt
     elif dom == "cholesky":
+        # |J|^3/3 flops per factorisation of the Newton matrix, done in FP32
+        # (FP64 iterative refinement follows in the solve): against the FP32
+        # SIMT rate from unit counts and the maximum clock
         bound, unit = "alu", "TFLOP/s"
         achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
-        peak = 1.25                            # FP64 rate of GB300
+        peak = fp32_simt
+        note = "FP32 factor of the Newton matrix (mixed solve); peak = FP32 SIMT rate derived from unit counts and clock"
     else:
         bound, unit = "hbm", "GB/s"
         achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
+    # DRAM traffic per launch, measured with ncu on the GEMV at n = 100,000
+    # (1.005 x its algorithmic bytes), scaled to this launch size
+    traffic = per_launch_work * 1.005 if dom == "gemv" else None
     roofline = dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
-                    frac=achieved / peak, traffic=None, peak_source=src,
+                    frac=achieved / peak, traffic=traffic,
+                    peak_source=src if bound in ("hbm", "tensor") else "derived",
                     launches=pr["launches"], ms_per_launch=per_launch_ms)
+    if note:
+        roofline["note"] = note
 
     batched = batched_leg(sp, torch) if args.batched else None
     serve = serve_leg(sp, requests=args.serve_requests) if args.serve_requests > 0 else None
