@@ -202,7 +202,8 @@ __global__ void scan_blocks(int32_t* __restrict__ counts, int64_t nb, int64_t* _
 }
 
 __global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
-                           const int32_t* __restrict__ offsets, int32_t* __restrict__ pos) {
+                           const int32_t* __restrict__ offsets, int32_t* __restrict__ pos,
+                           int32_t* __restrict__ list) {
   __shared__ int32_t sh[SC_PTS];
   const int64_t base = (int64_t)blockIdx.x * SC_PTS;
   for (int p = 0; p < 4; ++p) {
@@ -225,7 +226,10 @@ __global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
   const int32_t excl = ts[threadIdx.x] - run + offsets[blockIdx.x];
   for (int p = 0; p < 4; ++p) {
     const int64_t i = base + threadIdx.x * 4 + p;
-    if (i < n) pos[i] = excl + local[p];
+    if (i < n) {
+      pos[i] = excl + local[p];
+      if (sh[threadIdx.x * 4 + p]) list[excl + local[p]] = (int32_t)i;   // active indices, in order
+    }
   }
 }
 
@@ -237,8 +241,9 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
     KView K, int64_t rows, int64_t n, const uint8_t* __restrict__ active,
     const int32_t* __restrict__ pos, const float* __restrict__ w1, const float* __restrict__ w2,
     void* kc_data, int64_t kc_ld, int64_t kc_plane, int64_t chunks_per_block,
-    double2* __restrict__ part) {
+    double2* __restrict__ part, const int64_t* __restrict__ ns_dev, int64_t gather_max) {
   __shared__ double sh[32];
+  if (*ns_dev <= gather_max) return;   // few active points: compact_gather does this
   const int64_t j0 = (int64_t)blockIdx.x * CP_ROWS;
   const int64_t c_begin = (int64_t)blockIdx.y * chunks_per_block;
   const int64_t nchunks = ceil_div(n, (int64_t)CP_T);
@@ -295,10 +300,74 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
   }
 }
 
+// Few active points (at most gather_max): one block per CP_ROWS basis rows
+// walks the list of active indices, reads their kernel values (scattered,
+// one sector each), writes them compacted and reduces the two weighted sums
+// into partial slice 0 (same chunked FP32 -> FP64 promotion as the scan).
+__global__ void __launch_bounds__(CP_T) compact_gather(
+    KView K, int64_t rows, const int32_t* __restrict__ list, const int64_t* __restrict__ ns_dev,
+    int64_t gather_max, const float* __restrict__ w1, const float* __restrict__ w2, void* kc_data,
+    int64_t kc_ld, int64_t kc_plane, double2* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t ns = *ns_dev;
+  if (ns > gather_max) return;
+  const int64_t j0 = (int64_t)blockIdx.x * CP_ROWS;
+  double s1[CP_ROWS], s2[CP_ROWS];
+  float f1[CP_ROWS], f2[CP_ROWS];
+#pragma unroll
+  for (int r = 0; r < CP_ROWS; ++r) { s1[r] = 0.0; s2[r] = 0.0; f1[r] = 0.f; f2[r] = 0.f; }
+  int since = 0;
+  for (int64_t q = threadIdx.x; q < ns; q += CP_T) {
+    const int64_t i = list[q];
+    const float a = w1 ? w1[i] : 0.f, b = w2 ? w2[i] : 0.f;
+#pragma unroll
+    for (int r = 0; r < CP_ROWS; ++r) {
+      const int64_t j = j0 + r;
+      if (j >= rows) break;
+      float v;
+      if (K.format == SPSVM_FP32) {
+        v = static_cast<const float*>(K.data)[j * K.ld + i];
+        if (kc_data) static_cast<float*>(kc_data)[j * kc_ld + q] = v;
+      } else {
+        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(K.data);
+        const __nv_bfloat16 h = src[j * K.ld + i], l = src[K.plane + j * K.ld + i];
+        if (kc_data) {
+          __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(kc_data);
+          dst[j * kc_ld + q] = h;
+          dst[kc_plane + j * kc_ld + q] = l;
+        }
+        v = __bfloat162float(h) + __bfloat162float(l);
+      }
+      f1[r] = fmaf(a, v, f1[r]);
+      f2[r] = fmaf(b, v, f2[r]);
+    }
+    if (++since == 32) {
+#pragma unroll
+      for (int r = 0; r < CP_ROWS; ++r) {
+        s1[r] += (double)f1[r]; s2[r] += (double)f2[r]; f1[r] = 0.f; f2[r] = 0.f;
+      }
+      since = 0;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < CP_ROWS; ++r) { s1[r] += (double)f1[r]; s2[r] += (double)f2[r]; }
+  for (int r = 0; r < CP_ROWS; ++r) {
+    const double a = block_sum(s1[r], sh);
+    __syncthreads();
+    const double b = block_sum(s2[r], sh);
+    __syncthreads();
+    const int64_t j = j0 + r;
+    if (threadIdx.x == 0 && j < rows) part[j] = make_double2(a, b);
+  }
+}
+
+// Sums the partial slices of the path that ran (one slice for the gather).
 __global__ void compact_finish(const double2* __restrict__ part, int64_t ysplit, int64_t rows,
-                               double* w1out, double* w2out) {
+                               double* w1out, double* w2out, const int64_t* __restrict__ ns_dev,
+                               int64_t gather_max) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= rows) return;
+  if (*ns_dev <= gather_max) ysplit = 1;
   double a = 0.0, b = 0.0;
   for (int64_t s = 0; s < ysplit; ++s) {
     const double2 p = part[s * rows + j];
@@ -400,7 +469,8 @@ extern "C" size_t spsvm_compact_scratch_bytes(int64_t n, int64_t rows) {
   // partials for the largest split the launcher may pick (bounded by chunks)
   const int64_t ysplit = ceil_div(n, CP_T) < 1024 ? ceil_div(n, CP_T) : 1024;
   return (size_t)(round_up(scan_blocks_n * 4, 256) +
-                  round_up((ysplit > 0 ? ysplit : 1) * (rows > 0 ? rows : 1) * 16, 256));
+                  round_up((ysplit > 0 ? ysplit : 1) * (rows > 0 ? rows : 1) * 16, 256) +
+                  round_up((n > 0 ? n : 1) * 4, 256));   // list of active indices
 }
 
 extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, const float* w1,
@@ -423,6 +493,12 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
   const int64_t sb = ceil_div(n, SC_PTS);
   int32_t* counts = static_cast<int32_t*>(scratch);
   double2* part = reinterpret_cast<double2*>(static_cast<char*>(scratch) + round_up(sb * 4, 256));
+  const int64_t ysplit_max = ceil_div(n, CP_T) < 1024 ? ceil_div(n, CP_T) : 1024;
+  int32_t* list = reinterpret_cast<int32_t*>(
+      static_cast<char*>(scratch) + round_up(sb * 4, 256) +
+      round_up((ysplit_max > 0 ? ysplit_max : 1) * (K->rows > 0 ? K->rows : 1) * 16, 256));
+  // below this many active points the scattered gather beats the full scan
+  const int64_t gather_max = n / 64;
   if (n == 0) {
     SPSVM_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(int64_t), s));
   } else {
@@ -430,7 +506,7 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
     SPSVM_LAUNCH_CHECK();
     scan_blocks<<<1, 1024, 0, s>>>(counts, sb, n_active);
     SPSVM_LAUNCH_CHECK();
-    scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts, pos);
+    scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts, pos, list);
     SPSVM_LAUNCH_CHECK();
   }
   if (K->rows > 0 && n > 0) {
@@ -442,11 +518,16 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
     dim3 grid((unsigned)ceil_div(K->rows, CP_ROWS), (unsigned)ysplit);
     compact_kernel<<<grid, CP_T, 0, s>>>(view(K), K->rows, n, active, pos, w1, w2,
                                          Kc ? Kc->data : nullptr, Kc ? Kc->ld : 0,
-                                         Kc ? Kc->plane : 0, per, part);
+                                         Kc ? Kc->plane : 0, per, part, n_active, gather_max);
+    SPSVM_LAUNCH_CHECK();
+    compact_gather<<<(unsigned)ceil_div(K->rows, CP_ROWS), CP_T, 0, s>>>(
+        view(K), K->rows, list, n_active, gather_max, w1, w2, Kc ? Kc->data : nullptr,
+        Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, part);
     SPSVM_LAUNCH_CHECK();
     if (w1out || w2out) {
       compact_finish<<<(unsigned)ceil_div(K->rows, 256), 256, 0, s>>>(part, ysplit, K->rows,
-                                                                       w1out, w2out);
+                                                                       w1out, w2out, n_active,
+                                                                       gather_max);
       SPSVM_LAUNCH_CHECK();
     }
   } else if (K->rows > 0) {

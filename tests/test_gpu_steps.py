@@ -156,7 +156,9 @@ def test_outputs_gemv(sp, fmt, n, m):
 
 
 @pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
-@pytest.mark.parametrize("n,m,p", [(5000, 70, 0.5), (1000, 8, 0.0), (1000, 9, 1.0), (777, 64, 0.03)])
+# few active points (at most n / 64) take the gather path, more the scan
+@pytest.mark.parametrize("n,m,p", [(5000, 70, 0.5), (1000, 8, 0.0), (1000, 9, 1.0), (777, 64, 0.03),
+                                   (20000, 70, 0.01), (50000, 130, 0.005), (6400, 20, 0.018)])
 def test_compact_and_masked_products(sp, fmt, n, m, p):
     g = np.random.default_rng(6)
     K = np.exp(-g.random((m, n)) * 3)
