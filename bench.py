@@ -206,6 +206,38 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
                 workers=workers, budget_gb=budget_gb, arrival_rate=20.0)
 
 
+def growth_leg(sp, torch, model, X, y, p, work, opts, stream, holdout=100_000):
+    from paper_1404_1066_gb300 import synth
+    eps = sp._lib.SPSVM_GROWTH_EPS_PAPER
+    Xh, yh = synth.mixture_holdout(p, holdout, seed=88)
+    Xhd = torch.from_numpy(Xh).cuda()
+    n = X.shape[0]
+
+    def acc(m):
+        f = sp.spsvm_predict(m, Xhd).cpu().numpy()
+        return float(np.mean(np.where(f >= 0, 1.0, -1.0) == yh))
+
+    ends = {}
+    for h in model.history():
+        ends[h["basis"]] = h["errors"]
+    curve = [[b, e / n] for b, e in sorted(ends.items())]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ms = sp.spsvm_fit(X, y, p.gamma, p.lam, p.budget, 1e-6, workspace=work,
+                      growth_tol=eps, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    info = ms.info()
+    hist = ms.history()
+    return dict(eps=eps, rounds=info["rounds"], basis=info["n_basis"],
+                fit_s=e0.elapsed_time(e1) / 1e3,
+                train_error=hist[-1]["errors"] / n if hist else None,
+                holdout_accuracy=acc(ms), holdout=holdout,
+                budget_basis=p.budget, budget_holdout_accuracy=acc(model),
+                train_error_vs_basis=curve)
+
+
 def run_micro(args):
     """FP64 Cholesky factorisation and solve of the Newton system alone, at
     the given sizes: random SPD matrices A A^T / m + I / 2 (seeded), one
@@ -389,6 +421,13 @@ def run_ours(args):
     kb_tflops = split * 2.0 * n * J * d / (kb_ms * 1e-3) / 1e12
     del km
 
+    # growth stop of Section 4 at the paper's epsilon, and the accuracy
+    # against |J| of the run to budget (training error after each round,
+    # held-out accuracy at the end) on fresh points of the same mixture
+    growth = None
+    if args.growth:
+        growth = growth_leg(sp, torch, model, X, y, p, work, opts, stream)
+
     # FP32 form on the same workload (one fit), for the "vs FP32 form" leg
     fp32_form = None
     if args.fp32_form and prec != "fp32":
@@ -466,7 +505,7 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, batched=batched, serve=serve)
+                fp32_form=fp32_form, growth_stop=growth, batched=batched, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, factor, cores, sample = cpu_baseline_run(steps=1)
         line["cpu_baseline"] = dict(value=times[0] * factor, unit="s", cores=cores, kind="oracle",
@@ -494,6 +533,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--growth", type=int, default=1,
+                    help="report the growth stop at epsilon = 5e-6 and accuracy vs |J|")
     ap.add_argument("--micro", choices=["cholesky"], default=None,
                     help="time one hot-path step alone instead of the whole fit")
     ap.add_argument("--sizes", default="512,1024,2048,4096")

@@ -63,6 +63,11 @@ extern "C" {
 #define SPSVM_SOLVE_MIXED 0
 #define SPSVM_SOLVE_FP64  1
 
+/* The growth stop's epsilon in the paper's experiments (Section 5): pass it
+ * as spsvm_options.growth_tol to stop growing J when the training error rate
+ * falls by less than this per added basis vector (0 runs to the budget). */
+#define SPSVM_GROWTH_EPS_PAPER 5e-6
+
 /* ---- stored kernel matrix ---------------------------------------------- */
 /* K_nJ stored basis-major: row j (one basis vector) holds k(x_i, x_{J_j})
  * for i = 0..n-1 contiguously.  FP32: element (j, i) at
@@ -249,7 +254,12 @@ int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b, voi
  * overwritten, unlike spsvm_cholesky).  shift >= 0.
  * spsvm_cholesky_mixed converts and factors into work (device, 256-byte
  * aligned, spsvm_mixed_work_bytes(m) bytes); info: device int32, 0 on success,
- * else k+1 for the first non-positive FP32 pivot k.  spsvm_solve_mixed then
+ * else k+1 for the first non-positive FP32 pivot k.  The FP32 factor L is
+ * the lower triangle of the first m rows x round_up(m, 4) floats of work
+ * (row-major); the upper triangle of each 64 x 64 diagonal block holds that
+ * block's inverse, transposed.  The factorisation is one launch over
+ * 64 x 64 tiles whose bounded waits give up after about a second
+ * (spsvm_device_status then reports TIMEOUT).  spsvm_solve_mixed then
  * solves for b (device FP64, m) into x (device FP64, m) with the factor in
  * work; it synchronises the stream once per refinement step and returns OK,
  * or SPSVM_ERR_NO_CONVERGE when the residual stops shrinking (by half per

@@ -393,6 +393,7 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
         rnd += 1
         E = float(np.mean(y * o <= 0))
+        res.rounds[-1]["error_rate"] = E
         if growth_tol > 0 and (E_prev - E) / len(chosen) < growth_tol:
             break
         E_prev = E

@@ -25,6 +25,7 @@ SPSVM_FP32 = 0
 SPSVM_BF16X3 = 1
 SPSVM_SOLVE_MIXED = 0
 SPSVM_SOLVE_FP64 = 1
+SPSVM_GROWTH_EPS_PAPER = 5e-6
 
 PRECISIONS = {"fp32": SPSVM_FP32, "bf16x3": SPSVM_BF16X3}
 

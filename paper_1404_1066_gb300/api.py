@@ -248,6 +248,20 @@ def spsvm_solve_mixed(H: torch.Tensor, b: torch.Tensor, shift=0.0, max_iter=30, 
     return 0, st, x, it.value, be.value
 
 
+def spsvm_cholesky_mixed(H: torch.Tensor, shift=0.0):
+    """FP32 Cholesky factor of H + shift I (H FP64, full symmetric, not
+    overwritten).  Returns (info, L): L is the m x round_up(m, 4) FP32 view
+    of the work buffer whose lower triangle holds the factor."""
+    m = H.shape[0]
+    wb = _lib().spsvm_mixed_work_bytes(m)
+    work = torch.empty(max(256, wb), dtype=torch.uint8, device=H.device)
+    info = torch.zeros(1, dtype=torch.int32, device=H.device)
+    check(_lib().spsvm_cholesky_mixed(ptr(H), m, H.stride(0), float(shift), ptr(info), ptr(work),
+                                      wb, stream_ptr()), "spsvm_cholesky_mixed")
+    ldl = (m + 3) // 4 * 4
+    return int(info.item()), work[:m * ldl * 4].view(torch.float32).view(m, ldl)
+
+
 def spsvm_cholesky_solve(Lf: torch.Tensor, b: torch.Tensor):
     wb = _lib().spsvm_cholesky_solve_work_bytes(Lf.shape[0])
     work = torch.empty(max(16, wb), dtype=torch.uint8, device=Lf.device)

@@ -503,152 +503,315 @@ __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ 
   }
 }
 
-// FP32 panel step in one launch: every CTA factors the PB x PB diagonal
-// block at k0 with its first warp (registers and shuffles; the same
-// instructions on the same data in every CTA, so every copy is the same
-// bits), CTA 0 stores it, and all CTAs solve their 32 rows below it
-// (L[r][k0:k0+PB] = H[r][k0:k0+PB] L_kk^{-T}, four threads per row as in
-// trsm_panel).  Replaces a factor launch and a solve launch per panel.
-__global__ void __launch_bounds__(PT) panel32(float* __restrict__ H, int64_t ldh, int64_t m,
-                                              int64_t k0, int32_t* __restrict__ info,
-                                              float* __restrict__ diag_out) {
-  __shared__ float Ls[PB][PB + 1];
-  __shared__ float rd[PB];
-  __shared__ int fail_s;
-  if (*info != 0) return;
-  const int nb = (int)min64(PB, m - k0);
+// ---------------------------------------------------------------------------
+// FP32 factor in one persistent launch over 64 x 64 tiles, left-looking.
+// Tile (i, j), i >= j, is C_ij - sum_{k<j} L_ik L_jk^T, then the factor of
+// the diagonal tile (i == j) or the solve X L_jj^T = C (i > j).  CTAs take
+// tiles by ticket, column by column with the diagonal tile first, so a tile
+// only waits for tiles with smaller tickets, which running CTAs hold or have
+// finished: the schedule progresses whatever the number of resident CTAs,
+// and columns overlap without a launch boundary between them.  A finished
+// tile publishes its flag (1 done, 2 abandoned); waits are bounded, and an
+// abandoned or timed-out dependency abandons the tile.
+// ---------------------------------------------------------------------------
+constexpr int DT = 64;          // tile
+constexpr int DP = DT + 4;      // staging rows, 16-byte aligned
+constexpr int DAG_T = 256;
+constexpr size_t DAG_SMEM = (size_t)4 * DT * DP * sizeof(float);   // two stages of (A, B)
+
+__host__ __device__ __forceinline__ int64_t dag_col_start(int64_t T, int64_t j) {
+  return j * T - j * (j - 1) / 2;   // tiles in columns 0 .. j-1
+}
+
+// Rows r0 .. r0+63 (zeros past m), columns c0 .. c0+63 of L as 16-byte
+// vectors; a warp covers 8 rows x 64 contiguous bytes per vector.
+__device__ __forceinline__ void dag_load(float4 (&v)[4], const float* __restrict__ L, int64_t ldl,
+                                         int64_t m, int64_t r0, int64_t c0) {
   const int t = threadIdx.x, lane = t & 31;
-  if (t < 32) {
-    float a[PB];
 #pragma unroll
-    for (int c = 0; c < PB; ++c)
-      a[c] = (lane < nb && c <= lane) ? H[(k0 + lane) * ldh + k0 + c] : (c == lane ? 1.0f : 0.0f);
-    int fail = 0;
-#pragma unroll
-    for (int j = 0; j < PB; ++j) {
-      if (j < nb && fail == 0) {
-        const float d = __shfl_sync(0xffffffffu, a[j], j);
-        if (!(d > 0.0f) || !(d < 3.0e38f)) {
-          fail = j + 1;
-        } else {
-          const float y = rsqrt_t(d);
-          if (lane == j) a[j] = d * y;
-          else if (lane > j) a[j] *= y;
-          // all of the column's shuffles first (independent, issued back to
-          // back), then the updates
-          float col[PB];
-#pragma unroll
-          for (int l = j + 1; l < PB; ++l) col[l] = __shfl_sync(0xffffffffu, a[j], l);
-#pragma unroll
-          for (int l = j + 1; l < PB; ++l)
-            if (lane >= l) a[l] = fmaf(-a[j], col[l], a[l]);
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < PB; ++c) Ls[lane][c] = (c <= lane) ? a[c] : 0.0f;
-    if (lane == 0) fail_s = fail;
-    // CTA 0 keeps the factor: in diag_out when a trailing update follows
-    // (it copies it into place; other CTAs of this launch may still be
-    // reading the unfactored block), in place for the last panel (one CTA)
-    if (blockIdx.x == 0 && fail == 0 && lane < nb) {
-      const bool last = m - k0 <= PB;
-      float* dst = last ? H + (k0 + lane) * ldh + k0 : diag_out + lane * PB;
-#pragma unroll
-      for (int c = 0; c < PB; ++c)
-        if (c <= lane) dst[c] = a[c];
-    }
-  }
-  __syncthreads();
-  if (fail_s) {
-    if (blockIdx.x == 0 && t == 0) *info = (int32_t)(k0 + fail_s);
-    return;
-  }
-  if (t < PB) rd[t] = 1.0f / Ls[t][t];
-  __syncthreads();
-  const int q = t & 3;
-  const int64_t r = k0 + PB + (int64_t)blockIdx.x * (PT / 4) + (t >> 2);
-  const bool ok = r < m;
-  float* row = H + (ok ? r : k0) * ldh + k0;
-  float x[PB / 4];
-#pragma unroll
-  for (int i = 0; i < PB / 4; ++i) x[i] = ok ? row[q + 4 * i] : 0.0f;
-#pragma unroll
-  for (int j = 0; j < PB; ++j) {
-    const int owner = j & 3, ji = j >> 2;
-    if (q == owner) x[ji] *= rd[j];
-    const float xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
-#pragma unroll
-    for (int i = ji; i < PB / 4; ++i)
-      if (q + 4 * i > j) x[i] = fmaf(-xj, Ls[q + 4 * i][j], x[i]);
-  }
-  if (ok) {
-#pragma unroll
-    for (int i = 0; i < PB / 4; ++i) row[q + 4 * i] = x[i];
+  for (int u = 0; u < 4; ++u) {
+    const int w = (t >> 5) + 8 * u;
+    const int row = 8 * (w & 7) + (lane & 7), c4 = 4 * (w >> 3) + (lane >> 3);
+    const int64_t gr = r0 + row;
+    v[u] = gr < m ? __ldcg(reinterpret_cast<const float4*>(L + gr * ldl + c0) + c4)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
-// FP32 trailing update A[r][c] -= sum_l L[r][k0+l] L[c][k0+l], r >= c >= k0 + PB,
-// over 64 x 64 lower tiles: 256 threads, a 4 x 4 register block each (rows
-// 4 ty .. +3, columns 4 tx .. +3), the panel strips in shared memory read
-// as 16-byte vectors (two shared loads per 16 FMAs).
-constexpr int SY_T = 64;
-constexpr int SY_P = SY_T + 4;   // 16-byte aligned strip rows
-__global__ void __launch_bounds__(256) syrk32_tile64(float* __restrict__ H, int64_t ldh, int64_t m,
-                                                     int64_t k0, const int32_t* __restrict__ info,
-                                                     const float* __restrict__ diag_in) {
-  __shared__ __align__(16) float Ar[PB][SY_P];   // Ar[l][rr] = L[r0 + rr][k0 + l]
-  __shared__ __align__(16) float Ac[PB][SY_P];   // Ac[l][cc] = L[c0 + cc][k0 + l]
-  if (*info != 0) return;
-  if (blockIdx.x == 0) {   // the panel's diagonal factor into place (not read here)
-    for (int e = threadIdx.x; e < PB * PB; e += 256) {
-      const int rr = e / PB, cc = e % PB;
-      if (cc <= rr) H[(k0 + rr) * ldh + k0 + cc] = diag_in[rr * PB + cc];
-    }
+// S[l][r] = tile[r][l] (transposed, so the update reads 16-byte vectors).
+__device__ __forceinline__ void dag_stage(float (*S)[DP], const float4 (&v)[4]) {
+  const int t = threadIdx.x, lane = t & 31;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int w = (t >> 5) + 8 * u;
+    const int row = 8 * (w & 7) + (lane & 7), c4 = 4 * (w >> 3) + (lane >> 3);
+    S[4 * c4 + 0][row] = v[u].x;
+    S[4 * c4 + 1][row] = v[u].y;
+    S[4 * c4 + 2][row] = v[u].z;
+    S[4 * c4 + 3][row] = v[u].w;
   }
-  const int64_t base = k0 + PB;
-  const int64_t ntile = ceil_div(m - base, (int64_t)SY_T);
-  int64_t tt = blockIdx.x, ti = 0;
-  while (tt > ti) {
-    tt -= ti + 1;
-    ++ti;
-  }
-  const int64_t tj = tt;
-  if (ti >= ntile) return;
-  const int64_t r0 = base + ti * SY_T, c0 = base + tj * SY_T;
-  for (int e = threadIdx.x; e < SY_T * PB; e += 256) {
-    const int rr = e / PB, ll = e % PB;
-    const int64_t gr = r0 + rr, gc = c0 + rr;
-    Ar[ll][rr] = (gr < m) ? H[gr * ldh + k0 + ll] : 0.0f;
-    Ac[ll][rr] = (gc < m) ? H[gc * ldh + k0 + ll] : 0.0f;
-  }
-  __syncthreads();
+}
+
+// acc[a][b] -= sum_l A^T[l][4 ty + a] B^T[l][4 tx + b]
+__device__ __forceinline__ void dag_update(float (&acc)[4][4], const float (*A)[DP],
+                                           const float (*B)[DP]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
 #pragma unroll 8
-  for (int l = 0; l < PB; ++l) {
-    const float4 av = *reinterpret_cast<const float4*>(&Ar[l][4 * ty]);
-    const float4 bv = *reinterpret_cast<const float4*>(&Ac[l][4 * tx]);
+  for (int l = 0; l < DT; ++l) {
+    const float4 av = *reinterpret_cast<const float4*>(&A[l][4 * ty]);
+    const float4 bv = *reinterpret_cast<const float4*>(&B[l][4 * tx]);
     const float ar[4] = {av.x, av.y, av.z, av.w};
     const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(-ar[a], br[b], acc[a][b]);
+  }
+}
+
+// Factor of the 32 x 32 lower block of S at (o, o), one warp, lane = row:
+// returns the 1-based column of a non-positive pivot, 0 on success.
+__device__ __forceinline__ int dag_potrf32(float (*S)[DT + 1], int o) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? S[o + lane][o + c] : 0.0f;
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (fail == 0) {
+      const float d = __shfl_sync(0xffffffffu, a[j], j);
+      if (!(d > 0.0f) || !(d < 3.0e38f)) {
+        fail = j + 1;
+      } else {
+        const float y = rsqrt_t(d);
+        if (lane == j) a[j] = d * y;
+        else if (lane > j) a[j] *= y;
+        float col[32];
+#pragma unroll
+        for (int l = j + 1; l < 32; ++l) col[l] = __shfl_sync(0xffffffffu, a[j], l);
+#pragma unroll
+        for (int l = j + 1; l < 32; ++l)
+          if (lane >= l) a[l] = fmaf(-a[j], col[l], a[l]);
+      }
+    }
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t r = r0 + 4 * ty + a;
-    if (r >= m) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t c = c0 + 4 * tx + b;
-      if (c <= r) H[r * ldh + c] -= acc[a][b];
+  for (int c = 0; c < 32; ++c)
+    if (c <= lane) S[o + lane][o + c] = a[c];
+  return fail;
+}
+
+__device__ __forceinline__ unsigned dag_poll2(const unsigned* f1, const unsigned* f2) {
+  const unsigned a = ld_acquire_u32(f1), b = ld_acquire_u32(f2);
+  if (a == 2u || b == 2u) return 2u;
+  return (a == 1u && b == 1u) ? 1u : 0u;
+}
+
+__device__ __forceinline__ unsigned dag_wait2(const unsigned* f1, const unsigned* f2, int code) {
+  const unsigned a = wait_flag(f1, code);
+  const unsigned b = (f2 == f1 || a != 1u) ? a : wait_flag(f2, code);
+  return (a == 1u && b == 1u) ? 1u : 2u;
+}
+
+__global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
+                                                      int64_t T, unsigned* __restrict__ flags,
+                                                      unsigned* __restrict__ ticket,
+                                                      int32_t* __restrict__ info) {
+  extern __shared__ __align__(16) float dag_smem[];
+  float (*As)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem);
+  float (*Bs)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem + 2 * DT * DP);
+  float (*S)[DT + 1] = reinterpret_cast<float (*)[DT + 1]>(dag_smem);   // within As[0]
+  __shared__ int64_t tile_s[2];
+  __shared__ unsigned nxt_s[2], st_s;
+  __shared__ float rd[DT];
+  __shared__ int fail_s;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4, lane = t & 31;
+  const int64_t ntiles = T * (T + 1) / 2;
+  for (;;) {
+    if (t == 0) {
+      const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
+      int64_t i = 0, j = -1;
+      if (tk < ntiles) {
+        const float b = 2.0f * (float)T + 1.0f;
+        j = (int64_t)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)tk, 0.0f))));
+        j = j < 0 ? 0 : (j > T - 1 ? T - 1 : j);
+        while (j + 1 < T && dag_col_start(T, j + 1) <= tk) ++j;
+        while (j > 0 && dag_col_start(T, j) > tk) --j;
+        i = j + (tk - dag_col_start(T, j));
+      }
+      tile_s[0] = i;
+      tile_s[1] = j;
     }
+    __syncthreads();
+    const int64_t i = tile_s[0], j = tile_s[1];
+    if (j < 0) return;
+    const bool diag = i == j;
+    const int64_t r0 = i * DT, c0 = j * DT;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * ty + a;
+      const int64_t gr = r0 + r;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = 4 * tx + b;
+        const int64_t gc = c0 + c;
+        float v = 0.0f;
+        if (gr < m && gc < m && (!diag || c <= r)) v = __ldcg(L + gr * ldl + gc);
+        if (diag && r == c && gr >= m) v = 1.0f;   // identity past m in the last diagonal tile
+        acc[a][b] = v;
+      }
+    }
+    bool ok = true;
+    if (j > 0) {
+      if (t == 0) st_s = dag_wait2(&flags[i * T], &flags[j * T], 23);
+      __syncthreads();
+      ok = st_s == 1u;
+      float4 pa[4], pb[4];
+      if (ok) {
+        dag_load(pa, L, ldl, m, r0, 0);
+        if (!diag) dag_load(pb, L, ldl, m, c0, 0);
+      }
+      for (int64_t k = 0; ok && k < j; ++k) {
+        const int sb = (int)(k & 1);
+        dag_stage(As[sb], pa);
+        if (!diag) dag_stage(Bs[sb], pb);
+        if (t == 0)
+          nxt_s[sb] = (k + 1 < j) ? dag_poll2(&flags[i * T + k + 1], &flags[j * T + k + 1]) : 0u;
+        __syncthreads();
+        const unsigned nx = nxt_s[sb];
+        if (nx == 1u) {   // next tiles ready: their loads overlap this update
+          dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
+          if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
+        }
+        dag_update(acc, As[sb], diag ? As[sb] : Bs[sb]);
+        if (k + 1 < j && nx != 1u) {
+          if (nx == 2u) {
+            ok = false;
+          } else {
+            if (t == 0) st_s = dag_wait2(&flags[i * T + k + 1], &flags[j * T + k + 1], 23);
+            __syncthreads();
+            if (st_s != 1u) {
+              ok = false;
+            } else {
+              dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
+              if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();   // staging buffers free
+    if (ok && diag) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) S[4 * ty + a][4 * tx + b] = acc[a][b];
+      if (t == 0) fail_s = 0;
+      __syncthreads();
+      if (t < 32) {
+        const int f = dag_potrf32(S, 0);
+        if (lane == 0) fail_s = f;
+      }
+      __syncthreads();
+      if (fail_s == 0) {
+        if (t < 32) rd[t] = 1.0f / S[t][t];
+        __syncthreads();
+        if (t < 128) {   // S21 <- S21 L11^{-T}, four threads per row
+          const int r = 32 + (t >> 2), q = t & 3;
+          float x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = S[r][q + 4 * u];
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int owner = jj & 3, ji = jj >> 2;
+            if (q == owner) x[ji] *= rd[jj];
+            const float xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
+#pragma unroll
+            for (int u = ji; u < 8; ++u)
+              if (q + 4 * u > jj) x[u] = fmaf(-xj, S[q + 4 * u][jj], x[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) S[r][q + 4 * u] = x[u];
+        }
+        __syncthreads();
+        {   // S22 -= S21 S21^T (lower)
+          const int r = 32 + (t >> 3), cg = t & 7;
+          float sacc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+          for (int l = 0; l < 32; ++l) {
+            const float h = S[r][l];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sacc[e] = fmaf(h, S[32 + 4 * cg + e][l], sacc[e]);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (32 + 4 * cg + e <= r) S[r][32 + 4 * cg + e] -= sacc[e];
+        }
+        __syncthreads();
+        if (t < 32) {
+          const int f = dag_potrf32(S, 32);
+          if (lane == 0 && f) fail_s = 32 + f;
+        }
+        __syncthreads();
+      }
+      if (fail_s != 0) {
+        if (t == 0) atomicCAS(info, 0, (int32_t)(c0 + fail_s));
+        ok = false;
+      } else {
+        for (int e = t; e < DT * DT; e += DAG_T) {
+          const int r = e / DT, c = e % DT;
+          if (c <= r && r0 + r < m) __stcg(L + (r0 + r) * ldl + c0 + c, S[r][c]);
+        }
+      }
+    } else if (ok) {
+      if (t == 0) st_s = wait_flag(&flags[j * T + j], 24);
+      __syncthreads();
+      if (st_s != 1u) {
+        ok = false;
+      } else {
+        float4 pd[4];
+        dag_load(pd, L, ldl, m, c0, c0);   // j < T - 1: a full tile
+        dag_stage(As[0], pd);              // As[0][c][r] = L_jj[r][c]
+        __syncthreads();
+        if (t < DT) rd[t] = 1.0f / As[0][t][t];
+        __syncthreads();
+        // X L_jj^T = C column by column; column c's owner (tx = c / 4) scales
+        // it, its row group (a half warp) takes it by shuffle
+        for (int c4 = 0; c4 < DT / 4; ++c4) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 4 * c4 + e;
+            if (tx == c4) {
+#pragma unroll
+              for (int a = 0; a < 4; ++a) acc[a][e] *= rd[c];
+            }
+            float xv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xv[a] = __shfl_sync(0xffffffffu, acc[a][e], (lane & 16) | c4);
+            const float4 lv = *reinterpret_cast<const float4*>(&As[0][c][4 * tx]);
+            const float lb[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (4 * tx + b > c) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a][b] = fmaf(-xv[a], lb[b], acc[a][b]);
+              }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int64_t gr = r0 + 4 * ty + a;
+          if (gr < m)
+            __stcg(reinterpret_cast<float4*>(L + gr * ldl + c0 + 4 * tx),
+                   make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
+        }
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) st_release_u32(&flags[i * T + j], ok ? 1u : 2u);
   }
 }
 
@@ -959,7 +1122,8 @@ namespace {
 
 struct MixedLayout {
   int64_t ldl, B, nrow_blocks, nvec_blocks;
-  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, diag, total;
+  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, dag, total;
+  int64_t tiles;   // tile rows of the factor
 };
 
 MixedLayout mixed_layout(int64_t m) {
@@ -979,7 +1143,8 @@ MixedLayout mixed_layout(int64_t m) {
   ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
   ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
   ly.norms = off;  off += al(8 * 8);
-  ly.diag = off;   off += al((size_t)PB * PB * 4);   // a panel's diagonal factor in transit
+  ly.tiles = ceil_div(m, (int64_t)DT);
+  ly.dag = off;    off += al((size_t)(ly.tiles * ly.tiles + 1) * 4);   // tile flags, ticket
   ly.total = off;
   return ly;
 }
@@ -1001,20 +1166,17 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   ProfScope prof(PROF_CHOLESKY, s, (double)m * m * m / 3.0);
   char* w = static_cast<char*>(work);
   float* L = reinterpret_cast<float*>(w + ly.L);
-  float* diagbuf = reinterpret_cast<float*>(w + ly.diag);
+  unsigned* dflags = reinterpret_cast<unsigned*>(w + ly.dag);
+  const int64_t T = ly.tiles, ntiles = T * (T + 1) / 2;
+  SPSVM_CUDA_TRY(cudaMemsetAsync(dflags, 0, (size_t)(T * T + 1) * 4, s));
   to_f32_shift<<<(unsigned)m, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
                                             reinterpret_cast<double*>(w + ly.rowmax));
   SPSVM_LAUNCH_CHECK();
-  for (int64_t k0 = 0; k0 < m; k0 += PB) {
-    const int64_t below = m - (k0 + PB);
-    panel32<<<(unsigned)(below > 0 ? ceil_div(below, (int64_t)(PT / 4)) : 1), PT, 0, s>>>(
-        L, ly.ldl, m, k0, info, diagbuf);
-    SPSVM_LAUNCH_CHECK();
-    if (below <= 0) break;
-    const int64_t nt = ceil_div(below, (int64_t)SY_T);
-    syrk32_tile64<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(L, ly.ldl, m, k0, info, diagbuf);
-    SPSVM_LAUNCH_CHECK();
-  }
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(chol32_dag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DAG_SMEM));
+  chol32_dag<<<(unsigned)min64(ntiles, 2 * (int64_t)sm_count()), DAG_T, DAG_SMEM, s>>>(
+      L, ly.ldl, m, T, dflags, dflags + T * T, info);
+  SPSVM_LAUNCH_CHECK();
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;

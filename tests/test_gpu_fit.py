@@ -86,6 +86,52 @@ def test_growth_replay_mixture(sp, prec):
     _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
 
 
+def test_growth_stop_replay_mixture(sp):
+    """Section 4's growth stop on the GPU.  The per-round training error
+    rates of a run to budget, replayed by the oracle, fix where the rule
+    stops for each epsilon; epsilon is put in a gap between the drops per
+    vector wider than the drop can move when the FP32 outputs flip two
+    points near the margin.  The stopped run must end at that round, with
+    the budget run's basis, and its own error counts must give the same
+    decision."""
+    p = synth.gaussian_mixture(n=3000, d=16, budget=320, seed=11, lam=1e-3)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    n, q = len(p.y), 64
+    kw = dict(precision="fp32", candidates=128, add_per_round=q, seed=77, record=True)
+    m = sp.spsvm_fit(X, y, p.gamma, p.lam, 320, 1e-8, **kw)
+    R = m.info()["rounds"]
+    assert R == 5
+    rep = [dict(candidates=c, chosen=ch) for c, ch in (m.round(k) for k in range(R))]
+    r = O.fit(p.X, p.y, p.gamma, p.lam, 320, tol=1e-10, kappa=128, q=q, seed=77, replay=rep,
+              replay_rtol=1e-4)
+    E = [1.0] + [rd["error_rate"] for rd in r.rounds]
+    ends = {}
+    for h in m.history():
+        ends[h["basis"]] = h["errors"]
+    Eg = [1.0] + [ends[q * (k + 1)] / n for k in range(R)]
+    assert max(abs(a - b) for a, b in zip(E, Eg)) <= 2.0 / n
+    drop = [(E[k] - E[k + 1]) / q for k in range(R)]
+    slack = 4.0 / (n * q)
+
+    def stop_round(d, eps):
+        return next((k + 1 for k, v in enumerate(d) if v < eps), len(d))
+
+    srt = sorted(set(drop))
+    picks = [0.5 * (a + b) for a, b in zip(srt, srt[1:]) if b - a > 4 * slack]
+    picks = [e for e in picks if 2 <= stop_round(drop, e) < R]
+    assert picks, drop
+    eps = picks[0]
+    want = stop_round(drop, eps)
+    assert stop_round([(Eg[k] - Eg[k + 1]) / q for k in range(R)], eps) == want
+    ms = sp.spsvm_fit(X, y, p.gamma, p.lam, 320, 1e-8, growth_tol=eps, **kw)
+    info = ms.info()
+    assert info["rounds"] == want and info["n_basis"] == q * want
+    J_full, _ = m.basis_and_beta()
+    J_stop, _ = ms.basis_and_beta()
+    np.testing.assert_array_equal(J_stop, J_full[:q * want])
+
+
 def test_fit_argument_errors(sp):
     X = torch.zeros((10, 3), device="cuda")
     y = torch.ones(10, device="cuda")

@@ -290,6 +290,32 @@ def test_mixed_solve_reaches_fp64_backward_error(sp, m, shift):
     assert np.linalg.norm(xs - xr) <= 1e-10 * np.linalg.norm(xr) * max(1.0, np.linalg.cond(Hs) * 1e-4)
 
 
+@pytest.mark.parametrize("m", [1, 63, 64, 65, 200, 1000, 4100])
+def test_mixed_factor_meets_fp32_cholesky_backward_error(sp, m):
+    """The FP32 factor of H + shift I from the tiled factorisation obeys the
+    componentwise backward-error bound of Cholesky in precision u = 2^-24
+    (Higham, Accuracy and Stability, Thm 10.3): |L L^T - A| <= g |L| |L|^T
+    with g = (m + 1) u / (1 - (m + 1) u), plus u |A| for rounding A to FP32.
+    A wrong tile (a transposed operand, a missed update) breaks it by orders
+    of magnitude; ragged sizes cover the identity-padded last tile."""
+    g = np.random.default_rng(m)
+    A = g.standard_normal((m, m + 4)) / np.sqrt(m + 4)
+    H = A @ A.T + 0.05 * np.eye(m)
+    shift = 0.01
+    info, Lw = sp.spsvm_cholesky_mixed(_t(H), shift)
+    assert info == 0
+    Lf = np.tril(Lw[:, :m].cpu().numpy().astype(np.float64))
+    Ash = H + shift * np.eye(m)
+    u = 2.0 ** -24
+    gam = (m + 1) * u / (1 - (m + 1) * u)
+    bound = gam * (np.abs(Lf) @ np.abs(Lf).T) + u * np.abs(Ash)
+    err = np.abs(Lf @ Lf.T - Ash)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # and it is the factor: compare with the FP64 factor (condition ~ 1e2)
+    R = np.linalg.cholesky(Ash)
+    assert np.max(np.abs(Lf - R)) <= 1e-4 * np.max(np.abs(R))
+
+
 def test_mixed_solve_reports_fp32_breakdown_and_stagnation(sp):
     H = np.eye(100)
     H[70, 70] = -1.0

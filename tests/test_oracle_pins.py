@@ -284,6 +284,30 @@ def test_fit_growth_rounds():
     assert np.mean(O.labels(r.o) == y) > 0.8
 
 
+def test_growth_stop_rule():
+    """Section 4's growth stop: after each round, stop when the drop in the
+    training error rate divided by the number of vectors added falls below
+    epsilon.  The rate starts at 1 (at beta = 0 every y_i o_i = 0 counts as
+    an error).  A run to budget fixes the per-round rates; for each epsilon
+    the stopped run must end at the first round whose drop per vector is
+    below it, with the budget run's basis up to there."""
+    X, y = _blobs(400, 4, 22, sep=1.2)
+    full = O.fit(X, y, 0.25, 1e-3, 96, tol=1e-10, kappa=32, q=16, seed=9)
+    E = [1.0] + [rd["error_rate"] for rd in full.rounds]
+    # the last recorded rate is the training error of the final decision values
+    dec_vals = O.predict(X, X[full.J], full.beta, 0.25)
+    assert E[-1] == np.mean(y * dec_vals <= 0)
+    drop = [(E[k] - E[k + 1]) / 16 for k in range(len(full.rounds))]
+    stops = set()
+    for eps in (1.0, 1e-3, 5e-4, 1e-9):
+        want = next((k + 1 for k, d in enumerate(drop) if d < eps), len(drop))
+        stops.add(want)
+        r = O.fit(X, y, 0.25, 1e-3, 96, tol=1e-10, kappa=32, q=16, seed=9, growth_tol=eps)
+        assert len(r.rounds) == want
+        np.testing.assert_array_equal(r.J, full.J[:16 * want])
+    assert len(stops) >= 3   # the epsilons exercise different rounds
+
+
 def test_replay_adopts_other_choice_and_rejects_bad_one():
     X, y = _blobs(200, 3, 30)
     r = O.fit(X, y, 0.3, 1e-3, 32, tol=1e-10, kappa=24, q=16, seed=4)
