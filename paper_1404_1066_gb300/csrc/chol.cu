@@ -569,61 +569,55 @@ __device__ __forceinline__ void dag_update(float (&acc)[4][4], const float (*A)[
   }
 }
 
-// Factor of the 32 x 32 lower block of S at (o, o), one warp, lane = row:
-// returns the 1-based column of a non-positive pivot, 0 on success.
-__device__ __forceinline__ int dag_potrf32(float (*S)[DT + 1], int o) {
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Warp 0: the first k in [k0, j) whose flags (i, k) or (j, k) are not yet
+// done (j if all are), by relaxed loads 32 at a time, followed by an acquire
+// fence for the flags seen done; -1 if that first flag is abandoned.  Waits,
+// bounded, while the flag at k0 itself is not done.
+__device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __restrict__ fj,
+                            int64_t k0, int64_t j, int code) {
   const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? S[o + lane][o + c] : 0.0f;
-  int fail = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (fail == 0) {
-      const float d = __shfl_sync(0xffffffffu, a[j], j);
-      if (!(d > 0.0f) || !(d < 3.0e38f)) {
-        fail = j + 1;
-      } else {
-        const float y = rsqrt_t(d);
-        if (lane == j) a[j] = d * y;
-        else if (lane > j) a[j] *= y;
-        float col[32];
-#pragma unroll
-        for (int l = j + 1; l < 32; ++l) col[l] = __shfl_sync(0xffffffffu, a[j], l);
-#pragma unroll
-        for (int l = j + 1; l < 32; ++l)
-          if (lane >= l) a[l] = fmaf(-a[j], col[l], a[l]);
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    int64_t r = j;
+    for (int64_t base = k0; base < j; base += 32) {
+      const int64_t k = base + lane;
+      unsigned a = 1u, b = 1u;
+      if (k < j) {
+        a = ld_relaxed_u32(fi + k);
+        b = ld_relaxed_u32(fj + k);
+      }
+      const unsigned notdone = __ballot_sync(0xffffffffu, !(a == 1u && b == 1u));
+      if (notdone) {
+        const int first = __ffs(notdone) - 1;
+        const unsigned bad = __ballot_sync(0xffffffffu, a == 2u || b == 2u);
+        r = (bad >> first) & 1u ? -1 : base + first;
+        break;
       }
     }
+    if (r != k0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      return r;
+    }
+    if (it >= 16) __nanosleep(64);
   }
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c <= lane) S[o + lane][o + c] = a[c];
-  return fail;
+  if (lane == 0) atomicCAS(&g_sv_status, 0, code);
+  return -1;
 }
 
-__device__ __forceinline__ unsigned dag_poll2(const unsigned* f1, const unsigned* f2) {
-  const unsigned a = ld_acquire_u32(f1), b = ld_acquire_u32(f2);
-  if (a == 2u || b == 2u) return 2u;
-  return (a == 1u && b == 1u) ? 1u : 0u;
-}
-
-__device__ __forceinline__ unsigned dag_wait2(const unsigned* f1, const unsigned* f2, int code) {
-  const unsigned a = wait_flag(f1, code);
-  const unsigned b = (f2 == f1 || a != 1u) ? a : wait_flag(f2, code);
-  return (a == 1u && b == 1u) ? 1u : 2u;
-}
-
-__global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
+__global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
                                                       int64_t T, unsigned* __restrict__ flags,
                                                       unsigned* __restrict__ ticket,
                                                       int32_t* __restrict__ info) {
   extern __shared__ __align__(16) float dag_smem[];
   float (*As)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem);
   float (*Bs)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem + 2 * DT * DP);
-  float (*S)[DT + 1] = reinterpret_cast<float (*)[DT + 1]>(dag_smem);   // within As[0]
-  __shared__ int64_t tile_s[2];
-  __shared__ unsigned nxt_s[2], st_s;
+  __shared__ int64_t tile_s[2], rdy_s;
+  __shared__ unsigned st_s;
   __shared__ float rd[DT];
   __shared__ int fail_s;
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4, lane = t & 31;
@@ -665,9 +659,16 @@ __global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, in
     }
     bool ok = true;
     if (j > 0) {
-      if (t == 0) st_s = dag_wait2(&flags[i * T], &flags[j * T], 23);
+      // rdy: the first k whose tiles are not known to be done
+      const unsigned* fi = flags + i * T;
+      const unsigned* fj = flags + j * T;
+      if (t < 32) {
+        const int64_t r = dag_scan(fi, fj, 0, j, 23);
+        if (t == 0) rdy_s = r;
+      }
       __syncthreads();
-      ok = st_s == 1u;
+      int64_t rdy = rdy_s;
+      ok = rdy > 0;
       float4 pa[4], pb[4];
       if (ok) {
         dag_load(pa, L, ldl, m, r0, 0);
@@ -677,92 +678,113 @@ __global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, in
         const int sb = (int)(k & 1);
         dag_stage(As[sb], pa);
         if (!diag) dag_stage(Bs[sb], pb);
-        if (t == 0)
-          nxt_s[sb] = (k + 1 < j) ? dag_poll2(&flags[i * T + k + 1], &flags[j * T + k + 1]) : 0u;
         __syncthreads();
-        const unsigned nx = nxt_s[sb];
-        if (nx == 1u) {   // next tiles ready: their loads overlap this update
+        const bool pre = k + 1 < rdy;
+        if (pre) {   // next tiles known done: their loads overlap this update
           dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
           if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
         }
         dag_update(acc, As[sb], diag ? As[sb] : Bs[sb]);
-        if (k + 1 < j && nx != 1u) {
-          if (nx == 2u) {
+        if (k + 1 < j && !pre) {
+          if (t < 32) {
+            const int64_t r = dag_scan(fi, fj, k + 1, j, 23);
+            if (t == 0) rdy_s = r;
+          }
+          __syncthreads();
+          rdy = rdy_s;
+          if (rdy < 0) {
             ok = false;
           } else {
-            if (t == 0) st_s = dag_wait2(&flags[i * T + k + 1], &flags[j * T + k + 1], 23);
-            __syncthreads();
-            if (st_s != 1u) {
-              ok = false;
-            } else {
-              dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
-              if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
-            }
+            dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
+            if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
           }
         }
       }
     }
     __syncthreads();   // staging buffers free
+    // The tile stays in registers (thread (ty, tx): rows 4 ty .. +3, columns
+    // 4 tx .. +3); both epilogues go right-looking over 16 pivot blocks of 4
+    // columns, so a pivot costs a few dependent instructions in one thread
+    // and a barrier, not a chain of shuffles.
+    float4* Xb = reinterpret_cast<float4*>(dag_smem + 2 * DT * DP);   // [2][DT] rows, in Bs
     if (ok && diag) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) S[4 * ty + a][4 * tx + b] = acc[a][b];
       if (t == 0) fail_s = 0;
-      __syncthreads();
-      if (t < 32) {
-        const int f = dag_potrf32(S, 0);
-        if (lane == 0) fail_s = f;
-      }
-      __syncthreads();
-      if (fail_s == 0) {
-        if (t < 32) rd[t] = 1.0f / S[t][t];
+      for (int p = 0; p < DT / 4; ++p) {
+        float4* P = Xb + (p & 1) * DT;
+        if (ty == p && tx == p) {   // the 4 x 4 diagonal block
+          int f = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float d = acc[c][c];
+            if (f == 0 && (!(d > 0.0f) || !(d < 3.0e38f))) f = c + 1;
+            if (f == 0) {
+              const float y = rsqrt_t(d);
+              acc[c][c] = d * y;
+              rd[4 * p + c] = y;
+#pragma unroll
+              for (int r = c + 1; r < 4; ++r) acc[r][c] *= y;
+#pragma unroll
+              for (int c2 = c + 1; c2 < 4; ++c2)
+#pragma unroll
+                for (int r = c2; r < 4; ++r) acc[r][c2] = fmaf(-acc[r][c], acc[c2][c], acc[r][c2]);
+            }
+          }
+          if (f) fail_s = 4 * p + f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) P[4 * p + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        }
         __syncthreads();
-        if (t < 128) {   // S21 <- S21 L11^{-T}, four threads per row
-          const int r = 32 + (t >> 2), q = t & 3;
-          float x[8];
+        if (fail_s) break;
+        if (tx == p && ty > p) {   // panel block: X L_pp^T = C
+          float lp[4][4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) x[u] = S[r][q + 4 * u];
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int owner = jj & 3, ji = jj >> 2;
-            if (q == owner) x[ji] *= rd[jj];
-            const float xj = __shfl_sync(0xffffffffu, x[ji], (lane & ~3) | owner);
-#pragma unroll
-            for (int u = ji; u < 8; ++u)
-              if (q + 4 * u > jj) x[u] = fmaf(-xj, S[q + 4 * u][jj], x[u]);
+          for (int a = 0; a < 4; ++a) {
+            const float4 v = P[4 * p + a];
+            lp[a][0] = v.x; lp[a][1] = v.y; lp[a][2] = v.z; lp[a][3] = v.w;
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) S[r][q + 4 * u] = x[u];
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              float v = acc[a][c];
+#pragma unroll
+              for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lp[c][l], v);
+              acc[a][c] = v * rd[4 * p + c];
+            }
+#pragma unroll
+          for (int a = 0; a < 4; ++a) P[4 * ty + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
         }
         __syncthreads();
-        {   // S22 -= S21 S21^T (lower)
-          const int r = 32 + (t >> 3), cg = t & 7;
-          float sacc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-          for (int l = 0; l < 32; ++l) {
-            const float h = S[r][l];
+        if (tx > p && ty >= tx) {   // trailing: C -= L_(ty,p) L_(tx,p)^T
+          float4 pa4[4], pb4[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) sacc[e] = fmaf(h, S[32 + 4 * cg + e][l], sacc[e]);
+          for (int a = 0; a < 4; ++a) {
+            pa4[a] = P[4 * ty + a];
+            pb4[a] = P[4 * tx + a];
           }
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (32 + 4 * cg + e <= r) S[r][32 + 4 * cg + e] -= sacc[e];
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              acc[a][b] -= pa4[a].x * pb4[b].x + pa4[a].y * pb4[b].y + pa4[a].z * pb4[b].z +
+                           pa4[a].w * pb4[b].w;
         }
-        __syncthreads();
-        if (t < 32) {
-          const int f = dag_potrf32(S, 32);
-          if (lane == 0 && f) fail_s = 32 + f;
-        }
-        __syncthreads();
       }
       if (fail_s != 0) {
         if (t == 0) atomicCAS(info, 0, (int32_t)(c0 + fail_s));
         ok = false;
-      } else {
-        for (int e = t; e < DT * DT; e += DAG_T) {
-          const int r = e / DT, c = e % DT;
-          if (c <= r && r0 + r < m) __stcg(L + (r0 + r) * ldl + c0 + c, S[r][c]);
+      } else if (ty >= tx) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int64_t gr = r0 + 4 * ty + a;
+          if (gr >= m) continue;
+          float* dst = L + gr * ldl + c0 + 4 * tx;
+          if (ty > tx) {
+            __stcg(reinterpret_cast<float4*>(dst), make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
+          } else {
+#pragma unroll
+            for (int b = 0; b <= a; ++b) __stcg(dst + b, acc[a][b]);
+          }
         }
       }
     } else if (ok) {
@@ -777,27 +799,46 @@ __global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, in
         __syncthreads();
         if (t < DT) rd[t] = 1.0f / As[0][t][t];
         __syncthreads();
-        // X L_jj^T = C column by column; column c's owner (tx = c / 4) scales
-        // it, its row group (a half warp) takes it by shuffle
-        for (int c4 = 0; c4 < DT / 4; ++c4) {
+        // X L_jj^T = C by pivot blocks of 4 columns.  The rows of a half
+        // warp (one row group) depend on nothing else: its owner lane
+        // (tx = p) solves its 4 x 4 block against the diagonal block L_pp,
+        // hands the block to the half warp by shuffle, and the lanes right
+        // of it apply it -- no barrier in the loop.
+#pragma unroll 2
+        for (int p = 0; p < DT / 4; ++p) {
+          float lpp[4][4], rdp[4];
+          float4 lv[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = 4 * c4 + e;
-            if (tx == c4) {
+          for (int c = 0; c < 4; ++c) {
+            rdp[c] = rd[4 * p + c];
 #pragma unroll
-              for (int a = 0; a < 4; ++a) acc[a][e] *= rd[c];
-            }
-            float xv[4];
+            for (int l = 0; l < c; ++l) lpp[c][l] = As[0][4 * p + l][4 * p + c];
+            lv[c] = *reinterpret_cast<const float4*>(&As[0][4 * p + c][4 * tx]);   // L_jj[4tx+b][4p+c]
+          }
+          if (tx == p) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a) xv[a] = __shfl_sync(0xffffffffu, acc[a][e], (lane & 16) | c4);
-            const float4 lv = *reinterpret_cast<const float4*>(&As[0][c][4 * tx]);
-            const float lb[4] = {lv.x, lv.y, lv.z, lv.w};
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (4 * tx + b > c) {
+              for (int a = 0; a < 4; ++a) {
+                float v = acc[a][c];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a][b] = fmaf(-xv[a], lb[b], acc[a][b]);
+                for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lpp[c][l], v);
+                acc[a][c] = v * rdp[c];
               }
+          }
+          float x[4][4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) x[a][l] = __shfl_sync(0xffffffffu, acc[a][l], (lane & 16) | p);
+          if (tx > p) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              acc[a][0] -= x[a][0] * lv[0].x + x[a][1] * lv[1].x + x[a][2] * lv[2].x + x[a][3] * lv[3].x;
+              acc[a][1] -= x[a][0] * lv[0].y + x[a][1] * lv[1].y + x[a][2] * lv[2].y + x[a][3] * lv[3].y;
+              acc[a][2] -= x[a][0] * lv[0].z + x[a][1] * lv[1].z + x[a][2] * lv[2].z + x[a][3] * lv[3].z;
+              acc[a][3] -= x[a][0] * lv[0].w + x[a][1] * lv[1].w + x[a][2] * lv[2].w + x[a][3] * lv[3].w;
+            }
           }
         }
 #pragma unroll
@@ -809,9 +850,11 @@ __global__ void __launch_bounds__(DAG_T, 2) chol32_dag(float* __restrict__ L, in
         }
       }
     }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) st_release_u32(&flags[i * T + j], ok ? 1u : 2u);
+    __syncthreads();   // the tile's stores, then one release (cumulative over the CTA)
+    if (t == 0) {
+      __threadfence();
+      st_release_u32(&flags[i * T + j], ok ? 1u : 2u);
+    }
   }
 }
 
@@ -1174,7 +1217,7 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   SPSVM_LAUNCH_CHECK();
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(chol32_dag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DAG_SMEM));
-  chol32_dag<<<(unsigned)min64(ntiles, 2 * (int64_t)sm_count()), DAG_T, DAG_SMEM, s>>>(
+  chol32_dag<<<(unsigned)min64(ntiles, (int64_t)sm_count()), DAG_T, DAG_SMEM, s>>>(
       L, ly.ldl, m, T, dflags, dflags + T * T, info);
   SPSVM_LAUNCH_CHECK();
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
