@@ -10,7 +10,7 @@ namespace spsvm {
 
 namespace {
 
-constexpr int GV_T = 256;          // threads per block
+constexpr int GV_T = 128;          // threads per block (with 8 rows in flight: 0.99 of HBM)
 constexpr int GV_P = 8;            // consecutive points per thread
 constexpr int GV_PTS = GV_T * GV_P;
 constexpr int GV_CHUNK = 32;       // terms summed in FP32 before promotion
@@ -60,7 +60,7 @@ __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64
 #pragma unroll
       for (int p = 0; p < GV_P; ++p) f[p] = 0.f;
       if (full) {
-#pragma unroll 4
+#pragma unroll 8
         for (int c = c0; c < ce; ++c) {
           float k[8];
           load8<FMT>(K, j0 + c, i, k);

@@ -4,8 +4,11 @@
 // linear and nondecreasing; each pass evaluates it on a 33-point grid over
 // the current bracket and counts the breakpoints m_i / v_i inside each of
 // the 32 cells, so that the root is solved exactly on a cell free of
-// breakpoints.
+// breakpoints.  The whole search is one cooperative launch: all CTAs make a
+// pass, CTA 0 reduces it and picks the next bracket, and two grid barriers
+// (bounded waits) separate the passes -- no host round trip per pass.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -17,39 +20,68 @@ namespace {
 constexpr int LP = 33;          // grid points per pass
 constexpr int LC = LP - 1;      // cells
 constexpr int LT = 256;
+constexpr int kMaxPasses = 64;  // the search needs at most 1 + 12 + 9
 
 struct LsPart {
   double F[LP];
   int32_t cnt[LC];
 };
 
-__global__ void ls_coeffs(const float* __restrict__ o, const float* __restrict__ u,
-                          const double* __restrict__ d, const int64_t* __restrict__ J, int32_t m,
-                          double lambda, double* __restrict__ out) {
-  __shared__ double sh[32];
-  double s0 = 0.0, s1 = 0.0;
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    const int64_t j = J[k];
-    s0 += d[k] * (double)o[j];
-    s1 += d[k] * (double)u[j];
-  }
-  s0 = block_sum(s0, sh);
-  __syncthreads();
-  s1 = block_sum(s1, sh);
-  if (threadIdx.x == 0) {
-    out[0] = lambda * s0;
-    out[1] = lambda * s1;
-  }
+// Bracket handed from CTA 0 to all CTAs between passes, and the result.
+struct LsState {
+  double lo, hi, t;
+  int32_t done, err;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-__global__ void __launch_bounds__(LT) ls_pass(const float* __restrict__ o, const float* __restrict__ u,
-                                              const float* __restrict__ y, int64_t n, double lo,
-                                              double hi, LsPart* __restrict__ part) {
-  __shared__ double red[LT / 32][LP];
-  __shared__ int32_t cnt[LC];
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier of all CTAs of a cooperative launch (counter + generation; the
+// last arrival resets the counter and advances the generation).  Gives up
+// after about a second and returns true.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+  __shared__ int to_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* count = bar;
+    unsigned* gen = bar + 1;
+    const unsigned g = ld_acquire_u32(gen);
+    __threadfence();
+    int to = 0;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      st_release_u32(gen, g + 1);
+    } else {
+      for (uint32_t it = 0; ld_acquire_u32(gen) == g; ++it) {
+        if (it >= (1u << 22)) {
+          to = 1;
+          break;
+        }
+        if (it >= 32) __nanosleep(64);
+      }
+    }
+    to_s = to;
+  }
+  __syncthreads();
+  return to_s != 0;
+}
+
+// One pass of this CTA over its points for the bracket [lo, hi].
+__device__ void ls_pass(const float* __restrict__ o, const float* __restrict__ u,
+                        const float* __restrict__ y, int64_t n, double lo, double hi,
+                        LsPart* __restrict__ part, double (*red)[LP], int32_t* cnt) {
   if (threadIdx.x < LC) cnt[threadIdx.x] = 0;
   __syncthreads();
   const double h = (hi - lo) / (double)LC;
+  const float flo = (float)(lo - 1e-4 * fabs(lo)) - 1e-30f;
+  const float fhi = (float)(hi + 1e-4 * fabs(hi)) + 1e-30f;
   float tk[LP];
 #pragma unroll
   for (int k = 0; k < LP; ++k) tk[k] = (float)(lo + h * (double)k);
@@ -63,6 +95,10 @@ __global__ void __launch_bounds__(LT) ls_pass(const float* __restrict__ o, const
     if (v == 0.0f) continue;
 #pragma unroll
     for (int k = 0; k < LP; ++k) F[k] = fmaf(v, fmaxf(0.0f, fmaf(-tk[k], v, m)), F[k]);
+    // the exact breakpoint (FP64 division, slow on GB300) only where a
+    // fast FP32 estimate (error a few ulp) puts it near the bracket
+    const float bf = __fdividef(m, v);
+    if (!(bf > flo && bf < fhi)) continue;
     const double b = (double)m / (double)v;
     if (b > lo && b < hi) {
       int c = (int)((b - lo) / h);
@@ -82,26 +118,162 @@ __global__ void __launch_bounds__(LT) ls_pass(const float* __restrict__ o, const
   if (threadIdx.x < LP) {
     double s = 0.0;
     for (int q = 0; q < LT / 32; ++q) s += red[q][threadIdx.x];
-    part[blockIdx.x].F[threadIdx.x] = s;
+    part->F[threadIdx.x] = s;
   }
-  if (threadIdx.x < LC) part[blockIdx.x].cnt[threadIdx.x] = cnt[threadIdx.x];
+  if (threadIdx.x < LC) part->cnt[threadIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void ls_reduce(const LsPart* __restrict__ part, int nblocks, LsPart* __restrict__ out) {
-  const int k = threadIdx.x;
-  if (k < LP) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[b].F[k];
-    out->F[k] = s;
+__global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
+                                                const float* __restrict__ u,
+                                                const float* __restrict__ y, int64_t n,
+                                                const double* __restrict__ d,
+                                                const int64_t* __restrict__ J, int32_t m,
+                                                double lambda, LsPart* __restrict__ part,
+                                                LsState* __restrict__ st, unsigned* __restrict__ bar) {
+  __shared__ double red[LT / 32][LP];
+  __shared__ int32_t cnt[LC];
+  __shared__ double Fs[LP], sh[32];
+  __shared__ int32_t Cs[LC];
+  __shared__ double lo_s, hi_s;
+  __shared__ int done_s;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned nb = gridDim.x;
+  // CTA 0, thread 0 carries the search state across passes
+  double a0 = 0.0, a1 = 0.0, d0 = 0.0;
+  int phase = 0, grow = 0, depth = 0;
+  if (t == 0) {
+    lo_s = 0.0;
+    hi_s = 2.0;
+    done_s = 0;
   }
-  if (k < LC) {
-    int32_t c = 0;
-    for (int b = 0; b < nblocks; ++b) c += part[b].cnt[k];
-    out->cnt[k] = c;
+  __syncthreads();
+  for (int pass = 0; pass < kMaxPasses; ++pass) {
+    const double lo = lo_s, hi = hi_s;
+    ls_pass(o, u, y, n, lo, hi, &part[blockIdx.x], red, cnt);
+    if (grid_barrier(bar, nb)) {
+      if (t == 0) atomicExch(&st->err, 1);
+      return;
+    }
+    if (blockIdx.x == 0) {
+      // sums over the CTAs' partials, one warp per value
+      for (int v = w; v < LP + LC; v += LT / 32) {
+        if (v < LP) {
+          double sv = 0.0;
+          for (unsigned b = lane; b < nb; b += 32) sv += __ldcg(&part[b].F[v]);
+          sv = warp_sum(sv);
+          if (lane == 0) Fs[v] = sv;
+        } else {
+          int sv = 0;
+          for (unsigned b = lane; b < nb; b += 32) sv += __ldcg(&part[b].cnt[v - LP]);
+          sv = warp_sum(sv);
+          if (lane == 0) Cs[v - LP] = sv;
+        }
+      }
+      if (pass == 0) {   // a0 = lambda d^T K_JJ beta, a1 = lambda d^T K_JJ d
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = t; k < m; k += LT) {
+          const int64_t j = J[k];
+          s0 += d[k] * (double)o[j];
+          s1 += d[k] * (double)u[j];
+        }
+        s0 = block_sum(s0, sh);
+        __syncthreads();
+        s1 = block_sum(s1, sh);
+        if (t == 0) {
+          a0 = lambda * s0;
+          a1 = lambda * s1;
+        }
+      }
+      __syncthreads();
+      if (t == 0) {
+        auto dphi = [&](int k) {
+          const double tk = lo + (hi - lo) / (double)LC * (double)k;
+          return a0 + a1 * tk - Fs[k];
+        };
+        double tt = 0.0, nlo = lo, nhi = hi;
+        int done = 0;
+        bool next = false;
+        if (phase == 0) {
+          d0 = dphi(0);
+          if (!(d0 < 0.0)) {
+            tt = 0.0;
+            done = 1;
+          } else if (fabs(dphi(LC / 2)) <= 1e-6 * fabs(d0)) {
+            tt = 1.0;
+            done = 1;
+          } else {
+            phase = 1;
+          }
+        }
+        if (!done && phase == 1) {   // grow the bracket until phi' >= 0 at its right end
+          if (dphi(LC) < 0.0 && grow < 12) {
+            nlo = hi;
+            nhi = hi * 8.0;
+            ++grow;
+            next = true;
+          } else if (dphi(LC) < 0.0) {
+            tt = hi;   // phi still decreasing: take the far end (bounded)
+            done = 1;
+          } else {
+            phase = 2;
+          }
+        }
+        if (!done && !next) {   // the cell holding the root
+          int k = 0;
+          while (k < LC && dphi(k + 1) < 0.0) ++k;
+          if (k >= LC) k = LC - 1;
+          const double hstep = (hi - lo) / (double)LC;
+          const double tl = lo + hstep * k, tr = lo + hstep * (k + 1);
+          const double fl = dphi(k), fr = dphi(k + 1);
+          if (Cs[k] == 0 || depth >= 8 || !(fr > fl)) {
+            tt = (fr > fl) ? tl - fl * (tr - tl) / (fr - fl) : tl;
+            if (tt < tl) tt = tl;
+            if (tt > tr) tt = tr;
+            done = 1;
+          } else {
+            nlo = tl;
+            nhi = tr;
+            ++depth;
+          }
+        }
+        if (pass == kMaxPasses - 1 && !done) {
+          tt = lo;
+          done = 1;
+        }
+        st->lo = nlo;
+        st->hi = nhi;
+        st->t = tt;
+        st->done = done;
+      }
+    }
+    if (grid_barrier(bar, nb)) {
+      if (t == 0) atomicExch(&st->err, 1);
+      return;
+    }
+    if (t == 0) {
+      lo_s = __ldcg(&st->lo);
+      hi_s = __ldcg(&st->hi);
+      done_s = __ldcg(&st->done);
+    }
+    __syncthreads();
+    if (done_s) break;
   }
 }
 
-int ls_blocks() { return 2 * sm_count(); }
+int ls_grid() {
+  static std::mutex mu;
+  static int per_sm[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  std::lock_guard<std::mutex> g(mu);
+  if (per_sm[dev] == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ls_search, LT, 0) != cudaSuccess || b < 1)
+      return -1;
+    per_sm[dev] = b < 2 ? b : 2;
+  }
+  return per_sm[dev] * sm_count();
+}
 
 }  // namespace
 }  // namespace spsvm
@@ -110,7 +282,7 @@ using namespace spsvm;
 
 extern "C" size_t spsvm_line_scratch_bytes(int64_t n) {
   (void)n;
-  return (size_t)(ls_blocks() + 1) * sizeof(LsPart) + 256;
+  return (size_t)(2 * sm_count()) * sizeof(LsPart) + 256;
 }
 
 extern "C" int spsvm_line_search(const float* o, const float* u, const float* y, int64_t n,
@@ -123,68 +295,21 @@ extern "C" int spsvm_line_search(const float* o, const float* u, const float* y,
     return set_error(SPSVM_ERR_OOM, "line_search: scratch too small");
   cudaStream_t s = as_stream(stream);
   ProfScope prof(PROF_LINE, s, 12.0 * (double)n);
-  const int nb = ls_blocks();
-  double* coef = static_cast<double*>(scratch);
+  const int grid = ls_grid();
+  if (grid < 1) return set_error(SPSVM_ERR_CUDA, "line_search: occupancy query failed");
+  LsState* st = static_cast<LsState*>(scratch);
+  unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);
   LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
-  LsPart* res = part + nb;
-  ls_coeffs<<<1, 256, 0, s>>>(o, u, d, J, m, lambda, coef);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  void* args[] = {(void*)&o, (void*)&u, (void*)&y, (void*)&n, (void*)&d, (void*)&J,
+                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar};
+  SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ls_search, dim3(grid), dim3(LT), args, 0, s));
   SPSVM_LAUNCH_CHECK();
-  double a[2];
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(a, coef, sizeof(a), cudaMemcpyDeviceToHost, s));
-  LsPart h;
-  auto run = [&](double lo, double hi) -> int {
-    ls_pass<<<nb, LT, 0, s>>>(o, u, y, n, lo, hi, part);
-    SPSVM_LAUNCH_CHECK();
-    ls_reduce<<<1, 64, 0, s>>>(part, nb, res);
-    SPSVM_LAUNCH_CHECK();
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(&h, res, sizeof(LsPart), cudaMemcpyDeviceToHost, s));
-    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
-    return SPSVM_OK;
-  };
-  double lo = 0.0, hi = 2.0;
-  SPSVM_TRY(run(lo, hi));
-  auto dphi = [&](int k, double l, double r) {
-    const double tk = l + (r - l) / (double)LC * (double)k;
-    return a[0] + a[1] * tk - h.F[k];
-  };
-  double t = 0.0;
-  const double d0 = dphi(0, lo, hi);
-  if (!(d0 < 0.0)) {
-    t = 0.0;
-  } else if (std::fabs(dphi(LC / 2, lo, hi)) <= 1e-6 * std::fabs(d0)) {
-    t = 1.0;
-  } else {
-    // grow the bracket until phi' >= 0 at its right end
-    int grow = 0;
-    while (dphi(LC, lo, hi) < 0.0 && grow < 12) {
-      lo = hi;
-      hi = hi * 8.0;
-      SPSVM_TRY(run(lo, hi));
-      ++grow;
-    }
-    if (dphi(LC, lo, hi) < 0.0) {
-      t = hi;   // phi still decreasing: take the far end (bounded)
-    } else {
-      for (int depth = 0;; ++depth) {
-        int k = 0;
-        while (k < LC && dphi(k + 1, lo, hi) < 0.0) ++k;
-        if (k >= LC) k = LC - 1;
-        const double hstep = (hi - lo) / (double)LC;
-        const double tl = lo + hstep * k, tr = lo + hstep * (k + 1);
-        const double fl = dphi(k, lo, hi), fr = dphi(k + 1, lo, hi);
-        if (h.cnt[k] == 0 || depth >= 8 || !(fr > fl)) {
-          t = (fr > fl) ? tl - fl * (tr - tl) / (fr - fl) : tl;
-          if (t < tl) t = tl;
-          if (t > tr) t = tr;
-          break;
-        }
-        lo = tl;
-        hi = tr;
-        SPSVM_TRY(run(lo, hi));
-      }
-    }
-  }
-  *t_host = t;
+  LsState h{};
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(LsState), cudaMemcpyDeviceToHost, s));
+  SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.err) return set_error(SPSVM_ERR_TIMEOUT, "line_search: grid barrier timed out");
+  *t_host = h.t;
   if (t_dev) SPSVM_CUDA_TRY(cudaMemcpyAsync(t_dev, t_host, sizeof(double), cudaMemcpyHostToDevice, s));
   return SPSVM_OK;
 }
