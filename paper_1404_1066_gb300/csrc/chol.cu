@@ -447,6 +447,202 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
   if (t == 0) st_release_u32(&flags[k], 1u);
 }
 
+// FP32 one-pass triangular solves whose results travel as self-validating
+// 64-bit words (tag << 32 | float bits; a 64-bit store is single-copy
+// atomic), so a block's result needs no flag, fence or second load.  In each
+// CTA warp 0 alone polls (two words per lane cover a 64-value block), takes
+// up to SV_BATCH published blocks at once into shared memory, and one
+// barrier hands them to the CTA.  A block that gives up publishes with the
+// tag's top bit set; its dependants give up at once.
+constexpr int SV_BATCH = 8;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Warp 0: stages the published blocks blk[0], blk[1], ... (up to want, in
+// that order; rows at or past m count as published zeros) into xs until the
+// first one not yet published, waiting (bounded) while not even blk[0] is.
+// Returns the number staged, or -1 when a block is abandoned or the wait
+// runs out.
+__device__ int grab_blocks(const unsigned long long* __restrict__ wt, int64_t m, int64_t first,
+                           int step, int want, unsigned tag, float (*xs)[NB], int code) {
+  const int lane = threadIdx.x & 31;
+  const unsigned abt = tag | 0x80000000u;
+  for (uint32_t it = 0;; ++it) {
+    unsigned long long w0[SV_BATCH], w1[SV_BATCH];
+#pragma unroll
+    for (int u = 0; u < SV_BATCH; ++u) {
+      const int64_t base = (first + (int64_t)step * u) * NB;
+      w0[u] = w1[u] = (unsigned long long)tag << 32;
+      if (u < want) {
+        if (base + lane < m) w0[u] = ld_relaxed_u64(wt + base + lane);
+        if (base + 32 + lane < m) w1[u] = ld_relaxed_u64(wt + base + 32 + lane);
+      }
+    }
+    int got = 0;
+    bool ab = false;
+#pragma unroll
+    for (int u = 0; u < SV_BATCH; ++u) {
+      if (u < want && got == u && !ab) {
+        const unsigned h0 = (unsigned)(w0[u] >> 32), h1 = (unsigned)(w1[u] >> 32);
+        ab = __any_sync(0xffffffffu, h0 == abt || h1 == abt);
+        if (!ab && __all_sync(0xffffffffu, h0 == tag && h1 == tag)) {
+          xs[u][lane] = __uint_as_float((unsigned)w0[u]);
+          xs[u][32 + lane] = __uint_as_float((unsigned)w1[u]);
+          ++got;
+        }
+      }
+    }
+    if (ab) return -1;
+    if (got > 0) return got;
+    if (it >= (1u << 20)) {
+      if (lane == 0) atomicCAS(&g_sv_status, 0, code);
+      return -1;
+    }
+    if (it >= 8) __nanosleep(32);
+  }
+}
+
+// z = L^{-1} b (FP32).  Thread t: row t / 4 of the block row, columns
+// 16 (t % 4) .. + 15 of each earlier 64-column block.
+__global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict__ L, int64_t ldh,
+                                                        int64_t m, const float* __restrict__ b,
+                                                        unsigned long long* __restrict__ zt,
+                                                        float* __restrict__ z,
+                                                        unsigned* __restrict__ ticket, unsigned tag) {
+  __shared__ float Li[NB][NB + 1];
+  __shared__ float xs[SV_BATCH][NB];
+  __shared__ float v[NB];
+  __shared__ unsigned k_s;
+  __shared__ int n_s;
+  const int t = threadIdx.x;
+  if (t == 0) k_s = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t k = k_s;
+  const int64_t r0 = k * NB;
+  const int nb = (int)min64(NB, m - r0);
+  load_diag_inverse(L, ldh, r0, nb, Li);
+  const int r = t >> 2, q = t & 3;
+  const bool row_ok = r < nb;
+  const float* __restrict__ Lrow = L + (r0 + (row_ok ? r : 0)) * ldh + 16 * q;
+  float acc = 0.0f;
+  bool ok = true;
+  for (int64_t j = 0; j < k;) {
+    float a[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a[c] = row_ok ? __ldg(Lrow + j * NB + c) : 0.0f;
+    if (t < 32) {
+      const int g = grab_blocks(zt, m, j, 1, (int)min64(SV_BATCH, k - j), tag, xs, 21);
+      if (t == 0) n_s = g;
+    }
+    __syncthreads();
+    const int got = n_s;
+    if (got < 0) {
+      ok = false;
+      break;
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc = fmaf(a[c], xs[0][16 * q + c], acc);
+    for (int u = 1; u < got; ++u) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        acc = fmaf(row_ok ? __ldg(Lrow + (j + u) * NB + c) : 0.0f, xs[u][16 * q + c], acc);
+    }
+    __syncthreads();   // xs free again
+    j += got;
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (q == 0) v[r] = row_ok ? b[r0 + r] - acc : 0.0f;
+  __syncthreads();
+  float sres = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) sres = fmaf(Li[r][16 * q + c], v[16 * q + c], sres);
+  sres += __shfl_xor_sync(0xffffffffu, sres, 1);
+  sres += __shfl_xor_sync(0xffffffffu, sres, 2);
+  if (q == 0 && row_ok) {
+    z[r0 + r] = sres;
+    st_relaxed_u64(zt + r0 + r, ((unsigned long long)(ok ? tag : (tag | 0x80000000u)) << 32) |
+                                    __float_as_uint(sres));
+  }
+}
+
+// x = L^{-T} z (FP32).  Block rows from the last; thread t: column t % 64 of
+// the block, rows 16 (t / 64) .. + 15 of each later 64-row block.
+__global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict__ L, int64_t ldh,
+                                                        int64_t m, const float* __restrict__ z,
+                                                        unsigned long long* __restrict__ xt,
+                                                        float* __restrict__ x,
+                                                        unsigned* __restrict__ ticket, unsigned tag) {
+  __shared__ float Li[NB][NB + 1];
+  __shared__ float xs[SV_BATCH][NB];
+  __shared__ float part[4][NB];
+  __shared__ float v[NB];
+  __shared__ unsigned k_s;
+  __shared__ int n_s;
+  const int t = threadIdx.x;
+  const int64_t B = ceil_div(m, (int64_t)NB);
+  if (t == 0) k_s = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t k = B - 1 - (int64_t)k_s;
+  const int64_t r0 = k * NB;
+  const int nb = (int)min64(NB, m - r0);
+  load_diag_inverse(L, ldh, r0, nb, Li);
+  const int c = t & (NB - 1), g = t >> 6;
+  const bool col_ok = c < nb;
+  float acc = 0.0f;
+  bool ok = true;
+  for (int64_t j = B - 1; j > k;) {   // later blocks, last first
+    float a[16];
+    const int64_t rb = j * NB + 16 * g;
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr)
+      a[rr] = (col_ok && rb + rr < m) ? __ldg(L + (rb + rr) * ldh + r0 + c) : 0.0f;
+    if (t < 32) {
+      const int gb = grab_blocks(xt, m, j, -1, (int)min64(SV_BATCH, j - k), tag, xs, 22);
+      if (t == 0) n_s = gb;
+    }
+    __syncthreads();
+    const int got = n_s;
+    if (got < 0) {
+      ok = false;
+      break;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) acc = fmaf(a[rr], xs[0][16 * g + rr], acc);
+    for (int u = 1; u < got; ++u) {
+      const int64_t rbu = (j - u) * NB + 16 * g;   // a full block (only the last is partial)
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr)
+        acc = fmaf(col_ok ? __ldg(L + (rbu + rr) * ldh + r0 + c) : 0.0f, xs[u][16 * g + rr], acc);
+    }
+    __syncthreads();
+    j -= got;
+  }
+  part[g][c] = acc;
+  __syncthreads();
+  if (t < NB) v[t] = (t < nb) ? z[r0 + t] - (part[0][t] + part[1][t] + part[2][t] + part[3][t]) : 0.0f;
+  __syncthreads();
+  float sres = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) sres = fmaf(Li[16 * g + i][c], v[16 * g + i], sres);
+  part[g][c] = sres;
+  __syncthreads();
+  if (t < nb) {
+    const float xv = part[0][t] + part[1][t] + part[2][t] + part[3][t];
+    x[r0 + t] = xv;
+    st_relaxed_u64(xt + r0 + t, ((unsigned long long)(ok ? tag : (tag | 0x80000000u)) << 32) |
+                                    __float_as_uint(xv));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Mixed precision: FP32 factor of H + shift I, FP64 iterative refinement.
 // ---------------------------------------------------------------------------
@@ -1163,6 +1359,8 @@ extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, dou
 // ---------------------------------------------------------------------------
 namespace {
 
+constexpr int kTicketSteps = 64;   // refinement steps between ticket resets
+
 struct MixedLayout {
   int64_t ldl, B, nrow_blocks, nvec_blocks;
   size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, dag, total;
@@ -1178,7 +1376,10 @@ MixedLayout mixed_layout(int64_t m) {
   ly.nvec_blocks = ceil_div(m, (int64_t)MX_T);
   size_t off = 0;
   ly.L = off;      off += al((size_t)m * ly.ldl * 4);
-  ly.sw = off;     ly.sw_bytes = al((size_t)m * 4) + al((size_t)(2 * ly.B + 2) * 4); off += ly.sw_bytes;
+  // solve scratch: the forward result (FP32), the tagged words of both
+  // solves, and per-step tickets of the two launches (zeroed once per call)
+  ly.sw = off;     ly.sw_bytes = al((size_t)m * 4) + al((size_t)m * 16) + al((size_t)2 * kTicketSteps * 4);
+  off += ly.sw_bytes;
   ly.z32 = off;    off += al((size_t)m * 4);
   ly.r = off;      off += al((size_t)m * 8);
   ly.rowmax = off; off += al((size_t)m * 8);
@@ -1242,7 +1443,11 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
   char* w = static_cast<char*>(work);
   const float* L = reinterpret_cast<const float*>(w + ly.L);
   float* zw = reinterpret_cast<float*>(w + ly.sw);
-  unsigned* flags = reinterpret_cast<unsigned*>(w + ly.sw + round_up(m * 4, (int64_t)256));
+  char* tagged_region = w + ly.sw + round_up(m * 4, (int64_t)256);
+  unsigned long long* zt = reinterpret_cast<unsigned long long*>(tagged_region);
+  unsigned long long* xt = zt + m;
+  unsigned* tickets = reinterpret_cast<unsigned*>(tagged_region + round_up(m * 16, (int64_t)256));
+  const size_t tagged_bytes = (size_t)round_up(m * 16, (int64_t)256) + (size_t)2 * kTicketSteps * 4;
   float* z32 = reinterpret_cast<float*>(w + ly.z32);
   double* r = reinterpret_cast<double*>(w + ly.r);
   double* rowmax = reinterpret_cast<double*>(w + ly.rowmax);
@@ -1254,6 +1459,7 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
   const bool vec = (ldh % 2) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
+  SPSVM_CUDA_TRY(cudaMemsetAsync(tagged_region, 0, tagged_bytes, s));
   SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
   absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax);
   SPSVM_LAUNCH_CHECK();
@@ -1267,12 +1473,14 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
     // z = (L L^T)^{-1} r in FP32, x += z, r = b - (H + shift I) x in FP64
     to_f32_vec<<<vb, MX_T, 0, s>>>(r, m, z32);
     SPSVM_LAUNCH_CHECK();
-    SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(2 * ly.B + 2) * 4, s));
-    trsv_fwd_onepass<float><<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zw, flags,
-                                                                  flags + 2 * ly.B);
+    // tags 1, 2, ... (the tagged words start zeroed); tickets per step
+    const unsigned tag = (unsigned)(it + 1);
+    if (it > 0 && it % kTicketSteps == 0)
+      SPSVM_CUDA_TRY(cudaMemsetAsync(tickets, 0, (size_t)2 * kTicketSteps * 4, s));
+    unsigned* tk = tickets + 2 * (it % kTicketSteps);
+    trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag);
     SPSVM_LAUNCH_CHECK();
-    trsv_bwd_onepass<float><<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, z32, flags + ly.B,
-                                                                  flags + 2 * ly.B + 1);
+    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag);
     SPSVM_LAUNCH_CHECK();
     add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
     SPSVM_LAUNCH_CHECK();
