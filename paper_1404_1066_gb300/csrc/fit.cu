@@ -151,7 +151,7 @@ struct Layout {
   size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
       off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_tmp2, off_ws, off_sv, off_J,
       off_cand,
-      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, total;
+      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, off_kjj, total;
   size_t scratch_bytes;
   size_t kbytes;
   size_t chw_bytes, sv_bytes, mix_bytes;
@@ -210,7 +210,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   sc = std::max(sc, spsvm_reduce_scratch_bytes(n));
   sc = std::max(sc, spsvm_compact_scratch_bytes(n, L.jcap));
   // the Gram split count depends on |J|: cover every size the fit can reach
-  for (int64_t mm = 1; mm <= L.jcap; ++mm) sc = std::max(sc, spsvm_gram_scratch_bytes(mm, n));
+  for (int64_t mm = 1; mm <= L.jcap; ++mm) sc = std::max(sc, gram_part_bytes(mm, n));
   sc = std::max(sc, spsvm_line_scratch_bytes(n));
   L.scratch_bytes = al(sc);
   L.off_scratch = take(L.scratch_bytes);
@@ -219,6 +219,8 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   // FP32 factor and refinement vectors of the mixed Newton solve
   L.mix_bytes = solver == SPSVM_SOLVE_MIXED ? spsvm_mixed_work_bytes(L.jcap) : 0;
   L.off_mix = take(L.mix_bytes);
+  // symmetric K_JJ (FP64), extended as the basis grows; read by the Gram finish
+  L.off_kjj = take((size_t)L.jcap * L.jcap * 8);
   L.total = off;
   return L;
 }
@@ -429,7 +431,7 @@ struct Fit {
                              "Newton matrix not positive definite up to jitter 1e-2 tr(H)/|J| (|J|=%d)", m);
           if (!h_fresh) {
             SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb,
-                                s, st[2]));
+                                s, st[2], at<double>(L.off_kjj), L.jcap));
             h_fresh = true;
           }
           if (lv >= 0 && tr < 0.0) {
@@ -547,6 +549,7 @@ struct Fit {
       spsvm_kmat K = kmat();
       SPSVM_TRY(spsvm_kernel_block(&pts, Jd, m, gamma, op.precision, &K, 0, ws + L.off_scratch,
                                    L.scratch_bytes, s));
+      SPSVM_TRY(kjj_fill(&K, Jd, m, 0, at<double>(L.off_kjj), L.jcap, s));
       SPSVM_TRY(newton());
     }
     double st[3];
@@ -586,6 +589,7 @@ struct Fit {
       spsvm_kmat K = kmat();
       SPSVM_TRY(spsvm_kernel_block(&pts, Jd + m0, qq, gamma, op.precision, &K, m0,
                                    ws + L.off_scratch, L.scratch_bytes, s));
+      SPSVM_TRY(kjj_fill(&K, Jd, m, m0, at<double>(L.off_kjj), L.jcap, s));
       SPSVM_TRY(newton());
       ++round;
       SPSVM_TRY(flags(act_cur, st));

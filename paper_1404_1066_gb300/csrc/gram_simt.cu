@@ -114,27 +114,95 @@ int launch_gram_simt(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max
   return SPSVM_OK;
 }
 
-// H[a][b] = lambda * (K[b][J[a]] + K[a][J[b]]) / 2 + sum_s part[s][min][max].
-__global__ void gram_finish_kernel(const double* __restrict__ part, int64_t splits, int64_t ldp,
-                                   KView K, const int64_t* __restrict__ J, int64_t m,
-                                   double lambda, double* __restrict__ H, int64_t ldh,
-                                   int upper_only_tiles) {
+// K_JJ[a][b] = (K[b][J[a]] + K[a][J[b]]) / 2 (the stored values made
+// symmetric; exact in FP64) for the rows and columns from row0 on: thread
+// (r, c), r >= row0, writes (r, c) and (c, r).  A fit keeps K_JJ in its
+// workspace and extends it once per round, so the Gram finish reads it
+// coalesced instead of gathering two scattered kernel values per entry.
+__global__ void kjj_fill_kernel(KView K, const int64_t* __restrict__ J, int64_t m, int64_t row0,
+                                double* __restrict__ kjj, int64_t ldk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m * m) return;
-  const int64_t a = e / m, b = e % m;
-  const int64_t lo = a < b ? a : b, hi = a < b ? b : a;
-  double s = 0.0;
-  for (int64_t k = 0; k < splits; ++k) s += part[k * ldp * ldp + lo * ldp + hi];
-  const double kjj = 0.5 * ((double)K.at(hi, J[lo]) + (double)K.at(lo, J[hi]));
-  H[a * ldh + b] = lambda * kjj + s;
+  const int64_t rows = m - row0;
+  if (e >= rows * m) return;
+  const int64_t r = row0 + e / m, c = e % m;
+  const double v = 0.5 * ((double)K.at(c, J[r]) + (double)K.at(r, J[c]));
+  kjj[r * ldk + c] = v;
+  kjj[c * ldk + r] = v;
 }
 
-int launch_gram_finish(const double* part, int64_t splits, int64_t ldp, const spsvm_kmat* K,
-                       const int64_t* J, int64_t m, double lambda, double* H, int64_t ldh,
+// H[a][b] = H[b][a] = lambda K_JJ[a][b] + sum_s part[s][min(a,b)][max(a,b)]
+// over 32 x 32 upper tiles: the partials, K_JJ and both halves of H move
+// through shared memory so that every global access is coalesced.
+constexpr int FT = 32;
+__global__ void __launch_bounds__(FT * 8) gram_finish_kernel(const double* __restrict__ part,
+                                                             int64_t splits, int64_t ldp,
+                                                             const double* __restrict__ kjj,
+                                                             int64_t ldk, int64_t m, double lambda,
+                                                             double* __restrict__ H, int64_t ldh) {
+  __shared__ double P[FT][FT + 1];
+  __shared__ double Kt[FT][FT + 1];
+  const int64_t T = ceil_div(m, (int64_t)FT);
+  int64_t rem = blockIdx.x, ta = 0;
+  while (rem >= T - ta) {
+    rem -= T - ta;
+    ++ta;
+  }
+  const int64_t tb = ta + rem;
+  const int64_t a0 = ta * FT, b0 = tb * FT;
+  const int c = threadIdx.x;
+  const int64_t b = b0 + c;
+  for (int r = threadIdx.y; r < FT; r += 8) {
+    const int64_t a = a0 + r;
+    double sum = 0.0, kv = 0.0;
+    if (a < m && b < m) {
+      for (int64_t k = 0; k < splits; ++k) sum += part[k * ldp * ldp + a * ldp + b];
+      kv = kjj[a * ldk + b];
+    }
+    P[r][c] = sum;
+    Kt[r][c] = kv;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < FT; r += 8) {
+    const int64_t a = a0 + r;
+    if (a < m && b < m) {
+      // the partial of the upper triangle for both orientations
+      const double pv = (ta == tb && r > c) ? P[c][r] : P[r][c];
+      H[a * ldh + b] = lambda * Kt[r][c] + pv;
+    }
+  }
+  if (ta != tb) {   // mirror tile: H[b0 + r][a0 + c] from the transposed values
+    const int64_t a = a0 + c;
+    for (int r = threadIdx.y; r < FT; r += 8) {
+      const int64_t bb = b0 + r;
+      if (a < m && bb < m) H[bb * ldh + a] = lambda * Kt[c][r] + P[c][r];
+    }
+  }
+}
+
+int launch_gram_finish(const double* part, int64_t splits, int64_t ldp, const double* kjj,
+                       int64_t ldk, int64_t m, double lambda, double* H, int64_t ldh,
                        cudaStream_t s) {
-  const int64_t total = m * m;
-  gram_finish_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, splits, ldp, view(K), J,
-                                                                     m, lambda, H, ldh, 1);
+  const int64_t T = ceil_div(m, (int64_t)FT);
+  gram_finish_kernel<<<(unsigned)(T * (T + 1) / 2), dim3(FT, 8), 0, s>>>(part, splits, ldp, kjj,
+                                                                         ldk, m, lambda, H, ldh);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+size_t gram_part_bytes(int64_t m, int64_t ns) {
+  if (m < 0 || ns < 0) return 0;
+  const int64_t ldp = round_up(m > 0 ? m : 1, 64);
+  int64_t splits = gram_simt_splits(m, ns);
+  const int64_t tc = gram_tc_splits(m, ns);
+  if (tc > splits) splits = tc;
+  return (size_t)(splits * ldp * ldp * (int64_t)sizeof(double));
+}
+
+int kjj_fill(const spsvm_kmat* K, const int64_t* J, int64_t m, int64_t row0, double* kjj,
+             int64_t ldk, cudaStream_t s) {
+  if (m <= row0) return SPSVM_OK;
+  const int64_t total = (m - row0) * m;
+  kjj_fill_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(view(K), J, m, row0, kjj, ldk);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -146,16 +214,15 @@ using namespace spsvm;
 extern "C" size_t spsvm_gram_scratch_bytes(int64_t m, int64_t ns) {
   if (m < 0 || ns < 0) return 0;
   const int64_t ldp = round_up(m > 0 ? m : 1, 64);
-  int64_t splits = gram_simt_splits(m, ns);
-  const int64_t tc = gram_tc_splits(m, ns);
-  if (tc > splits) splits = tc;
-  return (size_t)(splits * ldp * ldp * (int64_t)sizeof(double));
+  // the partial sums, then K_JJ gathered from K (a fit keeps its own)
+  return gram_part_bytes(m, ns) + (size_t)(ldp * ldp * (int64_t)sizeof(double));
 }
 
 namespace spsvm {
 int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const spsvm_kmat* K,
               const int64_t* J, double lambda, int32_t precision, double* H, int64_t ldh,
-              void* scratch, size_t scratch_bytes, cudaStream_t s, double ns_work) {
+              void* scratch, size_t scratch_bytes, cudaStream_t s, double ns_work,
+              const double* kjj, int64_t ldk) {
   SPSVM_TRY(check_kmat(Kc, "gram(Kc)"));
   SPSVM_TRY(check_kmat(K, "gram(K)"));
   if (!ns_dev || !J || !H) return set_error(SPSVM_ERR_ARG, "gram: NULL pointer");
@@ -164,12 +231,18 @@ int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const
     return set_error(SPSVM_ERR_ARG, "gram: bad shapes m=%lld Kc.rows=%lld ldh=%lld ns_max=%lld",
                      (long long)m, (long long)Kc->rows, (long long)ldh, (long long)ns_max);
   if (m == 0) return SPSVM_OK;
-  if (!scratch || scratch_bytes < spsvm_gram_scratch_bytes(m, ns_max))
-    return set_error(SPSVM_ERR_OOM, "gram: scratch too small");
+  const size_t need = kjj ? gram_part_bytes(m, ns_max) : spsvm_gram_scratch_bytes(m, ns_max);
+  if (!scratch || scratch_bytes < need) return set_error(SPSVM_ERR_OOM, "gram: scratch too small");
   // algorithmic work: one multiply-add per active point per unique entry
   ProfScope prof(PROF_GRAM, s, ns_work * (double)m * (double)(m + 1));
   const int64_t ldp = round_up(m, 64);
   double* part = static_cast<double*>(scratch);
+  if (!kjj) {   // gather K_JJ into the scratch behind the partial sums
+    double* kj = reinterpret_cast<double*>(static_cast<char*>(scratch) + gram_part_bytes(m, ns_max));
+    SPSVM_TRY(kjj_fill(K, J, m, 0, kj, ldp, s));
+    kjj = kj;
+    ldk = ldp;
+  }
   int64_t splits;
   if (precision == SPSVM_BF16X3) {
     if (Kc->format != SPSVM_BF16X3) return set_error(SPSVM_ERR_ARG, "gram: BF16X3 needs split planes");
@@ -181,7 +254,7 @@ int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const
   } else {
     return set_error(SPSVM_ERR_ARG, "gram: bad precision");
   }
-  return launch_gram_finish(part, splits, ldp, K, J, m, lambda, H, ldh, s);
+  return launch_gram_finish(part, splits, ldp, kjj, ldk, m, lambda, H, ldh, s);
 }
 }  // namespace spsvm
 
@@ -190,5 +263,5 @@ extern "C" int spsvm_gram(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t n
                           double* H, int64_t ldh, void* scratch, size_t scratch_bytes,
                           void* stream) {
   return gram_impl(Kc, ns_dev, ns_max, K, J, lambda, precision, H, ldh, scratch, scratch_bytes,
-                   as_stream(stream), (double)ns_max);
+                   as_stream(stream), (double)ns_max, nullptr, 0);
 }
