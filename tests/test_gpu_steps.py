@@ -316,6 +316,24 @@ def test_mixed_factor_meets_fp32_cholesky_backward_error(sp, m):
     assert np.max(np.abs(Lf - R)) <= 1e-4 * np.max(np.abs(R))
 
 
+@pytest.mark.parametrize("m", [16384, 16400])
+def test_mixed_solve_large(sp, m):
+    """Past 256 tile rows (more solve blocks than SMs; the last block ragged at
+    16,400) the mixed solve still reaches FP64 backward error.
+    H = c I + U U^T (U 64 wide) is built and checked on the device."""
+    g = torch.Generator(device="cuda").manual_seed(m)
+    U = torch.randn((m, 64), generator=g, dtype=torch.float64, device="cuda")
+    H = U @ U.T
+    H.diagonal().add_(8.0)
+    b = torch.randn(m, generator=g, dtype=torch.float64, device="cuda")
+    info, st, x, iters, be = sp.spsvm_solve_mixed(H, b)
+    assert info == 0 and st == 0, (info, st, iters, be)
+    r = b - H @ x
+    bound = 1e-13 * (H.abs().sum(1).max() * x.abs().max() + b.abs().max())
+    assert float(r.abs().max()) <= float(bound)
+    del U, H
+
+
 def test_mixed_solve_reports_fp32_breakdown_and_stagnation(sp):
     H = np.eye(100)
     H[70, 70] = -1.0
