@@ -410,6 +410,64 @@ def predict(Xq, XJ, beta, gamma):
     return rbf_kernel(Xq, XJ, gamma) @ beta
 
 
+def ovo_pairs(classes):
+    """The one-vs-one binary problems (a, b), a < b, in the order (0, 1),
+    (0, 2), ..., (0, C-1), (1, 2), ... (Section 5 trains its multiclass
+    sets one-vs-one)."""
+    return [(a, b) for a in range(classes) for b in range(a + 1, classes)]
+
+
+def ovo_vote(decisions, classes):
+    """Labels from one-vs-one decision values: decisions[p][i], the value of
+    pair p = (a, b) of ovo_pairs(classes) at query i, is a vote for a when
+    it is >= 0 and for b otherwise; the class with the most votes wins, a
+    tie going to the smaller class (a reading: the paper names no rule).
+    Returns (labels, votes)."""
+    decisions = np.asarray(decisions)
+    nq = decisions.shape[1]
+    votes = np.zeros((nq, classes), dtype=np.int64)
+    for p, (a, b) in enumerate(ovo_pairs(classes)):
+        for i in range(nq):
+            if decisions[p, i] >= 0:
+                votes[i, a] += 1
+            else:
+                votes[i, b] += 1
+    out = np.zeros(nq, dtype=np.int64)
+    for i in range(nq):
+        best = 0
+        for c in range(1, classes):
+            if votes[i, c] > votes[i, best]:
+                best = c
+        out[i] = best
+    return out, votes
+
+
+def fit_ovo(X, class_labels, classes, gamma, lam, budget, replay=None, **kw):
+    """One binary SP-SVM per pair (a, b) on the points of class a (y = +1)
+    and class b (y = -1), the budget capped at the pair's point count.
+    Returns [(rows, FitResult)] in ovo_pairs order; replay, if given, holds
+    one replay list per pair."""
+    X = np.asarray(X, dtype=np.float64)
+    class_labels = np.asarray(class_labels)
+    out = []
+    for p, (a, b) in enumerate(ovo_pairs(classes)):
+        rows = np.flatnonzero((class_labels == a) | (class_labels == b))
+        y = np.where(class_labels[rows] == a, 1.0, -1.0)
+        r = fit(X[rows], y, gamma, lam, min(budget, len(rows)),
+                replay=None if replay is None else replay[p], **kw)
+        out.append((rows, r))
+    return out
+
+
+def predict_ovo(X, fitted, classes, Xq, gamma):
+    """Labels (and votes) of the queries Xq by one-vs-one voting over the
+    pair models of fit_ovo (basis rows taken from X through each pair's
+    rows)."""
+    X = np.asarray(X, dtype=np.float64)
+    dec = np.stack([predict(Xq, X[rows][r.J], r.beta, gamma) for rows, r in fitted])
+    return ovo_vote(dec, classes)
+
+
 def labels(decision):
     """sign with sign(0) = +1."""
     return np.where(np.asarray(decision) >= 0, 1.0, -1.0)

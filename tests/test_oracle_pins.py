@@ -308,6 +308,48 @@ def test_growth_stop_rule():
     assert len(stops) >= 3   # the epsilons exercise different rounds
 
 
+def test_ovo_pairs_and_hand_counted_votes():
+    """One-vs-one voting on decision values counted by hand: three classes,
+    pairs (0,1), (0,2), (1,2).  Query 0: 0 beats 1, 2 beats 0, 1 beats 2 --
+    one vote each, the tie goes to class 0.  Query 1: 1, 2, 2 -> class 2.
+    Query 2: 0, 0, 1 -> class 0 with two votes.  A decision of exactly 0
+    votes for the first class of the pair."""
+    assert O.ovo_pairs(3) == [(0, 1), (0, 2), (1, 2)]
+    assert len(O.ovo_pairs(10)) == 45 and O.ovo_pairs(4)[3] == (1, 2)
+    dec = np.array([[+1.0, -1.0, +0.5],
+                    [-1.0, -1.0, +2.0],
+                    [+1.0, -0.5, 0.0]])
+    lab, votes = O.ovo_vote(dec, 3)
+    np.testing.assert_array_equal(votes, [[1, 1, 1], [0, 1, 2], [2, 1, 0]])
+    np.testing.assert_array_equal(lab, [0, 2, 0])
+
+
+def test_ovo_two_classes_is_the_binary_machine():
+    # with two classes one-vs-one is the binary SP-SVM: class 0 where f >= 0
+    X, y = _blobs(120, 3, 40, sep=1.0)
+    cls = np.where(y > 0, 0, 1)
+    fitted = O.fit_ovo(X, cls, 2, 0.3, 1e-3, 16, tol=1e-10, kappa=24, q=8, seed=3)
+    rows, r = fitted[0]
+    np.testing.assert_array_equal(rows, np.arange(len(y)))
+    Xq = X[:50] + 0.1
+    lab, _ = O.predict_ovo(X, fitted, 2, Xq, 0.3)
+    f = O.predict(Xq, X[r.J], r.beta, 0.3)
+    np.testing.assert_array_equal(lab, np.where(f >= 0, 0, 1))
+
+
+def test_ovo_separates_far_apart_classes():
+    # three tight clusters far apart: every training point gets its class
+    g = np.random.default_rng(8)
+    centres = np.array([[0.0, 0.0], [6.0, 0.0], [0.0, 6.0]])
+    cls = np.repeat(np.arange(3), 30)
+    X = centres[cls] + 0.3 * g.standard_normal((90, 2))
+    fitted = O.fit_ovo(X, cls, 3, 0.5, 1e-3, 12, tol=1e-10, kappa=20, q=6, seed=2)
+    assert [len(rows) for rows, _ in fitted] == [60, 60, 60]
+    lab, votes = O.predict_ovo(X, fitted, 3, X, 0.5)
+    np.testing.assert_array_equal(lab, cls)
+    assert np.all(votes.sum(axis=1) == 3)
+
+
 def test_replay_adopts_other_choice_and_rejects_bad_one():
     X, y = _blobs(200, 3, 30)
     r = O.fit(X, y, 0.3, 1e-3, 32, tol=1e-10, kappa=24, q=16, seed=4)
