@@ -206,6 +206,31 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
                 workers=workers, budget_gb=budget_gb, arrival_rate=20.0)
 
 
+def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x3"):
+    """One-vs-one over a 10-class mixture (the grouped form of Section 5's
+    multiclass runs): the 45 pair problems as one batch, then voting on
+    fresh points of the same mixture."""
+    from paper_1404_1066_gb300 import synth
+    p = synth.gaussian_mixture(n=n, d=d, components=classes, seed=1006, lam=1e-4, budget=budget)
+    cls = p.meta["components"].astype(np.int64)
+    Xq, cq = synth.mixture_holdout(p, 20_000, seed=89, components=True)
+    X = torch.from_numpy(p.X).cuda()
+    Xqd = torch.from_numpy(Xq).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    models, st = sp.spsvm_fit_ovo(X, cls, classes, p.gamma, p.lam, budget, 1e-6, workers=workers,
+                                  precision=precision, candidates=256, add_per_round=64, seed=1)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    lab, _ = sp.spsvm_predict_ovo(models, classes, Xqd)
+    lab = lab.cpu().numpy()
+    pred_s = time.perf_counter() - t1
+    return dict(classes=classes, pairs=len(models), ok=int(sum(1 for s in st if s == 0)), n=n, d=d,
+                basis=budget, fit_s=fit_s, pairs_per_s=len(models) / fit_s, predict_s=pred_s,
+                queries=len(Xq), holdout_accuracy=float(np.mean(lab == cq)), workers=workers)
+
+
 def growth_leg(sp, torch, model, X, y, p, work, opts, stream, holdout=100_000):
     from paper_1404_1066_gb300 import synth
     eps = sp._lib.SPSVM_GROWTH_EPS_PAPER
@@ -490,6 +515,7 @@ def run_ours(args):
         roofline["note"] = note
 
     batched = batched_leg(sp, torch) if args.batched else None
+    ovo = ovo_leg(sp, torch) if args.ovo else None
     serve = serve_leg(sp, requests=args.serve_requests) if args.serve_requests > 0 else None
 
     line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
@@ -505,7 +531,7 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, growth_stop=growth, batched=batched, serve=serve)
+                fp32_form=fp32_form, growth_stop=growth, batched=batched, ovo=ovo, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, factor, cores, sample = cpu_baseline_run(steps=1)
         line["cpu_baseline"] = dict(value=times[0] * factor, unit="s", cores=cores, kind="oracle",
@@ -533,6 +559,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--ovo", type=int, default=1, help="one-vs-one leg (10 classes, 45 pairs)")
     ap.add_argument("--growth", type=int, default=1,
                     help="report the growth stop at epsilon = 5e-6 and accuracy vs |J|")
     ap.add_argument("--micro", choices=["cholesky"], default=None,

@@ -423,6 +423,32 @@ int spsvm_fit_batched(const float* X, int64_t n, int64_t d, int64_t ldx,
                       const spsvm_problem* probs, int32_t count, const spsvm_options* opt,
                       int32_t workers, spsvm_model** outs, int32_t* status);
 
+/* One-vs-one multiclass (Section 5 trains its multiclass sets one against
+ * one).  labels: host int32, n entries in [0, classes), every class present;
+ * 2 <= classes <= 64.  The C = classes (classes - 1) / 2 binary problems are
+ * the pairs (a, b), a < b, in the order (0,1), (0,2), ..., (0,C-1), (1,2),
+ * ...; problem (a, b) holds the rows of class a (y = +1) and class b
+ * (y = -1) in X order, with the basis budget capped at its row count, and
+ * all of them are fitted as one batch by spsvm_fit_batched (same options,
+ * workers, ownership and status rules).  outs and status: host arrays of C
+ * entries, in pair order. */
+int spsvm_fit_ovo(const float* X, int64_t n, int64_t d, int64_t ldx, const int32_t* labels,
+                  int32_t classes, float gamma, double lambda, int32_t basis_budget, double tol,
+                  const spsvm_options* opt, int32_t workers, spsvm_model** outs,
+                  int32_t* status);
+
+/* Labels of nq queries (device, nq x d, row pitch ldq) by one-vs-one voting:
+ * pair model p = (a, b) (pair order as above; models: host array of its C
+ * models) votes a where its decision value is >= 0 and b otherwise; the
+ * class with the most votes wins, a tie going to the smaller class.
+ * labels: device int32, nq; votes: device int32 nq x classes (row-major) or
+ * NULL; work: device, spsvm_predict_ovo_work_bytes(classes, nq) bytes (the
+ * pair decision values).  Runs on `stream`. */
+size_t spsvm_predict_ovo_work_bytes(int32_t classes, int64_t nq);
+int spsvm_predict_ovo(const spsvm_model* const* models, int32_t classes, const float* Xq,
+                      int64_t nq, int64_t ldq, int32_t* labels, int32_t* votes, void* work,
+                      size_t work_bytes, void* stream);
+
 /* Request loop.  Requests carry host data (copied at submission).  Each has
  * an HBM footprint (fit: X, y, the fit workspace and the model; predict: the
  * queries and results); a request is admitted, in arrival order, when a

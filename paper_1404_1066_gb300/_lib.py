@@ -121,6 +121,10 @@ SIGNATURES = {
     "spsvm_draw_candidates": (_I32, [_I64, _P, _I32, _I32, C.c_uint64, C.c_uint32, _P]),
     "spsvm_fit_batched": (_I32, [_P, _I64, _I64, _I64, C.POINTER(spsvm_problem), _I32,
                                  C.POINTER(spsvm_options), _I32, _P, _P]),
+    "spsvm_fit_ovo": (_I32, [_P, _I64, _I64, _I64, _P, _I32, _F, C.c_double, _I32, C.c_double,
+                             C.POINTER(spsvm_options), _I32, _P, _P]),
+    "spsvm_predict_ovo_work_bytes": (_SZ, [_I32, _I64]),
+    "spsvm_predict_ovo": (_I32, [_P, _I32, _P, _I64, _I64, _P, _P, _P, _SZ, _P]),
     "spsvm_server_create": (_I32, [_SZ, _I32, C.POINTER(_P)]),
     "spsvm_server_submit_fit": (_I32, [_P, _P, _I64, _I64, _P, _F, _D, _I32, _D,
                                        C.POINTER(spsvm_options), C.POINTER(_I64)]),

@@ -472,6 +472,49 @@ def spsvm_fit_batched(X: torch.Tensor, problems, workers=4, **opts):
     return models, [st[k] for k in range(len(problems))]
 
 
+def spsvm_fit_ovo(X: torch.Tensor, labels, classes, gamma, lam, budget, tol=1e-6, workers=4,
+                  **opts):
+    """One-vs-one: one binary model per class pair (a, b), a < b, in the order
+    (0,1), (0,2), ..., fitted as one batch on the device X (n x d float32);
+    labels: host ints in [0, classes).  Returns (models, statuses)."""
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.stride(1) == 1
+    n, d = X.shape
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    assert lab.shape == (n,)
+    P = classes * (classes - 1) // 2
+    o, keep = make_options(**opts)
+    outs = (C.c_void_p * max(1, P))()
+    st = (C.c_int32 * max(1, P))()
+    rc = _lib().spsvm_fit_ovo(ptr(X), n, d, X.stride(0), lab.ctypes.data, int(classes),
+                              float(gamma), float(lam), int(budget), float(tol), C.byref(o),
+                              int(workers), C.cast(outs, C.c_void_p), C.cast(st, C.c_void_p))
+    del keep
+    models = [Model(outs[k], st[k]) if outs[k] else None for k in range(P)]
+    if rc != L.SPSVM_OK and all(m is None for m in models):
+        check(rc, "spsvm_fit_ovo")
+    return models, [st[k] for k in range(P)]
+
+
+def spsvm_predict_ovo(models, classes, Xq: torch.Tensor, votes=False, stream=None):
+    """Labels (device int32) of the queries by one-vs-one voting over the pair
+    models of spsvm_fit_ovo; with votes=True also the nq x classes vote
+    counts."""
+    _require_cuda(Xq)
+    assert Xq.dtype == torch.float32 and Xq.stride(1) == 1
+    nq = Xq.shape[0]
+    P = classes * (classes - 1) // 2
+    arr = (C.c_void_p * max(1, P))(*[m.handle.value for m in models])
+    wb = _lib().spsvm_predict_ovo_work_bytes(int(classes), nq)
+    work = torch.empty(max(256, wb), dtype=torch.uint8, device=Xq.device)
+    lab = torch.empty(max(1, nq), dtype=torch.int32, device=Xq.device)
+    vt = torch.empty((max(1, nq), classes), dtype=torch.int32, device=Xq.device) if votes else None
+    check(_lib().spsvm_predict_ovo(C.cast(arr, C.c_void_p), int(classes), ptr(Xq), nq, Xq.stride(0),
+                                   ptr(lab), ptr(vt), ptr(work), wb, stream_ptr(stream)),
+          "spsvm_predict_ovo")
+    return (lab[:nq], vt[:nq] if vt is not None else None)
+
+
 class _Borrowed(Model):
     """A model owned by the server (not freed here)."""
 

@@ -125,14 +125,17 @@ def gaussian_mixture(n=500_000, d=128, components=10, sigma_m=1.0,
                          "label_class": label_class})
 
 
-def mixture_holdout(problem: Problem, m: int, seed: int):
+def mixture_holdout(problem: Problem, m: int, seed: int, components=False):
     """Labelled held-out points (float32 X, +-1 y) drawn afresh from the
     same mixture as a gaussian_mixture problem (its component means and
-    scales), labelled the same way."""
+    scales), labelled the same way; with components=True the component
+    index (the multiclass label) instead of y."""
     mu, s = problem.meta["means"], problem.meta["scales"]
     g = _rng(seed)
     comp = g.integers(0, mu.shape[0], size=m)
     X = (mu[comp] + s[comp, None] * g.standard_normal((m, mu.shape[1]))).astype(np.float32)
+    if components:
+        return X, comp.astype(np.int64)
     lc = problem.meta["label_class"]
     y = np.where(comp % 2 == 0, 1.0, -1.0) if lc is None else np.where(comp == lc, 1.0, -1.0)
     return X, y.astype(np.float32)
