@@ -252,6 +252,36 @@ def score_candidates(X, y, J, beta, o, cand, gamma, lam):
     return g * g / (2.0 * h), g, h
 
 
+def score_candidates_exact(X, y, J, beta, o, cand, gamma, lam):
+    """Exact one-dimensional variant of the selection score: f restricted to
+    a new coefficient beta_c (every other coefficient fixed) is convex and
+    piecewise quadratic in beta_c, and Delta_c is its exact decrease,
+    f(beta) - min_t f(beta + t e_c).  The minimiser is found by the exact
+    line search on the basis J + [c] along -sign(g_c) e_c (g_c the first
+    derivative, as in score_candidates), which covers both signs of the new
+    coefficient.  Returns (Delta, t) with t the signed minimiser."""
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    _, g, _ = score_candidates(X, y, J, beta, o, cand, gamma, lam)
+    deltas, ts = [], []
+    for k, c in enumerate(cand):
+        Ja = [int(j) for j in J] + [int(c)]
+        KnJa = rbf_kernel(X, X[Ja], gamma)
+        KJJa = KnJa[Ja]
+        ba = np.concatenate([np.asarray(beta, dtype=np.float64), [0.0]])
+        if g[k] == 0.0:
+            deltas.append(0.0)
+            ts.append(0.0)
+            continue
+        sgn = -1.0 if g[k] > 0 else 1.0
+        d = np.zeros(len(Ja))
+        d[-1] = sgn
+        t = line_search(ba, d, o, KnJa @ d, y, KJJa, lam)
+        deltas.append(objective(ba, KnJa, KJJa, y, lam) - objective(ba + t * d, KnJa, KJJa, y, lam))
+        ts.append(sgn * t)
+    return np.asarray(deltas), np.asarray(ts)
+
+
 def select_top(delta, cand, q):
     """The q candidates with the largest Delta, in decreasing Delta; equal
     scores go to the smaller point index first."""

@@ -308,6 +308,66 @@ def test_growth_stop_rule():
     assert len(stops) >= 3   # the epsilons exercise different rounds
 
 
+def _score_case(seed, n=60, d=3, m=5, lam=1e-2, gamma=0.4):
+    X, y = _blobs(n, d, seed, sep=0.8)
+    g = np.random.default_rng(seed)
+    J = list(g.choice(n, m, replace=False))
+    KnJ = O.rbf_kernel(X, X[J], gamma)
+    beta = 0.3 * g.standard_normal(m)
+    o = KnJ @ beta
+    cand = np.array([c for c in range(n) if c not in J][:12])
+    return X, y, J, beta, o, cand, gamma, lam
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_exact_score_is_the_one_dimensional_minimum(seed):
+    """Delta_c of the exact score equals f(beta) minus the minimum of f over a
+    fine grid of the new coefficient (brute force, refined around the best
+    grid point), and is never below the heuristic's prediction evaluated on
+    the true objective at the heuristic's step -g_c / h_c."""
+    X, y, J, beta, o, cand, gamma, lam = _score_case(seed)
+    dex, tex = O.score_candidates_exact(X, y, J, beta, o, cand, gamma, lam)
+    _, g, h = O.score_candidates(X, y, J, beta, o, cand, gamma, lam)
+    for k, c in enumerate(cand):
+        Ja = J + [int(c)]
+        KnJa = O.rbf_kernel(X, X[Ja], gamma)
+        KJJa = KnJa[Ja]
+        ba = np.concatenate([beta, [0.0]])
+
+        def f(t):
+            b = ba.copy()
+            b[-1] = t
+            return O.objective(b, KnJa, KJJa, y, lam)
+
+        f0 = f(0.0)
+        grid = np.linspace(-20.0, 20.0, 4001)
+        vals = np.array([f(t) for t in grid])
+        t0 = grid[np.argmin(vals)]
+        fine = np.linspace(t0 - 0.01, t0 + 0.01, 2001)
+        best = min(f(t) for t in fine)
+        assert dex[k] >= -1e-14
+        assert abs((f0 - best) - dex[k]) <= 1e-9 * max(1.0, f0)
+        assert abs(f(tex[k]) - best) <= 1e-9 * max(1.0, f0)
+        assert dex[k] >= f0 - f(-g[k] / h[k]) - 1e-12 * max(1.0, f0)
+
+
+def test_exact_score_equals_heuristic_without_margin_crossings():
+    """With every point inside the margin before and after the step (a large
+    lambda keeps the outputs near 0, so y o < 1 throughout), f along the new
+    coefficient is one quadratic piece and its exact decrease is the
+    heuristic's g^2 / (2 h)."""
+    X, y, J, beta, o, cand, gamma, lam = _score_case(4, lam=5.0)
+    beta = 0.01 * beta
+    o = O.rbf_kernel(X, X[J], gamma) @ beta
+    dex, tex = O.score_candidates_exact(X, y, J, beta, o, cand, gamma, lam)
+    dh, g, h = O.score_candidates(X, y, J, beta, o, cand, gamma, lam)
+    for k, c in enumerate(cand):
+        after = o + tex[k] * O.rbf_kernel(X, X[[int(c)]], gamma)[:, 0]
+        assert np.all(y * o < 1) and np.all(y * after < 1)
+    np.testing.assert_allclose(dex, dh, rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(tex, -g / h, rtol=1e-9, atol=1e-15)
+
+
 def test_ovo_pairs_and_hand_counted_votes():
     """One-vs-one voting on decision values counted by hand: three classes,
     pairs (0,1), (0,2), (1,2).  Query 0: 0 beats 1, 2 beats 0, 1 beats 2 --
