@@ -63,6 +63,10 @@ extern "C" {
 #define SPSVM_SOLVE_MIXED 0
 #define SPSVM_SOLVE_FP64  1
 
+/* spsvm_options.score */
+#define SPSVM_SCORE_HEURISTIC 0
+#define SPSVM_SCORE_EXACT     1
+
 /* The growth stop's epsilon in the paper's experiments (Section 5): pass it
  * as spsvm_options.growth_tol to stop growing J when the training error rate
  * falls by less than this per added basis vector (0 runs to the budget). */
@@ -141,6 +145,25 @@ int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o
                            double lambda, int32_t precision, double* g, double* h,
                            double* delta, void* scratch, size_t scratch_bytes,
                            void* stream);
+
+/* Exact one-dimensional variant of the selection score (the variant the
+ * paper's "estimate of the reduction" heuristic approximates): f restricted
+ * to a new coefficient beta_c, every other coefficient fixed, is convex and
+ * piecewise quadratic; for each candidate c = idx[k] its minimiser t[k]
+ * (signed) is found exactly -- 33-point grid passes over the points counting
+ * the margin crossings in each cell, as the line search does, until the
+ * root's cell holds none -- and delta[k] = f(beta) - f(beta + t[k] e_c)
+ * (FP64).  The candidates' kernel rows are computed once, in `precision`,
+ * into scratch; then one cooperative launch (bounded grid barriers) runs
+ * all candidates, in groups of the GPU's co-resident CTAs.  y, o: device, n;
+ * idx: device, kappa; delta, t: device FP64, kappa (t may be NULL);
+ * scratch: device, 256-byte aligned, spsvm_score_exact_scratch_bytes bytes.
+ * A wait that gives up returns SPSVM_ERR_TIMEOUT. */
+size_t spsvm_score_exact_scratch_bytes(int64_t n, int64_t d, int32_t kappa, int32_t precision);
+int spsvm_score_candidates_exact(const spsvm_points* p, const float* y, const float* o,
+                                 const int64_t* idx, int32_t kappa, float gamma, double lambda,
+                                 int32_t precision, double* delta, double* t, void* scratch,
+                                 size_t scratch_bytes, void* stream);
 
 /* Candidate scores without any device allocation or caller scratch.  The
  * paper has no counterpart: this serves callers that must not allocate
@@ -327,6 +350,9 @@ typedef struct spsvm_options {
   int32_t  newton_solver;  /* SPSVM_SOLVE_MIXED (0): FP32 factor + FP64 refinement to FP64
                               backward error, FP64 factorisation when that fails;
                               SPSVM_SOLVE_FP64: FP64 factorisation always */
+  int32_t  score;          /* basis selection: SPSVM_SCORE_HEURISTIC (0), Section 4's
+                              second-order estimate g^2 / (2h); SPSVM_SCORE_EXACT, the
+                              exact one-dimensional decrease (spsvm_score_candidates_exact) */
 } spsvm_options;
 
 /* Per-Newton-step record (kept for every fit). */

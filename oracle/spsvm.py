@@ -369,7 +369,7 @@ class FitResult:
 
 def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         initial_basis=None, grow=True, seed=0, growth_tol=0.0, replay=None,
-        replay_rtol=1e-6):
+        replay_rtol=1e-6, score="heuristic"):
     """SP-SVM (Section 4): alternate basis-vector selection and
     reoptimisation until |J| = budget or the growth stop fires.
 
@@ -397,7 +397,10 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         cand = draw_candidates(n, J, kappa, seed, rnd)
         if len(cand) == 0:
             break
-        delta, _, _ = score_candidates(X, y, J, beta, o, cand, gamma, lam)
+        if score == "exact":
+            delta, _ = score_candidates_exact(X, y, J, beta, o, cand, gamma, lam)
+        else:
+            delta, _, _ = score_candidates(X, y, J, beta, o, cand, gamma, lam)
         qq = min(q, budget - len(J), len(cand))
         chosen = select_top(delta, cand, qq)
         info = dict(candidates=cand, delta=delta, chosen=chosen)

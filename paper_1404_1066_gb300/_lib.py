@@ -26,6 +26,8 @@ SPSVM_BF16X3 = 1
 SPSVM_SOLVE_MIXED = 0
 SPSVM_SOLVE_FP64 = 1
 SPSVM_GROWTH_EPS_PAPER = 5e-6
+SPSVM_SCORE_HEURISTIC = 0
+SPSVM_SCORE_EXACT = 1
 
 PRECISIONS = {"fp32": SPSVM_FP32, "bf16x3": SPSVM_BF16X3}
 
@@ -49,7 +51,7 @@ class spsvm_options(C.Structure):
                 ("seed", C.c_uint64), ("initial_basis", C.POINTER(C.c_int64)),
                 ("n_initial", C.c_int32), ("fixed_basis", C.c_int32),
                 ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p),
-                ("newton_solver", C.c_int32)]
+                ("newton_solver", C.c_int32), ("score", C.c_int32)]
 
 
 class spsvm_problem(C.Structure):
@@ -121,6 +123,9 @@ SIGNATURES = {
     "spsvm_draw_candidates": (_I32, [_I64, _P, _I32, _I32, C.c_uint64, C.c_uint32, _P]),
     "spsvm_fit_batched": (_I32, [_P, _I64, _I64, _I64, C.POINTER(spsvm_problem), _I32,
                                  C.POINTER(spsvm_options), _I32, _P, _P]),
+    "spsvm_score_exact_scratch_bytes": (_SZ, [_I64, _I64, _I32, _I32]),
+    "spsvm_score_candidates_exact": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F,
+                                            C.c_double, _I32, _P, _P, _P, _SZ, _P]),
     "spsvm_fit_ovo": (_I32, [_P, _I64, _I64, _I64, _P, _I32, _F, C.c_double, _I32, C.c_double,
                              C.POINTER(spsvm_options), _I32, _P, _P]),
     "spsvm_predict_ovo_work_bytes": (_SZ, [_I32, _I64]),

@@ -144,6 +144,24 @@ def spsvm_score_candidates(P: Points, y, o, idx, gamma, lam, precision):
     return g, h, delta
 
 
+def spsvm_score_candidates_exact(P: Points, y, o, idx, gamma, lam, precision):
+    """Exact one-dimensional selection scores: (delta, t), FP64 device
+    tensors of the candidates' exact decrease of f and signed minimiser."""
+    n, d = P.X.shape
+    kappa = int(idx.numel())
+    dev = P.X.device
+    delta = torch.empty(max(1, kappa), dtype=torch.float64, device=dev)
+    t = torch.empty_like(delta)
+    sb = _lib().spsvm_score_exact_scratch_bytes(n, d, kappa, _prec(precision))
+    scratch = torch.empty(max(256, sb), dtype=torch.uint8, device=dev)
+    s = P.struct()
+    check(_lib().spsvm_score_candidates_exact(C.byref(s), ptr(y), ptr(o), ptr(idx), kappa,
+                                              float(gamma), float(lam), _prec(precision),
+                                              ptr(delta), ptr(t), ptr(scratch), sb, stream_ptr()),
+          "spsvm_score_candidates_exact")
+    return delta[:kappa], t[:kappa]
+
+
 def spsvm_score_candidates_noalloc(P: Points, y, o, idx, gamma, lam, precision):
     """spsvm_score_candidates without caller scratch: the partial sums go to
     the library's fixed device array (see include/spsvm.h)."""
@@ -308,7 +326,7 @@ def spsvm_draw_candidates(n, J, kappa, seed, round_index):
 # ---------------------------------------------------------------- fit/predict
 def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp32",
                  growth_tol=0.0, rel_tol=0.0, seed=0, initial_basis=None, fixed_basis=False,
-                 refine=0, record=False, stream=None, newton_solver="mixed"):
+                 refine=0, record=False, stream=None, newton_solver="mixed", score="heuristic"):
     o = spsvm_options()
     o.candidates = int(candidates)
     o.add_per_round = int(add_per_round)
@@ -327,6 +345,7 @@ def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp3
     o.record = int(bool(record))
     o.stream = stream_ptr(stream) if torch.cuda.is_available() else None
     o.newton_solver = {"mixed": L.SPSVM_SOLVE_MIXED, "fp64": L.SPSVM_SOLVE_FP64}[newton_solver]
+    o.score = {"heuristic": L.SPSVM_SCORE_HEURISTIC, "exact": L.SPSVM_SCORE_EXACT}[score]
     return o, keep
 
 

@@ -160,7 +160,7 @@ struct Layout {
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int32_t kappa,
-                   int32_t q, int32_t solver) {
+                   int32_t q, int32_t solver, int32_t score) {
   Layout L{};
   L.n = n;
   L.d = d;
@@ -212,6 +212,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   // the Gram split count depends on |J|: cover every size the fit can reach
   for (int64_t mm = 1; mm <= L.jcap; ++mm) sc = std::max(sc, gram_part_bytes(mm, n));
   sc = std::max(sc, spsvm_line_scratch_bytes(n));
+  if (score == SPSVM_SCORE_EXACT) sc = std::max(sc, spsvm_score_exact_scratch_bytes(n, d, kappa, precision));
   L.scratch_bytes = al(sc);
   L.off_scratch = take(L.scratch_bytes);
   L.chw_bytes = spsvm_cholesky_work_bytes(L.jcap);
@@ -226,7 +227,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
 }
 
 struct Opts {
-  int32_t kappa, q, max_newton, precision, refine, record, solver;
+  int32_t kappa, q, max_newton, precision, refine, record, solver, score;
   double growth_tol, rel_tol;
   uint64_t seed;
   bool fixed;
@@ -247,6 +248,7 @@ Opts resolve(const spsvm_options* o) {
   r.fixed = o && o->fixed_basis;
   r.stream = o ? as_stream(o->stream) : nullptr;
   r.solver = (o && o->newton_solver == SPSVM_SOLVE_FP64) ? SPSVM_SOLVE_FP64 : SPSVM_SOLVE_MIXED;
+  r.score = (o && o->score == SPSVM_SCORE_EXACT) ? SPSVM_SCORE_EXACT : SPSVM_SCORE_HEURISTIC;
   return r;
 }
 
@@ -563,9 +565,15 @@ struct Fit {
       if (nc <= 0) break;
       int64_t* cd = at<int64_t>(L.off_cand);
       SPSVM_CUDA_TRY(cudaMemcpyAsync(cd, cand.data(), nc * 8, cudaMemcpyHostToDevice, s));
-      SPSVM_TRY(spsvm_score_candidates(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
-                                       op.precision, at<double>(L.off_cg), at<double>(L.off_ch),
-                                       at<double>(L.off_cd), ws + L.off_scratch, L.scratch_bytes, s));
+      if (op.score == SPSVM_SCORE_EXACT)
+        SPSVM_TRY(spsvm_score_candidates_exact(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
+                                               op.precision, at<double>(L.off_cd),
+                                               at<double>(L.off_cg), ws + L.off_scratch,
+                                               L.scratch_bytes, s));
+      else
+        SPSVM_TRY(spsvm_score_candidates(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
+                                         op.precision, at<double>(L.off_cg), at<double>(L.off_ch),
+                                         at<double>(L.off_cd), ws + L.off_scratch, L.scratch_bytes, s));
       SPSVM_CUDA_TRY(cudaMemcpyAsync(delta.data(), at<double>(L.off_cd), nc * 8,
                                      cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
@@ -655,7 +663,7 @@ extern "C" size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_
                                             const spsvm_options* opt) {
   if (n < 1 || d < 1 || basis_budget < 1) return 0;
   const Opts op = resolve(opt);
-  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver).total;
+  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score).total;
 }
 
 extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
@@ -688,7 +696,7 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     if ((int32_t)J0.size() > basis_budget) basis_budget = (int32_t)J0.size();
   }
   if (op.fixed && J0.empty()) return set_error(SPSVM_ERR_ARG, "fit: fixed_basis needs an initial basis");
-  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver);
+  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score);
   bool own = false;
   if (!workspace) {
     cudaError_t e = cudaMalloc(&workspace, L.total);

@@ -86,6 +86,28 @@ def test_growth_replay_mixture(sp, prec):
     _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
 
 
+def test_growth_replay_exact_score(sp):
+    """Basis selection by the exact one-dimensional score: the oracle replays
+    the GPU's rounds scoring with its own exact scores (every chosen point
+    within 1e-3 of the q-th best), adopts the choices, and the fitted outputs
+    and active set agree."""
+    p = synth.gaussian_mixture(n=2000, d=12, budget=128, seed=13, lam=1e-3)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    m = sp.spsvm_fit(X, y, p.gamma, p.lam, 128, 1e-8, precision="fp32", candidates=64,
+                     add_per_round=32, seed=7, record=True, score="exact")
+    info = m.info()
+    assert info["rounds"] == 4 and info["n_basis"] == 128
+    rep = [dict(candidates=c, chosen=ch) for c, ch in (m.round(k) for k in range(4))]
+    r = O.fit(p.X, p.y, p.gamma, p.lam, 128, tol=1e-10, kappa=64, q=32, seed=7, replay=rep,
+              replay_rtol=1e-3, score="exact")
+    J, beta = m.basis_and_beta()
+    np.testing.assert_array_equal(J, r.J)
+    o = m.outputs(len(p.y))
+    _cmp_decisions(o, r.o)
+    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
+
+
 def test_growth_stop_replay_mixture(sp):
     """Section 4's growth stop on the GPU.  The per-round training error
     rates of a run to budget, replayed by the oracle, fix where the rule

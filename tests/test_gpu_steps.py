@@ -121,6 +121,44 @@ def test_score_candidates(sp, prec):
     assert np.all(rel <= 2 * (gtol / np.abs(gr) + htol / hr) + 1e-12)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_score_candidates_exact(sp, prec):
+    """Exact one-dimensional scores against the oracle's (exact line search
+    along each new coefficient, float64, direct differences) on the same o.
+    The kernel-value errors bound the errors of g and h as for the heuristic
+    score; delta moves by at most |t| dg + t^2 dh / 2 (plus FP32 summation),
+    and t by (dg + |t| dh) / h."""
+    n, d = 2100, 24
+    X, y = _data(n, d, 3)
+    gamma, lam = 1.0 / d, 1e-3
+    g = np.random.default_rng(4)
+    J = g.choice(n, size=40, replace=False)
+    beta = g.standard_normal(40) * 0.3
+    o = (O.rbf_kernel(X, X[J], gamma) @ beta).astype(np.float32).astype(np.float64)
+    pool = np.setdiff1d(np.arange(n), J)
+    cand = g.choice(pool, size=100, replace=False).astype(np.int64)
+    P = sp.spsvm_prepare_points(_t(X), prec)
+    dd, tt = sp.spsvm_score_candidates_exact(P, _t(y), _t(o.astype(np.float32)), _t(cand), gamma,
+                                             lam, prec)
+    dg, tg = dd.cpu().numpy(), tt.cpu().numpy()
+    dref, tref = O.score_candidates_exact(X, y.astype(np.float64), list(J), beta, o, cand, gamma, lam)
+    _, gr, hr = O.score_candidates(X, y.astype(np.float64), list(J), beta, o, cand, gamma, lam)
+    S = y * o < 1
+    res = np.where(S, o - y, 0)
+    Kc = O.rbf_kernel(X, X[cand], gamma)
+    ktol = 4 * 2 ** -24 if prec == "fp32" else 6e-5
+    sq = (X.astype(np.float64) ** 2).sum(1)
+    kerr = ktol * gamma * 2 * sq.max() + 2e-6
+    gtol = 1e-5 * (np.abs(res) @ Kc + lam * np.abs(o[cand])) + kerr * (np.abs(res).sum() + n)
+    htol = 1e-5 * hr + 2 * kerr * n
+    loss0 = 0.5 * np.sum(np.where(S, 1 - y * o, 0) ** 2)
+    dtol = np.abs(tref) * gtol + 0.5 * tref ** 2 * htol + 1e-5 * np.abs(dref) + 1e-6 * loss0 / n
+    assert np.all(dg >= 0)
+    assert np.all(np.abs(dg - dref) <= dtol), float(np.max(np.abs(dg - dref) / dtol))
+    ttol = 2 * (gtol + np.abs(tref) * htol) / hr + 1e-6 * np.abs(tref)
+    assert np.all(np.abs(tg - tref) <= ttol), float(np.max(np.abs(tg - tref) / ttol))
+
+
 @pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("n,m", [(1000, 70), (4099, 129), (33, 1)])
 def test_outputs_gemv(sp, fmt, n, m):
