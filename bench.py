@@ -206,6 +206,12 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
                 workers=workers, budget_gb=budget_gb, arrival_rate=20.0)
 
 
+# DRAM bytes / algorithmic bytes of the GEMV launch, from the ncu capture in
+# profiles/gemv_bf16x3_dram_traffic_n100k.md (None until measured on the
+# current kernel)
+GEMV_TRAFFIC_RATIO = None
+
+
 def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x3"):
     """One-vs-one over a 10-class mixture (the grouped form of Section 5's
     multiclass runs): the 45 pair problems as one batch, then voting on
@@ -229,6 +235,31 @@ def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, preci
     return dict(classes=classes, pairs=len(models), ok=int(sum(1 for s in st if s == 0)), n=n, d=d,
                 basis=budget, fit_s=fit_s, pairs_per_s=len(models) / fit_s, predict_s=pred_s,
                 queries=len(Xq), holdout_accuracy=float(np.mean(lab == cq)), workers=workers)
+
+
+def exact_score_leg(sp, torch, n=100_000, d=128, budget=512, precision="bf16x3"):
+    """Basis selection by Section 4's heuristic estimate against the exact
+    one-dimensional decrease, on a mixture of the bench's kind: fit seconds
+    and held-out accuracy of each."""
+    from paper_1404_1066_gb300 import synth
+    p = synth.gaussian_mixture(n=n, d=d, seed=1007, budget=budget)
+    Xh, yh = synth.mixture_holdout(p, 20_000, seed=90)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    Xhd = torch.from_numpy(Xh).cuda()
+    out = {}
+    for score in ("heuristic", "exact"):
+        sp.spsvm_fit(X, y, p.gamma, p.lam, 64, 1e-6, precision=precision, seed=1, score=score)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = sp.spsvm_fit(X, y, p.gamma, p.lam, budget, 1e-6, precision=precision, candidates=256,
+                         add_per_round=64, seed=1, score=score)
+        torch.cuda.synchronize()
+        fs = time.perf_counter() - t0
+        f = sp.spsvm_predict(m, Xhd).cpu().numpy()
+        out[score] = dict(fit_s=fs, holdout_accuracy=float(np.mean(np.where(f >= 0, 1.0, -1.0) == yh)),
+                          objective=m.info()["objective"], newton_steps=m.info()["newton_steps"])
+    return dict(n=n, d=d, basis=budget, **out)
 
 
 def growth_leg(sp, torch, model, X, y, p, work, opts, stream, holdout=100_000):
@@ -505,8 +536,8 @@ def run_ours(args):
         achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
     # DRAM traffic per launch, measured with ncu on the GEMV at n = 100,000
-    # (1.005 x its algorithmic bytes), scaled to this launch size
-    traffic = per_launch_work * 1.005 if dom == "gemv" else None
+    # (GEMV_TRAFFIC_RATIO x its algorithmic bytes), scaled to this launch size
+    traffic = per_launch_work * GEMV_TRAFFIC_RATIO if dom == "gemv" and GEMV_TRAFFIC_RATIO else None
     roofline = dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit=unit,
                     frac=achieved / peak, traffic=traffic,
                     peak_source=src if bound in ("hbm", "tensor") else "derived",
@@ -516,6 +547,7 @@ def run_ours(args):
 
     batched = batched_leg(sp, torch) if args.batched else None
     ovo = ovo_leg(sp, torch) if args.ovo else None
+    exact = exact_score_leg(sp, torch) if args.exact_score else None
     serve = serve_leg(sp, requests=args.serve_requests) if args.serve_requests > 0 else None
 
     line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
@@ -531,7 +563,8 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, growth_stop=growth, batched=batched, ovo=ovo, serve=serve)
+                fp32_form=fp32_form, growth_stop=growth, batched=batched, ovo=ovo,
+                exact_score=exact, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, factor, cores, sample = cpu_baseline_run(steps=1)
         line["cpu_baseline"] = dict(value=times[0] * factor, unit="s", cores=cores, kind="oracle",
@@ -560,6 +593,8 @@ def main():
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--ovo", type=int, default=1, help="one-vs-one leg (10 classes, 45 pairs)")
+    ap.add_argument("--exact-score", type=int, default=1,
+                    help="heuristic vs exact one-dimensional selection score leg")
     ap.add_argument("--growth", type=int, default=1,
                     help="report the growth stop at epsilon = 5e-6 and accuracy vs |J|")
     ap.add_argument("--micro", choices=["cholesky"], default=None,
