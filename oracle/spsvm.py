@@ -277,8 +277,14 @@ def score_candidates_exact(X, y, J, beta, o, cand, gamma, lam):
         d = np.zeros(len(Ja))
         d[-1] = sgn
         t = line_search(ba, d, o, KnJa @ d, y, KJJa, lam)
-        deltas.append(objective(ba, KnJa, KJJa, y, lam) - objective(ba + t * d, KnJa, KJJa, y, lam))
-        ts.append(sgn * t)
+        # f(beta + x e_c) - f(beta) written out from o (which carries any bias):
+        # lambda x k_cJ beta + lambda/2 x^2 k_cc + 1/2 sum [xi(x)^2 - xi(0)^2]
+        x = sgn * t
+        kc = KnJa[:, -1]
+        reg = lam * x * (KJJa[-1, :-1] @ np.asarray(beta, dtype=np.float64)) + 0.5 * lam * x * x * KJJa[-1, -1]
+        loss = 0.5 * np.sum(np.maximum(0.0, 1.0 - y * (o + x * kc)) ** 2 - np.maximum(0.0, 1.0 - y * o) ** 2)
+        deltas.append(-(reg + loss))
+        ts.append(x)
     return np.asarray(deltas), np.asarray(ts)
 
 
@@ -362,14 +368,15 @@ class FitResult:
     history: list = field(default_factory=list)
     rounds: list = field(default_factory=list)
     status: str = ""
+    bias: float = 0.0
 
     def decision(self, X, Xq, gamma):
-        return predict(Xq, np.asarray(X)[self.J], self.beta, gamma)
+        return predict(Xq, np.asarray(X)[self.J], self.beta, gamma, self.bias)
 
 
 def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         initial_basis=None, grow=True, seed=0, growth_tol=0.0, replay=None,
-        replay_rtol=1e-6, score="heuristic"):
+        replay_rtol=1e-6, score="heuristic", bias=False):
     """SP-SVM (Section 4): alternate basis-vector selection and
     reoptimisation until |J| = budget or the growth stop fires.
 
@@ -377,18 +384,36 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
     other implementation's 'candidates' and 'chosen'.  The oracle then checks
     that its own draw gives the same candidates and that every chosen point
     scores at least (q-th best oracle score) * (1 - replay_rtol), and adopts
-    the chosen list, so that near-ties cannot make the two runs diverge."""
+    the chosen list, so that near-ties cannot make the two runs diverge.
+
+    bias=True adds Eq. 4's bias b as an unregularised coordinate: the Newton
+    iteration runs on the basis extended by a column of ones whose row and
+    column of the regulariser are zero, and the model is f(x) = k(x, X_J)
+    beta + b.  The scores see b through o alone."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     n = X.shape[0]
     J = [] if initial_basis is None else [int(j) for j in initial_basis]
     KnJ = rbf_kernel(X, X[J], gamma) if J else np.zeros((n, 0))
     beta = np.zeros(len(J))
+    b = 0.0
     res = FitResult(J=np.asarray(J, dtype=np.int64), beta=beta, o=np.zeros(n))
     status = ""
     jitter = [-1]
-    if J:
-        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
+
+    def reoptimise(beta, b):
+        if not bias:
+            beta, o, st = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
+            return beta, 0.0, o, st
+        m = KnJ.shape[1]
+        KJJa = np.zeros((m + 1, m + 1))
+        KJJa[1:, 1:] = KnJ[J]
+        ba, o, st = newton(np.hstack([np.ones((n, 1)), KnJ]), KJJa, y, lam,
+                           np.concatenate([[b], beta]), tol, max_newton, res.history, jitter)
+        return ba[1:], ba[0], o, st
+
+    if J or bias:
+        beta, b, o, status = reoptimise(beta, b)
     else:
         o = np.zeros(n)
     E_prev = float(np.mean(y * o <= 0))
@@ -423,7 +448,7 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         J = J + [int(c) for c in chosen]
         KnJ = np.hstack([KnJ, rbf_kernel(X, X[chosen], gamma)])
         beta = np.concatenate([beta, np.zeros(len(chosen))])
-        beta, o, status = newton(KnJ, KnJ[J], y, lam, beta, tol, max_newton, res.history, jitter)
+        beta, b, o, status = reoptimise(beta, b)
         rnd += 1
         E = float(np.mean(y * o <= 0))
         res.rounds[-1]["error_rate"] = E
@@ -432,15 +457,16 @@ def fit(X, y, gamma, lam, budget, tol=1e-8, kappa=256, q=64, max_newton=50,
         E_prev = E
     res.J = np.asarray(J, dtype=np.int64)
     res.beta = beta
+    res.bias = float(b)
     res.o = o
     res.status = status
     return res
 
 
-def predict(Xq, XJ, beta, gamma):
-    """Decision values f(x) = sum_{j in J} beta_j k(x, x_j) (Section 4,
-    h(x) = w^T phi(x) with w restricted to the basis)."""
-    return rbf_kernel(Xq, XJ, gamma) @ beta
+def predict(Xq, XJ, beta, gamma, bias=0.0):
+    """Decision values f(x) = sum_{j in J} beta_j k(x, x_j) + b (Section 4,
+    h(x) = w^T phi(x) with w restricted to the basis; b = 0 unless fitted)."""
+    return rbf_kernel(Xq, XJ, gamma) @ beta + bias
 
 
 def ovo_pairs(classes):

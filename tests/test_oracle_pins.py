@@ -368,6 +368,46 @@ def test_exact_score_equals_heuristic_without_margin_crossings():
     np.testing.assert_allclose(tex, -g / h, rtol=1e-9, atol=1e-15)
 
 
+def test_bias_first_step_is_regularised_least_squares_with_intercept():
+    """Eq. 4 with its bias b on a fixed basis J = all points, lambda large enough
+    that every point stays active: one Newton step from (beta, b) = 0 is the
+    minimiser of lambda/2 beta^T K beta + 1/2 ||K beta + b 1 - y||^2, here
+    found independently as the least-squares solution of the stacked system
+    [K 1; sqrt(lambda) R 0] z = [y; 0] with K = R^T R (SVD-based lstsq)."""
+    X, y = _blobs(40, 3, 31, sep=0.3)
+    gamma, lam = 0.5, 50.0
+    K = O.rbf_kernel(X, X, gamma)
+    r = O.fit(X, y, gamma, lam, 40, tol=1e-12, initial_basis=list(range(40)), grow=False,
+              max_newton=1, bias=True)
+    o = K @ r.beta + r.bias
+    assert np.all(y * o < 1)   # still all active: the one step is the minimiser
+    R = np.linalg.cholesky(K + 1e-12 * np.eye(40)).T
+    A = np.block([[K, np.ones((40, 1))], [np.sqrt(lam) * R, np.zeros((40, 1))]])
+    z = np.linalg.lstsq(A, np.concatenate([y, np.zeros(40)]), rcond=None)[0]
+    np.testing.assert_allclose(r.beta, z[:40], rtol=1e-6, atol=1e-9)
+    assert abs(r.bias - z[40]) <= 1e-8
+
+
+def test_bias_kkt_at_the_optimum():
+    """At a fitted optimum with bias the gradient of Eq. 4 vanishes in both
+    parts: lambda K_JJ beta + K_SJ^T (o_S - y_S) = 0 and sum_{i in S} (o_i - y_i)
+    = 0 (b is not regularised); and with labels all +1 and a huge lambda,
+    beta -> 0 and b -> 1 (each max(0, 1 - b)^2 is minimised at b = 1)."""
+    X, y = _blobs(150, 3, 32, sep=1.0)
+    y = np.where(np.arange(150) % 3 == 0, -y, y)   # unbalanced, overlapping
+    r = O.fit(X, y, 0.4, 1e-2, 24, tol=1e-12, kappa=32, q=8, seed=5, bias=True)
+    KnJ = O.rbf_kernel(X, X[r.J], 0.4)
+    o = KnJ @ r.beta + r.bias
+    np.testing.assert_allclose(o, r.o, rtol=1e-10, atol=1e-12)
+    S = y * o < 1
+    gb = np.sum(o[S] - y[S])
+    gbeta = 1e-2 * (KnJ[r.J] @ r.beta) + KnJ[S].T @ (o[S] - y[S])
+    assert abs(gb) <= 1e-9 * S.sum() and np.linalg.norm(gbeta) <= 1e-9 * S.sum()
+    assert abs(r.bias) > 1e-3   # the bias is used on unbalanced labels
+    r1 = O.fit(X, np.ones(150), 0.4, 1e6, 8, tol=1e-14, kappa=16, q=8, seed=1, bias=True)
+    assert np.max(np.abs(r1.beta)) <= 1e-5 and abs(r1.bias - 1.0) <= 1e-5
+
+
 def test_ovo_pairs_and_hand_counted_votes():
     """One-vs-one voting on decision values counted by hand: three classes,
     pairs (0,1), (0,2), (1,2).  Query 0: 0 beats 1, 2 beats 0, 1 beats 2 --
