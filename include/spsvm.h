@@ -156,14 +156,16 @@ int spsvm_score_candidates(const spsvm_points* p, const float* y, const float* o
  * (FP64).  The candidates' kernel rows are computed once, in `precision`,
  * into scratch; then one cooperative launch (bounded grid barriers) runs
  * all candidates, in groups of the GPU's co-resident CTAs.  y, o: device, n;
- * idx: device, kappa; delta, t: device FP64, kappa (t may be NULL);
+ * idx: device, kappa; bias: device FP64, the model's b when o carries one
+ * (the regulariser's term is lambda (o_c - b)), or NULL; delta, t: device
+ * FP64, kappa (t may be NULL);
  * scratch: device, 256-byte aligned, spsvm_score_exact_scratch_bytes bytes.
  * A wait that gives up returns SPSVM_ERR_TIMEOUT. */
 size_t spsvm_score_exact_scratch_bytes(int64_t n, int64_t d, int32_t kappa, int32_t precision);
 int spsvm_score_candidates_exact(const spsvm_points* p, const float* y, const float* o,
                                  const int64_t* idx, int32_t kappa, float gamma, double lambda,
-                                 int32_t precision, double* delta, double* t, void* scratch,
-                                 size_t scratch_bytes, void* stream);
+                                 int32_t precision, const double* bias, double* delta, double* t,
+                                 void* scratch, size_t scratch_bytes, void* stream);
 
 /* Candidate scores without any device allocation or caller scratch.  The
  * paper has no counterpart: this serves callers that must not allocate
@@ -353,6 +355,9 @@ typedef struct spsvm_options {
   int32_t  score;          /* basis selection: SPSVM_SCORE_HEURISTIC (0), Section 4's
                               second-order estimate g^2 / (2h); SPSVM_SCORE_EXACT, the
                               exact one-dimensional decrease (spsvm_score_candidates_exact) */
+  int32_t  bias;           /* nonzero: fit Eq. 4's bias b as an unregularised coordinate
+                              (f(x) = k(x, X_J) beta + b; spsvm_model_bias reads it); 0: b = 0
+                              as Section 2 does.  Not with refine > 0. */
 } spsvm_options;
 
 /* Per-Newton-step record (kept for every fit). */
@@ -398,6 +403,9 @@ int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t
 int spsvm_model_info(const spsvm_model* model, int32_t* n_basis, int64_t* d,
                      float* gamma, double* lambda, double* objective,
                      int32_t* newton_steps, int32_t* rounds, int32_t* status);
+/* Eq. 4's bias b of the model (0 unless fitted with spsvm_options.bias). */
+int spsvm_model_bias(const spsvm_model* model, double* b);
+
 /* Copies J (host int64, n_basis) and beta (host FP64, n_basis). */
 int spsvm_model_get(const spsvm_model* model, int64_t* basis_idx, double* beta);
 /* Per-step history: copies min(cap, steps) records; *count = steps. */

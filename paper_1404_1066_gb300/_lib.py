@@ -51,7 +51,7 @@ class spsvm_options(C.Structure):
                 ("seed", C.c_uint64), ("initial_basis", C.POINTER(C.c_int64)),
                 ("n_initial", C.c_int32), ("fixed_basis", C.c_int32),
                 ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p),
-                ("newton_solver", C.c_int32), ("score", C.c_int32)]
+                ("newton_solver", C.c_int32), ("score", C.c_int32), ("bias", C.c_int32)]
 
 
 class spsvm_problem(C.Structure):
@@ -125,7 +125,8 @@ SIGNATURES = {
                                  C.POINTER(spsvm_options), _I32, _P, _P]),
     "spsvm_score_exact_scratch_bytes": (_SZ, [_I64, _I64, _I32, _I32]),
     "spsvm_score_candidates_exact": (_I32, [C.POINTER(spsvm_points), _P, _P, _P, _I32, _F,
-                                            C.c_double, _I32, _P, _P, _P, _SZ, _P]),
+                                            C.c_double, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "spsvm_model_bias": (_I32, [_P, C.POINTER(C.c_double)]),
     "spsvm_fit_ovo": (_I32, [_P, _I64, _I64, _I64, _P, _I32, _F, C.c_double, _I32, C.c_double,
                              C.POINTER(spsvm_options), _I32, _P, _P]),
     "spsvm_predict_ovo_work_bytes": (_SZ, [_I32, _I64]),

@@ -144,7 +144,7 @@ def spsvm_score_candidates(P: Points, y, o, idx, gamma, lam, precision):
     return g, h, delta
 
 
-def spsvm_score_candidates_exact(P: Points, y, o, idx, gamma, lam, precision):
+def spsvm_score_candidates_exact(P: Points, y, o, idx, gamma, lam, precision, bias=None):
     """Exact one-dimensional selection scores: (delta, t), FP64 device
     tensors of the candidates' exact decrease of f and signed minimiser."""
     n, d = P.X.shape
@@ -155,8 +155,9 @@ def spsvm_score_candidates_exact(P: Points, y, o, idx, gamma, lam, precision):
     sb = _lib().spsvm_score_exact_scratch_bytes(n, d, kappa, _prec(precision))
     scratch = torch.empty(max(256, sb), dtype=torch.uint8, device=dev)
     s = P.struct()
+    bb = torch.tensor([float(bias)], dtype=torch.float64, device=dev) if bias is not None else None
     check(_lib().spsvm_score_candidates_exact(C.byref(s), ptr(y), ptr(o), ptr(idx), kappa,
-                                              float(gamma), float(lam), _prec(precision),
+                                              float(gamma), float(lam), _prec(precision), ptr(bb),
                                               ptr(delta), ptr(t), ptr(scratch), sb, stream_ptr()),
           "spsvm_score_candidates_exact")
     return delta[:kappa], t[:kappa]
@@ -326,7 +327,8 @@ def spsvm_draw_candidates(n, J, kappa, seed, round_index):
 # ---------------------------------------------------------------- fit/predict
 def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp32",
                  growth_tol=0.0, rel_tol=0.0, seed=0, initial_basis=None, fixed_basis=False,
-                 refine=0, record=False, stream=None, newton_solver="mixed", score="heuristic"):
+                 refine=0, record=False, stream=None, newton_solver="mixed", score="heuristic",
+                 bias=False):
     o = spsvm_options()
     o.candidates = int(candidates)
     o.add_per_round = int(add_per_round)
@@ -346,6 +348,7 @@ def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp3
     o.stream = stream_ptr(stream) if torch.cuda.is_available() else None
     o.newton_solver = {"mixed": L.SPSVM_SOLVE_MIXED, "fp64": L.SPSVM_SOLVE_FP64}[newton_solver]
     o.score = {"heuristic": L.SPSVM_SCORE_HEURISTIC, "exact": L.SPSVM_SCORE_EXACT}[score]
+    o.bias = int(bool(bias))
     return o, keep
 
 
@@ -379,6 +382,11 @@ class Model:
         return dict(n_basis=nb.value, d=d.value, gamma=g.value, lam=lam.value,
                     objective=obj.value, newton_steps=steps.value, rounds=rounds.value,
                     status=st.value)
+
+    def bias(self):
+        b = C.c_double()
+        check(_lib().spsvm_model_bias(self.handle, C.byref(b)), "spsvm_model_bias")
+        return b.value
 
     def basis_and_beta(self):
         nb = self.info()["n_basis"]

@@ -24,6 +24,7 @@ struct spsvm_model {
   int32_t status = SPSVM_OK;
   int32_t rounds = 0;
   int device = 0;
+  double bias = 0.0;             // Eq. 4's b (0 unless fitted)
   float* basis_dev = nullptr;    // |J| x d, row-major
   double* beta_dev = nullptr;
   void* scratch_dev = nullptr;   // decision scratch
@@ -51,13 +52,24 @@ __global__ void sub_kernel(const float* __restrict__ a, const float* __restrict_
     out[i] = a[i] - b[i];
 }
 
-// g_k = lambda o[J_k] + gs_k ; rhs_k = -g_k
+// (K_JJ w)_k from outputs v = K_nJ w read at the basis points: the bias slot
+// (J_k < 0) has no regulariser row, and a bias w_0 (b0) carried by every
+// output is taken off.
+__device__ __forceinline__ double reg_at(const float* __restrict__ v, const int64_t* __restrict__ J,
+                                         int k, const double* __restrict__ b0) {
+  const int64_t j = J[k];
+  if (j < 0) return 0.0;
+  return (double)v[j] - (b0 ? *b0 : 0.0);
+}
+
+// g_k = lambda (K_JJ beta)_k + gs_k ; rhs_k = -g_k
 __global__ void grad_finish(const float* __restrict__ o, const int64_t* __restrict__ J,
                             const double* __restrict__ gs, int32_t m, double lambda,
-                            double* __restrict__ g, double* __restrict__ rhs) {
+                            double* __restrict__ g, double* __restrict__ rhs,
+                            const double* __restrict__ b0) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m) return;
-  const double v = lambda * (double)o[J[k]] + gs[k];
+  const double v = lambda * reg_at(o, J, k, b0) + gs[k];
   g[k] = v;
   rhs[k] = -v;
 }
@@ -93,14 +105,15 @@ __global__ void count_diff(const uint8_t* __restrict__ a, const uint8_t* __restr
   if (threadIdx.x == 0 && c) atomicAdd(out, (unsigned long long)c);
 }
 
-// out[0] = sum_k beta_k o[J_k] ; out[1] = sum g_k^2 ; out[2] = sum r_k^2
+// out[0] = beta^T K_JJ beta ; out[1] = sum g_k^2 ; out[2] = sum r_k^2
 __global__ void small_dots(const double* __restrict__ beta, const float* __restrict__ o,
                            const int64_t* __restrict__ J, const double* __restrict__ g,
-                           const double* __restrict__ r, int32_t m, double* __restrict__ out) {
+                           const double* __restrict__ r, int32_t m, double* __restrict__ out,
+                           const double* __restrict__ b0) {
   __shared__ double sh[32];
   double a = 0.0, b = 0.0, c = 0.0;
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    a += beta[k] * (double)o[J[k]];
+    a += beta[k] * reg_at(o, J, k, b0);
     b += g[k] * g[k];
     c += r[k] * r[k];
   }
@@ -114,6 +127,39 @@ __global__ void small_dots(const double* __restrict__ beta, const float* __restr
     out[1] = b;
     out[2] = c;
   }
+}
+
+// With the bias the heuristic score's lambda o_c term carries b: take it off
+// (h_c does not depend on it).
+__global__ void score_bias_fix(double* __restrict__ g, const double* __restrict__ h,
+                               double* __restrict__ delta, int32_t kappa, double lambda,
+                               const double* __restrict__ b0) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kappa) return;
+  const double gg = g[k] - lambda * (*b0);
+  g[k] = gg;
+  delta[k] = gg * gg / (2.0 * h[k]);
+}
+
+// Row 0 of the kernel matrix as the bias's column of ones (zero past n).
+__global__ void fill_bias_row(void* __restrict__ data, int32_t format, int64_t n, int64_t ld,
+                              int64_t plane) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ld;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (format == SPSVM_FP32) {
+      static_cast<float*>(data)[i] = i < n ? 1.0f : 0.0f;
+    } else {
+      __nv_bfloat16* h = static_cast<__nv_bfloat16*>(data);
+      h[i] = __float2bfloat16_rn(i < n ? 1.0f : 0.0f);
+      h[plane + i] = __float2bfloat16_rn(0.0f);
+    }
+  }
+}
+
+__global__ void add_const(float* __restrict__ v, int64_t n, float c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] += c;
 }
 
 __global__ void add_diag(double* __restrict__ H, int64_t ldh, int32_t m, double shift) {
@@ -160,13 +206,13 @@ struct Layout {
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int32_t kappa,
-                   int32_t q, int32_t solver, int32_t score) {
+                   int32_t q, int32_t solver, int32_t score, int32_t bias) {
   Layout L{};
   L.n = n;
   L.d = d;
   L.ldn = round_up(n > 0 ? n : 1, 128);
   L.ldh = round_up(d, 64);
-  L.jcap = round_up(budget, 64);
+  L.jcap = round_up(budget + (bias ? 1 : 0), 64);   // slot 0 holds the bias
   L.kappa = kappa;
   L.q = q;
   size_t off = 0;
@@ -227,7 +273,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
 }
 
 struct Opts {
-  int32_t kappa, q, max_newton, precision, refine, record, solver, score;
+  int32_t kappa, q, max_newton, precision, refine, record, solver, score, bias;
   double growth_tol, rel_tol;
   uint64_t seed;
   bool fixed;
@@ -249,6 +295,7 @@ Opts resolve(const spsvm_options* o) {
   r.stream = o ? as_stream(o->stream) : nullptr;
   r.solver = (o && o->newton_solver == SPSVM_SOLVE_FP64) ? SPSVM_SOLVE_FP64 : SPSVM_SOLVE_MIXED;
   r.score = (o && o->score == SPSVM_SCORE_EXACT) ? SPSVM_SCORE_EXACT : SPSVM_SCORE_HEURISTIC;
+  r.bias = (o && o->bias) ? 1 : 0;
   return r;
 }
 
@@ -387,9 +434,9 @@ struct Fit {
       // K_SJ is only needed for a new Gram matrix
       SPSVM_TRY(spsvm_compact_active(&K, act, res, y, wsum, r, reuse ? nullptr : &Kc, n_active,
                                      at<int32_t>(L.off_pos), scratch, sb, s));
-      grad_finish<<<mb, tpb, 0, s>>>(o, Jd, wsum, m, op_lambda(), g, rhs);
+      grad_finish<<<mb, tpb, 0, s>>>(o, Jd, wsum, m, op_lambda(), g, rhs, b0());
       SPSVM_LAUNCH_CHECK();
-      small_dots<<<1, 256, 0, s>>>(beta, o, Jd, g, r, m, dots);
+      small_dots<<<1, 256, 0, s>>>(beta, o, Jd, g, r, m, dots, b0());
       SPSVM_LAUNCH_CHECK();
       double dh[3];
       SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
@@ -417,7 +464,7 @@ struct Fit {
         const int rc = solve_with(fac_mixed, fac_shift, rhs, dir, kMixedTol);
         if (rc == SPSVM_OK) {
           SPSVM_TRY(finish_direction(act, fac_mixed, fac_shift));
-          SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
+          SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
           stepped = t > 0.0;
         } else if (rc != SPSVM_ERR_NO_CONVERGE) {
           return rc;
@@ -483,7 +530,7 @@ struct Fit {
         fac_mixed = mixed;
         fac_shift = shift;
         t = 0.0;
-        SPSVM_TRY(spsvm_line_search(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s));
+        SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
         if (t > 0.0 || jitter >= kJitterMaxLevel) break;
         ++jitter;
       }
@@ -526,6 +573,8 @@ struct Fit {
   }
 
   double op_lambda() const { return lambda; }
+  // the bias b = beta_0 on the device when fitted, else NULL
+  const double* b0() const { return op.bias ? reinterpret_cast<const double*>(ws + L.off_beta) : nullptr; }
 
   int run() {
     s = op.stream;
@@ -545,12 +594,20 @@ struct Fit {
     SPSVM_CUDA_TRY(cudaMemsetAsync(ws + L.off_beta, 0, L.jcap * 8, s));
     SPSVM_CUDA_TRY(cudaMemsetAsync(ws + L.off_o, 0, n * 4, s));
     int64_t* Jd = at<int64_t>(L.off_J);
+    // Eq. 4's bias: slot 0 of the basis, point index -1, a row of ones in K
+    const int32_t nb0 = op.bias ? 1 : 0;
+    if (op.bias) J.insert(J.begin(), -1);
     if (!J.empty()) {
       m = (int32_t)J.size();
       SPSVM_CUDA_TRY(cudaMemcpyAsync(Jd, J.data(), m * 8, cudaMemcpyHostToDevice, s));
       spsvm_kmat K = kmat();
-      SPSVM_TRY(spsvm_kernel_block(&pts, Jd, m, gamma, op.precision, &K, 0, ws + L.off_scratch,
-                                   L.scratch_bytes, s));
+      if (op.bias) {
+        fill_bias_row<<<grid_for(K.ld, 256), 256, 0, s>>>(K.data, K.format, n, K.ld, K.plane);
+        SPSVM_LAUNCH_CHECK();
+      }
+      if (m > nb0)
+        SPSVM_TRY(spsvm_kernel_block(&pts, Jd + nb0, m - nb0, gamma, op.precision, &K, nb0,
+                                     ws + L.off_scratch, L.scratch_bytes, s));
       SPSVM_TRY(kjj_fill(&K, Jd, m, 0, at<double>(L.off_kjj), L.jcap, s));
       SPSVM_TRY(newton());
     }
@@ -560,24 +617,30 @@ struct Fit {
     uint32_t round = 0;
     std::vector<int64_t> cand(op.kappa);
     std::vector<double> delta(op.kappa);
-    while (!op.fixed && m < budget) {
+    while (!op.fixed && m - nb0 < budget) {
       const int32_t nc = spsvm_draw_candidates(n, J.data(), m, op.kappa, op.seed, round, cand.data());
       if (nc <= 0) break;
       int64_t* cd = at<int64_t>(L.off_cand);
       SPSVM_CUDA_TRY(cudaMemcpyAsync(cd, cand.data(), nc * 8, cudaMemcpyHostToDevice, s));
-      if (op.score == SPSVM_SCORE_EXACT)
+      if (op.score == SPSVM_SCORE_EXACT) {
         SPSVM_TRY(spsvm_score_candidates_exact(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
-                                               op.precision, at<double>(L.off_cd),
+                                               op.precision, b0(), at<double>(L.off_cd),
                                                at<double>(L.off_cg), ws + L.off_scratch,
                                                L.scratch_bytes, s));
-      else
+      } else {
         SPSVM_TRY(spsvm_score_candidates(&pts, y, at<float>(L.off_o), cd, nc, gamma, lambda,
                                          op.precision, at<double>(L.off_cg), at<double>(L.off_ch),
                                          at<double>(L.off_cd), ws + L.off_scratch, L.scratch_bytes, s));
+        if (op.bias) {
+          score_bias_fix<<<(unsigned)ceil_div((int64_t)nc, (int64_t)256), 256, 0, s>>>(
+              at<double>(L.off_cg), at<double>(L.off_ch), at<double>(L.off_cd), nc, lambda, b0());
+          SPSVM_LAUNCH_CHECK();
+        }
+      }
       SPSVM_CUDA_TRY(cudaMemcpyAsync(delta.data(), at<double>(L.off_cd), nc * 8,
                                      cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
-      const int32_t qq = std::min<int32_t>(std::min(op.q, budget - m), nc);
+      const int32_t qq = std::min<int32_t>(std::min(op.q, budget - (m - nb0)), nc);
       std::vector<int32_t> order(nc);
       std::iota(order.begin(), order.end(), 0);
       std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -610,24 +673,28 @@ struct Fit {
   }
 
   int finish() {
-    model->J = J;
-    model->beta.assign(m, 0.0);
+    // the bias slot (0, when fitted) is kept apart from the basis
+    const int32_t nb0 = op.bias ? 1 : 0;
+    std::vector<double> bh(m, 0.0);
     if (m > 0)
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta.data(), ws + L.off_beta, m * 8,
-                                     cudaMemcpyDeviceToHost, s));
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(bh.data(), ws + L.off_beta, m * 8, cudaMemcpyDeviceToHost, s));
     model->o.assign(n, 0.f);
     SPSVM_CUDA_TRY(cudaMemcpyAsync(model->o.data(), ws + L.off_o, n * 4, cudaMemcpyDeviceToHost, s));
     SPSVM_TRY(sync());
-    if (m > 0) {
-      SPSVM_CUDA_TRY(cudaMalloc(&model->basis_dev, (size_t)m * d * 4));
-      SPSVM_CUDA_TRY(cudaMalloc(&model->beta_dev, (size_t)m * 8));
-      gather_rows<<<(unsigned)ceil_div((int64_t)m * d, 256), 256, 0, s>>>(
-          X, ldx, d, at<int64_t>(L.off_J), m, model->basis_dev);
+    model->bias = (op.bias && m > 0) ? bh[0] : 0.0;
+    model->J.assign(J.begin() + std::min<int32_t>(nb0, m), J.end());
+    model->beta.assign(bh.begin() + std::min<int32_t>(nb0, m), bh.end());
+    const int32_t mr = (int32_t)model->J.size();
+    if (mr > 0) {
+      SPSVM_CUDA_TRY(cudaMalloc(&model->basis_dev, (size_t)mr * d * 4));
+      SPSVM_CUDA_TRY(cudaMalloc(&model->beta_dev, (size_t)mr * 8));
+      gather_rows<<<(unsigned)ceil_div((int64_t)mr * d, 256), 256, 0, s>>>(
+          X, ldx, d, at<int64_t>(L.off_J) + nb0, mr, model->basis_dev);
       SPSVM_LAUNCH_CHECK();
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta_dev, model->beta.data(), m * 8,
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta_dev, model->beta.data(), mr * 8,
                                      cudaMemcpyHostToDevice, s));
     }
-    model->scratch_bytes = spsvm_decision_scratch_bytes(0, m, d);
+    model->scratch_bytes = spsvm_decision_scratch_bytes(0, mr, d);
     SPSVM_CUDA_TRY(cudaMalloc(&model->scratch_dev, model->scratch_bytes));
     return sync();
   }
@@ -663,7 +730,7 @@ extern "C" size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_
                                             const spsvm_options* opt) {
   if (n < 1 || d < 1 || basis_budget < 1) return 0;
   const Opts op = resolve(opt);
-  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score).total;
+  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias).total;
 }
 
 extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
@@ -681,6 +748,8 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
   Opts op = resolve(opt);
   if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16X3)
     return set_error(SPSVM_ERR_ARG, "fit: bad precision %d", op.precision);
+  if (op.bias && op.refine > 0)
+    return set_error(SPSVM_ERR_ARG, "fit: refinement sweeps are not available with the bias");
   std::vector<int64_t> J0;
   if (opt && opt->n_initial > 0) {
     if (!opt->initial_basis) return set_error(SPSVM_ERR_ARG, "fit: NULL initial_basis");
@@ -696,7 +765,7 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     if ((int32_t)J0.size() > basis_budget) basis_budget = (int32_t)J0.size();
   }
   if (op.fixed && J0.empty()) return set_error(SPSVM_ERR_ARG, "fit: fixed_basis needs an initial basis");
-  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score);
+  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias);
   bool own = false;
   if (!workspace) {
     cudaError_t e = cudaMalloc(&workspace, L.total);
@@ -752,13 +821,25 @@ extern "C" int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t 
   if (!model || !Xq || !decision || nq < 0 || ldq < model->d)
     return set_error(SPSVM_ERR_ARG, "predict: bad arguments");
   if (nq == 0) return SPSVM_OK;
+  cudaStream_t s = as_stream(stream);
   if (model->J.empty()) {
-    SPSVM_CUDA_TRY(cudaMemsetAsync(decision, 0, nq * 4, as_stream(stream)));
-    return SPSVM_OK;
+    SPSVM_CUDA_TRY(cudaMemsetAsync(decision, 0, nq * 4, s));
+  } else {
+    SPSVM_TRY(spsvm_decision(model->basis_dev, (int64_t)model->J.size(), model->d, model->beta_dev,
+                             Xq, nq, ldq, model->d, model->gamma, model->precision, decision,
+                             model->scratch_dev, model->scratch_bytes, stream));
   }
-  return spsvm_decision(model->basis_dev, (int64_t)model->J.size(), model->d, model->beta_dev, Xq, nq,
-                        ldq, model->d, model->gamma, model->precision, decision, model->scratch_dev,
-                        model->scratch_bytes, stream);
+  if (model->bias != 0.0) {   // f(x) + b
+    add_const<<<grid_for(nq, 256), 256, 0, s>>>(decision, nq, (float)model->bias);
+    SPSVM_LAUNCH_CHECK();
+  }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_model_bias(const spsvm_model* m, double* b) {
+  if (!m || !b) return set_error(SPSVM_ERR_ARG, "model_bias: NULL argument");
+  *b = m->bias;
+  return SPSVM_OK;
 }
 
 extern "C" int spsvm_model_info(const spsvm_model* m, int32_t* n_basis, int64_t* d, float* gamma,

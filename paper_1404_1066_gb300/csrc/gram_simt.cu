@@ -125,7 +125,8 @@ __global__ void kjj_fill_kernel(KView K, const int64_t* __restrict__ J, int64_t 
   const int64_t rows = m - row0;
   if (e >= rows * m) return;
   const int64_t r = row0 + e / m, c = e % m;
-  const double v = 0.5 * ((double)K.at(c, J[r]) + (double)K.at(r, J[c]));
+  // the bias slot (point index -1) has no regulariser row or column
+  const double v = (J[r] < 0 || J[c] < 0) ? 0.0 : 0.5 * ((double)K.at(c, J[r]) + (double)K.at(r, J[c]));
   kjj[r * ldk + c] = v;
   kjj[c * ldk + r] = v;
 }

@@ -151,4 +151,10 @@ bool tc_available();
 // (stream-ordered copies; returns TIMEOUT with *code set when one gave up).
 int device_status_on(cudaStream_t s, int32_t* code);
 
+// spsvm_line_search with Eq. 4's bias in basis slot 0 (point index -1):
+// b0 = &beta_0 on the device, or NULL without a bias.
+int line_search_impl(const float* o, const float* u, const float* y, int64_t n, const double* d,
+                     const int64_t* J, int32_t m, double lambda, double* t_host, double* t_dev,
+                     void* scratch, size_t scratch_bytes, void* stream, const double* b0);
+
 }  // namespace spsvm

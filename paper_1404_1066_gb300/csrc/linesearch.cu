@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
                                                 const double* __restrict__ d,
                                                 const int64_t* __restrict__ J, int32_t m,
                                                 double lambda, LsPart* __restrict__ part,
-                                                LsState* __restrict__ st, unsigned* __restrict__ bar) {
+                                                LsState* __restrict__ st, unsigned* __restrict__ bar,
+                                                const double* __restrict__ b0) {
   __shared__ double red[LT / 32][LP];
   __shared__ int32_t cnt[LC];
   __shared__ double Fs[LP], sh[32];
@@ -170,11 +171,15 @@ __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
         }
       }
       if (pass == 0) {   // a0 = lambda d^T K_JJ beta, a1 = lambda d^T K_JJ d
+        // (K_JJ beta)_k = o at basis point k (minus the bias b0 = beta_0 when
+        // slot 0, point index -1, holds it; that slot has no regulariser row)
+        const double bb = b0 ? *b0 : 0.0, db = b0 ? d[0] : 0.0;
         double s0 = 0.0, s1 = 0.0;
         for (int k = t; k < m; k += LT) {
           const int64_t j = J[k];
-          s0 += d[k] * (double)o[j];
-          s1 += d[k] * (double)u[j];
+          if (j < 0) continue;
+          s0 += d[k] * ((double)o[j] - bb);
+          s1 += d[k] * ((double)u[j] - db);
         }
         s0 = block_sum(s0, sh);
         __syncthreads();
@@ -289,6 +294,14 @@ extern "C" int spsvm_line_search(const float* o, const float* u, const float* y,
                                  const double* d, const int64_t* J, int32_t m, double lambda,
                                  double* t_host, double* t_dev, void* scratch,
                                  size_t scratch_bytes, void* stream) {
+  return spsvm::line_search_impl(o, u, y, n, d, J, m, lambda, t_host, t_dev, scratch, scratch_bytes,
+                                 stream, nullptr);
+}
+
+int spsvm::line_search_impl(const float* o, const float* u, const float* y, int64_t n,
+                            const double* d, const int64_t* J, int32_t m, double lambda,
+                            double* t_host, double* t_dev, void* scratch, size_t scratch_bytes,
+                            void* stream, const double* b0) {
   if (!o || !u || !y || !d || !J || !t_host || n < 0 || m < 0)
     return set_error(SPSVM_ERR_ARG, "line_search: bad arguments");
   if (!scratch || scratch_bytes < spsvm_line_scratch_bytes(n))
@@ -302,7 +315,7 @@ extern "C" int spsvm_line_search(const float* o, const float* u, const float* y,
   LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
   SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
   void* args[] = {(void*)&o, (void*)&u, (void*)&y, (void*)&n, (void*)&d, (void*)&J,
-                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar};
+                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar, (void*)&b0};
   SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ls_search, dim3(grid), dim3(LT), args, 0, s));
   SPSVM_LAUNCH_CHECK();
   LsState h{};

@@ -76,8 +76,8 @@ __device__ bool xgrid_barrier(unsigned* bar, unsigned nblocks) {
 __global__ void __launch_bounds__(XT) exact_score_kernel(
     KView Kc, int64_t n, const float* __restrict__ y, const float* __restrict__ o,
     const int64_t* __restrict__ idx, int32_t kappa, int32_t cpc, double lambda,
-    ExPart* __restrict__ part, ExState* __restrict__ st, unsigned* __restrict__ ctl,
-    double* __restrict__ delta, double* __restrict__ t_out) {
+    const double* __restrict__ bias, ExPart* __restrict__ part, ExState* __restrict__ st,
+    unsigned* __restrict__ ctl, double* __restrict__ delta, double* __restrict__ t_out) {
   __shared__ double red[XT / 32][XP];
   __shared__ int32_t cnt[XC];
   __shared__ double qred[XT / 32];
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(XT) exact_score_kernel(
     S->lo = 0.0;
     S->hi = 2.0;
     S->t = 0.0;
-    S->a0 = lambda * (double)o[idx[k]];
+    S->a0 = lambda * ((double)o[idx[k]] - (bias ? *bias : 0.0));   // lambda k_cJ beta
     S->sgn = 1.0;
     S->phase = 0;
     S->grow = 0;
@@ -339,9 +339,9 @@ extern "C" size_t spsvm_score_exact_scratch_bytes(int64_t n, int64_t d, int32_t 
 
 extern "C" int spsvm_score_candidates_exact(const spsvm_points* p, const float* y, const float* o,
                                             const int64_t* idx, int32_t kappa, float gamma,
-                                            double lambda, int32_t precision, double* delta,
-                                            double* t, void* scratch, size_t scratch_bytes,
-                                            void* stream) {
+                                            double lambda, int32_t precision, const double* bias,
+                                            double* delta, double* t, void* scratch,
+                                            size_t scratch_bytes, void* stream) {
   if (!p || !y || !o || !idx || !delta || kappa < 0 || !(gamma > 0.0f) || !(lambda > 0.0))
     return set_error(SPSVM_ERR_ARG, "score_exact: bad arguments");
   if (kappa == 0 || p->n == 0) return SPSVM_OK;
@@ -377,8 +377,8 @@ extern "C" int spsvm_score_candidates_exact(const spsvm_points* p, const float* 
     unsigned* ctl = reinterpret_cast<unsigned*>(w + ly.ctl);
     int64_t n = p->n;
     void* args[] = {(void*)&kv, (void*)&n, (void*)&y, (void*)&o, (void*)&ix, (void*)&kk,
-                    (void*)&cpc, (void*)&lambda, (void*)&part, (void*)&st, (void*)&ctl,
-                    (void*)&dl, (void*)&tt};
+                    (void*)&cpc, (void*)&lambda, (void*)&bias, (void*)&part, (void*)&st,
+                    (void*)&ctl, (void*)&dl, (void*)&tt};
     SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)exact_score_kernel, dim3((unsigned)(kk * cpc)),
                                                dim3(XT), args, 0, s));
     SPSVM_LAUNCH_CHECK();

@@ -108,6 +108,49 @@ def test_growth_replay_exact_score(sp):
     _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
 
 
+@pytest.mark.parametrize("prec,score", [("fp32", "heuristic"), ("bf16x3", "heuristic"),
+                                        ("fp32", "exact")])
+def test_growth_replay_with_bias(sp, prec, score):
+    """Eq. 4's bias b as an unregularised coordinate on unbalanced labels (one
+    class of four against the rest): the oracle replays the GPU's rounds with
+    its own bias-aware fit; the basis is the same, the outputs, the active set
+    and b agree, and predictions carry b."""
+    p = synth.gaussian_mixture(n=2400, d=10, components=4, label_class=0, budget=96, seed=17,
+                               lam=1e-3)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    m = sp.spsvm_fit(X, y, p.gamma, p.lam, 96, 1e-8, precision=prec, candidates=64,
+                     add_per_round=32, seed=9, record=True, score=score, bias=True)
+    info = m.info()
+    assert info["rounds"] == 3 and info["n_basis"] == 96
+    rep = [dict(candidates=c, chosen=ch) for c, ch in (m.round(k) for k in range(3))]
+    r = O.fit(p.X, p.y, p.gamma, p.lam, 96, tol=1e-10, kappa=64, q=32, seed=9, replay=rep,
+              replay_rtol=1e-3, score=score, bias=True)
+    J, beta = m.basis_and_beta()
+    np.testing.assert_array_equal(J, r.J)
+    b = m.bias()
+    assert abs(r.bias) > 1e-2   # the labels need the bias
+    assert abs(b - r.bias) <= (1e-4 if prec == "fp32" else 1e-3) * max(1.0, abs(r.bias))
+    o = m.outputs(len(p.y))
+    # training outputs from the stored kernel matrix: BF16X3's hi + lo values
+    # carry ~1e-5 relative error, so its outputs get the looser bound and tie
+    # band the other BF16X3 comparisons use
+    bf = prec == "bf16x3"
+    _cmp_decisions(o, r.o, rtol=5e-4 if bf else 1e-4)
+    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64), band=1e-3 if bf else 1e-5)
+    Xq = synth.queries_like(p, 300, seed=4)
+    f = sp.spsvm_predict(m, torch.from_numpy(Xq).cuda()).cpu().numpy().astype(np.float64)
+    fr = O.predict(Xq, p.X[J], beta, p.gamma, b)
+    np.testing.assert_allclose(f, fr, rtol=0, atol=(1e-5 if prec == "fp32" else 5e-4) * max(1.0, np.abs(fr).max()))
+
+
+def test_bias_argument_errors(sp):
+    X = torch.zeros((10, 3), device="cuda")
+    y = torch.ones(10, device="cuda")
+    with pytest.raises(sp.SpsvmError):
+        sp.spsvm_fit(X, y, 1.0, 1e-3, 5, bias=True, refine=1)
+
+
 def test_growth_stop_replay_mixture(sp):
     """Section 4's growth stop on the GPU.  The per-round training error
     rates of a run to budget, replayed by the oracle, fix where the rule
