@@ -209,9 +209,8 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
 
 
 # DRAM bytes / algorithmic bytes of the GEMV launch, from the ncu capture in
-# profiles/gemv_bf16x3_dram_traffic_n100k.md (None until measured on the
-# current kernel)
-GEMV_TRAFFIC_RATIO = None
+# profiles/gemv_bf16x3_dram_traffic_n100k.md (median over its launches)
+GEMV_TRAFFIC_RATIO = 1.002
 
 
 def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x3"):
