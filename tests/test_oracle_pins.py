@@ -351,6 +351,32 @@ def test_exact_score_is_the_one_dimensional_minimum(seed):
         assert dex[k] >= f0 - f(-g[k] / h[k]) - 1e-12 * max(1.0, f0)
 
 
+def test_exact_score_with_bias_is_the_one_dimensional_minimum():
+    """With a bias b carried by o the exact score's decrease equals f(beta, b)
+    minus the minimum over the new coefficient of the bias-aware objective
+    lambda/2 beta^T K_JJ beta + 1/2 sum max(0, 1 - y (K beta + b))^2 (brute
+    force on a grid refined around its best point)."""
+    X, y, J, beta, o, cand, gamma, lam = _score_case(5)
+    b = 0.37
+    o = o + b
+    dex, tex = O.score_candidates_exact(X, y, J, beta, o, cand, gamma, lam)
+    for k, c in enumerate(cand[:6]):
+        Ja = J + [int(c)]
+        KnJa = O.rbf_kernel(X, X[Ja], gamma)
+        KJJa = KnJa[Ja]
+
+        def f(t):
+            ba = np.concatenate([beta, [t]])
+            oo = KnJa @ ba + b
+            return 0.5 * lam * ba @ (KJJa @ ba) + 0.5 * np.sum(np.maximum(0.0, 1.0 - y * oo) ** 2)
+
+        grid = np.linspace(-20.0, 20.0, 4001)
+        t0 = grid[np.argmin([f(t) for t in grid])]
+        best = min(f(t) for t in np.linspace(t0 - 0.01, t0 + 0.01, 2001))
+        assert abs((f(0.0) - best) - dex[k]) <= 1e-9 * max(1.0, f(0.0))
+        assert abs(f(tex[k]) - best) <= 1e-9 * max(1.0, f(0.0))
+
+
 def test_exact_score_equals_heuristic_without_margin_crossings():
     """With every point inside the margin before and after the step (a large
     lambda keeps the outputs near 0, so y o < 1 throughout), f along the new
