@@ -213,6 +213,15 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
 GEMV_TRAFFIC_RATIO = 1.002
 
 
+def _leg(fn, *a, **k):
+    """An auxiliary leg of the bench line: its result, or its error, without
+    losing the line's headline measurement."""
+    try:
+        return fn(*a, **k)
+    except Exception as e:   # reported in the JSON line instead
+        return dict(error=f"{type(e).__name__}: {e}")
+
+
 def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x3"):
     """One-vs-one over a 10-class mixture (the grouped form of Section 5's
     multiclass runs): the 45 pair problems as one batch, then voting on
@@ -483,28 +492,33 @@ def run_ours(args):
     # held-out accuracy at the end) on fresh points of the same mixture
     growth = None
     if args.growth:
-        growth = growth_leg(sp, torch, model, X, y, p, work, opts, stream)
+        growth = _leg(growth_leg, sp, torch, model, X, y, p, work, opts, stream)
 
     # FP32 form on the same workload (one fit), for the "vs FP32 form" leg
     fp32_form = None
     if args.fp32_form and prec != "fp32":
         del work
         torch.cuda.empty_cache()
-        o32, _ = sp.make_options(**dict(opts, precision="fp32"))
-        w32 = torch.empty(lib.spsvm_fit_workspace_bytes(n, d, J, C.byref(o32)), dtype=torch.uint8,
-                          device="cuda")
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        m32 = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=w32, **dict(opts, precision="fp32"))
-        a1.record(stream)
-        torch.cuda.synchronize()
-        f32 = sp.spsvm_predict(m32, Xq).cpu().numpy()
-        fb = f.cpu().numpy()
-        fp32_form = dict(fit_s=a0.elapsed_time(a1) / 1e3,
-                         label_agreement_with_bf16x3=float(np.mean(np.sign(fb) == np.sign(f32))),
-                         newton_steps=m32.info()["newton_steps"])
-        del w32
+
+        def fp32_leg():
+            o32, _ = sp.make_options(**dict(opts, precision="fp32"))
+            w32 = torch.empty(lib.spsvm_fit_workspace_bytes(n, d, J, C.byref(o32)), dtype=torch.uint8,
+                              device="cuda")
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            m32 = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=w32,
+                               **dict(opts, precision="fp32"))
+            a1.record(stream)
+            torch.cuda.synchronize()
+            f32 = sp.spsvm_predict(m32, Xq).cpu().numpy()
+            fb = f.cpu().numpy()
+            return dict(fit_s=a0.elapsed_time(a1) / 1e3,
+                        label_agreement_with_bf16x3=float(np.mean(np.sign(fb) == np.sign(f32))),
+                        newton_steps=m32.info()["newton_steps"])
+
+        fp32_form = _leg(fp32_leg)
+        torch.cuda.empty_cache()
 
     # roofline for the dominant kernel of the step
     peaks, src = _peaks()
@@ -546,10 +560,10 @@ def run_ours(args):
     if note:
         roofline["note"] = note
 
-    batched = batched_leg(sp, torch) if args.batched else None
-    ovo = ovo_leg(sp, torch) if args.ovo else None
-    exact = exact_score_leg(sp, torch) if args.exact_score else None
-    serve = serve_leg(sp, requests=args.serve_requests) if args.serve_requests > 0 else None
+    batched = _leg(batched_leg, sp, torch) if args.batched else None
+    ovo = _leg(ovo_leg, sp, torch) if args.ovo else None
+    exact = _leg(exact_score_leg, sp, torch) if args.exact_score else None
+    serve = _leg(serve_leg, sp, requests=args.serve_requests) if args.serve_requests > 0 else None
 
     line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=False, scaling="weak",
