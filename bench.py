@@ -141,7 +141,7 @@ def cpu_baseline_run(seconds_budget=20.0, steps=1):
         f"scaled by (n ratio) x (|J| ratio)^3 = {factor:.3g} to the full workload"
 
 
-def batched_leg(sp, torch, workers=8, precision="bf16x3"):
+def batched_leg(sp, torch, workers=8, precision="bf16x4"):
     """One-vs-rest 10 classes x gamma in {0.25,0.5,1,2}/d x lambda in
     {1e-3,1e-4,1e-5} = 120 solves on seeded subsamples of a shared
     60,000 x 256 mixture, |J| in [256, 2048]."""
@@ -162,7 +162,7 @@ def batched_leg(sp, torch, workers=8, precision="bf16x3"):
                 basis_mean=float(np.mean([p["budget"] for p in probs])))
 
 
-def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
+def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x4"):
     """Poisson arrivals (mean 20 requests/s) of fit requests (n log-uniform in
     [1k, 200k], d in {32, 128, 784}, |J| in {128, ..., 2048}, mixture data)
     interleaved with predict requests of 1k-100k points; HBM admission budget
@@ -208,9 +208,9 @@ def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x3"):
                 workers=workers, budget_gb=budget_gb, arrival_rate=20.0)
 
 
-# DRAM bytes / algorithmic bytes of the GEMV launch, from the ncu capture in
-# profiles/gemv_bf16x3_dram_traffic_n100k.md (median over its launches)
-GEMV_TRAFFIC_RATIO = 1.002
+# DRAM bytes / algorithmic bytes of the GEMV launch, from an ncu capture of
+# the current kernel (None until one is taken: the line then reports null)
+GEMV_TRAFFIC_RATIO = None
 
 
 def _leg(fn, *a, **k):
@@ -222,7 +222,7 @@ def _leg(fn, *a, **k):
         return dict(error=f"{type(e).__name__}: {e}")
 
 
-def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x3"):
+def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, precision="bf16x4"):
     """One-vs-one over a 10-class mixture (the grouped form of Section 5's
     multiclass runs): the 45 pair problems as one batch, then voting on
     fresh points of the same mixture."""
@@ -247,7 +247,7 @@ def ovo_leg(sp, torch, n=60_000, d=256, classes=10, budget=256, workers=8, preci
                 queries=len(Xq), holdout_accuracy=float(np.mean(lab == cq)), workers=workers)
 
 
-def exact_score_leg(sp, torch, n=100_000, d=128, budget=512, precision="bf16x3"):
+def exact_score_leg(sp, torch, n=100_000, d=128, budget=512, precision="bf16x4"):
     """Basis selection by Section 4's heuristic estimate against the exact
     one-dimensional decrease, on a mixture of the bench's kind: fit seconds
     and held-out accuracy of each."""
@@ -471,7 +471,7 @@ def run_ours(args):
     # kernel-block throughput: the full n x |J| block of the final basis
     Jidx = torch.from_numpy(model.basis_and_beta()[0]).cuda()
     P = sp.spsvm_prepare_points(X, prec)
-    km = sp.kmat_empty(n, J, prec)
+    km = sp.kmat_empty(n, J, "fp32")   # K_nJ is stored in FP32 in both forms
     for _ in range(2):
         sp.spsvm_kernel_block(P, Jidx, p.gamma, prec, km)
     kb0 = torch.cuda.Event(enable_timing=True)
@@ -483,7 +483,7 @@ def run_ours(args):
     kb1.record(stream)
     torch.cuda.synchronize()
     kb_ms = kb0.elapsed_time(kb1) / reps
-    split = 3.0 if prec == "bf16x3" else 1.0
+    split = 4.0 if prec == "bf16x4" else 1.0   # hi/lo plane products per FP32 product
     kb_tflops = split * 2.0 * n * J * d / (kb_ms * 1e-3) / 1e12
     del km
 
@@ -514,7 +514,7 @@ def run_ours(args):
             f32 = sp.spsvm_predict(m32, Xq).cpu().numpy()
             fb = f.cpu().numpy()
             return dict(fit_s=a0.elapsed_time(a1) / 1e3,
-                        label_agreement_with_bf16x3=float(np.mean(np.sign(fb) == np.sign(f32))),
+                        label_agreement_with_bf16x4=float(np.mean(np.sign(fb) == np.sign(f32))),
                         newton_steps=m32.info()["newton_steps"])
 
         fp32_form = _leg(fp32_leg)
@@ -529,10 +529,10 @@ def run_ours(args):
     per_launch_work = pr["work"] / max(1, pr["launches"])
     fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x 2 flops x max clock (80.5)
     note = None
-    if dom in ("gram", "kernel_block", "score", "decision") and prec == "bf16x3":
+    if dom in ("gram", "kernel_block", "score", "decision") and prec == "bf16x4":
+        # the library counts the four plane products in the work of the form
         bound, unit = "tensor", "TFLOP/s"
-        products = 4.0 if dom == "gram" else 3.0    # split-BF16 products per FP32 product
-        achieved = products * per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
     elif dom in ("gram", "kernel_block", "score", "decision"):
         bound, unit = "alu", "TFLOP/s"
@@ -567,7 +567,8 @@ def run_ours(args):
 
     line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=False, scaling="weak",
-                vs_baseline=None, dtype="bf16x3+f64" if prec == "bf16x3" else "f32+f64",
+                vs_baseline=None,
+                dtype=("bf16x4" if prec == "bf16x4" else "f32") + " kernel/Gram, f32 factor + f64 refinement",
                 data="synthetic",
                 config=dict(WORKLOAD, precision=prec, l2="inputs larger than L2 (no flush)",
                             step="fit + predict(100k queries)", parallelism=f"replicas{ws}"),
@@ -597,7 +598,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--precision", default="bf16x4", choices=["bf16x4", "fp32"])
     ap.add_argument("--n", type=int, default=500_000)
     ap.add_argument("--d", type=int, default=128)
     ap.add_argument("--basis", type=int, default=4096)

@@ -48,16 +48,19 @@ extern "C" {
 #define SPSVM_ERR_BUSY        (-7)  /* server: request not admitted yet */
 
 /* ---- arithmetic forms -------------------------------------------------- */
-/* SPSVM_FP32: kernel block and Gram matrix in FP32 SIMT arithmetic, kernel
- *   matrix stored in FP32.
- * SPSVM_BF16X3: kernel block and Gram matrix on tcgen05 tensor cores with
- *   each FP32 operand split as hi + lo (both BF16) and the three products
- *   hi*hi + hi*lo + lo*hi accumulated in FP32; kernel matrix stored as the
- *   BF16 hi and lo planes.
- * In both forms the Cholesky factorisation, triangular solves and the
- * refinement of the Newton direction run in FP64. */
+/* SPSVM_FP32: kernel block and Gram matrix in FP32 SIMT arithmetic.
+ * SPSVM_BF16X4: kernel block and Gram matrix on tcgen05 tensor cores with
+ *   each FP32 operand split as hi + lo (both BF16, lo = bf16(x - hi)) and all
+ *   four products hi*hi + hi*lo + lo*hi + lo*lo accumulated in FP32 (the
+ *   exact product of the two-term representations).
+ * Both forms store the kernel matrix K_nJ in FP32; the BF16X4 fit keeps the
+ * compact copy K_SJ, the Gram matrix's operand, as hi / lo BF16 planes.  In
+ * both forms the Newton system is, by default, factored in FP32 and solved
+ * with FP64 iterative refinement to FP64 backward error (SPSVM_SOLVE_MIXED),
+ * or factored in FP64 (SPSVM_SOLVE_FP64, and the fallback of the mixed
+ * solve when its FP32 factor breaks down or the refinement stalls). */
 #define SPSVM_FP32    0
-#define SPSVM_BF16X3  1
+#define SPSVM_BF16X4  1
 
 /* Newton-system solvers (spsvm_options.newton_solver). */
 #define SPSVM_SOLVE_MIXED 0
@@ -74,21 +77,22 @@ extern "C" {
 
 /* ---- stored kernel matrix ---------------------------------------------- */
 /* K_nJ stored basis-major: row j (one basis vector) holds k(x_i, x_{J_j})
- * for i = 0..n-1 contiguously.  FP32: element (j, i) at
- * ((float*)data)[j*ld + i].  BF16X3: hi plane at ((uint16_t*)data)[j*ld + i],
- * lo plane at ((uint16_t*)data)[plane + j*ld + i]; value = hi + lo.
+ * for i = 0..n-1 contiguously.  format SPSVM_FP32: element (j, i) at
+ * ((float*)data)[j*ld + i].  format SPSVM_BF16X4 (two BF16 planes): hi plane
+ * at ((uint16_t*)data)[j*ld + i], lo plane at ((uint16_t*)data)[plane +
+ * j*ld + i]; value = hi + lo.
  * ld and plane are in elements; ld >= n, ld % 8 == 0, data 16-byte aligned. */
 typedef struct spsvm_kmat {
   void*   data;     /* device */
-  int32_t format;   /* SPSVM_FP32 or SPSVM_BF16X3 */
+  int32_t format;   /* SPSVM_FP32 or SPSVM_BF16X4 */
   int32_t pad_;
   int64_t n;        /* points (columns of the stored matrix) */
   int64_t rows;     /* basis vectors stored */
   int64_t ld;       /* elements between consecutive rows */
-  int64_t plane;    /* elements between hi and lo planes (BF16X3 only) */
+  int64_t plane;    /* elements between hi and lo planes (BF16X4 only) */
 } spsvm_kmat;
 
-/* Points prepared once per X: squared norms and, for SPSVM_BF16X3, the BF16
+/* Points prepared once per X: squared norms and, for SPSVM_BF16X4, the BF16
  * split planes (hi = bf16(x), lo = bf16(x - hi)), each n x ldh with the
  * columns d..ldh-1 zero.  All pointers device; X is borrowed. */
 typedef struct spsvm_points {
@@ -107,7 +111,7 @@ typedef struct spsvm_points {
 
 /* Row norms ||x_i||^2 of the RBF distance expansion
  * ||x - z||^2 = ||x||^2 + ||z||^2 - 2 x^T z (Section 2, RBF kernel); and for
- * precision == SPSVM_BF16X3 the hi/lo planes.  Fills p->norms (and p->hi,
+ * precision == SPSVM_BF16X4 the hi/lo planes.  Fills p->norms (and p->hi,
  * p->lo), which the caller allocated.  Errors: ARG if a pointer is NULL or
  * n < 0, d < 1, ldx < d, ldh < d or ldh % 64 != 0. */
 int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* stream);
@@ -115,10 +119,10 @@ int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* stream);
 /* Kernel block (Section 2 RBF; Section 4: K_nJ, O(|J| n) memory):
  *   out row (row0 + c), column i  =  exp(-gamma * max(0, ||x_i||^2 +
  *   ||x_{idx[c]}||^2 - 2 x_i^T x_{idx[c]}))   for c < m, i < n.
- * idx: device, m indices into the points.  out->format selects FP32 or
- * BF16X3 storage and must match `precision` (SPSVM_FP32 arithmetic may store
- * either).  Requires row0 + m <= out->rows.  scratch: device, at least
- * spsvm_kernel_block_scratch_bytes(m, d, precision) bytes (the BF16X3 form
+ * idx: device, m indices into the points.  The dot products are formed in
+ * `precision`; out->format selects the storage (FP32 or the two BF16
+ * planes), in either form.  Requires row0 + m <= out->rows.  scratch: device, at least
+ * spsvm_kernel_block_scratch_bytes(m, d, precision) bytes (the BF16X4 form
  * gathers the m basis rows there; 0 bytes for SPSVM_FP32).  Errors: ARG,
  * OOM (scratch too small). */
 size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision);
@@ -216,9 +220,11 @@ int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_t accumulat
  *   w1out_j = sum_{i active} w1_i K_ji,  w2out_j = sum_{i active} w2_i K_ji
  *   (each optional: NULL skips it).
  * active: device n bytes; w1, w2: device FP32 n; outputs device FP64.
- * n_active: device int64, written with |S|.  Kc must have the format of K,
- * the same rows and Kc->n >= |S| rounded up to 128 (Kc->n = round_up(n,128)
- * is always enough).  scratch: spsvm_compact_scratch_bytes(n, K->rows). */
+ * n_active: device int64, written with |S|.  Kc must have the format of K
+ * (or, for an FP32 K, the two BF16 planes: each value is then split as
+ * hi = bf16(v), lo = bf16(v - hi)), the same rows and Kc->n >= |S| rounded
+ * up to 128 (Kc->n = round_up(n,128) is always enough).  scratch:
+ * spsvm_compact_scratch_bytes(n, K->rows). */
 size_t spsvm_compact_scratch_bytes(int64_t n, int64_t rows);
 int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active,
                          const float* w1, const float* w2, double* w1out,
@@ -335,12 +341,11 @@ typedef struct spsvm_options {
   int32_t  candidates;     /* kappa, points sampled per selection round (0 -> 256) */
   int32_t  add_per_round;  /* q, basis vectors added per round (0 -> 64) */
   int32_t  max_newton;     /* Newton steps per reoptimisation (0 -> 50) */
-  int32_t  precision;      /* SPSVM_FP32 (0) or SPSVM_BF16X3 */
+  int32_t  precision;      /* SPSVM_FP32 (0) or SPSVM_BF16X4 */
   double   growth_tol;     /* Section 4 stop: (change in training error rate) /
                               (vectors added) < growth_tol; 0 -> run to budget.
                               Section 5 uses 5e-6. */
-  double   rel_tol;        /* also stop Newton when ||grad|| <= rel_tol ||r||
-                              (0 -> 1e-6 FP32, 2e-5 BF16X3) */
+  double   rel_tol;        /* gradient level of the Newton stop (0 -> 1e-6): see spsvm_fit */
   uint64_t seed;           /* candidate draw: counter-based splitmix64 */
   const int64_t* initial_basis;  /* host, n_initial indices (fixed basis), or NULL */
   int32_t  n_initial;
@@ -382,9 +387,15 @@ size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_budget,
  * spsvm_score_candidates, the q best appended) and reoptimisation of Eq. 4
  * by Newton steps with exact line search, until |J| = basis_budget or the
  * growth stop fires.  X: device, n x d (ldx); y: device, n values +-1.
- * gamma > 0, lambda > 0, 1 <= basis_budget <= n.  Newton stops at
- * ||grad|| <= max(tol, rel_tol ||r||), when the active set repeats after a
- * full step, or at max_newton.  workspace: device, spsvm_fit_workspace_bytes
+ * gamma > 0, lambda > 0, 1 <= basis_budget <= n.  The Newton iteration of a
+ * round stops at ||grad|| <= tol; or, once ||grad|| <= rel_tol ||r|| (r =
+ * K_SJ^T y_S), when the next Newton step is below 1e-5 ||beta|| (it is not
+ * taken), or when a step that kept the active set
+ * did not halve ||grad|| or found no descent (rounding level); once the
+ * fit runs with a diagonal jitter (beta is then not determined beyond the
+ * gradient), at ||grad|| <= max(rel_tol, 5e-6) ||r||; or at max_newton
+ * (NO_CONVERGE).
+ * workspace: device, spsvm_fit_workspace_bytes
  * bytes, or NULL to let the library allocate (and free) it.  On success
  * *out is a self-contained model (basis rows copied).  Returns OK,
  * NO_CONVERGE (model still returned), or an error (no model).

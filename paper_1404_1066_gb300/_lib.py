@@ -22,14 +22,14 @@ SPSVM_ERR_TIMEOUT = -6
 SPSVM_ERR_BUSY = -7
 
 SPSVM_FP32 = 0
-SPSVM_BF16X3 = 1
+SPSVM_BF16X4 = 1
 SPSVM_SOLVE_MIXED = 0
 SPSVM_SOLVE_FP64 = 1
 SPSVM_GROWTH_EPS_PAPER = 5e-6
 SPSVM_SCORE_HEURISTIC = 0
 SPSVM_SCORE_EXACT = 1
 
-PRECISIONS = {"fp32": SPSVM_FP32, "bf16x3": SPSVM_BF16X3}
+PRECISIONS = {"fp32": SPSVM_FP32, "bf16x4": SPSVM_BF16X4}
 
 
 class spsvm_kmat(C.Structure):

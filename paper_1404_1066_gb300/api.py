@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from ._lib import (SPSVM_BF16X3, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
+from ._lib import (SPSVM_BF16X4, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
                    spsvm_kmat, spsvm_options, spsvm_points, spsvm_problem, spsvm_step)
 
 
@@ -60,7 +60,7 @@ def spsvm_prepare_points(X: torch.Tensor, precision="fp32") -> Points:
     p = _prec(precision)
     norms = torch.empty(n, dtype=torch.float32, device=X.device)
     hi = lo = None
-    if p == SPSVM_BF16X3:
+    if p == SPSVM_BF16X4:
         hi = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
         lo = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
     P = Points(X, norms, hi, lo, ldh)
@@ -91,7 +91,7 @@ class KMat:
         return s
 
     def to_float(self, rows=None):
-        """FP32 copy of rows x n (hi + lo for BF16X3), on the device."""
+        """FP32 copy of rows x n (hi + lo for BF16X4), on the device."""
         r = self.rows if rows is None else rows
         if self.format == SPSVM_FP32:
             return self.buf.view(-1)[: r * self.ld].view(r, self.ld)[:, : self.n].clone()

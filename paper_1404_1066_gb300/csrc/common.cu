@@ -36,12 +36,12 @@ int sm_count() {
 
 int check_kmat(const spsvm_kmat* K, const char* what) {
   if (!K || !K->data) return set_error(SPSVM_ERR_ARG, "%s: NULL kernel matrix", what);
-  if (K->format != SPSVM_FP32 && K->format != SPSVM_BF16X3)
+  if (K->format != SPSVM_FP32 && K->format != SPSVM_BF16X4)
     return set_error(SPSVM_ERR_ARG, "%s: bad format %d", what, K->format);
   if (K->n < 0 || K->rows < 0 || K->ld < K->n || (K->ld % 8) != 0)
     return set_error(SPSVM_ERR_ARG, "%s: bad shape n=%lld rows=%lld ld=%lld", what,
                      (long long)K->n, (long long)K->rows, (long long)K->ld);
-  if (K->format == SPSVM_BF16X3 && K->plane < K->rows * K->ld)
+  if (K->format == SPSVM_BF16X4 && K->plane < K->rows * K->ld)
     return set_error(SPSVM_ERR_ARG, "%s: hi/lo planes overlap", what);
   if ((reinterpret_cast<uintptr_t>(K->data) & 15) != 0)
     return set_error(SPSVM_ERR_ARG, "%s: data not 16-byte aligned", what);
@@ -200,9 +200,9 @@ extern "C" int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* st
   if (p->n < 0 || p->d < 1 || p->ldx < p->d)
     return set_error(SPSVM_ERR_ARG, "prepare_points: bad shape n=%lld d=%lld ldx=%lld",
                      (long long)p->n, (long long)p->d, (long long)p->ldx);
-  if (precision == SPSVM_BF16X3) {
+  if (precision == SPSVM_BF16X4) {
     if (!p->hi || !p->lo || p->ldh < p->d || (p->ldh % 64) != 0)
-      return set_error(SPSVM_ERR_ARG, "prepare_points: BF16X3 needs hi/lo planes with ldh %% 64 == 0");
+      return set_error(SPSVM_ERR_ARG, "prepare_points: BF16X4 needs hi/lo planes with ldh %% 64 == 0");
   } else if (precision != SPSVM_FP32) {
     return set_error(SPSVM_ERR_ARG, "prepare_points: bad precision %d", precision);
   }
@@ -211,8 +211,8 @@ extern "C" int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* st
   dim3 grid((unsigned)ceil_div(p->n, warps));
   prepare_points_kernel<<<grid, warps * 32, 0, as_stream(stream)>>>(
       p->X, p->n, p->d, p->ldx, p->norms,
-      precision == SPSVM_BF16X3 ? reinterpret_cast<__nv_bfloat16*>(p->hi) : nullptr,
-      precision == SPSVM_BF16X3 ? reinterpret_cast<__nv_bfloat16*>(p->lo) : nullptr, p->ldh);
+      precision == SPSVM_BF16X4 ? reinterpret_cast<__nv_bfloat16*>(p->hi) : nullptr,
+      precision == SPSVM_BF16X4 ? reinterpret_cast<__nv_bfloat16*>(p->lo) : nullptr, p->ldh);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }

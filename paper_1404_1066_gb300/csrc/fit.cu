@@ -129,6 +129,24 @@ __global__ void small_dots(const double* __restrict__ beta, const float* __restr
   }
 }
 
+// out[0] = ||d||^2, out[1] = ||beta||^2
+__global__ void step_norms(const double* __restrict__ d, const double* __restrict__ beta, int32_t m,
+                           double* __restrict__ out) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    a += d[k] * d[k];
+    b += beta[k] * beta[k];
+  }
+  a = block_sum(a, sh);
+  __syncthreads();
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
 // With the bias the heuristic score's lambda o_c term carries b: take it off
 // (h_c does not depend on it).
 __global__ void score_bias_fix(double* __restrict__ g, const double* __restrict__ h,
@@ -222,7 +240,7 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
     return o;
   };
   L.off_norms = take(n * 4);
-  const bool bf = precision == SPSVM_BF16X3;
+  const bool bf = precision == SPSVM_BF16X4;
   L.off_xhi = take(bf ? (size_t)n * L.ldh * 2 : 0);
   L.off_xlo = take(bf ? (size_t)n * L.ldh * 2 : 0);
   L.kbytes = (size_t)L.jcap * L.ldn * 4;   // FP32, or two BF16 planes
@@ -289,7 +307,7 @@ Opts resolve(const spsvm_options* o) {
   r.refine = (o && o->refine > 0) ? o->refine : 0;
   r.record = o ? o->record : 0;
   r.growth_tol = o ? o->growth_tol : 0.0;
-  r.rel_tol = (o && o->rel_tol > 0) ? o->rel_tol : (r.precision == SPSVM_BF16X3 ? 2e-5 : 1e-6);
+  r.rel_tol = (o && o->rel_tol > 0) ? o->rel_tol : 1e-6;
   r.seed = o ? o->seed : 0;
   r.fixed = o && o->fixed_basis;
   r.stream = o ? as_stream(o->stream) : nullptr;
@@ -300,6 +318,14 @@ Opts resolve(const spsvm_options* o) {
 }
 
 constexpr int32_t kJitterMaxLevel = 8;   // largest jitter 1e-2 tr(H)/|J|
+// Newton stop once the gradient is small (||grad|| <= rel_tol ||r||): the
+// next Newton step is below this fraction of ||beta|| (and is not taken)
+constexpr double kStepTol = 1e-5;
+// rounding-level stop only below this gradient level (relative to ||r||)
+constexpr double kFloorGuard = 1e-3;
+// gradient level (relative to ||r||) that ends the iteration of a fit that
+// runs with a diagonal jitter
+constexpr double kJitterRelTol = 5e-6;
 // mixed Newton solve: refinement steps and the FP64-level backward error it
 // must reach (else the FP64 factorisation is used)
 constexpr int32_t kMixedIters = 30;
@@ -326,20 +352,25 @@ struct Fit {
   template <typename T>
   T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
 
+  // K_nJ is stored in FP32 in both forms; the compact copy K_SJ, the Gram
+  // matrix's operand, is FP32 for the FP32 form and the hi / lo BF16 planes
+  // of the tensor-core Gram matrix for BF16X4 (same 4 bytes per element)
   spsvm_kmat kmat() {
     spsvm_kmat K{};
     K.data = ws + L.off_K;
-    K.format = op.precision == SPSVM_BF16X3 ? SPSVM_BF16X3 : SPSVM_FP32;
+    K.format = SPSVM_FP32;
     K.n = n;
     K.rows = m;
     K.ld = L.ldn;
-    K.plane = (int64_t)L.jcap * L.ldn;
+    K.plane = 0;
     return K;
   }
   spsvm_kmat kcmat() {
     spsvm_kmat K = kmat();
     K.data = ws + L.off_Kc;
     K.n = L.ldn;
+    K.format = op.precision == SPSVM_BF16X4 ? SPSVM_BF16X4 : SPSVM_FP32;
+    K.plane = (int64_t)L.jcap * L.ldn;
     return K;
   }
 
@@ -427,6 +458,20 @@ struct Fit {
     // the factor in hand (valid while the active set does not change)
     bool reuse = false, fac_mixed = false;
     double fac_shift = 0.0;
+    // ||d|| <= kStepTol ||beta|| for the direction just solved
+    auto step_small = [&](bool* small) -> int {
+      step_norms<<<1, 256, 0, s>>>(dir, beta, m, dots + 4);
+      SPSVM_LAUNCH_CHECK();
+      double v[2];
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(v, dots + 4, sizeof(v), cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      *small = std::sqrt(v[0]) <= kStepTol * std::sqrt(v[1]);
+      return SPSVM_OK;
+    };
+    // gradient norm before the previous step, and whether that step kept the
+    // active set
+    double gprev = INFINITY;
+    bool kept_prev = false;
     for (int it = 0; it < op.max_newton; ++it) {
       uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
       sub_kernel<<<grid_for(n, tpb), tpb, 0, s>>>(o, y, n, res);
@@ -443,12 +488,34 @@ struct Fit {
       SPSVM_TRY(sync());
       const double gnorm = std::sqrt(dh[1]), rnorm = std::sqrt(dh[2]);
       model->objective = 0.5 * lambda * dh[0] + st[0];
-      if (gnorm <= std::max(tol, op.rel_tol * rnorm)) {
+      // Newton stop (the paper gives none):
+      //  * ||grad|| <= tol;
+      //  * rounding level: a near-full step that kept the active set did not
+      //    halve ||grad|| (on a fixed active set the Newton step is exact up
+      //    to the rounding of H), with ||grad|| <= kFloorGuard ||r||, where
+      //    r = K_SJ^T y_S;
+      //  * with a diagonal jitter in use, ||grad|| <= max(rel_tol,
+      //    kJitterRelTol) ||r||: H is at rounding level in its smallest
+      //    directions, where beta is not determined;
+      //  * otherwise, once ||grad|| <= rel_tol ||r||: the next Newton step
+      //    is below kStepTol ||beta|| (checked below, once the step is
+      //    solved; it is then not taken), or a step finds no descent.
+      const bool gsmall = gnorm <= op.rel_tol * rnorm;
+      // with a jitter the damped steps converge slowly in the directions
+      // where H is at rounding level, which the objective hardly sees
+      const bool gsmall_jit = gnorm <= std::max(op.rel_tol, kJitterRelTol) * rnorm;
+      auto converged = [&]() {
         spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
         model->history.push_back(rec);
         status = SPSVM_OK;
+      };
+      if (gnorm <= tol || (gsmall_jit && jitter >= 0) || (gsmall && kept_prev && gnorm > 0.5 * gprev) ||
+          (kept_prev && gnorm > 0.5 * gprev && gnorm <= kFloorGuard * rnorm)) {
+        converged();
         break;
       }
+      gprev = gnorm;
+      bool done = false;
       // Newton system on the active set.  Factorise H + 10^(l-10) tr(H)/|J| I
       // for l = jitter, jitter + 1, ... (l = -1: H itself): a computed H of a
       // smooth kernel can be indefinite at rounding level.  The direction is
@@ -463,9 +530,18 @@ struct Fit {
         // so H has not either: only the right-hand side is new
         const int rc = solve_with(fac_mixed, fac_shift, rhs, dir, kMixedTol);
         if (rc == SPSVM_OK) {
+          if (gsmall) SPSVM_TRY(step_small(&done));
+          if (done) {
+            converged();
+            break;
+          }
           SPSVM_TRY(finish_direction(act, fac_mixed, fac_shift));
           SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
           stepped = t > 0.0;
+          if (!stepped && gsmall) {   // no descent at rounding level
+            converged();
+            break;
+          }
         } else if (rc != SPSVM_ERR_NO_CONVERGE) {
           return rc;
         }
@@ -525,19 +601,28 @@ struct Fit {
             break;
           }
         }
-        // d = -(H + shift I)^{-1} g (computed above), u = K_nJ d
-        SPSVM_TRY(finish_direction(act, mixed, shift));
         fac_mixed = mixed;
         fac_shift = shift;
+        if (gsmall) SPSVM_TRY(step_small(&done));
+        if (done) break;
+        // d = -(H + shift I)^{-1} g (computed above), u = K_nJ d
+        SPSVM_TRY(finish_direction(act, mixed, shift));
         t = 0.0;
         SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
-        if (t > 0.0 || jitter >= kJitterMaxLevel) break;
+        // with a small gradient, no descent means rounding level: no jitter
+        if (t > 0.0 || gsmall || jitter >= kJitterMaxLevel) break;
         ++jitter;
       }
+      if (done) {
+        converged();
+        break;
+      }
       if (!(t > 0.0)) {
-        // no descent even at the largest jitter: rounding level reached
+        // no descent even at the largest jitter (or with a small gradient):
+        // rounding level reached
         spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
         model->history.push_back(rec);
+        if (gsmall) status = SPSVM_OK;
         break;
       }
       axpy_d<<<mb, tpb, 0, s>>>(beta, dir, t, m);
@@ -567,6 +652,7 @@ struct Fit {
         break;
       }
       reuse = nd == 0;
+      kept_prev = nd == 0 && t >= 0.5;
     }
     model->status = status;
     return SPSVM_OK;
@@ -586,7 +672,7 @@ struct Fit {
     pts.ldx = ldx;
     pts.norms = at<float>(L.off_norms);
     pts.ldh = L.ldh;
-    if (op.precision == SPSVM_BF16X3) {
+    if (op.precision == SPSVM_BF16X4) {
       pts.hi = at<uint16_t>(L.off_xhi);
       pts.lo = at<uint16_t>(L.off_xlo);
     }
@@ -746,7 +832,7 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     return set_error(SPSVM_ERR_ARG, "fit: need gamma > 0, lambda > 0, 1 <= budget <= n, tol >= 0");
   if (n > (int64_t)INT32_MAX) return set_error(SPSVM_ERR_ARG, "fit: n too large");
   Opts op = resolve(opt);
-  if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16X3)
+  if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16X4)
     return set_error(SPSVM_ERR_ARG, "fit: bad precision %d", op.precision);
   if (op.bias && op.refine > 0)
     return set_error(SPSVM_ERR_ARG, "fit: refinement sweeps are not available with the bias");

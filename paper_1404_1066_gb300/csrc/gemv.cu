@@ -10,37 +10,37 @@ namespace spsvm {
 
 namespace {
 
-constexpr int GV_T = 128;          // threads per block (with 8 rows in flight: 0.99 of HBM)
-constexpr int GV_P = 8;            // consecutive points per thread
+constexpr int GV_T = 256;          // threads per block
+constexpr int GV_P = 2;            // consecutive points per thread
 constexpr int GV_PTS = GV_T * GV_P;
-constexpr int GV_CHUNK = 32;       // terms summed in FP32 before promotion
+constexpr int GV_CHUNK = 32;       // terms summed in FP32 before promotion (all in flight)
 constexpr int GV_BETA = 2048;      // beta entries staged in shared memory per pass
 
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// Loads 8 consecutive kernel values of row j from point i (i % 8 == 0,
-// i + 7 < n) as FP32: two 16-byte loads either way (FP32, or the hi and lo
-// BF16 planes).
+// Loads the thread's 2 consecutive kernel values of row j from point i
+// (i even, i + 1 < n) as FP32: one 8-byte load (FP32), or one 4-byte load
+// per BF16 plane.  A warp's load instruction covers 256 contiguous bytes of
+// a row; with a whole chunk of 32 rows in flight per thread this layout
+// streams at the HBM read rate (fewer, wider loads per thread kept fewer
+// bytes in flight).
 template <int FMT>
-__device__ __forceinline__ void load8(const KView& K, int64_t j, int64_t i, float k[8]) {
+__device__ __forceinline__ void load2(const KView& K, int64_t j, int64_t i, float k[2]) {
   if (FMT == SPSVM_FP32) {
-    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(K.data) + j * K.ld + i);
-    const float4 a = p[0], b = p[1];
-    k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
-    k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+    const float2 a = *reinterpret_cast<const float2*>(static_cast<const float*>(K.data) + j * K.ld + i);
+    k[0] = a.x;
+    k[1] = a.y;
   } else {
     const uint16_t* base = static_cast<const uint16_t*>(K.data);
-    const uint4 h = *reinterpret_cast<const uint4*>(base + j * K.ld + i);
-    const uint4 l = *reinterpret_cast<const uint4*>(base + K.plane + j * K.ld + i);
-    k[0] = bf_lo(h.x) + bf_lo(l.x); k[1] = bf_hi(h.x) + bf_hi(l.x);
-    k[2] = bf_lo(h.y) + bf_lo(l.y); k[3] = bf_hi(h.y) + bf_hi(l.y);
-    k[4] = bf_lo(h.z) + bf_lo(l.z); k[5] = bf_hi(h.z) + bf_hi(l.z);
-    k[6] = bf_lo(h.w) + bf_lo(l.w); k[7] = bf_hi(h.w) + bf_hi(l.w);
+    const uint32_t h = *reinterpret_cast<const uint32_t*>(base + j * K.ld + i);
+    const uint32_t l = *reinterpret_cast<const uint32_t*>(base + K.plane + j * K.ld + i);
+    k[0] = bf_lo(h) + bf_lo(l);
+    k[1] = bf_hi(h) + bf_hi(l);
   }
 }
 
-// acc[p] = sum_j K[j][i+p] v_j for the thread's 8 points.
+// acc[p] = sum_j K[j][i + p] v_j for the thread's points.
 template <int FMT>
 __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64_t n,
                                              const double* __restrict__ v, int64_t i,
@@ -55,20 +55,20 @@ __device__ __forceinline__ void row_products(const KView& K, int64_t rows, int64
     __syncthreads();
     if (i >= n) continue;
     for (int c0 = 0; c0 < cnt; c0 += GV_CHUNK) {
-      const int ce = min(cnt, c0 + GV_CHUNK);
       float f[GV_P];
 #pragma unroll
       for (int p = 0; p < GV_P; ++p) f[p] = 0.f;
-      if (full) {
-#pragma unroll 8
-        for (int c = c0; c < ce; ++c) {
-          float k[8];
-          load8<FMT>(K, j0 + c, i, k);
+      if (full && c0 + GV_CHUNK <= cnt) {
+#pragma unroll
+        for (int c = c0; c < c0 + GV_CHUNK; ++c) {
+          float k[GV_P];
+          load2<FMT>(K, j0 + c, i, k);
           const float b = vs[c];
 #pragma unroll
           for (int p = 0; p < GV_P; ++p) f[p] = fmaf(k[p], b, f[p]);
         }
       } else {
+        const int ce = min(cnt, c0 + GV_CHUNK);
         for (int c = c0; c < ce; ++c) {
           const float b = vs[c];
           for (int p = 0; p < GV_P; ++p)
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(GV_T) outputs_kernel(
   double acc[GV_P];
   if (beta) row_products<FMT>(K, rows, n, beta, i, vs, acc);
   double loss = 0.0, err = 0.0, act = 0.0;
-  if (i < n) {
+  {
 #pragma unroll
     for (int p = 0; p < GV_P; ++p) {
       const int64_t ii = i + p;
@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(GV_T) gemv_kernel(KView K, int64_t rows, int64
   const int64_t i = ((int64_t)blockIdx.x * GV_T + threadIdx.x) * GV_P;
   double acc[GV_P];
   row_products<FMT>(K, rows, n, v, i, vs, acc);
-  if (i >= n) return;
 #pragma unroll
   for (int p = 0; p < GV_P; ++p) {
     const int64_t ii = i + p;
@@ -237,10 +236,26 @@ __global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
 constexpr int CP_T = 256;
 constexpr int CP_ROWS = 8;      // basis rows per block
 
+// Writes kernel value v (read from K as `h` + `l` in the planes format) to
+// column q of row j of the compact matrix: FP32, or hi / lo planes (copied
+// from K's planes, or split from an FP32 value).
+__device__ __forceinline__ void kc_put(void* kc_data, int32_t kc_format, int64_t kc_ld,
+                                       int64_t kc_plane, int32_t k_format, int64_t j, int64_t q,
+                                       float v, __nv_bfloat16 h, __nv_bfloat16 l) {
+  if (kc_format == SPSVM_FP32) {
+    static_cast<float*>(kc_data)[j * kc_ld + q] = v;
+    return;
+  }
+  if (k_format == SPSVM_FP32) split_bf16(v, h, l);
+  __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(kc_data);
+  dst[j * kc_ld + q] = h;
+  dst[kc_plane + j * kc_ld + q] = l;
+}
+
 __global__ void __launch_bounds__(CP_T) compact_kernel(
     KView K, int64_t rows, int64_t n, const uint8_t* __restrict__ active,
     const int32_t* __restrict__ pos, const float* __restrict__ w1, const float* __restrict__ w2,
-    void* kc_data, int64_t kc_ld, int64_t kc_plane, int64_t chunks_per_block,
+    void* kc_data, int32_t kc_format, int64_t kc_ld, int64_t kc_plane, int64_t chunks_per_block,
     double2* __restrict__ part, const int64_t* __restrict__ ns_dev, int64_t gather_max) {
   __shared__ double sh[32];
   if (*ns_dev <= gather_max) return;   // few active points: compact_gather does this
@@ -264,19 +279,16 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
       const int64_t j = j0 + r;
       if (j >= rows) break;
       float v;
+      __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
       if (K.format == SPSVM_FP32) {
         v = static_cast<const float*>(K.data)[j * K.ld + i];
-        if (kc_data) static_cast<float*>(kc_data)[j * kc_ld + q] = v;
       } else {
         const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(K.data);
-        const __nv_bfloat16 h = src[j * K.ld + i], l = src[K.plane + j * K.ld + i];
-        if (kc_data) {
-          __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(kc_data);
-          dst[j * kc_ld + q] = h;
-          dst[kc_plane + j * kc_ld + q] = l;
-        }
+        h = src[j * K.ld + i];
+        l = src[K.plane + j * K.ld + i];
         v = __bfloat162float(h) + __bfloat162float(l);
       }
+      if (kc_data) kc_put(kc_data, kc_format, kc_ld, kc_plane, K.format, j, q, v, h, l);
       f1[r] = fmaf(a, v, f1[r]);
       f2[r] = fmaf(b, v, f2[r]);
     }
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
 __global__ void __launch_bounds__(CP_T) compact_gather(
     KView K, int64_t rows, const int32_t* __restrict__ list, const int64_t* __restrict__ ns_dev,
     int64_t gather_max, const float* __restrict__ w1, const float* __restrict__ w2, void* kc_data,
-    int64_t kc_ld, int64_t kc_plane, double2* __restrict__ part) {
+    int32_t kc_format, int64_t kc_ld, int64_t kc_plane, double2* __restrict__ part) {
   __shared__ double sh[32];
   const int64_t ns = *ns_dev;
   if (ns > gather_max) return;
@@ -325,19 +337,16 @@ __global__ void __launch_bounds__(CP_T) compact_gather(
       const int64_t j = j0 + r;
       if (j >= rows) break;
       float v;
+      __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
       if (K.format == SPSVM_FP32) {
         v = static_cast<const float*>(K.data)[j * K.ld + i];
-        if (kc_data) static_cast<float*>(kc_data)[j * kc_ld + q] = v;
       } else {
         const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(K.data);
-        const __nv_bfloat16 h = src[j * K.ld + i], l = src[K.plane + j * K.ld + i];
-        if (kc_data) {
-          __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(kc_data);
-          dst[j * kc_ld + q] = h;
-          dst[kc_plane + j * kc_ld + q] = l;
-        }
+        h = src[j * K.ld + i];
+        l = src[K.plane + j * K.ld + i];
         v = __bfloat162float(h) + __bfloat162float(l);
       }
+      if (kc_data) kc_put(kc_data, kc_format, kc_ld, kc_plane, K.format, j, q, v, h, l);
       f1[r] = fmaf(a, v, f1[r]);
       f2[r] = fmaf(b, v, f2[r]);
     }
@@ -425,7 +434,7 @@ extern "C" int spsvm_outputs(const spsvm_kmat* K, const double* beta, const floa
     outputs_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y,
                                                                   o, active, part, 0);
   else
-    outputs_kernel<SPSVM_BF16X3><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta,
+    outputs_kernel<SPSVM_BF16X4><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta,
                                                                     y, o, active, part, 0);
   SPSVM_LAUNCH_CHECK();
   if (stats) {
@@ -446,7 +455,7 @@ extern "C" int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_
     gemv_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
         view(K), K->rows, K->n, v, u, accumulate);
   else
-    gemv_kernel<SPSVM_BF16X3><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
+    gemv_kernel<SPSVM_BF16X4><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
         view(K), K->rows, K->n, v, u, accumulate);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
@@ -481,7 +490,9 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
   if (!active || !n_active || !pos) return set_error(SPSVM_ERR_ARG, "compact: NULL pointer");
   if (Kc) {
     SPSVM_TRY(check_kmat(Kc, "compact(out)"));
-    if (Kc->format != K->format || Kc->rows < K->rows || Kc->n < round_up(K->n, 128))
+    // the compact copy keeps K's format, or splits FP32 values into hi / lo planes
+    const bool fmt_ok = Kc->format == K->format || (K->format == SPSVM_FP32 && Kc->format == SPSVM_BF16X4);
+    if (!fmt_ok || Kc->rows < K->rows || Kc->n < round_up(K->n, 128))
       return set_error(SPSVM_ERR_ARG, "compact: output matrix too small or wrong format");
   }
   if ((w1out && !w1) || (w2out && !w2)) return set_error(SPSVM_ERR_ARG, "compact: missing weights");
@@ -517,12 +528,13 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
     ysplit = ceil_div(nchunks, per);
     dim3 grid((unsigned)ceil_div(K->rows, CP_ROWS), (unsigned)ysplit);
     compact_kernel<<<grid, CP_T, 0, s>>>(view(K), K->rows, n, active, pos, w1, w2,
-                                         Kc ? Kc->data : nullptr, Kc ? Kc->ld : 0,
-                                         Kc ? Kc->plane : 0, per, part, n_active, gather_max);
+                                         Kc ? Kc->data : nullptr, Kc ? Kc->format : 0,
+                                         Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, per, part, n_active,
+                                         gather_max);
     SPSVM_LAUNCH_CHECK();
     compact_gather<<<(unsigned)ceil_div(K->rows, CP_ROWS), CP_T, 0, s>>>(
         view(K), K->rows, list, n_active, gather_max, w1, w2, Kc ? Kc->data : nullptr,
-        Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, part);
+        Kc ? Kc->format : 0, Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, part);
     SPSVM_LAUNCH_CHECK();
     if (w1out || w2out) {
       compact_finish<<<(unsigned)ceil_div(K->rows, 256), 256, 0, s>>>(part, ysplit, K->rows,

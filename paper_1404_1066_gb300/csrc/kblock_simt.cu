@@ -194,7 +194,7 @@ int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t 
 using namespace spsvm;
 
 extern "C" size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision) {
-  if (m < 0 || d < 1 || precision != SPSVM_BF16X3) return 0;
+  if (m < 0 || d < 1 || precision != SPSVM_BF16X4) return 0;
   return kernel_block_tc_scratch(m, round_up(d, 64));
 }
 
@@ -208,10 +208,12 @@ extern "C" int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int
     return set_error(SPSVM_ERR_ARG, "kernel_block: m=%d row0=%lld rows=%lld n=%lld/%lld gamma=%g",
                      m, (long long)row0, (long long)out->rows, (long long)out->n,
                      (long long)p->n, (double)gamma);
-  ProfScope prof(PROF_KERNEL_BLOCK, as_stream(stream), 2.0 * (double)p->n * m * (double)p->d);
-  if (precision == SPSVM_BF16X3) {
-    if (out->format != SPSVM_BF16X3 || !p->hi || !p->lo)
-      return set_error(SPSVM_ERR_ARG, "kernel_block: BF16X3 needs split planes and BF16X3 output");
+  // algorithmic work: 2 n m d multiply-adds, times the four products of the split form
+  ProfScope prof(PROF_KERNEL_BLOCK, as_stream(stream),
+                 (precision == SPSVM_BF16X4 ? 8.0 : 2.0) * (double)p->n * m * (double)p->d);
+  if (precision == SPSVM_BF16X4) {
+    if (!p->hi || !p->lo)
+      return set_error(SPSVM_ERR_ARG, "kernel_block: BF16X4 needs the split planes of the points");
     return launch_kernel_block_tc(p, idx, m, gamma, out, row0, scratch, scratch_bytes,
                                   as_stream(stream));
   }
@@ -252,11 +254,11 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
   if (scratch_bytes < need || !scratch)
     return set_error(SPSVM_ERR_OOM, "score_candidates: scratch %zu < %zu", scratch_bytes, need);
   cudaStream_t s = as_stream(stream);
-  ProfScope prof(PROF_SCORE, s, 2.0 * (double)p->n * kappa * (double)p->d);
+  ProfScope prof(PROF_SCORE, s, (precision == SPSVM_BF16X4 ? 8.0 : 2.0) * (double)p->n * kappa * (double)p->d);
   double2* part = static_cast<double2*>(scratch);
   int64_t tiles = ceil_div(p->n, TM);
-  if (precision == SPSVM_BF16X3) {
-    if (!p->hi || !p->lo) return set_error(SPSVM_ERR_ARG, "score_candidates: BF16X3 needs split planes");
+  if (precision == SPSVM_BF16X4) {
+    if (!p->hi || !p->lo) return set_error(SPSVM_ERR_ARG, "score_candidates: BF16X4 needs split planes");
     tiles = score_tc_tiles(p->n);
     const size_t pb = score_part_bytes(p->n, kappa);
     SPSVM_TRY(launch_score_tc(p, y, o, idx, kappa, gamma, part, tiles,

@@ -321,7 +321,7 @@ ExLayout ex_layout(int64_t n, int64_t d, int32_t kappa, int32_t precision) {
   L.ctl = off;    off += al(16);
   L.part = off;   off += al((size_t)4 * 2048 * sizeof(ExPart));   // up to 4 CTAs per SM x 512 SMs
   L.kb = off;     off += al(spsvm_kernel_block_scratch_bytes(kappa, d, precision));
-  L.kc = off;     off += al((size_t)kappa * L.ld * 4);               // FP32, or two BF16 planes
+  L.kc = off;     off += al((size_t)kappa * L.ld * 4);               // FP32
   L.total = off;
   return L;
 }
@@ -350,14 +350,15 @@ extern "C" int spsvm_score_candidates_exact(const spsvm_points* p, const float* 
     return set_error(SPSVM_ERR_OOM, "score_exact: scratch too small or misaligned");
   cudaStream_t s = as_stream(stream);
   char* w = static_cast<char*>(scratch);
-  // the candidates' kernel rows, computed once in the given precision
+  // the candidates' kernel rows, computed once in the given precision and
+  // stored in FP32
   spsvm_kmat kc{};
   kc.data = w + ly.kc;
-  kc.format = precision;
+  kc.format = SPSVM_FP32;
   kc.n = p->n;
   kc.rows = kappa;
   kc.ld = ly.ld;
-  kc.plane = (int64_t)kappa * ly.ld;
+  kc.plane = 0;
   SPSVM_TRY(spsvm_kernel_block(p, idx, kappa, gamma, precision, &kc, 0, w + ly.kb,
                                spsvm_kernel_block_scratch_bytes(kappa, p->d, precision), stream));
   const int slots = max_coresident();
@@ -368,7 +369,7 @@ extern "C" int spsvm_score_candidates_exact(const spsvm_points* p, const float* 
     const int32_t cpc = (int32_t)min64(8, slots / kk);
     SPSVM_CUDA_TRY(cudaMemsetAsync(w + ly.ctl, 0, 16, s));
     KView kv = view(&kc);
-    kv.data = static_cast<const char*>(kc.data) + (size_t)k0 * ly.ld * (precision == SPSVM_FP32 ? 4 : 2);
+    kv.data = static_cast<const char*>(kc.data) + (size_t)k0 * ly.ld * 4;
     const int64_t* ix = idx + k0;
     double* dl = delta + k0;
     double* tt = t ? t + k0 : nullptr;

@@ -1,13 +1,15 @@
-// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16X3 form.  Every
-// FP32 operand x is split as hi + lo (both BF16) and a product x*z is formed
-// as hi*hi + hi*lo + lo*hi (three BF16 MMAs accumulating in FP32 in TMEM);
-// the dropped lo*lo term is below 2^-16 of |x z|.
+// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16X4 form.  Every
+// FP32 operand x is split as hi + lo (both BF16, lo = bf16(x - hi)) and a
+// product x*z is formed as hi*hi + hi*lo + lo*hi + lo*lo (four BF16 MMAs
+// accumulating in FP32 in TMEM): the exact product of the two-term
+// representations, whose own error is below 2^-17 of |x z|.
 //
 //   * kernel block / candidate scores (RBF kernel of Section 2 through the
 //     distance expansion; the basis-vector score of Section 4): points X
 //     (TMA, 128 rows per tile) times gathered basis / candidate rows, fused
 //     epilogue exp(-gamma max(0, |x|^2 + |z|^2 - 2 x.z)) that either stores
-//     the kernel values or reduces the score sums without storing them;
+//     the kernel values (FP32, or hi / lo planes) or reduces the score sums
+//     without storing them;
 //   * masked Gram matrix K_SJ^T K_SJ (the Hessian term of Eq. 4 on the
 //     active set): warp-specialised TMA producer / MMA issuer / epilogue over
 //     128 x 128 upper-triangular tiles with two TMEM accumulators, FP32
@@ -37,7 +39,7 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // Kernel block / scores, persistent and warp-specialised.  D[c][i] = z_c . x_i
 // over tiles of 128 basis (or candidate) rows c (MMA M; the rows gathered
 // beforehand into contiguous BF16 planes Z) by 128 points i (MMA N), both
-// operands streamed by TMA through a 3-stage shared-memory ring.  Warp 0
+// operands streamed by TMA through a 2-stage shared-memory ring.  Warp 0
 // issues the TMA loads, warp 1 the MMAs into one of two TMEM accumulators,
 // warps 2-9 drain the other accumulator (TMEM lane c = row c; warps w and
 // w + 4 share a lane quarter and split the 128 columns), so the epilogue of
@@ -52,8 +54,8 @@ constexpr int PK_PLANE_B = PK_N * 128;
 constexpr int PK_STAGE = 2 * PK_PLANE_A + 2 * PK_PLANE_B;  // 64 KB
 constexpr int PK_EPI_WARPS = 8;
 constexpr int PK_THREADS = 32 * (2 + PK_EPI_WARPS);
-constexpr int PK_OUT_BOX = 32 * 128;                       // one plane: 32 rows x 64 BF16
-constexpr int PK_OUT_OFF = PK_STAGES * PK_STAGE;           // per epilogue warp: hi and lo boxes
+constexpr int PK_OUT_BOX = 32 * 128;                       // 32 rows x 128 bytes
+constexpr int PK_OUT_OFF = PK_STAGES * PK_STAGE;           // per epilogue warp: two boxes
 constexpr int PK_BAR_OFF = PK_OUT_OFF + PK_EPI_WARPS * 2 * PK_OUT_BOX;
 constexpr int PK_RED_OFF = PK_BAR_OFF + 256;
 constexpr int PK_STAGE_OFF = PK_RED_OFF + 4 * 32 * 8;      // per epilogue warp: 3 x 64 floats
@@ -93,7 +95,11 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT,
   pt = g0 + r % gw;
 }
 
-template <bool SCORE>
+// Epilogue modes: store FP32 kernel values, store them as hi / lo BF16
+// planes, or reduce the candidate-score sums.
+enum KbMode { KB_STORE_F32 = 0, KB_STORE_PLANES = 1, KB_SCORE = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     const __grid_constant__ CUtensorMap map_zhi, const __grid_constant__ CUtensorMap map_zlo,
     const __grid_constant__ CUtensorMap map_xhi, const __grid_constant__ CUtensorMap map_xlo,
@@ -101,6 +107,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     int64_t ldh, int64_t n, int32_t m, const float* __restrict__ norms,
     const int64_t* __restrict__ idx, float gamma, int64_t row0, const float* __restrict__ y,
     const float* __restrict__ o, double2* __restrict__ part, int32_t kappa) {
+  constexpr bool SCORE = MODE == KB_SCORE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + PK_BAR_OFF);
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
                      (kc | k) != 0 ? 1u : 0u);
             mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_lo + koff), IDESC, 1u);
             mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_hi + koff), IDESC, 1u);
+            mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_lo + koff), IDESC, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -274,7 +282,17 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
           v[jj + 2] = ex2_approx(fminf(fmaf(-g2, x4.z, fmaf(2.0f * g2, v[jj + 2], zz)), 0.0f));
           v[jj + 3] = ex2_approx(fminf(fmaf(-g2, x4.w, fmaf(2.0f * g2, v[jj + 3], zz)), 0.0f));
         }
-        if (!SCORE) {
+        if (MODE == KB_STORE_F32) {
+          // 32 FP32 values into box cc of this warp (row = lane, 128-byte
+          // swizzle: 16-byte chunk ch of row r at chunk ch ^ (r & 7))
+          uint8_t* bx = obox + cc * PK_OUT_BOX;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            const int so = lane * 128 + ((ch ^ (lane & 7)) << 4);
+            *reinterpret_cast<float4*>(bx + so) =
+                make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
+          }
+        } else if (MODE == KB_STORE_PLANES) {
           // hi / lo into this warp's swizzled output boxes (row = lane)
           uint8_t* bh = obox;
           uint8_t* bl = obox + PK_OUT_BOX;
@@ -311,8 +329,14 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
         __syncwarp();
         if (lane == 0) {
           const int x = (int)ib, yrow = (int)(row0 + (int64_t)cb * PK_M + 32 * quarter);
-          tma_store_2d(&map_ohi, x, yrow, obox);
-          tma_store_2d(&map_olo, x, yrow, obox + PK_OUT_BOX);
+          if (MODE == KB_STORE_F32) {
+            // boxes of 32 points; the second starts past n only when npts <= 32
+            tma_store_2d(&map_ohi, x, yrow, obox);
+            if (npts > 32) tma_store_2d(&map_ohi, x + 32, yrow, obox + PK_OUT_BOX);
+          } else {
+            tma_store_2d(&map_ohi, x, yrow, obox);
+            tma_store_2d(&map_olo, x, yrow, obox + PK_OUT_BOX);
+          }
           bulk_commit();
         }
       }
@@ -542,32 +566,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D BF16 map over rows x inner (row pitch `pitch_elems`), 64 x box_rows boxes,
-// 128-byte swizzle, zero fill outside the tensor.
+// 2-D map over rows x inner (row pitch `pitch_elems`) of BF16 (or FP32 with
+// f32), box_inner x box_rows boxes of 128 bytes per row, 128-byte swizzle,
+// zero fill outside the tensor.
 int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int64_t pitch_elems,
-             uint32_t box_rows, uint32_t box_inner) {
+             uint32_t box_rows, uint32_t box_inner, bool f32 = false) {
   auto fn = encode_fn();
   if (!fn) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * 2) % 16)
-    return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned");
+  const int64_t esz = f32 ? 4 : 2;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * esz) % 16 || box_inner * esz != 128)
+    return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned, or box row not 128 bytes");
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)(rows > 0 ? rows : 1)};
-  cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * 2)};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * esz)};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SPSVM_OK;
 }
 
-template <bool SCORE>
-int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, uint16_t* out,
+template <int MODE>
+int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, void* out,
               int64_t ld, int64_t plane, int64_t row0, const float* y, const float* o,
               double2* part, int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s) {
   const int64_t m_pad = round_up(m, (int64_t)PK_M);
   if (!zbuf || zbytes < (size_t)(m_pad * p->ldh * 4))
-    return set_error(SPSVM_ERR_OOM, "BF16X3 kernel block: scratch too small for the gathered rows");
+    return set_error(SPSVM_ERR_OOM, "BF16X4 kernel block: scratch too small for the gathered rows");
   uint16_t* zhi = static_cast<uint16_t*>(zbuf);
   uint16_t* zlo = zhi + m_pad * p->ldh;
   const int64_t work = m_pad * (p->ldh / 8);
@@ -579,15 +606,19 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
   SPSVM_TRY(make_map(&mzl, zlo, p->ldh, m_pad, p->ldh, PK_M, 64));
   SPSVM_TRY(make_map(&mxh, p->hi, p->ldh, p->n, p->ldh, PK_N, 64));
   SPSVM_TRY(make_map(&mxl, p->lo, p->ldh, p->n, p->ldh, PK_N, 64));
-  if (!SCORE) {
-    // output rows [0, row0 + m): rows past the basis block are clipped, never written
-    SPSVM_TRY(make_map(&moh, out, p->n, row0 + m, ld, 32, 64));
-    SPSVM_TRY(make_map(&mol, out + plane, p->n, row0 + m, ld, 32, 64));
+  // output rows [0, row0 + m): rows past the basis block are clipped, never written
+  if (MODE == KB_STORE_F32) {
+    SPSVM_TRY(make_map(&moh, out, p->n, row0 + m, ld, 32, 32, true));
+    mol = moh;
+  } else if (MODE == KB_STORE_PLANES) {
+    uint16_t* o16 = static_cast<uint16_t*>(out);
+    SPSVM_TRY(make_map(&moh, o16, p->n, row0 + m, ld, 32, 64));
+    SPSVM_TRY(make_map(&mol, o16 + plane, p->n, row0 + m, ld, 32, 64));
   } else {
     moh = mxh;
     mol = mxl;
   }
-  auto kern = kblock_tc_kernel<SCORE>;
+  auto kern = kblock_tc_kernel<MODE>;
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
   const int64_t tiles = ceil_div((int64_t)m, (int64_t)PK_M) * ceil_div(p->n, (int64_t)PK_N);
   const int grid = (int)min64(tiles, (int64_t)sm_count());
@@ -609,11 +640,13 @@ int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m,
                            spsvm_kmat* out, int64_t row0, void* scratch, size_t scratch_bytes,
                            cudaStream_t s) {
   if (m == 0 || p->n == 0) return SPSVM_OK;
-  if (out->format != SPSVM_BF16X3 || (out->ld % 8) != 0 || (out->plane % 8) != 0)
-    return set_error(SPSVM_ERR_ARG,
-                     "BF16X3 kernel block: needs BF16X3 storage with ld %% 8 == 0, plane %% 8 == 0");
-  return launch_kb<false>(p, idx, m, gamma, static_cast<uint16_t*>(out->data), out->ld, out->plane,
-                          row0, nullptr, nullptr, nullptr, 0, scratch, scratch_bytes, s);
+  if ((out->ld % 8) != 0 || (out->format == SPSVM_BF16X4 && (out->plane % 8) != 0))
+    return set_error(SPSVM_ERR_ARG, "BF16X4 kernel block: needs ld %% 8 == 0 (and plane %% 8 == 0)");
+  if (out->format == SPSVM_FP32)
+    return launch_kb<KB_STORE_F32>(p, idx, m, gamma, out->data, out->ld, 0, row0, nullptr, nullptr,
+                                   nullptr, 0, scratch, scratch_bytes, s);
+  return launch_kb<KB_STORE_PLANES>(p, idx, m, gamma, out->data, out->ld, out->plane, row0, nullptr,
+                                    nullptr, nullptr, 0, scratch, scratch_bytes, s);
 }
 
 int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)PK_N); }
@@ -622,7 +655,7 @@ int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const
                     int32_t kappa, float gamma, double2* part, int64_t tiles, void* zbuf,
                     size_t zbytes, cudaStream_t s) {
   (void)tiles;
-  return launch_kb<true>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
+  return launch_kb<KB_SCORE>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
 }
 
 int64_t gram_tc_splits(int64_t m, int64_t ns_max) {

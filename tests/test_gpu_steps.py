@@ -6,8 +6,10 @@ step under test differs.
 
 Tolerances (derived from the arithmetic, stated per test):
   * kernel values: FP32 form, |dK| <= 2e-6 + 4 eps32 gamma (|x|^2+|z|^2);
-    BF16X3 form, split products carry 2^-16 relative error per operand, so
-    |dK| <= 6e-5 * gamma * (|x|^2 + |z|^2) + 2e-6.
+    BF16X4 form, the hi + lo split of each operand is exact to 2^-18
+    relative and all four products are formed, so the dot product is off by
+    at most 2^-17 |x||z| <= 2^-18 (|x|^2 + |z|^2) plus FP32 accumulation:
+    |dK| <= 2e-5 * gamma * (|x|^2 + |z|^2) + 2e-6.
   * sums of n products in FP32 with FP64 promotion every 32 terms:
     |err| <= 1e-5 * sum |terms|.
   * FP64 Cholesky / solves: backward-stable, 1e-10 relative.
@@ -63,9 +65,13 @@ def sp():
     return sp
 
 
-@pytest.mark.parametrize("n,d,m", [(1000, 20, 70), (257, 37, 64), (130, 5, 1), (3000, 130, 129)])
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_kernel_block(sp, n, d, m, prec):
+@pytest.mark.parametrize("n,d,m", [(1000, 20, 70), (257, 37, 64), (130, 5, 1), (3000, 130, 129),
+                                   (290, 64, 200)])
+@pytest.mark.parametrize("prec,store", [("fp32", "fp32"), ("fp32", "bf16x4"), ("bf16x4", "fp32"),
+                                        ("bf16x4", "bf16x4")])
+def test_kernel_block(sp, n, d, m, prec, store):
+    """Arithmetic form x storage format; the stored hi + lo planes add 2^-17
+    relative rounding of each value."""
     X, _ = _data(n, d, 1)
     gamma = 1.0 / d
     g = np.random.default_rng(2)
@@ -73,20 +79,22 @@ def test_kernel_block(sp, n, d, m, prec):
     P = sp.spsvm_prepare_points(_t(X), prec)
     nrm = P.norms.cpu().numpy()
     np.testing.assert_allclose(nrm, (X.astype(np.float64) ** 2).sum(1), rtol=1e-6)
-    km = sp.kmat_empty(n, m + 3, prec)
+    km = sp.kmat_empty(n, m + 3, store)
     sp.spsvm_kernel_block(P, _t(idx), gamma, prec, km, row0=3)
     torch.cuda.synchronize()
     got = km.to_float().cpu().numpy().astype(np.float64)[3:]
     ref = O.rbf_kernel(X, X[idx], gamma).T
     sq = (X.astype(np.float64) ** 2).sum(1)
     scale = gamma * (sq[None, :] + sq[idx][:, None])
-    tol = (4 * 2 ** -24 * scale + 2e-6) if prec == "fp32" else (6e-5 * scale + 2e-6)
+    tol = (4 * 2 ** -24 * scale + 2e-6) if prec == "fp32" else (2e-5 * scale + 2e-6)
+    if store == "bf16x4":
+        tol = tol + 2.0 ** -17 * np.abs(ref)
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
     # rows before row0 untouched
     assert float(km.to_float()[:3].abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
 def test_score_candidates(sp, prec):
     n, d = 2100, 24
     X, y = _data(n, d, 3)
@@ -108,7 +116,7 @@ def test_score_candidates(sp, prec):
     res = np.where(S, o - y, 0)
     Kc = O.rbf_kernel(X, X[cand], gamma)
     gabs = np.abs(res) @ Kc + lam * np.abs(o[cand])
-    ktol = 4 * 2 ** -24 if prec == "fp32" else 6e-5
+    ktol = 4 * 2 ** -24 if prec == "fp32" else 2e-5
     sq = (X.astype(np.float64) ** 2).sum(1)
     kerr = ktol * gamma * (sq.max() + sq.max()) + 2e-6
     gtol = 1e-5 * gabs + kerr * np.abs(res).sum()
@@ -121,7 +129,7 @@ def test_score_candidates(sp, prec):
     assert np.all(rel <= 2 * (gtol / np.abs(gr) + htol / hr) + 1e-12)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
 def test_score_candidates_exact(sp, prec):
     """Exact one-dimensional scores against the oracle's (exact line search
     along each new coefficient, float64, direct differences) on the same o.
@@ -146,7 +154,7 @@ def test_score_candidates_exact(sp, prec):
     S = y * o < 1
     res = np.where(S, o - y, 0)
     Kc = O.rbf_kernel(X, X[cand], gamma)
-    ktol = 4 * 2 ** -24 if prec == "fp32" else 6e-5
+    ktol = 4 * 2 ** -24 if prec == "fp32" else 2e-5
     sq = (X.astype(np.float64) ** 2).sum(1)
     kerr = ktol * gamma * 2 * sq.max() + 2e-6
     gtol = 1e-5 * (np.abs(res) @ Kc + lam * np.abs(o[cand])) + kerr * (np.abs(res).sum() + n)
@@ -159,7 +167,7 @@ def test_score_candidates_exact(sp, prec):
     assert np.all(np.abs(tg - tref) <= ttol), float(np.max(np.abs(tg - tref) / ttol))
 
 
-@pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("fmt", ["fp32", "bf16x4"])
 @pytest.mark.parametrize("n,m", [(1000, 70), (4099, 129), (33, 1)])
 def test_outputs_gemv(sp, fmt, n, m):
     g = np.random.default_rng(5)
@@ -193,27 +201,37 @@ def test_outputs_gemv(sp, fmt, n, m):
     assert np.all(np.abs(u.cpu().numpy() - 2 * u_ref) <= 4e-6 * (np.abs(Kref.T) @ np.abs(v)) + 2e-7 * np.abs(u_ref))
 
 
-@pytest.mark.parametrize("fmt", ["fp32", "bf16x3"])
+def _split_ref(K):
+    """hi + lo of FP32 values, as the compaction splits them (float64)."""
+    K32 = torch.from_numpy(np.asarray(K, dtype=np.float32))
+    hi = K32.to(torch.bfloat16)
+    lo = (K32 - hi.float()).to(torch.bfloat16)
+    return (hi.double() + lo.double()).numpy()
+
+
+@pytest.mark.parametrize("fmt,kc_fmt", [("fp32", "fp32"), ("bf16x4", "bf16x4"), ("fp32", "bf16x4")])
 # few active points (at most n / 64) take the gather path, more the scan
 @pytest.mark.parametrize("n,m,p", [(5000, 70, 0.5), (1000, 8, 0.0), (1000, 9, 1.0), (777, 64, 0.03),
                                    (20000, 70, 0.01), (50000, 130, 0.005), (6400, 20, 0.018)])
-def test_compact_and_masked_products(sp, fmt, n, m, p):
+def test_compact_and_masked_products(sp, fmt, kc_fmt, n, m, p):
     g = np.random.default_rng(6)
     K = np.exp(-g.random((m, n)) * 3)
     km, Kref = _store(K, fmt, sp)
     act = (g.random(n) < p).astype(np.uint8)
     w1 = g.standard_normal(n).astype(np.float32)
     w2 = g.standard_normal(n).astype(np.float32)
-    kc = sp.kmat_empty(km.ld, m, fmt, ld=km.ld)
+    kc = sp.kmat_empty(km.ld, m, kc_fmt, ld=km.ld)
     a, b, nact, pos = sp.spsvm_compact_active(km, _t(act), _t(w1), _t(w2), kc)
     torch.cuda.synchronize()
     S = act.astype(bool)
     ns = int(S.sum())
     assert int(nact.item()) == ns
     np.testing.assert_array_equal(pos.cpu().numpy()[S], np.arange(ns))
-    # the compacted rows are exact copies; the tail to a multiple of 128 is zero
+    # the compacted rows are exact copies (or the exact hi / lo split of the
+    # FP32 values); the tail to a multiple of 128 is zero
     kcf = kc.to_float().cpu().numpy().astype(np.float64)
-    np.testing.assert_array_equal(kcf[:, :ns], Kref[:, S])
+    want = Kref[:, S] if fmt == kc_fmt else _split_ref(Kref[:, S])
+    np.testing.assert_array_equal(kcf[:, :ns], want)
     tail = ((ns + 127) // 128) * 128
     assert np.all(kcf[:, ns:tail] == 0)
     ra = Kref[:, S] @ w1[S].astype(np.float64)
@@ -224,15 +242,17 @@ def test_compact_and_masked_products(sp, fmt, n, m, p):
     assert np.all(np.abs(b.cpu().numpy() - rb) <= tolb)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec,kfmt", [("fp32", "fp32"), ("bf16x4", "bf16x4"), ("bf16x4", "fp32")])
 @pytest.mark.parametrize("n,m,p", [(9000, 70, 0.6), (20000, 130, 0.5), (300, 64, 1.0), (2000, 1, 0.7)])
-def test_gram(sp, prec, n, m, p):
+def test_gram(sp, prec, kfmt, n, m, p):
+    """The BF16X4 Gram matrix reads the compact copy as hi / lo planes, from
+    K stored as planes or (the fit's layout) in FP32 and split on the way."""
     g = np.random.default_rng(7)
     n_all = n
     X, _ = _data(n_all, 12, 8)
     J = g.choice(n_all, size=m, replace=False)
     K = O.rbf_kernel(X, X[J], 1.0 / 12).T          # rows = basis
-    km, Kref = _store(K, prec, sp)
+    km, Kref = _store(K, kfmt, sp)
     act = (g.random(n) < p).astype(np.uint8)
     kc = sp.kmat_empty(km.ld, m, prec, ld=km.ld)
     _, _, nact, _ = sp.spsvm_compact_active(km, _t(act), None, None, kc)
@@ -246,8 +266,8 @@ def test_gram(sp, prec, n, m, p):
     Hg = H.cpu().numpy()
     np.testing.assert_array_equal(Hg, Hg.T)
     bound = np.abs(KS) @ np.abs(KS).T
-    # BF16X3: the stored hi+lo kernel values carry ~2^-17 relative error,
-    # plus tensor-core FP32 accumulation
+    # BF16X4: the hi+lo kernel values carry ~2^-17 relative error, plus
+    # tensor-core FP32 accumulation
     rel = 1e-5 if prec == "fp32" else 1e-4
     assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))
 
