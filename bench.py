@@ -38,7 +38,7 @@ WORKLOAD = dict(workload="gaussian_mixture_precision_form", n=500_000, d=128, ba
                 queries=100_000)
 
 SLOTS = ["kernel_block", "score", "outputs", "gemv", "compact", "gram", "cholesky", "solve",
-         "line_search", "decision", "fit"]
+         "line_search", "decision", "fit", "lowrank"]
 
 
 def _peaks():
@@ -494,6 +494,37 @@ def run_ours(args):
     if args.growth:
         growth = _leg(growth_leg, sp, torch, model, X, y, p, work, opts, stream)
 
+    # the same fit with the low-rank correction of the Newton factor
+    # (spsvm_options.lowrank): fit time, and how the Newton systems were solved
+    lowrank = None
+    if args.lowrank:
+        def lowrank_leg():
+            lib.spsvm_profile_enable(1)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            ml = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=None, lowrank=True, **opts)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            pl = {}
+            for k, name in enumerate(SLOTS):
+                if name not in ("cholesky", "lowrank", "solve"):
+                    continue
+                nm, L_, t_, w_ = C.c_char_p(), C.c_int64(), C.c_double(), C.c_double()
+                lib.spsvm_profile_read(k, C.byref(nm), C.byref(L_), C.byref(t_), C.byref(w_))
+                pl[name] = dict(launches=L_.value, ms=t_.value)
+            lib.spsvm_profile_enable(0)
+            kinds = {}
+            for h in ml.history():
+                kinds[h["solve"]] = kinds.get(h["solve"], 0) + 1
+            fl = ml.predict(Xq).cpu().numpy()
+            return dict(fit_s=a0.elapsed_time(a1) / 1e3, newton_steps=ml.info()["newton_steps"],
+                        steps_factor=kinds.get(1, 0), steps_reuse=kinds.get(2, 0),
+                        steps_lowrank=kinds.get(3, 0), profile=pl,
+                        max_decision_diff=float(np.max(np.abs(fl - f.cpu().numpy())
+                                                       / np.maximum(1.0, np.abs(f.cpu().numpy())))))
+        lowrank = _leg(lowrank_leg)
+
     # FP32 form on the same workload (one fit), for the "vs FP32 form" leg
     fp32_form = None
     if args.fp32_form and prec != "fp32":
@@ -579,7 +610,7 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, growth_stop=growth, batched=batched, ovo=ovo,
+                fp32_form=fp32_form, lowrank=lowrank, growth_stop=growth, batched=batched, ovo=ovo,
                 exact_score=exact, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         times, factor, cores, sample = cpu_baseline_run(steps=1)
@@ -611,6 +642,8 @@ def main():
     ap.add_argument("--ovo", type=int, default=1, help="one-vs-one leg (10 classes, 45 pairs)")
     ap.add_argument("--exact-score", type=int, default=1,
                     help="heuristic vs exact one-dimensional selection score leg")
+    ap.add_argument("--lowrank", type=int, default=1,
+                    help="one fit with the low-rank correction of the Newton factor")
     ap.add_argument("--growth", type=int, default=1,
                     help="report the growth stop at epsilon = 5e-6 and accuracy vs |J|")
     ap.add_argument("--micro", choices=["cholesky"], default=None,

@@ -232,6 +232,19 @@ int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active,
                          int32_t* pos, void* scratch, size_t scratch_bytes,
                          void* stream);
 
+/* Change of the active set (Section 4 reoptimisation: between Newton steps
+ * the set S of points with y_i o_i < 1 changes by a few points, and the
+ * Newton matrix by their kernel rows):
+ *   D = {i : active[i] != ref[i]} in increasing i, *k_dev = |D|;
+ * when |D| <= kmax also Wt[j*ldw + r] = K row j, column D_r (j < K->rows,
+ * r < |D|; columns |D|..ldw-1 untouched) and sign[r] = +1 if D_r entered S
+ * (active) and -1 if it left.  active, ref: device n bytes; Wt: device FP32,
+ * K->rows x ldw, ldw >= kmax; sign: device FP32, kmax; k_dev: device int32.
+ * scratch: spsvm_compact_scratch_bytes(n, 0) bytes. */
+int spsvm_active_diff(const spsvm_kmat* K, const uint8_t* active, const uint8_t* ref, int32_t kmax,
+                      float* Wt, int64_t ldw, float* sign, int32_t* k_dev, void* scratch,
+                      size_t scratch_bytes, void* stream);
+
 /* Masked Gram matrix (the generalised Hessian of Eq. 4 on the active set):
  *   H = lambda * K_JJ + Kc^T Kc,   Kc = K_SJ (compacted, rows = basis),
  * where K_JJ[a][b] = K row b at column J[a] (symmetrised).  The
@@ -303,6 +316,35 @@ int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift, con
                       double* x, int32_t max_iter, double tol, int32_t* iters,
                       double* backward_error, void* work, size_t work_bytes, void* stream);
 
+/* Low-rank correction of the mixed solve's factor (Section 4
+ * reoptimisation, the Newton system after the active set changed by k
+ * points): H = H_a + W^T Sigma W, where H_a is the matrix whose FP32 factor
+ * L (L L^T = H_a, no shift) spsvm_cholesky_mixed left in mixed_work, W
+ * (k x m) holds the kernel rows of the k points and Sigma = diag(sign) (+1
+ * entered, -1 left).  spsvm_lowrank_factor forms V = L^{-1} W^T (FP32, one
+ * launch over 64 x 16 tiles with bounded flag waits), the capacitance
+ * C = Sigma + V^T V and its inverse (FP32 Gauss-Jordan, partial pivoting)
+ * in lr_work; info: device int32, 0, or p + 1 when pivot p of C is below
+ * 1e-3 of its largest entry (C too ill-conditioned for its FP32 inverse:
+ * factor H afresh).
+ * spsvm_solve_lowrank then solves H x = b by iterative refinement with FP64
+ * residuals of the given H (full, symmetric, FP64), each step applying
+ * H^{-1} ~ L^{-T} (I - V C^{-1} V^T) L^{-1} (Sherman-Morrison-Woodbury), with
+ * the stopping rules and results of spsvm_solve_mixed; it leaves the factor
+ * and the correction intact, so later right-hand sides reuse them.
+ * Wt: device FP32, m x ldw (ldw >= k); sign: device FP32, k;
+ * 1 <= k <= SPSVM_LOWRANK_KMAX; lr_work: device, 256-byte aligned,
+ * spsvm_lowrank_work_bytes(m, k) bytes (enough for every smaller m and k). */
+#define SPSVM_LOWRANK_KMAX 128
+size_t spsvm_lowrank_work_bytes(int64_t m, int32_t kmax);
+int spsvm_lowrank_factor(void* mixed_work, size_t mixed_bytes, int64_t m, const float* Wt,
+                         int64_t ldw, const float* sign, int32_t k, void* lr_work,
+                         size_t lr_bytes, int32_t* info, void* stream);
+int spsvm_solve_lowrank(const double* H, int64_t m, int64_t ldh, const double* b, double* x,
+                        int32_t max_iter, double tol, int32_t* iters, double* backward_error,
+                        void* mixed_work, size_t mixed_bytes, void* lr_work, size_t lr_bytes,
+                        int32_t k, void* stream);
+
 /* Exact line search along a Newton direction (f is convex and piecewise
  * quadratic along a line; Section 4's Newton reoptimisation):
  *   phi'(t) = a0 + a1 t - sum_i v_i max(0, m_i - t v_i),
@@ -363,6 +405,13 @@ typedef struct spsvm_options {
   int32_t  bias;           /* nonzero: fit Eq. 4's bias b as an unregularised coordinate
                               (f(x) = k(x, X_J) beta + b; spsvm_model_bias reads it); 0: b = 0
                               as Section 2 does.  Not with refine > 0. */
+  int32_t  lowrank;        /* nonzero: with SPSVM_SOLVE_MIXED and |J| >= 512, when the active
+                              set changed by k <= min(64, |J| / 8) points since the unshifted
+                              FP32 factor in hand was formed, correct that factor by their
+                              low-rank term (spsvm_lowrank_factor) instead of factoring afresh
+                              (a correction whose capacitance fails the pivot test, or whose
+                              direction finds no descent, falls back to a fresh factor);
+                              0 (default): factor afresh whenever the active set changes */
 } spsvm_options;
 
 /* Per-Newton-step record (kept for every fit). */
@@ -375,7 +424,18 @@ typedef struct spsvm_step {
   int32_t errors;          /* #{y_i o_i <= 0} after the step */
   int32_t jitter;          /* diagonal jitter level l of the factorisation: H + 10^(l-10) tr(H)/|J| I
                               (-1: none); tried upwards from the fit's previous level */
+  int32_t changed;         /* points whose active flag the step changed */
+  int32_t solve;           /* how the Newton system was solved: SPSVM_NEWTON_* (0 when no
+                              step was taken) */
 } spsvm_step;
+
+/* spsvm_step.solve */
+#define SPSVM_NEWTON_NONE     0  /* no Newton system solved (final check) */
+#define SPSVM_NEWTON_FACTOR   1  /* new factorisation of H (+ shift) */
+#define SPSVM_NEWTON_REUSE    2  /* factor in hand, the active set unchanged */
+#define SPSVM_NEWTON_LOWRANK  3  /* factor in hand plus the low-rank correction
+                                    (spsvm_lowrank_factor) for the points that
+                                    entered or left the active set */
 
 /* Device bytes the fit needs for n points in d dimensions and the budget;
  * the fit lays out all its buffers inside one workspace of this size. */
@@ -529,10 +589,11 @@ uint64_t spsvm_launch_count(void);
  * around each step's launches.  enable(1) clears the totals and starts
  * recording, enable(0) stops.  Slots: 0 kernel_block, 1 score, 2 outputs,
  * 3 gemv, 4 compact, 5 gram, 6 cholesky, 7 solve, 8 line_search,
- * 9 decision, 10 fit.  read() waits for the recorded events and returns the
- * launch count, total milliseconds and total algorithmic work (flops for
- * kernel_block / score / gram / cholesky / decision, bytes for the HBM
- * passes) of a slot.  `name` receives a static string. */
+ * 9 decision, 10 fit, 11 lowrank (spsvm_lowrank_factor).  read() waits for
+ * the recorded events and returns the launch count, total milliseconds and
+ * total algorithmic work (flops for kernel_block / score / gram / cholesky /
+ * decision / lowrank, bytes for the HBM passes) of a slot.  `name` receives
+ * a static string. */
 int spsvm_profile_enable(int32_t on);
 int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches, double* ms,
                        double* work);

@@ -51,7 +51,8 @@ class spsvm_options(C.Structure):
                 ("seed", C.c_uint64), ("initial_basis", C.POINTER(C.c_int64)),
                 ("n_initial", C.c_int32), ("fixed_basis", C.c_int32),
                 ("refine", C.c_int32), ("record", C.c_int32), ("stream", C.c_void_p),
-                ("newton_solver", C.c_int32), ("score", C.c_int32), ("bias", C.c_int32)]
+                ("newton_solver", C.c_int32), ("score", C.c_int32), ("bias", C.c_int32),
+                ("lowrank", C.c_int32)]
 
 
 class spsvm_problem(C.Structure):
@@ -64,7 +65,14 @@ class spsvm_problem(C.Structure):
 class spsvm_step(C.Structure):
     _fields_ = [("basis", C.c_int32), ("active", C.c_int32), ("gnorm", C.c_double),
                 ("t", C.c_double), ("loss", C.c_double), ("errors", C.c_int32),
-                ("jitter", C.c_int32)]
+                ("jitter", C.c_int32), ("changed", C.c_int32), ("solve", C.c_int32)]
+
+
+SPSVM_NEWTON_NONE = 0
+SPSVM_NEWTON_FACTOR = 1
+SPSVM_NEWTON_REUSE = 2
+SPSVM_NEWTON_LOWRANK = 3
+SPSVM_LOWRANK_KMAX = 128
 
 
 _P = C.c_void_p
@@ -102,6 +110,12 @@ SIGNATURES = {
     "spsvm_solve_mixed": (_I32, [_P, _I64, _I64, C.c_double, _P, _P, _I32, C.c_double,
                                  C.POINTER(_I32), C.POINTER(C.c_double), _P, _SZ, _P]),
     "spsvm_cholesky_solve": (_I32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "spsvm_active_diff": (_I32, [C.POINTER(spsvm_kmat), _P, _P, _I32, _P, _I64, _P, _P, _P, _SZ,
+                                 _P]),
+    "spsvm_lowrank_work_bytes": (_SZ, [_I64, _I32]),
+    "spsvm_lowrank_factor": (_I32, [_P, _SZ, _I64, _P, _I64, _P, _I32, _P, _SZ, _P, _P]),
+    "spsvm_solve_lowrank": (_I32, [_P, _I64, _I64, _P, _P, _I32, C.c_double, C.POINTER(_I32),
+                                   C.POINTER(C.c_double), _P, _SZ, _P, _SZ, _I32, _P]),
     "spsvm_line_scratch_bytes": (_SZ, [_I64]),
     "spsvm_line_search": (_I32, [_P, _P, _P, _I64, _P, _P, _I32, _D, C.POINTER(_D), _P, _P, _SZ,
                                  _P]),

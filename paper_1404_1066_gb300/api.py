@@ -267,6 +267,64 @@ def spsvm_solve_mixed(H: torch.Tensor, b: torch.Tensor, shift=0.0, max_iter=30, 
     return 0, st, x, it.value, be.value
 
 
+def spsvm_solve_lowrank(Ha: torch.Tensor, H: torch.Tensor, Wt: torch.Tensor, sign: torch.Tensor,
+                        b: torch.Tensor, max_iter=30, tol=1e-13, extra_rhs=()):
+    """Solves H x = b where H = Ha + W^T diag(sign) W (all FP64 full
+    symmetric on the device; Wt = W^T, m x k FP32; sign FP32 +-1): the FP32
+    factor of Ha, the low-rank correction for W, FP64 refinement against H.
+    Returns (info_factor, info_capacitance, status, x, iters, backward_error,
+    xs) with xs the solutions of extra_rhs (same factor and correction)."""
+    m = H.shape[0]
+    k = Wt.shape[1]
+    wb = _lib().spsvm_mixed_work_bytes(m)
+    work = torch.empty(max(256, wb), dtype=torch.uint8, device=H.device)
+    info = torch.zeros(2, dtype=torch.int32, device=H.device)
+    check(_lib().spsvm_cholesky_mixed(ptr(Ha), m, Ha.stride(0), 0.0, ptr(info), ptr(work), wb,
+                                      stream_ptr()), "spsvm_cholesky_mixed")
+    x = torch.zeros(m, dtype=torch.float64, device=H.device)
+    if int(info[0].item()) != 0:
+        return int(info[0].item()), None, None, x, 0, None, []
+    lb = _lib().spsvm_lowrank_work_bytes(m, k)
+    lw = torch.empty(max(256, lb), dtype=torch.uint8, device=H.device)
+    check(_lib().spsvm_lowrank_factor(ptr(work), wb, m, ptr(Wt), Wt.stride(0), ptr(sign), k,
+                                      ptr(lw), lb, ptr(info[1:]), stream_ptr()),
+          "spsvm_lowrank_factor")
+    ic = int(info[1].item())
+    if ic != 0:
+        return 0, ic, None, x, 0, None, []
+    out = []
+    for rhs in (b,) + tuple(extra_rhs):
+        xx = torch.zeros(m, dtype=torch.float64, device=H.device)
+        it = C.c_int32()
+        be = C.c_double()
+        st = _lib().spsvm_solve_lowrank(ptr(H), m, H.stride(0), ptr(rhs), ptr(xx), int(max_iter),
+                                        float(tol), C.byref(it), C.byref(be), ptr(work), wb,
+                                        ptr(lw), lb, k, stream_ptr())
+        if st not in (L.SPSVM_OK, L.SPSVM_ERR_NO_CONVERGE):
+            check(st, "spsvm_solve_lowrank")
+        out.append((st, xx, it.value, be.value))
+    st, x, its, be = out[0]
+    return 0, 0, st, x, its, be, [o[1] for o in out[1:]]
+
+
+def spsvm_active_diff(K: KMat, active, ref, kmax, rows=None):
+    """(k, Wt, sign): the points whose flag differs between active and ref,
+    in increasing order, their kernel rows (Wt[j, r] = K[j, D_r]) and signs
+    (+1 entered, -1 left); Wt and sign are filled when k <= kmax."""
+    ks = K.struct(rows)
+    sb = _lib().spsvm_compact_scratch_bytes(K.n, 0)
+    scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=K.buf.device)
+    ldw = max(1, kmax)
+    Wt = torch.zeros((ks.rows, ldw), dtype=torch.float32, device=K.buf.device)
+    sign = torch.zeros(ldw, dtype=torch.float32, device=K.buf.device)
+    kd = torch.zeros(1, dtype=torch.int32, device=K.buf.device)
+    check(_lib().spsvm_active_diff(C.byref(ks), ptr(active), ptr(ref), int(kmax), ptr(Wt), ldw,
+                                   ptr(sign), ptr(kd), ptr(scratch), sb, stream_ptr()),
+          "spsvm_active_diff")
+    k = int(kd.item())
+    return k, Wt[:, :min(k, kmax)], sign[:min(k, kmax)]
+
+
 def spsvm_cholesky_mixed(H: torch.Tensor, shift=0.0):
     """FP32 Cholesky factor of H + shift I (H FP64, full symmetric, not
     overwritten).  Returns (info, L): L is the m x round_up(m, 4) FP32 view
@@ -328,7 +386,7 @@ def spsvm_draw_candidates(n, J, kappa, seed, round_index):
 def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp32",
                  growth_tol=0.0, rel_tol=0.0, seed=0, initial_basis=None, fixed_basis=False,
                  refine=0, record=False, stream=None, newton_solver="mixed", score="heuristic",
-                 bias=False):
+                 bias=False, lowrank=False):
     o = spsvm_options()
     o.candidates = int(candidates)
     o.add_per_round = int(add_per_round)
@@ -349,6 +407,7 @@ def make_options(candidates=256, add_per_round=64, max_newton=50, precision="fp3
     o.newton_solver = {"mixed": L.SPSVM_SOLVE_MIXED, "fp64": L.SPSVM_SOLVE_FP64}[newton_solver]
     o.score = {"heuristic": L.SPSVM_SCORE_HEURISTIC, "exact": L.SPSVM_SCORE_EXACT}[score]
     o.bias = int(bool(bias))
+    o.lowrank = int(bool(lowrank))
     return o, keep
 
 
@@ -403,7 +462,8 @@ class Model:
         check(_lib().spsvm_model_history(self.handle, C.cast(arr, C.c_void_p), cnt.value,
                                          C.byref(cnt)), "spsvm_model_history")
         return [dict(basis=a.basis, active=a.active, gnorm=a.gnorm, t=a.t, loss=a.loss,
-                     errors=a.errors, jitter=a.jitter) for a in arr[:cnt.value]]
+                     errors=a.errors, jitter=a.jitter, changed=a.changed, solve=a.solve)
+                for a in arr[:cnt.value]]
 
     def round(self, r):
         nc = C.c_int32()

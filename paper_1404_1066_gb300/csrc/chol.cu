@@ -1182,6 +1182,295 @@ __global__ void __launch_bounds__(MX_T) absmax_blocks(const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank correction of the FP32 factor.  Between Newton steps of Section
+// 4's reoptimisation the active set changes by a few points, and with it the
+// Newton matrix by a rank-k term: H = H_a + W^T Sigma W, W (k x m) the kernel
+// rows of the points that entered (Sigma = +1) or left (-1) S since the
+// factored matrix H_a = L L^T.  With V = L^{-1} W^T (m x k) and the k x k
+// capacitance C = Sigma + V^T V, the Sherman-Morrison-Woodbury identity gives
+//   H^{-1} = L^{-T} (I - V C^{-1} V^T) L^{-1},
+// which the refinement loop applies as its preconditioner (the residual is
+// still taken with the freshly built FP64 H, so the result reaches the same
+// FP64 backward error).
+// ---------------------------------------------------------------------------
+constexpr int LR_G = 16;     // columns of a V tile
+constexpr int LR_T = 256;    // threads of the tile solve
+
+// Tile (block row i, column group g) of V = L^{-1} W^T, left-looking:
+// V_ig = L_ii^{-1} (W_ig - sum_{j<i} L_ij V_jg).  Tiles are taken by ticket
+// in (i, g) order, so each waits only for tiles of CTAs that started before
+// it.  Thread t: row t / 4, columns 4 (t % 4) .. + 3 of the tile.  Flags:
+// 0 pending, 1 published, 2 abandoned (a wait gave up).
+__global__ void __launch_bounds__(LR_T) lr_trsm_fwd(const float* __restrict__ L, int64_t ldl,
+                                                   int64_t m, const float* __restrict__ Wt,
+                                                   int64_t ldw_in, int32_t k,
+                                                   float* __restrict__ V, int64_t ldv, int32_t G,
+                                                   unsigned* __restrict__ flags,
+                                                   unsigned* __restrict__ ticket) {
+  __shared__ float Li[NB][NB + 1];
+  __shared__ float Ls[NB][NB + 1];
+  __shared__ float Vs[NB][LR_G];
+  __shared__ unsigned k_s;
+  __shared__ unsigned st_s;
+  const int t = threadIdx.x;
+  if (t == 0) k_s = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t i = k_s / G;
+  const int g = (int)(k_s % G);
+  const int64_t r0 = i * NB;
+  const int nb = (int)min64(NB, m - r0);
+  const int r = t >> 2, c0 = 4 * (t & 3);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  bool ok = true;
+  // the diagonal block's inverse does not depend on V: read it first, off
+  // the chain of tiles
+  load_diag_inverse(L, ldl, r0, nb, Li);
+  for (int64_t j = 0; j < i && ok; ++j) {
+    // (the previous pass's reads of Ls / Vs end at this barrier)
+    if (t == 0) st_s = wait_flag(&flags[j * G + g], 31);
+    __syncthreads();
+    if (st_s != 1u) {
+      ok = false;
+      break;
+    }
+    for (int e = t; e < NB * NB; e += LR_T) {
+      const int rr = e / NB, cc = e % NB;
+      Ls[rr][cc] = rr < nb ? L[(r0 + rr) * ldl + j * NB + cc] : 0.f;
+    }
+    for (int e = t; e < NB * LR_G; e += LR_T) {
+      const int rr = e / LR_G, cc = e % LR_G;
+      Vs[rr][cc] = __ldcg(V + (j * NB + rr) * ldv + g * LR_G + cc);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < NB; ++q) {
+      const float a = Ls[r][q];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] = fmaf(a, Vs[q][c0 + c], acc[c]);
+    }
+  }
+  __syncthreads();
+  // right-hand side minus the updates, then the diagonal-block inverse
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int col = g * LR_G + c0 + c;   // columns past k are zero
+    Vs[r][c0 + c] = (r < nb && col < k) ? Wt[(r0 + r) * ldw_in + col] - acc[c] : 0.f;
+  }
+  __syncthreads();
+  float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+  for (int q = 0; q < NB; ++q) {
+    const float a = Li[r][q];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = fmaf(a, Vs[q][c0 + c], out[c]);
+  }
+  if (r < nb)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) __stcg(V + (r0 + r) * ldv + g * LR_G + c0 + c, out[c]);
+  __threadfence();
+  __syncthreads();
+  if (t == 0) st_release_u32(&flags[i * G + g], ok ? 1u : 2u);
+}
+
+// Partial sums of V^T V over slices of LR_ROWS rows of V (FP32 products,
+// FP64 sums): part[z][a][b] for slice z.  One block per 16 x 16 tile of the
+// k x k result and slice; thread t: entry (t / 16, t % 16).
+constexpr int LR_ROWS = 256;
+__global__ void __launch_bounds__(256) lr_capacitance(const float* __restrict__ V, int64_t ldv,
+                                                     int64_t m, int64_t ldp,
+                                                     double* __restrict__ part) {
+  __shared__ float A[64][LR_G + 1], B[64][LR_G + 1];
+  const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+  const int ga = blockIdx.x * LR_G, gb = blockIdx.y * LR_G;
+  const int64_t lo = (int64_t)blockIdx.z * LR_ROWS, hi = min64(m, lo + LR_ROWS);
+  double acc = 0.0;
+  for (int64_t i0 = lo; i0 < hi; i0 += 64) {
+    for (int e = threadIdx.x; e < 64 * LR_G; e += 256) {
+      const int rr = e / LR_G, cc = e % LR_G;
+      const bool in = i0 + rr < hi;
+      A[rr][cc] = in ? V[(i0 + rr) * ldv + ga + cc] : 0.f;
+      B[rr][cc] = in ? V[(i0 + rr) * ldv + gb + cc] : 0.f;
+    }
+    __syncthreads();
+    float f = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < 64; ++q) f = fmaf(A[q][a], B[q][b], f);
+    acc += (double)f;
+    __syncthreads();
+  }
+  part[(int64_t)blockIdx.z * ldp * ldp + (int64_t)(ga + a) * ldp + gb + b] = acc;
+}
+
+// C = Sigma + sum_z part[z] (slices in order), stored FP32 with row pitch ldc.
+__global__ void lr_capacitance_sum(const double* __restrict__ part, int64_t slices, int64_t ldp,
+                                   const float* __restrict__ sign, int32_t k, float* __restrict__ C,
+                                   int64_t ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int64_t a = e / k, b = e % k;
+  double v = a == b ? (double)sign[a] : 0.0;
+  for (int64_t z = 0; z < slices; ++z) v += part[z * ldp * ldp + a * ldp + b];
+  C[a * ldc + b] = (float)v;
+}
+
+// In-place Gauss-Jordan inversion of the k x k capacitance with partial
+// pivoting (one CTA; C in shared memory): C <- C^{-1}.  info: 0, or p + 1
+// when pivot p is below kLrPivotTol of the largest entry of C (C too
+// ill-conditioned for an FP32 inverse: the caller refactors instead).
+constexpr int LR_INV_T = 1024;
+// a pivot below this fraction of max |C| rejects the correction: an FP32
+// inverse of a worse-conditioned capacitance slows the refinement down more
+// than a fresh factorisation costs
+constexpr float kLrPivotTol = 1e-3f;
+__global__ void __launch_bounds__(LR_INV_T) lr_invert(float* __restrict__ C, int64_t ldc, int32_t k,
+                                                      int32_t* __restrict__ info) {
+  extern __shared__ float sh[];
+  float* A = sh;                              // k x (k + 1)
+  int* perm = reinterpret_cast<int*>(A + k * (k + 1));
+  __shared__ int piv_s;
+  __shared__ float cmax_s;
+  __shared__ float wmax[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int ld = k + 1;
+  float lmax = 0.f;
+  for (int e = t; e < k * k; e += LR_INV_T) {
+    const float v = C[(e / k) * ldc + e % k];
+    A[(e / k) * ld + e % k] = v;
+    lmax = fmaxf(lmax, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if (lane == 0) wmax[w] = lmax;
+  __syncthreads();
+  if (t == 0) {
+    float mx = 0.f;
+    for (int q = 0; q < LR_INV_T / 32; ++q) mx = fmaxf(mx, wmax[q]);
+    cmax_s = mx;
+  }
+  __syncthreads();
+  const float tiny = kLrPivotTol * cmax_s;
+  for (int p = 0; p < k; ++p) {
+    // pivot: the largest |A[r][p]|, r >= p (ties to the smaller row)
+    if (w == 0) {
+      float best = -1.f;
+      int bi = p;
+      for (int rr = p + lane; rr < k; rr += 32) {
+        const float v = fabsf(A[rr * ld + p]);
+        if (v > best) { best = v; bi = rr; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        piv_s = (best > tiny) ? bi : -1;
+        perm[p] = bi;
+      }
+    }
+    __syncthreads();
+    const int pr = piv_s;
+    if (pr < 0) {
+      if (t == 0) *info = p + 1;
+      return;
+    }
+    if (pr != p)
+      for (int c = t; c < k; c += LR_INV_T) {
+        const float a = A[p * ld + c];
+        A[p * ld + c] = A[pr * ld + c];
+        A[pr * ld + c] = a;
+      }
+    __syncthreads();
+    const float inv = 1.0f / A[p * ld + p];
+    __syncthreads();
+    for (int c = t; c < k; c += LR_INV_T) A[p * ld + c] = (c == p ? 1.0f : A[p * ld + c]) * inv;
+    __syncthreads();
+    // eliminate column p from every other row (the pivot column becomes the
+    // inverse's column: A[i][p] <- -A[i][p] / pivot)
+    for (int e = t; e < k * k; e += LR_INV_T) {
+      const int ii = e / k, c = e % k;
+      if (ii == p) continue;
+      const float f = A[ii * ld + p];
+      if (c == p) continue;
+      A[ii * ld + c] = fmaf(-f, A[p * ld + c], A[ii * ld + c]);
+    }
+    __syncthreads();
+    for (int ii = t; ii < k; ii += LR_INV_T)
+      if (ii != p) A[ii * ld + p] = -A[ii * ld + p] * inv;
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int p = k - 1; p >= 0; --p) {
+    const int pr = perm[p];
+    if (pr != p)
+      for (int rr = t; rr < k; rr += LR_INV_T) {
+        const float a = A[rr * ld + p];
+        A[rr * ld + p] = A[rr * ld + pr];
+        A[rr * ld + pr] = a;
+      }
+    __syncthreads();
+  }
+  for (int e = t; e < k * k; e += LR_INV_T) C[(e / k) * ldc + e % k] = A[(e / k) * ld + e % k];
+  if (t == 0) *info = 0;
+}
+
+// Partial dot products s_z[a] = sum_{i in slice z} V[i][a] z[i] over slices
+// of LR_ROWS rows (FP32 products and sums): one block per slice and 16
+// columns; thread t: column t % 16, rows t / 16 + 16 q of the slice.
+__global__ void __launch_bounds__(256) lr_dots(const float* __restrict__ V, int64_t ldv, int64_t m,
+                                              const float* __restrict__ z, int64_t ldp,
+                                              float* __restrict__ sp) {
+  __shared__ float part[16][LR_G + 1];
+  const int c = threadIdx.x & 15, rr = threadIdx.x >> 4;
+  const int a = blockIdx.x * LR_G + c;
+  const int64_t lo = (int64_t)blockIdx.y * LR_ROWS, hi = min64(m, lo + LR_ROWS);
+  float f = 0.f;
+  for (int64_t i = lo + rr; i < hi; i += 16) f = fmaf(V[i * ldv + a], z[i], f);
+  part[rr][c] = f;
+  __syncthreads();
+  if (rr == 0) {
+    float v = 0.f;
+    for (int q = 0; q < 16; ++q) v += part[q][c];
+    sp[(int64_t)blockIdx.y * ldp + a] = v;
+  }
+}
+
+// z[i] -= sum_a V[i][a] w[a], w = C^{-1} s with s the sum of the slices'
+// partial dot products (fixed order), computed by every block (k^2
+// multiply-adds, cheap next to a launch).  Sixteen rows per block pass; lane
+// c of a row covers columns c, c + 16, ...
+__global__ void __launch_bounds__(256) lr_update(const float* __restrict__ V, int64_t ldv, int64_t m,
+                                                const float* __restrict__ Ci, int64_t ldc,
+                                                const float* __restrict__ sp, int64_t slices,
+                                                int64_t ldp, int32_t k, float* __restrict__ z) {
+  __shared__ float ws[SPSVM_LOWRANK_KMAX];
+  __shared__ float ss[SPSVM_LOWRANK_KMAX];
+  for (int a = threadIdx.x; a < k; a += 256) {
+    double v = 0.0;
+    for (int64_t q = 0; q < slices; ++q) v += (double)sp[q * ldp + a];
+    ss[a] = (float)v;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += 256) {
+    float v = 0.f;
+    for (int b = 0; b < k; ++b) v = fmaf(Ci[a * ldc + b], ss[b], v);
+    ws[a] = v;
+  }
+  __syncthreads();
+  const int c = threadIdx.x & 15, rr = threadIdx.x >> 4;
+  for (int64_t i0 = (int64_t)blockIdx.x * 16; i0 < m; i0 += (int64_t)gridDim.x * 16) {
+    const int64_t i = i0 + rr;
+    float v = 0.f;
+    if (i < m)
+      for (int a = c; a < k; a += 16) v = fmaf(V[i * ldv + a], ws[a], v);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+    if (c == 0 && i < m) z[i] -= v;
+  }
+}
+
 }  // namespace
 }  // namespace spsvm
 
@@ -1426,10 +1715,45 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   return SPSVM_OK;
 }
 
-extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift,
-                                 const double* b, double* x, int32_t max_iter, double tol,
-                                 int32_t* iters, double* backward_error, void* work,
-                                 size_t work_bytes, void* stream) {
+namespace {
+
+// The low-rank correction's state inside its work buffer (sizes from k).
+struct LowRankLayout {
+  int64_t ldv, G, slices;
+  size_t V, Ci, s, cpart, flags, total;
+};
+
+LowRankLayout lowrank_layout(int64_t m, int32_t k) {
+  auto al = [](size_t b) { return (size_t)round_up((int64_t)b, (int64_t)256); };
+  LowRankLayout ly{};
+  ly.G = ceil_div((int64_t)k, (int64_t)LR_G);
+  ly.ldv = ly.G * LR_G;
+  ly.slices = ceil_div(m, (int64_t)LR_ROWS);
+  const int64_t B = ceil_div(m, (int64_t)NB);
+  size_t off = 0;
+  ly.V = off;      off += al((size_t)B * NB * ly.ldv * 4);
+  ly.Ci = off;     off += al((size_t)k * ly.ldv * 4);
+  ly.s = off;      off += al((size_t)ly.slices * ly.ldv * 4);              // partial dots
+  ly.cpart = off;  off += al((size_t)ly.slices * ly.ldv * ly.ldv * 8);     // partial V^T V
+  ly.flags = off;  off += al((size_t)(B * ly.G + 1) * 4);
+  ly.total = off;
+  return ly;
+}
+
+struct LowRankView {
+  const float* V;
+  const float* Ci;
+  float* s;
+  int64_t ldv, slices;
+  int32_t k, G;
+};
+
+}  // namespace
+
+static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shift,
+                            const double* b, double* x, int32_t max_iter, double tol,
+                            int32_t* iters, double* backward_error, void* work,
+                            size_t work_bytes, const LowRankView* lr, void* stream) {
   if (!H || !b || !x || m < 0 || ldh < m || max_iter < 1 || !(tol > 0.0) || !(shift >= 0.0))
     return set_error(SPSVM_ERR_ARG, "solve_mixed: bad arguments");
   if (iters) *iters = 0;
@@ -1480,6 +1804,14 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
     unsigned* tk = tickets + 2 * (it % kTicketSteps);
     trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag);
     SPSVM_LAUNCH_CHECK();
+    if (lr) {   // z <- (I - V C^{-1} V^T) z
+      lr_dots<<<dim3((unsigned)lr->G, (unsigned)lr->slices), 256, 0, s>>>(lr->V, lr->ldv, m, zw,
+                                                                          lr->ldv, lr->s);
+      SPSVM_LAUNCH_CHECK();
+      lr_update<<<(unsigned)min64(ceil_div(m, (int64_t)16), 2 * (int64_t)sm_count()), 256, 0, s>>>(
+          lr->V, lr->ldv, m, lr->Ci, lr->ldv, lr->s, lr->slices, lr->ldv, lr->k, zw);
+      SPSVM_LAUNCH_CHECK();
+    }
     trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag);
     SPSVM_LAUNCH_CHECK();
     add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
@@ -1506,4 +1838,69 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
     prev = nv[1];
   }
   return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: %d iterations not enough", max_iter);
+}
+
+extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift,
+                                 const double* b, double* x, int32_t max_iter, double tol,
+                                 int32_t* iters, double* backward_error, void* work,
+                                 size_t work_bytes, void* stream) {
+  return solve_mixed_impl(H, m, ldh, shift, b, x, max_iter, tol, iters, backward_error, work,
+                          work_bytes, nullptr, stream);
+}
+
+extern "C" size_t spsvm_lowrank_work_bytes(int64_t m, int32_t kmax) {
+  if (m < 1 || kmax < 1 || kmax > SPSVM_LOWRANK_KMAX) return 0;
+  return lowrank_layout(m, kmax).total;
+}
+
+extern "C" int spsvm_lowrank_factor(void* mixed_work, size_t mixed_bytes, int64_t m, const float* Wt,
+                                    int64_t ldw, const float* sign, int32_t k, void* lr_work,
+                                    size_t lr_bytes, int32_t* info, void* stream) {
+  if (!mixed_work || !Wt || !sign || !lr_work || !info || m < 1 || k < 1 ||
+      k > SPSVM_LOWRANK_KMAX || ldw < k)
+    return set_error(SPSVM_ERR_ARG, "lowrank_factor: bad arguments (m=%lld k=%d)", (long long)m, k);
+  const MixedLayout ml = mixed_layout(m);
+  const LowRankLayout ly = lowrank_layout(m, k);
+  if (mixed_bytes < ml.total || lr_bytes < ly.total || (reinterpret_cast<uintptr_t>(lr_work) & 255) != 0)
+    return set_error(SPSVM_ERR_OOM, "lowrank_factor: work too small or misaligned");
+  cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_LOWRANK, s, (double)m * m * k + 2.0 * (double)m * k * k + (double)k * k * k);
+  char* w = static_cast<char*>(lr_work);
+  const float* L = reinterpret_cast<const float*>(static_cast<char*>(mixed_work) + ml.L);
+  float* V = reinterpret_cast<float*>(w + ly.V);
+  float* Ci = reinterpret_cast<float*>(w + ly.Ci);
+  unsigned* flags = reinterpret_cast<unsigned*>(w + ly.flags);
+  const int64_t B = ceil_div(m, (int64_t)NB);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(B * ly.G + 1) * 4, s));
+  lr_trsm_fwd<<<(unsigned)(B * ly.G), LR_T, 0, s>>>(L, ml.ldl, m, Wt, ldw, k, V, ly.ldv, (int32_t)ly.G,
+                                                    flags, flags + B * ly.G);
+  SPSVM_LAUNCH_CHECK();
+  double* cpart = reinterpret_cast<double*>(w + ly.cpart);
+  lr_capacitance<<<dim3((unsigned)ly.G, (unsigned)ly.G, (unsigned)ly.slices), 256, 0, s>>>(
+      V, ly.ldv, m, ly.ldv, cpart);
+  SPSVM_LAUNCH_CHECK();
+  lr_capacitance_sum<<<(unsigned)ceil_div((int64_t)k * k, (int64_t)256), 256, 0, s>>>(
+      cpart, ly.slices, ly.ldv, sign, k, Ci, ly.ldv);
+  SPSVM_LAUNCH_CHECK();
+  const size_t smem = (size_t)k * (k + 1) * 4 + (size_t)k * 4;
+  SPSVM_CUDA_TRY(cudaFuncSetAttribute(lr_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  lr_invert<<<1, LR_INV_T, smem, s>>>(Ci, ly.ldv, k, info);
+  SPSVM_LAUNCH_CHECK();
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_solve_lowrank(const double* H, int64_t m, int64_t ldh, const double* b, double* x,
+                                   int32_t max_iter, double tol, int32_t* iters,
+                                   double* backward_error, void* mixed_work, size_t mixed_bytes,
+                                   void* lr_work, size_t lr_bytes, int32_t k, void* stream) {
+  if (!lr_work || k < 1 || k > SPSVM_LOWRANK_KMAX || m < 1)
+    return set_error(SPSVM_ERR_ARG, "solve_lowrank: bad arguments");
+  const LowRankLayout ly = lowrank_layout(m, k);
+  if (lr_bytes < ly.total) return set_error(SPSVM_ERR_OOM, "solve_lowrank: work too small");
+  char* w = static_cast<char*>(lr_work);
+  LowRankView v{reinterpret_cast<const float*>(w + ly.V), reinterpret_cast<const float*>(w + ly.Ci),
+                reinterpret_cast<float*>(w + ly.s), ly.ldv, ly.slices, k, (int32_t)ly.G};
+  return solve_mixed_impl(H, m, ldh, 0.0, b, x, max_iter, tol, iters, backward_error, mixed_work,
+                          mixed_bytes, &v, stream);
 }

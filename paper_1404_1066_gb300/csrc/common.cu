@@ -81,7 +81,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 namespace {
 const char* kSlotNames[PROF_SLOTS] = {"kernel_block", "score", "outputs", "gemv", "compact",
                                       "gram", "cholesky", "solve", "line_search", "decision",
-                                      "fit"};
+                                      "fit", "lowrank"};
 struct Pending {
   int slot;
   cudaEvent_t e0, e1;

@@ -209,22 +209,31 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
+// smallest |J| at which a changed active set corrects the factor in hand by
+// a low-rank term instead of factoring afresh (below it the factorisation
+// is as cheap as the correction)
+constexpr int64_t kLowRankMinBasis = 512;
+// largest rank of the correction the fit uses (the correction's cost grows
+// with it, and past it a fresh factorisation costs about the same)
+constexpr int64_t kLowRankMax = 64;
+
 // ---- workspace layout ------------------------------------------------------
 struct Layout {
   int64_t n, d, ldn, ldh, jcap, kappa, q;
   size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
       off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_tmp2, off_ws, off_sv, off_J,
       off_cand,
-      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, off_kjj, total;
+      off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, off_kjj, off_anchor, off_Wt,
+      off_sign, off_lr, total;
   size_t scratch_bytes;
   size_t kbytes;
-  size_t chw_bytes, sv_bytes, mix_bytes;
+  size_t chw_bytes, sv_bytes, mix_bytes, lr_bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int32_t kappa,
-                   int32_t q, int32_t solver, int32_t score, int32_t bias) {
+                   int32_t q, int32_t solver, int32_t score, int32_t bias, int32_t lowrank) {
   Layout L{};
   L.n = n;
   L.d = d;
@@ -286,12 +295,20 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
   L.off_mix = take(L.mix_bytes);
   // symmetric K_JJ (FP64), extended as the basis grows; read by the Gram finish
   L.off_kjj = take((size_t)L.jcap * L.jcap * 8);
+  // low-rank correction of the mixed solve: active flags of the factored
+  // matrix, kernel rows and signs of the changed points, the correction
+  const bool lr = lowrank && solver == SPSVM_SOLVE_MIXED && L.jcap >= kLowRankMinBasis;
+  L.off_anchor = take(lr ? (size_t)n : 0);
+  L.off_Wt = take(lr ? (size_t)L.jcap * SPSVM_LOWRANK_KMAX * 4 : 0);
+  L.off_sign = take(lr ? (size_t)SPSVM_LOWRANK_KMAX * 4 : 0);
+  L.lr_bytes = lr ? spsvm_lowrank_work_bytes(L.jcap, SPSVM_LOWRANK_KMAX) : 0;
+  L.off_lr = take(L.lr_bytes);
   L.total = off;
   return L;
 }
 
 struct Opts {
-  int32_t kappa, q, max_newton, precision, refine, record, solver, score, bias;
+  int32_t kappa, q, max_newton, precision, refine, record, solver, score, bias, lowrank;
   double growth_tol, rel_tol;
   uint64_t seed;
   bool fixed;
@@ -314,10 +331,13 @@ Opts resolve(const spsvm_options* o) {
   r.solver = (o && o->newton_solver == SPSVM_SOLVE_FP64) ? SPSVM_SOLVE_FP64 : SPSVM_SOLVE_MIXED;
   r.score = (o && o->score == SPSVM_SCORE_EXACT) ? SPSVM_SCORE_EXACT : SPSVM_SCORE_HEURISTIC;
   r.bias = (o && o->bias) ? 1 : 0;
+  r.lowrank = (o && o->lowrank) ? 1 : 0;
   return r;
 }
 
 constexpr int32_t kJitterMaxLevel = 8;   // largest jitter 1e-2 tr(H)/|J|
+// kinds of the Newton-system factor in hand
+enum { FAC_MIXED = 0, FAC_LOWRANK = 1, FAC_FP64 = 2 };
 // Newton stop once the gradient is small (||grad|| <= rel_tol ||r||): the
 // next Newton step is below this fraction of ||beta|| (and is not taken)
 constexpr double kStepTol = 1e-5;
@@ -348,6 +368,9 @@ struct Fit {
   int32_t m = 0;              // current |J|
   int32_t act_cur = 0;        // which active buffer holds the current flags
   int32_t jitter = -1;        // jitter level that factorised the last Newton matrix
+  int64_t anchor_m = -1;      // |J| of the unshifted FP32 factor in hand (its active set
+                              // in the anchor flags), or -1
+  int32_t lr_k = 0;           // rank of the low-rank correction in hand
 
   template <typename T>
   T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
@@ -428,18 +451,27 @@ struct Fit {
     int32_t status = SPSVM_ERR_NO_CONVERGE;
     double* tmp2 = at<double>(L.off_tmp2);
     void* mixw = ws + L.off_mix;
+    void* lrw = ws + L.off_lr;
+    float* Wt = at<float>(L.off_Wt);
+    float* sgn = at<float>(L.off_sign);
+    int32_t* kdev = reinterpret_cast<int32_t*>(small + 184);
+    uint8_t* anchor = at<uint8_t>(L.off_anchor);
     // (H + shift I)^{-1} b with the factor in hand: the FP32 one with FP64
-    // refinement (H kept), or the FP64 one in H
-    auto solve_with = [&](bool use_mixed, double sh, const double* b, double* x, double btol) -> int {
-      if (use_mixed)
+    // refinement (H kept), the same plus the low-rank correction for the
+    // points that changed since it was formed, or the FP64 one in H
+    auto solve_with = [&](int kind, double sh, const double* b, double* x, double btol) -> int {
+      if (kind == FAC_MIXED)
         return spsvm_solve_mixed(H, m, ldH, sh, b, x, kMixedIters, btol, nullptr, nullptr, mixw,
                                  L.mix_bytes, s);
+      if (kind == FAC_LOWRANK)
+        return spsvm_solve_lowrank(H, m, ldH, b, x, kMixedIters, btol, nullptr, nullptr, mixw,
+                                   L.mix_bytes, lrw, L.lr_bytes, lr_k, s);
       if (x != b) SPSVM_CUDA_TRY(cudaMemcpyAsync(x, b, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
       return spsvm_cholesky_solve(H, m, ldH, x, ws + L.off_sv, L.sv_bytes, s);
     };
     // u = K_nJ d, then the optional refinement sweeps against the exactly
     // applied H (two more passes over K each)
-    auto finish_direction = [&](const uint8_t* act, bool use_mixed, double sh) -> int {
+    auto finish_direction = [&](const uint8_t* act, int kind, double sh) -> int {
       SPSVM_TRY(spsvm_gemv(&K, dir, u, 0, s));
       for (int k = 0; k < op.refine; ++k) {
         SPSVM_TRY(spsvm_compact_active(&K, act, u, nullptr, wsum, nullptr, nullptr, n_active,
@@ -447,7 +479,7 @@ struct Fit {
         refine_resid<<<mb, tpb, 0, s>>>(g, u, Jd, wsum, m, lambda, tmp);
         SPSVM_LAUNCH_CHECK();
         // a correction of ~1e-5 relative size: 1e-6 backward error suffices
-        const int rc = solve_with(use_mixed, sh, tmp, tmp2, 1e-6);
+        const int rc = solve_with(kind, sh, tmp, tmp2, 1e-6);
         if (rc != SPSVM_OK && rc != SPSVM_ERR_NO_CONVERGE) return rc;
         axpy_d<<<mb, tpb, 0, s>>>(dir, tmp2, 1.0, m);
         SPSVM_LAUNCH_CHECK();
@@ -456,7 +488,8 @@ struct Fit {
       return SPSVM_OK;
     };
     // the factor in hand (valid while the active set does not change)
-    bool reuse = false, fac_mixed = false;
+    bool reuse = false;
+    int fac_kind = FAC_MIXED;
     double fac_shift = 0.0;
     // ||d|| <= kStepTol ||beta|| for the direction just solved
     auto step_small = [&](bool* small) -> int {
@@ -505,7 +538,8 @@ struct Fit {
       // where H is at rounding level, which the objective hardly sees
       const bool gsmall_jit = gnorm <= std::max(op.rel_tol, kJitterRelTol) * rnorm;
       auto converged = [&]() {
-        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
+        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter, 0,
+                       SPSVM_NEWTON_NONE};
         model->history.push_back(rec);
         status = SPSVM_OK;
       };
@@ -525,28 +559,73 @@ struct Fit {
       // level never goes down within a fit.
       double t = 0.0;
       bool stepped = false;
+      bool h_fresh = false;   // H holds the unfactorised, unshifted matrix
+      int how = SPSVM_NEWTON_FACTOR;
+      // A direction from the factor in hand (kind, shift), then u = K_nJ d
+      // and the line search; false when the solve does not reach FP64
+      // backward error or the line search finds no descent (the caller then
+      // factors afresh).
+      bool searched = false;   // try_direction ran the line search
+      auto try_direction = [&](int kind, double sh, bool* ok) -> int {
+        *ok = false;
+        searched = false;
+        const int rc = solve_with(kind, sh, rhs, dir, kMixedTol);
+        if (rc == SPSVM_ERR_NO_CONVERGE) return SPSVM_OK;
+        SPSVM_TRY(rc);
+        if (gsmall) SPSVM_TRY(step_small(&done));
+        if (done) return SPSVM_OK;
+        SPSVM_TRY(finish_direction(act, kind, sh));
+        SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
+        searched = true;
+        *ok = t > 0.0;
+        return SPSVM_OK;
+      };
       if (reuse) {
-        // the active set has not changed since the factor in hand was formed,
-        // so H has not either: only the right-hand side is new
-        const int rc = solve_with(fac_mixed, fac_shift, rhs, dir, kMixedTol);
-        if (rc == SPSVM_OK) {
-          if (gsmall) SPSVM_TRY(step_small(&done));
-          if (done) {
-            converged();
-            break;
+        // the active set has not changed since the factor in hand (and its
+        // low-rank correction) was formed, so H has not either: only the
+        // right-hand side is new
+        SPSVM_TRY(try_direction(fac_kind, fac_shift, &stepped));
+        how = SPSVM_NEWTON_REUSE;
+        if (!stepped && searched && gsmall && !done) {   // no descent at rounding level
+          converged();
+          break;
+        }
+      } else if (op.lowrank && anchor_m == m && jitter < 0 && m >= kLowRankMinBasis) {
+        // the active set moved by k points since the unshifted FP32 factor in
+        // hand was formed: correct that factor by the rank-k term instead of
+        // factoring afresh (H itself is rebuilt for the refinement residuals)
+        const int32_t kmax = (int32_t)std::min<int64_t>(kLowRankMax, m / 8);
+        SPSVM_TRY(spsvm_active_diff(&K, act, anchor, kmax, Wt, SPSVM_LOWRANK_KMAX, sgn, kdev, scratch,
+                                    sb, s));
+        int32_t kk = 0;
+        SPSVM_CUDA_TRY(cudaMemcpyAsync(&kk, kdev, sizeof(kk), cudaMemcpyDeviceToHost, s));
+        SPSVM_TRY(sync());
+        if (kk >= 1 && kk <= kmax) {
+          SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s,
+                              st[2], at<double>(L.off_kjj), L.jcap));
+          h_fresh = true;
+          int32_t* lr_info = reinterpret_cast<int32_t*>(small + 188);
+          SPSVM_TRY(spsvm_lowrank_factor(mixw, L.mix_bytes, m, Wt, SPSVM_LOWRANK_KMAX, sgn, kk, lrw,
+                                         L.lr_bytes, lr_info, s));
+          int32_t li = 1;
+          SPSVM_CUDA_TRY(cudaMemcpyAsync(&li, lr_info, sizeof(li), cudaMemcpyDeviceToHost, s));
+          SPSVM_TRY(sync());
+          if (li == 0) {
+            lr_k = kk;
+            SPSVM_TRY(try_direction(FAC_LOWRANK, 0.0, &stepped));
+            if (stepped || done) {
+              fac_kind = FAC_LOWRANK;
+              fac_shift = 0.0;
+              how = SPSVM_NEWTON_LOWRANK;
+            }
           }
-          SPSVM_TRY(finish_direction(act, fac_mixed, fac_shift));
-          SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
-          stepped = t > 0.0;
-          if (!stepped && gsmall) {   // no descent at rounding level
-            converged();
-            break;
-          }
-        } else if (rc != SPSVM_ERR_NO_CONVERGE) {
-          return rc;
         }
       }
-      bool h_fresh = false;   // H holds the unfactorised, unshifted matrix
+      if (done) {
+        converged();
+        break;
+      }
+      if (!stepped) how = SPSVM_NEWTON_FACTOR;
       bool mixed = false;     // the factor in use is the FP32 one (H kept intact)
       double tr = -1.0, shift = 0.0;
       for (; !stepped;) {
@@ -574,11 +653,17 @@ struct Fit {
             SPSVM_TRY(spsvm_cholesky_mixed(H, m, ldH, shift, info, mixw, L.mix_bytes, s));
             SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
             SPSVM_TRY(sync());
+            // the factor in the mixed work is now that of this matrix: an
+            // anchor for low-rank corrections when unshifted
+            anchor_m = (op.lowrank && info_h == 0 && shift == 0.0 && m >= kLowRankMinBasis) ? m : -1;
+            if (anchor_m == m)
+              SPSVM_CUDA_TRY(cudaMemcpyAsync(anchor, act, n, cudaMemcpyDeviceToDevice, s));
             if (info_h == 0) {
               const int rc = spsvm_solve_mixed(H, m, ldH, shift, rhs, dir, kMixedIters, kMixedTol,
                                                nullptr, nullptr, mixw, L.mix_bytes, s);
               if (rc == SPSVM_OK) mixed = true;
               else if (rc != SPSVM_ERR_NO_CONVERGE) return rc;
+              else anchor_m = -1;   // this factor does not refine to FP64 accuracy
             }
           }
           if (mixed) {
@@ -601,12 +686,12 @@ struct Fit {
             break;
           }
         }
-        fac_mixed = mixed;
+        fac_kind = mixed ? FAC_MIXED : FAC_FP64;
         fac_shift = shift;
         if (gsmall) SPSVM_TRY(step_small(&done));
         if (done) break;
         // d = -(H + shift I)^{-1} g (computed above), u = K_nJ d
-        SPSVM_TRY(finish_direction(act, mixed, shift));
+        SPSVM_TRY(finish_direction(act, fac_kind, shift));
         t = 0.0;
         SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
         // with a small gradient, no descent means rounding level: no jitter
@@ -620,7 +705,8 @@ struct Fit {
       if (!(t > 0.0)) {
         // no descent even at the largest jitter (or with a small gradient):
         // rounding level reached
-        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter};
+        spsvm_step rec{m, (int32_t)st[2], gnorm, 0.0, st[0], (int32_t)st[1], jitter, 0,
+                       SPSVM_NEWTON_NONE};
         model->history.push_back(rec);
         if (gsmall) status = SPSVM_OK;
         break;
@@ -639,7 +725,7 @@ struct Fit {
       unsigned long long nd = 0;
       SPSVM_CUDA_TRY(cudaMemcpyAsync(&nd, ndiff, sizeof(nd), cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
-      spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], jitter};
+      spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], jitter, (int32_t)nd, how};
       model->history.push_back(rec);
       act_cur = nxt;
       std::memcpy(st, st2, sizeof(st));
@@ -816,7 +902,8 @@ extern "C" size_t spsvm_fit_workspace_bytes(int64_t n, int64_t d, int32_t basis_
                                             const spsvm_options* opt) {
   if (n < 1 || d < 1 || basis_budget < 1) return 0;
   const Opts op = resolve(opt);
-  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias).total;
+  return make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias,
+                     op.lowrank).total;
 }
 
 extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
@@ -851,7 +938,8 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     if ((int32_t)J0.size() > basis_budget) basis_budget = (int32_t)J0.size();
   }
   if (op.fixed && J0.empty()) return set_error(SPSVM_ERR_ARG, "fit: fixed_basis needs an initial basis");
-  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias);
+  Layout L = make_layout(n, d, basis_budget, op.precision, op.kappa, op.q, op.solver, op.score, op.bias,
+                     op.lowrank);
   bool own = false;
   if (!workspace) {
     cudaError_t e = cudaMalloc(&workspace, L.total);

@@ -162,13 +162,20 @@ __global__ void sum_triples(const double* __restrict__ part, int64_t blocks, dou
 constexpr int SC_T = 256;
 constexpr int SC_PTS = SC_T * 4;
 
-__global__ void scan_count(const uint8_t* __restrict__ active, int64_t n, int32_t* __restrict__ counts) {
+// The scanned flag of point i: active[i], or with ref, active[i] != ref[i].
+__device__ __forceinline__ int scan_flag(const uint8_t* __restrict__ active,
+                                         const uint8_t* __restrict__ ref, int64_t i) {
+  return ref ? (active[i] != ref[i]) : active[i];
+}
+
+__global__ void scan_count(const uint8_t* __restrict__ active, const uint8_t* __restrict__ ref,
+                           int64_t n, int32_t* __restrict__ counts) {
   __shared__ int sh[32];
   const int64_t base = (int64_t)blockIdx.x * SC_PTS;
   int c = 0;
   for (int p = 0; p < 4; ++p) {
     const int64_t i = base + threadIdx.x + (int64_t)SC_T * p;
-    if (i < n) c += active[i];
+    if (i < n) c += scan_flag(active, ref, i);
   }
   c = block_sum(c, sh);
   if (threadIdx.x == 0) counts[blockIdx.x] = c;
@@ -200,14 +207,14 @@ __global__ void scan_blocks(int32_t* __restrict__ counts, int64_t nb, int64_t* _
   if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
-                           const int32_t* __restrict__ offsets, int32_t* __restrict__ pos,
+__global__ void scan_write(const uint8_t* __restrict__ active, const uint8_t* __restrict__ ref,
+                           int64_t n, const int32_t* __restrict__ offsets, int32_t* __restrict__ pos,
                            int32_t* __restrict__ list) {
   __shared__ int32_t sh[SC_PTS];
   const int64_t base = (int64_t)blockIdx.x * SC_PTS;
   for (int p = 0; p < 4; ++p) {
     const int64_t i = base + threadIdx.x * 4 + p;
-    sh[threadIdx.x * 4 + p] = (i < n) ? active[i] : 0;
+    sh[threadIdx.x * 4 + p] = (i < n) ? scan_flag(active, ref, i) : 0;
   }
   __syncthreads();
   // sequential scan per thread over its 4, then block scan of thread sums
@@ -226,8 +233,8 @@ __global__ void scan_write(const uint8_t* __restrict__ active, int64_t n,
   for (int p = 0; p < 4; ++p) {
     const int64_t i = base + threadIdx.x * 4 + p;
     if (i < n) {
-      pos[i] = excl + local[p];
-      if (sh[threadIdx.x * 4 + p]) list[excl + local[p]] = (int32_t)i;   // active indices, in order
+      if (pos) pos[i] = excl + local[p];
+      if (sh[threadIdx.x * 4 + p]) list[excl + local[p]] = (int32_t)i;   // flagged indices, in order
     }
   }
 }
@@ -408,6 +415,26 @@ __global__ void zero_tail(void* kc_data, int32_t format, int64_t rows, int64_t k
   }
 }
 
+// Wt[j][r] = K[j][list[r]] for the k = *k_dev listed points (nothing when
+// k > kmax); sign[r] = +1 when list[r] is active, else -1.  Blocks stride
+// over the basis rows, threads over the points.
+__global__ void diff_gather(KView K, int64_t rows, const int32_t* __restrict__ list,
+                            const int32_t* __restrict__ k_dev, int32_t kmax,
+                            const uint8_t* __restrict__ active, float* __restrict__ Wt,
+                            int64_t ldw, float* __restrict__ sign) {
+  const int32_t k = *k_dev;
+  if (k > kmax) return;
+  if (blockIdx.x == 0)
+    for (int r = threadIdx.x; r < k; r += blockDim.x) sign[r] = active[list[r]] ? 1.0f : -1.0f;
+  for (int64_t j = blockIdx.x; j < rows; j += gridDim.x)
+    for (int r = threadIdx.x; r < k; r += blockDim.x) Wt[j * ldw + r] = K.at(j, list[r]);
+}
+
+// *k_dev = (int32) *total
+__global__ void store_count(const int64_t* __restrict__ total, int32_t* __restrict__ k_dev) {
+  *k_dev = (int32_t)*total;
+}
+
 }  // namespace
 }  // namespace spsvm
 
@@ -513,11 +540,11 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
   if (n == 0) {
     SPSVM_CUDA_TRY(cudaMemsetAsync(n_active, 0, sizeof(int64_t), s));
   } else {
-    scan_count<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts);
+    scan_count<<<(unsigned)sb, SC_T, 0, s>>>(active, nullptr, n, counts);
     SPSVM_LAUNCH_CHECK();
     scan_blocks<<<1, 1024, 0, s>>>(counts, sb, n_active);
     SPSVM_LAUNCH_CHECK();
-    scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, n, counts, pos, list);
+    scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, nullptr, n, counts, pos, list);
     SPSVM_LAUNCH_CHECK();
   }
   if (K->rows > 0 && n > 0) {
@@ -550,6 +577,43 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
     const int64_t kc_n = round_up(n, 128) <= Kc->n ? round_up(n, 128) : Kc->n;
     zero_tail<<<4 * sm_count(), 256, 0, s>>>(Kc->data, Kc->format, K->rows, Kc->ld, Kc->plane,
                                              kc_n, n_active);
+    SPSVM_LAUNCH_CHECK();
+  }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_active_diff(const spsvm_kmat* K, const uint8_t* active, const uint8_t* ref,
+                                 int32_t kmax, float* Wt, int64_t ldw, float* sign, int32_t* k_dev,
+                                 void* scratch, size_t scratch_bytes, void* stream) {
+  SPSVM_TRY(check_kmat(K, "active_diff"));
+  if (!active || !ref || !k_dev || kmax < 0 || (kmax > 0 && (!Wt || !sign || ldw < kmax)))
+    return set_error(SPSVM_ERR_ARG, "active_diff: bad arguments");
+  if (!scratch || scratch_bytes < spsvm_compact_scratch_bytes(K->n, 0))
+    return set_error(SPSVM_ERR_OOM, "active_diff: scratch too small");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = K->n;
+  if (n == 0) {
+    SPSVM_CUDA_TRY(cudaMemsetAsync(k_dev, 0, sizeof(int32_t), s));
+    return SPSVM_OK;
+  }
+  const int64_t sb = ceil_div(n, SC_PTS);
+  int32_t* counts = static_cast<int32_t*>(scratch);
+  // the compaction's scratch: counts, partial sums (one slot for no rows), list
+  int64_t* total = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + round_up(sb * 4, 256));
+  const int64_t ysplit_max = ceil_div(n, CP_T) < 1024 ? ceil_div(n, CP_T) : 1024;
+  int32_t* list = reinterpret_cast<int32_t*>(
+      static_cast<char*>(scratch) + round_up(sb * 4, 256) + round_up(ysplit_max * 16, 256));
+  scan_count<<<(unsigned)sb, SC_T, 0, s>>>(active, ref, n, counts);
+  SPSVM_LAUNCH_CHECK();
+  scan_blocks<<<1, 1024, 0, s>>>(counts, sb, total);
+  SPSVM_LAUNCH_CHECK();
+  scan_write<<<(unsigned)sb, SC_T, 0, s>>>(active, ref, n, counts, nullptr, list);
+  SPSVM_LAUNCH_CHECK();
+  store_count<<<1, 1, 0, s>>>(total, k_dev);
+  SPSVM_LAUNCH_CHECK();
+  if (kmax > 0 && K->rows > 0) {
+    diff_gather<<<(unsigned)min64(K->rows, 4 * (int64_t)sm_count()), 128, 0, s>>>(
+        view(K), K->rows, list, k_dev, kmax, active, Wt, ldw, sign);
     SPSVM_LAUNCH_CHECK();
   }
   return SPSVM_OK;

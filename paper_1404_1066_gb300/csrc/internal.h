@@ -127,7 +127,7 @@ __device__ __forceinline__ T block_sum(T v, T* sh /* >= 32 entries */) {
 // Kernel timing slots (CUDA events on the launching stream, when enabled).
 enum ProfSlot {
   PROF_KERNEL_BLOCK = 0, PROF_SCORE, PROF_OUTPUTS, PROF_GEMV, PROF_COMPACT, PROF_GRAM,
-  PROF_CHOLESKY, PROF_SOLVE, PROF_LINE, PROF_DECISION, PROF_FIT, PROF_SLOTS
+  PROF_CHOLESKY, PROF_SOLVE, PROF_LINE, PROF_DECISION, PROF_FIT, PROF_LOWRANK, PROF_SLOTS
 };
 struct ProfScope {
   int slot;
