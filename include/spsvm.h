@@ -183,7 +183,9 @@ int spsvm_score_candidates_exact(const spsvm_points* p, const float* y, const fl
  * spsvm_score_scratch_bytes(n, d, kappa) <= 16 MiB (e.g. n = 500,000,
  * d = 128, kappa = 256); larger sizes are rejected with SPSVM_ERR_ARG
  * before any work.  The first call on each device (made current) looks up the array's
- * device address; make that first call before any stream capture.  Calls
+ * device address (and so does the first call after the device's context was
+ * made anew, e.g. after cudaDeviceReset); make that first call before any
+ * stream capture.  Calls
  * share the array: calls whose work overlaps on the GPU (different streams
  * or devices' threads racing on one device) race on it, so serialise them.
  * Every call overwrites the partial sums it reads, so nothing needs
@@ -598,15 +600,26 @@ int spsvm_profile_enable(int32_t on);
 int spsvm_profile_read(int32_t slot, const char** name, int64_t* launches, double* ms,
                        double* work);
 
-/* Status words of the kernels that wait on the device (tensor-core kernel
- * block, score and Gram; the Cholesky update; the triangular solves).
- * Every such wait is bounded; a wait that gives up records a nonzero site
- * code and the kernel returns without its result.  Waits for the legacy
- * default stream, then reads and clears the words; returns OK, or TIMEOUT
- * with *code set (site codes of the Cholesky update are offset by 100,
- * those of the triangular solves by 200).  The fits check them
- * themselves, in order on their own stream. */
+/* Status of the kernels that wait on the device (tensor-core kernel block,
+ * score and Gram; the FP64 Cholesky update; the FP32 tile factorisation; the
+ * triangular solves; the low-rank tile solve).  Every such wait is bounded;
+ * a wait that gives up records a nonzero site code in the status word of
+ * the stream its kernel runs on (one word per stream: work on other
+ * streams never sees it), and the kernel returns without its result.
+ * spsvm_stream_status waits for `stream`, then reads and clears its word;
+ * returns OK, or TIMEOUT with *code set (site codes: 11-27 tensor-core
+ * kernels, 101-102 the FP64 Cholesky update, 221-231 the factorisation and
+ * solves).  spsvm_device_status is the same for the legacy default stream
+ * (work enqueued with stream NULL).  The fits check their own stream.  The
+ * library tracks up to 1024 streams; past that the least recently used
+ * stream's word is reused. */
+int spsvm_stream_status(void* stream, int32_t* code);
 int spsvm_device_status(int32_t* code);
+/* Poll limit of every bounded device wait launched from now on (0, the
+ * default, restores each wait's own limit, about a second).  A small limit
+ * makes waits give up early, for testing the timeout path: results of the
+ * affected kernels are then incomplete and the status reports TIMEOUT. */
+void spsvm_set_wait_limit(uint32_t polls);
 
 const char* spsvm_strerror(int code);
 const char* spsvm_last_error(void);

@@ -9,14 +9,6 @@
 
 namespace spsvm {
 
-// Status word of the triangular solves' bounded waits (site codes 21, 22).
-__device__ int g_sv_status = 0;
-
-int sv_status_address(void** p) {
-  SPSVM_CUDA_TRY(cudaGetSymbolAddress(p, g_sv_status));
-  return SPSVM_OK;
-}
-
 namespace {
 
 constexpr int NB = 64;   // diagonal blocks of the triangular solve
@@ -302,14 +294,16 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One thread waits for a flag to leave 0, giving up after roughly a second.
-__device__ unsigned wait_flag(const unsigned* f, int code) {
-  for (uint32_t it = 0; it < (1u << 23); ++it) {
+// One thread waits for a flag to leave 0, giving up after the wait limit
+// (by default 2^23 polls, roughly a second) with the stream's status set.
+__device__ unsigned wait_flag(const unsigned* f, int code, const WaitCtx& w) {
+  const uint32_t lim = wait_limit(w, 1u << 23);
+  for (uint32_t it = 0; it < lim; ++it) {
     const unsigned v = ld_acquire_u32(f);
     if (v != 0u) return v;
     if (it >= 16) __nanosleep(64);
   }
-  atomicCAS(&g_sv_status, 0, code);
+  wait_gave_up(w, code);
   return 2u;
 }
 
@@ -335,7 +329,7 @@ __device__ __forceinline__ void load_diag_inverse(const T* __restrict__ L, int64
 template <typename T>
 __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
     const T* __restrict__ L, int64_t ldh, int64_t m, const T* __restrict__ b,
-    T* __restrict__ z, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
+    T* __restrict__ z, unsigned* __restrict__ flags, unsigned* __restrict__ ticket, WaitCtx wc) {
   __shared__ T Li[NB][NB + 1];
   __shared__ T xs[2][NB];
   __shared__ T v[NB];
@@ -356,7 +350,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
     T a[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) a[c] = row_ok ? __ldg(Lrow + j * NB + c) : 0.0;
-    if (t == 0) state_s = wait_flag(&flags[j], 21);
+    if (t == 0) state_s = wait_flag(&flags[j], 221, wc);
     __syncthreads();
     if (state_s != 1u) {
       ok = false;
@@ -392,7 +386,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_fwd_onepass(
 template <typename T>
 __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
     const T* __restrict__ L, int64_t ldh, int64_t m, const T* __restrict__ z,
-    T* __restrict__ x, unsigned* __restrict__ flags, unsigned* __restrict__ ticket) {
+    T* __restrict__ x, unsigned* __restrict__ flags, unsigned* __restrict__ ticket, WaitCtx wc) {
   __shared__ T Li[NB][NB + 1];
   __shared__ T xs[2][NB];
   __shared__ T part[4][NB];
@@ -415,7 +409,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr)
       a[rr] = (c < nb && rb + rr < m) ? __ldg(L + (rb + rr) * ldh + r0 + c) : 0.0;
-    if (t == 0) state_s = wait_flag(&flags[j], 22);
+    if (t == 0) state_s = wait_flag(&flags[j], 222, wc);
     __syncthreads();
     if (state_s != 1u) {
       ok = false;
@@ -472,7 +466,9 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 // Returns the number staged, or -1 when a block is abandoned or the wait
 // runs out.
 __device__ int grab_blocks(const unsigned long long* __restrict__ wt, int64_t m, int64_t first,
-                           int step, int want, unsigned tag, float (*xs)[NB], int code) {
+                           int step, int want, unsigned tag, float (*xs)[NB], int code,
+                           const WaitCtx& w) {
+  const uint32_t lim = wait_limit(w, 1u << 20);
   const int lane = threadIdx.x & 31;
   const unsigned abt = tag | 0x80000000u;
   for (uint32_t it = 0;; ++it) {
@@ -502,8 +498,8 @@ __device__ int grab_blocks(const unsigned long long* __restrict__ wt, int64_t m,
     }
     if (ab) return -1;
     if (got > 0) return got;
-    if (it >= (1u << 20)) {
-      if (lane == 0) atomicCAS(&g_sv_status, 0, code);
+    if (it >= lim) {
+      if (lane == 0) wait_gave_up(w, code);
       return -1;
     }
     if (it >= 8) __nanosleep(32);
@@ -516,7 +512,8 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
                                                         int64_t m, const float* __restrict__ b,
                                                         unsigned long long* __restrict__ zt,
                                                         float* __restrict__ z,
-                                                        unsigned* __restrict__ ticket, unsigned tag) {
+                                                        unsigned* __restrict__ ticket, unsigned tag,
+                                                        WaitCtx wc) {
   __shared__ float Li[NB][NB + 1];
   __shared__ float xs[SV_BATCH][NB];
   __shared__ float v[NB];
@@ -539,7 +536,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
 #pragma unroll
     for (int c = 0; c < 16; ++c) a[c] = row_ok ? __ldg(Lrow + j * NB + c) : 0.0f;
     if (t < 32) {
-      const int g = grab_blocks(zt, m, j, 1, (int)min64(SV_BATCH, k - j), tag, xs, 21);
+      const int g = grab_blocks(zt, m, j, 1, (int)min64(SV_BATCH, k - j), tag, xs, 221, wc);
       if (t == 0) n_s = g;
     }
     __syncthreads();
@@ -580,7 +577,8 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
                                                         int64_t m, const float* __restrict__ z,
                                                         unsigned long long* __restrict__ xt,
                                                         float* __restrict__ x,
-                                                        unsigned* __restrict__ ticket, unsigned tag) {
+                                                        unsigned* __restrict__ ticket, unsigned tag,
+                                                        WaitCtx wc) {
   __shared__ float Li[NB][NB + 1];
   __shared__ float xs[SV_BATCH][NB];
   __shared__ float part[4][NB];
@@ -606,7 +604,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
     for (int rr = 0; rr < 16; ++rr)
       a[rr] = (col_ok && rb + rr < m) ? __ldg(L + (rb + rr) * ldh + r0 + c) : 0.0f;
     if (t < 32) {
-      const int gb = grab_blocks(xt, m, j, -1, (int)min64(SV_BATCH, j - k), tag, xs, 22);
+      const int gb = grab_blocks(xt, m, j, -1, (int)min64(SV_BATCH, j - k), tag, xs, 222, wc);
       if (t == 0) n_s = gb;
     }
     __syncthreads();
@@ -776,9 +774,10 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
 // fence for the flags seen done; -1 if that first flag is abandoned.  Waits,
 // bounded, while the flag at k0 itself is not done.
 __device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __restrict__ fj,
-                            int64_t k0, int64_t j, int code) {
+                            int64_t k0, int64_t j, int code, const WaitCtx& w) {
   const int lane = threadIdx.x & 31;
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+  const uint32_t lim = wait_limit(w, 1u << 22);
+  for (uint32_t it = 0; it < lim; ++it) {
     int64_t r = j;
     for (int64_t base = k0; base < j; base += 32) {
       const int64_t k = base + lane;
@@ -801,14 +800,14 @@ __device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __r
     }
     if (it >= 16) __nanosleep(64);
   }
-  if (lane == 0) atomicCAS(&g_sv_status, 0, code);
+  if (lane == 0) wait_gave_up(w, code);
   return -1;
 }
 
 __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
                                                       int64_t T, unsigned* __restrict__ flags,
                                                       unsigned* __restrict__ ticket,
-                                                      int32_t* __restrict__ info) {
+                                                      int32_t* __restrict__ info, WaitCtx wc) {
   extern __shared__ __align__(16) float dag_smem[];
   float (*As)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem);
   float (*Bs)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem + 2 * DT * DP);
@@ -859,7 +858,7 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
       const unsigned* fi = flags + i * T;
       const unsigned* fj = flags + j * T;
       if (t < 32) {
-        const int64_t r = dag_scan(fi, fj, 0, j, 23);
+        const int64_t r = dag_scan(fi, fj, 0, j, 223, wc);
         if (t == 0) rdy_s = r;
       }
       __syncthreads();
@@ -883,7 +882,7 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
         dag_update(acc, As[sb], diag ? As[sb] : Bs[sb]);
         if (k + 1 < j && !pre) {
           if (t < 32) {
-            const int64_t r = dag_scan(fi, fj, k + 1, j, 23);
+            const int64_t r = dag_scan(fi, fj, k + 1, j, 223, wc);
             if (t == 0) rdy_s = r;
           }
           __syncthreads();
@@ -984,7 +983,7 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
         }
       }
     } else if (ok) {
-      if (t == 0) st_s = wait_flag(&flags[j * T + j], 24);
+      if (t == 0) st_s = wait_flag(&flags[j * T + j], 224, wc);
       __syncthreads();
       if (st_s != 1u) {
         ok = false;
@@ -1207,7 +1206,7 @@ __global__ void __launch_bounds__(LR_T) lr_trsm_fwd(const float* __restrict__ L,
                                                    int64_t ldw_in, int32_t k,
                                                    float* __restrict__ V, int64_t ldv, int32_t G,
                                                    unsigned* __restrict__ flags,
-                                                   unsigned* __restrict__ ticket) {
+                                                   unsigned* __restrict__ ticket, WaitCtx wc) {
   __shared__ float Li[NB][NB + 1];
   __shared__ float Ls[NB][NB + 1];
   __shared__ float Vs[NB][LR_G];
@@ -1228,7 +1227,7 @@ __global__ void __launch_bounds__(LR_T) lr_trsm_fwd(const float* __restrict__ L,
   load_diag_inverse(L, ldl, r0, nb, Li);
   for (int64_t j = 0; j < i && ok; ++j) {
     // (the previous pass's reads of Ls / Vs end at this barrier)
-    if (t == 0) st_s = wait_flag(&flags[j * G + g], 31);
+    if (t == 0) st_s = wait_flag(&flags[j * G + g], 231, wc);
     __syncthreads();
     if (st_s != 1u) {
       ok = false;
@@ -1636,9 +1635,12 @@ extern "C" int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, dou
   double* z = static_cast<double*>(work);
   unsigned* flags = reinterpret_cast<unsigned*>(static_cast<char*>(work) + solve_flags_offset(m));
   SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(2 * B + 2) * 4, s));
-  trsv_fwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, b, z, flags, flags + 2 * B);
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
+  trsv_fwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, b, z, flags, flags + 2 * B, wc);
   SPSVM_LAUNCH_CHECK();
-  trsv_bwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, z, b, flags + B, flags + 2 * B + 1);
+  trsv_bwd_onepass<double><<<(unsigned)B, SV_THREADS, 0, s>>>(L, ldh, m, z, b, flags + B, flags + 2 * B + 1,
+                                                              wc);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -1707,8 +1709,10 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   SPSVM_LAUNCH_CHECK();
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(chol32_dag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DAG_SMEM));
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
   chol32_dag<<<(unsigned)min64(ntiles, (int64_t)sm_count()), DAG_T, DAG_SMEM, s>>>(
-      L, ly.ldl, m, T, dflags, dflags + T * T, info);
+      L, ly.ldl, m, T, dflags, dflags + T * T, info, wc);
   SPSVM_LAUNCH_CHECK();
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
   SPSVM_LAUNCH_CHECK();
@@ -1782,6 +1786,8 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
   const unsigned vb = (unsigned)ly.nvec_blocks, rb = (unsigned)ly.nrow_blocks;
   const bool vec = (ldh % 2) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
   SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
   SPSVM_CUDA_TRY(cudaMemsetAsync(tagged_region, 0, tagged_bytes, s));
   SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
@@ -1802,7 +1808,7 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
     if (it > 0 && it % kTicketSteps == 0)
       SPSVM_CUDA_TRY(cudaMemsetAsync(tickets, 0, (size_t)2 * kTicketSteps * 4, s));
     unsigned* tk = tickets + 2 * (it % kTicketSteps);
-    trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag);
+    trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag, wc);
     SPSVM_LAUNCH_CHECK();
     if (lr) {   // z <- (I - V C^{-1} V^T) z
       lr_dots<<<dim3((unsigned)lr->G, (unsigned)lr->slices), 256, 0, s>>>(lr->V, lr->ldv, m, zw,
@@ -1812,7 +1818,7 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
           lr->V, lr->ldv, m, lr->Ci, lr->ldv, lr->s, lr->slices, lr->ldv, lr->k, zw);
       SPSVM_LAUNCH_CHECK();
     }
-    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag);
+    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag, wc);
     SPSVM_LAUNCH_CHECK();
     add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
     SPSVM_LAUNCH_CHECK();
@@ -1873,8 +1879,10 @@ extern "C" int spsvm_lowrank_factor(void* mixed_work, size_t mixed_bytes, int64_
   const int64_t B = ceil_div(m, (int64_t)NB);
   SPSVM_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   SPSVM_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)(B * ly.G + 1) * 4, s));
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
   lr_trsm_fwd<<<(unsigned)(B * ly.G), LR_T, 0, s>>>(L, ml.ldl, m, Wt, ldw, k, V, ly.ldv, (int32_t)ly.G,
-                                                    flags, flags + B * ly.G);
+                                                    flags, flags + B * ly.G, wc);
   SPSVM_LAUNCH_CHECK();
   double* cpart = reinterpret_cast<double*>(w + ly.cpart);
   lr_capacitance<<<dim3((unsigned)ly.G, (unsigned)ly.G, (unsigned)ly.slices), 256, 0, s>>>(

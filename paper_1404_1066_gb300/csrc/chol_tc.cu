@@ -33,7 +33,6 @@ constexpr int OZ_BAR_OFF = OZ_B_OFF + OZ_SLICES * OZ_B_SLICE;
 constexpr int OZ_EXP_OFF = OZ_BAR_OFF + 64;
 constexpr int OZ_SMEM = OZ_EXP_OFF + OZ_TN * 4 + 1024;
 
-__device__ int g_oz_status = 0;
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   const uint32_t a = smem_u32(p);
@@ -93,14 +92,15 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
                                                       double* __restrict__ H, int64_t ldh,
                                                       int64_t m, int64_t cbase, int64_t cend,
                                                       const int32_t* __restrict__ ex,
-                                                      const int32_t* __restrict__ info) {
+                                                      const int32_t* __restrict__ info,
+                                                      WaitCtx wc) {
   extern __shared__ uint8_t smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ti = blockIdx.y, tj = blockIdx.x;
   const int64_t r0 = cbase + ti * OZ_TM, c0 = cbase + tj * OZ_TN;
   // only tiles touching the lower triangle
   if (c0 > r0 + OZ_TM - 1) return;
-  if (__syncthreads_or(tid == 0 && (*(volatile int*)&g_oz_status != 0 || *info != 0))) return;
+  if (__syncthreads_or(tid == 0 && (*(volatile int*)wc.st != 0 || *info != 0))) return;
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_BAR_OFF);
   uint64_t* done = full + 1;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
       tma_load_3d(smem + s * OZ_A_SLICE, &map_a, 0, (int)r0, s, full);
       tma_load_3d(smem + OZ_B_OFF + s * OZ_B_SLICE, &map_b, 0, (int)c0, s, full);
     }
-    ok = mbar_wait(full, 0, &g_oz_status, 1);
+    ok = mbar_wait(full, 0, wc.st, 101, wc.lim);
     if (ok) {
       fence_after_sync();
       constexpr uint32_t IDESC = idesc_bf16_f32(OZ_TM, OZ_TN);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128, 1) oz_trailing(const __grid_constant__ CU
     mma_commit(done);
   }
   ok = __syncthreads_and(ok);
-  const bool got = __syncthreads_and(mbar_wait(done, 0, &g_oz_status, 2)) && ok;
+  const bool got = __syncthreads_and(mbar_wait(done, 0, wc.st, 102, wc.lim)) && ok;
   fence_after_sync();
   if (got) {
     const int64_t r = r0 + 32 * warp + lane;
@@ -317,15 +317,12 @@ int chol_tc_update(double* H, int64_t ldh, int64_t m, int64_t cbase, int64_t cen
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(oz_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       OZ_SMEM));
   dim3 grid((unsigned)ceil_div(cend - cbase, (int64_t)OZ_TN), (unsigned)ceil_div(R, (int64_t)OZ_TM));
-  oz_trailing<<<grid, 128, OZ_SMEM, s>>>(ma, mb, H, ldh, m, cbase, cend, ex, info);
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
+  oz_trailing<<<grid, 128, OZ_SMEM, s>>>(ma, mb, H, ldh, m, cbase, cend, ex, info, wc);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
 
-// Device address of the status word (symbols are per translation unit).
-int oz_status_address(void** p) {
-  SPSVM_CUDA_TRY(cudaGetSymbolAddress(p, g_oz_status));
-  return SPSVM_OK;
-}
 
 }  // namespace spsvm

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -76,6 +77,71 @@ __global__ void prepare_points_kernel(const float* __restrict__ X, int64_t n, in
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- status words of the bounded device waits, one per stream --------------
+namespace {
+constexpr int kStatusSlots = 1024;
+__device__ int g_wait_status[kStatusSlots];
+std::atomic<uint32_t> g_wait_limit{0};
+std::mutex g_slot_mu;
+struct SlotUse {
+  int slot;
+  uint64_t last;
+};
+std::unordered_map<cudaStream_t, SlotUse> g_slot_of;
+uint64_t g_slot_clock = 0;
+}  // namespace
+
+// The stream's slot is assigned on its first use (zeroed in order on the
+// stream) and kept; with every slot taken, the least recently used stream's
+// slot is handed over.  The table's device address is looked up on each call
+// (no cached address survives a context reset).
+int wait_ctx(cudaStream_t s, WaitCtx* w) {
+  void* base = nullptr;
+  SPSVM_CUDA_TRY(cudaGetSymbolAddress(&base, g_wait_status));
+  int slot = -1;
+  bool fresh = false;
+  {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    ++g_slot_clock;
+    auto it = g_slot_of.find(s);
+    if (it != g_slot_of.end()) {
+      it->second.last = g_slot_clock;
+      slot = it->second.slot;
+    } else {
+      if ((int)g_slot_of.size() < kStatusSlots) {
+        slot = (int)g_slot_of.size();
+      } else {
+        auto lru = g_slot_of.begin();
+        for (auto jt = g_slot_of.begin(); jt != g_slot_of.end(); ++jt)
+          if (jt->second.last < lru->second.last) lru = jt;
+        slot = lru->second.slot;
+        g_slot_of.erase(lru);
+      }
+      g_slot_of[s] = SlotUse{slot, g_slot_clock};
+      fresh = true;
+    }
+  }
+  w->st = static_cast<int*>(base) + slot;
+  w->lim = g_wait_limit.load(std::memory_order_relaxed);
+  if (fresh) SPSVM_CUDA_TRY(cudaMemsetAsync(w->st, 0, sizeof(int), s));
+  return SPSVM_OK;
+}
+
+int device_status_on(cudaStream_t s, int32_t* code) {
+  WaitCtx w;
+  SPSVM_TRY(wait_ctx(s, &w));
+  int v = 0;
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v, w.st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (v != 0) {
+    SPSVM_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(int), s));
+    SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  if (code) *code = v;
+  if (v != 0) return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", v);
+  return SPSVM_OK;
+}
 
 // ---- kernel timing -----------------------------------------------------
 namespace {
@@ -215,4 +281,17 @@ extern "C" int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* st
       precision == SPSVM_BF16X4 ? reinterpret_cast<__nv_bfloat16*>(p->lo) : nullptr, p->ldh);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
+}
+
+extern "C" int spsvm_stream_status(void* stream, int32_t* code) {
+  if (code) *code = 0;
+  const int rc = spsvm::device_status_on(as_stream(stream), code);
+  if (rc == SPSVM_ERR_CUDA && code) *code = -1;
+  return rc;
+}
+
+extern "C" int spsvm_device_status(int32_t* code) { return spsvm_stream_status(nullptr, code); }
+
+extern "C" void spsvm_set_wait_limit(uint32_t polls) {
+  spsvm::g_wait_limit.store(polls, std::memory_order_relaxed);
 }

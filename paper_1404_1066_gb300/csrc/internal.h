@@ -147,8 +147,26 @@ int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m,
 size_t kernel_block_tc_scratch(int64_t m, int64_t ldh);
 bool tc_available();
 
-// Synchronises s and takes the status words of the bounded device waits
-// (stream-ordered copies; returns TIMEOUT with *code set when one gave up).
+// Bounded device waits.  Every kernel that waits on the device gets the
+// wait context of the stream it runs on: the stream's status word (the site
+// code of the first wait that gave up, 0 while none did; a word of its own
+// per stream, so that concurrent fits never see each other's codes) and the
+// iteration limit of each wait (0: the site's default, about a second;
+// spsvm_set_wait_limit sets it).
+struct WaitCtx {
+  int* st;
+  uint32_t lim;
+};
+// The wait context for launches on stream s.
+int wait_ctx(cudaStream_t s, WaitCtx* w);
+__device__ __forceinline__ uint32_t wait_limit(const WaitCtx& w, uint32_t dflt) {
+  return w.lim ? w.lim : dflt;
+}
+// Records a wait that gave up (the first code on the stream is kept).
+__device__ __forceinline__ void wait_gave_up(const WaitCtx& w, int code) { atomicCAS(w.st, 0, code); }
+
+// Synchronises s and takes (reads and clears) the status word of stream s
+// (stream-ordered copies; returns TIMEOUT with *code set when a wait gave up).
 int device_status_on(cudaStream_t s, int32_t* code);
 
 // spsvm_line_search with Eq. 4's bias in basis slot 0 (point index -1):

@@ -284,6 +284,8 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
 // moment it must not.  For them the score's per-tile partial sums live in a
 // fixed array in this library's device memory instead of caller scratch.
 // ---------------------------------------------------------------------------
+#include <cuda.h>
+
 #include <mutex>
 
 namespace spsvm {
@@ -293,7 +295,26 @@ constexpr size_t kScoreScratchMax = size_t(16) << 20;
 // Held by every GPU that loads this library until the process exits.
 __device__ __align__(256) unsigned char g_score_scratch[kScoreScratchMax];
 std::mutex g_score_scratch_mu;
+// the array's device address per device, with the context it was looked up
+// in (a context torn down and made again, e.g. by cudaDeviceReset, may load
+// the module at another address: the set-up then runs again)
 void* g_score_scratch_ptr[64] = {};
+CUcontext g_score_scratch_ctx[64] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static const CtxGetCurrentFn fn = []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<CtxGetCurrentFn>(f);
+    cudaGetLastError();
+    return (CtxGetCurrentFn) nullptr;
+  }();
+  return fn;
+}
 }  // namespace
 }  // namespace spsvm
 
@@ -314,15 +335,20 @@ extern "C" int spsvm_score_candidates_noalloc(const spsvm_points* p, const float
   if (dev < 0 || dev >= 64) return set_error(SPSVM_ERR_ARG, "score_candidates_noalloc: device %d", dev);
   void* ptr = nullptr;
   {
-    // first call on this device (current): look up the array's device address
+    // set-up on the first call on this device (current), and again when the
+    // device's context is not the one of the last set-up: look up the
+    // array's device address
+    CUcontext ctx = nullptr;
+    if (auto fn = ctx_get_current()) fn(&ctx);
     std::lock_guard<std::mutex> lk(g_score_scratch_mu);
-    if (!g_score_scratch_ptr[dev]) {
+    if (!g_score_scratch_ptr[dev] || g_score_scratch_ctx[dev] != ctx) {
       void* a = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&a, g_score_scratch);
       if (e != cudaSuccess || !a)
         return set_error(SPSVM_ERR_CUDA, "score_candidates_noalloc: cudaGetSymbolAddress: %s",
                          cudaGetErrorString(e));
       g_score_scratch_ptr[dev] = a;
+      g_score_scratch_ctx[dev] = ctx;
     }
     ptr = g_score_scratch_ptr[dev];
   }

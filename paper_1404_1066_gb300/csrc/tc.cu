@@ -28,8 +28,6 @@ namespace {
 
 using namespace tc;
 
-__device__ int g_tc_status = 0;
-
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   const uint32_t a = smem_u32(p);
   return p + ((1024u - (a & 1023u)) & 1023u);
@@ -106,7 +104,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     const __grid_constant__ CUtensorMap map_ohi, const __grid_constant__ CUtensorMap map_olo,
     int64_t ldh, int64_t n, int32_t m, const float* __restrict__ norms,
     const int64_t* __restrict__ idx, float gamma, int64_t row0, const float* __restrict__ y,
-    const float* __restrict__ o, double2* __restrict__ part, int32_t kappa) {
+    const float* __restrict__ o, double2* __restrict__ part, int32_t kappa, WaitCtx wc) {
   constexpr bool SCORE = MODE == KB_SCORE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -120,7 +118,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
   float2* red = reinterpret_cast<float2*>(smem + PK_RED_OFF);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (__syncthreads_or(tid == 0 && *(volatile int*)&g_tc_status != 0)) return;
+  if (__syncthreads_or(tid == 0 && *(volatile int*)wc.st != 0)) return;
   const int64_t nCB = ceil_div((int64_t)m, (int64_t)PK_M);
   const int64_t nPT = ceil_div(n, (int64_t)PK_N);
   const int64_t T = nCB * nPT;
@@ -168,7 +166,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
         for (int kc = 0; kc < nK; ++kc, ++q) {
           const int s = (int)(q % PK_STAGES);
           const uint32_t ph = (uint32_t)((q / PK_STAGES) & 1);
-          if (!mbar_wait(&empty[s], ph ^ 1u, &g_tc_status, 21)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, wc.st, 21, wc.lim)) {
             ok = false;
             break;
           }
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       }
       // no copy may be in flight when the block exits
       for (int64_t r = (q > PK_STAGES ? q - PK_STAGES : 0); r < q; ++r)
-        mbar_wait(&full[r % PK_STAGES], (uint32_t)((r / PK_STAGES) & 1), &g_tc_status, 22);
+        mbar_wait(&full[r % PK_STAGES], (uint32_t)((r / PK_STAGES) & 1), wc.st, 22, wc.lim);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -191,13 +189,13 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       bool ok = true;
       for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x, ++j) {
         const int acc = (int)(j & 1);
-        if (!mbar_wait(&tempty[acc], (uint32_t)(((j >> 1) & 1) ^ 1), &g_tc_status, 23)) break;
+        if (!mbar_wait(&tempty[acc], (uint32_t)(((j >> 1) & 1) ^ 1), wc.st, 23, wc.lim)) break;
         fence_after_sync();
         const uint32_t d = tmem + acc * PK_N;
         for (int kc = 0; kc < nK; ++kc, ++q) {
           const int s = (int)(q % PK_STAGES);
           const uint32_t ph = (uint32_t)((q / PK_STAGES) & 1);
-          if (!mbar_wait(&full[s], ph, &g_tc_status, 24)) {
+          if (!mbar_wait(&full[s], ph, wc.st, 24, wc.lim)) {
             ok = false;
             break;
           }
@@ -258,7 +256,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       }
       __syncwarp();
       const int acc = (int)(j & 1);
-      if (!mbar_wait(&tfull[acc], (uint32_t)((j >> 1) & 1), &g_tc_status, 25)) break;
+      if (!mbar_wait(&tfull[acc], (uint32_t)((j >> 1) & 1), wc.st, 25, wc.lim)) break;
       fence_after_sync();
       float gs = 0.f, hs = 0.f;
       const uint32_t tb = tmem + acc * PK_N + half * 64 + ((uint32_t)(32 * quarter) << 16);
@@ -344,11 +342,11 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
         // the two warps of a lane quarter combine their halves of the tile
         const uint32_t par = (uint32_t)(j & 1);
         if (half == 1) {
-          if (!mbar_wait(&rede[quarter], par ^ 1u, &g_tc_status, 26)) break;
+          if (!mbar_wait(&rede[quarter], par ^ 1u, wc.st, 26, wc.lim)) break;
           red[quarter * 32 + lane] = make_float2(gs, hs);
           mbar_arrive(&redf[quarter]);
         } else {
-          if (!mbar_wait(&redf[quarter], par, &g_tc_status, 27)) break;
+          if (!mbar_wait(&redf[quarter], par, wc.st, 27, wc.lim)) break;
           const float2 r2 = red[quarter * 32 + lane];
           mbar_arrive(&rede[quarter]);
           if (crow)
@@ -406,7 +404,7 @@ constexpr int64_t GR_CHUNKS_PER_SLICE = GRAM_SLICE / 64;
 __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
     const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
     int64_t m, const int64_t* __restrict__ ns_dev, int64_t slices_per_split,
-    double* __restrict__ part, int64_t ldp) {
+    double* __restrict__ part, int64_t ldp, WaitCtx wc) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + GR_BAR_OFF);
@@ -416,7 +414,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (__syncthreads_or(tid == 0 && *(volatile int*)&g_tc_status != 0)) return;
+  if (__syncthreads_or(tid == 0 && *(volatile int*)wc.st != 0)) return;
   // upper-triangular tile (ta <= tb)
   const int64_t T = ceil_div(m, (int64_t)GR_TILE);
   int64_t rem = blockIdx.x, ta = 0;
@@ -460,7 +458,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
     for (int64_t q = 0; q < nch; ++q) {
       const int s = (int)(q % GR_STAGES);
       const uint32_t ph = (uint32_t)((q / GR_STAGES) & 1);
-      if (!mbar_wait(&empty[s], ph ^ 1u, &g_tc_status, 11)) break;
+      if (!mbar_wait(&empty[s], ph ^ 1u, wc.st, 11, wc.lim)) break;
       uint8_t* st = smem + s * GR_STAGE;
       const int x = (int)((c_begin + q) * 64);
       mbar_expect_tx(&full[s], GR_STAGE);
@@ -472,14 +470,14 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
     }
     // wait for the copies of the last stages so none is in flight at exit
     for (int64_t q = (issued > GR_STAGES ? issued - GR_STAGES : 0); q < issued; ++q)
-      mbar_wait(&full[q % GR_STAGES], (uint32_t)((q / GR_STAGES) & 1), &g_tc_status, 12);
+      mbar_wait(&full[q % GR_STAGES], (uint32_t)((q / GR_STAGES) & 1), wc.st, 12, wc.lim);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     bool ok = true;
     for (int64_t t = 0; t < nslices && ok; ++t) {
       const int acc = (int)(t & 1);
       const uint32_t use = (uint32_t)((t >> 1) & 1);
-      if (!mbar_wait(&acce[acc], use ^ 1u, &g_tc_status, 13)) break;
+      if (!mbar_wait(&acce[acc], use ^ 1u, wc.st, 13, wc.lim)) break;
       fence_after_sync();
       const uint32_t d = tmem + acc * GR_TILE;
       const int64_t q0 = t * GR_CHUNKS_PER_SLICE;
@@ -487,7 +485,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
       for (int64_t q = q0; q < q1; ++q) {
         const int s = (int)(q % GR_STAGES);
         const uint32_t ph = (uint32_t)((q / GR_STAGES) & 1);
-        if (!mbar_wait(&full[s], ph, &g_tc_status, 14)) {
+        if (!mbar_wait(&full[s], ph, wc.st, 14, wc.lim)) {
           ok = false;
           break;
         }
@@ -521,7 +519,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) gram_tc_kernel(
     for (int64_t t = 0; t < nslices; ++t) {
       const int acc = (int)(t & 1);
       const uint32_t use = (uint32_t)((t >> 1) & 1);
-      if (!mbar_wait(&accf[acc], use, &g_tc_status, 15)) break;
+      if (!mbar_wait(&accf[acc], use, wc.st, 15, wc.lim)) break;
       fence_after_sync();
       const uint32_t tbase = tmem + acc * GR_TILE + ((uint32_t)(32 * quarter) << 16);
       for (int cc = 0; cc < GR_TILE / 32; ++cc) {
@@ -622,8 +620,10 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
   const int64_t tiles = ceil_div((int64_t)m, (int64_t)PK_M) * ceil_div(p->n, (int64_t)PK_N);
   const int grid = (int)min64(tiles, (int64_t)sm_count());
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
   kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzl, mxh, mxl, moh, mol, p->ldh, p->n, m, p->norms,
-                                         idx, gamma, row0, y, o, part, kappa);
+                                         idx, gamma, row0, y, o, part, kappa, wc);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -682,68 +682,12 @@ int launch_gram_tc(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, 
   const int64_t slices = ceil_div(ns_max > 0 ? ns_max : 1, GRAM_SLICE);
   const int64_t per = ceil_div(slices, splits);
   dim3 grid((unsigned)tiles, (unsigned)splits);
-  gram_tc_kernel<<<grid, GR_THREADS, GR_SMEM, s>>>(mh, ml, m, ns_dev, per, part, ldp);
+  WaitCtx wc;
+  SPSVM_TRY(wait_ctx(s, &wc));
+  gram_tc_kernel<<<grid, GR_THREADS, GR_SMEM, s>>>(mh, ml, m, ns_dev, per, part, ldp, wc);
   SPSVM_LAUNCH_CHECK();
-  return SPSVM_OK;
-}
-
-int oz_status_address(void** p);
-int sv_status_address(void** p);
-
-// Device addresses of the status words of the bounded waits (kernel block /
-// score / Gram, Cholesky update, triangular solves), looked up once per
-// device.
-constexpr int kStatusWords = 3;
-
-static int status_addresses(void* out[kStatusWords]) {
-  constexpr int kMaxDev = 64;
-  static std::mutex mu;
-  static void* addr[kMaxDev][kStatusWords] = {};
-  int dev = 0;
-  SPSVM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDev) return set_error(SPSVM_ERR_CUDA, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev][0]) {
-    void* a[kStatusWords] = {};
-    SPSVM_CUDA_TRY(cudaGetSymbolAddress(&a[0], g_tc_status));
-    SPSVM_TRY(oz_status_address(&a[1]));
-    SPSVM_TRY(sv_status_address(&a[2]));
-    for (int k = 0; k < kStatusWords; ++k) addr[dev][k] = a[k];
-  }
-  for (int k = 0; k < kStatusWords; ++k) out[k] = addr[dev][k];
-  return SPSVM_OK;
-}
-
-// Synchronises stream s and takes (reads and clears) the status words, in
-// order on s: no legacy-stream copy, so concurrent fits on other streams are
-// not serialised by it.  code: 0, or the site of the first wait that gave up
-// (Cholesky update sites + 100, triangular-solve sites + 200).
-int device_status_on(cudaStream_t s, int32_t* code) {
-  void* a[kStatusWords];
-  SPSVM_TRY(status_addresses(a));
-  int v[kStatusWords] = {};
-  for (int k = 0; k < kStatusWords; ++k)
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(&v[k], a[k], sizeof(int), cudaMemcpyDeviceToHost, s));
-  SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
-  int c = 0;
-  bool any = false;
-  for (int k = 0; k < kStatusWords; ++k) {
-    if (v[k] == 0) continue;
-    SPSVM_CUDA_TRY(cudaMemsetAsync(a[k], 0, sizeof(int), s));
-    if (!any) c = 100 * k + v[k];
-    any = true;
-  }
-  if (any) SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (code) *code = c;
-  if (c != 0) return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", c);
   return SPSVM_OK;
 }
 
 }  // namespace spsvm
 
-extern "C" int spsvm_device_status(int32_t* code) {
-  if (code) *code = 0;
-  const int rc = spsvm::device_status_on(cudaStreamLegacy, code);
-  if (rc == SPSVM_ERR_CUDA && code) *code = -1;
-  return rc;
-}

@@ -40,10 +40,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the phase of `bar` with the given parity to complete, giving up
-// after roughly a second; on give-up records `code` in *status and returns
-// false.  No wait in these kernels is unbounded.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
-  for (uint32_t it = 0; it < (1u << 23); ++it) {
+// after `limit` polls (0: 2^23, roughly a second); on give-up records `code`
+// in *status (unless a code is there already) and returns false.  No wait in
+// these kernels is unbounded.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code,
+                                          uint32_t limit) {
+  const uint32_t lim = limit ? limit : (1u << 23);
+  for (uint32_t it = 0; it < lim; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it >= 32) __nanosleep(128);
   }
