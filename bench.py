@@ -99,6 +99,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class UtilSampler:
+    """nvidia-smi utilization.gpu (percent of time a kernel ran) every 100 ms."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"spsvm_util_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=utilization.gpu",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        v = []
+        for line in open(self.path):
+            try:
+                v.append(float(line.strip()))
+            except ValueError:
+                pass
+        return {"mean": statistics.mean(v) if v else None, "samples": len(v)}
+
+
 def max_over_ranks(x, ws, device="cuda"):
     """Largest value of x over the ranks (the slowest replica's time)."""
     if ws <= 1:
@@ -117,28 +153,70 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline_run(seconds_budget=20.0, steps=1):
-    """The float64 oracle, as it stands, on a bounded sample of the workload:
-    n = 4,000 rows of the same mixture, d = 128, |J| = 256 (4 rounds of 64
-    from 256 candidates).  Returns per-step sample seconds, the factor that
-    scales a sample fit to the full workload, and the BLAS thread count."""
-    from oracle import spsvm as O
-    from paper_1404_1066_gb300 import synth
-    p = synth.gaussian_mixture(n=4000, d=128, budget=256, seed=1003)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        O.fit(p.X, p.y, p.gamma, p.lam, 256, tol=1e-6, kappa=256, q=64, seed=1)
-        times.append(time.perf_counter() - t0)
+def _cpu_facts():
+    """Host cores the oracle ran on (nproc, the BLAS thread count) and the CPU model."""
     try:
         from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+        blas = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
     except Exception:
-        cores = os.cpu_count() or 1
-    # cost model of a fit: rounds ~ |J|, each Newton step ~ n |J|^2
-    factor = (500_000 / 4000) * (4096 / 256) ** 3
-    return times, factor, cores, "oracle fit on n=4,000 rows of the same mixture, d=128, |J|=256; " \
-        f"scaled by (n ratio) x (|J| ratio)^3 = {factor:.3g} to the full workload"
+        blas = None
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return dict(nproc=os.cpu_count(), blas_threads=blas, cpu_model=model)
+
+
+# Bounded samples of the workload for the oracle: (n, |J|) with d = 128 and
+# the same mixture, kappa = 256, q = 64.  The first is the timed sample; the
+# other two vary n and |J| alone, which fixes the exponents of the fit time
+# t ~ n^a |J|^b used to extrapolate (labelled an estimate).
+CPU_SAMPLES = ((4000, 256), (8000, 256), (4000, 512))
+
+
+def _oracle_fit_seconds(n, J):
+    from oracle import spsvm as O
+    from paper_1404_1066_gb300 import synth
+    p = synth.gaussian_mixture(n=n, d=128, budget=J, seed=1003)
+    t0 = time.perf_counter()
+    O.fit(p.X, p.y, p.gamma, p.lam, J, tol=1e-6, kappa=256, q=64, seed=1)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_run(steps=1, scaling=True):
+    """The float64 oracle, as it stands, timed on the host cores: `steps`
+    fits of the first sample (n = 4,000 rows of the same mixture, d = 128,
+    |J| = 256), and, with `scaling`, one fit each of the other two samples,
+    from which the exponents a, b of t ~ n^a |J|^b and an extrapolated
+    full-size fit time (an estimate, not a measurement) follow."""
+    n0, J0 = CPU_SAMPLES[0]
+    times = [_oracle_fit_seconds(n0, J0) for _ in range(steps)]
+    out = dict(sample=f"oracle fit on n={n0:,} rows of the same mixture, d=128, |J|={J0} "
+                      f"(kappa=256, q=64)", sample_seconds=times, **_cpu_facts())
+    if scaling:
+        t0 = statistics.median(times)
+        tn = _oracle_fit_seconds(*CPU_SAMPLES[1])
+        tj = _oracle_fit_seconds(*CPU_SAMPLES[2])
+        a = math.log(tn / t0) / math.log(CPU_SAMPLES[1][0] / n0)
+        b = math.log(tj / t0) / math.log(CPU_SAMPLES[2][1] / J0)
+        est = t0 * (500_000 / n0) ** a * (4096 / J0) ** b
+        out.update(points=[dict(n=n, basis=J, seconds=t) for (n, J), t in
+                           zip(CPU_SAMPLES, (t0, tn, tj))],
+                   exponent_n=a, exponent_basis=b, full_size_estimate_s=est)
+    return out
 
 
 def batched_leg(sp, torch, workers=8, precision="bf16x4"):
@@ -151,15 +229,19 @@ def batched_leg(sp, torch, workers=8, precision="bf16x4"):
                   lam=s.lam, budget=s.budget, tol=1e-6, seed=10_000 + s.solve_id) for s in solves]
     Xd = torch.from_numpy(X).cuda()
     torch.cuda.synchronize()
+    util = UtilSampler(torch.cuda.current_device())
+    util.start()
     t0 = time.perf_counter()
     models, st = sp.spsvm_fit_batched(Xd, probs, workers=workers, precision=precision,
                                       candidates=256, add_per_round=64)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    busy = util.stop()
     ok = sum(1 for v in st if v in (0, -4))
     return dict(solves=len(probs), ok=ok, seconds=el, solves_per_s=len(probs) / el,
                 workers=workers, rows_mean=float(np.mean([len(p["rows"]) for p in probs])),
-                basis_mean=float(np.mean([p["budget"] for p in probs])))
+                basis_mean=float(np.mean([p["budget"] for p in probs])),
+                gpu_busy_pct_mean=busy.get("mean"), gpu_busy_samples=busy.get("samples"))
 
 
 def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x4"):
@@ -361,19 +443,24 @@ def run_micro(args):
 
 
 def run_reference(args):
+    """The float64 oracle, as it stands, on the host cores: each step one fit
+    of the bounded sample (n = 4,000, |J| = 256 of the same mixture); the
+    line's value is that measured time per step."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_baseline_run(steps=1)
-    times, factor, cores, sample = cpu_baseline_run(steps=args.steps)
-    per = statistics.mean(times) * factor
+        _oracle_fit_seconds(*CPU_SAMPLES[0])
+    cb = cpu_baseline_run(steps=args.steps, scaling=False)
+    per = statistics.mean(cb["sample_seconds"])
     line = dict(metric=METRIC, value=per, unit="s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(WORKLOAD, l2="inputs larger than L2"), impl="reference",
-                cpu_baseline=dict(value=per, unit="s", cores=cores, kind="oracle", sample=sample,
-                                  sample_seconds=times),
+                config=dict(WORKLOAD, l2="inputs larger than L2", sample=cb["sample"]),
+                impl="reference",
+                cpu_baseline=dict(value=per, unit="s", cores=cb["nproc"], kind="oracle",
+                                  sample=cb["sample"], sample_seconds=cb["sample_seconds"],
+                                  blas_threads=cb["blas_threads"], cpu_model=cb["cpu_model"]),
                 e2e=dict(value=per, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -558,7 +645,10 @@ def run_ours(args):
     pr = prof[dom]
     per_launch_ms = pr["ms"] / max(1, pr["launches"])
     per_launch_work = pr["work"] / max(1, pr["launches"])
-    fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x 2 flops x max clock (80.5)
+    # FP32 SIMT rate from the unit counts: SMs x 128 FP32 lanes x 2 flops x
+    # the maximum SM clock (sampled; 2,070 MHz when unsampled)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_simt = sms * 128 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
     note = None
     if dom in ("gram", "kernel_block", "score", "decision") and prec == "bf16x4":
         # the library counts the four plane products in the work of the form
@@ -613,9 +703,13 @@ def run_ours(args):
                 fp32_form=fp32_form, lowrank=lowrank, growth_stop=growth, batched=batched, ovo=ovo,
                 exact_score=exact, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        times, factor, cores, sample = cpu_baseline_run(steps=1)
-        line["cpu_baseline"] = dict(value=times[0] * factor, unit="s", cores=cores, kind="oracle",
-                                    sample=sample, sample_seconds=times[0])
+        cb = cpu_baseline_run(steps=1)
+        line["cpu_baseline"] = dict(value=cb["sample_seconds"][0], unit="s", cores=cb["nproc"],
+                                    kind="oracle", sample=cb["sample"],
+                                    blas_threads=cb["blas_threads"], cpu_model=cb["cpu_model"],
+                                    points=cb["points"], exponent_n=cb["exponent_n"],
+                                    exponent_basis=cb["exponent_basis"],
+                                    full_size_estimate_s=cb["full_size_estimate_s"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -634,7 +728,8 @@ def main():
     ap.add_argument("--d", type=int, default=128)
     ap.add_argument("--basis", type=int, default=4096)
     ap.add_argument("--queries", type=int, default=100_000)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (0: the same count as the device-timed steps)")
     ap.add_argument("--fp32-form", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
@@ -652,6 +747,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.e2e_steps <= 0:
+        args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
     if args.micro:

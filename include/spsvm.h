@@ -476,6 +476,8 @@ int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t
 int spsvm_model_info(const spsvm_model* model, int32_t* n_basis, int64_t* d,
                      float* gamma, double* lambda, double* objective,
                      int32_t* newton_steps, int32_t* rounds, int32_t* status);
+/* Device bytes the model holds (its basis rows, beta, prediction scratch). */
+size_t spsvm_model_device_bytes(const spsvm_model* model);
 /* Eq. 4's bias b of the model (0 unless fitted with spsvm_options.bias). */
 int spsvm_model_bias(const spsvm_model* model, double* b);
 
@@ -556,15 +558,21 @@ int spsvm_predict_ovo(const spsvm_model* const* models, int32_t classes, const f
                       int64_t nq, int64_t ldq, int32_t* labels, int32_t* votes, void* work,
                       size_t work_bytes, void* stream);
 
-/* Request loop.  Requests carry host data (copied at submission).  Each has
- * an HBM footprint (fit: X, y, the fit workspace and the model; predict: the
- * queries and results); a request is admitted, in arrival order, when a
- * worker is free and the footprints of the requests running plus its own fit
- * in the budget; later requests that fit run ahead of one that does not
- * (continuous batching), unless it has waited more than two seconds.  A
- * predict request is admitted once its fit request has finished.  Workers
- * own one CUDA stream each, so admitted requests overlap on the device.
- * The server allocates device memory per request and frees it when done. */
+/* Request loop.  Requests carry host data (copied at submission).  The
+ * HBM budget counts the device bytes the server holds: every worker's
+ * buffers (the fit's X, y and workspace; the predict's queries and results),
+ * which a worker keeps and grows across requests, so that the loop
+ * allocates no transient buffers and frees none; and every fitted model,
+ * from the start of its fit until spsvm_server_release (or destroy).  A
+ * request is admitted, in arrival order, when a worker is free and the bytes
+ * that worker must add to run it (its buffers grown to the request's needs,
+ * plus the model of a fit) fit in what is left of the budget; later
+ * requests that fit run ahead of one that does not (continuous batching),
+ * unless it has waited more than two seconds, when idle workers give their
+ * buffers back until it fits.  A predict request is admitted once its fit
+ * request has finished.  Workers own one CUDA stream each, so admitted
+ * requests overlap on the device.  A request whose own needs exceed the
+ * budget is refused at submission (SPSVM_ERR_OOM). */
 typedef struct spsvm_server spsvm_server;
 int spsvm_server_create(size_t hbm_budget_bytes, int32_t workers, spsvm_server** out);
 int spsvm_server_submit_fit(spsvm_server* s, const float* X, int64_t n, int64_t d,
@@ -580,6 +588,11 @@ int spsvm_server_wait(spsvm_server* s, int64_t request_id, double timeout_s, int
  * predict, or the model of a fit (owned by the server until destroy). */
 int spsvm_server_result(spsvm_server* s, int64_t request_id, float* decision, int64_t cap,
                         spsvm_model** model);
+/* Frees the model of a finished fit request (predicts of it can no longer
+ * be submitted; BUSY while some are pending) and returns its bytes to the
+ * budget. */
+int spsvm_server_release(spsvm_server* s, int64_t fit_request_id);
+/* hbm_in_use / hbm_peak: the budget's current and largest count (bytes). */
 int spsvm_server_stats(spsvm_server* s, int64_t* done, int64_t* queued, size_t* hbm_in_use,
                        size_t* hbm_peak);
 void spsvm_server_destroy(spsvm_server* s);

@@ -154,6 +154,8 @@ SIGNATURES = {
     "spsvm_server_stats": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_SZ),
                                   C.POINTER(_SZ)]),
     "spsvm_server_destroy": (None, [_P]),
+    "spsvm_server_release": (_I32, [_P, _I64]),
+    "spsvm_model_device_bytes": (_SZ, [_P]),
     "spsvm_launch_count": (C.c_uint64, []),
     "spsvm_profile_enable": (_I32, [_I32]),
     "spsvm_profile_read": (_I32, [_I32, C.POINTER(C.c_char_p), C.POINTER(_I64), C.POINTER(_D),

@@ -476,6 +476,9 @@ class Model:
                                        ch.ctypes.data, C.byref(nch)), "spsvm_model_round")
         return cand[:nc.value], ch[:nch.value]
 
+    def device_bytes(self):
+        return int(_lib().spsvm_model_device_bytes(self.handle))
+
     def outputs(self, n):
         o = np.empty(n, dtype=np.float32)
         check(_lib().spsvm_model_outputs(self.handle, o.ctypes.data, int(n)), "spsvm_model_outputs")
@@ -658,6 +661,9 @@ class Server:
         check(_lib().spsvm_server_result(self.h, int(rid), None, 0, C.byref(m)),
               "spsvm_server_result")
         return _Borrowed(m.value, 0) if m.value else None
+
+    def release(self, fit_id):
+        check(_lib().spsvm_server_release(self.h, int(fit_id)), "spsvm_server_release")
 
     def stats(self):
         a, b = C.c_int64(), C.c_int64()

@@ -1010,6 +1010,13 @@ extern "C" int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t 
   return SPSVM_OK;
 }
 
+extern "C" size_t spsvm_model_device_bytes(const spsvm_model* m) {
+  if (!m) return 0;
+  const size_t mr = m->J.size();
+  return (m->basis_dev ? mr * (size_t)m->d * 4 : 0) + (m->beta_dev ? mr * 8 : 0) +
+         (m->scratch_dev ? m->scratch_bytes : 0);
+}
+
 extern "C" int spsvm_model_bias(const spsvm_model* m, double* b) {
   if (!m || !b) return set_error(SPSVM_ERR_ARG, "model_bias: NULL argument");
   *b = m->bias;

@@ -6,10 +6,12 @@
 //    worker threads, each with its own CUDA stream and workspace, largest
 //    problem first.  A problem's result does not depend on which worker ran
 //    it or what ran beside it (each fit's reductions have a fixed order).
-//  * spsvm_server: requests (fit, predict) admitted first-come by their HBM
-//    footprint against a budget; a request that does not fit waits while later
-//    ones that do fit run (continuous batching), and a request that has
-//    waited longer than two seconds blocks later ones until it is admitted.
+//  * spsvm_server: requests (fit, predict) admitted first-come against an
+//    HBM budget that counts what the server holds (its workers' buffers, kept
+//    and grown across requests, and the resident models); a request that does
+//    not fit waits while later ones that do fit run (continuous batching),
+//    and a request that has waited longer than two seconds blocks later ones
+//    until it is admitted (idle workers then give their buffers back).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -44,11 +46,17 @@ double now_ms() {
 struct DeviceBuf {
   void* p = nullptr;
   size_t bytes = 0;
-  int ensure(size_t want) {
-    if (want <= bytes) return SPSVM_OK;
+  DeviceBuf() = default;
+  DeviceBuf(const DeviceBuf&) = delete;
+  DeviceBuf& operator=(const DeviceBuf&) = delete;
+  void reset() {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+  }
+  int ensure(size_t want) {
+    if (want <= bytes) return SPSVM_OK;
+    reset();
     if (want == 0) return SPSVM_OK;
     if (cudaMalloc(&p, want) != cudaSuccess) {
       cudaGetLastError();
@@ -185,13 +193,18 @@ struct SpsvmRequest {
   std::vector<float> Xq, out;
   int64_t nq = 0;
   // bookkeeping
-  size_t footprint = 0;
+  size_t footprint = 0;     // device bytes the request needs (checked against the budget)
+  size_t model_bytes = 0;   // device bytes of the fitted model while resident
   double t_submit = 0, t_start = 0, t_end = 0;
   int state = 0;   // 0 queued, 1 running, 2 done
   int32_t status = SPSVM_OK;
 };
 
 struct spsvm_server {
+  // in_use: device bytes the server holds -- every worker's buffers (kept
+  // across requests, grown on demand) and every resident model (until
+  // spsvm_server_release or destroy), plus the model reserve of a fit that
+  // is running
   size_t budget = 0, in_use = 0, peak = 0;
   int device = 0;
   std::mutex mu;
@@ -206,10 +219,44 @@ struct spsvm_server {
 
 namespace {
 
-// First admissible request in FIFO order (lock held).  A request waiting
-// longer than two seconds reserves admission for itself.
-std::shared_ptr<SpsvmRequest> take_admissible(spsvm_server* S) {
+// A worker's device buffers, kept across requests (grown, never shrunk
+// while requests keep fitting the budget).
+struct WorkerBufs {
+  DeviceBuf X, y, ws, Q, out;
+  size_t held() const { return X.bytes + y.bytes + ws.bytes + Q.bytes + out.bytes; }
+  void release() {
+    X.reset();
+    y.reset();
+    ws.reset();
+    Q.reset();
+    out.reset();
+  }
+};
+
+// Device bytes a fit's model holds at most (basis rows, beta, decision scratch).
+size_t model_reserve(const SpsvmRequest& r) {
+  return (size_t)r.budget * r.d * 4 + (size_t)r.budget * 8 +
+         spsvm_decision_scratch_bytes(0, r.budget, r.d);
+}
+
+size_t grow_of(const DeviceBuf& b, size_t want) { return want > b.bytes ? want - b.bytes : 0; }
+
+// Device bytes the worker must add to run r (its buffers grown to r's needs,
+// plus the model reserve of a fit).
+size_t extra_for(const SpsvmRequest& r, const WorkerBufs& W) {
+  if (r.kind == 0)
+    return grow_of(W.X, r.X.size() * 4) + grow_of(W.y, r.y.size() * 4) +
+           grow_of(W.ws, spsvm_fit_workspace_bytes(r.n, r.d, r.budget, &r.opt)) + model_reserve(r);
+  return grow_of(W.Q, r.Xq.size() * 4) + grow_of(W.out, (size_t)r.nq * 4);
+}
+
+// First admissible request in FIFO order for this worker (lock held): its
+// extra bytes fit the budget; the bytes are reserved.  A request waiting
+// longer than two seconds blocks later ones; *aged is set when that head
+// does not fit, and the caller then gives its own buffers back.
+std::shared_ptr<SpsvmRequest> take_admissible(spsvm_server* S, const WorkerBufs& W, bool* aged) {
   const double t = now_ms();
+  *aged = false;
   for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
     auto r = S->reqs[*it];
     bool ready = true;
@@ -217,47 +264,48 @@ std::shared_ptr<SpsvmRequest> take_admissible(spsvm_server* S) {
       auto f = S->reqs.find(r->fit_id);
       ready = (f != S->reqs.end() && f->second->state == 2);
     }
-    const bool fits = S->in_use + r->footprint <= S->budget;
-    if (ready && fits) {
+    const size_t extra = ready ? extra_for(*r, W) : 0;
+    if (ready && S->in_use + extra <= S->budget) {
       S->queue.erase(it);
-      S->in_use += r->footprint;
+      S->in_use += extra;
       S->peak = std::max(S->peak, S->in_use);
       r->state = 1;
       r->t_start = t;
       return r;
     }
-    if (ready && t - r->t_submit > 2000.0) return nullptr;   // aged head blocks the rest
+    if (ready && t - r->t_submit > 2000.0) {   // aged head blocks the rest
+      *aged = true;
+      return nullptr;
+    }
   }
   return nullptr;
 }
 
-int run_fit(SpsvmRequest& r, cudaStream_t s) {
-  DeviceBuf X, y, ws;
-  SPSVM_TRY(X.ensure(r.X.size() * 4));
-  SPSVM_TRY(y.ensure(r.y.size() * 4));
+int run_fit(SpsvmRequest& r, WorkerBufs& W, cudaStream_t s) {
+  SPSVM_TRY(W.X.ensure(r.X.size() * 4));
+  SPSVM_TRY(W.y.ensure(r.y.size() * 4));
   spsvm_options o = r.opt;
   o.stream = s;
   if (!r.init_basis.empty()) {
     o.initial_basis = r.init_basis.data();
     o.n_initial = (int32_t)r.init_basis.size();
   }
-  SPSVM_TRY(ws.ensure(spsvm_fit_workspace_bytes(r.n, r.d, r.budget, &o)));
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(X.p, r.X.data(), r.X.size() * 4, cudaMemcpyHostToDevice, s));
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(y.p, r.y.data(), r.y.size() * 4, cudaMemcpyHostToDevice, s));
-  const int rc = spsvm_fit(static_cast<float*>(X.p), r.n, r.d, r.d, static_cast<float*>(y.p),
-                           r.gamma, r.lambda, r.budget, r.tol, &o, ws.p, ws.bytes, &r.model);
+  SPSVM_TRY(W.ws.ensure(spsvm_fit_workspace_bytes(r.n, r.d, r.budget, &o)));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(W.X.p, r.X.data(), r.X.size() * 4, cudaMemcpyHostToDevice, s));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(W.y.p, r.y.data(), r.y.size() * 4, cudaMemcpyHostToDevice, s));
+  const int rc = spsvm_fit(static_cast<float*>(W.X.p), r.n, r.d, r.d, static_cast<float*>(W.y.p),
+                           r.gamma, r.lambda, r.budget, r.tol, &o, W.ws.p, W.ws.bytes, &r.model);
   cudaStreamSynchronize(s);
   return rc;
 }
 
-int run_predict(SpsvmRequest& r, spsvm_model* m, cudaStream_t s) {
-  DeviceBuf Q, out;
-  SPSVM_TRY(Q.ensure(r.Xq.size() * 4));
-  SPSVM_TRY(out.ensure((size_t)r.nq * 4));
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(Q.p, r.Xq.data(), r.Xq.size() * 4, cudaMemcpyHostToDevice, s));
-  SPSVM_TRY(spsvm_predict(m, static_cast<float*>(Q.p), r.nq, r.d, static_cast<float*>(out.p), s));
+int run_predict(SpsvmRequest& r, spsvm_model* m, WorkerBufs& W, cudaStream_t s) {
+  SPSVM_TRY(W.Q.ensure(r.Xq.size() * 4));
+  SPSVM_TRY(W.out.ensure((size_t)r.nq * 4));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(W.Q.p, r.Xq.data(), r.Xq.size() * 4, cudaMemcpyHostToDevice, s));
+  SPSVM_TRY(spsvm_predict(m, static_cast<float*>(W.Q.p), r.nq, r.d, static_cast<float*>(W.out.p), s));
   r.out.resize(r.nq);
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(r.out.data(), out.p, r.nq * 4, cudaMemcpyDeviceToHost, s));
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(r.out.data(), W.out.p, r.nq * 4, cudaMemcpyDeviceToHost, s));
   SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
   return SPSVM_OK;
 }
@@ -266,30 +314,44 @@ void worker_loop(spsvm_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t s = nullptr;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  WorkerBufs W;
   for (;;) {
     std::shared_ptr<SpsvmRequest> r;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
         if (S->stop) {
+          S->in_use -= W.held();
+          lk.unlock();
+          W.release();
           cudaStreamDestroy(s);
           return;
         }
-        r = take_admissible(S);
+        bool aged = false;
+        r = take_admissible(S, W, &aged);
         if (r) break;
+        if (aged && W.held() > 0) {
+          // an aged request does not fit: give this worker's buffers back
+          // (a device-synchronising free, on this rare path only)
+          S->in_use -= W.held();
+          lk.unlock();
+          W.release();
+          lk.lock();
+          continue;
+        }
         S->cv.wait_for(lk, std::chrono::milliseconds(50));
       }
     }
     int rc;
+    spsvm_model* fm = nullptr;
     if (r->kind == 0) {
-      rc = run_fit(*r, s);
+      rc = run_fit(*r, W, s);
     } else {
-      spsvm_model* m = nullptr;
       {
         std::lock_guard<std::mutex> lk(S->mu);
-        m = S->reqs[r->fit_id]->model;
+        fm = S->reqs[r->fit_id]->model;
       }
-      rc = m ? run_predict(*r, m, s) : set_error(SPSVM_ERR_ARG, "predict: fit produced no model");
+      rc = fm ? run_predict(*r, fm, W, s) : set_error(SPSVM_ERR_ARG, "predict: fit produced no model");
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -300,7 +362,13 @@ void worker_loop(spsvm_server* S) {
       r->X.shrink_to_fit();
       r->Xq.clear();
       r->Xq.shrink_to_fit();
-      S->in_use -= r->footprint;
+      // a fit's model reserve becomes the model's actual bytes (resident
+      // until released); a failed fit returns its reserve
+      if (r->kind == 0) {
+        S->in_use -= model_reserve(*r);
+        r->model_bytes = spsvm_model_device_bytes(r->model);
+        S->in_use += r->model_bytes;
+      }
       ++S->done;
     }
     S->cv.notify_all();
@@ -365,7 +433,7 @@ extern "C" int spsvm_server_submit_fit(spsvm_server* S, const float* X, int64_t 
   r->opt.initial_basis = nullptr;
   r->opt.n_initial = 0;
   r->footprint = (size_t)n * d * 4 + (size_t)n * 4 +
-                 spsvm_fit_workspace_bytes(n, d, basis_budget, &r->opt) + (size_t)basis_budget * d * 4;
+                 spsvm_fit_workspace_bytes(n, d, basis_budget, &r->opt) + model_reserve(*r);
   return enqueue(S, r, request_id);
 }
 
@@ -380,6 +448,9 @@ extern "C" int spsvm_server_submit_predict(spsvm_server* S, int64_t fit_id, cons
     if (f == S->reqs.end() || f->second->kind != 0)
       return set_error(SPSVM_ERR_ARG, "server_submit_predict: unknown fit request %lld",
                        (long long)fit_id);
+    if (f->second->state == 2 && !f->second->model)
+      return set_error(SPSVM_ERR_ARG, "server_submit_predict: fit request %lld has no model "
+                       "(failed or released)", (long long)fit_id);
     d = f->second->d;
   }
   auto r = std::make_shared<SpsvmRequest>();
@@ -425,6 +496,29 @@ extern "C" int spsvm_server_result(spsvm_server* S, int64_t request_id, float* d
     if (cap < r.nq) return set_error(SPSVM_ERR_ARG, "server_result: output too small");
     std::copy(r.out.begin(), r.out.end(), decision);
   }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_server_release(spsvm_server* S, int64_t fit_request_id) {
+  if (!S) return set_error(SPSVM_ERR_ARG, "server_release: NULL server");
+  spsvm_model* m = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(fit_request_id);
+    if (it == S->reqs.end() || it->second->kind != 0 || it->second->state != 2)
+      return set_error(SPSVM_ERR_ARG, "server_release: %lld is not a finished fit",
+                       (long long)fit_request_id);
+    for (auto& kv : S->reqs)   // predicts of this model still queued or running
+      if (kv.second->kind == 1 && kv.second->fit_id == fit_request_id && kv.second->state != 2)
+        return set_error(SPSVM_ERR_BUSY, "server_release: predicts of %lld pending",
+                         (long long)fit_request_id);
+    m = it->second->model;
+    it->second->model = nullptr;
+    S->in_use -= it->second->model_bytes;
+    it->second->model_bytes = 0;
+  }
+  spsvm_free(m);
+  S->cv.notify_all();
   return SPSVM_OK;
 }
 

@@ -95,8 +95,16 @@ def test_server_mix_equals_alone(sp):
         lat += [l1, l2]
     assert all(v > 0 for v in lat)
     s = srv.stats()
-    assert s["done"] == 8 and s["queued"] == 0 and s["hbm_in_use"] == 0
+    assert s["done"] == 8 and s["queued"] == 0
+    # the budget held while the workers kept their buffers and the models
+    # stayed resident; the models' bytes are counted until released
     assert s["hbm_peak"] <= int(2.2 * one)
+    mb = [srv.model(f).device_bytes() for f in fit_ids]
+    assert all(b > 0 for b in mb)
+    assert s["hbm_in_use"] >= sum(mb)
+    for f in fit_ids:
+        srv.release(f)
+    assert srv.stats()["hbm_in_use"] == s["hbm_in_use"] - sum(mb)
     for p, pid in zip(probs, pred_ids):
         Xs = torch.from_numpy(X[p["rows"]].copy()).cuda()
         ys = torch.from_numpy(p["y"]).cuda()
@@ -104,6 +112,31 @@ def test_server_mix_equals_alone(sp):
                              candidates=128, add_per_round=64)
         ref = alone.predict(torch.from_numpy(Xq).cuda()).cpu().numpy()
         np.testing.assert_array_equal(srv.decision(pid), ref)
+    srv.close()
+
+
+def test_server_budget_holds_with_resident_models(sp):
+    """A budget that admits one fit at a time: six fits run one after
+    another on two workers, every model stays resident and counted, the peak
+    never passes the budget, and a released model gives its bytes back."""
+    X, probs = _grid(count=6, seed=35)
+    one = sp.spsvm_fit_workspace_bytes(4000, 32, 192, sp.make_options(candidates=128)[0])
+    budget = int(1.6 * one)
+    srv = sp.Server(hbm_budget_bytes=budget, workers=2)
+    ids = [srv.submit_fit(X[p["rows"]], p["y"], p["gamma"], p["lam"], p["budget"], p["tol"],
+                          candidates=128, add_per_round=64, seed=p["seed"]) for p in probs]
+    for f in ids:
+        assert srv.wait(f, 120.0)[0] == 0
+    s = srv.stats()
+    assert s["hbm_peak"] <= budget
+    mb = [srv.model(f).device_bytes() for f in ids]
+    assert s["hbm_in_use"] >= sum(mb)
+    srv.release(ids[0])
+    assert srv.stats()["hbm_in_use"] == s["hbm_in_use"] - mb[0]
+    with pytest.raises(sp.SpsvmError):   # its model is gone
+        srv.submit_predict(ids[0], X[:10])
+    pid = srv.submit_predict(ids[1], X[:10])
+    assert srv.wait(pid, 60.0)[0] == 0
     srv.close()
 
 
