@@ -244,6 +244,40 @@ def batched_leg(sp, torch, workers=8, precision="bf16x4"):
                 gpu_busy_pct_mean=busy.get("mean"), gpu_busy_samples=busy.get("samples"))
 
 
+def gram_stress_leg(sp, torch, lib, n=200_000, d=128, budget=2048, sigma_m=0.3,
+                    precision="bf16x4"):
+    """A fit where the masked Gram matrix carries real work: the same
+    mixture generator with component means drawn at sigma_m = 0.3 (classes
+    overlap: training error ~10%, ~40% of the points active), n = 200,000,
+    |J| = 2,048.  Reports the Gram matrix's event-timed TFLOP/s over the fit
+    (four plane products) against the measured sustained BF16 peak."""
+    import ctypes as C
+    from paper_1404_1066_gb300 import synth
+    p = synth.gaussian_mixture(n=n, d=d, budget=budget, seed=1007, sigma_m=sigma_m)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    lib.spsvm_profile_enable(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    m = sp.spsvm_fit(X, y, p.gamma, p.lam, budget, 1e-6, precision=precision, candidates=256,
+                     add_per_round=64, seed=1)
+    e1.record()
+    torch.cuda.synchronize()
+    nm, L_, t_, w_ = C.c_char_p(), C.c_int64(), C.c_double(), C.c_double()
+    lib.spsvm_profile_read(SLOTS.index("gram"), C.byref(nm), C.byref(L_), C.byref(t_), C.byref(w_))
+    lib.spsvm_profile_enable(0)
+    h = m.history()
+    last = [x["active"] for x in h if x["basis"] == budget]
+    peaks, src = _peaks()
+    tf = w_.value / (t_.value * 1e-3) / 1e12 if t_.value > 0 else None
+    return dict(n=n, d=d, basis=budget, sigma_m=sigma_m, fit_s=e0.elapsed_time(e1) / 1e3,
+                newton_steps=m.info()["newton_steps"], status=m.status,
+                active_fraction_last_round=float(np.mean(last)) / n if last else None,
+                train_error=h[-1]["errors"] / n, gram_launches=L_.value, gram_ms=t_.value,
+                gram_tflops=tf, gram_frac=(tf / peaks["bf16_tflops_sustained"]) if tf else None,
+                peak_source=src)
+
+
 def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16x4"):
     """Poisson arrivals (mean 20 requests/s) of fit requests (n log-uniform in
     [1k, 200k], d in {32, 128, 784}, |J| in {128, ..., 2048}, mixture data)
@@ -384,6 +418,76 @@ def growth_leg(sp, torch, model, X, y, p, work, opts, stream, holdout=100_000):
                 holdout_accuracy=acc(ms), holdout=holdout,
                 budget_basis=p.budget, budget_holdout_accuracy=acc(model),
                 train_error_vs_basis=curve)
+
+
+def run_micro_kblock(args):
+    """The tensor-core kernel block alone: the mixture workload's points
+    (n x d, prepared once), |J| = --basis random basis rows, K stored in
+    FP32 as the fit stores it; event-timed per launch.  TFLOP/s counts the
+    four plane products (4 x 2 n |J| d); GB/s counts the n |J| x 4 bytes
+    written."""
+    import torch
+    import paper_1404_1066_gb300 as sp
+    from paper_1404_1066_gb300 import synth
+    sp.load()
+    n, d, m, prec = args.n, args.d, args.basis, args.precision
+    p = synth.gaussian_mixture(n=n, d=d, budget=m, seed=1003)
+    X = torch.from_numpy(p.X).cuda()
+    P = sp.spsvm_prepare_points(X, prec)
+    idx = torch.from_numpy(np.random.default_rng(1).choice(n, m, replace=False).astype(np.int64)).cuda()
+    km = sp.kmat_empty(n, m, "fp32")
+    for _ in range(args.warmup):
+        sp.spsvm_kernel_block(P, idx, p.gamma, prec, km)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sp.spsvm_kernel_block(P, idx, p.gamma, prec, km)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    prod = 4.0 if prec == "bf16x4" else 1.0
+    print(json.dumps(dict(micro="kblock", n=n, d=d, basis=m, precision=prec, ms=ms,
+                          tflops=prod * 2.0 * n * m * d / (ms * 1e-3) / 1e12,
+                          write_gbs=4.0 * n * m / (ms * 1e-3) / 1e9, steps=args.steps)), flush=True)
+    return 0
+
+
+def run_micro_gram(args):
+    """The masked Gram matrix alone: K_nJ of the mixture workload (kernel
+    block, FP32), every point active (|S| = n), compacted into the hi / lo
+    planes and contracted on the tensor cores (BF16X4) or in FP32 SIMT;
+    event-timed per spsvm_gram call (contraction + finish).  TFLOP/s counts
+    4 x |S| |J| (|J| + 1) flops (four plane products, upper triangle)."""
+    import torch
+    import paper_1404_1066_gb300 as sp
+    from paper_1404_1066_gb300 import synth
+    sp.load()
+    n, d, m, prec = args.n, args.d, args.basis, args.precision
+    p = synth.gaussian_mixture(n=n, d=d, budget=m, seed=1003)
+    X = torch.from_numpy(p.X).cuda()
+    P = sp.spsvm_prepare_points(X, prec)
+    J = torch.from_numpy(np.random.default_rng(1).choice(n, m, replace=False).astype(np.int64)).cuda()
+    km = sp.kmat_empty(n, m, "fp32")
+    sp.spsvm_kernel_block(P, J, p.gamma, prec, km)
+    act = torch.ones(n, dtype=torch.uint8, device="cuda")
+    kc = sp.kmat_empty(km.ld, m, prec, ld=km.ld)
+    _, _, nact, _ = sp.spsvm_compact_active(km, act, None, None, kc)
+    for _ in range(args.warmup):
+        sp.spsvm_gram(kc, nact, n, km, J, p.lam, prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sp.spsvm_gram(kc, nact, n, km, J, p.lam, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    prod = 4.0 if prec == "bf16x4" else 1.0
+    print(json.dumps(dict(micro="gram", n=n, active=n, basis=m, precision=prec, ms=ms,
+                          tflops=prod * n * m * (m + 1) / (ms * 1e-3) / 1e12, steps=args.steps)),
+          flush=True)
+    return 0
 
 
 def run_micro(args):
@@ -681,6 +785,7 @@ def run_ours(args):
     if note:
         roofline["note"] = note
 
+    gram_stress = _leg(gram_stress_leg, sp, torch, lib) if args.gram_stress else None
     batched = _leg(batched_leg, sp, torch) if args.batched else None
     ovo = _leg(ovo_leg, sp, torch) if args.ovo else None
     exact = _leg(exact_score_leg, sp, torch) if args.exact_score else None
@@ -700,7 +805,8 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, lowrank=lowrank, growth_stop=growth, batched=batched, ovo=ovo,
+                fp32_form=fp32_form, lowrank=lowrank, growth_stop=growth, gram_stress=gram_stress,
+                batched=batched, ovo=ovo,
                 exact_score=exact, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline_run(steps=1)
@@ -737,11 +843,13 @@ def main():
     ap.add_argument("--ovo", type=int, default=1, help="one-vs-one leg (10 classes, 45 pairs)")
     ap.add_argument("--exact-score", type=int, default=1,
                     help="heuristic vs exact one-dimensional selection score leg")
+    ap.add_argument("--gram-stress", type=int, default=1,
+                    help="a fit on an overlapping mixture where the Gram matrix carries real work")
     ap.add_argument("--lowrank", type=int, default=1,
                     help="one fit with the low-rank correction of the Newton factor")
     ap.add_argument("--growth", type=int, default=1,
                     help="report the growth stop at epsilon = 5e-6 and accuracy vs |J|")
-    ap.add_argument("--micro", choices=["cholesky"], default=None,
+    ap.add_argument("--micro", choices=["cholesky", "kblock", "gram"], default=None,
                     help="time one hot-path step alone instead of the whole fit")
     ap.add_argument("--sizes", default="512,1024,2048,4096")
     args = ap.parse_args()
@@ -751,6 +859,10 @@ def main():
         args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.micro == "kblock":
+        return run_micro_kblock(args)
+    if args.micro == "gram":
+        return run_micro_gram(args)
     if args.micro:
         return run_micro(args)
     return run_ours(args)
