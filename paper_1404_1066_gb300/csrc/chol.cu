@@ -1757,7 +1757,8 @@ struct LowRankView {
 static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shift,
                             const double* b, double* x, int32_t max_iter, double tol,
                             int32_t* iters, double* backward_error, void* work,
-                            size_t work_bytes, const LowRankView* lr, void* stream) {
+                            size_t work_bytes, const LowRankView* lr, const int32_t* factor_info,
+                            void* stream) {
   if (!H || !b || !x || m < 0 || ldh < m || max_iter < 1 || !(tol > 0.0) || !(shift >= 0.0))
     return set_error(SPSVM_ERR_ARG, "solve_mixed: bad arguments");
   if (iters) *iters = 0;
@@ -1829,10 +1830,19 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
     SPSVM_LAUNCH_CHECK();
     max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4);
     SPSVM_LAUNCH_CHECK();
+    // the first step never reaches FP64 backward error from an FP32 factor:
+    // the first check (a host round trip) follows the second step
+    if (it == 0 && max_iter > 1) continue;
     double nv[2] = {0, 0};
     SPSVM_CUDA_TRY(cudaMemcpyAsync(nv, norms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int32_t finfo = 0;
+    if (factor_info && it <= 1)
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(&finfo, factor_info, sizeof(finfo), cudaMemcpyDeviceToHost, s));
     int32_t code = 0;
     SPSVM_TRY(device_status_on(s, &code));   // synchronises s
+    if (finfo != 0)
+      return set_error(SPSVM_ERR_NOT_PD, "solve_mixed: the FP32 factorisation broke down at pivot %d",
+                       finfo - 1);
     const double denom = hn[0] * nv[0] + hn[1];
     const double be = denom > 0.0 ? nv[1] / denom : 0.0;
     if (iters) *iters = it + 1;
@@ -1851,7 +1861,19 @@ extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double
                                  int32_t* iters, double* backward_error, void* work,
                                  size_t work_bytes, void* stream) {
   return solve_mixed_impl(H, m, ldh, shift, b, x, max_iter, tol, iters, backward_error, work,
-                          work_bytes, nullptr, stream);
+                          work_bytes, nullptr, nullptr, stream);
+}
+
+// spsvm_solve_mixed right after spsvm_cholesky_mixed, without a host read of
+// the factorisation's info in between: the first refinement check reads it
+// and returns SPSVM_ERR_NOT_PD when the FP32 factorisation broke down (the
+// refinement's results are then discarded).
+int spsvm::solve_mixed_after_factor(const double* H, int64_t m, int64_t ldh, double shift,
+                                    const double* b, double* x, int32_t max_iter, double tol,
+                                    void* work, size_t work_bytes, const int32_t* factor_info,
+                                    void* stream) {
+  return solve_mixed_impl(H, m, ldh, shift, b, x, max_iter, tol, nullptr, nullptr, work,
+                          work_bytes, nullptr, factor_info, stream);
 }
 
 extern "C" size_t spsvm_lowrank_work_bytes(int64_t m, int32_t kmax) {
@@ -1910,5 +1932,5 @@ extern "C" int spsvm_solve_lowrank(const double* H, int64_t m, int64_t ldh, cons
   LowRankView v{reinterpret_cast<const float*>(w + ly.V), reinterpret_cast<const float*>(w + ly.Ci),
                 reinterpret_cast<float*>(w + ly.s), ly.ldv, ly.slices, k, (int32_t)ly.G};
   return solve_mixed_impl(H, m, ldh, 0.0, b, x, max_iter, tol, iters, backward_error, mixed_work,
-                          mixed_bytes, &v, stream);
+                          mixed_bytes, &v, nullptr, stream);
 }

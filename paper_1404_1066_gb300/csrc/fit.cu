@@ -505,20 +505,30 @@ struct Fit {
     // active set
     double gprev = INFINITY;
     bool kept_prev = false;
-    for (int it = 0; it < op.max_newton; ++it) {
-      uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
+    // Gradient pass on the flags `act`: residuals o - y, compaction with the
+    // masked transposed products (w = K_SJ^T (o_S - y_S), r = K_SJ^T y_S;
+    // the copy K_SJ is rewritten unless *kc_cond is zero, i.e. unless the
+    // active set is unchanged), gradient and the dots of the stopping test.
+    auto grad_pass = [&](uint8_t* act_f, const unsigned long long* kc_cond) -> int {
       sub_kernel<<<grid_for(n, tpb), tpb, 0, s>>>(o, y, n, res);
       SPSVM_LAUNCH_CHECK();
-      // K_SJ is only needed for a new Gram matrix
-      SPSVM_TRY(spsvm_compact_active(&K, act, res, y, wsum, r, reuse ? nullptr : &Kc, n_active,
-                                     at<int32_t>(L.off_pos), scratch, sb, s));
+      SPSVM_TRY(compact_active_impl(&K, act_f, res, y, wsum, r, &Kc, kc_cond, n_active,
+                                    at<int32_t>(L.off_pos), scratch, sb, s));
       grad_finish<<<mb, tpb, 0, s>>>(o, Jd, wsum, m, op_lambda(), g, rhs, b0());
       SPSVM_LAUNCH_CHECK();
       small_dots<<<1, 256, 0, s>>>(beta, o, Jd, g, r, m, dots, b0());
       SPSVM_LAUNCH_CHECK();
-      double dh[3];
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
+      return SPSVM_OK;
+    };
+    // the small area's layout, read back in one copy after each step:
+    // [0, 24) loss / errors / |S|, [96, 104) changed flags, [128, 152) dots
+    constexpr size_t kSmallRead = 160;
+    double dh[3] = {0.0, 0.0, 0.0};
+    SPSVM_TRY(grad_pass(at<uint8_t>(act_cur ? L.off_act1 : L.off_act0), nullptr));
+    SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
+    SPSVM_TRY(sync());
+    for (int it = 0; it < op.max_newton; ++it) {
+      uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
       const double gnorm = std::sqrt(dh[1]), rnorm = std::sqrt(dh[2]);
       model->objective = 0.5 * lambda * dh[0] + st[0];
       // Newton stop (the paper gives none):
@@ -650,21 +660,17 @@ struct Fit {
           // error; H is kept, so a failure costs no Gram rebuild
           mixed = false;
           if (op.solver == SPSVM_SOLVE_MIXED) {
+            // the factorisation's info is read at the refinement's first check
             SPSVM_TRY(spsvm_cholesky_mixed(H, m, ldH, shift, info, mixw, L.mix_bytes, s));
-            SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
-            SPSVM_TRY(sync());
+            const int rc = solve_mixed_after_factor(H, m, ldH, shift, rhs, dir, kMixedIters,
+                                                    kMixedTol, mixw, L.mix_bytes, info, s);
+            if (rc == SPSVM_OK) mixed = true;
+            else if (rc != SPSVM_ERR_NO_CONVERGE && rc != SPSVM_ERR_NOT_PD) return rc;
             // the factor in the mixed work is now that of this matrix: an
-            // anchor for low-rank corrections when unshifted
-            anchor_m = (op.lowrank && info_h == 0 && shift == 0.0 && m >= kLowRankMinBasis) ? m : -1;
+            // anchor for low-rank corrections when unshifted and refined
+            anchor_m = (op.lowrank && mixed && shift == 0.0 && m >= kLowRankMinBasis) ? m : -1;
             if (anchor_m == m)
               SPSVM_CUDA_TRY(cudaMemcpyAsync(anchor, act, n, cudaMemcpyDeviceToDevice, s));
-            if (info_h == 0) {
-              const int rc = spsvm_solve_mixed(H, m, ldH, shift, rhs, dir, kMixedIters, kMixedTol,
-                                               nullptr, nullptr, mixw, L.mix_bytes, s);
-              if (rc == SPSVM_OK) mixed = true;
-              else if (rc != SPSVM_ERR_NO_CONVERGE) return rc;
-              else anchor_m = -1;   // this factor does not refine to FP64 accuracy
-            }
           }
           if (mixed) {
             jitter = lv;
@@ -715,16 +721,27 @@ struct Fit {
       SPSVM_LAUNCH_CHECK();
       update_o<<<grid_for(n, tpb), tpb, 0, s>>>(o, u, t, n);
       SPSVM_LAUNCH_CHECK();
+      // after the step: new flags and stats, the count of changed flags, and
+      // the next gradient pass, then one read of all their scalars
       const int nxt = act_cur ^ 1;
-      double st2[3];
-      SPSVM_TRY(flags(nxt, st2));
+      {
+        spsvm_kmat Kf = kmat();
+        SPSVM_TRY(spsvm_outputs(&Kf, nullptr, y, o, at<uint8_t>(nxt ? L.off_act1 : L.off_act0),
+                                at<double>(L.off_small), scratch, sb, s));
+      }
       SPSVM_CUDA_TRY(cudaMemsetAsync(ndiff, 0, sizeof(*ndiff), s));
       count_diff<<<grid_for(n, tpb), tpb, 0, s>>>(at<uint8_t>(L.off_act0), at<uint8_t>(L.off_act1),
                                                   n, ndiff);
       SPSVM_LAUNCH_CHECK();
-      unsigned long long nd = 0;
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(&nd, ndiff, sizeof(nd), cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(grad_pass(at<uint8_t>(nxt ? L.off_act1 : L.off_act0), ndiff));
+      alignas(8) unsigned char sm_h[kSmallRead];
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(sm_h, small, kSmallRead, cudaMemcpyDeviceToHost, s));
       SPSVM_TRY(sync());
+      double st2[3];
+      unsigned long long nd = 0;
+      std::memcpy(st2, sm_h, sizeof(st2));
+      std::memcpy(&nd, sm_h + 96, sizeof(nd));
+      std::memcpy(dh, sm_h + 128, sizeof(dh));
       spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], jitter, (int32_t)nd, how};
       model->history.push_back(rec);
       act_cur = nxt;

@@ -263,9 +263,11 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
     KView K, int64_t rows, int64_t n, const uint8_t* __restrict__ active,
     const int32_t* __restrict__ pos, const float* __restrict__ w1, const float* __restrict__ w2,
     void* kc_data, int32_t kc_format, int64_t kc_ld, int64_t kc_plane, int64_t chunks_per_block,
-    double2* __restrict__ part, const int64_t* __restrict__ ns_dev, int64_t gather_max) {
+    double2* __restrict__ part, const int64_t* __restrict__ ns_dev, int64_t gather_max,
+    const unsigned long long* __restrict__ kc_cond) {
   __shared__ double sh[32];
   if (*ns_dev <= gather_max) return;   // few active points: compact_gather does this
+  if (kc_cond && *kc_cond == 0) kc_data = nullptr;   // the caller keeps the copy it has
   const int64_t j0 = (int64_t)blockIdx.x * CP_ROWS;
   const int64_t c_begin = (int64_t)blockIdx.y * chunks_per_block;
   const int64_t nchunks = ceil_div(n, (int64_t)CP_T);
@@ -326,10 +328,12 @@ __global__ void __launch_bounds__(CP_T) compact_kernel(
 __global__ void __launch_bounds__(CP_T) compact_gather(
     KView K, int64_t rows, const int32_t* __restrict__ list, const int64_t* __restrict__ ns_dev,
     int64_t gather_max, const float* __restrict__ w1, const float* __restrict__ w2, void* kc_data,
-    int32_t kc_format, int64_t kc_ld, int64_t kc_plane, double2* __restrict__ part) {
+    int32_t kc_format, int64_t kc_ld, int64_t kc_plane, double2* __restrict__ part,
+    const unsigned long long* __restrict__ kc_cond) {
   __shared__ double sh[32];
   const int64_t ns = *ns_dev;
   if (ns > gather_max) return;
+  if (kc_cond && *kc_cond == 0) kc_data = nullptr;
   const int64_t j0 = (int64_t)blockIdx.x * CP_ROWS;
   double s1[CP_ROWS], s2[CP_ROWS];
   float f1[CP_ROWS], f2[CP_ROWS];
@@ -396,7 +400,9 @@ __global__ void compact_finish(const double2* __restrict__ part, int64_t ysplit,
 
 // Zero columns [ns, kc_n) of every row of the compact matrix.
 __global__ void zero_tail(void* kc_data, int32_t format, int64_t rows, int64_t kc_ld,
-                          int64_t kc_plane, int64_t kc_n, const int64_t* __restrict__ ns_dev) {
+                          int64_t kc_plane, int64_t kc_n, const int64_t* __restrict__ ns_dev,
+                          const unsigned long long* __restrict__ kc_cond) {
+  if (kc_cond && *kc_cond == 0) return;
   const int64_t ns = *ns_dev;
   const int64_t end = min(kc_n, round_up(ns, (int64_t)128));
   const int64_t width = end - ns;
@@ -513,6 +519,17 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
                                     const float* w2, double* w1out, double* w2out,
                                     spsvm_kmat* Kc, int64_t* n_active, int32_t* pos,
                                     void* scratch, size_t scratch_bytes, void* stream) {
+  return compact_active_impl(K, active, w1, w2, w1out, w2out, Kc, nullptr, n_active, pos, scratch,
+                             scratch_bytes, stream);
+}
+
+// With kc_cond, K_SJ is written only when *kc_cond (read on the device) is
+// nonzero: the fit passes the count of points whose active flag changed, so
+// an unchanged active set keeps the copy in hand without a host round trip.
+int spsvm::compact_active_impl(const spsvm_kmat* K, const uint8_t* active, const float* w1,
+                               const float* w2, double* w1out, double* w2out, spsvm_kmat* Kc,
+                               const unsigned long long* kc_cond, int64_t* n_active,
+                               int32_t* pos, void* scratch, size_t scratch_bytes, void* stream) {
   SPSVM_TRY(check_kmat(K, "compact"));
   if (!active || !n_active || !pos) return set_error(SPSVM_ERR_ARG, "compact: NULL pointer");
   if (Kc) {
@@ -557,11 +574,11 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
     compact_kernel<<<grid, CP_T, 0, s>>>(view(K), K->rows, n, active, pos, w1, w2,
                                          Kc ? Kc->data : nullptr, Kc ? Kc->format : 0,
                                          Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, per, part, n_active,
-                                         gather_max);
+                                         gather_max, kc_cond);
     SPSVM_LAUNCH_CHECK();
     compact_gather<<<(unsigned)ceil_div(K->rows, CP_ROWS), CP_T, 0, s>>>(
         view(K), K->rows, list, n_active, gather_max, w1, w2, Kc ? Kc->data : nullptr,
-        Kc ? Kc->format : 0, Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, part);
+        Kc ? Kc->format : 0, Kc ? Kc->ld : 0, Kc ? Kc->plane : 0, part, kc_cond);
     SPSVM_LAUNCH_CHECK();
     if (w1out || w2out) {
       compact_finish<<<(unsigned)ceil_div(K->rows, 256), 256, 0, s>>>(part, ysplit, K->rows,
@@ -576,7 +593,7 @@ extern "C" int spsvm_compact_active(const spsvm_kmat* K, const uint8_t* active, 
   if (Kc && K->rows > 0) {
     const int64_t kc_n = round_up(n, 128) <= Kc->n ? round_up(n, 128) : Kc->n;
     zero_tail<<<4 * sm_count(), 256, 0, s>>>(Kc->data, Kc->format, K->rows, Kc->ld, Kc->plane,
-                                             kc_n, n_active);
+                                             kc_n, n_active, kc_cond);
     SPSVM_LAUNCH_CHECK();
   }
   return SPSVM_OK;

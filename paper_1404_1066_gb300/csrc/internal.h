@@ -175,4 +175,18 @@ int line_search_impl(const float* o, const float* u, const float* y, int64_t n, 
                      const int64_t* J, int32_t m, double lambda, double* t_host, double* t_dev,
                      void* scratch, size_t scratch_bytes, void* stream, const double* b0);
 
+// spsvm_solve_mixed right after spsvm_cholesky_mixed with its info word
+// read at the first refinement check (SPSVM_ERR_NOT_PD when it is nonzero).
+int solve_mixed_after_factor(const double* H, int64_t m, int64_t ldh, double shift,
+                             const double* b, double* x, int32_t max_iter, double tol,
+                             void* work, size_t work_bytes, const int32_t* factor_info,
+                             void* stream);
+
+// spsvm_compact_active whose K_SJ copy is written only when *kc_cond (read
+// on the device) is nonzero; kc_cond NULL: always.
+int compact_active_impl(const spsvm_kmat* K, const uint8_t* active, const float* w1,
+                        const float* w2, double* w1out, double* w2out, spsvm_kmat* Kc,
+                        const unsigned long long* kc_cond, int64_t* n_active, int32_t* pos,
+                        void* scratch, size_t scratch_bytes, void* stream);
+
 }  // namespace spsvm
