@@ -88,10 +88,22 @@ __global__ void axpy_d(double* __restrict__ y, const double* __restrict__ x, dou
   if (k < m) y[k] += a * x[k];
 }
 
-__global__ void update_o(float* __restrict__ o, const float* __restrict__ u, double t, int64_t n) {
+// beta += t d and o += t u with t read on the device (the line search's
+// result, 0 when it found no descent)
+__global__ void axpy_t(double* __restrict__ y, const double* __restrict__ x,
+                       const double* __restrict__ t, int32_t m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double a = *t;
+  if (k < m && a != 0.0) y[k] += a * x[k];
+}
+
+__global__ void update_o_t(float* __restrict__ o, const float* __restrict__ u,
+                           const double* __restrict__ t, int64_t n) {
+  const double a = *t;
+  if (a == 0.0) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = (float)((double)o[i] + t * (double)u[i]);
+    o[i] = (float)((double)o[i] + a * (double)u[i]);
 }
 
 __global__ void count_diff(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b, int64_t n,
@@ -521,9 +533,48 @@ struct Fit {
       return SPSVM_OK;
     };
     // the small area's layout, read back in one copy after each step:
-    // [0, 24) loss / errors / |S|, [96, 104) changed flags, [128, 152) dots
-    constexpr size_t kSmallRead = 160;
+    // [0, 24) loss / errors / |S|, [96, 104) changed flags, [128, 152) dots,
+    // [200, 208) the line search's t, [208, 212) its error word
+    constexpr size_t kSmallRead = 216;
+    double* t_dev = reinterpret_cast<double*>(small + 200);
+    int32_t* ls_err = reinterpret_cast<int32_t*>(small + 208);
     double dh[3] = {0.0, 0.0, 0.0};
+    double st_next[3] = {0.0, 0.0, 0.0}, dh_next[3] = {0.0, 0.0, 0.0};
+    unsigned long long nd_next = 0;
+    // The line search along dir and, in the same stream order, the step it
+    // gives with its consequences -- beta += t dir, o += t u, the new flags
+    // and stats, the count of changed flags and the next gradient pass --
+    // then one read of all their scalars.  With t = 0 (no descent) the step
+    // leaves beta and o as they were and the rest recomputes the same values.
+    auto search_and_step = [&](double* t_out) -> int {
+      SPSVM_TRY(line_search_async(o, u, y, n, dir, Jd, m, lambda, t_dev, ls_err, scratch, sb, s, b0()));
+      axpy_t<<<mb, tpb, 0, s>>>(beta, dir, t_dev, m);
+      SPSVM_LAUNCH_CHECK();
+      update_o_t<<<grid_for(n, tpb), tpb, 0, s>>>(o, u, t_dev, n);
+      SPSVM_LAUNCH_CHECK();
+      const int nxt = act_cur ^ 1;
+      {
+        spsvm_kmat Kf = kmat();
+        SPSVM_TRY(spsvm_outputs(&Kf, nullptr, y, o, at<uint8_t>(nxt ? L.off_act1 : L.off_act0),
+                                at<double>(L.off_small), scratch, sb, s));
+      }
+      SPSVM_CUDA_TRY(cudaMemsetAsync(ndiff, 0, sizeof(*ndiff), s));
+      count_diff<<<grid_for(n, tpb), tpb, 0, s>>>(at<uint8_t>(L.off_act0), at<uint8_t>(L.off_act1),
+                                                  n, ndiff);
+      SPSVM_LAUNCH_CHECK();
+      SPSVM_TRY(grad_pass(at<uint8_t>(nxt ? L.off_act1 : L.off_act0), ndiff));
+      alignas(8) unsigned char sm_h[kSmallRead];
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(sm_h, small, kSmallRead, cudaMemcpyDeviceToHost, s));
+      SPSVM_TRY(sync());
+      int32_t err = 0;
+      std::memcpy(&err, sm_h + 208, sizeof(err));
+      if (err) return set_error(SPSVM_ERR_TIMEOUT, "line_search: grid barrier timed out");
+      std::memcpy(st_next, sm_h, sizeof(st_next));
+      std::memcpy(&nd_next, sm_h + 96, sizeof(nd_next));
+      std::memcpy(dh_next, sm_h + 128, sizeof(dh_next));
+      std::memcpy(t_out, sm_h + 200, sizeof(double));
+      return SPSVM_OK;
+    };
     SPSVM_TRY(grad_pass(at<uint8_t>(act_cur ? L.off_act1 : L.off_act0), nullptr));
     SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
     SPSVM_TRY(sync());
@@ -585,7 +636,7 @@ struct Fit {
         if (gsmall) SPSVM_TRY(step_small(&done));
         if (done) return SPSVM_OK;
         SPSVM_TRY(finish_direction(act, kind, sh));
-        SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
+        SPSVM_TRY(search_and_step(&t));
         searched = true;
         *ok = t > 0.0;
         return SPSVM_OK;
@@ -699,7 +750,7 @@ struct Fit {
         // d = -(H + shift I)^{-1} g (computed above), u = K_nJ d
         SPSVM_TRY(finish_direction(act, fac_kind, shift));
         t = 0.0;
-        SPSVM_TRY(line_search_impl(o, u, y, n, dir, Jd, m, lambda, &t, nullptr, scratch, sb, s, b0()));
+        SPSVM_TRY(search_and_step(&t));
         // with a small gradient, no descent means rounding level: no jitter
         if (t > 0.0 || gsmall || jitter >= kJitterMaxLevel) break;
         ++jitter;
@@ -717,31 +768,12 @@ struct Fit {
         if (gsmall) status = SPSVM_OK;
         break;
       }
-      axpy_d<<<mb, tpb, 0, s>>>(beta, dir, t, m);
-      SPSVM_LAUNCH_CHECK();
-      update_o<<<grid_for(n, tpb), tpb, 0, s>>>(o, u, t, n);
-      SPSVM_LAUNCH_CHECK();
-      // after the step: new flags and stats, the count of changed flags, and
-      // the next gradient pass, then one read of all their scalars
+      // the step and its consequences ran with the line search
       const int nxt = act_cur ^ 1;
-      {
-        spsvm_kmat Kf = kmat();
-        SPSVM_TRY(spsvm_outputs(&Kf, nullptr, y, o, at<uint8_t>(nxt ? L.off_act1 : L.off_act0),
-                                at<double>(L.off_small), scratch, sb, s));
-      }
-      SPSVM_CUDA_TRY(cudaMemsetAsync(ndiff, 0, sizeof(*ndiff), s));
-      count_diff<<<grid_for(n, tpb), tpb, 0, s>>>(at<uint8_t>(L.off_act0), at<uint8_t>(L.off_act1),
-                                                  n, ndiff);
-      SPSVM_LAUNCH_CHECK();
-      SPSVM_TRY(grad_pass(at<uint8_t>(nxt ? L.off_act1 : L.off_act0), ndiff));
-      alignas(8) unsigned char sm_h[kSmallRead];
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(sm_h, small, kSmallRead, cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
       double st2[3];
-      unsigned long long nd = 0;
-      std::memcpy(st2, sm_h, sizeof(st2));
-      std::memcpy(&nd, sm_h + 96, sizeof(nd));
-      std::memcpy(dh, sm_h + 128, sizeof(dh));
+      const unsigned long long nd = nd_next;
+      std::memcpy(st2, st_next, sizeof(st2));
+      std::memcpy(dh, dh_next, sizeof(dh));
       spsvm_step rec{m, (int32_t)st[2], gnorm, t, st2[0], (int32_t)st2[1], jitter, (int32_t)nd, how};
       model->history.push_back(rec);
       act_cur = nxt;

@@ -175,6 +175,13 @@ int line_search_impl(const float* o, const float* u, const float* y, int64_t n, 
                      const int64_t* J, int32_t m, double lambda, double* t_host, double* t_dev,
                      void* scratch, size_t scratch_bytes, void* stream, const double* b0);
 
+// line_search_impl without a host round trip: t (0 when no descent or when
+// a grid barrier gave up) and the barrier error word go to device memory,
+// in order on the stream.
+int line_search_async(const float* o, const float* u, const float* y, int64_t n, const double* d,
+                      const int64_t* J, int32_t m, double lambda, double* t_dev, int32_t* err_dev,
+                      void* scratch, size_t scratch_bytes, void* stream, const double* b0);
+
 // spsvm_solve_mixed right after spsvm_cholesky_mixed with its info word
 // read at the first refinement check (SPSVM_ERR_NOT_PD when it is nonzero).
 int solve_mixed_after_factor(const double* H, int64_t m, int64_t ldh, double shift,

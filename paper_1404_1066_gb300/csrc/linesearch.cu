@@ -265,6 +265,14 @@ __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
   }
 }
 
+// The search's result for the caller's stream-ordered use: t and the
+// grid-barrier error word.
+__global__ void ls_export(const LsState* __restrict__ st, double* __restrict__ t_dev,
+                          int32_t* __restrict__ err_dev) {
+  *t_dev = st->err ? 0.0 : st->t;
+  *err_dev = st->err;
+}
+
 int ls_grid() {
   static std::mutex mu;
   static int per_sm[64] = {};
@@ -324,5 +332,30 @@ int spsvm::line_search_impl(const float* o, const float* u, const float* y, int6
   if (h.err) return set_error(SPSVM_ERR_TIMEOUT, "line_search: grid barrier timed out");
   *t_host = h.t;
   if (t_dev) SPSVM_CUDA_TRY(cudaMemcpyAsync(t_dev, t_host, sizeof(double), cudaMemcpyHostToDevice, s));
+  return SPSVM_OK;
+}
+
+int spsvm::line_search_async(const float* o, const float* u, const float* y, int64_t n,
+                             const double* d, const int64_t* J, int32_t m, double lambda,
+                             double* t_dev, int32_t* err_dev, void* scratch, size_t scratch_bytes,
+                             void* stream, const double* b0) {
+  if (!o || !u || !y || !d || !J || !t_dev || !err_dev || n < 0 || m < 0)
+    return set_error(SPSVM_ERR_ARG, "line_search: bad arguments");
+  if (!scratch || scratch_bytes < spsvm_line_scratch_bytes(n))
+    return set_error(SPSVM_ERR_OOM, "line_search: scratch too small");
+  cudaStream_t s = as_stream(stream);
+  ProfScope prof(PROF_LINE, s, 12.0 * (double)n);
+  const int grid = ls_grid();
+  if (grid < 1) return set_error(SPSVM_ERR_CUDA, "line_search: occupancy query failed");
+  LsState* st = static_cast<LsState*>(scratch);
+  unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);
+  LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  void* args[] = {(void*)&o, (void*)&u, (void*)&y, (void*)&n, (void*)&d, (void*)&J,
+                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar, (void*)&b0};
+  SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ls_search, dim3(grid), dim3(LT), args, 0, s));
+  SPSVM_LAUNCH_CHECK();
+  ls_export<<<1, 1, 0, s>>>(st, t_dev, err_dev);
+  SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
