@@ -49,18 +49,23 @@ extern "C" {
 
 /* ---- arithmetic forms -------------------------------------------------- */
 /* SPSVM_FP32: kernel block and Gram matrix in FP32 SIMT arithmetic.
- * SPSVM_BF16X4: kernel block and Gram matrix on tcgen05 tensor cores with
- *   each FP32 operand split as hi + lo (both BF16, lo = bf16(x - hi)) and all
- *   four products hi*hi + hi*lo + lo*hi + lo*lo accumulated in FP32 (the
- *   exact product of the two-term representations).
- * Both forms store the kernel matrix K_nJ in FP32; the BF16X4 fit keeps the
- * compact copy K_SJ, the Gram matrix's operand, as hi / lo BF16 planes.  In
- * both forms the Newton system is, by default, factored in FP32 and solved
- * with FP64 iterative refinement to FP64 backward error (SPSVM_SOLVE_MIXED),
- * or factored in FP64 (SPSVM_SOLVE_FP64, and the fallback of the mixed
- * solve when its FP32 factor breaks down or the refinement stalls). */
+ * SPSVM_BF16SPLIT: kernel block and Gram matrix on tcgen05 tensor cores
+ *   with FP32 operands split into BF16 terms and FP32 accumulation.  The
+ *   kernel block splits each point as x = hi + mid + lo (three BF16 terms,
+ *   exact for FP32) and forms the six products hi hi, hi mid, mid hi,
+ *   mid mid, hi lo, lo hi (the three dropped ones are below 2^-24 of |x z|):
+ *   kernel values as accurate as FP32 arithmetic.  The Gram matrix reads the
+ *   compact copy K_SJ split as hi + lo and forms all four products (the
+ *   Newton matrix then carries 2^-17 relative rounding; the gradient, and
+ *   with it the minimiser the Newton iteration converges to, come from the
+ *   FP32 kernel values).
+ * Both forms store the kernel matrix K_nJ in FP32.  In both the Newton
+ * system is, by default, factored in FP32 and solved with FP64 iterative
+ * refinement to FP64 backward error (SPSVM_SOLVE_MIXED), or factored in FP64
+ * (SPSVM_SOLVE_FP64, and the fallback of the mixed solve when its FP32
+ * factor breaks down or the refinement stalls). */
 #define SPSVM_FP32    0
-#define SPSVM_BF16X4  1
+#define SPSVM_BF16SPLIT  1
 
 /* Newton-system solvers (spsvm_options.newton_solver). */
 #define SPSVM_SOLVE_MIXED 0
@@ -78,23 +83,24 @@ extern "C" {
 /* ---- stored kernel matrix ---------------------------------------------- */
 /* K_nJ stored basis-major: row j (one basis vector) holds k(x_i, x_{J_j})
  * for i = 0..n-1 contiguously.  format SPSVM_FP32: element (j, i) at
- * ((float*)data)[j*ld + i].  format SPSVM_BF16X4 (two BF16 planes): hi plane
+ * ((float*)data)[j*ld + i].  format SPSVM_BF16SPLIT (two BF16 planes): hi plane
  * at ((uint16_t*)data)[j*ld + i], lo plane at ((uint16_t*)data)[plane +
  * j*ld + i]; value = hi + lo.
  * ld and plane are in elements; ld >= n, ld % 8 == 0, data 16-byte aligned. */
 typedef struct spsvm_kmat {
   void*   data;     /* device */
-  int32_t format;   /* SPSVM_FP32 or SPSVM_BF16X4 */
+  int32_t format;   /* SPSVM_FP32 or SPSVM_BF16SPLIT */
   int32_t pad_;
   int64_t n;        /* points (columns of the stored matrix) */
   int64_t rows;     /* basis vectors stored */
   int64_t ld;       /* elements between consecutive rows */
-  int64_t plane;    /* elements between hi and lo planes (BF16X4 only) */
+  int64_t plane;    /* elements between hi and lo planes (BF16SPLIT only) */
 } spsvm_kmat;
 
-/* Points prepared once per X: squared norms and, for SPSVM_BF16X4, the BF16
- * split planes (hi = bf16(x), lo = bf16(x - hi)), each n x ldh with the
- * columns d..ldh-1 zero.  All pointers device; X is borrowed. */
+/* Points prepared once per X: squared norms and, for SPSVM_BF16SPLIT, the
+ * three BF16 split planes (hi = bf16(x), mid = bf16(x - hi), lo = bf16(x -
+ * hi - mid)), each n x ldh with the columns d..ldh-1 zero.  All pointers
+ * device; X is borrowed. */
 typedef struct spsvm_points {
   const float* X;   /* device, n x d row-major, leading dimension ldx */
   int64_t n, d, ldx;
@@ -102,6 +108,7 @@ typedef struct spsvm_points {
   uint16_t* hi;     /* device, n x ldh, or NULL for SPSVM_FP32 */
   uint16_t* lo;     /* device, n x ldh, or NULL */
   int64_t   ldh;    /* multiple of 64, >= d */
+  uint16_t* mid;    /* device, n x ldh, or NULL */
 } spsvm_points;
 
 /* ======================================================================= */
@@ -111,20 +118,21 @@ typedef struct spsvm_points {
 
 /* Row norms ||x_i||^2 of the RBF distance expansion
  * ||x - z||^2 = ||x||^2 + ||z||^2 - 2 x^T z (Section 2, RBF kernel); and for
- * precision == SPSVM_BF16X4 the hi/lo planes.  Fills p->norms (and p->hi,
- * p->lo), which the caller allocated.  Errors: ARG if a pointer is NULL or
- * n < 0, d < 1, ldx < d, ldh < d or ldh % 64 != 0. */
+ * precision == SPSVM_BF16SPLIT the hi / mid / lo planes.  Fills p->norms
+ * (and p->hi, p->mid, p->lo), which the caller allocated.  Errors: ARG if a
+ * pointer is NULL or n < 0, d < 1, ldx < d, ldh < d or ldh % 64 != 0. */
 int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* stream);
 
 /* Kernel block (Section 2 RBF; Section 4: K_nJ, O(|J| n) memory):
  *   out row (row0 + c), column i  =  exp(-gamma * max(0, ||x_i||^2 +
  *   ||x_{idx[c]}||^2 - 2 x_i^T x_{idx[c]}))   for c < m, i < n.
  * idx: device, m indices into the points.  The dot products are formed in
- * `precision`; out->format selects the storage (FP32 or the two BF16
- * planes), in either form.  Requires row0 + m <= out->rows.  scratch: device, at least
- * spsvm_kernel_block_scratch_bytes(m, d, precision) bytes (the BF16X4 form
- * gathers the m basis rows there; 0 bytes for SPSVM_FP32).  Errors: ARG,
- * OOM (scratch too small). */
+ * `precision`; out->format selects the storage: FP32 (either form) or the
+ * two BF16 planes (SPSVM_FP32 arithmetic only).  Requires row0 + m <=
+ * out->rows.  scratch: device, at least
+ * spsvm_kernel_block_scratch_bytes(m, d, precision) bytes (the BF16SPLIT form
+ * gathers the m basis rows' three planes there; 0 bytes for SPSVM_FP32).
+ * Errors: ARG, OOM (scratch too small). */
 size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision);
 int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int32_t m,
                        float gamma, int32_t precision, spsvm_kmat* out,
@@ -181,7 +189,7 @@ int spsvm_score_candidates_exact(const spsvm_points* p, const float* y, const fl
  * library (a file-scope __device__ array, held by every GPU that loads the
  * library until the process exits).  Limit:
  * spsvm_score_scratch_bytes(n, d, kappa) <= 16 MiB (e.g. n = 500,000,
- * d = 128, kappa = 256); larger sizes are rejected with SPSVM_ERR_ARG
+ * d = 128, kappa = 256 needs 16.2 MB); larger sizes are rejected with SPSVM_ERR_ARG
  * before any work.  The first call on each device (made current) looks up the array's
  * device address (and so does the first call after the device's context was
  * made anew, e.g. after cudaDeviceReset); make that first call before any
@@ -385,7 +393,7 @@ typedef struct spsvm_options {
   int32_t  candidates;     /* kappa, points sampled per selection round (0 -> 256) */
   int32_t  add_per_round;  /* q, basis vectors added per round (0 -> 64) */
   int32_t  max_newton;     /* Newton steps per reoptimisation (0 -> 50) */
-  int32_t  precision;      /* SPSVM_FP32 (0) or SPSVM_BF16X4 */
+  int32_t  precision;      /* SPSVM_FP32 (0) or SPSVM_BF16SPLIT */
   double   growth_tol;     /* Section 4 stop: (change in training error rate) /
                               (vectors added) < growth_tol; 0 -> run to budget.
                               Section 5 uses 5e-6. */

@@ -3,7 +3,7 @@ Vector Machines in Practice", Section 4, Eq. 4, as hand-written CUDA behind
 the C ABI of include/spsvm.h.
 
     import paper_1404_1066_gb300 as sp
-    model = sp.spsvm_fit(X, y, gamma, lam, budget, tol, precision="bf16x4")
+    model = sp.spsvm_fit(X, y, gamma, lam, budget, tol, precision="bf16split")
     f = sp.spsvm_predict(model, Xq)
 
 The CUDA library is built in-tree on first use (paper_1404_1066_gb300.build)
@@ -18,4 +18,4 @@ from .api import (  # noqa: F401
     spsvm_solve_lowrank, spsvm_active_diff,
     spsvm_predict_ovo, Server,
 )
-from ._lib import SPSVM_BF16X4, SPSVM_FP32, SpsvmError, load  # noqa: F401
+from ._lib import SPSVM_BF16SPLIT, SPSVM_FP32, SpsvmError, load  # noqa: F401

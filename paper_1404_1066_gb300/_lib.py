@@ -22,14 +22,14 @@ SPSVM_ERR_TIMEOUT = -6
 SPSVM_ERR_BUSY = -7
 
 SPSVM_FP32 = 0
-SPSVM_BF16X4 = 1
+SPSVM_BF16SPLIT = 1
 SPSVM_SOLVE_MIXED = 0
 SPSVM_SOLVE_FP64 = 1
 SPSVM_GROWTH_EPS_PAPER = 5e-6
 SPSVM_SCORE_HEURISTIC = 0
 SPSVM_SCORE_EXACT = 1
 
-PRECISIONS = {"fp32": SPSVM_FP32, "bf16x4": SPSVM_BF16X4}
+PRECISIONS = {"fp32": SPSVM_FP32, "bf16split": SPSVM_BF16SPLIT}
 
 
 class spsvm_kmat(C.Structure):
@@ -41,7 +41,7 @@ class spsvm_kmat(C.Structure):
 class spsvm_points(C.Structure):
     _fields_ = [("X", C.c_void_p), ("n", C.c_int64), ("d", C.c_int64), ("ldx", C.c_int64),
                 ("norms", C.c_void_p), ("hi", C.c_void_p), ("lo", C.c_void_p),
-                ("ldh", C.c_int64)]
+                ("ldh", C.c_int64), ("mid", C.c_void_p)]
 
 
 class spsvm_options(C.Structure):

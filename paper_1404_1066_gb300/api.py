@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from ._lib import (SPSVM_BF16X4, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
+from ._lib import (SPSVM_BF16SPLIT, SPSVM_FP32, check, ptr, stream_ptr,  # noqa: F401
                    spsvm_kmat, spsvm_options, spsvm_points, spsvm_problem, spsvm_step)
 
 
@@ -39,6 +39,7 @@ class Points:
     hi: torch.Tensor | None
     lo: torch.Tensor | None
     ldh: int
+    mid: torch.Tensor | None = None
 
     def struct(self):
         s = spsvm_points()
@@ -49,6 +50,7 @@ class Points:
         s.hi = ptr(self.hi)
         s.lo = ptr(self.lo)
         s.ldh = self.ldh
+        s.mid = ptr(self.mid)
         return s
 
 
@@ -59,11 +61,12 @@ def spsvm_prepare_points(X: torch.Tensor, precision="fp32") -> Points:
     ldh = ((d + 63) // 64) * 64
     p = _prec(precision)
     norms = torch.empty(n, dtype=torch.float32, device=X.device)
-    hi = lo = None
-    if p == SPSVM_BF16X4:
+    hi = mid = lo = None
+    if p == SPSVM_BF16SPLIT:
         hi = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
+        mid = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
         lo = torch.empty((n, ldh), dtype=torch.bfloat16, device=X.device)
-    P = Points(X, norms, hi, lo, ldh)
+    P = Points(X, norms, hi, lo, ldh, mid)
     s = P.struct()
     check(_lib().spsvm_prepare_points(C.byref(s), p, stream_ptr()), "spsvm_prepare_points")
     return P
@@ -91,7 +94,7 @@ class KMat:
         return s
 
     def to_float(self, rows=None):
-        """FP32 copy of rows x n (hi + lo for BF16X4), on the device."""
+        """FP32 copy of rows x n (hi + lo for BF16SPLIT), on the device."""
         r = self.rows if rows is None else rows
         if self.format == SPSVM_FP32:
             return self.buf.view(-1)[: r * self.ld].view(r, self.ld)[:, : self.n].clone()

@@ -37,22 +37,25 @@ int sm_count() {
 
 int check_kmat(const spsvm_kmat* K, const char* what) {
   if (!K || !K->data) return set_error(SPSVM_ERR_ARG, "%s: NULL kernel matrix", what);
-  if (K->format != SPSVM_FP32 && K->format != SPSVM_BF16X4)
+  if (K->format != SPSVM_FP32 && K->format != SPSVM_BF16SPLIT)
     return set_error(SPSVM_ERR_ARG, "%s: bad format %d", what, K->format);
   if (K->n < 0 || K->rows < 0 || K->ld < K->n || (K->ld % 8) != 0)
     return set_error(SPSVM_ERR_ARG, "%s: bad shape n=%lld rows=%lld ld=%lld", what,
                      (long long)K->n, (long long)K->rows, (long long)K->ld);
-  if (K->format == SPSVM_BF16X4 && K->plane < K->rows * K->ld)
+  if (K->format == SPSVM_BF16SPLIT && K->plane < K->rows * K->ld)
     return set_error(SPSVM_ERR_ARG, "%s: hi/lo planes overlap", what);
   if ((reinterpret_cast<uintptr_t>(K->data) & 15) != 0)
     return set_error(SPSVM_ERR_ARG, "%s: data not 16-byte aligned", what);
   return SPSVM_OK;
 }
 
-// One warp per point: ||x_i||^2 in FP64, and the BF16 split of the row.
+// One warp per point: ||x_i||^2 in FP64, and the three-term BF16 split of
+// the row (hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); the
+// differences are exact in FP32).
 __global__ void prepare_points_kernel(const float* __restrict__ X, int64_t n, int64_t d,
                                       int64_t ldx, float* __restrict__ norms,
                                       __nv_bfloat16* __restrict__ hi,
+                                      __nv_bfloat16* __restrict__ mid,
                                       __nv_bfloat16* __restrict__ lo, int64_t ldh) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -67,9 +70,14 @@ __global__ void prepare_points_kernel(const float* __restrict__ X, int64_t n, in
   if (lane == 0) norms[i] = (float)acc;
   if (hi) {
     for (int64_t k = lane; k < ldh; k += 32) {
-      __nv_bfloat16 h = __float2bfloat16_rn(0.0f), l = h;
-      if (k < d) split_bf16(x[k], h, l);
+      __nv_bfloat16 h = __float2bfloat16_rn(0.0f), md = h, l = h;
+      if (k < d) {
+        const float v = x[k];
+        split_bf16(v, h, md);                                  // h, md = bf16(v - h)
+        l = __float2bfloat16_rn((v - __bfloat162float(h)) - __bfloat162float(md));
+      }
       hi[i * ldh + k] = h;
+      mid[i * ldh + k] = md;
       lo[i * ldh + k] = l;
     }
   }
@@ -266,9 +274,10 @@ extern "C" int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* st
   if (p->n < 0 || p->d < 1 || p->ldx < p->d)
     return set_error(SPSVM_ERR_ARG, "prepare_points: bad shape n=%lld d=%lld ldx=%lld",
                      (long long)p->n, (long long)p->d, (long long)p->ldx);
-  if (precision == SPSVM_BF16X4) {
-    if (!p->hi || !p->lo || p->ldh < p->d || (p->ldh % 64) != 0)
-      return set_error(SPSVM_ERR_ARG, "prepare_points: BF16X4 needs hi/lo planes with ldh %% 64 == 0");
+  if (precision == SPSVM_BF16SPLIT) {
+    if (!p->hi || !p->mid || !p->lo || p->ldh < p->d || (p->ldh % 64) != 0)
+      return set_error(SPSVM_ERR_ARG,
+                       "prepare_points: BF16SPLIT needs hi / mid / lo planes with ldh %% 64 == 0");
   } else if (precision != SPSVM_FP32) {
     return set_error(SPSVM_ERR_ARG, "prepare_points: bad precision %d", precision);
   }
@@ -277,8 +286,9 @@ extern "C" int spsvm_prepare_points(spsvm_points* p, int32_t precision, void* st
   dim3 grid((unsigned)ceil_div(p->n, warps));
   prepare_points_kernel<<<grid, warps * 32, 0, as_stream(stream)>>>(
       p->X, p->n, p->d, p->ldx, p->norms,
-      precision == SPSVM_BF16X4 ? reinterpret_cast<__nv_bfloat16*>(p->hi) : nullptr,
-      precision == SPSVM_BF16X4 ? reinterpret_cast<__nv_bfloat16*>(p->lo) : nullptr, p->ldh);
+      precision == SPSVM_BF16SPLIT ? reinterpret_cast<__nv_bfloat16*>(p->hi) : nullptr,
+      precision == SPSVM_BF16SPLIT ? reinterpret_cast<__nv_bfloat16*>(p->mid) : nullptr,
+      precision == SPSVM_BF16SPLIT ? reinterpret_cast<__nv_bfloat16*>(p->lo) : nullptr, p->ldh);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }

@@ -136,7 +136,7 @@ extern "C" int spsvm_decision(const float* B, int64_t m, int64_t ldb, const doub
                               void* stream) {
   if (!B || !beta || !Q || !out || m < 0 || nq < 0 || d < 1 || ldb < d || ldq < d || !(gamma > 0.f))
     return set_error(SPSVM_ERR_ARG, "decision: bad arguments");
-  if (precision != SPSVM_FP32 && precision != SPSVM_BF16X4)
+  if (precision != SPSVM_FP32 && precision != SPSVM_BF16SPLIT)
     return set_error(SPSVM_ERR_ARG, "decision: bad precision");
   if (nq == 0) return SPSVM_OK;
   if (!scratch || scratch_bytes < spsvm_decision_scratch_bytes(nq, m, d))

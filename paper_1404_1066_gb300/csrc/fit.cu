@@ -232,7 +232,7 @@ constexpr int64_t kLowRankMax = 64;
 // ---- workspace layout ------------------------------------------------------
 struct Layout {
   int64_t n, d, ldn, ldh, jcap, kappa, q;
-  size_t off_norms, off_xhi, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
+  size_t off_norms, off_xhi, off_xmid, off_xlo, off_K, off_Kc, off_o, off_u, off_res, off_act0, off_act1,
       off_pos, off_H, off_beta, off_dir, off_g, off_r, off_rhs, off_tmp, off_tmp2, off_ws, off_sv, off_J,
       off_cand,
       off_cg, off_ch, off_cd, off_small, off_scratch, off_chw, off_mix, off_kjj, off_anchor, off_Wt,
@@ -261,8 +261,9 @@ Layout make_layout(int64_t n, int64_t d, int32_t budget, int32_t precision, int3
     return o;
   };
   L.off_norms = take(n * 4);
-  const bool bf = precision == SPSVM_BF16X4;
+  const bool bf = precision == SPSVM_BF16SPLIT;
   L.off_xhi = take(bf ? (size_t)n * L.ldh * 2 : 0);
+  L.off_xmid = take(bf ? (size_t)n * L.ldh * 2 : 0);
   L.off_xlo = take(bf ? (size_t)n * L.ldh * 2 : 0);
   L.kbytes = (size_t)L.jcap * L.ldn * 4;   // FP32, or two BF16 planes
   L.off_K = take(L.kbytes);
@@ -389,7 +390,7 @@ struct Fit {
 
   // K_nJ is stored in FP32 in both forms; the compact copy K_SJ, the Gram
   // matrix's operand, is FP32 for the FP32 form and the hi / lo BF16 planes
-  // of the tensor-core Gram matrix for BF16X4 (same 4 bytes per element)
+  // of the tensor-core Gram matrix for BF16SPLIT (same 4 bytes per element)
   spsvm_kmat kmat() {
     spsvm_kmat K{};
     K.data = ws + L.off_K;
@@ -404,7 +405,7 @@ struct Fit {
     spsvm_kmat K = kmat();
     K.data = ws + L.off_Kc;
     K.n = L.ldn;
-    K.format = op.precision == SPSVM_BF16X4 ? SPSVM_BF16X4 : SPSVM_FP32;
+    K.format = op.precision == SPSVM_BF16SPLIT ? SPSVM_BF16SPLIT : SPSVM_FP32;
     K.plane = (int64_t)L.jcap * L.ldn;
     return K;
   }
@@ -807,8 +808,9 @@ struct Fit {
     pts.ldx = ldx;
     pts.norms = at<float>(L.off_norms);
     pts.ldh = L.ldh;
-    if (op.precision == SPSVM_BF16X4) {
+    if (op.precision == SPSVM_BF16SPLIT) {
       pts.hi = at<uint16_t>(L.off_xhi);
+      pts.mid = at<uint16_t>(L.off_xmid);
       pts.lo = at<uint16_t>(L.off_xlo);
     }
     SPSVM_TRY(spsvm_prepare_points(&pts, op.precision, s));
@@ -968,7 +970,7 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
     return set_error(SPSVM_ERR_ARG, "fit: need gamma > 0, lambda > 0, 1 <= budget <= n, tol >= 0");
   if (n > (int64_t)INT32_MAX) return set_error(SPSVM_ERR_ARG, "fit: n too large");
   Opts op = resolve(opt);
-  if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16X4)
+  if (op.precision != SPSVM_FP32 && op.precision != SPSVM_BF16SPLIT)
     return set_error(SPSVM_ERR_ARG, "fit: bad precision %d", op.precision);
   if (op.bias && op.refine > 0)
     return set_error(SPSVM_ERR_ARG, "fit: refinement sweeps are not available with the bias");

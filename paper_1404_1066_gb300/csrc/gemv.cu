@@ -467,7 +467,7 @@ extern "C" int spsvm_outputs(const spsvm_kmat* K, const double* beta, const floa
     outputs_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta, y,
                                                                   o, active, part, 0);
   else
-    outputs_kernel<SPSVM_BF16X4><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta,
+    outputs_kernel<SPSVM_BF16SPLIT><<<(unsigned)blocks, GV_T, 0, s>>>(view(K), K->rows, K->n, beta,
                                                                     y, o, active, part, 0);
   SPSVM_LAUNCH_CHECK();
   if (stats) {
@@ -488,7 +488,7 @@ extern "C" int spsvm_gemv(const spsvm_kmat* K, const double* v, float* u, int32_
     gemv_kernel<SPSVM_FP32><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
         view(K), K->rows, K->n, v, u, accumulate);
   else
-    gemv_kernel<SPSVM_BF16X4><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
+    gemv_kernel<SPSVM_BF16SPLIT><<<(unsigned)blocks, GV_T, 0, as_stream(stream)>>>(
         view(K), K->rows, K->n, v, u, accumulate);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
@@ -535,7 +535,7 @@ int spsvm::compact_active_impl(const spsvm_kmat* K, const uint8_t* active, const
   if (Kc) {
     SPSVM_TRY(check_kmat(Kc, "compact(out)"));
     // the compact copy keeps K's format, or splits FP32 values into hi / lo planes
-    const bool fmt_ok = Kc->format == K->format || (K->format == SPSVM_FP32 && Kc->format == SPSVM_BF16X4);
+    const bool fmt_ok = Kc->format == K->format || (K->format == SPSVM_FP32 && Kc->format == SPSVM_BF16SPLIT);
     if (!fmt_ok || Kc->rows < K->rows || Kc->n < round_up(K->n, 128))
       return set_error(SPSVM_ERR_ARG, "compact: output matrix too small or wrong format");
   }

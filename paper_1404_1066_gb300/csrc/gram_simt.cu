@@ -235,9 +235,9 @@ int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const
   const size_t need = kjj ? gram_part_bytes(m, ns_max) : spsvm_gram_scratch_bytes(m, ns_max);
   if (!scratch || scratch_bytes < need) return set_error(SPSVM_ERR_OOM, "gram: scratch too small");
   // algorithmic work: one multiply-add per active point per unique entry,
-  // times the four plane products of the BF16X4 form
+  // times the four plane products of the BF16SPLIT form
   ProfScope prof(PROF_GRAM, s,
-                 (precision == SPSVM_BF16X4 ? 4.0 : 1.0) * ns_work * (double)m * (double)(m + 1));
+                 (precision == SPSVM_BF16SPLIT ? 4.0 : 1.0) * ns_work * (double)m * (double)(m + 1));
   const int64_t ldp = round_up(m, 64);
   double* part = static_cast<double*>(scratch);
   if (!kjj) {   // gather K_JJ into the scratch behind the partial sums
@@ -247,8 +247,8 @@ int gram_impl(const spsvm_kmat* Kc, const int64_t* ns_dev, int64_t ns_max, const
     ldk = ldp;
   }
   int64_t splits;
-  if (precision == SPSVM_BF16X4) {
-    if (Kc->format != SPSVM_BF16X4) return set_error(SPSVM_ERR_ARG, "gram: BF16X4 needs split planes");
+  if (precision == SPSVM_BF16SPLIT) {
+    if (Kc->format != SPSVM_BF16SPLIT) return set_error(SPSVM_ERR_ARG, "gram: BF16SPLIT needs split planes");
     splits = gram_tc_splits(m, ns_max);
     SPSVM_TRY(launch_gram_tc(Kc, ns_dev, ns_max, m, part, ldp, splits, s));
   } else if (precision == SPSVM_FP32) {

@@ -2,6 +2,8 @@
 // SPSVM_FP32 form).  RBF kernel of Section 2 through the distance expansion
 // ||x - z||^2 = ||x||^2 + ||z||^2 - 2 x^T z; the basis-vector score of
 // Section 4 ("Basis vector selection") fused into the same tile loop.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace spsvm {
@@ -194,7 +196,7 @@ int launch_kernel_block_simt(const spsvm_points* p, const int64_t* idx, int32_t 
 using namespace spsvm;
 
 extern "C" size_t spsvm_kernel_block_scratch_bytes(int64_t m, int64_t d, int32_t precision) {
-  if (m < 0 || d < 1 || precision != SPSVM_BF16X4) return 0;
+  if (m < 0 || d < 1 || precision != SPSVM_BF16SPLIT) return 0;
   return kernel_block_tc_scratch(m, round_up(d, 64));
 }
 
@@ -208,12 +210,12 @@ extern "C" int spsvm_kernel_block(const spsvm_points* p, const int64_t* idx, int
     return set_error(SPSVM_ERR_ARG, "kernel_block: m=%d row0=%lld rows=%lld n=%lld/%lld gamma=%g",
                      m, (long long)row0, (long long)out->rows, (long long)out->n,
                      (long long)p->n, (double)gamma);
-  // algorithmic work: 2 n m d multiply-adds, times the four products of the split form
+  // algorithmic work: 2 n m d multiply-adds, times the six products of the split form
   ProfScope prof(PROF_KERNEL_BLOCK, as_stream(stream),
-                 (precision == SPSVM_BF16X4 ? 8.0 : 2.0) * (double)p->n * m * (double)p->d);
-  if (precision == SPSVM_BF16X4) {
-    if (!p->hi || !p->lo)
-      return set_error(SPSVM_ERR_ARG, "kernel_block: BF16X4 needs the split planes of the points");
+                 (precision == SPSVM_BF16SPLIT ? 12.0 : 2.0) * (double)p->n * m * (double)p->d);
+  if (precision == SPSVM_BF16SPLIT) {
+    if (!p->hi || !p->mid || !p->lo)
+      return set_error(SPSVM_ERR_ARG, "kernel_block: BF16SPLIT needs the split planes of the points");
     return launch_kernel_block_tc(p, idx, m, gamma, out, row0, scratch, scratch_bytes,
                                   as_stream(stream));
   }
@@ -230,7 +232,9 @@ namespace {
 // per-tile partial sums (tiles of 128 points in both forms), then room for
 // the gathered candidate rows of the tensor-core form
 size_t score_part_bytes(int64_t n, int32_t kappa) {
-  return (size_t)round_up(ceil_div(n, TM) * (int64_t)kappa * (int64_t)sizeof(double2), 256);
+  // the larger of the two forms' tile counts (both tile 128 points today)
+  const int64_t tiles = std::max<int64_t>(ceil_div(n, TM), score_tc_tiles(n));
+  return (size_t)round_up(tiles * (int64_t)kappa * (int64_t)sizeof(double2), 256);
 }
 }  // namespace
 }  // namespace spsvm
@@ -254,11 +258,12 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
   if (scratch_bytes < need || !scratch)
     return set_error(SPSVM_ERR_OOM, "score_candidates: scratch %zu < %zu", scratch_bytes, need);
   cudaStream_t s = as_stream(stream);
-  ProfScope prof(PROF_SCORE, s, (precision == SPSVM_BF16X4 ? 8.0 : 2.0) * (double)p->n * kappa * (double)p->d);
+  ProfScope prof(PROF_SCORE, s, (precision == SPSVM_BF16SPLIT ? 12.0 : 2.0) * (double)p->n * kappa * (double)p->d);
   double2* part = static_cast<double2*>(scratch);
   int64_t tiles = ceil_div(p->n, TM);
-  if (precision == SPSVM_BF16X4) {
-    if (!p->hi || !p->lo) return set_error(SPSVM_ERR_ARG, "score_candidates: BF16X4 needs split planes");
+  if (precision == SPSVM_BF16SPLIT) {
+    if (!p->hi || !p->mid || !p->lo)
+      return set_error(SPSVM_ERR_ARG, "score_candidates: BF16SPLIT needs split planes");
     tiles = score_tc_tiles(p->n);
     const size_t pb = score_part_bytes(p->n, kappa);
     SPSVM_TRY(launch_score_tc(p, y, o, idx, kappa, gamma, part, tiles,
@@ -290,7 +295,8 @@ extern "C" int spsvm_score_candidates(const spsvm_points* p, const float* y, con
 
 namespace spsvm {
 namespace {
-// 16 MiB: enough for n = 500,000 points and 256 candidates in either form.
+// 16 MiB: enough for n = 500,000 points and 256 candidates in either form
+// (16.2 MB of per-tile partial sums and gathered candidate rows).
 constexpr size_t kScoreScratchMax = size_t(16) << 20;
 // Held by every GPU that loads this library until the process exits.
 __device__ __align__(256) unsigned char g_score_scratch[kScoreScratchMax];

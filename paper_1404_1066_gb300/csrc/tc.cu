@@ -1,4 +1,4 @@
-// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16X4 form.  Every
+// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16SPLIT form.  Every
 // FP32 operand x is split as hi + lo (both BF16, lo = bf16(x - hi)) and a
 // product x*z is formed as hi*hi + hi*lo + lo*hi + lo*lo (four BF16 MMAs
 // accumulating in FP32 in TMEM): the exact product of the two-term
@@ -37,27 +37,37 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // Kernel block / scores, persistent and warp-specialised.  D[c][i] = z_c . x_i
 // over tiles of 128 basis (or candidate) rows c (MMA M; the rows gathered
 // beforehand into contiguous BF16 planes Z) by 128 points i (MMA N), both
-// operands streamed by TMA through a 2-stage shared-memory ring.  Warp 0
-// issues the TMA loads, warp 1 the MMAs into one of two TMEM accumulators,
-// warps 2-9 drain the other accumulator (TMEM lane c = row c; warps w and
-// w + 4 share a lane quarter and split the 128 columns), so the epilogue of
-// one tile overlaps the MMAs of the next.  Tiles are ordered point-tile
-// major so the CTAs in flight share their X tiles through L2.
+// operands streamed by TMA through a 3-stage shared-memory ring (32-element
+// K slices, 64-byte swizzle) holding the three planes of each (x = hi + mid
+// + lo, exact for FP32) and multiplied as the six products hi hi, hi mid,
+// mid hi, mid mid, hi lo, lo hi (the three dropped ones are below 2^-24 of
+// |x z|), hi hi into one TMEM accumulator and the rest into a second (the
+// FP32 accumulation's rounding grows with the MMAs a sum takes, and only the
+// few large-term ones then count).  Warp 0 issues the TMA loads, warp 1 the
+// MMAs into one of two tile buffers, warps 2-9 drain the other (TMEM lane c =
+// row c; warps w and w + 4 share a lane quarter and split the 128 columns),
+// so the epilogue of one tile overlaps the MMAs of the next.  Tiles are ordered point-tile major so the CTAs in flight share their
+// X tiles through L2.
 // ---------------------------------------------------------------------------
 constexpr int PK_M = 128;
 constexpr int PK_N = 128;
-constexpr int PK_STAGES = 2;
-constexpr int PK_PLANE_A = PK_M * 128;                     // 16 KB: 128 rows x 64 BF16
-constexpr int PK_PLANE_B = PK_N * 128;
-constexpr int PK_STAGE = 2 * PK_PLANE_A + 2 * PK_PLANE_B;  // 64 KB
+constexpr int PK_KC = 32;                                  // K elements per stage (64-byte rows)
+constexpr int PK_WP = PK_N / 2;                            // points per epilogue warp
+constexpr int PK_ACC_COLS = 2 * PK_N;                      // TMEM per tile: large + small terms
+constexpr int PK_STAGES = 3;
+constexpr int PK_PLANE_A = PK_M * PK_KC * 2;               // 8 KB: 128 rows x 32 BF16
+constexpr int PK_PLANE_B = PK_N * PK_KC * 2;               // 8 KB
+constexpr int PK_STAGE = 3 * PK_PLANE_A + 3 * PK_PLANE_B;  // 48 KB
 constexpr int PK_EPI_WARPS = 8;
 constexpr int PK_THREADS = 32 * (2 + PK_EPI_WARPS);
-constexpr int PK_OUT_BOX = 32 * 128;                       // 32 rows x 128 bytes
+constexpr int PK_OUT_BOX = 32 * 128;                       // 32 rows x 32 FP32
 constexpr int PK_OUT_OFF = PK_STAGES * PK_STAGE;           // per epilogue warp: two boxes
 constexpr int PK_BAR_OFF = PK_OUT_OFF + PK_EPI_WARPS * 2 * PK_OUT_BOX;
 constexpr int PK_RED_OFF = PK_BAR_OFF + 256;
 constexpr int PK_STAGE_OFF = PK_RED_OFF + 4 * 32 * 8;      // per epilogue warp: 3 x 64 floats
-constexpr int PK_SMEM = PK_STAGE_OFF + PK_EPI_WARPS * 192 * 4 + 1024;   // + alignment slack
+constexpr int PK_SMEM = PK_STAGE_OFF + PK_EPI_WARPS * 3 * PK_WP * 4 + 1024;   // + alignment slack
+static_assert(PK_SMEM <= 227 * 1024, "kernel block shared memory");
+static_assert(2 * PK_ACC_COLS <= 512, "two tiles of two accumulators fit TMEM");
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
   asm volatile(
@@ -80,9 +90,9 @@ __device__ __forceinline__ void bulk_wait_all() {
 // Tile order: groups of PK_GROUP consecutive point tiles, each group swept
 // over all basis blocks with the point tile varying fastest.  The CTAs in
 // flight then share a few X tiles through L2 while each basis row receives
-// PK_GROUP x 256 contiguous bytes per plane, so the kernel-matrix writes
-// reach DRAM in long runs.
-constexpr int64_t PK_GROUP = 16;
+// PK_GROUP x 256 contiguous bytes, so the kernel-matrix writes reach DRAM in
+// long runs.
+constexpr int64_t PK_GROUP = 32;
 __device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT, int& cb,
                                             int64_t& pt) {
   const int64_t per = nCB * PK_GROUP;
@@ -93,18 +103,19 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT,
   pt = g0 + r % gw;
 }
 
-// Epilogue modes: store FP32 kernel values, store them as hi / lo BF16
-// planes, or reduce the candidate-score sums.
-enum KbMode { KB_STORE_F32 = 0, KB_STORE_PLANES = 1, KB_SCORE = 2 };
+// Epilogue modes: store the FP32 kernel values, or reduce the
+// candidate-score sums without storing them.
+enum KbMode { KB_STORE_F32 = 0, KB_SCORE = 2 };
 
 template <int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
-    const __grid_constant__ CUtensorMap map_zhi, const __grid_constant__ CUtensorMap map_zlo,
-    const __grid_constant__ CUtensorMap map_xhi, const __grid_constant__ CUtensorMap map_xlo,
-    const __grid_constant__ CUtensorMap map_ohi, const __grid_constant__ CUtensorMap map_olo,
-    int64_t ldh, int64_t n, int32_t m, const float* __restrict__ norms,
-    const int64_t* __restrict__ idx, float gamma, int64_t row0, const float* __restrict__ y,
-    const float* __restrict__ o, double2* __restrict__ part, int32_t kappa, WaitCtx wc) {
+    const __grid_constant__ CUtensorMap map_zhi, const __grid_constant__ CUtensorMap map_zmid,
+    const __grid_constant__ CUtensorMap map_zlo, const __grid_constant__ CUtensorMap map_xhi,
+    const __grid_constant__ CUtensorMap map_xmid, const __grid_constant__ CUtensorMap map_xlo,
+    const __grid_constant__ CUtensorMap map_out, int64_t ldh, int64_t n, int32_t m,
+    const float* __restrict__ norms, const int64_t* __restrict__ idx, float gamma, int64_t row0,
+    const float* __restrict__ y, const float* __restrict__ o, double2* __restrict__ part,
+    int32_t kappa, WaitCtx wc) {
   constexpr bool SCORE = MODE == KB_SCORE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -122,7 +133,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
   const int64_t nCB = ceil_div((int64_t)m, (int64_t)PK_M);
   const int64_t nPT = ceil_div(n, (int64_t)PK_N);
   const int64_t T = nCB * nPT;
-  const int nK = (int)(ldh / 64);
+  const int nK = (int)(ldh / PK_KC);
   constexpr uint32_t IDESC = idesc_bf16_f32(PK_M, PK_N);
 
   if (tid == 0) {
@@ -140,15 +151,14 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     }
     fence_barrier_init();
     prefetch_tmap(&map_zhi);
+    prefetch_tmap(&map_zmid);
     prefetch_tmap(&map_zlo);
     prefetch_tmap(&map_xhi);
+    prefetch_tmap(&map_xmid);
     prefetch_tmap(&map_xlo);
-    if (!SCORE) {
-      prefetch_tmap(&map_ohi);
-      prefetch_tmap(&map_olo);
-    }
+    if (!SCORE) prefetch_tmap(&map_out);
   }
-  if (warp == 0) tmem_alloc(tmem_slot, 2 * PK_N);
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * PK_ACC_COLS);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -171,11 +181,14 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
             break;
           }
           uint8_t* st = smem + s * PK_STAGE;
+          uint8_t* sb = st + 3 * PK_PLANE_A;
           mbar_expect_tx(&full[s], PK_STAGE);
-          tma_load_2d(st, &map_zhi, kc * 64, cb * PK_M, &full[s]);
-          tma_load_2d(st + PK_PLANE_A, &map_zlo, kc * 64, cb * PK_M, &full[s]);
-          tma_load_2d(st + 2 * PK_PLANE_A, &map_xhi, kc * 64, pt * PK_N, &full[s]);
-          tma_load_2d(st + 2 * PK_PLANE_A + PK_PLANE_B, &map_xlo, kc * 64, pt * PK_N, &full[s]);
+          tma_load_2d(st, &map_zhi, kc * PK_KC, cb * PK_M, &full[s]);
+          tma_load_2d(st + PK_PLANE_A, &map_zmid, kc * PK_KC, cb * PK_M, &full[s]);
+          tma_load_2d(st + 2 * PK_PLANE_A, &map_zlo, kc * PK_KC, cb * PK_M, &full[s]);
+          tma_load_2d(sb, &map_xhi, kc * PK_KC, (int)(pt * PK_N), &full[s]);
+          tma_load_2d(sb + PK_PLANE_B, &map_xmid, kc * PK_KC, (int)(pt * PK_N), &full[s]);
+          tma_load_2d(sb + 2 * PK_PLANE_B, &map_xlo, kc * PK_KC, (int)(pt * PK_N), &full[s]);
         }
       }
       // no copy may be in flight when the block exits
@@ -191,7 +204,11 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
         const int acc = (int)(j & 1);
         if (!mbar_wait(&tempty[acc], (uint32_t)(((j >> 1) & 1) ^ 1), wc.st, 23, wc.lim)) break;
         fence_after_sync();
-        const uint32_t d = tmem + acc * PK_N;
+        // hi hi products in one accumulator, the five smaller ones (2^-8 and
+        // below) in another: the FP32 accumulation's rounding then grows with
+        // the few large-term MMAs only
+        const uint32_t d_big = tmem + acc * PK_ACC_COLS;
+        const uint32_t d_small = d_big + PK_N;
         for (int kc = 0; kc < nK; ++kc, ++q) {
           const int s = (int)(q % PK_STAGES);
           const uint32_t ph = (uint32_t)((q / PK_STAGES) & 1);
@@ -201,16 +218,19 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
           }
           fence_after_sync();
           const uint32_t base = smem_u32(smem + s * PK_STAGE);
-          const uint32_t a_hi = base, a_lo = base + PK_PLANE_A;
-          const uint32_t b_hi = base + 2 * PK_PLANE_A, b_lo = b_hi + PK_PLANE_B;
+          const uint32_t a_hi = base, a_mid = base + PK_PLANE_A, a_lo = base + 2 * PK_PLANE_A;
+          const uint32_t b_hi = base + 3 * PK_PLANE_A, b_mid = b_hi + PK_PLANE_B,
+                         b_lo = b_hi + 2 * PK_PLANE_B;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < PK_KC / 16; ++k) {
             const uint32_t koff = k * 32;
-            mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_hi + koff), IDESC,
-                     (kc | k) != 0 ? 1u : 0u);
-            mma_bf16(d, desc_sw128(a_hi + koff), desc_sw128(b_lo + koff), IDESC, 1u);
-            mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_hi + koff), IDESC, 1u);
-            mma_bf16(d, desc_sw128(a_lo + koff), desc_sw128(b_lo + koff), IDESC, 1u);
+            const uint32_t first = (kc | k) != 0 ? 1u : 0u;
+            mma_bf16(d_small, desc_sw64(a_lo + koff), desc_sw64(b_hi + koff), IDESC, first);
+            mma_bf16(d_small, desc_sw64(a_hi + koff), desc_sw64(b_lo + koff), IDESC, 1u);
+            mma_bf16(d_small, desc_sw64(a_mid + koff), desc_sw64(b_mid + koff), IDESC, 1u);
+            mma_bf16(d_small, desc_sw64(a_mid + koff), desc_sw64(b_hi + koff), IDESC, 1u);
+            mma_bf16(d_small, desc_sw64(a_hi + koff), desc_sw64(b_mid + koff), IDESC, 1u);
+            mma_bf16(d_big, desc_sw64(a_hi + koff), desc_sw64(b_hi + koff), IDESC, first);
           }
           mma_commit(&empty[s]);
         }
@@ -218,12 +238,12 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       }
     }
   } else {
-    // ---- epilogue
+    // ---- epilogue: warp w drains lane quarter w % 4, points half * 64 ..
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     const int c_in = 32 * quarter + lane;
     const float g2 = gamma * 1.4426950408889634f;   // K = 2^(-g2 |x - z|^2)
-    float* stage = reinterpret_cast<float*>(smem + PK_STAGE_OFF) + (warp - 2) * 192;
+    float* stage = reinterpret_cast<float*>(smem + PK_STAGE_OFF) + (warp - 2) * 3 * PK_WP;
     uint8_t* obox = smem + PK_OUT_OFF + (warp - 2) * 2 * PK_OUT_BOX;
     int64_t j = 0;
     for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++j) {
@@ -233,10 +253,10 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       const int64_t c = (int64_t)cb * PK_M + c_in;
       const bool crow = c < m;
       const float zn = crow ? norms[idx[c]] : 0.f;
-      const int64_t ib = pt * PK_N + half * 64;
-      const int64_t npts = min64(64, n - ib);
+      const int64_t ib = pt * PK_N + half * PK_WP;
+      const int64_t npts = min64(PK_WP, n - ib);
       // this warp's 64 points: norms (and for scores the active residual / flag)
-      for (int h2 = 0; h2 < 2; ++h2) {
+      for (int h2 = 0; h2 < PK_WP / 32; ++h2) {
         const int jj = h2 * 32 + lane;
         const int64_t i = ib + jj;
         const bool in = jj < npts;
@@ -250,8 +270,8 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
               a = 1.f;
             }
           }
-          stage[64 + jj] = r;
-          stage[128 + jj] = a;
+          stage[PK_WP + jj] = r;
+          stage[2 * PK_WP + jj] = a;
         }
       }
       __syncwarp();
@@ -259,17 +279,20 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       if (!mbar_wait(&tfull[acc], (uint32_t)((j >> 1) & 1), wc.st, 25, wc.lim)) break;
       fence_after_sync();
       float gs = 0.f, hs = 0.f;
-      const uint32_t tb = tmem + acc * PK_N + half * 64 + ((uint32_t)(32 * quarter) << 16);
+      const uint32_t tb = tmem + acc * PK_ACC_COLS + half * PK_WP + ((uint32_t)(32 * quarter) << 16);
       if (!SCORE) {
         // the previous tile's boxes must have been read out before they are rewritten
         if (lane == 0) bulk_wait_read();
         __syncwarp();
       }
       const float zz = -g2 * zn;
-      for (int cc = 0; cc < 2; ++cc) {
+      for (int cc = 0; cc < PK_WP / 32; ++cc) {
         if (cc * 32 >= npts) break;   // uniform per warp
-        float v[32];
+        float v[32], w[32];
         tmem_ld32(tb + cc * 32, v);
+        tmem_ld32(tb + PK_N + cc * 32, w);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) v[jj] += w[jj];   // x.z = large terms + small terms
         // arg = -g2 * max(|x|^2 + |z|^2 - 2 x.z, 0); points past n carry zero
         // norms here and are clipped by the store or weighted by zero flags
 #pragma unroll
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
           v[jj + 2] = ex2_approx(fminf(fmaf(-g2, x4.z, fmaf(2.0f * g2, v[jj + 2], zz)), 0.0f));
           v[jj + 3] = ex2_approx(fminf(fmaf(-g2, x4.w, fmaf(2.0f * g2, v[jj + 3], zz)), 0.0f));
         }
-        if (MODE == KB_STORE_F32) {
+        if (!SCORE) {
           // 32 FP32 values into box cc of this warp (row = lane, 128-byte
           // swizzle: 16-byte chunk ch of row r at chunk ch ^ (r & 7))
           uint8_t* bx = obox + cc * PK_OUT_BOX;
@@ -290,33 +313,12 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
             *reinterpret_cast<float4*>(bx + so) =
                 make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
           }
-        } else if (MODE == KB_STORE_PLANES) {
-          // hi / lo into this warp's swizzled output boxes (row = lane)
-          uint8_t* bh = obox;
-          uint8_t* bl = obox + PK_OUT_BOX;
-#pragma unroll
-          for (int qd = 0; qd < 4; ++qd) {
-            uint32_t wh[4], wl[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float a0 = v[8 * qd + 2 * u], a1 = v[8 * qd + 2 * u + 1];
-              const __nv_bfloat162 h2v = __floats2bfloat162_rn(a0, a1);
-              const float2 hf = __bfloat1622float2(h2v);
-              const __nv_bfloat162 l2v = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
-              wh[u] = *reinterpret_cast<const uint32_t*>(&h2v);
-              wl[u] = *reinterpret_cast<const uint32_t*>(&l2v);
-            }
-            const int ch = cc * 4 + qd;   // 16-byte chunk of the 128-byte box row
-            const int so = lane * 128 + ((ch ^ (lane & 7)) << 4);
-            *reinterpret_cast<uint4*>(bh + so) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-            *reinterpret_cast<uint4*>(bl + so) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-          }
         } else {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
             const float kv = v[jj];
-            gs = fmaf(stage[64 + cc * 32 + jj], kv, gs);
-            hs = fmaf(stage[128 + cc * 32 + jj] * kv, kv, hs);
+            gs = fmaf(stage[PK_WP + cc * 32 + jj], kv, gs);
+            hs = fmaf(stage[2 * PK_WP + cc * 32 + jj] * kv, kv, hs);
           }
         }
       }
@@ -327,14 +329,9 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
         __syncwarp();
         if (lane == 0) {
           const int x = (int)ib, yrow = (int)(row0 + (int64_t)cb * PK_M + 32 * quarter);
-          if (MODE == KB_STORE_F32) {
-            // boxes of 32 points; the second starts past n only when npts <= 32
-            tma_store_2d(&map_ohi, x, yrow, obox);
-            if (npts > 32) tma_store_2d(&map_ohi, x + 32, yrow, obox + PK_OUT_BOX);
-          } else {
-            tma_store_2d(&map_ohi, x, yrow, obox);
-            tma_store_2d(&map_olo, x, yrow, obox + PK_OUT_BOX);
-          }
+          // boxes of 32 points; the second starts past n only when npts <= 32
+          tma_store_2d(&map_out, x, yrow, obox);
+          if (npts > 32) tma_store_2d(&map_out, x + 32, yrow, obox + PK_OUT_BOX);
           bulk_commit();
         }
       }
@@ -362,26 +359,29 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
   if (warp == 0) {
     __syncwarp();
     fence_after_sync();
-    tmem_dealloc(tmem, 2 * PK_N);
+    tmem_dealloc(tmem, 2 * PK_ACC_COLS);
   }
 }
 
-// Z planes: rows idx[0..m) of the split X planes, zero rows up to m_pad.
-__global__ void gather_rows_bf16(const uint16_t* __restrict__ Xhi, const uint16_t* __restrict__ Xlo,
-                                 int64_t ldh, const int64_t* __restrict__ idx, int32_t m,
-                                 int64_t m_pad, uint16_t* __restrict__ Zhi,
+// Z planes: rows idx[0..m) of the three split X planes, zero rows up to m_pad.
+__global__ void gather_rows_bf16(const uint16_t* __restrict__ Xhi, const uint16_t* __restrict__ Xmid,
+                                 const uint16_t* __restrict__ Xlo, int64_t ldh,
+                                 const int64_t* __restrict__ idx, int32_t m, int64_t m_pad,
+                                 uint16_t* __restrict__ Zhi, uint16_t* __restrict__ Zmid,
                                  uint16_t* __restrict__ Zlo) {
   const int64_t chunks = ldh / 8;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m_pad * chunks) return;
   const int64_t r = e / chunks, ch = e % chunks;
-  uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
+  uint4 vh = make_uint4(0, 0, 0, 0), vm = vh, vl = vh;
   if (r < m) {
     const int64_t src = idx[r] * ldh + ch * 8;
     vh = *reinterpret_cast<const uint4*>(Xhi + src);
+    vm = *reinterpret_cast<const uint4*>(Xmid + src);
     vl = *reinterpret_cast<const uint4*>(Xlo + src);
   }
   *reinterpret_cast<uint4*>(Zhi + r * ldh + ch * 8) = vh;
+  *reinterpret_cast<uint4*>(Zmid + r * ldh + ch * 8) = vm;
   *reinterpret_cast<uint4*>(Zlo + r * ldh + ch * 8) = vl;
 }
 
@@ -572,15 +572,18 @@ int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, in
   auto fn = encode_fn();
   if (!fn) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int64_t esz = f32 ? 4 : 2;
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * esz) % 16 || box_inner * esz != 128)
-    return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned, or box row not 128 bytes");
+  const int64_t row_bytes = box_inner * esz;   // 128-byte rows swizzled by 128, 64-byte rows by 64
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_elems * esz) % 16 ||
+      (row_bytes != 128 && row_bytes != 64))
+    return set_error(SPSVM_ERR_ARG, "tensor map: base or pitch not 16-byte aligned, or box row not 64/128 bytes");
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)(rows > 0 ? rows : 1)};
   cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * esz)};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                   const_cast<void*>(base), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SPSVM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SPSVM_OK;
@@ -588,42 +591,36 @@ int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, in
 
 template <int MODE>
 int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, void* out,
-              int64_t ld, int64_t plane, int64_t row0, const float* y, const float* o,
-              double2* part, int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s) {
+              int64_t ld, int64_t row0, const float* y, const float* o, double2* part,
+              int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s) {
   const int64_t m_pad = round_up(m, (int64_t)PK_M);
-  if (!zbuf || zbytes < (size_t)(m_pad * p->ldh * 4))
-    return set_error(SPSVM_ERR_OOM, "BF16X4 kernel block: scratch too small for the gathered rows");
+  if (!zbuf || zbytes < (size_t)(m_pad * p->ldh * 6))
+    return set_error(SPSVM_ERR_OOM, "BF16SPLIT kernel block: scratch too small for the gathered rows");
   uint16_t* zhi = static_cast<uint16_t*>(zbuf);
-  uint16_t* zlo = zhi + m_pad * p->ldh;
+  uint16_t* zmid = zhi + m_pad * p->ldh;
+  uint16_t* zlo = zmid + m_pad * p->ldh;
   const int64_t work = m_pad * (p->ldh / 8);
   gather_rows_bf16<<<(unsigned)ceil_div(work, (int64_t)256), 256, 0, s>>>(
-      p->hi, p->lo, p->ldh, idx, m, m_pad, zhi, zlo);
+      p->hi, p->mid, p->lo, p->ldh, idx, m, m_pad, zhi, zmid, zlo);
   SPSVM_LAUNCH_CHECK();
-  CUtensorMap mzh, mzl, mxh, mxl, moh, mol;
-  SPSVM_TRY(make_map(&mzh, zhi, p->ldh, m_pad, p->ldh, PK_M, 64));
-  SPSVM_TRY(make_map(&mzl, zlo, p->ldh, m_pad, p->ldh, PK_M, 64));
-  SPSVM_TRY(make_map(&mxh, p->hi, p->ldh, p->n, p->ldh, PK_N, 64));
-  SPSVM_TRY(make_map(&mxl, p->lo, p->ldh, p->n, p->ldh, PK_N, 64));
+  CUtensorMap mzh, mzm, mzl, mxh, mxm, mxl, mo;
+  SPSVM_TRY(make_map(&mzh, zhi, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mzm, zmid, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mzl, zlo, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mxh, p->hi, p->ldh, p->n, p->ldh, PK_N, PK_KC));
+  SPSVM_TRY(make_map(&mxm, p->mid, p->ldh, p->n, p->ldh, PK_N, PK_KC));
+  SPSVM_TRY(make_map(&mxl, p->lo, p->ldh, p->n, p->ldh, PK_N, PK_KC));
   // output rows [0, row0 + m): rows past the basis block are clipped, never written
-  if (MODE == KB_STORE_F32) {
-    SPSVM_TRY(make_map(&moh, out, p->n, row0 + m, ld, 32, 32, true));
-    mol = moh;
-  } else if (MODE == KB_STORE_PLANES) {
-    uint16_t* o16 = static_cast<uint16_t*>(out);
-    SPSVM_TRY(make_map(&moh, o16, p->n, row0 + m, ld, 32, 64));
-    SPSVM_TRY(make_map(&mol, o16 + plane, p->n, row0 + m, ld, 32, 64));
-  } else {
-    moh = mxh;
-    mol = mxl;
-  }
+  if (MODE == KB_STORE_F32) SPSVM_TRY(make_map(&mo, out, p->n, row0 + m, ld, 32, 32, true));
+  else mo = mxh;
   auto kern = kblock_tc_kernel<MODE>;
   SPSVM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM));
   const int64_t tiles = ceil_div((int64_t)m, (int64_t)PK_M) * ceil_div(p->n, (int64_t)PK_N);
   const int grid = (int)min64(tiles, (int64_t)sm_count());
   WaitCtx wc;
   SPSVM_TRY(wait_ctx(s, &wc));
-  kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzl, mxh, mxl, moh, mol, p->ldh, p->n, m, p->norms,
-                                         idx, gamma, row0, y, o, part, kappa, wc);
+  kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzm, mzl, mxh, mxm, mxl, mo, p->ldh, p->n, m,
+                                         p->norms, idx, gamma, row0, y, o, part, kappa, wc);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -633,20 +630,17 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
 bool tc_available() { return encode_fn() != nullptr; }
 
 size_t kernel_block_tc_scratch(int64_t m, int64_t ldh) {
-  return (size_t)(round_up(m, (int64_t)PK_M) * ldh * 4);
+  return (size_t)(round_up(m, (int64_t)PK_M) * ldh * 6);   // three BF16 planes of the rows
 }
 
 int launch_kernel_block_tc(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
                            spsvm_kmat* out, int64_t row0, void* scratch, size_t scratch_bytes,
                            cudaStream_t s) {
   if (m == 0 || p->n == 0) return SPSVM_OK;
-  if ((out->ld % 8) != 0 || (out->format == SPSVM_BF16X4 && (out->plane % 8) != 0))
-    return set_error(SPSVM_ERR_ARG, "BF16X4 kernel block: needs ld %% 8 == 0 (and plane %% 8 == 0)");
-  if (out->format == SPSVM_FP32)
-    return launch_kb<KB_STORE_F32>(p, idx, m, gamma, out->data, out->ld, 0, row0, nullptr, nullptr,
-                                   nullptr, 0, scratch, scratch_bytes, s);
-  return launch_kb<KB_STORE_PLANES>(p, idx, m, gamma, out->data, out->ld, out->plane, row0, nullptr,
-                                    nullptr, nullptr, 0, scratch, scratch_bytes, s);
+  if (out->format != SPSVM_FP32 || (out->ld % 8) != 0)
+    return set_error(SPSVM_ERR_ARG, "BF16SPLIT kernel block: stores FP32 (ld %% 8 == 0)");
+  return launch_kb<KB_STORE_F32>(p, idx, m, gamma, out->data, out->ld, row0, nullptr, nullptr,
+                                 nullptr, 0, scratch, scratch_bytes, s);
 }
 
 int64_t score_tc_tiles(int64_t n) { return ceil_div(n, (int64_t)PK_N); }
@@ -655,7 +649,7 @@ int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const
                     int32_t kappa, float gamma, double2* part, int64_t tiles, void* zbuf,
                     size_t zbytes, cudaStream_t s) {
   (void)tiles;
-  return launch_kb<KB_SCORE>(p, idx, kappa, gamma, nullptr, 0, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
+  return launch_kb<KB_SCORE>(p, idx, kappa, gamma, nullptr, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
 }
 
 int64_t gram_tc_splits(int64_t m, int64_t ns_max) {

@@ -116,6 +116,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// The same for the 64-byte swizzled layout: rows of 32 BF16 (64 bytes),
+// 8-row groups 512 bytes apart; tile base 512-byte aligned.  Advancing along
+// K by 16 elements adds 32 bytes to the start address.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)4 << 61;              // 64-byte swizzle
+  return d;
+}
+
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte
 // swizzled layout: rows of 64 BF16 (128 bytes), 8-row groups 1024 bytes
 // apart; the tile base must be 1024-byte aligned.  Advancing along K by 16

@@ -33,7 +33,7 @@ def _grid(n=8000, d=32, count=6, seed=21):
     return base.X, probs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_batched_equals_alone(sp, prec):
     X, probs = _grid()
     Xd = torch.from_numpy(X).cuda()

@@ -109,7 +109,7 @@ def _replayed_fit(sp, p, prec, budget, kappa, q, seed, replay_rtol, **kw):
     return m, r, J, beta
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_growth_replay_headline_tolerance(sp, prec):
     """The benchmark workload's generator (10-component mixture, d = 128,
     gamma = 1/d, lambda = 1e-4) at n = 20,000 grown to |J| = 512 from 256
@@ -118,7 +118,7 @@ def test_growth_replay_headline_tolerance(sp, prec):
     form: decision values of the model (on the training points and on fresh
     points of the mixture) within 1e-4 max(1, |f|), ||dbeta|| <= 1e-4
     ||beta||, and active sets equal except for margin ties (|1 - y o| within
-    1e-5 for FP32; 1e-3 for BF16X4, whose training outputs come from the
+    1e-5 for FP32; 1e-3 for BF16SPLIT, whose training outputs come from the
     stored hi + lo kernel planes, each value rounded to 2^-17 relative)."""
     p = synth.gaussian_mixture(n=20000, d=128, budget=512, seed=1103, lam=1e-4)
     m, r, J, beta = _replayed_fit(sp, p, prec, 512, 256, 64, 31,
@@ -173,7 +173,7 @@ def test_growth_replay_exact_score(sp):
     _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
 
 
-@pytest.mark.parametrize("prec,score", [("fp32", "heuristic"), ("bf16x4", "heuristic"),
+@pytest.mark.parametrize("prec,score", [("fp32", "heuristic"), ("bf16split", "heuristic"),
                                         ("fp32", "exact")])
 def test_growth_replay_with_bias(sp, prec, score):
     """Eq. 4's bias b as an unregularised coordinate on unbalanced labels (one
@@ -197,10 +197,10 @@ def test_growth_replay_with_bias(sp, prec, score):
     assert abs(r.bias) > 1e-2   # the labels need the bias
     assert abs(b - r.bias) <= (1e-4 if prec == "fp32" else 1e-3) * max(1.0, abs(r.bias))
     o = m.outputs(len(p.y))
-    # training outputs from the stored kernel matrix: BF16X4's hi + lo values
+    # training outputs from the stored kernel matrix: BF16SPLIT's hi + lo values
     # carry ~1e-5 relative error, so its outputs get the looser bound and tie
-    # band the other BF16X4 comparisons use
-    bf = prec == "bf16x4"
+    # band the other BF16SPLIT comparisons use
+    bf = prec == "bf16split"
     _cmp_decisions(o, r.o, rtol=5e-4 if bf else 1e-4)
     _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64), band=1e-3 if bf else 1e-5)
     Xq = synth.queries_like(p, 300, seed=4)
@@ -273,12 +273,12 @@ def test_fit_argument_errors(sp):
         sp.spsvm_fit(X, y, 1.0, 1e-3, 5, initial_basis=[1, 1], fixed_basis=True)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_smooth_kernel_small_lambda_reaches_oracle_minimum(sp, prec):
     """gamma = 0.25/d, lambda = 1e-5 on a nearly separable mixture: after the
     first step the active set holds a few points and H ~ lambda K_JJ has
     relative smallest eigenvalue ~5e-7, under the rounding level of K in
-    BF16X4 (and near that of FP32), so the computed H can be indefinite and
+    BF16SPLIT (and near that of FP32), so the computed H can be indefinite and
     the diagonal jitter schedule must carry the fit.  beta is then
     ill-determined but the objective is not: the float64 objective at the
     GPU beta must reach the oracle's minimum on the same basis."""
@@ -301,11 +301,11 @@ def test_smooth_kernel_small_lambda_reaches_oracle_minimum(sp, prec):
     f_orc = O.objective(r.beta, K, K[J0], yd, lam)
     levels = sorted({h["jitter"] for h in mdl.history()})
     assert f_orc * (1 - 1e-9) <= f_gpu <= f_orc * (1 + 1e-3), (f_gpu, f_orc, levels)
-    if prec == "bf16x4":
+    if prec == "bf16split":
         assert max(levels) >= 0, levels
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_mixed_and_fp64_newton_solvers_agree(sp, prec):
     """The mixed Newton solve (FP32 factor, FP64 refinement to FP64 backward
     error) and the FP64 factorisation give the same fit: same Newton step

@@ -1,5 +1,5 @@
 """Parity at the full workload sizes, in the launch configuration the
-benchmark times (BF16X4 kernel values, FP64 Newton system, kappa = 256
+benchmark times (BF16SPLIT kernel values, FP64 Newton system, kappa = 256
 candidates, q = 64 added per round, tol 1e-6):
 
   * Gaussian mixture n = 500,000, d = 128, |J| = 4096 (64 rounds);
@@ -16,7 +16,7 @@ beta (direct-difference kernels, float64):
     coordinates of the gradient g_j = lambda (K_JJ beta)_j +
     sum_{i in S} k(x_i, x_j) (o_i - y_i).
 
-Tolerances follow from the stored arithmetic: a BF16X4 kernel value carries
+Tolerances follow from the stored arithmetic: a BF16SPLIT kernel value carries
 |dK| <= 6e-5 gamma (|x|^2 + |z|^2) + 1e-5 K + 2e-6 (split dot products,
 hi+lo storage, exp2 epilogue), the FP32 predict path |dK| <= 2e-6 +
 4 eps32 gamma (|x|^2 + |z|^2), and sums promote to FP64 every 32 terms
@@ -58,7 +58,7 @@ def fitted(request, sp):
     Xq = synth.queries_like(p, case["queries"], seed=77)
     X = torch.from_numpy(p.X).cuda()
     y = torch.from_numpy(p.y).cuda()
-    m = sp.spsvm_fit(X, y, p.gamma, p.lam, p.budget, 1e-6, precision="bf16x4",
+    m = sp.spsvm_fit(X, y, p.gamma, p.lam, p.budget, 1e-6, precision="bf16split",
                      candidates=256, add_per_round=64, seed=1)
     f = sp.spsvm_predict(m, torch.from_numpy(Xq).cuda()).cpu().numpy().astype(np.float64)
     J, beta = m.basis_and_beta()
@@ -69,7 +69,7 @@ def fitted(request, sp):
     return dict(p=p, Xq=Xq, J=J, beta=beta, o=o, f=f, info=info, name=request.param)
 
 
-def _bf16x4_bound(Xs, XJ, K, beta, gamma):
+def _bf16split_bound(Xs, XJ, K, beta, gamma):
     nx = np.sum(Xs.astype(np.float64) ** 2, axis=1)[:, None]
     nz = np.sum(XJ.astype(np.float64) ** 2, axis=1)[None, :]
     dK = 6e-5 * gamma * (nx + nz) + 1e-5 * K + 2e-6
@@ -88,7 +88,7 @@ def test_sampled_training_outputs(fitted):
     rows = np.sort(np.random.default_rng(5).choice(p.X.shape[0], 1000, replace=False))
     K = O.rbf_kernel(p.X[rows], p.X[J], p.gamma)
     ref = K @ beta
-    bound = _bf16x4_bound(p.X[rows], p.X[J], K, beta, p.gamma)
+    bound = _bf16split_bound(p.X[rows], p.X[J], K, beta, p.gamma)
     err = np.abs(fitted["o"][rows] - ref)
     print(fitted["name"], "outputs: max err/bound", np.max(err / bound))
     assert np.all(err <= bound), f"max err/bound {np.max(err / bound):.3g}"
@@ -116,7 +116,7 @@ def test_objective_with_oracle_quadratic_term(fitted):
     quad = 0.5 * p.lam * beta @ (KJJ @ beta)
     xi = np.maximum(0.0, 1.0 - p.y.astype(np.float64) * o)
     f_ref = quad + 0.5 * np.sum(xi * xi)
-    # the quadratic term's BF16X4 kernel errors relative to |beta|^T |K_JJ| |beta|
+    # the quadratic term's BF16SPLIT kernel errors relative to |beta|^T |K_JJ| |beta|
     tol = 1e-4 * (0.5 * p.lam * np.abs(beta) @ (KJJ @ np.abs(beta))) + 1e-6 * f_ref
     print(fitted["name"], "objective: err/tol", abs(fitted["info"]["objective"] - f_ref) / tol)
     assert abs(fitted["info"]["objective"] - f_ref) <= tol, (fitted["info"]["objective"], f_ref)

@@ -120,7 +120,7 @@ def test_lowrank_wrong_correction_never_claims_convergence(sp):
         assert ci != 0 or st == -4
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_fit_lowrank_steps_against_oracle_and_refactoring(sp, prec):
     """A growth run to |J| = 1024 on the benchmark workload's generator
     (mixture, d = 128, gamma = 1/d) at n = 20,000: Newton steps past

@@ -6,10 +6,10 @@ step under test differs.
 
 Tolerances (derived from the arithmetic, stated per test):
   * kernel values: FP32 form, |dK| <= 2e-6 + 4 eps32 gamma (|x|^2+|z|^2);
-    BF16X4 form, the hi + lo split of each operand is exact to 2^-18
-    relative and all four products are formed, so the dot product is off by
-    at most 2^-17 |x||z| <= 2^-18 (|x|^2 + |z|^2) plus FP32 accumulation:
-    |dK| <= 2e-5 * gamma * (|x|^2 + |z|^2) + 2e-6.
+    BF16SPLIT form, the three-term split is exact for FP32 operands and the
+    three dropped products are below 2^-24 |x z| each, so the dot product
+    carries FP32 rounding of its 6 d products accumulated in FP32:
+    |dK| <= 2e-6 + 8 eps32 gamma (|x|^2 + |z|^2).
   * sums of n products in FP32 with FP64 promotion every 32 terms:
     |err| <= 1e-5 * sum |terms|.
   * FP64 Cholesky / solves: backward-stable, 1e-10 relative.
@@ -24,6 +24,9 @@ import torch
 from oracle import spsvm as O
 
 pytestmark = pytest.mark.gpu
+
+# kernel-value bound of the split form, relative to gamma (|x|^2 + |z|^2)
+KTOL_SPLIT = 8 * 2 ** -24
 
 DEV = "cuda"
 
@@ -67,11 +70,10 @@ def sp():
 
 @pytest.mark.parametrize("n,d,m", [(1000, 20, 70), (257, 37, 64), (130, 5, 1), (3000, 130, 129),
                                    (290, 64, 200)])
-@pytest.mark.parametrize("prec,store", [("fp32", "fp32"), ("fp32", "bf16x4"), ("bf16x4", "fp32"),
-                                        ("bf16x4", "bf16x4")])
+@pytest.mark.parametrize("prec,store", [("fp32", "fp32"), ("fp32", "bf16split"), ("bf16split", "fp32")])
 def test_kernel_block(sp, n, d, m, prec, store):
-    """Arithmetic form x storage format; the stored hi + lo planes add 2^-17
-    relative rounding of each value."""
+    """Arithmetic form x storage format (the tensor-core form stores FP32);
+    the stored hi + lo planes add 2^-17 relative rounding of each value."""
     X, _ = _data(n, d, 1)
     gamma = 1.0 / d
     g = np.random.default_rng(2)
@@ -86,15 +88,15 @@ def test_kernel_block(sp, n, d, m, prec, store):
     ref = O.rbf_kernel(X, X[idx], gamma).T
     sq = (X.astype(np.float64) ** 2).sum(1)
     scale = gamma * (sq[None, :] + sq[idx][:, None])
-    tol = (4 * 2 ** -24 * scale + 2e-6) if prec == "fp32" else (2e-5 * scale + 2e-6)
-    if store == "bf16x4":
+    tol = (4 * 2 ** -24 if prec == "fp32" else KTOL_SPLIT) * scale + 2e-6
+    if store == "bf16split":
         tol = tol + 2.0 ** -17 * np.abs(ref)
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
     # rows before row0 untouched
     assert float(km.to_float()[:3].abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_score_candidates(sp, prec):
     n, d = 2100, 24
     X, y = _data(n, d, 3)
@@ -116,7 +118,7 @@ def test_score_candidates(sp, prec):
     res = np.where(S, o - y, 0)
     Kc = O.rbf_kernel(X, X[cand], gamma)
     gabs = np.abs(res) @ Kc + lam * np.abs(o[cand])
-    ktol = 4 * 2 ** -24 if prec == "fp32" else 2e-5
+    ktol = 4 * 2 ** -24 if prec == "fp32" else KTOL_SPLIT
     sq = (X.astype(np.float64) ** 2).sum(1)
     kerr = ktol * gamma * (sq.max() + sq.max()) + 2e-6
     gtol = 1e-5 * gabs + kerr * np.abs(res).sum()
@@ -129,7 +131,7 @@ def test_score_candidates(sp, prec):
     assert np.all(rel <= 2 * (gtol / np.abs(gr) + htol / hr) + 1e-12)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 def test_score_candidates_exact(sp, prec):
     """Exact one-dimensional scores against the oracle's (exact line search
     along each new coefficient, float64, direct differences) on the same o.
@@ -154,7 +156,7 @@ def test_score_candidates_exact(sp, prec):
     S = y * o < 1
     res = np.where(S, o - y, 0)
     Kc = O.rbf_kernel(X, X[cand], gamma)
-    ktol = 4 * 2 ** -24 if prec == "fp32" else 2e-5
+    ktol = 4 * 2 ** -24 if prec == "fp32" else KTOL_SPLIT
     sq = (X.astype(np.float64) ** 2).sum(1)
     kerr = ktol * gamma * 2 * sq.max() + 2e-6
     gtol = 1e-5 * (np.abs(res) @ Kc + lam * np.abs(o[cand])) + kerr * (np.abs(res).sum() + n)
@@ -167,7 +169,7 @@ def test_score_candidates_exact(sp, prec):
     assert np.all(np.abs(tg - tref) <= ttol), float(np.max(np.abs(tg - tref) / ttol))
 
 
-@pytest.mark.parametrize("fmt", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("fmt", ["fp32", "bf16split"])
 @pytest.mark.parametrize("n,m", [(1000, 70), (4099, 129), (33, 1)])
 def test_outputs_gemv(sp, fmt, n, m):
     g = np.random.default_rng(5)
@@ -209,7 +211,7 @@ def _split_ref(K):
     return (hi.double() + lo.double()).numpy()
 
 
-@pytest.mark.parametrize("fmt,kc_fmt", [("fp32", "fp32"), ("bf16x4", "bf16x4"), ("fp32", "bf16x4")])
+@pytest.mark.parametrize("fmt,kc_fmt", [("fp32", "fp32"), ("bf16split", "bf16split"), ("fp32", "bf16split")])
 # few active points (at most n / 64) take the gather path, more the scan
 @pytest.mark.parametrize("n,m,p", [(5000, 70, 0.5), (1000, 8, 0.0), (1000, 9, 1.0), (777, 64, 0.03),
                                    (20000, 70, 0.01), (50000, 130, 0.005), (6400, 20, 0.018)])
@@ -242,10 +244,10 @@ def test_compact_and_masked_products(sp, fmt, kc_fmt, n, m, p):
     assert np.all(np.abs(b.cpu().numpy() - rb) <= tolb)
 
 
-@pytest.mark.parametrize("prec,kfmt", [("fp32", "fp32"), ("bf16x4", "bf16x4"), ("bf16x4", "fp32")])
+@pytest.mark.parametrize("prec,kfmt", [("fp32", "fp32"), ("bf16split", "bf16split"), ("bf16split", "fp32")])
 @pytest.mark.parametrize("n,m,p", [(9000, 70, 0.6), (20000, 130, 0.5), (300, 64, 1.0), (2000, 1, 0.7)])
 def test_gram(sp, prec, kfmt, n, m, p):
-    """The BF16X4 Gram matrix reads the compact copy as hi / lo planes, from
+    """The BF16SPLIT Gram matrix reads the compact copy as hi / lo planes, from
     K stored as planes or (the fit's layout) in FP32 and split on the way."""
     g = np.random.default_rng(7)
     n_all = n
@@ -266,7 +268,7 @@ def test_gram(sp, prec, kfmt, n, m, p):
     Hg = H.cpu().numpy()
     np.testing.assert_array_equal(Hg, Hg.T)
     bound = np.abs(KS) @ np.abs(KS).T
-    # BF16X4: the hi+lo kernel values carry ~2^-17 relative error, plus
+    # BF16SPLIT: the hi+lo kernel values carry ~2^-17 relative error, plus
     # tensor-core FP32 accumulation
     rel = 1e-5 if prec == "fp32" else 1e-4
     assert np.all(np.abs(Hg - Href) <= rel * bound + 1e-12), np.max(np.abs(Hg - Href) / (bound + 1e-30))

@@ -62,7 +62,7 @@ def test_workspace_size_and_argument_checks():
     import ctypes as C
     import paper_1404_1066_gb300 as sp
     lib = sp.load()
-    o, _ = sp.make_options(precision="bf16x4")
+    o, _ = sp.make_options(precision="bf16split")
     b = lib.spsvm_fit_workspace_bytes(500_000, 128, 4096, C.byref(o))
     # two kernel-matrix copies of 4096 x 500,096 x 4 bytes dominate
     assert 2 * 4096 * 500_096 * 4 <= b < 2 * 4096 * 500_096 * 4 + 2 * 10 ** 9

@@ -21,7 +21,7 @@ def _problem(n, d, kappa, seed):
     return X, y, o, idx
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x4"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
 @pytest.mark.parametrize("n,d,kappa", [(3000, 24, 100), (20000, 128, 256)])
 def test_noalloc_matches_scratch_entry_point_twice(prec, n, d, kappa):
     import paper_1404_1066_gb300 as sp
