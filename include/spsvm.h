@@ -375,8 +375,17 @@ int spsvm_line_search(const float* o, const float* u, const float* y, int64_t n,
  *   out[i] = sum_{j<m} beta_j exp(-gamma ||q_i - b_j||^2)
  * for query rows q (nq x d, ldq) and basis rows b (m x d, ldb), computed
  * tile by tile without storing the kernel block.  beta FP64; out FP32.
- * All device.  scratch: spsvm_decision_scratch_bytes(nq, m, d). */
-size_t spsvm_decision_scratch_bytes(int64_t nq, int64_t m, int64_t d);
+ * SPSVM_FP32: FP32 SIMT dot products, beta_j k summed in FP64.
+ * SPSVM_BF16SPLIT: the kernel block's tensor-core engine (basis rows and
+ * queries split into three BF16 planes, six products: the dot products
+ * carry FP32-level error), beta_j k summed in FP32 over groups of 32 basis
+ * rows and the groups in FP64 in a fixed order (results do not depend on
+ * the launch); queries go in passes of at most 32,768.
+ * All device.  scratch: spsvm_decision_scratch_bytes(nq, m, d, precision)
+ * bytes (SPSVM_BF16SPLIT: the basis planes, one pass of query planes and
+ * the partial sums, about m d 6 + min(nq, 32768) (6 d + m / 8) bytes).
+ * Errors: ARG, OOM (scratch too small). */
+size_t spsvm_decision_scratch_bytes(int64_t nq, int64_t m, int64_t d, int32_t precision);
 int spsvm_decision(const float* B, int64_t m, int64_t ldb, const double* beta,
                    const float* Q, int64_t nq, int64_t ldq, int64_t d, float gamma,
                    int32_t precision, float* out, void* scratch,
@@ -476,9 +485,19 @@ int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, const float* y,
               spsvm_model** out);
 
 /* Decision values for nq query rows (device, nq x d, ldq) into decision
- * (device FP32, nq); label = +1 if decision >= 0 else -1. */
+ * (device FP32, nq); label = +1 if decision >= 0 else -1.  Computed in the
+ * model's precision form (spsvm_decision).  A model of the BF16SPLIT form
+ * takes spsvm_predict_work_bytes(model, nq) bytes of device work memory per
+ * call: spsvm_predict takes them stream-ordered (cudaMallocAsync /
+ * cudaFreeAsync on `stream`, no device synchronisation); spsvm_predict_ws
+ * uses the caller's `work` (device, work_bytes >= that size; NULL / 0 when
+ * the size is 0).  Concurrent calls on one model are safe when each has its
+ * own work memory.  Errors: ARG, OOM (work too small). */
+size_t spsvm_predict_work_bytes(const spsvm_model* model, int64_t nq);
 int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
                   float* decision, void* stream);
+int spsvm_predict_ws(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
+                     float* decision, void* work, size_t work_bytes, void* stream);
 
 /* Model facts.  Any output pointer may be NULL. */
 int spsvm_model_info(const spsvm_model* model, int32_t* n_basis, int64_t* d,

@@ -15,7 +15,7 @@ from .api import (  # noqa: F401
     spsvm_fit_workspace_bytes, spsvm_gemv, spsvm_gram, spsvm_kernel_block, spsvm_line_search,
     spsvm_outputs, spsvm_predict, spsvm_prepare_points, spsvm_score_candidates,
     spsvm_score_candidates_noalloc, spsvm_score_candidates_exact, spsvm_fit_batched, spsvm_solve_mixed, spsvm_cholesky_mixed, spsvm_fit_ovo,
-    spsvm_solve_lowrank, spsvm_active_diff,
+    spsvm_solve_lowrank, spsvm_active_diff, spsvm_predict_work_bytes,
     spsvm_predict_ovo, Server,
 )
 from ._lib import SPSVM_BF16SPLIT, SPSVM_FP32, SpsvmError, load  # noqa: F401

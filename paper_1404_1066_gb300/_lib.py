@@ -119,13 +119,15 @@ SIGNATURES = {
     "spsvm_line_scratch_bytes": (_SZ, [_I64]),
     "spsvm_line_search": (_I32, [_P, _P, _P, _I64, _P, _P, _I32, _D, C.POINTER(_D), _P, _P, _SZ,
                                  _P]),
-    "spsvm_decision_scratch_bytes": (_SZ, [_I64, _I64, _I64]),
+    "spsvm_decision_scratch_bytes": (_SZ, [_I64, _I64, _I64, _I32]),
     "spsvm_decision": (_I32, [_P, _I64, _I64, _P, _P, _I64, _I64, _I64, _F, _I32, _P, _P, _SZ,
                               _P]),
     "spsvm_fit_workspace_bytes": (_SZ, [_I64, _I64, _I32, C.POINTER(spsvm_options)]),
     "spsvm_fit": (_I32, [_P, _I64, _I64, _I64, _P, _F, _D, _I32, _D, C.POINTER(spsvm_options),
                          _P, _SZ, C.POINTER(_P)]),
     "spsvm_predict": (_I32, [_P, _P, _I64, _I64, _P, _P]),
+    "spsvm_predict_work_bytes": (_SZ, [_P, _I64]),
+    "spsvm_predict_ws": (_I32, [_P, _P, _I64, _I64, _P, _P, _SZ, _P]),
     "spsvm_model_info": (_I32, [_P, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_F),
                                 C.POINTER(_D), C.POINTER(_D), C.POINTER(_I32), C.POINTER(_I32),
                                 C.POINTER(_I32)]),

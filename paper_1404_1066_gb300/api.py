@@ -366,7 +366,7 @@ def spsvm_decision(B, beta, Q, gamma, precision="fp32"):
     m, d = B.shape
     nq = Q.shape[0]
     out = torch.empty(nq, dtype=torch.float32, device=Q.device)
-    sb = _lib().spsvm_decision_scratch_bytes(nq, m, d)
+    sb = _lib().spsvm_decision_scratch_bytes(nq, m, d, _prec(precision))
     scratch = torch.empty(max(1, sb), dtype=torch.uint8, device=Q.device)
     check(_lib().spsvm_decision(ptr(B), m, B.stride(0), ptr(beta), ptr(Q), nq, Q.stride(0), d,
                                 float(gamma), _prec(precision), ptr(out), ptr(scratch), sb,
@@ -517,12 +517,26 @@ def spsvm_fit(X: torch.Tensor, y: torch.Tensor, gamma, lam, budget, tol=1e-6, wo
     return Model(handle.value, rc)
 
 
-def spsvm_predict(model: Model, Xq: torch.Tensor, stream=None):
+def spsvm_predict_work_bytes(model: Model, nq: int) -> int:
+    """Device work bytes one spsvm_predict_ws call on nq queries needs."""
+    return int(_lib().spsvm_predict_work_bytes(model.handle, int(nq)))
+
+
+def spsvm_predict(model: Model, Xq: torch.Tensor, stream=None, work=None):
+    """Decision values of the model on the query rows Xq.  work: optional
+    device uint8 tensor of at least spsvm_predict_work_bytes(model, nq)
+    bytes (the library otherwise takes its work memory stream-ordered)."""
     _require_cuda(Xq)
     assert Xq.dtype == torch.float32 and Xq.stride(1) == 1
     out = torch.empty(Xq.shape[0], dtype=torch.float32, device=Xq.device)
-    check(_lib().spsvm_predict(model.handle, ptr(Xq), Xq.shape[0], Xq.stride(0), ptr(out),
-                               stream_ptr(stream)), "spsvm_predict")
+    if work is None:
+        check(_lib().spsvm_predict(model.handle, ptr(Xq), Xq.shape[0], Xq.stride(0), ptr(out),
+                                   stream_ptr(stream)), "spsvm_predict")
+    else:
+        assert work.dtype == torch.uint8 and work.is_cuda
+        check(_lib().spsvm_predict_ws(model.handle, ptr(Xq), Xq.shape[0], Xq.stride(0), ptr(out),
+                                      ptr(work), work.numel(), stream_ptr(stream)),
+              "spsvm_predict_ws")
     return out
 
 

@@ -1,10 +1,19 @@
 // Decision values f(q) = sum_j beta_j k(q, b_j) (Section 4: the classifier
 // h(x) = w^T phi(x) with w restricted to the basis J), tile by tile, never
-// storing the query-by-basis kernel block.  Plain FP32 SIMT dot products,
-// FP64 accumulation of beta_j k(q, b_j) per tile of 64 basis vectors.
+// storing the query-by-basis kernel block.  SPSVM_FP32: plain FP32 SIMT dot
+// products, FP64 accumulation of beta_j k(q, b_j) per tile of 64 basis
+// vectors.  SPSVM_BF16SPLIT: the tensor-core kernel block engine with the
+// basis rows and the queries split into three BF16 planes each, FP32 sums of
+// beta_j k over 32 basis rows per partial, the partials summed in FP64 in a
+// fixed order.
 #include "internal.h"
 
 namespace spsvm {
+
+int64_t decision_tc_parts(int64_t m);
+int launch_decision_tc(const spsvm_points* q, const void* zplanes, size_t zbytes, int64_t m,
+                       const float* znorm, const double* beta, float gamma, float* dpart,
+                       int64_t ldp, cudaStream_t s);
 
 namespace {
 
@@ -118,15 +127,55 @@ __global__ void __launch_bounds__(QT) decision_simt(
   }
 }
 
+// out[i] = sum over the P partials of column i, in FP64, in order.
+__global__ void decision_finish(const float* __restrict__ part, int64_t P, int64_t ldp,
+                                int64_t nq, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  double s = 0.0;
+  for (int64_t p = 0; p < P; ++p) s += (double)part[p * ldp + i];
+  out[i] = (float)s;
+}
+
+// Queries per pass of the tensor-core form (bounds the scratch).
+constexpr int64_t kDecideChunk = 32768;
+
+struct DecideLayout {
+  int64_t ldh, qc, parts;
+  size_t off_zn, off_z, z_bytes, off_qn, off_q, q_plane, off_part, total;
+};
+
+DecideLayout decide_layout(int64_t nq, int64_t m, int64_t d) {
+  DecideLayout L;
+  auto al = [](size_t b) { return (size_t)round_up((int64_t)b, 256); };
+  L.ldh = round_up(d, 64);
+  L.qc = round_up(min64(max64(nq, 1), kDecideChunk), 128);
+  L.parts = decision_tc_parts(m);
+  size_t o = 0;
+  L.off_zn = o;
+  o += al((size_t)m * 4);
+  L.off_z = o;
+  L.z_bytes = (size_t)m * L.ldh * 6;
+  o += al(L.z_bytes);
+  L.off_qn = o;
+  o += al((size_t)L.qc * 4);
+  L.off_q = o;
+  L.q_plane = (size_t)L.qc * L.ldh * 2;
+  o += al(3 * L.q_plane);
+  L.off_part = o;
+  o += al((size_t)L.parts * L.qc * 4);
+  L.total = o;
+  return L;
+}
+
 }  // namespace
 }  // namespace spsvm
 
 using namespace spsvm;
 
-extern "C" size_t spsvm_decision_scratch_bytes(int64_t nq, int64_t m, int64_t d) {
-  (void)nq;
-  (void)d;
-  if (m < 0) return 0;
+extern "C" size_t spsvm_decision_scratch_bytes(int64_t nq, int64_t m, int64_t d, int32_t precision) {
+  if (m < 0 || d < 1) return 0;
+  if (precision == SPSVM_BF16SPLIT) return decide_layout(nq, m, d).total;
   return (size_t)round_up(m * 4 + 16, 256);
 }
 
@@ -139,9 +188,37 @@ extern "C" int spsvm_decision(const float* B, int64_t m, int64_t ldb, const doub
   if (precision != SPSVM_FP32 && precision != SPSVM_BF16SPLIT)
     return set_error(SPSVM_ERR_ARG, "decision: bad precision");
   if (nq == 0) return SPSVM_OK;
-  if (!scratch || scratch_bytes < spsvm_decision_scratch_bytes(nq, m, d))
+  if (!scratch || scratch_bytes < spsvm_decision_scratch_bytes(nq, m, d, precision))
     return set_error(SPSVM_ERR_OOM, "decision: scratch too small");
   cudaStream_t s = as_stream(stream);
+  if (precision == SPSVM_BF16SPLIT) {
+    // algorithmic work: 2 nq m d multiply-adds, times the six plane products
+    ProfScope prof(PROF_DECISION, s, 12.0 * (double)nq * m * (double)d);
+    if (m == 0) {
+      SPSVM_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)nq * 4, s));
+      return SPSVM_OK;
+    }
+    const DecideLayout L = decide_layout(nq, m, d);
+    char* w = static_cast<char*>(scratch);
+    // the basis rows' norms and planes (rows past m read as zeros)
+    uint16_t* zp = reinterpret_cast<uint16_t*>(w + L.off_z);
+    spsvm_points zb{B, m, d, ldb, reinterpret_cast<float*>(w + L.off_zn), zp, zp + 2 * m * L.ldh,
+                    L.ldh, zp + m * L.ldh};
+    SPSVM_TRY(spsvm_prepare_points(&zb, SPSVM_BF16SPLIT, stream));
+    uint16_t* qp = reinterpret_cast<uint16_t*>(w + L.off_q);
+    float* part = reinterpret_cast<float*>(w + L.off_part);
+    for (int64_t q0 = 0; q0 < nq; q0 += L.qc) {
+      const int64_t cnt = min64(L.qc, nq - q0);
+      spsvm_points qb{Q + q0 * ldq, cnt, d, ldq, reinterpret_cast<float*>(w + L.off_qn), qp,
+                      qp + 2 * L.qc * L.ldh, L.ldh, qp + L.qc * L.ldh};
+      SPSVM_TRY(spsvm_prepare_points(&qb, SPSVM_BF16SPLIT, stream));
+      SPSVM_TRY(launch_decision_tc(&qb, zp, L.z_bytes, m, zb.norms, beta, gamma, part, L.qc, s));
+      decision_finish<<<(unsigned)ceil_div(cnt, (int64_t)256), 256, 0, s>>>(part, L.parts, L.qc,
+                                                                           cnt, out + q0);
+      SPSVM_LAUNCH_CHECK();
+    }
+    return SPSVM_OK;
+  }
   ProfScope prof(PROF_DECISION, s, 2.0 * (double)nq * m * (double)d);
   float* bnorm = static_cast<float*>(scratch);
   if (m > 0) {

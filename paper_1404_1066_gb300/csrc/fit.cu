@@ -917,7 +917,8 @@ struct Fit {
       SPSVM_CUDA_TRY(cudaMemcpyAsync(model->beta_dev, model->beta.data(), mr * 8,
                                      cudaMemcpyHostToDevice, s));
     }
-    model->scratch_bytes = spsvm_decision_scratch_bytes(0, mr, d);
+    // the SIMT form's basis norms (the split form's decision work is per call)
+    model->scratch_bytes = spsvm_decision_scratch_bytes(0, mr, d, SPSVM_FP32);
     SPSVM_CUDA_TRY(cudaMalloc(&model->scratch_dev, model->scratch_bytes));
     return sync();
   }
@@ -1041,23 +1042,53 @@ extern "C" int spsvm_fit(const float* X, int64_t n, int64_t d, int64_t ldx, cons
   return model->status == SPSVM_ERR_NO_CONVERGE ? SPSVM_ERR_NO_CONVERGE : SPSVM_OK;
 }
 
-extern "C" int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
-                             float* decision, void* stream) {
+extern "C" size_t spsvm_predict_work_bytes(const spsvm_model* model, int64_t nq) {
+  if (!model || nq < 1 || model->J.empty() || model->precision != SPSVM_BF16SPLIT) return 0;
+  return spsvm_decision_scratch_bytes(nq, (int64_t)model->J.size(), model->d, SPSVM_BF16SPLIT);
+}
+
+extern "C" int spsvm_predict_ws(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
+                                float* decision, void* work, size_t work_bytes, void* stream) {
   if (!model || !Xq || !decision || nq < 0 || ldq < model->d)
     return set_error(SPSVM_ERR_ARG, "predict: bad arguments");
   if (nq == 0) return SPSVM_OK;
   cudaStream_t s = as_stream(stream);
   if (model->J.empty()) {
     SPSVM_CUDA_TRY(cudaMemsetAsync(decision, 0, nq * 4, s));
+  } else if (model->precision == SPSVM_BF16SPLIT) {
+    const size_t need = spsvm_predict_work_bytes(model, nq);
+    if (!work || work_bytes < need)
+      return set_error(SPSVM_ERR_OOM, "predict: work %zu < %zu bytes", work_bytes, need);
+    SPSVM_TRY(spsvm_decision(model->basis_dev, (int64_t)model->J.size(), model->d, model->beta_dev,
+                             Xq, nq, ldq, model->d, model->gamma, SPSVM_BF16SPLIT, decision, work,
+                             work_bytes, stream));
   } else {
     SPSVM_TRY(spsvm_decision(model->basis_dev, (int64_t)model->J.size(), model->d, model->beta_dev,
-                             Xq, nq, ldq, model->d, model->gamma, model->precision, decision,
+                             Xq, nq, ldq, model->d, model->gamma, SPSVM_FP32, decision,
                              model->scratch_dev, model->scratch_bytes, stream));
   }
   if (model->bias != 0.0) {   // f(x) + b
     add_const<<<grid_for(nq, 256), 256, 0, s>>>(decision, nq, (float)model->bias);
     SPSVM_LAUNCH_CHECK();
   }
+  return SPSVM_OK;
+}
+
+extern "C" int spsvm_predict(const spsvm_model* model, const float* Xq, int64_t nq, int64_t ldq,
+                             float* decision, void* stream) {
+  if (!model) return set_error(SPSVM_ERR_ARG, "predict: NULL model");
+  const size_t need = spsvm_predict_work_bytes(model, nq);
+  if (need == 0) return spsvm_predict_ws(model, Xq, nq, ldq, decision, nullptr, 0, stream);
+  // stream-ordered work memory: no device synchronisation, and every
+  // concurrent call on the same model has its own
+  cudaStream_t s = as_stream(stream);
+  void* w = nullptr;
+  SPSVM_CUDA_TRY(cudaMallocAsync(&w, need, s));
+  const int rc = spsvm_predict_ws(model, Xq, nq, ldq, decision, w, need, stream);
+  const cudaError_t e = cudaFreeAsync(w, s);
+  if (rc != SPSVM_OK) return rc;
+  if (e != cudaSuccess)
+    return set_error(SPSVM_ERR_CUDA, "predict: cudaFreeAsync: %s", cudaGetErrorString(e));
   return SPSVM_OK;
 }
 

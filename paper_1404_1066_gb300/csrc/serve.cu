@@ -195,6 +195,7 @@ struct SpsvmRequest {
   // bookkeeping
   size_t footprint = 0;     // device bytes the request needs (checked against the budget)
   size_t model_bytes = 0;   // device bytes of the fitted model while resident
+  size_t work_bytes = 0;    // a predict's decision work (at most, for the fit's budget)
   double t_submit = 0, t_start = 0, t_end = 0;
   int state = 0;   // 0 queued, 1 running, 2 done
   int32_t status = SPSVM_OK;
@@ -222,21 +223,22 @@ namespace {
 // A worker's device buffers, kept across requests (grown, never shrunk
 // while requests keep fitting the budget).
 struct WorkerBufs {
-  DeviceBuf X, y, ws, Q, out;
-  size_t held() const { return X.bytes + y.bytes + ws.bytes + Q.bytes + out.bytes; }
+  DeviceBuf X, y, ws, Q, out, pw;
+  size_t held() const { return X.bytes + y.bytes + ws.bytes + Q.bytes + out.bytes + pw.bytes; }
   void release() {
     X.reset();
     y.reset();
     ws.reset();
     Q.reset();
     out.reset();
+    pw.reset();
   }
 };
 
 // Device bytes a fit's model holds at most (basis rows, beta, decision scratch).
 size_t model_reserve(const SpsvmRequest& r) {
   return (size_t)r.budget * r.d * 4 + (size_t)r.budget * 8 +
-         spsvm_decision_scratch_bytes(0, r.budget, r.d);
+         spsvm_decision_scratch_bytes(0, r.budget, r.d, SPSVM_FP32);
 }
 
 size_t grow_of(const DeviceBuf& b, size_t want) { return want > b.bytes ? want - b.bytes : 0; }
@@ -247,7 +249,8 @@ size_t extra_for(const SpsvmRequest& r, const WorkerBufs& W) {
   if (r.kind == 0)
     return grow_of(W.X, r.X.size() * 4) + grow_of(W.y, r.y.size() * 4) +
            grow_of(W.ws, spsvm_fit_workspace_bytes(r.n, r.d, r.budget, &r.opt)) + model_reserve(r);
-  return grow_of(W.Q, r.Xq.size() * 4) + grow_of(W.out, (size_t)r.nq * 4);
+  return grow_of(W.Q, r.Xq.size() * 4) + grow_of(W.out, (size_t)r.nq * 4) +
+         grow_of(W.pw, r.work_bytes);
 }
 
 // First admissible request in FIFO order for this worker (lock held): its
@@ -302,8 +305,10 @@ int run_fit(SpsvmRequest& r, WorkerBufs& W, cudaStream_t s) {
 int run_predict(SpsvmRequest& r, spsvm_model* m, WorkerBufs& W, cudaStream_t s) {
   SPSVM_TRY(W.Q.ensure(r.Xq.size() * 4));
   SPSVM_TRY(W.out.ensure((size_t)r.nq * 4));
+  SPSVM_TRY(W.pw.ensure(r.work_bytes));
   SPSVM_CUDA_TRY(cudaMemcpyAsync(W.Q.p, r.Xq.data(), r.Xq.size() * 4, cudaMemcpyHostToDevice, s));
-  SPSVM_TRY(spsvm_predict(m, static_cast<float*>(W.Q.p), r.nq, r.d, static_cast<float*>(W.out.p), s));
+  SPSVM_TRY(spsvm_predict_ws(m, static_cast<float*>(W.Q.p), r.nq, r.d, static_cast<float*>(W.out.p),
+                             W.pw.p, W.pw.bytes, s));
   r.out.resize(r.nq);
   SPSVM_CUDA_TRY(cudaMemcpyAsync(r.out.data(), W.out.p, r.nq * 4, cudaMemcpyDeviceToHost, s));
   SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -442,6 +447,7 @@ extern "C" int spsvm_server_submit_predict(spsvm_server* S, int64_t fit_id, cons
   if (!S || !Xq || nq < 1 || !request_id)
     return set_error(SPSVM_ERR_ARG, "server_submit_predict: bad arguments");
   int64_t d = 0;
+  size_t work = 0;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     auto f = S->reqs.find(fit_id);
@@ -452,6 +458,9 @@ extern "C" int spsvm_server_submit_predict(spsvm_server* S, int64_t fit_id, cons
       return set_error(SPSVM_ERR_ARG, "server_submit_predict: fit request %lld has no model "
                        "(failed or released)", (long long)fit_id);
     d = f->second->d;
+    // the decision work of the split form, for the fit's basis budget
+    if (f->second->opt.precision == SPSVM_BF16SPLIT)
+      work = spsvm_decision_scratch_bytes(nq, f->second->budget, d, SPSVM_BF16SPLIT);
   }
   auto r = std::make_shared<SpsvmRequest>();
   r->kind = 1;
@@ -459,7 +468,8 @@ extern "C" int spsvm_server_submit_predict(spsvm_server* S, int64_t fit_id, cons
   r->d = d;
   r->nq = nq;
   r->Xq.assign(Xq, Xq + nq * d);
-  r->footprint = (size_t)nq * d * 4 + (size_t)nq * 4;
+  r->work_bytes = work;
+  r->footprint = (size_t)nq * d * 4 + (size_t)nq * 4 + work;
   return enqueue(S, r, request_id);
 }
 

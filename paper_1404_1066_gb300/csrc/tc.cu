@@ -103,9 +103,28 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT,
   pt = g0 + r % gw;
 }
 
-// Epilogue modes: store the FP32 kernel values, or reduce the
-// candidate-score sums without storing them.
-enum KbMode { KB_STORE_F32 = 0, KB_SCORE = 2 };
+// Epilogue modes: store the FP32 kernel values, reduce the candidate-score
+// sums without storing them, or reduce the decision values
+// f(x_i) = sum_c beta_c k(z_c, x_i) (Z the basis rows, X the queries) over
+// each warp's 32 basis rows, also without storing the kernel values.
+enum KbMode { KB_STORE_F32 = 0, KB_SCORE = 2, KB_DECIDE = 3 };
+
+// Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j): after
+// five exchange steps, each halving the columns a lane holds and summing
+// the pair, lane l holds the sum of column l (31 shuffles in all).
+__device__ __forceinline__ float warp_column_sums(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float give = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, give, h);
+    }
+  }
+  return v[0];
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
@@ -115,8 +134,11 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     const __grid_constant__ CUtensorMap map_out, int64_t ldh, int64_t n, int32_t m,
     const float* __restrict__ norms, const int64_t* __restrict__ idx, float gamma, int64_t row0,
     const float* __restrict__ y, const float* __restrict__ o, double2* __restrict__ part,
-    int32_t kappa, WaitCtx wc) {
+    int32_t kappa, const float* __restrict__ znorm, const double* __restrict__ beta,
+    float* __restrict__ dpart, int64_t ldp, WaitCtx wc) {
   constexpr bool SCORE = MODE == KB_SCORE;
+  constexpr bool STORE = MODE == KB_STORE_F32;
+  constexpr bool DECIDE = MODE == KB_DECIDE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + PK_BAR_OFF);
@@ -156,7 +178,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
     prefetch_tmap(&map_xhi);
     prefetch_tmap(&map_xmid);
     prefetch_tmap(&map_xlo);
-    if (!SCORE) prefetch_tmap(&map_out);
+    if (STORE) prefetch_tmap(&map_out);
   }
   if (warp == 0) tmem_alloc(tmem_slot, 2 * PK_ACC_COLS);
   fence_before_sync();
@@ -252,7 +274,8 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       tile_coords(t, nCB, nPT, cb, pt);
       const int64_t c = (int64_t)cb * PK_M + c_in;
       const bool crow = c < m;
-      const float zn = crow ? norms[idx[c]] : 0.f;
+      const float zn = crow ? (DECIDE ? znorm[c] : norms[idx[c]]) : 0.f;
+      const float bc = DECIDE && crow ? (float)beta[c] : 0.f;
       const int64_t ib = pt * PK_N + half * PK_WP;
       const int64_t npts = min64(PK_WP, n - ib);
       // this warp's 64 points: norms (and for scores the active residual / flag)
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       fence_after_sync();
       float gs = 0.f, hs = 0.f;
       const uint32_t tb = tmem + acc * PK_ACC_COLS + half * PK_WP + ((uint32_t)(32 * quarter) << 16);
-      if (!SCORE) {
+      if (STORE) {
         // the previous tile's boxes must have been read out before they are rewritten
         if (lane == 0) bulk_wait_read();
         __syncwarp();
@@ -303,7 +326,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
           v[jj + 2] = ex2_approx(fminf(fmaf(-g2, x4.z, fmaf(2.0f * g2, v[jj + 2], zz)), 0.0f));
           v[jj + 3] = ex2_approx(fminf(fmaf(-g2, x4.w, fmaf(2.0f * g2, v[jj + 3], zz)), 0.0f));
         }
-        if (!SCORE) {
+        if (STORE) {
           // 32 FP32 values into box cc of this warp (row = lane, 128-byte
           // swizzle: 16-byte chunk ch of row r at chunk ch ^ (r & 7))
           uint8_t* bx = obox + cc * PK_OUT_BOX;
@@ -313,18 +336,27 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
             *reinterpret_cast<float4*>(bx + so) =
                 make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
           }
-        } else {
+        } else if (SCORE) {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
             const float kv = v[jj];
             gs = fmaf(stage[PK_WP + cc * 32 + jj], kv, gs);
             hs = fmaf(stage[2 * PK_WP + cc * 32 + jj] * kv, kv, hs);
           }
+        } else {
+          // beta_c k(z_c, x_i) summed over this warp's 32 basis rows (rows
+          // past m carry beta 0); one partial per (basis block, lane
+          // quarter) and query, summed in a fixed order by the finish
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) v[jj] *= bc;
+          const float f = warp_column_sums(v, lane);
+          if (cc * 32 + lane < npts)
+            dpart[((int64_t)cb * 4 + quarter) * ldp + ib + cc * 32 + lane] = f;
         }
       }
       fence_before_sync();
       mbar_arrive(&tempty[acc]);
-      if (!SCORE && npts > 0) {
+      if (STORE && npts > 0) {
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) {
@@ -352,7 +384,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
       }
       __syncwarp();
     }
-    if (!SCORE && lane == 0) bulk_wait_all();
+    if (STORE && lane == 0) bulk_wait_all();
   }
   fence_before_sync();
   __syncthreads();
@@ -589,24 +621,40 @@ int make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, in
   return SPSVM_OK;
 }
 
+// Extra arguments of the decision mode: basis norms, beta, the partial sums
+// and their row pitch.
+struct DecideArgs {
+  const float* znorm = nullptr;
+  const double* beta = nullptr;
+  float* dpart = nullptr;
+  int64_t ldp = 0;
+};
+
+// STORE / SCORE: the m rows idx of the points' planes are gathered into zbuf
+// first (zero rows up to a multiple of 128).  DECIDE: zbuf already holds the
+// basis planes (m rows of pitch ldh; the tensor maps zero-fill past m).
 template <int MODE>
 int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma, void* out,
               int64_t ld, int64_t row0, const float* y, const float* o, double2* part,
-              int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s) {
+              int32_t kappa, void* zbuf, size_t zbytes, cudaStream_t s,
+              const DecideArgs& da = DecideArgs()) {
   const int64_t m_pad = round_up(m, (int64_t)PK_M);
-  if (!zbuf || zbytes < (size_t)(m_pad * p->ldh * 6))
-    return set_error(SPSVM_ERR_OOM, "BF16SPLIT kernel block: scratch too small for the gathered rows");
+  const int64_t zrows = MODE == KB_DECIDE ? (int64_t)m : m_pad;
+  if (!zbuf || zbytes < (size_t)(zrows * p->ldh * 6))
+    return set_error(SPSVM_ERR_OOM, "BF16SPLIT kernel block: scratch too small for the basis planes");
   uint16_t* zhi = static_cast<uint16_t*>(zbuf);
-  uint16_t* zmid = zhi + m_pad * p->ldh;
-  uint16_t* zlo = zmid + m_pad * p->ldh;
-  const int64_t work = m_pad * (p->ldh / 8);
-  gather_rows_bf16<<<(unsigned)ceil_div(work, (int64_t)256), 256, 0, s>>>(
-      p->hi, p->mid, p->lo, p->ldh, idx, m, m_pad, zhi, zmid, zlo);
-  SPSVM_LAUNCH_CHECK();
+  uint16_t* zmid = zhi + zrows * p->ldh;
+  uint16_t* zlo = zmid + zrows * p->ldh;
+  if (MODE != KB_DECIDE) {
+    const int64_t work = m_pad * (p->ldh / 8);
+    gather_rows_bf16<<<(unsigned)ceil_div(work, (int64_t)256), 256, 0, s>>>(
+        p->hi, p->mid, p->lo, p->ldh, idx, m, m_pad, zhi, zmid, zlo);
+    SPSVM_LAUNCH_CHECK();
+  }
   CUtensorMap mzh, mzm, mzl, mxh, mxm, mxl, mo;
-  SPSVM_TRY(make_map(&mzh, zhi, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
-  SPSVM_TRY(make_map(&mzm, zmid, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
-  SPSVM_TRY(make_map(&mzl, zlo, p->ldh, m_pad, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mzh, zhi, p->ldh, zrows, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mzm, zmid, p->ldh, zrows, p->ldh, PK_M, PK_KC));
+  SPSVM_TRY(make_map(&mzl, zlo, p->ldh, zrows, p->ldh, PK_M, PK_KC));
   SPSVM_TRY(make_map(&mxh, p->hi, p->ldh, p->n, p->ldh, PK_N, PK_KC));
   SPSVM_TRY(make_map(&mxm, p->mid, p->ldh, p->n, p->ldh, PK_N, PK_KC));
   SPSVM_TRY(make_map(&mxl, p->lo, p->ldh, p->n, p->ldh, PK_N, PK_KC));
@@ -620,7 +668,8 @@ int launch_kb(const spsvm_points* p, const int64_t* idx, int32_t m, float gamma,
   WaitCtx wc;
   SPSVM_TRY(wait_ctx(s, &wc));
   kern<<<grid, PK_THREADS, PK_SMEM, s>>>(mzh, mzm, mzl, mxh, mxm, mxl, mo, p->ldh, p->n, m,
-                                         p->norms, idx, gamma, row0, y, o, part, kappa, wc);
+                                         p->norms, idx, gamma, row0, y, o, part, kappa, da.znorm,
+                                         da.beta, da.dpart, da.ldp, wc);
   SPSVM_LAUNCH_CHECK();
   return SPSVM_OK;
 }
@@ -650,6 +699,21 @@ int launch_score_tc(const spsvm_points* p, const float* y, const float* o, const
                     size_t zbytes, cudaStream_t s) {
   (void)tiles;
   return launch_kb<KB_SCORE>(p, idx, kappa, gamma, nullptr, 0, 0, y, o, part, kappa, zbuf, zbytes, s);
+}
+
+int64_t decision_tc_parts(int64_t m) { return 4 * ceil_div(m, (int64_t)PK_M); }
+
+int launch_decision_tc(const spsvm_points* q, const void* zplanes, size_t zbytes, int64_t m,
+                       const float* znorm, const double* beta, float gamma, float* dpart,
+                       int64_t ldp, cudaStream_t s) {
+  if (m == 0 || q->n == 0) return SPSVM_OK;
+  DecideArgs da;
+  da.znorm = znorm;
+  da.beta = beta;
+  da.dpart = dpart;
+  da.ldp = ldp;
+  return launch_kb<KB_DECIDE>(q, nullptr, (int32_t)m, gamma, nullptr, 0, 0, nullptr, nullptr,
+                              nullptr, 0, const_cast<void*>(zplanes), zbytes, s, da);
 }
 
 int64_t gram_tc_splits(int64_t m, int64_t ns_max) {

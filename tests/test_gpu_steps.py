@@ -470,19 +470,58 @@ def test_line_search(sp, seed):
     assert t == pytest.approx(t_ref, rel=2e-4, abs=1e-6)
 
 
-@pytest.mark.parametrize("nq,m,d", [(1000, 70, 20), (129, 1, 3), (5000, 257, 64)])
-def test_decision(sp, nq, m, d):
-    g = np.random.default_rng(9)
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
+@pytest.mark.parametrize("nq,m,d", [(1000, 70, 20), (129, 1, 3), (5000, 257, 64),
+                                    (70001, 300, 40), (3000, 1031, 128)])
+def test_decision(sp, prec, nq, m, d):
+    """Decision values against the oracle's FP64 kernel: the split form on
+    the tensor cores (several basis blocks, a ragged query tail, three query
+    passes at nq = 70,001) within the kernel-value bound of its dot
+    products plus the ex2 approximation."""
+    g = np.random.default_rng(9 + m)
     B = g.standard_normal((m, d)).astype(np.float32)
     Q = g.standard_normal((nq, d)).astype(np.float32)
     beta = g.standard_normal(m)
     gamma = 0.5 / d
-    out = sp.spsvm_decision(_t(B), _t(beta), _t(Q), gamma)
+    out = sp.spsvm_decision(_t(B), _t(beta), _t(Q), gamma, prec)
     torch.cuda.synchronize()
     Kq = O.rbf_kernel(Q, B, gamma)
     ref = Kq @ beta
     sq = (Q.astype(np.float64) ** 2).sum(1)
     sb = (B.astype(np.float64) ** 2).sum(1)
-    krel = 4 * 2 ** -24 * gamma * (sq[:, None] + sb[None, :])
+    if prec == "fp32":
+        krel = 4 * 2 ** -24 * gamma * (sq[:, None] + sb[None, :])
+    else:
+        krel = KTOL_SPLIT * gamma * (sq[:, None] + sb[None, :]) + 2.0 ** -21
     tol = (Kq * krel) @ np.abs(beta) + 1e-6 * (Kq @ np.abs(beta)) + 1e-7
-    assert np.all(np.abs(out.cpu().numpy() - ref) <= tol)
+    err = np.abs(out.cpu().numpy() - ref)
+    assert np.all(err <= tol), float(np.max(err - tol))
+
+
+def test_decision_split_is_deterministic_and_work_is_private(sp):
+    """The split form's predict: the caller-owned work path equals the
+    stream-ordered one bit for bit, and two calls on one model from two
+    streams, each with its own work, give the same values as alone."""
+    g = np.random.default_rng(5)
+    n, d = 6000, 32
+    X = g.standard_normal((n, d)).astype(np.float32)
+    y = np.where(X[:, 0] + 0.3 * X[:, 1] > 0, 1.0, -1.0).astype(np.float32)
+    m = sp.spsvm_fit(_t(X), _t(y), 1.0 / d, 1e-3, 256, 1e-6, precision="bf16split",
+                     candidates=128, add_per_round=64, seed=3)
+    Qa = _t(g.standard_normal((40000, d)).astype(np.float32))
+    Qb = _t(g.standard_normal((1234, d)).astype(np.float32))
+    ra = sp.spsvm_predict(m, Qa)
+    rb = sp.spsvm_predict(m, Qb)
+    wa = torch.empty(sp.spsvm_predict_work_bytes(m, Qa.shape[0]), dtype=torch.uint8, device="cuda")
+    wb = torch.empty(sp.spsvm_predict_work_bytes(m, Qb.shape[0]), dtype=torch.uint8, device="cuda")
+    assert wa.numel() > 0 and wb.numel() > 0
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        fa = sp.spsvm_predict(m, Qa, stream=s1, work=wa)
+    with torch.cuda.stream(s2):
+        fb = sp.spsvm_predict(m, Qb, stream=s2, work=wb)
+    torch.cuda.synchronize()
+    assert torch.equal(fa, ra) and torch.equal(fb, rb)
+    with pytest.raises(sp.SpsvmError):
+        sp.spsvm_predict(m, Qa, work=wb[:16])
