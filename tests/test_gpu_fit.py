@@ -2,9 +2,11 @@
 
 Decision values must agree within 1e-4 relative (|f_gpu - f_orc| <=
 1e-4 max(1, |f_orc|)); active sets must agree except for points whose
-oracle margin lies within the tie band |1 - y_i o_i| <= 1e-5 (FP32 outputs
-carry ~1e-6 relative error); growth runs use the replay protocol (the
-oracle checks each GPU choice against its own scores and adopts it)."""
+oracle margin lies within the tie band |1 - y_i o_i| <= 1e-5 (the outputs
+come from FP32 kernel values in both arithmetic forms and carry ~1e-6
+relative error); ||beta_gpu - beta_orc|| <= 1e-4 ||beta_orc||; growth runs use
+the replay protocol (the oracle checks each GPU choice against its own
+scores and adopts it)."""
 import numpy as np
 import pytest
 import torch
@@ -117,31 +119,30 @@ def test_growth_replay_headline_tolerance(sp, prec):
     oracle replaying the rounds.  Held to the parity bar of the precision
     form: decision values of the model (on the training points and on fresh
     points of the mixture) within 1e-4 max(1, |f|), ||dbeta|| <= 1e-4
-    ||beta||, and active sets equal except for margin ties (|1 - y o| within
-    1e-5 for FP32; 1e-3 for BF16SPLIT, whose training outputs come from the
-    stored hi + lo kernel planes, each value rounded to 2^-17 relative)."""
+    ||beta||, and active sets equal except for margin ties |1 - y o| <= 1e-5
+    (both forms store FP32 kernel values)."""
     p = synth.gaussian_mixture(n=20000, d=128, budget=512, seed=1103, lam=1e-4)
-    m, r, J, beta = _replayed_fit(sp, p, prec, 512, 256, 64, 31,
-                                  replay_rtol=1e-4 if prec == "fp32" else 1e-3)
+    m, r, J, beta = _replayed_fit(sp, p, prec, 512, 256, 64, 31, replay_rtol=1e-4)
     rb = _cmp_beta(beta, r.beta)
     Xh, _ = synth.mixture_holdout(p, 4000, seed=77)
     for Xq in (p.X, Xh):
         f = m.predict(torch.from_numpy(Xq).cuda()).cpu().numpy().astype(np.float64)
         _cmp_decisions(f, O.predict(Xq, p.X[J], r.beta, p.gamma))
     o = m.outputs(len(p.y))
-    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64),
-                band=1e-5 if prec == "fp32" else 1e-3)
+    _cmp_decisions(o, r.o)
+    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
     print(f"{prec}: ||dbeta||/||beta|| = {rb:.2e}")
 
 
-def test_growth_replay_mnist_like_fp32(sp):
-    """The plain FP32 form on the MNIST-like generator (d = 784, 80% zero
-    features, Uniform(0,1] otherwise, labels from an RBF teacher, gamma =
-    1/(d var), lambda = 1e-4) at n = 6,000 grown to |J| = 256 (128
-    candidates, 64 per round): basis, decision values, beta and the active
-    set against the oracle's replay at the 1e-4 bar."""
+@pytest.mark.parametrize("prec", ["fp32", "bf16split"])
+def test_growth_replay_mnist_like(sp, prec):
+    """The MNIST-like generator (d = 784, 80% zero features, Uniform(0,1]
+    otherwise, labels from an RBF teacher, gamma = 1/(d var), lambda = 1e-4)
+    at n = 6,000 grown to |J| = 256 (128 candidates, 64 per round), in each
+    arithmetic form: basis, decision values, beta and the active set against
+    the oracle's replay at the 1e-4 bar."""
     p = synth.sparse_teacher(n=6000, d=784, budget=256, kappa=128, q=64, seed=1102)
-    m, r, J, beta = _replayed_fit(sp, p, "fp32", 256, 128, 64, 19, replay_rtol=1e-4)
+    m, r, J, beta = _replayed_fit(sp, p, prec, 256, 128, 64, 19, replay_rtol=1e-4)
     _cmp_beta(beta, r.beta)
     Xq = synth.queries_like(p, 2000, seed=8)
     f = m.predict(torch.from_numpy(Xq).cuda()).cpu().numpy().astype(np.float64)
@@ -190,23 +191,19 @@ def test_growth_replay_with_bias(sp, prec, score):
     assert info["rounds"] == 3 and info["n_basis"] == 96
     rep = [dict(candidates=c, chosen=ch) for c, ch in (m.round(k) for k in range(3))]
     r = O.fit(p.X, p.y, p.gamma, p.lam, 96, tol=1e-10, kappa=64, q=32, seed=9, replay=rep,
-              replay_rtol=1e-3, score=score, bias=True)
+              replay_rtol=1e-4 if score == "heuristic" else 1e-3, score=score, bias=True)
     J, beta = m.basis_and_beta()
     np.testing.assert_array_equal(J, r.J)
     b = m.bias()
     assert abs(r.bias) > 1e-2   # the labels need the bias
-    assert abs(b - r.bias) <= (1e-4 if prec == "fp32" else 1e-3) * max(1.0, abs(r.bias))
+    assert abs(b - r.bias) <= 1e-4 * max(1.0, abs(r.bias))
+    _cmp_beta(beta, r.beta)
     o = m.outputs(len(p.y))
-    # training outputs from the stored kernel matrix: BF16SPLIT's hi + lo values
-    # carry ~1e-5 relative error, so its outputs get the looser bound and tie
-    # band the other BF16SPLIT comparisons use
-    bf = prec == "bf16split"
-    _cmp_decisions(o, r.o, rtol=5e-4 if bf else 1e-4)
-    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64), band=1e-3 if bf else 1e-5)
+    _cmp_decisions(o, r.o)
+    _cmp_active(o.astype(np.float64), r.o, p.y.astype(np.float64))
     Xq = synth.queries_like(p, 300, seed=4)
     f = sp.spsvm_predict(m, torch.from_numpy(Xq).cuda()).cpu().numpy().astype(np.float64)
-    fr = O.predict(Xq, p.X[J], beta, p.gamma, b)
-    np.testing.assert_allclose(f, fr, rtol=0, atol=(1e-5 if prec == "fp32" else 5e-4) * max(1.0, np.abs(fr).max()))
+    _cmp_decisions(f, O.predict(Xq, p.X[J], r.beta, p.gamma, r.bias))
 
 
 def test_bias_argument_errors(sp):
@@ -300,7 +297,8 @@ def test_smooth_kernel_small_lambda_reaches_oracle_minimum(sp, prec):
     f_gpu = O.objective(beta, K, K[J0], yd, lam)
     f_orc = O.objective(r.beta, K, K[J0], yd, lam)
     levels = sorted({h["jitter"] for h in mdl.history()})
-    assert f_orc * (1 - 1e-9) <= f_gpu <= f_orc * (1 + 1e-3), (f_gpu, f_orc, levels)
+    print(f"{prec}: objective excess {(f_gpu - f_orc) / f_orc:.2e}, jitter levels {levels}")
+    assert f_orc * (1 - 1e-9) <= f_gpu <= f_orc * (1 + 1e-4), (f_gpu, f_orc, levels)
     if prec == "bf16split":
         assert max(levels) >= 0, levels
 
