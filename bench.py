@@ -278,7 +278,7 @@ def gram_stress_leg(sp, torch, lib, n=200_000, d=128, budget=2048, sigma_m=0.3,
                 peak_source=src)
 
 
-def serve_leg(sp, requests=100, workers=4, budget_gb=150.0, precision="bf16split"):
+def serve_leg(sp, requests=100, workers=8, budget_gb=150.0, precision="bf16split"):
     """Poisson arrivals (mean 20 requests/s) of fit requests (n log-uniform in
     [1k, 200k], d in {32, 128, 784}, |J| in {128, ..., 2048}, mixture data)
     interleaved with predict requests of 1k-100k points; HBM admission budget
@@ -790,7 +790,8 @@ def run_ours(args):
     batched = _leg(batched_leg, sp, torch) if args.batched else None
     ovo = _leg(ovo_leg, sp, torch) if args.ovo else None
     exact = _leg(exact_score_leg, sp, torch) if args.exact_score else None
-    serve = _leg(serve_leg, sp, requests=args.serve_requests) if args.serve_requests > 0 else None
+    serve = (_leg(serve_leg, sp, requests=args.serve_requests, workers=args.serve_workers)
+             if args.serve_requests > 0 else None)
 
     line = dict(metric=METRIC, value=ms / 1e3, unit="s", n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=False, scaling="weak",
@@ -841,6 +842,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--ovo", type=int, default=1, help="one-vs-one leg (10 classes, 45 pairs)")
     ap.add_argument("--exact-score", type=int, default=1,
                     help="heuristic vs exact one-dimensional selection score leg")

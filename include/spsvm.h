@@ -315,10 +315,13 @@ int spsvm_cholesky_solve(const double* L, int64_t m, int64_t ldh, double* b, voi
  * 64 x 64 tiles whose bounded waits give up after about a second
  * (spsvm_device_status then reports TIMEOUT).  spsvm_solve_mixed then
  * solves for b (device FP64, m) into x (device FP64, m) with the factor in
- * work; it synchronises the stream once per refinement step and returns OK,
- * or SPSVM_ERR_NO_CONVERGE when the residual stops shrinking (by half per
- * step) or max_iter steps do not reach tol (x then holds the last iterate).
- * iters, backward_error: host, may be NULL. */
+ * work.  The first three refinement steps are queued at once (a step's
+ * kernels return at once on the device when an earlier step reached tol),
+ * then the stream is synchronised once, and once per further step; it
+ * returns OK, or SPSVM_ERR_NO_CONVERGE when the residual stops shrinking (by
+ * half per step, from the third step on) or max_iter steps do not reach tol
+ * (x then holds the last iterate).  iters, backward_error: host, may be
+ * NULL. */
 size_t spsvm_mixed_work_bytes(int64_t m);
 int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, double shift, int32_t* info,
                          void* work, size_t work_bytes, void* stream);

@@ -450,6 +450,14 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_bwd_onepass(
 // tag's top bit set; its dependants give up at once.
 constexpr int SV_BATCH = 8;
 
+// A refinement step's kernels return at once when the solve's stop word is
+// set (the backward error was reached, or the refinement failed): the host
+// enqueues several steps ahead and checks once.
+__device__ __forceinline__ bool refine_stopped(const int* stop) {
+  return stop && *reinterpret_cast<const volatile int*>(stop) != 0;
+}
+
+
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -513,7 +521,8 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
                                                         unsigned long long* __restrict__ zt,
                                                         float* __restrict__ z,
                                                         unsigned* __restrict__ ticket, unsigned tag,
-                                                        WaitCtx wc) {
+                                                        WaitCtx wc, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ float Li[NB][NB + 1];
   __shared__ float xs[SV_BATCH][NB];
   __shared__ float v[NB];
@@ -578,7 +587,8 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
                                                         unsigned long long* __restrict__ xt,
                                                         float* __restrict__ x,
                                                         unsigned* __restrict__ ticket, unsigned tag,
-                                                        WaitCtx wc) {
+                                                        WaitCtx wc, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ float Li[NB][NB + 1];
   __shared__ float xs[SV_BATCH][NB];
   __shared__ float part[4][NB];
@@ -1053,17 +1063,18 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   }
 }
 
-// z = (float) r, and the block maxima of |r| (the right-hand side's norm on
-// the first call).
+// z = (float) r.
 __global__ void __launch_bounds__(MX_T) to_f32_vec(const double* __restrict__ r, int64_t m,
-                                                   float* __restrict__ z) {
+                                                   float* __restrict__ z, const int* stop) {
+  if (refine_stopped(stop)) return;
   const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
   if (i < m) z[i] = f64_to_f32_rn(r[i]);
 }
 
 // x += (double) z; block maxima of |x|.
 __global__ void __launch_bounds__(MX_T) add_f32(double* __restrict__ x, const float* __restrict__ z,
-                                                int64_t m, double* __restrict__ xmax) {
+                                                int64_t m, double* __restrict__ xmax, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ double wm[MX_T / 32];
   const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
   double a = 0.0;
@@ -1092,7 +1103,8 @@ __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ 
                                                      const double* __restrict__ b,
                                                      const double* __restrict__ x,
                                                      double* __restrict__ r,
-                                                     double* __restrict__ rmax) {
+                                                     double* __restrict__ rmax, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ double wm[MX_T / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (MX_T / 32) + w;
@@ -1145,7 +1157,8 @@ __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ 
 __global__ void __launch_bounds__(MX_T) max3(const double* __restrict__ a, int64_t na,
                                              const double* __restrict__ b, int64_t nb,
                                              const double* __restrict__ c, int64_t nc,
-                                             double* __restrict__ out) {
+                                             double* __restrict__ out, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ double sm[3][MX_T];
   const double* src[3] = {a, b, c};
   const int64_t n[3] = {na, nb, nc};
@@ -1420,7 +1433,8 @@ __global__ void __launch_bounds__(LR_INV_T) lr_invert(float* __restrict__ C, int
 // columns; thread t: column t % 16, rows t / 16 + 16 q of the slice.
 __global__ void __launch_bounds__(256) lr_dots(const float* __restrict__ V, int64_t ldv, int64_t m,
                                               const float* __restrict__ z, int64_t ldp,
-                                              float* __restrict__ sp) {
+                                              float* __restrict__ sp, const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ float part[16][LR_G + 1];
   const int c = threadIdx.x & 15, rr = threadIdx.x >> 4;
   const int a = blockIdx.x * LR_G + c;
@@ -1443,7 +1457,9 @@ __global__ void __launch_bounds__(256) lr_dots(const float* __restrict__ V, int6
 __global__ void __launch_bounds__(256) lr_update(const float* __restrict__ V, int64_t ldv, int64_t m,
                                                 const float* __restrict__ Ci, int64_t ldc,
                                                 const float* __restrict__ sp, int64_t slices,
-                                                int64_t ldp, int32_t k, float* __restrict__ z) {
+                                                int64_t ldp, int32_t k, float* __restrict__ z,
+                                                const int* stop) {
+  if (refine_stopped(stop)) return;
   __shared__ float ws[SPSVM_LOWRANK_KMAX];
   __shared__ float ss[SPSVM_LOWRANK_KMAX];
   for (int a = threadIdx.x; a < k; a += 256) {
@@ -1468,6 +1484,37 @@ __global__ void __launch_bounds__(256) lr_update(const float* __restrict__ V, in
     for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
     if (c == 0 && i < m) z[i] -= v;
   }
+}
+
+// The refinement's state on the device: stop word (0 running, 1 backward
+// error reached, 2 stagnation, 3 not finite, 4 the FP32 factorisation broke
+// down), steps taken, the last backward error and residual norm.
+struct RefineState {
+  int32_t stop, iters;
+  double be, rprev;
+};
+
+// After refinement step `it`: the normwise backward error
+// ||r|| / (||H + shift I|| ||x|| + ||b||) from the norms, and the stop word.
+// Stagnation (the residual norm not halved) counts from the third step, the
+// first two being the FP32 solve and its first correction.
+__global__ void refine_decide(const double* __restrict__ norms, const int32_t* __restrict__ finfo,
+                              int it, double tol, void* state) {
+  RefineState* st = static_cast<RefineState*>(state);
+  if (threadIdx.x != 0 || st->stop) return;
+  if (finfo && *finfo != 0) {
+    st->stop = 4;
+    return;
+  }
+  const double hn = norms[0], bn = norms[1], xn = norms[4], rn = norms[5];
+  const double denom = hn * xn + bn;
+  const double be = denom > 0.0 ? rn / denom : 0.0;
+  st->iters = it + 1;
+  st->be = be;
+  if (!(be == be)) st->stop = 3;
+  else if (be <= tol) st->stop = 1;
+  else if (it >= 2 && rn > 0.5 * st->rprev) st->stop = 2;
+  st->rprev = rn;
 }
 
 }  // namespace
@@ -1654,7 +1701,7 @@ constexpr int kTicketSteps = 64;   // refinement steps between ticket resets
 
 struct MixedLayout {
   int64_t ldl, B, nrow_blocks, nvec_blocks;
-  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, dag, total;
+  size_t L, sw, sw_bytes, z32, r, rowmax, xmax, rmax, bmax, norms, state, dag, total;
   int64_t tiles;   // tile rows of the factor
 };
 
@@ -1678,6 +1725,7 @@ MixedLayout mixed_layout(int64_t m) {
   ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
   ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
   ly.norms = off;  off += al(8 * 8);
+  ly.state = off;  off += al(sizeof(RefineState));
   ly.tiles = ceil_div(m, (int64_t)DT);
   ly.dag = off;    off += al((size_t)(ly.tiles * ly.tiles + 1) * 4);   // tile flags, ticket
   ly.total = off;
@@ -1754,6 +1802,9 @@ struct LowRankView {
 
 }  // namespace
 
+// Refinement steps queued before the first host check.
+constexpr int kRefineAhead = 3;
+
 static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shift,
                             const double* b, double* x, int32_t max_iter, double tol,
                             int32_t* iters, double* backward_error, void* work,
@@ -1787,73 +1838,88 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
   const unsigned vb = (unsigned)ly.nvec_blocks, rb = (unsigned)ly.nrow_blocks;
   const bool vec = (ldh % 2) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  RefineState* state = reinterpret_cast<RefineState*>(w + ly.state);
+  const int* stop = &state->stop;
   WaitCtx wc;
   SPSVM_TRY(wait_ctx(s, &wc));
   SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
   SPSVM_CUDA_TRY(cudaMemsetAsync(tagged_region, 0, tagged_bytes, s));
+  SPSVM_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(RefineState), s));
   SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
   absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax);
   SPSVM_LAUNCH_CHECK();
-  // norms[0] = ||H + shift I||_inf, norms[3] = ||b||_inf
-  max3<<<1, MX_T, 0, s>>>(rowmax, m, bmax, ly.nvec_blocks, nullptr, 0, norms);
+  // norms[0] = ||H + shift I||_inf, norms[1] = ||b||_inf
+  max3<<<1, MX_T, 0, s>>>(rowmax, m, bmax, ly.nvec_blocks, nullptr, 0, norms, nullptr);
   SPSVM_LAUNCH_CHECK();
-  double hn[3] = {0, 0, 0};
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  double prev = INFINITY;
-  for (int it = 0; it < max_iter; ++it) {
-    // z = (L L^T)^{-1} r in FP32, x += z, r = b - (H + shift I) x in FP64
-    to_f32_vec<<<vb, MX_T, 0, s>>>(r, m, z32);
+  // One refinement step: z = (L L^T)^{-1} r in FP32, x += z, r = b - (H +
+  // shift I) x in FP64, then the stop word.  Every kernel of a step returns
+  // at once once the stop word is set.
+  auto step = [&](int it) -> int {
+    to_f32_vec<<<vb, MX_T, 0, s>>>(r, m, z32, stop);
     SPSVM_LAUNCH_CHECK();
     // tags 1, 2, ... (the tagged words start zeroed); tickets per step
     const unsigned tag = (unsigned)(it + 1);
     if (it > 0 && it % kTicketSteps == 0)
       SPSVM_CUDA_TRY(cudaMemsetAsync(tickets, 0, (size_t)2 * kTicketSteps * 4, s));
     unsigned* tk = tickets + 2 * (it % kTicketSteps);
-    trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag, wc);
+    trsv32_fwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, z32, zt, zw, tk, tag, wc, stop);
     SPSVM_LAUNCH_CHECK();
     if (lr) {   // z <- (I - V C^{-1} V^T) z
       lr_dots<<<dim3((unsigned)lr->G, (unsigned)lr->slices), 256, 0, s>>>(lr->V, lr->ldv, m, zw,
-                                                                          lr->ldv, lr->s);
+                                                                          lr->ldv, lr->s, stop);
       SPSVM_LAUNCH_CHECK();
       lr_update<<<(unsigned)min64(ceil_div(m, (int64_t)16), 2 * (int64_t)sm_count()), 256, 0, s>>>(
-          lr->V, lr->ldv, m, lr->Ci, lr->ldv, lr->s, lr->slices, lr->ldv, lr->k, zw);
+          lr->V, lr->ldv, m, lr->Ci, lr->ldv, lr->s, lr->slices, lr->ldv, lr->k, zw, stop);
       SPSVM_LAUNCH_CHECK();
     }
-    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag, wc);
+    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag, wc, stop);
     SPSVM_LAUNCH_CHECK();
-    add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax);
+    add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax, stop);
     SPSVM_LAUNCH_CHECK();
     if (vec)
-      residual_f64<true><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
+      residual_f64<true><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax, stop);
     else
-      residual_f64<false><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax);
+      residual_f64<false><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax, stop);
     SPSVM_LAUNCH_CHECK();
-    max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4);
+    max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4, stop);
     SPSVM_LAUNCH_CHECK();
-    // the first step never reaches FP64 backward error from an FP32 factor:
-    // the first check (a host round trip) follows the second step
-    if (it == 0 && max_iter > 1) continue;
-    double nv[2] = {0, 0};
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(nv, norms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    int32_t finfo = 0;
-    if (factor_info && it <= 1)
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(&finfo, factor_info, sizeof(finfo), cudaMemcpyDeviceToHost, s));
-    int32_t code = 0;
-    SPSVM_TRY(device_status_on(s, &code));   // synchronises s
-    if (finfo != 0)
-      return set_error(SPSVM_ERR_NOT_PD, "solve_mixed: the FP32 factorisation broke down at pivot %d",
-                       finfo - 1);
-    const double denom = hn[0] * nv[0] + hn[1];
-    const double be = denom > 0.0 ? nv[1] / denom : 0.0;
-    if (iters) *iters = it + 1;
-    if (backward_error) *backward_error = be;
-    if (!(be == be)) return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: not finite");
-    if (be <= tol) return SPSVM_OK;
-    if (it > 0 && nv[1] > 0.5 * prev)
-      return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: refinement stagnates (backward error %.3g)", be);
-    prev = nv[1];
+    refine_decide<<<1, 32, 0, s>>>(norms, it <= 1 ? factor_info : nullptr, it, tol, state);
+    SPSVM_LAUNCH_CHECK();
+    return SPSVM_OK;
+  };
+  // an FP32 factor reaches FP64 backward error in about three steps: they
+  // are queued before the first host check, later ones one at a time
+  int it = 0;
+  for (; it < max_iter && it < kRefineAhead; ++it) SPSVM_TRY(step(it));
+  for (;;) {
+    RefineState h{};
+    const ReadChunk c{&h, state, sizeof(h)};
+    SPSVM_TRY(read_back(s, &c, 1));
+    if (iters) *iters = h.iters;
+    if (backward_error) *backward_error = h.be;
+    switch (h.stop) {
+      case 1:
+        return SPSVM_OK;
+      case 2:
+        return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: refinement stagnates (backward error %.3g)",
+                         h.be);
+      case 3:
+        return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: not finite");
+      case 4: {
+        int32_t fi = 0;
+        const ReadChunk cf{&fi, factor_info, sizeof(fi)};
+        SPSVM_TRY(read_back(s, &cf, 1));
+        return set_error(SPSVM_ERR_NOT_PD, "solve_mixed: the FP32 factorisation broke down at pivot %d",
+                         fi - 1);
+      }
+      default:
+        break;
+    }
+    if (it >= max_iter)
+      return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: %d iterations not enough", max_iter);
+    SPSVM_TRY(step(it));
+    ++it;
   }
-  return set_error(SPSVM_ERR_NO_CONVERGE, "solve_mixed: %d iterations not enough", max_iter);
 }
 
 extern "C" int spsvm_solve_mixed(const double* H, int64_t m, int64_t ldh, double shift,

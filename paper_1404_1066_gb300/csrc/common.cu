@@ -136,20 +136,62 @@ int wait_ctx(cudaStream_t s, WaitCtx* w) {
   return SPSVM_OK;
 }
 
-int device_status_on(cudaStream_t s, int32_t* code) {
+namespace {
+// Pinned staging memory of one host thread for read_back (grown on demand,
+// released at thread exit).
+struct PinnedStage {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local PinnedStage t_stage;
+
+int read_back_code(cudaStream_t s, const ReadChunk* c, int n, int32_t* code) {
+  size_t total = 16;
+  for (int k = 0; k < n; ++k) total += (size_t)round_up((int64_t)c[k].bytes, 16);
+  if (t_stage.bytes < total) {
+    if (t_stage.p) cudaFreeHost(t_stage.p);
+    t_stage.p = nullptr;
+    t_stage.bytes = 0;
+    const size_t want = total < 4096 ? 4096 : total;
+    SPSVM_CUDA_TRY(cudaMallocHost(&t_stage.p, want));
+    t_stage.bytes = want;
+  }
   WaitCtx w;
   SPSVM_TRY(wait_ctx(s, &w));
-  int v = 0;
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(&v, w.st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  char* h = static_cast<char*>(t_stage.p);
+  size_t off = 16;
+  for (int k = 0; k < n; ++k) {
+    if (c[k].bytes)
+      SPSVM_CUDA_TRY(cudaMemcpyAsync(h + off, c[k].src, c[k].bytes, cudaMemcpyDeviceToHost, s));
+    off += (size_t)round_up((int64_t)c[k].bytes, 16);
+  }
+  SPSVM_CUDA_TRY(cudaMemcpyAsync(h, w.st, sizeof(int), cudaMemcpyDeviceToHost, s));
   SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+  off = 16;
+  for (int k = 0; k < n; ++k) {
+    if (c[k].bytes) memcpy(c[k].dst, h + off, c[k].bytes);
+    off += (size_t)round_up((int64_t)c[k].bytes, 16);
+  }
+  int v = 0;
+  memcpy(&v, h, sizeof(int));
+  if (code) *code = v;
   if (v != 0) {
     SPSVM_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(int), s));
     SPSVM_CUDA_TRY(cudaStreamSynchronize(s));
+    return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", v);
   }
-  if (code) *code = v;
-  if (v != 0) return set_error(SPSVM_ERR_TIMEOUT, "a bounded device wait gave up (site %d)", v);
   return SPSVM_OK;
 }
+}  // namespace
+
+int read_back(cudaStream_t s, const ReadChunk* chunks, int n) {
+  return read_back_code(s, chunks, n, nullptr);
+}
+
+int device_status_on(cudaStream_t s, int32_t* code) { return read_back_code(s, nullptr, 0, code); }
 
 // ---- kernel timing -----------------------------------------------------
 namespace {

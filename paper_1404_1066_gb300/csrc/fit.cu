@@ -418,6 +418,13 @@ struct Fit {
     return device_status_on(s, &code);
   }
 
+  // bytes from device memory to the host after the work queued on the
+  // stream, with the bounded-wait check, through one synchronisation
+  int read(void* dst, const void* src, size_t bytes) {
+    const ReadChunk c{dst, src, bytes};
+    return read_back(s, &c, 1);
+  }
+
   // Refresh active flags and stats from the current o into buffer `which`.
   int flags(int which, double stats_host[3]) {
     spsvm_kmat K = kmat();
@@ -425,8 +432,7 @@ struct Fit {
     double* st = at<double>(L.off_small);
     SPSVM_TRY(spsvm_outputs(&K, nullptr, y, at<float>(L.off_o), act, st, ws + L.off_scratch,
                             L.scratch_bytes, s));
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(stats_host, st, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    return sync();
+    return read(stats_host, st, 3 * sizeof(double));
   }
 
   int newton() {
@@ -459,8 +465,7 @@ struct Fit {
     double st[3];
     SPSVM_TRY(spsvm_outputs(&K, beta, y, o, at<uint8_t>(act_cur ? L.off_act1 : L.off_act0),
                             at<double>(L.off_small), scratch, sb, s));
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(st, at<double>(L.off_small), sizeof(st), cudaMemcpyDeviceToHost, s));
-    SPSVM_TRY(sync());
+    SPSVM_TRY(read(st, at<double>(L.off_small), sizeof(st)));
     int32_t status = SPSVM_ERR_NO_CONVERGE;
     double* tmp2 = at<double>(L.off_tmp2);
     void* mixw = ws + L.off_mix;
@@ -509,8 +514,7 @@ struct Fit {
       step_norms<<<1, 256, 0, s>>>(dir, beta, m, dots + 4);
       SPSVM_LAUNCH_CHECK();
       double v[2];
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(v, dots + 4, sizeof(v), cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
+      SPSVM_TRY(read(v, dots + 4, sizeof(v)));
       *small = std::sqrt(v[0]) <= kStepTol * std::sqrt(v[1]);
       return SPSVM_OK;
     };
@@ -565,8 +569,7 @@ struct Fit {
       SPSVM_LAUNCH_CHECK();
       SPSVM_TRY(grad_pass(at<uint8_t>(nxt ? L.off_act1 : L.off_act0), ndiff));
       alignas(8) unsigned char sm_h[kSmallRead];
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(sm_h, small, kSmallRead, cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
+      SPSVM_TRY(read(sm_h, small, kSmallRead));
       int32_t err = 0;
       std::memcpy(&err, sm_h + 208, sizeof(err));
       if (err) return set_error(SPSVM_ERR_TIMEOUT, "line_search: grid barrier timed out");
@@ -577,8 +580,7 @@ struct Fit {
       return SPSVM_OK;
     };
     SPSVM_TRY(grad_pass(at<uint8_t>(act_cur ? L.off_act1 : L.off_act0), nullptr));
-    SPSVM_CUDA_TRY(cudaMemcpyAsync(dh, dots, sizeof(dh), cudaMemcpyDeviceToHost, s));
-    SPSVM_TRY(sync());
+    SPSVM_TRY(read(dh, dots, sizeof(dh)));
     for (int it = 0; it < op.max_newton; ++it) {
       uint8_t* act = at<uint8_t>(act_cur ? L.off_act1 : L.off_act0);
       const double gnorm = std::sqrt(dh[1]), rnorm = std::sqrt(dh[2]);
@@ -660,8 +662,7 @@ struct Fit {
         SPSVM_TRY(spsvm_active_diff(&K, act, anchor, kmax, Wt, SPSVM_LOWRANK_KMAX, sgn, kdev, scratch,
                                     sb, s));
         int32_t kk = 0;
-        SPSVM_CUDA_TRY(cudaMemcpyAsync(&kk, kdev, sizeof(kk), cudaMemcpyDeviceToHost, s));
-        SPSVM_TRY(sync());
+        SPSVM_TRY(read(&kk, kdev, sizeof(kk)));
         if (kk >= 1 && kk <= kmax) {
           SPSVM_TRY(gram_impl(&Kc, n_active, n, &K, Jd, lambda, op.precision, H, ldH, scratch, sb, s,
                               st[2], at<double>(L.off_kjj), L.jcap));
@@ -670,8 +671,7 @@ struct Fit {
           SPSVM_TRY(spsvm_lowrank_factor(mixw, L.mix_bytes, m, Wt, SPSVM_LOWRANK_KMAX, sgn, kk, lrw,
                                          L.lr_bytes, lr_info, s));
           int32_t li = 1;
-          SPSVM_CUDA_TRY(cudaMemcpyAsync(&li, lr_info, sizeof(li), cudaMemcpyDeviceToHost, s));
-          SPSVM_TRY(sync());
+          SPSVM_TRY(read(&li, lr_info, sizeof(li)));
           if (li == 0) {
             lr_k = kk;
             SPSVM_TRY(try_direction(FAC_LOWRANK, 0.0, &stepped));
@@ -703,8 +703,7 @@ struct Fit {
           if (lv >= 0 && tr < 0.0) {
             diag_sum<<<1, 256, 0, s>>>(H, ldH, m, dots + 3);
             SPSVM_LAUNCH_CHECK();
-            SPSVM_CUDA_TRY(cudaMemcpyAsync(&tr, dots + 3, sizeof(tr), cudaMemcpyDeviceToHost, s));
-            SPSVM_TRY(sync());
+            SPSVM_TRY(read(&tr, dots + 3, sizeof(tr)));
           }
           shift = lv >= 0 ? std::pow(10.0, lv - 10) * tr / m : 0.0;
           int32_t info_h = 0;
@@ -735,8 +734,7 @@ struct Fit {
           }
           h_fresh = false;
           SPSVM_TRY(spsvm_cholesky(H, m, ldH, info, ws + L.off_chw, L.chw_bytes, s));
-          SPSVM_CUDA_TRY(cudaMemcpyAsync(&info_h, info, sizeof(info_h), cudaMemcpyDeviceToHost, s));
-          SPSVM_TRY(sync());
+          SPSVM_TRY(read(&info_h, info, sizeof(info_h)));
           if (info_h == 0) {
             jitter = lv;
             SPSVM_CUDA_TRY(cudaMemcpyAsync(dir, rhs, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -860,9 +858,7 @@ struct Fit {
           SPSVM_LAUNCH_CHECK();
         }
       }
-      SPSVM_CUDA_TRY(cudaMemcpyAsync(delta.data(), at<double>(L.off_cd), nc * 8,
-                                     cudaMemcpyDeviceToHost, s));
-      SPSVM_TRY(sync());
+      SPSVM_TRY(read(delta.data(), at<double>(L.off_cd), nc * 8));
       const int32_t qq = std::min<int32_t>(std::min(op.q, budget - (m - nb0)), nc);
       std::vector<int32_t> order(nc);
       std::iota(order.begin(), order.end(), 0);

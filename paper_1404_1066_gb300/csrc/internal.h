@@ -169,6 +169,18 @@ __device__ __forceinline__ void wait_gave_up(const WaitCtx& w, int code) { atomi
 // (stream-ordered copies; returns TIMEOUT with *code set when a wait gave up).
 int device_status_on(cudaStream_t s, int32_t* code);
 
+// Device-to-host reads after the work queued on s: every chunk and the
+// stream's status word are copied in order on s into a pinned staging
+// buffer of the calling thread, s is synchronised once, and the chunks are
+// copied out.  Returns TIMEOUT (status word taken and cleared) when a
+// bounded wait gave up on s.
+struct ReadChunk {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+int read_back(cudaStream_t s, const ReadChunk* chunks, int n);
+
 // spsvm_line_search with Eq. 4's bias in basis slot 0 (point index -1):
 // b0 = &beta_0 on the device, or NULL without a bias.
 int line_search_impl(const float* o, const float* u, const float* y, int64_t n, const double* d,

@@ -2,9 +2,9 @@
 
 Decision values must agree within 1e-4 relative (|f_gpu - f_orc| <=
 1e-4 max(1, |f_orc|)); active sets must agree except for points whose
-oracle margin lies within the tie band |1 - y_i o_i| <= 1e-5 (the outputs
-come from FP32 kernel values in both arithmetic forms and carry ~1e-6
-relative error); ||beta_gpu - beta_orc|| <= 1e-4 ||beta_orc||; growth runs use
+oracle margin lies within the tie band |1 - y_i o_i| <= 1e-6 (the outputs
+come from FP32 kernel values in both arithmetic forms); ||beta_gpu -
+beta_orc|| <= 1e-4 ||beta_orc||; growth runs use
 the replay protocol (the oracle checks each GPU choice against its own
 scores and adopts it)."""
 import numpy as np
@@ -30,11 +30,14 @@ def _cmp_decisions(f_gpu, f_orc, rtol=1e-4):
     assert np.all(err <= bound), f"max err/bound {np.max(err / bound):.3g}"
 
 
-def _cmp_active(o_gpu, o_orc, y, band=1e-5):
+def _cmp_active(o_gpu, o_orc, y, band=1e-6):
     Sg = y * o_gpu < 1
     So = y * o_orc < 1
     tie = np.abs(1 - y * o_orc) <= band
-    assert np.all((Sg == So) | tie), int(np.sum((Sg != So) & ~tie))
+    diff = Sg != So
+    need = float(np.max(np.abs(1 - y * o_orc)[diff])) if diff.any() else 0.0
+    print(f"active sets: {int(diff.sum())} of {len(y)} differ, widest margin among them {need:.2e}")
+    assert np.all(~diff | tie), int(np.sum(diff & ~tie))
 
 
 @pytest.mark.parametrize("prec", ["fp32"])
@@ -119,7 +122,7 @@ def test_growth_replay_headline_tolerance(sp, prec):
     oracle replaying the rounds.  Held to the parity bar of the precision
     form: decision values of the model (on the training points and on fresh
     points of the mixture) within 1e-4 max(1, |f|), ||dbeta|| <= 1e-4
-    ||beta||, and active sets equal except for margin ties |1 - y o| <= 1e-5
+    ||beta||, and active sets equal except for margin ties |1 - y o| <= 1e-6
     (both forms store FP32 kernel values)."""
     p = synth.gaussian_mixture(n=20000, d=128, budget=512, seed=1103, lam=1e-4)
     m, r, J, beta = _replayed_fit(sp, p, prec, 512, 256, 64, 31, replay_rtol=1e-4)
