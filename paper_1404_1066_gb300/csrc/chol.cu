@@ -310,9 +310,29 @@ __device__ unsigned wait_flag(const unsigned* f, int code, const WaitCtx& w) {
 // Inverse of the 64 x 64 diagonal block at r0 (lower), Li[i][j], from the
 // transposed copy diag_inverse leaves in the upper triangle; zero-padded
 // past nb.
+// All of a thread's loads are issued before its first store (the block is
+// read at the start of every solve CTA, the first one's on the critical path).
 template <typename T>
 __device__ __forceinline__ void load_diag_inverse(const T* __restrict__ L, int64_t ldh,
                                                   int64_t r0, int nb, T (*Li)[NB + 1]) {
+  if (blockDim.x == SV_THREADS) {
+    constexpr int PER = NB * NB / SV_THREADS;
+    T v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + SV_THREADS * u;
+      const int j = e / NB, i = e % NB;   // stored at (row r0 + j, column r0 + i)
+      v[u] = T(0);
+      if (i < nb && j < nb && j <= i) v[u] = L[(r0 + j) * ldh + r0 + i];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + SV_THREADS * u;
+      const int j = e / NB, i = e % NB;
+      Li[i][j] = (i == j && i < nb) ? T(1) / v[u] : v[u];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int j = e / NB, i = e % NB;   // stored at (row r0 + j, column r0 + i)
     T v = 0.0;
@@ -540,10 +560,17 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
   const float* __restrict__ Lrow = L + (r0 + (row_ok ? r : 0)) * ldh + 16 * q;
   float acc = 0.0f;
   bool ok = true;
-  for (int64_t j = 0; j < k;) {
-    float a[16];
+  // the row's values against block jj (zeros past k); blocks j (a) and
+  // j + 1 (nxt) are loaded a step ahead of their use
+  auto ld = [&](float (&v)[16], int64_t jj) {
+    const bool in = row_ok && jj < k;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) a[c] = row_ok ? __ldg(Lrow + j * NB + c) : 0.0f;
+    for (int c = 0; c < 16; ++c) v[c] = in ? __ldg(Lrow + jj * NB + c) : 0.0f;
+  };
+  float a[16], nxt[16];
+  ld(a, 0);
+  ld(nxt, 1);
+  for (int64_t j = 0; j < k;) {
     if (t < 32) {
       const int g = grab_blocks(zt, m, j, 1, (int)min64(SV_BATCH, k - j), tag, xs, 221, wc);
       if (t == 0) n_s = g;
@@ -556,13 +583,24 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc = fmaf(a[c], xs[0][16 * q + c], acc);
-    for (int u = 1; u < got; ++u) {
+    if (got > 1) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc = fmaf(nxt[c], xs[1][16 * q + c], acc);
+    }
+    for (int u = 2; u < got; ++u) {
 #pragma unroll
       for (int c = 0; c < 16; ++c)
         acc = fmaf(row_ok ? __ldg(Lrow + (j + u) * NB + c) : 0.0f, xs[u][16 * q + c], acc);
     }
     __syncthreads();   // xs free again
     j += got;
+    if (got == 1) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a[c] = nxt[c];
+    } else {
+      ld(a, j);
+    }
+    ld(nxt, j + 1);
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -607,12 +645,19 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
   const bool col_ok = c < nb;
   float acc = 0.0f;
   bool ok = true;
-  for (int64_t j = B - 1; j > k;) {   // later blocks, last first
-    float a[16];
-    const int64_t rb = j * NB + 16 * g;
+  // block jj's rows against this block's column (zeros at or before k);
+  // blocks j (a) and j - 1 (nxt) are loaded a step ahead of their use
+  auto ld = [&](float (&v)[16], int64_t jj) {
+    const int64_t rb = jj * NB + 16 * g;
+    const bool live = col_ok && jj > k;
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr)
-      a[rr] = (col_ok && rb + rr < m) ? __ldg(L + (rb + rr) * ldh + r0 + c) : 0.0f;
+      v[rr] = (live && rb + rr < m) ? __ldg(L + (rb + rr) * ldh + r0 + c) : 0.0f;
+  };
+  float a[16], nxt[16];
+  ld(a, B - 1);
+  ld(nxt, B - 2);
+  for (int64_t j = B - 1; j > k;) {   // later blocks, last first
     if (t < 32) {
       const int gb = grab_blocks(xt, m, j, -1, (int)min64(SV_BATCH, j - k), tag, xs, 222, wc);
       if (t == 0) n_s = gb;
@@ -625,7 +670,11 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
     }
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) acc = fmaf(a[rr], xs[0][16 * g + rr], acc);
-    for (int u = 1; u < got; ++u) {
+    if (got > 1) {
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) acc = fmaf(nxt[rr], xs[1][16 * g + rr], acc);
+    }
+    for (int u = 2; u < got; ++u) {
       const int64_t rbu = (j - u) * NB + 16 * g;   // a full block (only the last is partial)
 #pragma unroll
       for (int rr = 0; rr < 16; ++rr)
@@ -633,6 +682,13 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
     }
     __syncthreads();
     j -= got;
+    if (got == 1) {
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) a[rr] = nxt[rr];
+    } else {
+      ld(a, j);
+    }
+    ld(nxt, j - 1);
   }
   part[g][c] = acc;
   __syncthreads();

@@ -1,19 +1,19 @@
-// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16SPLIT form.  Every
-// FP32 operand x is split as hi + lo (both BF16, lo = bf16(x - hi)) and a
-// product x*z is formed as hi*hi + hi*lo + lo*hi + lo*lo (four BF16 MMAs
-// accumulating in FP32 in TMEM): the exact product of the two-term
-// representations, whose own error is below 2^-17 of |x z|.
+// tcgen05 (sm_103a) tensor-core kernels of the SPSVM_BF16SPLIT form.
 //
-//   * kernel block / candidate scores (RBF kernel of Section 2 through the
-//     distance expansion; the basis-vector score of Section 4): points X
-//     (TMA, 128 rows per tile) times gathered basis / candidate rows, fused
-//     epilogue exp(-gamma max(0, |x|^2 + |z|^2 - 2 x.z)) that either stores
-//     the kernel values (FP32, or hi / lo planes) or reduces the score sums
-//     without storing them;
+//   * kernel block / candidate scores / decision values (RBF kernel of
+//     Section 2 through the distance expansion; the basis-vector score of
+//     Section 4; the classifier h(x) = w^T phi(x) on the basis): points X
+//     (TMA, 128 rows per tile) times gathered basis / candidate rows, each
+//     FP32 value split into three BF16 terms hi + mid + lo (exact) and
+//     multiplied as six products, with a fused epilogue
+//     exp(-gamma max(0, |x|^2 + |z|^2 - 2 x.z)) that stores the kernel
+//     values (FP32), or reduces the score sums or the beta-weighted decision
+//     sums without storing them;
 //   * masked Gram matrix K_SJ^T K_SJ (the Hessian term of Eq. 4 on the
-//     active set): warp-specialised TMA producer / MMA issuer / epilogue over
-//     128 x 128 upper-triangular tiles with two TMEM accumulators, FP32
-//     partial sums per 8192 points promoted to FP64.
+//     active set): the compact copy split as hi + lo (lo = bf16(x - hi)) and
+//     all four plane products, warp-specialised TMA producer / MMA issuer /
+//     epilogue over 128 x 128 upper-triangular tiles with two TMEM
+//     accumulators, FP32 partial sums per 8192 points promoted to FP64.
 #include <cudaTypedefs.h>
 
 #include <mutex>
