@@ -110,6 +110,23 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j): after
+// five exchange steps, each halving the columns a lane holds and summing
+// the pair, lane l holds the sum of column l (31 shuffles in all).
+__device__ __forceinline__ float warp_column_sums(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float give = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, give, h);
+    }
+  }
+  return v[0];
+}
+
 // Block sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh /* >= 32 entries */) {

@@ -5,8 +5,10 @@
 // the current bracket and counts the breakpoints m_i / v_i inside each of
 // the 32 cells, so that the root is solved exactly on a cell free of
 // breakpoints.  The whole search is one cooperative launch: all CTAs make a
-// pass, CTA 0 reduces it and picks the next bracket, and two grid barriers
-// (bounded waits) separate the passes -- no host round trip per pass.
+// pass and write their partial sums; after a grid barrier, 65 CTAs each
+// reduce one of the pass's values over the CTAs (a fixed order); after a
+// second barrier every CTA reads the 65 totals and takes the same decision
+// on the next bracket -- no host round trip per pass.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -22,16 +24,25 @@ constexpr int LC = LP - 1;      // cells
 constexpr int LT = 256;
 constexpr int kMaxPasses = 64;  // the search needs at most 1 + 12 + 9
 
-struct LsPart {
-  double F[LP];
-  int32_t cnt[LC];
-};
-
-// Bracket handed from CTA 0 to all CTAs between passes, and the result.
+// Result of the search (CTA 0 writes it) and the barrier's error word.
 struct LsState {
   double lo, hi, t;
   int32_t done, err;
 };
+
+// Scratch after the state and the barrier words: the pass totals (phi' sums
+// at the grid points, breakpoint counts per cell, and a0, a1), then the
+// CTAs' partials transposed (value-major, so one CTA reads one value's
+// partials contiguously).
+struct LsTotals {
+  double F[LP];
+  double a[2];
+  int32_t C[LC];
+};
+constexpr size_t kLsHead = 256;                       // state, barrier
+constexpr size_t kLsTotals = 1024;                    // LsTotals, padded
+constexpr size_t kLsPartOff = kLsHead + kLsTotals;
+static_assert(sizeof(LsTotals) <= kLsTotals, "line search totals");
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -76,7 +87,8 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
 // One pass of this CTA over its points for the bracket [lo, hi].
 __device__ void ls_pass(const float* __restrict__ o, const float* __restrict__ u,
                         const float* __restrict__ y, int64_t n, double lo, double hi,
-                        LsPart* __restrict__ part, double (*red)[LP], int32_t* cnt) {
+                        double* __restrict__ PF, int32_t* __restrict__ PC, double (*red)[LP],
+                        int32_t* cnt) {
   if (threadIdx.x < LC) cnt[threadIdx.x] = 0;
   __syncthreads();
   const double h = (hi - lo) / (double)LC;
@@ -109,18 +121,23 @@ __device__ void ls_pass(const float* __restrict__ o, const float* __restrict__ u
     }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // warp sums: grid points 0..31 by the column-sum exchange (lane k ends
+  // with point k), point 32 by a plain reduction
+  float v32[32];
 #pragma unroll
-  for (int k = 0; k < LP; ++k) {
-    const double s = warp_sum((double)F[k]);
-    if (lane == 0) red[w][k] = s;
-  }
+  for (int k = 0; k < 32; ++k) v32[k] = F[k];
+  const float fk = warp_column_sums(v32, lane);
+  const float f32 = warp_sum(F[LP - 1]);
+  red[w][lane] = (double)fk;
+  if (lane == 0) red[w][LP - 1] = (double)f32;
   __syncthreads();
+  const unsigned G = gridDim.x;
   if (threadIdx.x < LP) {
     double s = 0.0;
     for (int q = 0; q < LT / 32; ++q) s += red[q][threadIdx.x];
-    part->F[threadIdx.x] = s;
+    PF[(size_t)threadIdx.x * G + blockIdx.x] = s;
   }
-  if (threadIdx.x < LC) part->cnt[threadIdx.x] = cnt[threadIdx.x];
+  if (threadIdx.x < LC) PC[(size_t)threadIdx.x * G + blockIdx.x] = cnt[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
@@ -128,18 +145,23 @@ __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
                                                 const float* __restrict__ y, int64_t n,
                                                 const double* __restrict__ d,
                                                 const int64_t* __restrict__ J, int32_t m,
-                                                double lambda, LsPart* __restrict__ part,
+                                                double lambda, char* __restrict__ work,
                                                 LsState* __restrict__ st, unsigned* __restrict__ bar,
                                                 const double* __restrict__ b0) {
   __shared__ double red[LT / 32][LP];
   __shared__ int32_t cnt[LC];
   __shared__ double Fs[LP], sh[32];
   __shared__ int32_t Cs[LC];
+  __shared__ double a_s[2];
   __shared__ double lo_s, hi_s;
   __shared__ int done_s;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int t = threadIdx.x;
   const unsigned nb = gridDim.x;
-  // CTA 0, thread 0 carries the search state across passes
+  LsTotals* tot = reinterpret_cast<LsTotals*>(work + kLsHead);
+  double* PF = reinterpret_cast<double*>(work + kLsPartOff);
+  int32_t* PC = reinterpret_cast<int32_t*>(PF + (size_t)LP * nb);
+  // thread 0 of every CTA carries the search state across passes (all CTAs
+  // see the same totals and take the same decisions)
   double a0 = 0.0, a1 = 0.0, d0 = 0.0;
   int phase = 0, grow = 0, depth = 0;
   if (t == 0) {
@@ -150,115 +172,122 @@ __global__ void __launch_bounds__(LT) ls_search(const float* __restrict__ o,
   __syncthreads();
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const double lo = lo_s, hi = hi_s;
-    ls_pass(o, u, y, n, lo, hi, &part[blockIdx.x], red, cnt);
+    ls_pass(o, u, y, n, lo, hi, PF, PC, red, cnt);
+    if (pass == 0 && blockIdx.x == nb - 1) {
+      // a0 = lambda d^T K_JJ beta, a1 = lambda d^T K_JJ d: (K_JJ beta)_k = o
+      // at basis point k (minus the bias b0 = beta_0 when slot 0, point
+      // index -1, holds it; that slot has no regulariser row)
+      const double bb = b0 ? *b0 : 0.0, db = b0 ? d[0] : 0.0;
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = t; k < m; k += LT) {
+        const int64_t j = J[k];
+        if (j < 0) continue;
+        s0 += d[k] * ((double)o[j] - bb);
+        s1 += d[k] * ((double)u[j] - db);
+      }
+      s0 = block_sum(s0, sh);
+      __syncthreads();
+      s1 = block_sum(s1, sh);
+      if (t == 0) {
+        tot->a[0] = lambda * s0;
+        tot->a[1] = lambda * s1;
+      }
+    }
     if (grid_barrier(bar, nb)) {
       if (t == 0) atomicExch(&st->err, 1);
       return;
     }
-    if (blockIdx.x == 0) {
-      // sums over the CTAs' partials, one warp per value
-      for (int v = w; v < LP + LC; v += LT / 32) {
-        if (v < LP) {
-          double sv = 0.0;
-          for (unsigned b = lane; b < nb; b += 32) sv += __ldcg(&part[b].F[v]);
-          sv = warp_sum(sv);
-          if (lane == 0) Fs[v] = sv;
-        } else {
-          int sv = 0;
-          for (unsigned b = lane; b < nb; b += 32) sv += __ldcg(&part[b].cnt[v - LP]);
-          sv = warp_sum(sv);
-          if (lane == 0) Cs[v - LP] = sv;
-        }
-      }
-      if (pass == 0) {   // a0 = lambda d^T K_JJ beta, a1 = lambda d^T K_JJ d
-        // (K_JJ beta)_k = o at basis point k (minus the bias b0 = beta_0 when
-        // slot 0, point index -1, holds it; that slot has no regulariser row)
-        const double bb = b0 ? *b0 : 0.0, db = b0 ? d[0] : 0.0;
-        double s0 = 0.0, s1 = 0.0;
-        for (int k = t; k < m; k += LT) {
-          const int64_t j = J[k];
-          if (j < 0) continue;
-          s0 += d[k] * ((double)o[j] - bb);
-          s1 += d[k] * ((double)u[j] - db);
-        }
-        s0 = block_sum(s0, sh);
-        __syncthreads();
-        s1 = block_sum(s1, sh);
-        if (t == 0) {
-          a0 = lambda * s0;
-          a1 = lambda * s1;
-        }
+    // CTA v < LP + LC: the total of value v over the CTAs, in a fixed order
+    for (unsigned v = blockIdx.x; v < (unsigned)(LP + LC); v += nb) {
+      if (v < (unsigned)LP) {
+        double sv = 0.0;
+        for (unsigned b = t; b < nb; b += LT) sv += __ldcg(&PF[(size_t)v * nb + b]);
+        sv = block_sum(sv, sh);
+        if (t == 0) tot->F[v] = sv;
+      } else {
+        int sv = 0;
+        for (unsigned b = t; b < nb; b += LT) sv += __ldcg(&PC[(size_t)(v - LP) * nb + b]);
+        sv = block_sum(sv, reinterpret_cast<int*>(sh));
+        if (t == 0) tot->C[v - LP] = sv;
       }
       __syncthreads();
-      if (t == 0) {
-        auto dphi = [&](int k) {
-          const double tk = lo + (hi - lo) / (double)LC * (double)k;
-          return a0 + a1 * tk - Fs[k];
-        };
-        double tt = 0.0, nlo = lo, nhi = hi;
-        int done = 0;
-        bool next = false;
-        if (phase == 0) {
-          d0 = dphi(0);
-          if (!(d0 < 0.0)) {
-            tt = 0.0;
-            done = 1;
-          } else if (fabs(dphi(LC / 2)) <= 1e-6 * fabs(d0)) {
-            tt = 1.0;
-            done = 1;
-          } else {
-            phase = 1;
-          }
-        }
-        if (!done && phase == 1) {   // grow the bracket until phi' >= 0 at its right end
-          if (dphi(LC) < 0.0 && grow < 12) {
-            nlo = hi;
-            nhi = hi * 8.0;
-            ++grow;
-            next = true;
-          } else if (dphi(LC) < 0.0) {
-            tt = hi;   // phi still decreasing: take the far end (bounded)
-            done = 1;
-          } else {
-            phase = 2;
-          }
-        }
-        if (!done && !next) {   // the cell holding the root
-          int k = 0;
-          while (k < LC && dphi(k + 1) < 0.0) ++k;
-          if (k >= LC) k = LC - 1;
-          const double hstep = (hi - lo) / (double)LC;
-          const double tl = lo + hstep * k, tr = lo + hstep * (k + 1);
-          const double fl = dphi(k), fr = dphi(k + 1);
-          if (Cs[k] == 0 || depth >= 8 || !(fr > fl)) {
-            tt = (fr > fl) ? tl - fl * (tr - tl) / (fr - fl) : tl;
-            if (tt < tl) tt = tl;
-            if (tt > tr) tt = tr;
-            done = 1;
-          } else {
-            nlo = tl;
-            nhi = tr;
-            ++depth;
-          }
-        }
-        if (pass == kMaxPasses - 1 && !done) {
-          tt = lo;
+    }
+    if (grid_barrier(bar, nb)) {
+      if (t == 0) atomicExch(&st->err, 1);
+      return;
+    }
+    if (t < LP) Fs[t] = __ldcg(&tot->F[t]);
+    if (t < LC) Cs[t] = __ldcg(&tot->C[t]);
+    if (pass == 0 && t < 2) a_s[t] = __ldcg(&tot->a[t]);
+    __syncthreads();
+    if (t == 0) {
+      if (pass == 0) {
+        a0 = a_s[0];
+        a1 = a_s[1];
+      }
+      auto dphi = [&](int k) {
+        const double tk = lo + (hi - lo) / (double)LC * (double)k;
+        return a0 + a1 * tk - Fs[k];
+      };
+      double tt = 0.0, nlo = lo, nhi = hi;
+      int done = 0;
+      bool next = false;
+      if (phase == 0) {
+        d0 = dphi(0);
+        if (!(d0 < 0.0)) {
+          tt = 0.0;
           done = 1;
+        } else if (fabs(dphi(LC / 2)) <= 1e-6 * fabs(d0)) {
+          tt = 1.0;
+          done = 1;
+        } else {
+          phase = 1;
         }
+      }
+      if (!done && phase == 1) {   // grow the bracket until phi' >= 0 at its right end
+        if (dphi(LC) < 0.0 && grow < 12) {
+          nlo = hi;
+          nhi = hi * 8.0;
+          ++grow;
+          next = true;
+        } else if (dphi(LC) < 0.0) {
+          tt = hi;   // phi still decreasing: take the far end (bounded)
+          done = 1;
+        } else {
+          phase = 2;
+        }
+      }
+      if (!done && !next) {   // the cell holding the root
+        int k = 0;
+        while (k < LC && dphi(k + 1) < 0.0) ++k;
+        if (k >= LC) k = LC - 1;
+        const double hstep = (hi - lo) / (double)LC;
+        const double tl = lo + hstep * k, tr = lo + hstep * (k + 1);
+        const double fl = dphi(k), fr = dphi(k + 1);
+        if (Cs[k] == 0 || depth >= 8 || !(fr > fl)) {
+          tt = (fr > fl) ? tl - fl * (tr - tl) / (fr - fl) : tl;
+          if (tt < tl) tt = tl;
+          if (tt > tr) tt = tr;
+          done = 1;
+        } else {
+          nlo = tl;
+          nhi = tr;
+          ++depth;
+        }
+      }
+      if (pass == kMaxPasses - 1 && !done) {
+        tt = lo;
+        done = 1;
+      }
+      lo_s = nlo;
+      hi_s = nhi;
+      done_s = done;
+      if (blockIdx.x == 0) {
         st->lo = nlo;
         st->hi = nhi;
         st->t = tt;
         st->done = done;
       }
-    }
-    if (grid_barrier(bar, nb)) {
-      if (t == 0) atomicExch(&st->err, 1);
-      return;
-    }
-    if (t == 0) {
-      lo_s = __ldcg(&st->lo);
-      hi_s = __ldcg(&st->hi);
-      done_s = __ldcg(&st->done);
     }
     __syncthreads();
     if (done_s) break;
@@ -295,7 +324,7 @@ using namespace spsvm;
 
 extern "C" size_t spsvm_line_scratch_bytes(int64_t n) {
   (void)n;
-  return (size_t)(2 * sm_count()) * sizeof(LsPart) + 256;
+  return kLsPartOff + (size_t)(2 * sm_count()) * (LP * sizeof(double) + LC * sizeof(int32_t));
 }
 
 extern "C" int spsvm_line_search(const float* o, const float* u, const float* y, int64_t n,
@@ -320,10 +349,10 @@ int spsvm::line_search_impl(const float* o, const float* u, const float* y, int6
   if (grid < 1) return set_error(SPSVM_ERR_CUDA, "line_search: occupancy query failed");
   LsState* st = static_cast<LsState*>(scratch);
   unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);
-  LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
-  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  char* work = static_cast<char*>(scratch);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, kLsHead, s));
   void* args[] = {(void*)&o, (void*)&u, (void*)&y, (void*)&n, (void*)&d, (void*)&J,
-                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar, (void*)&b0};
+                  (void*)&m, (void*)&lambda, (void*)&work, (void*)&st, (void*)&bar, (void*)&b0};
   SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ls_search, dim3(grid), dim3(LT), args, 0, s));
   SPSVM_LAUNCH_CHECK();
   LsState h{};
@@ -349,10 +378,10 @@ int spsvm::line_search_async(const float* o, const float* u, const float* y, int
   if (grid < 1) return set_error(SPSVM_ERR_CUDA, "line_search: occupancy query failed");
   LsState* st = static_cast<LsState*>(scratch);
   unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);
-  LsPart* part = reinterpret_cast<LsPart*>(static_cast<char*>(scratch) + 256);
-  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  char* work = static_cast<char*>(scratch);
+  SPSVM_CUDA_TRY(cudaMemsetAsync(scratch, 0, kLsHead, s));
   void* args[] = {(void*)&o, (void*)&u, (void*)&y, (void*)&n, (void*)&d, (void*)&J,
-                  (void*)&m, (void*)&lambda, (void*)&part, (void*)&st, (void*)&bar, (void*)&b0};
+                  (void*)&m, (void*)&lambda, (void*)&work, (void*)&st, (void*)&bar, (void*)&b0};
   SPSVM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ls_search, dim3(grid), dim3(LT), args, 0, s));
   SPSVM_LAUNCH_CHECK();
   ls_export<<<1, 1, 0, s>>>(st, t_dev, err_dev);

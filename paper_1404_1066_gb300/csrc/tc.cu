@@ -109,22 +109,6 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t nCB, int64_t nPT,
 // each warp's 32 basis rows, also without storing the kernel values.
 enum KbMode { KB_STORE_F32 = 0, KB_SCORE = 2, KB_DECIDE = 3 };
 
-// Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j): after
-// five exchange steps, each halving the columns a lane holds and summing
-// the pair, lane l holds the sum of column l (31 shuffles in all).
-__device__ __forceinline__ float warp_column_sums(float (&v)[32], int lane) {
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool upper = (lane & h) != 0;
-#pragma unroll
-    for (int k = 0; k < h; ++k) {
-      const float give = upper ? v[k] : v[k + h];
-      const float keep = upper ? v[k + h] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, give, h);
-    }
-  }
-  return v[0];
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1) kblock_tc_kernel(
