@@ -779,10 +779,6 @@ constexpr int DP = DT + 4;      // staging rows, 16-byte aligned
 constexpr int DAG_T = 256;
 constexpr size_t DAG_SMEM = (size_t)4 * DT * DP * sizeof(float);   // two stages of (A, B)
 
-__host__ __device__ __forceinline__ int64_t dag_col_start(int64_t T, int64_t j) {
-  return j * T - j * (j - 1) / 2;   // tiles in columns 0 .. j-1
-}
-
 // Rows r0 .. r0+63 (zeros past m), columns c0 .. c0+63 of L as 16-byte
 // vectors; a warp covers 8 rows x 64 contiguous bytes per vector.
 __device__ __forceinline__ void dag_load(float4 (&v)[4], const float* __restrict__ L, int64_t ldl,
@@ -870,6 +866,326 @@ __device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __r
   return -1;
 }
 
+// Tiles (i, j) of the factor, i >= j, left-looking: C_ij - sum_{k<j} L_ik
+// L_jk^T, then the factor of a diagonal tile or the solve X L_jj^T = C of an
+// off-diagonal one.  The chain of the factorisation runs through the
+// diagonal tiles and the tiles just below them.  So one CTA, the unit U(s),
+// takes the last steps of both: a helper P(s) accumulates the tile
+// (s, s-1) over k < s-1 and leaves it in place (flag 3, partial); U(s)
+// accumulates (s, s) over k < s-1, then solves (s, s-1) against (s-1, s-1)
+// once that is factored, applies the result to (s, s) from its own
+// registers and factors (s, s) -- one hand-off between CTAs per 64-column
+// step, with the accumulation work spread as before.  Tickets go (0, 0),
+// then for s = 1, 2, ...: P(s), U(s), the other tiles of column s-1 (rows
+// s+1 ..); every tile waits only for tiles of smaller tickets.
+
+// Ticket tk -> work: kind 0 the tile (0, 0), kind 1 the unit U(s) (i = s,
+// j = s - 1), kind 2 the tile (i, j), kind 3 the helper P(s) (i = s,
+// j = s - 1); -1 past the end.
+__device__ __forceinline__ int dag_decode(int64_t tk, int64_t T, int64_t* i, int64_t* j) {
+  if (tk <= 0) {
+    *i = 0;
+    *j = 0;
+    return tk == 0 ? 0 : -1;
+  }
+  // block s (s >= 1) = P(s), U(s), then rows s+1 .. T-1 of column s-1:
+  // T - s + 1 tickets
+  int64_t s = 1, start = 1;
+  while (s < T && start + (T - s + 1) <= tk) {
+    start += T - s + 1;
+    ++s;
+  }
+  if (s >= T) return -1;
+  const int64_t e = tk - start;
+  *j = s - 1;
+  if (e <= 1) {
+    *i = s;
+    return e == 0 ? 3 : 1;
+  }
+  *i = s + e - 1;
+  return 2;
+}
+
+// Waits (bounded) for the helper's partial of a unit's off-diagonal tile:
+// true on flag 3, false when it was abandoned or the wait gave up.
+__device__ bool dag_wait_partial(const unsigned* f, const WaitCtx& w) {
+  const uint32_t lim = wait_limit(w, 1u << 23);
+  for (uint32_t it = 0; it < lim; ++it) {
+    const unsigned v = ld_acquire_u32(f);
+    if (v == 3u) return true;
+    if (v != 0u) return false;
+    if (it >= 16) __nanosleep(64);
+  }
+  wait_gave_up(w, 225);
+  return false;
+}
+
+// acc1 -= sum_{k<kend} L_ik L_jk^T (L_ik L_ik^T when same) as the tiles of
+// columns k come in, and with TWO also acc2 -= sum_{k<kend} L_ik L_ik^T.
+// All threads; false when a dependency was abandoned or a wait gave up.
+template <bool TWO>
+__device__ bool dag_accumulate(float (&acc1)[4][4], float (&acc2)[4][4],
+                               const float* __restrict__ L, int64_t ldl, int64_t m, int64_t i,
+                               int64_t j, int64_t kend, bool same,
+                               const unsigned* __restrict__ flags, int64_t T,
+                               float (*As)[DT][DP], float (*Bs)[DT][DP], int64_t* rdy_s,
+                               const WaitCtx& wc) {
+  const int t = threadIdx.x;
+  bool ok = true;
+  if (kend > 0) {
+    // rdy: the first k whose tiles are not known to be done
+    const unsigned* fi = flags + i * T;
+    const unsigned* fj = flags + j * T;
+    if (t < 32) {
+      const int64_t r = dag_scan(fi, fj, 0, kend, 223, wc);
+      if (t == 0) *rdy_s = r;
+    }
+    __syncthreads();
+    int64_t rdy = *rdy_s;
+    ok = rdy > 0;
+    float4 pa[4], pb[4];
+    if (ok) {
+      dag_load(pa, L, ldl, m, i * DT, 0);
+      if (!same) dag_load(pb, L, ldl, m, j * DT, 0);
+    }
+    for (int64_t k = 0; ok && k < kend; ++k) {
+      const int sb = (int)(k & 1);
+      dag_stage(As[sb], pa);
+      if (!same) dag_stage(Bs[sb], pb);
+      __syncthreads();
+      const bool pre = k + 1 < rdy;
+      if (pre) {   // next tiles known done: their loads overlap this update
+        dag_load(pa, L, ldl, m, i * DT, (k + 1) * DT);
+        if (!same) dag_load(pb, L, ldl, m, j * DT, (k + 1) * DT);
+      }
+      dag_update(acc1, As[sb], same ? As[sb] : Bs[sb]);
+      if (TWO) dag_update(acc2, As[sb], As[sb]);
+      if (k + 1 < kend && !pre) {
+        if (t < 32) {
+          const int64_t r = dag_scan(fi, fj, k + 1, kend, 223, wc);
+          if (t == 0) *rdy_s = r;
+        }
+        __syncthreads();
+        rdy = *rdy_s;
+        if (rdy < 0) {
+          ok = false;
+        } else {
+          dag_load(pa, L, ldl, m, i * DT, (k + 1) * DT);
+          if (!same) dag_load(pb, L, ldl, m, j * DT, (k + 1) * DT);
+        }
+      }
+    }
+  }
+  __syncthreads();   // staging buffers free
+  return ok;
+}
+
+// Factor of a diagonal tile held in registers (thread (ty, tx): rows 4 ty ..
+// +3, columns 4 tx .. +3), right-looking over 16 pivot blocks of 4 columns:
+// a pivot costs a few dependent instructions in one thread and a barrier,
+// not a chain of shuffles.  All threads; returns 0, or 1 + the tile column
+// of the first non-positive pivot.  P: 2 x DT float4 of shared memory.
+__device__ int dag_factor_diag(float (&acc)[4][4], float4* __restrict__ Xb, float* __restrict__ rd,
+                               int* fail_s) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  if (t == 0) *fail_s = 0;
+  for (int p = 0; p < DT / 4; ++p) {
+    float4* P = Xb + (p & 1) * DT;
+    if (ty == p && tx == p) {   // the 4 x 4 diagonal block
+      int f = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float d = acc[c][c];
+        if (f == 0 && (!(d > 0.0f) || !(d < 3.0e38f))) f = c + 1;
+        if (f == 0) {
+          const float y = rsqrt_t(d);
+          acc[c][c] = d * y;
+          rd[4 * p + c] = y;
+#pragma unroll
+          for (int r = c + 1; r < 4; ++r) acc[r][c] *= y;
+#pragma unroll
+          for (int c2 = c + 1; c2 < 4; ++c2)
+#pragma unroll
+            for (int r = c2; r < 4; ++r) acc[r][c2] = fmaf(-acc[r][c], acc[c2][c], acc[r][c2]);
+        }
+      }
+      if (f) *fail_s = 4 * p + f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) P[4 * p + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    }
+    __syncthreads();
+    if (*fail_s) break;
+    if (tx == p && ty > p) {   // panel block: X L_pp^T = C
+      float lp[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4 v = P[4 * p + a];
+        lp[a][0] = v.x; lp[a][1] = v.y; lp[a][2] = v.z; lp[a][3] = v.w;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float v = acc[a][c];
+#pragma unroll
+          for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lp[c][l], v);
+          acc[a][c] = v * rd[4 * p + c];
+        }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) P[4 * ty + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    }
+    __syncthreads();
+    if (tx > p && ty >= tx) {   // trailing: C -= L_(ty,p) L_(tx,p)^T
+      float4 pa4[4], pb4[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        pa4[a] = P[4 * ty + a];
+        pb4[a] = P[4 * tx + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          acc[a][b] -= pa4[a].x * pb4[b].x + pa4[a].y * pb4[b].y + pa4[a].z * pb4[b].z +
+                       pa4[a].w * pb4[b].w;
+    }
+  }
+  __syncthreads();
+  return *fail_s;
+}
+
+// Lower part of a factored diagonal tile to L (rows below m only).
+__device__ __forceinline__ void dag_store_diag(const float (&acc)[4][4], float* __restrict__ L,
+                                               int64_t ldl, int64_t m, int64_t r0, int64_t c0) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  if (ty < tx) return;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t gr = r0 + 4 * ty + a;
+    if (gr >= m) continue;
+    float* dst = L + gr * ldl + c0 + 4 * tx;
+    if (ty > tx) {
+      __stcg(reinterpret_cast<float4*>(dst), make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
+    } else {
+#pragma unroll
+      for (int b = 0; b <= a; ++b) __stcg(dst + b, acc[a][b]);
+    }
+  }
+}
+
+// X L_jj^T = C for an off-diagonal tile in registers, by pivot blocks of 4
+// columns, with S[c][r] = L_jj[r][c] staged in shared memory and rd the
+// reciprocals of its diagonal.  The rows of a half warp (one row group)
+// depend on nothing else: its owner lane (tx = p) solves its 4 x 4 block
+// against the diagonal block L_pp, hands the block to the half warp by
+// shuffle, and the lanes right of it apply it -- no barrier in the loop.
+__device__ __forceinline__ void dag_solve_sub(float (&acc)[4][4], const float (*S)[DP],
+                                              const float* __restrict__ rd) {
+  const int t = threadIdx.x, tx = t & 15, lane = t & 31;
+#pragma unroll 2
+  for (int p = 0; p < DT / 4; ++p) {
+    float lpp[4][4], rdp[4];
+    float4 lv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      rdp[c] = rd[4 * p + c];
+#pragma unroll
+      for (int l = 0; l < c; ++l) lpp[c][l] = S[4 * p + l][4 * p + c];
+      lv[c] = *reinterpret_cast<const float4*>(&S[4 * p + c][4 * tx]);   // L_jj[4tx+b][4p+c]
+    }
+    if (tx == p) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float v = acc[a][c];
+#pragma unroll
+          for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lpp[c][l], v);
+          acc[a][c] = v * rdp[c];
+        }
+    }
+    float x[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) x[a][l] = __shfl_sync(0xffffffffu, acc[a][l], (lane & 16) | p);
+    if (tx > p) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a][0] -= x[a][0] * lv[0].x + x[a][1] * lv[1].x + x[a][2] * lv[2].x + x[a][3] * lv[3].x;
+        acc[a][1] -= x[a][0] * lv[0].y + x[a][1] * lv[1].y + x[a][2] * lv[2].y + x[a][3] * lv[3].y;
+        acc[a][2] -= x[a][0] * lv[0].z + x[a][1] * lv[1].z + x[a][2] * lv[2].z + x[a][3] * lv[3].z;
+        acc[a][3] -= x[a][0] * lv[0].w + x[a][1] * lv[1].w + x[a][2] * lv[2].w + x[a][3] * lv[3].w;
+      }
+    }
+  }
+}
+
+// Waits for the factored diagonal tile (j, j), stages it transposed into S
+// with the reciprocals of its diagonal in rd, and solves the off-diagonal
+// tile in acc against it.  All threads; false when the tile was abandoned or
+// the wait gave up.
+__device__ bool dag_sub_from_diag(float (&acc)[4][4], const float* __restrict__ L, int64_t ldl,
+                                  int64_t m, int64_t j, const unsigned* __restrict__ flags,
+                                  int64_t T, float (*S)[DP], float* __restrict__ rd,
+                                  unsigned* st_s, const WaitCtx& wc) {
+  const int t = threadIdx.x;
+  if (t == 0) *st_s = wait_flag(&flags[j * T + j], 224, wc);
+  __syncthreads();
+  if (*st_s != 1u) return false;
+  float4 pd[4];
+  dag_load(pd, L, ldl, m, j * DT, j * DT);   // j < T - 1: a full tile
+  dag_stage(S, pd);                          // S[c][r] = L_jj[r][c]
+  __syncthreads();
+  if (t < DT) rd[t] = 1.0f / S[t][t];
+  __syncthreads();
+  dag_solve_sub(acc, S, rd);
+  return true;
+}
+
+__device__ __forceinline__ void dag_store_full(const float (&acc)[4][4], float* __restrict__ L,
+                                               int64_t ldl, int64_t m, int64_t r0, int64_t c0) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t gr = r0 + 4 * ty + a;
+    if (gr < m)
+      __stcg(reinterpret_cast<float4*>(L + gr * ldl + c0 + 4 * tx),
+             make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
+  }
+}
+
+// The tile (i, j) of H + shift I already converted into L: full, or the
+// lower part of a diagonal tile with the identity past m.
+__device__ __forceinline__ void dag_load_tile(float (&acc)[4][4], const float* __restrict__ L,
+                                              int64_t ldl, int64_t m, int64_t r0, int64_t c0,
+                                              bool diag) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = 4 * ty + a;
+    const int64_t gr = r0 + r;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = 4 * tx + b;
+      const int64_t gc = c0 + c;
+      float v = 0.0f;
+      if (gr < m && gc < m && (!diag || c <= r)) v = __ldcg(L + gr * ldl + gc);
+      if (diag && r == c && gr >= m) v = 1.0f;   // identity past m in the last diagonal tile
+      acc[a][b] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ void dag_publish(unsigned* flags, int64_t idx, bool ok,
+                                            unsigned done = 1u) {
+  __syncthreads();   // the tile's stores, then one release (cumulative over the CTA)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u32(&flags[idx], ok ? done : 2u);
+  }
+}
+
 __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
                                                       int64_t T, unsigned* __restrict__ flags,
                                                       unsigned* __restrict__ ticket,
@@ -877,245 +1193,94 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   extern __shared__ __align__(16) float dag_smem[];
   float (*As)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem);
   float (*Bs)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem + 2 * DT * DP);
+  float4* Xb = reinterpret_cast<float4*>(dag_smem + 2 * DT * DP);   // [2][DT] rows, in Bs
   __shared__ int64_t tile_s[2], rdy_s;
+  __shared__ int kind_s;
   __shared__ unsigned st_s;
   __shared__ float rd[DT];
   __shared__ int fail_s;
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4, lane = t & 31;
-  const int64_t ntiles = T * (T + 1) / 2;
+  const int t = threadIdx.x;
   for (;;) {
     if (t == 0) {
       const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
-      int64_t i = 0, j = -1;
-      if (tk < ntiles) {
-        const float b = 2.0f * (float)T + 1.0f;
-        j = (int64_t)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)tk, 0.0f))));
-        j = j < 0 ? 0 : (j > T - 1 ? T - 1 : j);
-        while (j + 1 < T && dag_col_start(T, j + 1) <= tk) ++j;
-        while (j > 0 && dag_col_start(T, j) > tk) --j;
-        i = j + (tk - dag_col_start(T, j));
-      }
+      int64_t i = 0, j = 0;
+      kind_s = dag_decode(tk, T, &i, &j);
       tile_s[0] = i;
       tile_s[1] = j;
     }
     __syncthreads();
+    const int kind = kind_s;
     const int64_t i = tile_s[0], j = tile_s[1];
-    if (j < 0) return;
-    const bool diag = i == j;
-    const int64_t r0 = i * DT, c0 = j * DT;
+    if (kind < 0) return;
     float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int r = 4 * ty + a;
-      const int64_t gr = r0 + r;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = 4 * tx + b;
-        const int64_t gc = c0 + c;
-        float v = 0.0f;
-        if (gr < m && gc < m && (!diag || c <= r)) v = __ldcg(L + gr * ldl + gc);
-        if (diag && r == c && gr >= m) v = 1.0f;   // identity past m in the last diagonal tile
-        acc[a][b] = v;
-      }
+    if (kind == 3) {
+      // the helper P(s): tile (s, s-1) accumulated over k < s-1, left in place
+      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, false);
+      const bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, false, flags, T, As, Bs,
+                                            &rdy_s, wc);
+      if (ok) dag_store_full(acc, L, ldl, m, i * DT, j * DT);
+      dag_publish(flags, i * T + j, ok, 3u);
+      continue;
     }
-    bool ok = true;
-    if (j > 0) {
-      // rdy: the first k whose tiles are not known to be done
-      const unsigned* fi = flags + i * T;
-      const unsigned* fj = flags + j * T;
-      if (t < 32) {
-        const int64_t r = dag_scan(fi, fj, 0, j, 223, wc);
-        if (t == 0) rdy_s = r;
-      }
-      __syncthreads();
-      int64_t rdy = rdy_s;
-      ok = rdy > 0;
-      float4 pa[4], pb[4];
-      if (ok) {
-        dag_load(pa, L, ldl, m, r0, 0);
-        if (!diag) dag_load(pb, L, ldl, m, c0, 0);
-      }
-      for (int64_t k = 0; ok && k < j; ++k) {
-        const int sb = (int)(k & 1);
-        dag_stage(As[sb], pa);
-        if (!diag) dag_stage(Bs[sb], pb);
-        __syncthreads();
-        const bool pre = k + 1 < rdy;
-        if (pre) {   // next tiles known done: their loads overlap this update
-          dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
-          if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
+    if (kind != 1) {
+      // one tile: (0, 0), or an off-diagonal tile below the unit of its column
+      const bool diag = kind == 0;
+      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, diag);
+      bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, diag, flags, T, As, Bs, &rdy_s, wc);
+      if (ok && diag) {
+        const int f = dag_factor_diag(acc, Xb, rd, &fail_s);
+        if (f) {
+          if (t == 0) atomicCAS(info, 0, (int32_t)(j * DT + f));
+          ok = false;
+        } else {
+          dag_store_diag(acc, L, ldl, m, i * DT, j * DT);
         }
-        dag_update(acc, As[sb], diag ? As[sb] : Bs[sb]);
-        if (k + 1 < j && !pre) {
-          if (t < 32) {
-            const int64_t r = dag_scan(fi, fj, k + 1, j, 223, wc);
-            if (t == 0) rdy_s = r;
-          }
-          __syncthreads();
-          rdy = rdy_s;
-          if (rdy < 0) {
-            ok = false;
-          } else {
-            dag_load(pa, L, ldl, m, r0, (k + 1) * DT);
-            if (!diag) dag_load(pb, L, ldl, m, c0, (k + 1) * DT);
-          }
-        }
+      } else if (ok) {
+        ok = dag_sub_from_diag(acc, L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
+        if (ok) dag_store_full(acc, L, ldl, m, i * DT, j * DT);
       }
+      dag_publish(flags, i * T + j, ok);
+      continue;
     }
-    __syncthreads();   // staging buffers free
-    // The tile stays in registers (thread (ty, tx): rows 4 ty .. +3, columns
-    // 4 tx .. +3); both epilogues go right-looking over 16 pivot blocks of 4
-    // columns, so a pivot costs a few dependent instructions in one thread
-    // and a barrier, not a chain of shuffles.
-    float4* Xb = reinterpret_cast<float4*>(dag_smem + 2 * DT * DP);   // [2][DT] rows, in Bs
-    if (ok && diag) {
-      if (t == 0) fail_s = 0;
-      for (int p = 0; p < DT / 4; ++p) {
-        float4* P = Xb + (p & 1) * DT;
-        if (ty == p && tx == p) {   // the 4 x 4 diagonal block
-          int f = 0;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float d = acc[c][c];
-            if (f == 0 && (!(d > 0.0f) || !(d < 3.0e38f))) f = c + 1;
-            if (f == 0) {
-              const float y = rsqrt_t(d);
-              acc[c][c] = d * y;
-              rd[4 * p + c] = y;
-#pragma unroll
-              for (int r = c + 1; r < 4; ++r) acc[r][c] *= y;
-#pragma unroll
-              for (int c2 = c + 1; c2 < 4; ++c2)
-#pragma unroll
-                for (int r = c2; r < 4; ++r) acc[r][c2] = fmaf(-acc[r][c], acc[c2][c], acc[r][c2]);
-            }
-          }
-          if (f) fail_s = 4 * p + f;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) P[4 * p + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-        }
-        __syncthreads();
-        if (fail_s) break;
-        if (tx == p && ty > p) {   // panel block: X L_pp^T = C
-          float lp[4][4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const float4 v = P[4 * p + a];
-            lp[a][0] = v.x; lp[a][1] = v.y; lp[a][2] = v.z; lp[a][3] = v.w;
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              float v = acc[a][c];
-#pragma unroll
-              for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lp[c][l], v);
-              acc[a][c] = v * rd[4 * p + c];
-            }
-#pragma unroll
-          for (int a = 0; a < 4; ++a) P[4 * ty + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-        }
-        __syncthreads();
-        if (tx > p && ty >= tx) {   // trailing: C -= L_(ty,p) L_(tx,p)^T
-          float4 pa4[4], pb4[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            pa4[a] = P[4 * ty + a];
-            pb4[a] = P[4 * tx + a];
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-              acc[a][b] -= pa4[a].x * pb4[b].x + pa4[a].y * pb4[b].y + pa4[a].z * pb4[b].z +
-                           pa4[a].w * pb4[b].w;
-        }
-      }
-      if (fail_s != 0) {
-        if (t == 0) atomicCAS(info, 0, (int32_t)(c0 + fail_s));
-        ok = false;
-      } else if (ty >= tx) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int64_t gr = r0 + 4 * ty + a;
-          if (gr >= m) continue;
-          float* dst = L + gr * ldl + c0 + 4 * tx;
-          if (ty > tx) {
-            __stcg(reinterpret_cast<float4*>(dst), make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
-          } else {
-#pragma unroll
-            for (int b = 0; b <= a; ++b) __stcg(dst + b, acc[a][b]);
-          }
-        }
-      }
-    } else if (ok) {
-      if (t == 0) st_s = wait_flag(&flags[j * T + j], 224, wc);
+    // the unit U(s), s = i: (s, s) over k < s-1, then the tile (s, s-1)
+    // below the diagonal from its helper's partial, then (s, s)
+    const int64_t s = i;
+    float accd[4][4];
+    dag_load_tile(accd, L, ldl, m, s * DT, s * DT, true);
+    bool ok = dag_accumulate<false>(accd, accd, L, ldl, m, s, s, j, true, flags, T, As, Bs, &rdy_s,
+                                    wc);
+    if (ok) {
+      if (t == 0) st_s = dag_wait_partial(&flags[s * T + j], wc) ? 1u : 2u;
       __syncthreads();
-      if (st_s != 1u) {
+      ok = st_s == 1u;
+    }
+    if (ok) {
+      dag_load_tile(acc, L, ldl, m, s * DT, j * DT, false);   // the partial, acquired above
+      ok = dag_sub_from_diag(acc, L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
+    }
+    if (ok) dag_store_full(acc, L, ldl, m, s * DT, j * DT);
+    dag_publish(flags, s * T + j, ok);
+    if (ok) {
+      // (s, s) -= L_s,s-1 L_s,s-1^T from this CTA's registers: S[l][r] =
+      // L_s,s-1[r][l] (As[1] is free: the solve read As[0])
+      const int tx = t & 15, ty = t >> 4;
+      float (*S)[DP] = As[1];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) S[4 * tx + b][4 * ty + a] = acc[a][b];
+      __syncthreads();
+      dag_update(accd, S, S);
+      __syncthreads();
+      const int f = dag_factor_diag(accd, Xb, rd, &fail_s);
+      if (f) {
+        if (t == 0) atomicCAS(info, 0, (int32_t)(s * DT + f));
         ok = false;
       } else {
-        float4 pd[4];
-        dag_load(pd, L, ldl, m, c0, c0);   // j < T - 1: a full tile
-        dag_stage(As[0], pd);              // As[0][c][r] = L_jj[r][c]
-        __syncthreads();
-        if (t < DT) rd[t] = 1.0f / As[0][t][t];
-        __syncthreads();
-        // X L_jj^T = C by pivot blocks of 4 columns.  The rows of a half
-        // warp (one row group) depend on nothing else: its owner lane
-        // (tx = p) solves its 4 x 4 block against the diagonal block L_pp,
-        // hands the block to the half warp by shuffle, and the lanes right
-        // of it apply it -- no barrier in the loop.
-#pragma unroll 2
-        for (int p = 0; p < DT / 4; ++p) {
-          float lpp[4][4], rdp[4];
-          float4 lv[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            rdp[c] = rd[4 * p + c];
-#pragma unroll
-            for (int l = 0; l < c; ++l) lpp[c][l] = As[0][4 * p + l][4 * p + c];
-            lv[c] = *reinterpret_cast<const float4*>(&As[0][4 * p + c][4 * tx]);   // L_jj[4tx+b][4p+c]
-          }
-          if (tx == p) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int a = 0; a < 4; ++a) {
-                float v = acc[a][c];
-#pragma unroll
-                for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lpp[c][l], v);
-                acc[a][c] = v * rdp[c];
-              }
-          }
-          float x[4][4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int l = 0; l < 4; ++l) x[a][l] = __shfl_sync(0xffffffffu, acc[a][l], (lane & 16) | p);
-          if (tx > p) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              acc[a][0] -= x[a][0] * lv[0].x + x[a][1] * lv[1].x + x[a][2] * lv[2].x + x[a][3] * lv[3].x;
-              acc[a][1] -= x[a][0] * lv[0].y + x[a][1] * lv[1].y + x[a][2] * lv[2].y + x[a][3] * lv[3].y;
-              acc[a][2] -= x[a][0] * lv[0].z + x[a][1] * lv[1].z + x[a][2] * lv[2].z + x[a][3] * lv[3].z;
-              acc[a][3] -= x[a][0] * lv[0].w + x[a][1] * lv[1].w + x[a][2] * lv[2].w + x[a][3] * lv[3].w;
-            }
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int64_t gr = r0 + 4 * ty + a;
-          if (gr < m)
-            __stcg(reinterpret_cast<float4*>(L + gr * ldl + c0 + 4 * tx),
-                   make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]));
-        }
+        dag_store_diag(accd, L, ldl, m, s * DT, s * DT);
       }
     }
-    __syncthreads();   // the tile's stores, then one release (cumulative over the CTA)
-    if (t == 0) {
-      __threadfence();
-      st_release_u32(&flags[i * T + j], ok ? 1u : 2u);
-    }
+    dag_publish(flags, s * T + s, ok);
   }
 }
 
@@ -1806,6 +1971,7 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   char* w = static_cast<char*>(work);
   float* L = reinterpret_cast<float*>(w + ly.L);
   unsigned* dflags = reinterpret_cast<unsigned*>(w + ly.dag);
+  // tickets: one per tile (the helper P(s) stands for the tile (s, s-1))
   const int64_t T = ly.tiles, ntiles = T * (T + 1) / 2;
   SPSVM_CUDA_TRY(cudaMemsetAsync(dflags, 0, (size_t)(T * T + 1) * 4, s));
   to_f32_shift<<<(unsigned)m, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
