@@ -623,7 +623,8 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_fwd(const float* __restrict
 __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict__ L, int64_t ldh,
                                                         int64_t m, const float* __restrict__ z,
                                                         unsigned long long* __restrict__ xt,
-                                                        float* __restrict__ x,
+                                                        double* __restrict__ xacc,
+                                                        double* __restrict__ xmax,
                                                         unsigned* __restrict__ ticket, unsigned tag,
                                                         WaitCtx wc, const int* stop) {
   if (refine_stopped(stop)) return;
@@ -631,6 +632,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
   __shared__ float xs[SV_BATCH][NB];
   __shared__ float part[4][NB];
   __shared__ float v[NB];
+  __shared__ double xm[2];
   __shared__ unsigned k_s;
   __shared__ int n_s;
   const int t = threadIdx.x;
@@ -699,12 +701,24 @@ __global__ void __launch_bounds__(SV_THREADS) trsv32_bwd(const float* __restrict
   for (int i = 0; i < 16; ++i) sres = fmaf(Li[16 * g + i][c], v[16 * g + i], sres);
   part[g][c] = sres;
   __syncthreads();
+  // publish the block (the chain), then x += the correction in FP64 and
+  // the block's maximum of |x|
+  double am = 0.0;
   if (t < nb) {
     const float xv = part[0][t] + part[1][t] + part[2][t] + part[3][t];
-    x[r0 + t] = xv;
     st_relaxed_u64(xt + r0 + t, ((unsigned long long)(ok ? tag : (tag | 0x80000000u)) << 32) |
                                     __float_as_uint(xv));
+    const double xn = xacc[r0 + t] + (double)xv;
+    xacc[r0 + t] = xn;
+    am = fabs(xn);
   }
+  if (t < NB) {   // warps 0 and 1
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if ((t & 31) == 0) xm[t >> 5] = am;
+  }
+  __syncthreads();
+  if (t == 0) xmax[k] = fmax(xm[0], xm[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1284,46 +1298,17 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   }
 }
 
-// z = (float) r.
-__global__ void __launch_bounds__(MX_T) to_f32_vec(const double* __restrict__ r, int64_t m,
-                                                   float* __restrict__ z, const int* stop) {
-  if (refine_stopped(stop)) return;
-  const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
-  if (i < m) z[i] = f64_to_f32_rn(r[i]);
-}
-
-// x += (double) z; block maxima of |x|.
-__global__ void __launch_bounds__(MX_T) add_f32(double* __restrict__ x, const float* __restrict__ z,
-                                                int64_t m, double* __restrict__ xmax, const int* stop) {
-  if (refine_stopped(stop)) return;
-  __shared__ double wm[MX_T / 32];
-  const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
-  double a = 0.0;
-  if (i < m) {
-    const double v = x[i] + (double)z[i];
-    x[i] = v;
-    a = fabs(v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int k = 0; k < MX_T / 32; ++k) mx = fmax(mx, wm[k]);
-    xmax[blockIdx.x] = mx;
-  }
-}
-
 // r = b - (H + shift I) x (H full and symmetric, FP64), one warp per row,
 // 16-byte loads four deep per lane when H's rows and x are 16-byte aligned;
-// block maxima of |r|.
+// z = (float) r, the next refinement step's right-hand side; block maxima
+// of |r|.
 template <bool VEC>
 __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ H, int64_t ldh,
                                                      int64_t m, double shift,
                                                      const double* __restrict__ b,
                                                      const double* __restrict__ x,
                                                      double* __restrict__ r,
+                                                     float* __restrict__ z,
                                                      double* __restrict__ rmax, const int* stop) {
   if (refine_stopped(stop)) return;
   __shared__ double wm[MX_T / 32];
@@ -1362,6 +1347,7 @@ __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ 
     if (lane == 0) {
       const double ri = b[i] - s - shift * x[i];
       r[i] = ri;
+      z[i] = f64_to_f32_rn(ri);
       a = fabs(ri);
     }
   }
@@ -1374,36 +1360,16 @@ __global__ void __launch_bounds__(MX_T) residual_f64(const double* __restrict__ 
   }
 }
 
-// out[k] = max of blocks of the partial maxima (three arrays, one block).
-__global__ void __launch_bounds__(MX_T) max3(const double* __restrict__ a, int64_t na,
-                                             const double* __restrict__ b, int64_t nb,
-                                             const double* __restrict__ c, int64_t nc,
-                                             double* __restrict__ out, const int* stop) {
-  if (refine_stopped(stop)) return;
-  __shared__ double sm[3][MX_T];
-  const double* src[3] = {a, b, c};
-  const int64_t n[3] = {na, nb, nc};
-  for (int k = 0; k < 3; ++k) {
-    double mx = 0.0;
-    if (src[k])
-      for (int64_t e = threadIdx.x; e < n[k]; e += MX_T) mx = fmax(mx, src[k][e]);
-    sm[k][threadIdx.x] = mx;
-  }
-  __syncthreads();
-  for (int o = MX_T / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] = fmax(sm[k][threadIdx.x], sm[k][threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x < 3) out[threadIdx.x] = sm[threadIdx.x][0];
-}
-
-// Block maxima of |v|.
+// Block maxima of |v|, and z = (float) v.
 __global__ void __launch_bounds__(MX_T) absmax_blocks(const double* __restrict__ v, int64_t m,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, float* __restrict__ z) {
   __shared__ double wm[MX_T / 32];
   const int64_t i = (int64_t)blockIdx.x * MX_T + threadIdx.x;
-  double a = i < m ? fabs(v[i]) : 0.0;
+  double a = 0.0;
+  if (i < m) {
+    a = fabs(v[i]);
+    z[i] = f64_to_f32_rn(v[i]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = a;
@@ -1715,19 +1681,52 @@ struct RefineState {
   double be, rprev;
 };
 
-// After refinement step `it`: the normwise backward error
-// ||r|| / (||H + shift I|| ||x|| + ||b||) from the norms, and the stop word.
-// Stagnation (the residual norm not halved) counts from the third step, the
-// first two being the FP32 solve and its first correction.
-__global__ void refine_decide(const double* __restrict__ norms, const int32_t* __restrict__ finfo,
-                              int it, double tol, void* state) {
+// Maximum of v[0..n) over the block (result in thread 0).
+__device__ double block_max(const double* __restrict__ v, int64_t n, double* sh) {
+  double a = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) a = fmax(a, v[e]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, sh[k]);
+  return r;
+}
+
+// After refinement step `it` (one block of MX_T threads): the norms from the
+// block maxima (at the first step also ||H + shift I|| and ||b||), the
+// normwise backward error ||r|| / (||H + shift I|| ||x|| + ||b||), and the
+// stop word.  Stagnation (the residual norm not halved) counts from the
+// third step, the first two being the FP32 solve and its first correction.
+__global__ void __launch_bounds__(MX_T) refine_decide(
+    const double* __restrict__ xmax, int64_t nx, const double* __restrict__ rmax, int64_t nr,
+    const double* __restrict__ rowmax, int64_t nh, const double* __restrict__ bmax, int64_t nbm,
+    double* __restrict__ norms, const int32_t* __restrict__ finfo, int it, double tol, void* state) {
+  __shared__ double sh[MX_T / 32];
+  __shared__ int stop_s;
   RefineState* st = static_cast<RefineState*>(state);
-  if (threadIdx.x != 0 || st->stop) return;
+  if (threadIdx.x == 0) stop_s = *reinterpret_cast<const volatile int32_t*>(&st->stop);
+  __syncthreads();
+  if (stop_s) return;
+  if (it == 0) {
+    const double h = block_max(rowmax, nh, sh);
+    const double bb = block_max(bmax, nbm, sh);
+    if (threadIdx.x == 0) {
+      norms[0] = h;
+      norms[1] = bb;
+    }
+  }
+  const double xn = block_max(xmax, nx, sh);
+  const double rn = block_max(rmax, nr, sh);
+  if (threadIdx.x != 0) return;
   if (finfo && *finfo != 0) {
     st->stop = 4;
     return;
   }
-  const double hn = norms[0], bn = norms[1], xn = norms[4], rn = norms[5];
+  const double hn = norms[0], bn = norms[1];
   const double denom = hn * xn + bn;
   const double be = denom > 0.0 ? rn / denom : 0.0;
   st->iters = it + 1;
@@ -1942,7 +1941,7 @@ MixedLayout mixed_layout(int64_t m) {
   ly.z32 = off;    off += al((size_t)m * 4);
   ly.r = off;      off += al((size_t)m * 8);
   ly.rowmax = off; off += al((size_t)m * 8);
-  ly.xmax = off;   off += al((size_t)ly.nvec_blocks * 8);
+  ly.xmax = off;   off += al((size_t)ly.B * 8);   // per 64-row block of the backward solve
   ly.rmax = off;   off += al((size_t)ly.nrow_blocks * 8);
   ly.bmax = off;   off += al((size_t)ly.nvec_blocks * 8);
   ly.norms = off;  off += al(8 * 8);
@@ -2067,18 +2066,14 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
   SPSVM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)m * 8, s));
   SPSVM_CUDA_TRY(cudaMemsetAsync(tagged_region, 0, tagged_bytes, s));
   SPSVM_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(RefineState), s));
-  SPSVM_CUDA_TRY(cudaMemcpyAsync(r, b, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
-  absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax);
+  // block maxima of |b| (||b||_inf) and the first right-hand side z = (float) b
+  absmax_blocks<<<vb, MX_T, 0, s>>>(b, m, bmax, z32);
   SPSVM_LAUNCH_CHECK();
-  // norms[0] = ||H + shift I||_inf, norms[1] = ||b||_inf
-  max3<<<1, MX_T, 0, s>>>(rowmax, m, bmax, ly.nvec_blocks, nullptr, 0, norms, nullptr);
-  SPSVM_LAUNCH_CHECK();
-  // One refinement step: z = (L L^T)^{-1} r in FP32, x += z, r = b - (H +
-  // shift I) x in FP64, then the stop word.  Every kernel of a step returns
-  // at once once the stop word is set.
+  // One refinement step: z = (L L^T)^{-1} r in FP32, x += z (with the
+  // backward solve), r = b - (H + shift I) x in FP64 and the next z =
+  // (float) r, then the norms and the stop word.  Every kernel of a step
+  // returns at once once the stop word is set.
   auto step = [&](int it) -> int {
-    to_f32_vec<<<vb, MX_T, 0, s>>>(r, m, z32, stop);
-    SPSVM_LAUNCH_CHECK();
     // tags 1, 2, ... (the tagged words start zeroed); tickets per step
     const unsigned tag = (unsigned)(it + 1);
     if (it > 0 && it % kTicketSteps == 0)
@@ -2094,18 +2089,17 @@ static int solve_mixed_impl(const double* H, int64_t m, int64_t ldh, double shif
           lr->V, lr->ldv, m, lr->Ci, lr->ldv, lr->s, lr->slices, lr->ldv, lr->k, zw, stop);
       SPSVM_LAUNCH_CHECK();
     }
-    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, z32, tk + 1, tag, wc, stop);
-    SPSVM_LAUNCH_CHECK();
-    add_f32<<<vb, MX_T, 0, s>>>(x, z32, m, xmax, stop);
+    trsv32_bwd<<<(unsigned)ly.B, SV_THREADS, 0, s>>>(L, ly.ldl, m, zw, xt, x, xmax, tk + 1, tag, wc,
+                                                     stop);
     SPSVM_LAUNCH_CHECK();
     if (vec)
-      residual_f64<true><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax, stop);
+      residual_f64<true><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, z32, rmax, stop);
     else
-      residual_f64<false><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, rmax, stop);
+      residual_f64<false><<<rb, MX_T, 0, s>>>(H, ldh, m, shift, b, x, r, z32, rmax, stop);
     SPSVM_LAUNCH_CHECK();
-    max3<<<1, MX_T, 0, s>>>(xmax, ly.nvec_blocks, rmax, ly.nrow_blocks, nullptr, 0, norms + 4, stop);
-    SPSVM_LAUNCH_CHECK();
-    refine_decide<<<1, 32, 0, s>>>(norms, it <= 1 ? factor_info : nullptr, it, tol, state);
+    refine_decide<<<1, MX_T, 0, s>>>(xmax, ly.B, rmax, ly.nrow_blocks, rowmax, m, bmax,
+                                     ly.nvec_blocks, norms, it <= 1 ? factor_info : nullptr, it, tol,
+                                     state);
     SPSVM_LAUNCH_CHECK();
     return SPSVM_OK;
   };
