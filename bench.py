@@ -196,6 +196,26 @@ def _oracle_fit_seconds(n, J):
     return time.perf_counter() - t0
 
 
+def gpu_sample_fit_seconds(sp, torch, precision="bf16split"):
+    """This library's fit on the CPU baseline's first sample (same rows,
+    d = 128, |J| = 256, kappa = 256, q = 64), event-timed after one warm-up:
+    the like-for-like partner of the oracle's time."""
+    from paper_1404_1066_gb300 import synth
+    n0, J0 = CPU_SAMPLES[0]
+    p = synth.gaussian_mixture(n=n0, d=128, budget=J0, seed=1003)
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    kw = dict(precision=precision, candidates=256, add_per_round=64, seed=1)
+    sp.spsvm_fit(X, y, p.gamma, p.lam, J0, 1e-6, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    sp.spsvm_fit(X, y, p.gamma, p.lam, J0, 1e-6, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
 def cpu_baseline_run(steps=1, scaling=True):
     """The float64 oracle, as it stands, timed on the host cores: `steps`
     fits of the first sample (n = 4,000 rows of the same mixture, d = 128,
@@ -853,7 +873,8 @@ def run_ours(args):
                                     blas_threads=cb["blas_threads"], cpu_model=cb["cpu_model"],
                                     points=cb["points"], exponent_n=cb["exponent_n"],
                                     exponent_basis=cb["exponent_basis"],
-                                    full_size_estimate_s=cb["full_size_estimate_s"])
+                                    full_size_estimate_s=cb["full_size_estimate_s"],
+                                    gpu_same_sample_s=_leg(gpu_sample_fit_seconds, sp, torch))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
