@@ -764,6 +764,35 @@ def run_ours(args):
                                                        / np.maximum(1.0, np.abs(f.cpu().numpy())))))
         lowrank = _leg(lowrank_leg)
 
+    # the same fit with the Newton system factored in FP64 (the precision the
+    # method's description names; the default factors in FP32 and refines in
+    # FP64): fit time, steps and agreement of the decision values
+    fp64_factor = None
+    if args.fp64_factor:
+        def fp64_leg():
+            lib.spsvm_profile_enable(1)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            m64 = sp.spsvm_fit(X, y, p.gamma, p.lam, J, 1e-6, workspace=None, newton_solver="fp64",
+                               **opts)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            pl = {}
+            for k, name in enumerate(SLOTS):
+                if name not in ("cholesky", "solve"):
+                    continue
+                nm, L_, t_, w_ = C.c_char_p(), C.c_int64(), C.c_double(), C.c_double()
+                lib.spsvm_profile_read(k, C.byref(nm), C.byref(L_), C.byref(t_), C.byref(w_))
+                pl[name] = dict(launches=L_.value, ms=t_.value)
+            lib.spsvm_profile_enable(0)
+            f64 = m64.predict(Xq).cpu().numpy()
+            fr = f.cpu().numpy()
+            return dict(fit_s=a0.elapsed_time(a1) / 1e3, newton_steps=m64.info()["newton_steps"],
+                        status=m64.status, profile=pl,
+                        max_decision_diff=float(np.max(np.abs(f64 - fr) / np.maximum(1.0, np.abs(fr)))))
+        fp64_factor = _leg(fp64_leg)
+
     # FP32 form on the same workload (one fit), for the "vs FP32 form" leg
     fp32_form = None
     if args.fp32_form and prec != "fp32":
@@ -863,7 +892,8 @@ def run_ours(args):
                 fit=dict(newton_steps=info["newton_steps"], rounds=info["rounds"],
                          objective=info["objective"], status=info["status"]),
                 profile={k: v for k, v in prof.items() if v["launches"]},
-                fp32_form=fp32_form, lowrank=lowrank, growth_stop=growth, gram_stress=gram_stress,
+                fp32_form=fp32_form, lowrank=lowrank, fp64_factor=fp64_factor, growth_stop=growth,
+                gram_stress=gram_stress,
                 batched=batched, ovo=ovo,
                 exact_score=exact, serve=serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -905,6 +935,8 @@ def main():
                     help="heuristic vs exact one-dimensional selection score leg")
     ap.add_argument("--gram-stress", type=int, default=1,
                     help="a fit on an overlapping mixture where the Gram matrix carries real work")
+    ap.add_argument("--fp64-factor", type=int, default=1,
+                    help="leg: the same fit with the Newton system factored in FP64")
     ap.add_argument("--lowrank", type=int, default=1,
                     help="one fit with the low-rank correction of the Newton factor")
     ap.add_argument("--growth", type=int, default=1,
