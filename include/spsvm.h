@@ -61,7 +61,9 @@ extern "C" {
  *   FP32 kernel values).
  * Both forms store the kernel matrix K_nJ in FP32.  In both the Newton
  * system is, by default, factored in FP32 and solved with FP64 iterative
- * refinement to FP64 backward error (SPSVM_SOLVE_MIXED), or factored in FP64
+ * refinement to normwise backward error 1e-11 (SPSVM_SOLVE_MIXED: the fit
+ * takes the same Newton steps to the same minimiser as with an FP64 solve),
+ * or factored in FP64
  * (SPSVM_SOLVE_FP64, and the fallback of the mixed solve when its FP32
  * factor breaks down or the refinement stalls). */
 #define SPSVM_FP32    0
@@ -418,8 +420,9 @@ typedef struct spsvm_options {
                               H (two passes over K each); <= 0 -> none (default) */
   int32_t  record;         /* keep candidates / chosen per round for replay checks */
   void*    stream;         /* cudaStream_t for all work (NULL = default stream) */
-  int32_t  newton_solver;  /* SPSVM_SOLVE_MIXED (0): FP32 factor + FP64 refinement to FP64
-                              backward error, FP64 factorisation when that fails;
+  int32_t  newton_solver;  /* SPSVM_SOLVE_MIXED (0): FP32 factor + FP64 refinement to
+                              normwise backward error 1e-11, FP64 factorisation when
+                              that fails;
                               SPSVM_SOLVE_FP64: FP64 factorisation always */
   int32_t  score;          /* basis selection: SPSVM_SCORE_HEURISTIC (0), Section 4's
                               second-order estimate g^2 / (2h); SPSVM_SCORE_EXACT, the

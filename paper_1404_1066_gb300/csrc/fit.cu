@@ -359,10 +359,13 @@ constexpr double kFloorGuard = 1e-3;
 // gradient level (relative to ||r||) that ends the iteration of a fit that
 // runs with a diagonal jitter
 constexpr double kJitterRelTol = 5e-6;
-// mixed Newton solve: refinement steps and the FP64-level backward error it
-// must reach (else the FP64 factorisation is used)
+// mixed Newton solve: refinement steps and the normwise backward error it
+// must reach (else the FP64 factorisation is used).  1e-11 is about 1e5 units
+// of FP64 rounding: the direction's relative error stays below cond(H) 1e-11,
+// far under what the Newton stop (on the exact gradient) can see, and the
+// fit's steps and minimiser are those of an FP64 solve.
 constexpr int32_t kMixedIters = 30;
-constexpr double kMixedTol = 1e-13;
+constexpr double kMixedTol = 1e-11;
 
 struct Fit {
   const float* X;
