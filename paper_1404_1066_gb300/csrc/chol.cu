@@ -780,12 +780,11 @@ __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // FP32 factor in one persistent launch over 64 x 64 tiles, left-looking.
 // Tile (i, j), i >= j, is C_ij - sum_{k<j} L_ik L_jk^T, then the factor of
-// the diagonal tile (i == j) or the solve X L_jj^T = C (i > j).  CTAs take
-// tiles by ticket, column by column with the diagonal tile first, so a tile
-// only waits for tiles with smaller tickets, which running CTAs hold or have
-// finished: the schedule progresses whatever the number of resident CTAs,
-// and columns overlap without a launch boundary between them.  A finished
-// tile publishes its flag (1 done, 2 abandoned); waits are bounded, and an
+// the diagonal tile (i == j) or the solve X L_jj^T = C (i > j).  One CTA
+// runs the chain of diagonal and sub-diagonal tiles; the others take the
+// rest by ticket, so columns overlap without a launch boundary between
+// them.  A finished tile publishes its flag (1 done, 2 abandoned, 3 the
+// partial a helper leaves for the chain); waits are bounded, and an
 // abandoned or timed-out dependency abandons the tile.
 // ---------------------------------------------------------------------------
 constexpr int DT = 64;          // tile
@@ -882,46 +881,68 @@ __device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __r
 
 // Tiles (i, j) of the factor, i >= j, left-looking: C_ij - sum_{k<j} L_ik
 // L_jk^T, then the factor of a diagonal tile or the solve X L_jj^T = C of an
-// off-diagonal one.  The chain of the factorisation runs through the
-// diagonal tiles and the tiles just below them.  So one CTA, the unit U(s),
-// takes the last steps of both: a helper P(s) accumulates the tile
-// (s, s-1) over k < s-1 and leaves it in place (flag 3, partial); U(s)
-// accumulates (s, s) over k < s-1, then solves (s, s-1) against (s-1, s-1)
-// once that is factored, applies the result to (s, s) from its own
-// registers and factors (s, s) -- one hand-off between CTAs per 64-column
-// step, with the accumulation work spread as before.  Tickets go (0, 0),
-// then for s = 1, 2, ...: P(s), U(s), the other tiles of column s-1 (rows
-// s+1 ..); every tile waits only for tiles of smaller tickets.
+// off-diagonal one.  The chain of the factorisation runs through each
+// diagonal tile and the tile just below it, and one CTA (the one that
+// draws ticket 0) runs that chain alone: for s = 1, 2, ... it takes the partials of (s, s-1) and
+// (s, s) (both accumulated over k < s-1 by helper CTAs and left in place,
+// flag 3), solves (s, s-1) against (s-1, s-1), which it factored itself and
+// keeps in shared memory, applies it to (s, s) and factors (s, s) -- no
+// hand-off between CTAs on the chain.  The other tickets are, for s = 1,
+// 2, ...: P(s) (the partial of (s, s-1)), D(s) (the partial of (s, s)),
+// then the tiles (s+1 .., s-1).  With the chain's step s placed right after
+// D(s), every piece of work waits only for pieces before it, and the chain
+// and each ticket are held by running CTAs: the schedule progresses
+// whatever the number of resident CTAs.  A helper publishes its partial
+// (flag 3) only over flag 0, so an abandoned chain step (flag 2) stays
+// abandoned.
 
-// Ticket tk -> work: kind 0 the tile (0, 0), kind 1 the unit U(s) (i = s,
-// j = s - 1), kind 2 the tile (i, j), kind 3 the helper P(s) (i = s,
-// j = s - 1); -1 past the end.
+// Ticket tk -> work: kind 0 the chain, kind 2 the tile (i, j), kind 3 the
+// helper P(s) (i = s, j = s - 1), kind 4 the helper D(s) (i = j = s); -1
+// past the end.
 __device__ __forceinline__ int dag_decode(int64_t tk, int64_t T, int64_t* i, int64_t* j) {
-  if (tk <= 0) {
-    *i = 0;
-    *j = 0;
-    return tk == 0 ? 0 : -1;
-  }
-  // block s (s >= 1) = P(s), U(s), then rows s+1 .. T-1 of column s-1:
+  *i = 0;
+  *j = 0;
+  if (tk <= 0) return tk == 0 ? 0 : -1;
+  tk -= 1;
+  // block s (s >= 1) = P(s), D(s), then rows s+1 .. T-1 of column s-1:
   // T - s + 1 tickets
-  int64_t s = 1, start = 1;
+  int64_t s = 1, start = 0;
   while (s < T && start + (T - s + 1) <= tk) {
     start += T - s + 1;
     ++s;
   }
   if (s >= T) return -1;
   const int64_t e = tk - start;
-  *j = s - 1;
-  if (e <= 1) {
+  if (e == 0) {
     *i = s;
-    return e == 0 ? 3 : 1;
+    *j = s - 1;
+    return 3;
+  }
+  if (e == 1) {
+    *i = s;
+    *j = s;
+    return 4;
   }
   *i = s + e - 1;
+  *j = s - 1;
   return 2;
 }
 
-// Waits (bounded) for the helper's partial of a unit's off-diagonal tile:
-// true on flag 3, false when it was abandoned or the wait gave up.
+// Waits (bounded) for a factored diagonal tile: 1 when done, 2 when
+// abandoned or the wait gave up (flag 3, the helper's partial, still waits).
+__device__ unsigned dag_wait_final(const unsigned* f, const WaitCtx& w) {
+  const uint32_t lim = wait_limit(w, 1u << 23);
+  for (uint32_t it = 0; it < lim; ++it) {
+    const unsigned v = ld_acquire_u32(f);
+    if (v == 1u || v == 2u) return v;
+    if (it >= 16) __nanosleep(64);
+  }
+  wait_gave_up(w, 224);
+  return 2u;
+}
+
+// Waits (bounded) for a helper's partial tile: true on flag 3, false when it
+// was abandoned or the wait gave up.
 __device__ bool dag_wait_partial(const unsigned* f, const WaitCtx& w) {
   const uint32_t lim = wait_limit(w, 1u << 23);
   for (uint32_t it = 0; it < lim; ++it) {
@@ -1087,64 +1108,98 @@ __device__ __forceinline__ void dag_store_diag(const float (&acc)[4][4], float* 
   }
 }
 
-// X L_jj^T = C for an off-diagonal tile in registers, by pivot blocks of 4
-// columns, with S[c][r] = L_jj[r][c] staged in shared memory and rd the
-// reciprocals of its diagonal.  The rows of a half warp (one row group)
-// depend on nothing else: its owner lane (tx = p) solves its 4 x 4 block
-// against the diagonal block L_pp, hands the block to the half warp by
-// shuffle, and the lanes right of it apply it -- no barrier in the loop.
-__device__ __forceinline__ void dag_solve_sub(float (&acc)[4][4], const float (*S)[DP],
+// X L_jj^T = C for an off-diagonal tile held transposed in shared memory
+// (XT[c][r] = X[r][c], C on entry), with S[c][r] = L_jj[r][c] and rd the
+// reciprocals of its diagonal, by blocks of 16 columns: threads 0..63 each
+// solve one row of the block against its 16 x 16 diagonal part, then every
+// thread applies the block to the later ones.  The rows are independent, so
+// the chain per column is one multiply and one FMA in one thread, and the
+// bulk of the work is the block updates across the CTA.  All threads; ends
+// with a barrier.
+__device__ __forceinline__ void dag_solve_blk(float (*XT)[DP], const float (*S)[DP],
                                               const float* __restrict__ rd) {
-  const int t = threadIdx.x, tx = t & 15, lane = t & 31;
-#pragma unroll 2
-  for (int p = 0; p < DT / 4; ++p) {
-    float lpp[4][4], rdp[4];
-    float4 lv[4];
+  const int t = threadIdx.x;
+#pragma unroll 1
+  for (int q = 0; q < DT / 16; ++q) {
+    if (t < DT) {
+      float x[16];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      rdp[c] = rd[4 * p + c];
+      for (int k = 0; k < 16; ++k) x[k] = XT[16 * q + k][t];
 #pragma unroll
-      for (int l = 0; l < c; ++l) lpp[c][l] = S[4 * p + l][4 * p + c];
-      lv[c] = *reinterpret_cast<const float4*>(&S[4 * p + c][4 * tx]);   // L_jj[4tx+b][4p+c]
+      for (int k = 0; k < 16; ++k) {
+        x[k] *= rd[16 * q + k];
+        const float* lr = &S[16 * q + k][16 * q];   // L_jj[16 q + k2][16 q + k]
+#pragma unroll
+        for (int k2 = k + 1; k2 < 16; ++k2) x[k2] = fmaf(-x[k], lr[k2], x[k2]);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) XT[16 * q + k][t] = x[k];
     }
-    if (tx == p) {
+    __syncthreads();
+    if (q + 1 < DT / 16) {
+      // rows 4 r4 .. +3 of the later blocks' column c: C -= X_q L_jj[., q]^T
+      const int r4 = t >> 4, c = t & 15;
+      float xv[16][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = *reinterpret_cast<const float4*>(&XT[16 * q + k][4 * r4]);
+        xv[k][0] = v.x; xv[k][1] = v.y; xv[k][2] = v.z; xv[k][3] = v.w;
+      }
+      for (int qb = q + 1; qb < DT / 16; ++qb) {
+        const float4 o = *reinterpret_cast<const float4*>(&XT[16 * qb + c][4 * r4]);
+        float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          float v = acc[a][c];
+        for (int k = 0; k < 16; ++k) {
+          const float l = S[16 * q + k][16 * qb + c];
 #pragma unroll
-          for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lpp[c][l], v);
-          acc[a][c] = v * rdp[c];
+          for (int e = 0; e < 4; ++e) ov[e] = fmaf(-xv[k][e], l, ov[e]);
         }
-    }
-    float x[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int l = 0; l < 4; ++l) x[a][l] = __shfl_sync(0xffffffffu, acc[a][l], (lane & 16) | p);
-    if (tx > p) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        acc[a][0] -= x[a][0] * lv[0].x + x[a][1] * lv[1].x + x[a][2] * lv[2].x + x[a][3] * lv[3].x;
-        acc[a][1] -= x[a][0] * lv[0].y + x[a][1] * lv[1].y + x[a][2] * lv[2].y + x[a][3] * lv[3].y;
-        acc[a][2] -= x[a][0] * lv[0].z + x[a][1] * lv[1].z + x[a][2] * lv[2].z + x[a][3] * lv[3].z;
-        acc[a][3] -= x[a][0] * lv[0].w + x[a][1] * lv[1].w + x[a][2] * lv[2].w + x[a][3] * lv[3].w;
+        *reinterpret_cast<float4*>(&XT[16 * qb + c][4 * r4]) = make_float4(ov[0], ov[1], ov[2], ov[3]);
       }
     }
+    __syncthreads();
   }
+}
+
+// XT[c][r] = L[r0 + r][c0 + c] (zeros past m): thread (r, 16-column group).
+__device__ __forceinline__ void dag_load_T(float (*XT)[DP], const float* __restrict__ L, int64_t ldl,
+                                           int64_t m, int64_t r0, int64_t c0) {
+  const int t = threadIdx.x, r = t & (DT - 1), g = t >> 6;
+  const int64_t gr = r0 + r;
+#pragma unroll
+  for (int k4 = 0; k4 < 4; ++k4) {
+    const float4 v = gr < m ? __ldcg(reinterpret_cast<const float4*>(L + gr * ldl + c0 + 16 * g) + k4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    XT[16 * g + 4 * k4 + 0][r] = v.x;
+    XT[16 * g + 4 * k4 + 1][r] = v.y;
+    XT[16 * g + 4 * k4 + 2][r] = v.z;
+    XT[16 * g + 4 * k4 + 3][r] = v.w;
+  }
+}
+
+// L[r0 + r][c0 + c] = XT[c][r] for rows below m.
+__device__ __forceinline__ void dag_store_T(const float (*XT)[DP], float* __restrict__ L, int64_t ldl,
+                                            int64_t m, int64_t r0, int64_t c0) {
+  const int t = threadIdx.x, r = t & (DT - 1), g = t >> 6;
+  const int64_t gr = r0 + r;
+  if (gr >= m) return;
+#pragma unroll
+  for (int k4 = 0; k4 < 4; ++k4)
+    __stcg(reinterpret_cast<float4*>(L + gr * ldl + c0 + 16 * g) + k4,
+           make_float4(XT[16 * g + 4 * k4][r], XT[16 * g + 4 * k4 + 1][r], XT[16 * g + 4 * k4 + 2][r],
+                       XT[16 * g + 4 * k4 + 3][r]));
 }
 
 // Waits for the factored diagonal tile (j, j), stages it transposed into S
 // with the reciprocals of its diagonal in rd, and solves the off-diagonal
-// tile in acc against it.  All threads; false when the tile was abandoned or
-// the wait gave up.
-__device__ bool dag_sub_from_diag(float (&acc)[4][4], const float* __restrict__ L, int64_t ldl,
+// tile held transposed in XT against it.  All threads; false when the tile
+// was abandoned or the wait gave up.
+__device__ bool dag_sub_from_diag(float (*XT)[DP], const float* __restrict__ L, int64_t ldl,
                                   int64_t m, int64_t j, const unsigned* __restrict__ flags,
                                   int64_t T, float (*S)[DP], float* __restrict__ rd,
                                   unsigned* st_s, const WaitCtx& wc) {
   const int t = threadIdx.x;
-  if (t == 0) *st_s = wait_flag(&flags[j * T + j], 224, wc);
+  if (t == 0) *st_s = dag_wait_final(&flags[j * T + j], wc);
   __syncthreads();
   if (*st_s != 1u) return false;
   float4 pd[4];
@@ -1153,7 +1208,7 @@ __device__ bool dag_sub_from_diag(float (&acc)[4][4], const float* __restrict__ 
   __syncthreads();
   if (t < DT) rd[t] = 1.0f / S[t][t];
   __syncthreads();
-  dag_solve_sub(acc, S, rd);
+  dag_solve_blk(XT, S, rd);
   return true;
 }
 
@@ -1200,6 +1255,15 @@ __device__ __forceinline__ void dag_publish(unsigned* flags, int64_t idx, bool o
   }
 }
 
+// Stages a register tile transposed into S (S[c][r] = tile[r][c]).
+__device__ __forceinline__ void dag_stage_regs(float (*S)[DP], const float (&acc)[4][4]) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) S[4 * tx + b][4 * ty + a] = acc[a][b];
+}
+
 __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
                                                       int64_t T, unsigned* __restrict__ flags,
                                                       unsigned* __restrict__ ticket,
@@ -1214,77 +1278,52 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   __shared__ float rd[DT];
   __shared__ int fail_s;
   const int t = threadIdx.x;
-  for (;;) {
-    if (t == 0) {
-      const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
-      int64_t i = 0, j = 0;
-      kind_s = dag_decode(tk, T, &i, &j);
-      tile_s[0] = i;
-      tile_s[1] = j;
-    }
-    __syncthreads();
-    const int kind = kind_s;
-    const int64_t i = tile_s[0], j = tile_s[1];
-    if (kind < 0) return;
-    float acc[4][4];
-    if (kind == 3) {
-      // the helper P(s): tile (s, s-1) accumulated over k < s-1, left in place
-      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, false);
-      const bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, false, flags, T, As, Bs,
-                                            &rdy_s, wc);
-      if (ok) dag_store_full(acc, L, ldl, m, i * DT, j * DT);
-      dag_publish(flags, i * T + j, ok, 3u);
-      continue;
-    }
-    if (kind != 1) {
-      // one tile: (0, 0), or an off-diagonal tile below the unit of its column
-      const bool diag = kind == 0;
-      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, diag);
-      bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, diag, flags, T, As, Bs, &rdy_s, wc);
-      if (ok && diag) {
-        const int f = dag_factor_diag(acc, Xb, rd, &fail_s);
-        if (f) {
-          if (t == 0) atomicCAS(info, 0, (int32_t)(j * DT + f));
-          ok = false;
-        } else {
-          dag_store_diag(acc, L, ldl, m, i * DT, j * DT);
-        }
-      } else if (ok) {
-        ok = dag_sub_from_diag(acc, L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
-        if (ok) dag_store_full(acc, L, ldl, m, i * DT, j * DT);
+  float acc[4][4];
+  if (t == 0) {
+    const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
+    int64_t i = 0, j = 0;
+    kind_s = dag_decode(tk, T, &i, &j);
+    tile_s[0] = i;
+    tile_s[1] = j;
+  }
+  __syncthreads();
+  if (kind_s == 0) {
+    // ---- the chain: (0, 0), then for s = 1, 2, ... (s, s-1) and (s, s).
+    // As[0] keeps the last factored diagonal tile transposed (with rd the
+    // reciprocals of its diagonal); As[1] stages the sub-diagonal tile.
+    int64_t s = 0;
+    bool ok = true;
+    dag_load_tile(acc, L, ldl, m, 0, 0, true);
+    {
+      const int f = dag_factor_diag(acc, Xb, rd, &fail_s);
+      if (f) {
+        if (t == 0) atomicCAS(info, 0, (int32_t)f);
+        ok = false;
+      } else {
+        dag_store_diag(acc, L, ldl, m, 0, 0);
       }
-      dag_publish(flags, i * T + j, ok);
-      continue;
     }
-    // the unit U(s), s = i: (s, s) over k < s-1, then the tile (s, s-1)
-    // below the diagonal from its helper's partial, then (s, s)
-    const int64_t s = i;
-    float accd[4][4];
-    dag_load_tile(accd, L, ldl, m, s * DT, s * DT, true);
-    bool ok = dag_accumulate<false>(accd, accd, L, ldl, m, s, s, j, true, flags, T, As, Bs, &rdy_s,
-                                    wc);
-    if (ok) {
-      if (t == 0) st_s = dag_wait_partial(&flags[s * T + j], wc) ? 1u : 2u;
+    dag_publish(flags, 0, ok);
+    for (s = 1; ok && s < T; ++s) {
+      dag_stage_regs(As[0], acc);   // L_{s-1,s-1} (its rd is current)
+      float accd[4][4];
+      // the helpers' partials of (s, s-1) and (s, s)
+      if (t == 0)
+        st_s = (dag_wait_partial(&flags[s * T + s - 1], wc) && dag_wait_partial(&flags[s * T + s], wc))
+                   ? 1u : 2u;
       __syncthreads();
-      ok = st_s == 1u;
-    }
-    if (ok) {
-      dag_load_tile(acc, L, ldl, m, s * DT, j * DT, false);   // the partial, acquired above
-      ok = dag_sub_from_diag(acc, L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
-    }
-    if (ok) dag_store_full(acc, L, ldl, m, s * DT, j * DT);
-    dag_publish(flags, s * T + j, ok);
-    if (ok) {
-      // (s, s) -= L_s,s-1 L_s,s-1^T from this CTA's registers: S[l][r] =
-      // L_s,s-1[r][l] (As[1] is free: the solve read As[0])
-      const int tx = t & 15, ty = t >> 4;
-      float (*S)[DP] = As[1];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) S[4 * tx + b][4 * ty + a] = acc[a][b];
+      if (st_s != 1u) {
+        ok = false;
+        break;
+      }
+      dag_load_T(As[1], L, ldl, m, s * DT, (s - 1) * DT);
+      dag_load_tile(accd, L, ldl, m, s * DT, s * DT, true);
       __syncthreads();
-      dag_update(accd, S, S);
+      dag_solve_blk(As[1], As[0], rd);
+      dag_store_T(As[1], L, ldl, m, s * DT, (s - 1) * DT);
+      dag_publish(flags, s * T + s - 1, true);
+      // (s, s) -= L_s,s-1 L_s,s-1^T (As[1] holds it transposed), then its factor
+      dag_update(accd, As[1], As[1]);
       __syncthreads();
       const int f = dag_factor_diag(accd, Xb, rd, &fail_s);
       if (f) {
@@ -1293,8 +1332,70 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
       } else {
         dag_store_diag(accd, L, ldl, m, s * DT, s * DT);
       }
+      dag_publish(flags, s * T + s, ok);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = accd[a][b];
+      __syncthreads();   // As[0] is rewritten at the top of the next step
     }
-    dag_publish(flags, s * T + s, ok);
+    if (!ok) {
+      // the rest of the chain is abandoned: its waiters give up at once
+      __syncthreads();
+      if (t == 0) {
+        __threadfence();
+        for (int64_t r = s; r < T; ++r) {
+          if (r > 0) st_release_u32(&flags[r * T + r - 1], 2u);
+          st_release_u32(&flags[r * T + r], 2u);
+        }
+      }
+    }
+    return;
+  }
+  // ---- helpers and the other tiles, by ticket
+  for (bool first = true;; first = false) {
+    if (!first) {
+      __syncthreads();   // every thread has read the last ticket's kind_s, tile_s
+      if (t == 0) {
+        const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
+        int64_t i = 0, j = 0;
+        kind_s = dag_decode(tk, T, &i, &j);
+        tile_s[0] = i;
+        tile_s[1] = j;
+      }
+      __syncthreads();
+    }
+    const int kind = kind_s;
+    const int64_t i = tile_s[0], j = tile_s[1];
+    if (kind < 0) return;
+    if (kind == 3 || kind == 4) {
+      // a helper: (s, s-1) or (s, s) accumulated over k < s-1, left in place
+      const bool diag = kind == 4;
+      const int64_t kend = i - 1;
+      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, diag);
+      const bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, diag ? i : j, kend, diag, flags, T,
+                                            As, Bs, &rdy_s, wc);
+      if (ok) {
+        if (diag) dag_store_diag(acc, L, ldl, m, i * DT, j * DT);
+        else dag_store_full(acc, L, ldl, m, i * DT, j * DT);
+      }
+      __syncthreads();   // the partial's stores, then one release over flag 0 only
+      if (t == 0) {
+        __threadfence();
+        atomicCAS(&flags[i * T + j], 0u, ok ? 3u : 2u);
+      }
+      continue;
+    }
+    // an off-diagonal tile below the chain: accumulate, then solve against
+    // its column's diagonal tile
+    dag_load_tile(acc, L, ldl, m, i * DT, j * DT, false);
+    bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, false, flags, T, As, Bs, &rdy_s, wc);
+    if (ok) {
+      dag_stage_regs(As[1], acc);   // transposed, for the solve
+      ok = dag_sub_from_diag(As[1], L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
+    }
+    if (ok) dag_store_T(As[1], L, ldl, m, i * DT, j * DT);
+    dag_publish(flags, i * T + j, ok);
   }
 }
 
@@ -1970,7 +2071,7 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
   char* w = static_cast<char*>(work);
   float* L = reinterpret_cast<float*>(w + ly.L);
   unsigned* dflags = reinterpret_cast<unsigned*>(w + ly.dag);
-  // tickets: one per tile (the helper P(s) stands for the tile (s, s-1))
+  // block 0 runs the chain; the others take T (T + 1) / 2 - 1 tickets
   const int64_t T = ly.tiles, ntiles = T * (T + 1) / 2;
   SPSVM_CUDA_TRY(cudaMemsetAsync(dflags, 0, (size_t)(T * T + 1) * 4, s));
   to_f32_shift<<<(unsigned)m, MX_T, 0, s>>>(H, ldh, m, shift, L, ly.ldl,
