@@ -666,6 +666,13 @@ int spsvm_device_status(int32_t* code);
  * makes waits give up early, for testing the timeout path: results of the
  * affected kernels are then incomplete and the status reports TIMEOUT. */
 void spsvm_set_wait_limit(uint32_t polls);
+/* Grid of every FP32 tile factorisation (spsvm_cholesky_mixed and the fits'
+ * mixed Newton solves) launched from now on: at most `ctas` CTAs (0, the
+ * default, one per SM).  One CTA completes the factorisation on its own (it
+ * runs the chain of diagonal tiles and takes the other tiles' work while it
+ * waits), so any grid gives the same factor; a small grid is slower and
+ * serves to test that. */
+void spsvm_set_factor_ctas(uint32_t ctas);
 
 const char* spsvm_strerror(int code);
 const char* spsvm_last_error(void);

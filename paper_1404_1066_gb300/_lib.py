@@ -165,6 +165,7 @@ SIGNATURES = {
     "spsvm_device_status": (_I32, [C.POINTER(_I32)]),
     "spsvm_stream_status": (_I32, [_P, C.POINTER(_I32)]),
     "spsvm_set_wait_limit": (None, [C.c_uint32]),
+    "spsvm_set_factor_ctas": (None, [C.c_uint32]),
     "spsvm_strerror": (C.c_char_p, [_I32]),
     "spsvm_last_error": (C.c_char_p, []),
     "spsvm_version": (C.c_char_p, []),

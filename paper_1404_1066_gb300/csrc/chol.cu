@@ -2,6 +2,7 @@
 // the Newton system of Section 4's reoptimisation.  Blocked right-looking
 // factorisation with 64 x 64 blocks: diagonal block in shared memory, panel
 // triangular solve, trailing symmetric update.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -787,10 +788,14 @@ __global__ void __launch_bounds__(MX_T) to_f32_shift(const double* __restrict__ 
 // partial a helper leaves for the chain); waits are bounded, and an
 // abandoned or timed-out dependency abandons the tile.
 // ---------------------------------------------------------------------------
+// Upper bound on the tile factorisation's grid (0: one CTA per SM).
+std::atomic<uint32_t> g_factor_ctas{0};
+
 constexpr int DT = 64;          // tile
 constexpr int DP = DT + 4;      // staging rows, 16-byte aligned
 constexpr int DAG_T = 256;
-constexpr size_t DAG_SMEM = (size_t)4 * DT * DP * sizeof(float);   // two stages of (A, B)
+// two stages of (A, B), and the chain's last diagonal tile
+constexpr size_t DAG_SMEM = (size_t)5 * DT * DP * sizeof(float);
 
 // Rows r0 .. r0+63 (zeros past m), columns c0 .. c0+63 of L as 16-byte
 // vectors; a warp covers 8 rows x 64 contiguous bytes per vector.
@@ -890,9 +895,11 @@ __device__ int64_t dag_scan(const unsigned* __restrict__ fi, const unsigned* __r
 // hand-off between CTAs on the chain.  The other tickets are, for s = 1,
 // 2, ...: P(s) (the partial of (s, s-1)), D(s) (the partial of (s, s)),
 // then the tiles (s+1 .., s-1).  With the chain's step s placed right after
-// D(s), every piece of work waits only for pieces before it, and the chain
-// and each ticket are held by running CTAs: the schedule progresses
-// whatever the number of resident CTAs.  A helper publishes its partial
+// D(s), every piece of work waits only for pieces before it.  While the
+// chain waits for P(s) and D(s) it takes any ticket up to D(s) that no CTA
+// holds yet and does that work itself, so the schedule progresses whatever
+// the number of resident CTAs, down to the chain's own (launches on other
+// streams may hold the rest of the GPU).  A helper publishes its partial
 // (flag 3) only over flag 0, so an abandoned chain step (flag 2) stays
 // abandoned.
 
@@ -928,6 +935,11 @@ __device__ __forceinline__ int dag_decode(int64_t tk, int64_t T, int64_t* i, int
   return 2;
 }
 
+// The ticket of D(s): 1 + the tickets of blocks 1 .. s-1, + 1.
+__device__ __forceinline__ int64_t dag_ticket_of_D(int64_t s, int64_t T) {
+  return 1 + (s - 1) * (T + 1) - (s - 1) * s / 2 + 1;
+}
+
 // Waits (bounded) for a factored diagonal tile: 1 when done, 2 when
 // abandoned or the wait gave up (flag 3, the helper's partial, still waits).
 __device__ unsigned dag_wait_final(const unsigned* f, const WaitCtx& w) {
@@ -939,20 +951,6 @@ __device__ unsigned dag_wait_final(const unsigned* f, const WaitCtx& w) {
   }
   wait_gave_up(w, 224);
   return 2u;
-}
-
-// Waits (bounded) for a helper's partial tile: true on flag 3, false when it
-// was abandoned or the wait gave up.
-__device__ bool dag_wait_partial(const unsigned* f, const WaitCtx& w) {
-  const uint32_t lim = wait_limit(w, 1u << 23);
-  for (uint32_t it = 0; it < lim; ++it) {
-    const unsigned v = ld_acquire_u32(f);
-    if (v == 3u) return true;
-    if (v != 0u) return false;
-    if (it >= 16) __nanosleep(64);
-  }
-  wait_gave_up(w, 225);
-  return false;
 }
 
 // acc1 -= sum_{k<kend} L_ik L_jk^T (L_ik L_ik^T when same) as the tiles of
@@ -1015,78 +1013,125 @@ __device__ bool dag_accumulate(float (&acc1)[4][4], float (&acc2)[4][4],
   return ok;
 }
 
-// Factor of a diagonal tile held in registers (thread (ty, tx): rows 4 ty ..
-// +3, columns 4 tx .. +3), right-looking over 16 pivot blocks of 4 columns:
-// a pivot costs a few dependent instructions in one thread and a barrier,
-// not a chain of shuffles.  All threads; returns 0, or 1 + the tile column
-// of the first non-positive pivot.  P: 2 x DT float4 of shared memory.
-__device__ int dag_factor_diag(float (&acc)[4][4], float4* __restrict__ Xb, float* __restrict__ rd,
-                               int* fail_s) {
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+// Factor of a diagonal tile held transposed in shared memory (AT[c][r] =
+// A[r][c], lower part; the rest is ignored), in place: AT[c][r] = L[r][c],
+// rd the reciprocals of L's diagonal.  By blocks of 16 columns: one warp
+// factors the 16 x 16 diagonal block (lane i holds row i; the two entries
+// of row c + 2 that the next pivots need travel by shuffle ahead of the
+// column update, so the chain per column is one reciprocal square root and
+// two FMAs), then one thread per row solves the panel below against it, then
+// the CTA applies the panel to the later column blocks.  All threads;
+// returns 0, or 1 + the tile column of the first non-positive pivot.
+__device__ int dag_factor_blk(float (*AT)[DP], float* __restrict__ rd, int* fail_s) {
+  const int t = threadIdx.x;
   if (t == 0) *fail_s = 0;
-  for (int p = 0; p < DT / 4; ++p) {
-    float4* P = Xb + (p & 1) * DT;
-    if (ty == p && tx == p) {   // the 4 x 4 diagonal block
-      int f = 0;
+#pragma unroll 1
+  for (int q = 0; q < DT / 16; ++q) {
+    const int b = 16 * q;
+    if (t < 32) {
+      const int i = t & 15;   // lanes 16..31 repeat lanes 0..15
+      float g[16];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float d = acc[c][c];
-        if (f == 0 && (!(d > 0.0f) || !(d < 3.0e38f))) f = c + 1;
-        if (f == 0) {
-          const float y = rsqrt_t(d);
-          acc[c][c] = d * y;
-          rd[4 * p + c] = y;
+      for (int j = 0; j < 16; ++j) g[j] = AT[b + j][b + i];
+      // pivot d, and row c + 1's entries (c + 1, c + 1), (c + 1, c)
+      float d = __shfl_sync(0xffffffffu, g[0], 0);
+      float An = __shfl_sync(0xffffffffu, g[1], 1), Bn = __shfl_sync(0xffffffffu, g[0], 1);
+      int fail = 0;
 #pragma unroll
-          for (int r = c + 1; r < 4; ++r) acc[r][c] *= y;
-#pragma unroll
-          for (int c2 = c + 1; c2 < 4; ++c2)
-#pragma unroll
-            for (int r = c2; r < 4; ++r) acc[r][c2] = fmaf(-acc[r][c], acc[c2][c], acc[r][c2]);
+      for (int c = 0; c < 16; ++c) {
+        fail = (fail == 0 && !(d > 0.0f && d < 3.0e38f)) ? c + 1 : fail;
+        const float y = rsqrt_t(d);
+        const float l = g[c] * y;    // L[i][c] (meaningful for i > c)
+        const float lb = Bn * y;     // L[c + 1][c]
+        const float dn = fmaf(-lb, lb, An);
+        float An2 = 0.0f, Bn2 = 0.0f;
+        if (c + 2 < 16) {
+          An2 = __shfl_sync(0xffffffffu, fmaf(-l, l, g[c + 2]), c + 2);
+          Bn2 = __shfl_sync(0xffffffffu, fmaf(-l, lb, g[c + 1]), c + 2);
         }
-      }
-      if (f) *fail_s = 4 * p + f;
+        g[c] = (i == c) ? d * y : l;
+        if (c + 1 < 16) g[c + 1] = fmaf(-l, lb, g[c + 1]);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) P[4 * p + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        for (int j = c + 2; j < 16; ++j) g[j] = fmaf(-l, __shfl_sync(0xffffffffu, l, j), g[j]);
+        if (t == 0) rd[b + c] = y;
+        d = dn;
+        An = An2;
+        Bn = Bn2;
+      }
+      if (t < 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j <= i) AT[b + j][b + i] = g[j];
+      }
+      if (t == 0 && fail) *fail_s = b + fail;
     }
     __syncthreads();
-    if (*fail_s) break;
-    if (tx == p && ty > p) {   // panel block: X L_pp^T = C
-      float lp[4][4];
+    if (*fail_s) return *fail_s;
+    if (q + 1 == DT / 16) break;
+    // the panel below, one thread per row: X L_bb^T = A[rows][b .. b + 15]
+    if (t >= b + 16 && t < DT) {
+      float x[16];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float4 v = P[4 * p + a];
-        lp[a][0] = v.x; lp[a][1] = v.y; lp[a][2] = v.z; lp[a][3] = v.w;
+      for (int k = 0; k < 16; ++k) x[k] = AT[b + k][t];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        x[k] *= rd[b + k];
+        const float* lr = &AT[b + k][b];   // lr[k2] = L[b + k2][b + k]
+#pragma unroll
+        for (int k2 = k + 1; k2 < 16; ++k2) x[k2] = fmaf(-x[k], lr[k2], x[k2]);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          float v = acc[a][c];
-#pragma unroll
-          for (int l = 0; l < c; ++l) v = fmaf(-acc[a][l], lp[c][l], v);
-          acc[a][c] = v * rd[4 * p + c];
-        }
-#pragma unroll
-      for (int a = 0; a < 4; ++a) P[4 * ty + a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+      for (int k = 0; k < 16; ++k) AT[b + k][t] = x[k];
     }
     __syncthreads();
-    if (tx > p && ty >= tx) {   // trailing: C -= L_(ty,p) L_(tx,p)^T
-      float4 pa4[4], pb4[4];
+    // the later column blocks: A[r][cb] -= sum_k L[r][b + k] L[cb][b + k],
+    // rows 4 r4 .. +3 at or below each block
+    {
+      const int r4 = t >> 4, c = t & 15;
+      if (4 * r4 >= b + 16) {
+        float xv[16][4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        pa4[a] = P[4 * ty + a];
-        pb4[a] = P[4 * tx + a];
+        for (int k = 0; k < 16; ++k) {
+          const float4 v = *reinterpret_cast<const float4*>(&AT[b + k][4 * r4]);
+          xv[k][0] = v.x; xv[k][1] = v.y; xv[k][2] = v.z; xv[k][3] = v.w;
+        }
+        for (int qb = q + 1; qb < DT / 16 && 16 * qb <= 4 * r4; ++qb) {
+          const float4 o = *reinterpret_cast<const float4*>(&AT[16 * qb + c][4 * r4]);
+          float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float lv = AT[b + k][16 * qb + c];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ov[e] = fmaf(-xv[k][e], lv, ov[e]);
+          }
+          *reinterpret_cast<float4*>(&AT[16 * qb + c][4 * r4]) = make_float4(ov[0], ov[1], ov[2], ov[3]);
+        }
       }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          acc[a][b] -= pa4[a].x * pb4[b].x + pa4[a].y * pb4[b].y + pa4[a].z * pb4[b].z +
-                       pa4[a].w * pb4[b].w;
     }
+    __syncthreads();
   }
-  __syncthreads();
-  return *fail_s;
+  return 0;
+}
+
+// Lower part of a factored diagonal tile held transposed (AT[c][r] =
+// L[r][c]) to L, rows below m only.
+__device__ __forceinline__ void dag_store_diag_T(const float (*AT)[DP], float* __restrict__ L,
+                                                 int64_t ldl, int64_t m, int64_t r0, int64_t c0) {
+  const int t = threadIdx.x, r = t & (DT - 1), g = t >> 6;
+  const int64_t gr = r0 + r;
+  if (gr >= m || 16 * g > r) return;
+  float* dst = L + gr * ldl + c0 + 16 * g;
+  if (16 * g + 15 <= r) {
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4)
+      __stcg(reinterpret_cast<float4*>(dst) + k4,
+             make_float4(AT[16 * g + 4 * k4][r], AT[16 * g + 4 * k4 + 1][r], AT[16 * g + 4 * k4 + 2][r],
+                         AT[16 * g + 4 * k4 + 3][r]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (16 * g + k <= r) __stcg(dst + k, AT[16 * g + k][r]);
+  }
 }
 
 // Lower part of a factored diagonal tile to L (rows below m only).
@@ -1264,6 +1309,46 @@ __device__ __forceinline__ void dag_stage_regs(float (*S)[DP], const float (&acc
     for (int b = 0; b < 4; ++b) S[4 * tx + b][4 * ty + a] = acc[a][b];
 }
 
+// One ticket's work (all threads): a helper's partial (kinds 3 and 4) or a
+// tile below the chain (kind 2).  Uses As, Bs, rd and acc; ends with the
+// tile's publish.
+__device__ __forceinline__ void dag_ticket_work(int kind, int64_t i, int64_t j, float* __restrict__ L,
+                                                int64_t ldl, int64_t m, int64_t T,
+                                                unsigned* __restrict__ flags, float (*As)[DT][DP],
+                                                float (*Bs)[DT][DP], float* __restrict__ rd,
+                                                int64_t* rdy_s, unsigned* st_s, const WaitCtx& wc) {
+  const int t = threadIdx.x;
+  float acc[4][4];
+  if (kind == 3 || kind == 4) {
+    // a helper: (s, s-1) or (s, s) accumulated over k < s-1, left in place
+    const bool diag = kind == 4;
+    const int64_t kend = i - 1;
+    dag_load_tile(acc, L, ldl, m, i * DT, j * DT, diag);
+    const bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, diag ? i : j, kend, diag, flags, T,
+                                          As, Bs, rdy_s, wc);
+    if (ok) {
+      if (diag) dag_store_diag(acc, L, ldl, m, i * DT, j * DT);
+      else dag_store_full(acc, L, ldl, m, i * DT, j * DT);
+    }
+    __syncthreads();   // the partial's stores, then one release over flag 0 only
+    if (t == 0) {
+      __threadfence();
+      atomicCAS(&flags[i * T + j], 0u, ok ? 3u : 2u);
+    }
+    return;
+  }
+  // an off-diagonal tile below the chain: accumulate, then solve against its
+  // column's diagonal tile
+  dag_load_tile(acc, L, ldl, m, i * DT, j * DT, false);
+  bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, false, flags, T, As, Bs, rdy_s, wc);
+  if (ok) {
+    dag_stage_regs(As[1], acc);   // transposed, for the solve
+    ok = dag_sub_from_diag(As[1], L, ldl, m, j, flags, T, As[0], rd, st_s, wc);
+  }
+  if (ok) dag_store_T(As[1], L, ldl, m, i * DT, j * DT);
+  dag_publish(flags, i * T + j, ok);
+}
+
 __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, int64_t ldl, int64_t m,
                                                       int64_t T, unsigned* __restrict__ flags,
                                                       unsigned* __restrict__ ticket,
@@ -1271,14 +1356,13 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   extern __shared__ __align__(16) float dag_smem[];
   float (*As)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem);
   float (*Bs)[DT][DP] = reinterpret_cast<float (*)[DT][DP]>(dag_smem + 2 * DT * DP);
-  float4* Xb = reinterpret_cast<float4*>(dag_smem + 2 * DT * DP);   // [2][DT] rows, in Bs
-  __shared__ int64_t tile_s[2], rdy_s;
-  __shared__ int kind_s;
+  float (*Cs)[DP] = reinterpret_cast<float (*)[DP]>(dag_smem + 4 * DT * DP);
+  __shared__ int64_t tile_s[2], rdy_s, took_s;
+  __shared__ int kind_s, chs_s;
   __shared__ unsigned st_s;
-  __shared__ float rd[DT];
+  __shared__ float rd[DT], rdc[DT];
   __shared__ int fail_s;
   const int t = threadIdx.x;
-  float acc[4][4];
   if (t == 0) {
     const int64_t tk = (int64_t)atomicAdd(ticket, 1u);
     int64_t i = 0, j = 0;
@@ -1289,55 +1373,91 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
   __syncthreads();
   if (kind_s == 0) {
     // ---- the chain: (0, 0), then for s = 1, 2, ... (s, s-1) and (s, s).
-    // As[0] keeps the last factored diagonal tile transposed (with rd the
-    // reciprocals of its diagonal); As[1] stages the sub-diagonal tile.
+    // Cs keeps the last factored diagonal tile transposed (with rdc the
+    // reciprocals of its diagonal); As[1] holds the sub-diagonal tile
+    // transposed, for its solve and for the update of (s, s).
     int64_t s = 0;
     bool ok = true;
-    dag_load_tile(acc, L, ldl, m, 0, 0, true);
     {
-      const int f = dag_factor_diag(acc, Xb, rd, &fail_s);
+      float acc[4][4];
+      dag_load_tile(acc, L, ldl, m, 0, 0, true);
+      dag_stage_regs(Cs, acc);
+    }
+    __syncthreads();
+    {
+      const int f = dag_factor_blk(Cs, rdc, &fail_s);
       if (f) {
         if (t == 0) atomicCAS(info, 0, (int32_t)f);
         ok = false;
       } else {
-        dag_store_diag(acc, L, ldl, m, 0, 0);
+        dag_store_diag_T(Cs, L, ldl, m, 0, 0);
       }
     }
     dag_publish(flags, 0, ok);
+    const uint32_t lim = wait_limit(wc, 1u << 23);
     for (s = 1; ok && s < T; ++s) {
-      dag_stage_regs(As[0], acc);   // L_{s-1,s-1} (its rd is current)
-      float accd[4][4];
-      // the helpers' partials of (s, s-1) and (s, s)
-      if (t == 0)
-        st_s = (dag_wait_partial(&flags[s * T + s - 1], wc) && dag_wait_partial(&flags[s * T + s], wc))
-                   ? 1u : 2u;
-      __syncthreads();
-      if (st_s != 1u) {
-        ok = false;
-        break;
+      // the helpers' partials of (s, s-1) and (s, s); meanwhile this CTA
+      // takes any ticket up to D(s) that nobody holds yet
+      const int64_t tkD = dag_ticket_of_D(s, T);
+      for (uint32_t idle = 0;;) {
+        if (t == 0) {
+          const unsigned fp = ld_acquire_u32(&flags[s * T + s - 1]);
+          const unsigned fd = ld_acquire_u32(&flags[s * T + s]);
+          int st = 0;   // 0 pending, 1 both ready, 2 abandoned
+          if (fp == 3u && fd == 3u) st = 1;
+          else if ((fp != 0u && fp != 3u) || (fd != 0u && fd != 3u)) st = 2;
+          int64_t took = -1;
+          if (st == 0) {
+            const unsigned cur = ld_relaxed_u32(ticket);
+            if ((int64_t)cur <= tkD && atomicCAS(ticket, cur, cur + 1u) == cur) took = cur;
+          }
+          chs_s = st;
+          took_s = took;
+        }
+        __syncthreads();
+        const int st = chs_s;
+        const int64_t took = took_s;
+        __syncthreads();   // read before thread 0 writes them again
+        if (st == 1) break;
+        if (st == 2) {
+          ok = false;
+          break;
+        }
+        if (took >= 0) {
+          int64_t i = 0, j = 0;
+          const int kind = dag_decode(took, T, &i, &j);
+          dag_ticket_work(kind, i, j, L, ldl, m, T, flags, As, Bs, rd, &rdy_s, &st_s, wc);
+          idle = 0;
+          continue;
+        }
+        if (++idle >= lim) {
+          if (t == 0) wait_gave_up(wc, 225);
+          ok = false;
+          break;
+        }
+        if (idle >= 16) __nanosleep(64);
       }
+      if (!ok) break;
+      float accd[4][4];
       dag_load_T(As[1], L, ldl, m, s * DT, (s - 1) * DT);
       dag_load_tile(accd, L, ldl, m, s * DT, s * DT, true);
       __syncthreads();
-      dag_solve_blk(As[1], As[0], rd);
+      dag_solve_blk(As[1], Cs, rdc);
       dag_store_T(As[1], L, ldl, m, s * DT, (s - 1) * DT);
       dag_publish(flags, s * T + s - 1, true);
       // (s, s) -= L_s,s-1 L_s,s-1^T (As[1] holds it transposed), then its factor
       dag_update(accd, As[1], As[1]);
+      dag_stage_regs(Cs, accd);   // the solve above was the last reader of L_{s-1,s-1}
       __syncthreads();
-      const int f = dag_factor_diag(accd, Xb, rd, &fail_s);
+      const int f = dag_factor_blk(Cs, rdc, &fail_s);
       if (f) {
         if (t == 0) atomicCAS(info, 0, (int32_t)(s * DT + f));
         ok = false;
       } else {
-        dag_store_diag(accd, L, ldl, m, s * DT, s * DT);
+        dag_store_diag_T(Cs, L, ldl, m, s * DT, s * DT);
       }
       dag_publish(flags, s * T + s, ok);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = accd[a][b];
-      __syncthreads();   // As[0] is rewritten at the top of the next step
+      __syncthreads();   // As[1] is rewritten at the top of the next step
     }
     if (!ok) {
       // the rest of the chain is abandoned: its waiters give up at once
@@ -1368,34 +1488,7 @@ __global__ void __launch_bounds__(DAG_T, 1) chol32_dag(float* __restrict__ L, in
     const int kind = kind_s;
     const int64_t i = tile_s[0], j = tile_s[1];
     if (kind < 0) return;
-    if (kind == 3 || kind == 4) {
-      // a helper: (s, s-1) or (s, s) accumulated over k < s-1, left in place
-      const bool diag = kind == 4;
-      const int64_t kend = i - 1;
-      dag_load_tile(acc, L, ldl, m, i * DT, j * DT, diag);
-      const bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, diag ? i : j, kend, diag, flags, T,
-                                            As, Bs, &rdy_s, wc);
-      if (ok) {
-        if (diag) dag_store_diag(acc, L, ldl, m, i * DT, j * DT);
-        else dag_store_full(acc, L, ldl, m, i * DT, j * DT);
-      }
-      __syncthreads();   // the partial's stores, then one release over flag 0 only
-      if (t == 0) {
-        __threadfence();
-        atomicCAS(&flags[i * T + j], 0u, ok ? 3u : 2u);
-      }
-      continue;
-    }
-    // an off-diagonal tile below the chain: accumulate, then solve against
-    // its column's diagonal tile
-    dag_load_tile(acc, L, ldl, m, i * DT, j * DT, false);
-    bool ok = dag_accumulate<false>(acc, acc, L, ldl, m, i, j, j, false, flags, T, As, Bs, &rdy_s, wc);
-    if (ok) {
-      dag_stage_regs(As[1], acc);   // transposed, for the solve
-      ok = dag_sub_from_diag(As[1], L, ldl, m, j, flags, T, As[0], rd, &st_s, wc);
-    }
-    if (ok) dag_store_T(As[1], L, ldl, m, i * DT, j * DT);
-    dag_publish(flags, i * T + j, ok);
+    dag_ticket_work(kind, i, j, L, ldl, m, T, flags, As, Bs, rd, &rdy_s, &st_s, wc);
   }
 }
 
@@ -2081,7 +2174,10 @@ extern "C" int spsvm_cholesky_mixed(const double* H, int64_t m, int64_t ldh, dou
                                       (int)DAG_SMEM));
   WaitCtx wc;
   SPSVM_TRY(wait_ctx(s, &wc));
-  chol32_dag<<<(unsigned)min64(ntiles, (int64_t)sm_count()), DAG_T, DAG_SMEM, s>>>(
+  int64_t grid = min64(ntiles, (int64_t)sm_count());
+  const uint32_t cap = g_factor_ctas.load(std::memory_order_relaxed);
+  if (cap > 0) grid = min64(grid, (int64_t)cap);
+  chol32_dag<<<(unsigned)grid, DAG_T, DAG_SMEM, s>>>(
       L, ly.ldl, m, T, dflags, dflags + T * T, info, wc);
   SPSVM_LAUNCH_CHECK();
   diag_inverse<float><<<(unsigned)ly.B, DI_T, 0, s>>>(L, ly.ldl, m);
@@ -2316,4 +2412,8 @@ extern "C" int spsvm_solve_lowrank(const double* H, int64_t m, int64_t ldh, cons
                 reinterpret_cast<float*>(w + ly.s), ly.ldv, ly.slices, k, (int32_t)ly.G};
   return solve_mixed_impl(H, m, ldh, 0.0, b, x, max_iter, tol, iters, backward_error, mixed_work,
                           mixed_bytes, &v, nullptr, stream);
+}
+
+extern "C" void spsvm_set_factor_ctas(uint32_t ctas) {
+  spsvm::g_factor_ctas.store(ctas, std::memory_order_relaxed);
 }

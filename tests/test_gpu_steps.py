@@ -525,3 +525,38 @@ def test_decision_split_is_deterministic_and_work_is_private(sp):
     assert torch.equal(fa, ra) and torch.equal(fb, rb)
     with pytest.raises(sp.SpsvmError):
         sp.spsvm_predict(m, Qa, work=wb[:16])
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3])
+def test_mixed_factor_completes_on_a_small_grid(sp, ctas):
+    """The tile factorisation completes with any number of resident CTAs,
+    down to one (launches on other streams may hold the rest of the GPU):
+    the CTA that runs the chain of diagonal tiles takes the other tiles'
+    work while it waits.  Grids of 1-3 CTAs against the full grid, on 17 and
+    5 tile rows (the last one ragged), with a breakdown at a late pivot."""
+    from paper_1404_1066_gb300 import _lib as L
+    lib = L.load()
+    g = np.random.default_rng(40 + ctas)
+    for m in (1050, 300):
+        A = g.standard_normal((m, m + 3)) / np.sqrt(m)
+        H = A @ A.T + 0.3 * np.eye(m)
+        b = g.standard_normal(m)
+        ref = sp.spsvm_solve_mixed(_t(H), _t(b))
+        lib.spsvm_set_factor_ctas(ctas)
+        try:
+            info, st, x, iters, be = sp.spsvm_solve_mixed(_t(H), _t(b))
+            Hb = H.copy()
+            Hb[m - 10, m - 10] = -5.0
+            info_b, st_b, _, _, _ = sp.spsvm_solve_mixed(_t(Hb), _t(b))
+        finally:
+            lib.spsvm_set_factor_ctas(0)
+        assert ref[0] == 0 and ref[1] == 0
+        assert info == 0 and st == 0, (info, st, iters, be)
+        xs, xr = x.cpu().numpy(), ref[2].cpu().numpy()
+        assert np.max(np.abs(xs - xr)) <= 1e-9 * np.max(np.abs(xr))
+        r = b - H @ xs
+        assert np.max(np.abs(r)) <= 1e-13 * (np.max(np.abs(H).sum(1)) * np.max(np.abs(xs)) + np.max(np.abs(b)))
+        # the FP32 factor breaks down at the planted pivot or before it
+        assert 1 <= info_b <= m - 9 and st_b is None, (info_b, st_b)
+        code = ctypes.c_int32()
+        assert lib.spsvm_device_status(ctypes.byref(code)) == 0, code.value
