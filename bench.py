@@ -1,8 +1,8 @@
 """SP-SVM benchmark on GB300.
 
 One step = one whole SP-SVM fit (row norms, candidate scoring, kernel-block
-growth, Newton reoptimisation with masked Gram, FP64 Cholesky, refinement and
-line search; Section 4, Eq. 4) followed by prediction on 100,000 held-out
+growth, Newton reoptimisation with masked Gram, the Newton solve (FP32 tile
+Cholesky with FP64 refinement by default) and line search; Section 4, Eq. 4) followed by prediction on 100,000 held-out
 queries, on the Gaussian-mixture workload n = 500,000, d = 128, |J| grown 64
 at a time from 256 candidates to 4,096.  Inputs stay resident in HBM; the
 kernel matrix (8.2 GB) and X (256 MB) are far larger than L2 (129 MB), so no
@@ -12,8 +12,9 @@ explicit L2 flush is needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU
 oracle on a bounded sample of the same workload on the host cores.
---micro cholesky [--sizes m1,m2,...] times the FP64 factorisation and solve
-of the Newton system alone (the profiles' capture command).
+--micro cholesky [--sizes m1,m2,...] times the Newton solve alone: the FP64
+factorisation and solve, and the FP32 tile factor with FP64 refinement (the
+profiles' capture command).
 """
 from __future__ import annotations
 
@@ -514,9 +515,10 @@ def run_micro_gram(args):
 
 
 def run_micro(args):
-    """FP64 Cholesky factorisation and solve of the Newton system alone, at
-    the given sizes: random SPD matrices A A^T / m + I / 2 (seeded), one
-    JSON line with event-timed milliseconds per factorisation and per solve."""
+    """The Newton solve alone at the given sizes, on random SPD matrices
+    A A^T / m + I / 2 (seeded): the FP64 factorisation and its solve, and the
+    FP32 tile factor with FP64 refinement (factor and refinement together,
+    and the refinement alone); one JSON line of event-timed milliseconds."""
     import torch
     import paper_1404_1066_gb300 as sp
     lib = sp.load()
